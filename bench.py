@@ -1,0 +1,447 @@
+#!/usr/bin/env python3
+"""Benchmark of the RANMAR hot path on GB300 (prints one JSON line).
+
+Workload: partitioned streams -- one seed (12345), 65,536 streams whose start
+states sit at k*J for J = 2^40, each producing 4,096 consecutive 24-bit
+outputs into a row-per-stream [65,536 x 4,096] uint32 array.  One step is one
+pass of the whole path: the jump of every stream (t^{kJ} mod phi, the
+linear combination of the 97 words, c in closed form) and the generation of
+all 2^28 outputs with the state written back.  Inputs are synthetic (the
+paper uses none).  `value` is outputs/s over the whole job.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank runs the same workload on its own k-range (weak
+scaling, no collective on the data path); rank 0 prints the line.  With
+--impl reference the CPU oracle is timed on a bounded sample of the same
+workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import ctypes
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "outputs/s & HBM fraction; jumps/s at J≈2^120; batched vs per-stream launch"
+UNIT = "outputs/s"
+L2_BYTES = 129 * 2**20
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+SMS = 152
+IMAD_PER_CLK_SM = 64          # 32-bit multiply-add results per clock per SM
+SQ_MACS = 97 * 98 // 2        # symmetric squaring of a degree-96 polynomial
+APPLY_MACS = 97 * 97          # sum_i b_i x_{i+k}, k = 0..96
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-extras", action="store_true", help="skip the side measurements")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+def dense_squarings(e: int) -> int:
+    return max(0, e.bit_length() - 7)
+
+
+def jump_macs(exps) -> int:
+    return sum(dense_squarings(int(e)) * SQ_MACS + APPLY_MACS for e in exps)
+
+
+def source_sha(*names) -> str:
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2512_00093_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str, sha: str):
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        rec = t.get(kernel)
+        if rec and rec.get("source_sha") == sha:
+            return rec
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].strip().lower() == "active"})
+        loaded = sorted(sm)[len(sm) // 4:] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_cores_used() -> int:
+    return 1
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(seconds: float, start_k: int, w):
+    """The CPU oracle, as it stands, on consecutive streams of the workload
+    (jump + 4,096 outputs each) until `seconds` have passed."""
+    from oracle import oracle
+    o = oracle()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        o.stream(w.seed, (start_k + n) * w.J, w.count)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and n >= 2:
+            return n, el
+
+
+def run_reference(args):
+    from paper_2512_00093_gb300.workloads import Partitioned
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = Partitioned()
+    per_step = max(0.2, min(3.0, 60.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup):
+        oracle_sample(per_step / 4, 1000 * i, w)
+    tot_n, tot_t = 0, 0.0
+    for s in range(args.steps):
+        n, el = oracle_sample(per_step, 4096 * s, w)
+        tot_n += n
+        tot_t += el
+    value = tot_n * w.count / tot_t
+    sample = (f"{tot_n} streams of the partitioned workload (jump to k*2^40 + 4096 outputs "
+              f"each), {args.steps} steps of ~{per_step:.2f} s, single-threaded C oracle")
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+          "steps": args.steps, "warmup": args.warmup,
+          "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+          "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+          "config": {"workload": "partitioned: seed 12345, 65536 streams at k*2^40, "
+                                 "4096 u24 outputs each (oracle on a bounded sample)"},
+          "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                           "sample": sample},
+          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                  "d2h_bytes_per_step": 0}})
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_2512_00093_gb300 as rm
+    from paper_2512_00093_gb300 import build as rbuild
+    from paper_2512_00093_gb300.workloads import LargeJumps, Partitioned, BatchedUneven
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = Partitioned()
+    n, count = w.n_streams, w.count
+    k0 = rank * n                      # each rank: its own disjoint block of streams
+    exps = [(k0 + i) * w.J for i in range(n)]
+    stream = torch.cuda.current_stream()
+
+    base = rm.seed(w.seed).to(dev)
+    states = torch.empty((n, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+    out = torch.empty(n * count, dtype=torch.int32, device=dev)
+    desc = rm.make_desc(np.arange(n), np.arange(n) * count, count, rm.DESC_WRITE_BACK, device=dev)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        rm.partition(base, w.J, k0, n, out=states)
+        rm.generate_u24(states, desc, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for s in range(K):
+        flush.fill_(s & 0xFF)          # L2 flush outside the timed events
+        ev[s][0].record(stream)
+        rm.partition(base, w.J, k0, n, out=states)
+        ev[s][1].record(stream)
+        rm.generate_u24(states, desc, out)
+        ev[s][2].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    t_jump = [ev[s][0].elapsed_time(ev[s][1]) for s in range(K)]
+    t_gen = [ev[s][1].elapsed_time(ev[s][2]) for s in range(K)]
+    ms_step = (sum(t_jump) + sum(t_gen)) / K
+    if dist:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * n * count / (ms_step * 1e-3)
+
+    # ---- end to end through the public API with host buffers ------------
+    h_base = rm.seed(w.seed).pin_memory()
+    h_out = torch.empty(n * count, dtype=torch.int32).pin_memory()
+    d_base = torch.empty_like(base)
+    e2e_steps = max(3, min(K, 10))
+    for _ in range(2):
+        d_base.copy_(h_base, non_blocking=True)
+        rm.partition(d_base, w.J, k0, n, out=states)
+        rm.generate_u24(states, desc, out)
+        h_out.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        d_base.copy_(h_base, non_blocking=True)
+        rm.partition(d_base, w.J, k0, n, out=states)
+        rm.generate_u24(states, desc, out)
+        h_out.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / e2e_steps
+    if dist:
+        t = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    ok_e2e = bool(np.array_equal(h_out[:count].numpy(), out[:count].cpu().numpy()))
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline ---------------------------------------------------------
+    peaks = {}
+    try:
+        with open(PEAKS_FILE) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = SMS * IMAD_PER_CLK_SM * sm_max * 1e6 / 1e12       # T mul-add / s
+    jump_ms = statistics.mean(t_jump)
+    gen_ms = statistics.mean(t_gen)
+    gen_bytes = n * count * 4 + n * (400 + 400 + 24)
+    jmacs = jump_macs(exps)
+    jump_sha = source_sha("jump.cuh", "ranmar_device.cuh")
+    gen_sha = source_sha("generate.cuh", "ranmar_device.cuh")
+    tj = traffic_for("jump_kernel", jump_sha)
+    tg = traffic_for("generate_desc_kernel", gen_sha)
+    roof_gen = {"kernel": "generate_desc_kernel<u24>", "bound": "hbm",
+                "achieved": gen_bytes / (gen_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                "unit": "GB/s", "frac": gen_bytes / (gen_ms * 1e-3) / 1e9 / hbm_peak,
+                "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes": gen_bytes,
+                "traffic": tg["bytes_per_launch"] if tg else None,
+                "avg_launch_ms": gen_ms}
+    roof_jump = {"kernel": "jump_kernel (partition)", "bound": "alu",
+                 "achieved": jmacs / (jump_ms * 1e-3) / 1e12, "peak": alu_peak,
+                 "unit": "Tmul-add/s", "frac": jmacs / (jump_ms * 1e-3) / 1e12 / alu_peak,
+                 "peak_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {sm_max:.0f} MHz",
+                 "algorithmic_macs": jmacs,
+                 "traffic": tj["bytes_per_launch"] if tj else None,
+                 "avg_launch_ms": jump_ms}
+    dominant = roof_jump if jump_ms >= gen_ms else roof_gen
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "partitioned: seed 12345, 65536 streams at k*2^40 "
+                               "(k = rank*65536 + 0..65535), 4096 u24 outputs each, "
+                               "write-back; step = jump + generate",
+                   "streams_per_gpu": n, "outputs_per_stream": count, "J": "2^40",
+                   "l2": "flushed (2x L2 buffer write) between timed steps; "
+                         "each step also writes 1.07 GB"},
+        "roofline": dominant, "roofline_generate": roof_gen, "roofline_jump": roof_jump,
+        "jump_ms": jump_ms, "generate_ms": gen_ms,
+        "jumps_per_s": n / (jump_ms * 1e-3),
+        "generate_outputs_per_s": n * count / (gen_ms * 1e-3),
+        "clocks": clk,
+        "e2e": {"value": world * n * count / (ms_e2e * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 400, "d2h_bytes_per_step": n * count * 4,
+                "ms_per_step": ms_e2e, "checked": ok_e2e},
+        "gpu_launches": 2 * K,
+        "library": rbuild.LIB,
+    }
+
+    if not args.no_extras:
+        result["extras"] = extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak)
+        if world == 1:
+            ns, el = oracle_sample(args.cpu_seconds, 0, w)
+            result["cpu_baseline"] = {
+                "value": ns * count / el, "unit": UNIT, "cores": cpu_cores_used(),
+                "kind": "oracle",
+                "sample": f"{ns} streams of this workload (jump + 4096 outputs), "
+                          f"{el:.1f} s, single-threaded C oracle on the host"}
+    emit(result)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
+    """Side measurements: large jumps (J = 2^120 + 12345), batched vs one
+    launch per stream on the uneven-length shape, and the probe ceilings."""
+    from paper_2512_00093_gb300 import build as rbuild
+    from paper_2512_00093_gb300.workloads import BatchedUneven, LargeJumps
+    res = {}
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = float("inf")
+        for _ in range(reps):
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    # large jumps
+    lj = LargeJumps()
+    base = rm.seed(lj.seed).to(dev)
+    st = torch.empty((lj.n_streams, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+    ms = timed(lambda: rm.partition(base, lj.J, 0, lj.n_streams, out=st))
+    macs = jump_macs([k * lj.J for k in range(lj.n_streams)])
+    res["large_jumps"] = {"streams": lj.n_streams, "J": "2^120+12345", "ms": ms,
+                          "jumps_per_s": lj.n_streams / (ms * 1e-3),
+                          "tmacs_per_s": macs / (ms * 1e-3) / 1e12,
+                          "alu_frac": macs / (ms * 1e-3) / 1e12 / alu_peak}
+
+    # batched (one launch) vs one plain launch per stream, uneven lengths
+    bu = BatchedUneven()
+    ns = 4096
+    lens = bu.lengths(ns)
+    offs = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    total = int(lens.sum())
+    stb = rm.partition(rm.seed(bu.seed).to(dev), bu.J, 0, ns)
+    outf = torch.empty(total, dtype=torch.float32, device=dev)
+    desc = rm.make_desc(np.arange(ns), offs, lens, 0, device=dev)
+    ms_b = timed(lambda: rm.generate_f32(stb, desc, outf))
+    rows = [stb[i] for i in range(ns)]
+    views = [outf[int(offs[i]):int(offs[i] + lens[i])] for i in range(ns)]
+
+    def plain():
+        for i in range(ns):
+            rm.generate_plain_f32(rows[i], int(lens[i]), views[i], write_back=False)
+    ms_p = timed(plain, reps=2)
+    res["batched_vs_plain"] = {"streams": ns, "outputs": total, "batched_ms": ms_b,
+                               "plain_ms": ms_p, "speedup": ms_p / ms_b,
+                               "batched_outputs_per_s": total / (ms_b * 1e-3),
+                               "plain_outputs_per_s": total / (ms_p * 1e-3)}
+
+    # probes: write-only HBM ceiling and IMAD ceiling on this GPU
+    try:
+        P = ctypes.CDLL(rbuild.PROBE_LIB)
+        P.ranmar_probe_write.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                         ctypes.c_void_p]
+        P.ranmar_probe_imad.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_void_p]
+        buf = torch.empty(2**30, dtype=torch.int32, device=dev)     # 4 GiB
+        ms_w = timed(lambda: P.ranmar_probe_write(buf.data_ptr(), buf.numel(), SMS * 8,
+                                                  stream.cuda_stream))
+        del buf
+        sink = torch.empty(SMS * 8 * 256, dtype=torch.int32, device=dev)
+        iters = 4096
+        ms_i = timed(lambda: P.ranmar_probe_imad(sink.data_ptr(), SMS * 8, iters,
+                                                 stream.cuda_stream))
+        res["probes"] = {"write_only_gbs": 4 * 2**30 / (ms_w * 1e-3) / 1e9,
+                         "imad_tops": SMS * 8 * 256 * iters * 16 / (ms_i * 1e-3) / 1e12}
+    except OSError as e:
+        res["probes"] = {"error": str(e)}
+    return res
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

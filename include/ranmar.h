@@ -1,0 +1,184 @@
+/*
+ * ranmar.h -- C ABI of libranmar: bulk generation of non-overlapping RANMAR
+ * streams on one GB300 GPU (sm_103a).
+ *
+ * Method: H. Haramoto and K. Suzuki, "Making the RANMAR pseudorandom number
+ * generator in LAMMPS up to four times faster, with an implementation of
+ * jump-ahead", arXiv 2512.00093.
+ *
+ * Notation (Sec. 2, Sec. 3, Algorithm 2):
+ *   lagged Fibonacci word   x_n = (x_{n-97} - x_{n-33}) mod 2^24
+ *   arithmetic sequence     c_n = (c_{n-1} - d) mod m,  d = 7654321,
+ *                           m = 2^24 - 3, c_0 = 362436 after seeding
+ *   output                  y_n = (x_{96+n} - c_n) mod 2^24   (1-based n,
+ *                           x_1..x_97 the state), float y_n * 2^-24
+ *   jump by E transitions   x P_E(A), P_E = t^E mod (t^97 + t^64 - 1) over
+ *                           Z/2^24 (Sec. 3.1), c_E = (c_0 - E d) mod m
+ *                           (Sec. 3.2).
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (RANMAR_OK) or a negative RANMAR_E* code; no exception ever
+ *     crosses the ABI.  ranmar_strerror() names each code.
+ *   - Pointers named d_* are device pointers on the current CUDA device;
+ *     h_* are host pointers.  The caller owns every buffer; the library
+ *     allocates nothing in these calls and keeps no pointer after return.
+ *   - Device work is enqueued on `stream` (a cudaStream_t; NULL means the
+ *     legacy default stream) and the call returns without waiting for it.
+ *   - Arguments visible on the host are checked before anything is
+ *     launched (RANMAR_EINVAL / RANMAR_ERANGE, nothing enqueued).  Values
+ *     only the device sees (indices inside descriptor arrays) are checked by
+ *     the kernel: a bad item is skipped and a RANMAR_ST_* bit is OR-ed into
+ *     *d_status when d_status is not NULL.
+ *   - RANMAR_ECUDA means a CUDA launch or query failed; the CUDA error
+ *     string is available from ranmar_last_cuda_error().
+ */
+#ifndef RANMAR_H
+#define RANMAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RANMAR_R 97               /* lag r (Sec. 2) */
+#define RANMAR_S 33               /* lag s (Sec. 2) */
+#define RANMAR_MAX_EXP_WORDS 5    /* jump exponents up to 2^160 - 1 */
+
+/* Return codes. */
+#define RANMAR_OK 0
+#define RANMAR_EINVAL (-1)        /* null pointer, misalignment, bad seed   */
+#define RANMAR_ERANGE (-2)        /* size or exponent out of range          */
+#define RANMAR_ECUDA (-3)         /* CUDA launch/runtime error              */
+#define RANMAR_ENOMEM (-4)        /* workspace allocation failed            */
+#define RANMAR_EDEVICE (-5)       /* device not sm_103a / not usable        */
+
+/* Bits OR-ed into *d_status by kernels. */
+#define RANMAR_ST_BAD_INDEX 1u    /* state or base index out of range       */
+#define RANMAR_ST_OUT_RANGE 2u    /* out_offset + count beyond out_len      */
+
+/* Descriptor flags. */
+#define RANMAR_DESC_WRITE_BACK 1u /* store the advanced state after output  */
+
+/*
+ * Generator state S = (x_1, ..., x_97, c) of Sec. 2 in its integer form
+ * (Sec. 3): x[q] = x_{q+1}, oldest word first, each in [0, 2^24); c is the
+ * numerator c' in [0, m) after the last transition, so the next output uses
+ * (c - d) mod m.  pos counts transitions applied since the caller's origin,
+ * modulo 2^64 (informational: jumps add E mod 2^64, generation adds count).
+ * 400 bytes; arrays of states must be 16-byte aligned.
+ */
+typedef struct ranmar_state {
+    uint32_t x[RANMAR_R];
+    uint32_t c;
+    uint64_t pos;
+} ranmar_state_t;
+
+/*
+ * One generation request: `count` consecutive outputs of the stream whose
+ * state is states[state_idx], written to out[out_offset .. out_offset +
+ * count).  With RANMAR_DESC_WRITE_BACK the state is advanced by `count`
+ * transitions in place (resume).  Two descriptors of one call must not name
+ * the same state with WRITE_BACK, nor overlapping output ranges.  24 bytes.
+ */
+typedef struct ranmar_desc {
+    uint32_t state_idx;
+    uint32_t flags;
+    uint64_t out_offset;
+    uint64_t count;
+} ranmar_desc_t;
+
+typedef struct CUstream_st *ranmar_stream_t;   /* == cudaStream_t */
+
+/*
+ * ranmar_seed -- Algorithm 3 (Appendix A): the LAMMPS RanMars seeding in
+ * integer form.  Host only, no device work.  Writes the seeded state in
+ * sequence order (x_1..x_97 = u_97, u_96, ..., u_1 with i = 97, j = 33),
+ * c = 362436, pos = 0.
+ * Errors: RANMAR_EINVAL if out is NULL or seed is outside 1..900000000 (the
+ * seed bound of Sec. 1; seed 0 would make seed - 1 negative).
+ */
+int ranmar_seed(int32_t seed, ranmar_state_t *h_out);
+
+/*
+ * ranmar_jump -- Sec. 3.1 and Sec. 3.2: d_out[i] = f^{E_i}(base), where base
+ * is d_base[d_base_idx[i]] (or d_base[0] when d_base_idx is NULL) and E_i is
+ * the little-endian integer d_exp[i*exp_words .. (i+1)*exp_words).  For each
+ * i the kernel forms P = t^{E_i} mod (t^97 + t^64 - 1) over Z/2^24 by
+ * left-to-right square-and-multiply, applies x P(A) as sum_j b_j x_{j+k},
+ * and sets c = (c_base - E_i d) mod m, pos = pos_base + E_i mod 2^64.
+ * One 32-lane warp serves 32 streams, one stream per lane.
+ * d_out must not overlap d_base.  n = 0 is a no-op.
+ * Errors: RANMAR_EINVAL (null pointer with n > 0, misaligned states,
+ * overlapping in/out), RANMAR_ERANGE (exp_words not in 1..5, n_base = 0, or
+ * n too large for one launch).  Device: RANMAR_ST_BAD_INDEX when
+ * d_base_idx[i] >= n_base (that d_out[i] is left untouched).
+ */
+int ranmar_jump(const ranmar_state_t *d_base, size_t n_base,
+                const uint32_t *d_base_idx,
+                const uint32_t *d_exp, uint32_t exp_words,
+                ranmar_state_t *d_out, size_t n,
+                uint32_t *d_status, ranmar_stream_t stream);
+
+/*
+ * ranmar_partition -- stream partitioning of Sec. 1: d_out[i] is the start
+ * of block k = k0 + i of length J of the sequence that starts at *d_base,
+ * i.e. f^{kJ}(base), computed as in ranmar_jump with E = (k0 + i) J formed
+ * on the device.  J is the little-endian host integer h_J[0..J_words).
+ * Errors: RANMAR_EINVAL (null pointer, misalignment, overlap),
+ * RANMAR_ERANGE (J_words not in 1..5, or (k0 + n - 1) J >= 2^160).
+ */
+int ranmar_partition(const ranmar_state_t *d_base, const uint32_t *h_J,
+                     uint32_t J_words, uint64_t k0,
+                     ranmar_state_t *d_out, size_t n, ranmar_stream_t stream);
+
+/*
+ * ranmar_generate_u24 / ranmar_generate_f32 -- Algorithm 2 over a batch of
+ * descriptors: for each desc, `count` outputs y_n = (x_{96+n} - c_n) mod
+ * 2^24 of its stream, as uint32 (u24) or as float y_n * 2^-24 (f32; exact,
+ * in [0, 1), 0.0 possible).  One warp runs one stream, 32 consecutive
+ * outputs per step (the lag 33 allows 32 in parallel), stores coalesced.
+ * out_len is the element count of d_out.
+ * Errors: RANMAR_EINVAL (null pointer with n_desc > 0, misaligned states or
+ * output), RANMAR_ERANGE (n_states = 0 with n_desc > 0).  Device:
+ * RANMAR_ST_BAD_INDEX (state_idx >= n_states), RANMAR_ST_OUT_RANGE
+ * (out_offset + count > out_len); the bad descriptor is skipped.
+ */
+int ranmar_generate_u24(ranmar_state_t *d_states, size_t n_states,
+                        const ranmar_desc_t *d_desc, size_t n_desc,
+                        uint32_t *d_out, size_t out_len,
+                        uint32_t *d_status, ranmar_stream_t stream);
+int ranmar_generate_f32(ranmar_state_t *d_states, size_t n_states,
+                        const ranmar_desc_t *d_desc, size_t n_desc,
+                        float *d_out, size_t out_len,
+                        uint32_t *d_status, ranmar_stream_t stream);
+
+/*
+ * ranmar_generate_plain_u24 / _f32 -- Algorithm 2 for ONE stream in one
+ * launch of one warp: `count` outputs of *d_state into d_out[0..count); if
+ * write_back != 0 the state is advanced in place.  This is the
+ * one-launch-per-stream path that the batched calls are measured against.
+ * Errors: RANMAR_EINVAL (null pointer with count > 0, misalignment).
+ */
+int ranmar_generate_plain_u24(ranmar_state_t *d_state, uint64_t count,
+                              uint32_t *d_out, int write_back,
+                              ranmar_stream_t stream);
+int ranmar_generate_plain_f32(ranmar_state_t *d_state, uint64_t count,
+                              float *d_out, int write_back,
+                              ranmar_stream_t stream);
+
+/* Name of a return code (static string, never NULL). */
+const char *ranmar_strerror(int code);
+
+/* The CUDA error string behind the last RANMAR_ECUDA on this thread. */
+const char *ranmar_last_cuda_error(void);
+
+/* ABI version of this header: (major << 16) | minor. */
+int ranmar_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RANMAR_H */

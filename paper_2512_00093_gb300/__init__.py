@@ -1,0 +1,12 @@
+"""RANMAR on GB300: bulk generation of non-overlapping streams of the 24-bit
+integer RANMAR generator with exact polynomial jump-ahead (arXiv 2512.00093).
+
+The compute path is libranmar (CUDA, sm_103a), reached through the C ABI in
+include/ranmar.h; this package is its thin binding plus the build step.
+"""
+from .binding import (  # noqa: F401
+    DESC_WRITE_BACK, MAX_EXP_WORDS, R, ST_BAD_INDEX, ST_OUT_RANGE, STATE_WORDS,
+    RanmarError, abi_version, exps_tensor, generate_f32, generate_plain_f32,
+    generate_plain_u24, generate_u24, jump, lib_path, make_desc, partition, seed,
+    state_words_np, words,
+)

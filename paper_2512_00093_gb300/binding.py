@@ -1,0 +1,227 @@
+"""Thin ctypes binding over libranmar (include/ranmar.h).
+
+Argument marshalling only: every step of the path runs in the library's
+CUDA kernels.  Device buffers are torch tensors (torch supplies memory and
+streams); states are int32 tensors of shape (n, 100) holding the 400-byte
+ranmar_state_t (x_1..x_97, c, pos as two words), descriptors are int64
+tensors of shape (n, 3) holding ranmar_desc_t.  If the library is missing the
+import of this module fails: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from .build import LIB
+
+R = 97
+STATE_WORDS = 100          # sizeof(ranmar_state_t) / 4
+DESC_WORDS64 = 3           # sizeof(ranmar_desc_t) / 8
+MAX_EXP_WORDS = 5
+DESC_WRITE_BACK = 1
+ST_BAD_INDEX = 1
+ST_OUT_RANGE = 2
+
+OK, EINVAL, ERANGE, ECUDA, ENOMEM, EDEVICE = 0, -1, -2, -3, -4, -5
+
+
+class RanmarError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib().ranmar_strerror(code).decode()
+        if code == ECUDA:
+            msg += " -- " + _lib().ranmar_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg}")
+        self.code = code
+
+
+_L: ctypes.CDLL | None = None
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+
+
+def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
+    lib.ranmar_abi_version.restype = ctypes.c_int
+    lib.ranmar_strerror.argtypes = [ctypes.c_int]
+    lib.ranmar_strerror.restype = ctypes.c_char_p
+    lib.ranmar_last_cuda_error.restype = ctypes.c_char_p
+    lib.ranmar_seed.argtypes = [ctypes.c_int32, _vp]
+    lib.ranmar_jump.argtypes = [_vp, _sz, _vp, _vp, _u32, _vp, _sz, _vp, _vp]
+    lib.ranmar_partition.argtypes = [_vp, _vp, _u32, _u64, _vp, _sz, _vp]
+    for name in ("ranmar_generate_u24", "ranmar_generate_f32"):
+        getattr(lib, name).argtypes = [_vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp]
+    for name in ("ranmar_generate_plain_u24", "ranmar_generate_plain_f32"):
+        getattr(lib, name).argtypes = [_vp, _u64, _vp, ctypes.c_int, _vp]
+    for name in ("ranmar_seed", "ranmar_jump", "ranmar_partition", "ranmar_generate_u24",
+                 "ranmar_generate_f32", "ranmar_generate_plain_u24",
+                 "ranmar_generate_plain_f32"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+def _lib() -> ctypes.CDLL:
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"libranmar is not built ({LIB}); run __graft_entry__.build()")
+        _L = _declare(ctypes.CDLL(LIB))
+    return _L
+
+
+def lib_path() -> str:
+    return LIB
+
+
+def _check(code: int, where: str) -> None:
+    if code != OK:
+        raise RanmarError(code, where)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _need(t: torch.Tensor, dtype, name: str, cuda: bool = True):
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if cuda and not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+
+
+def words(e: int, nw: int | None = None) -> list[int]:
+    """Non-negative integer -> little-endian 32-bit words (marshalling)."""
+    if e < 0:
+        raise ValueError("exponent must be non-negative")
+    if nw is None:
+        nw = max(1, (e.bit_length() + 31) // 32)
+    if e >> (32 * nw):
+        raise ValueError("exponent does not fit in the requested words")
+    return [(e >> (32 * w)) & 0xFFFFFFFF for w in range(nw)]
+
+
+def exps_tensor(exps, nw: int = MAX_EXP_WORDS, device="cuda") -> torch.Tensor:
+    """List of Python ints -> (n, nw) int32 tensor of exponent words."""
+    arr = np.array([words(int(e), nw) for e in exps], dtype=np.uint32).reshape(-1, nw)
+    return torch.from_numpy(arr.view(np.int32)).to(device)
+
+
+# ---------------------------------------------------------------------------
+def abi_version() -> int:
+    return _lib().ranmar_abi_version()
+
+
+def seed(seed: int) -> torch.Tensor:
+    """ranmar_seed: Algorithm 3 on the host -> (100,) int32 CPU tensor."""
+    buf = np.zeros(STATE_WORDS, np.uint32)
+    _check(_lib().ranmar_seed(int(seed), buf.ctypes.data), "ranmar_seed")
+    return torch.from_numpy(buf.view(np.int32).copy())
+
+
+def jump(base: torch.Tensor, exps: torch.Tensor, base_idx: torch.Tensor | None = None,
+         out: torch.Tensor | None = None, status: torch.Tensor | None = None,
+         stream=None) -> torch.Tensor:
+    """ranmar_jump: out[i] = f^{E_i}(base[base_idx[i]]); exps is (n, w) int32."""
+    base = base.reshape(-1, STATE_WORDS)
+    _need(base, torch.int32, "base")
+    _need(exps, torch.int32, "exps")
+    n, nw = exps.shape
+    if out is None:
+        out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=base.device)
+    _need(out, torch.int32, "out")
+    if base_idx is not None:
+        _need(base_idx, torch.int32, "base_idx")
+    if status is not None:
+        _need(status, torch.int32, "status")
+    _check(_lib().ranmar_jump(_ptr(base), base.shape[0], _ptr(base_idx), _ptr(exps), nw,
+                              _ptr(out), n, _ptr(status), _stream(stream)), "ranmar_jump")
+    return out
+
+
+def partition(base: torch.Tensor, J: int, k0: int, n: int, out: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    """ranmar_partition: out[i] = f^{(k0+i) J}(base) (Sec. 1 stream starts)."""
+    base = base.reshape(-1, STATE_WORDS)
+    _need(base, torch.int32, "base")
+    if out is None:
+        out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=base.device)
+    _need(out, torch.int32, "out")
+    jw = np.array(words(int(J)), dtype=np.uint32)
+    _check(_lib().ranmar_partition(_ptr(base), jw.ctypes.data, len(jw), int(k0), _ptr(out),
+                                   int(n), _stream(stream)), "ranmar_partition")
+    return out
+
+
+def make_desc(state_idx, out_offset, count, flags=DESC_WRITE_BACK, device="cuda") -> torch.Tensor:
+    """Pack ranmar_desc_t records into an (n, 3) int64 tensor."""
+    state_idx = np.asarray(state_idx, dtype=np.uint64)
+    n = state_idx.shape[0]
+    d = np.zeros((n, DESC_WORDS64), dtype=np.uint64)
+    d[:, 0] = state_idx | (np.broadcast_to(np.asarray(flags, np.uint64), (n,)) << np.uint64(32))
+    d[:, 1] = np.broadcast_to(np.asarray(out_offset, np.uint64), (n,))
+    d[:, 2] = np.broadcast_to(np.asarray(count, np.uint64), (n,))
+    return torch.from_numpy(d.view(np.int64)).to(device)
+
+
+def _generate(fn: str, out_dtype, states, desc, out, status, stream):
+    states = states.reshape(-1, STATE_WORDS)
+    _need(states, torch.int32, "states")
+    _need(desc, torch.int64, "desc")
+    _need(out, out_dtype, "out")
+    if status is not None:
+        _need(status, torch.int32, "status")
+    _check(getattr(_lib(), fn)(_ptr(states), states.shape[0], _ptr(desc), desc.shape[0],
+                               _ptr(out), out.numel(), _ptr(status), _stream(stream)), fn)
+    return out
+
+
+def generate_u24(states, desc, out, status=None, stream=None):
+    """ranmar_generate_u24 over a descriptor batch; out is int32 (24-bit values)."""
+    return _generate("ranmar_generate_u24", torch.int32, states, desc, out, status, stream)
+
+
+def generate_f32(states, desc, out, status=None, stream=None):
+    """ranmar_generate_f32 over a descriptor batch; out is float32 in [0, 1)."""
+    return _generate("ranmar_generate_f32", torch.float32, states, desc, out, status, stream)
+
+
+def generate_plain_u24(state, count: int, out, write_back: bool = True, stream=None):
+    """ranmar_generate_plain_u24: one stream, one launch."""
+    _need(state, torch.int32, "state")
+    _need(out, torch.int32, "out")
+    if out.numel() < count:
+        raise ValueError("out too small")
+    _check(_lib().ranmar_generate_plain_u24(_ptr(state), int(count), _ptr(out),
+                                            int(bool(write_back)), _stream(stream)),
+           "ranmar_generate_plain_u24")
+    return out
+
+
+def generate_plain_f32(state, count: int, out, write_back: bool = True, stream=None):
+    """ranmar_generate_plain_f32: one stream, one launch."""
+    _need(state, torch.int32, "state")
+    _need(out, torch.float32, "out")
+    if out.numel() < count:
+        raise ValueError("out too small")
+    _check(_lib().ranmar_generate_plain_f32(_ptr(state), int(count), _ptr(out),
+                                            int(bool(write_back)), _stream(stream)),
+           "ranmar_generate_plain_f32")
+    return out
+
+
+def state_words_np(states: torch.Tensor) -> np.ndarray:
+    """(n, 100) int32 tensor -> (n, 100) uint32 numpy view on the host."""
+    return states.reshape(-1, STATE_WORDS).cpu().numpy().view(np.uint32)

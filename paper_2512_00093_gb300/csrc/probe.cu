@@ -1,0 +1,58 @@
+// probe.cu -- roofline denominators measured on the running GPU (bench only).
+//
+// ranmar_probe_write: a store-only kernel over n 32-bit words (the HBM write
+// ceiling for generation, which only stores).  ranmar_probe_imad: independent
+// chains of 32-bit multiply-add (the integer-pipe ceiling for the jump).
+// Neither is part of the generator; both are timed by the caller with CUDA
+// events on `stream`.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace {
+
+__global__ void __launch_bounds__(256) probe_write_kernel(uint4* __restrict__ out, uint64_t n16,
+                                                          uint32_t v) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n16;
+       i += stride)
+    __stcs(out + i, make_uint4(v, v + 1, v + 2, v + 3));
+}
+
+// 16 independent multiply-add chains per thread, `iters` rounds each.
+__global__ void __launch_bounds__(256) probe_imad_kernel(uint32_t* __restrict__ sink,
+                                                         uint32_t iters, uint32_t seed) {
+  uint32_t a[16];
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) a[k] = t * 2654435761u + seed + k;
+  const uint32_t m = seed | 1u;
+#pragma unroll 1
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = a[k] * m + a[(k + 1) & 15];
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) s ^= a[k];
+  if (s == 0x9E3779B9u) sink[t] = s;   // practically never; keeps the chains live
+}
+
+}  // namespace
+
+extern "C" {
+
+int ranmar_probe_write(void* d_out, uint64_t n_words, uint32_t blocks, void* stream) {
+  if (!d_out || (reinterpret_cast<uintptr_t>(d_out) & 15) || (n_words & 3)) return -1;
+  probe_write_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<uint4*>(d_out), n_words / 4, 0x1234u);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// Multiply-adds issued: blocks * 256 * iters * 16.
+int ranmar_probe_imad(uint32_t* d_sink, uint32_t blocks, uint32_t iters, void* stream) {
+  if (!d_sink) return -1;
+  probe_imad_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_sink, iters, 7u);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+"""CPU-side checks of libranmar: it loads, exports every symbol the header
+declares, and its host logic (seeding, argument checks) is right.  No
+compute call reaches a GPU here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ranmar.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2512_00093_gb300.build import build_library
+    path = build_library()
+    from paper_2512_00093_gb300 import binding
+    return binding._lib(), path
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ranmar_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for need in ["ranmar_seed", "ranmar_jump", "ranmar_partition", "ranmar_generate_u24",
+                 "ranmar_generate_f32", "ranmar_generate_plain_u24", "ranmar_strerror"]:
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    L, path = lib
+    for name in declared_functions():
+        assert hasattr(L, name), f"{name} declared in ranmar.h but not exported by {path}"
+
+
+def test_abi_version_and_strerror(lib):
+    L, _ = lib
+    assert L.ranmar_abi_version() >> 16 == 1
+    for code in (0, -1, -2, -3, -4, -5, -99):
+        assert L.ranmar_strerror(code)
+
+
+def test_host_seed_matches_oracle(orc):
+    import paper_2512_00093_gb300 as rm
+    rng = np.random.default_rng(0)
+    seeds = [1, 2, 12345, 54217138, 900000000] + rng.integers(1, 900000001, 40).tolist()
+    for s in seeds:
+        st = rm.seed(int(s)).numpy().view(np.uint32)
+        x, c = orc.seeded_state(int(s))
+        assert np.array_equal(st[:97], x), s
+        assert st[97] == c and st[98] == 0 and st[99] == 0
+
+
+def test_seed_rejects_out_of_domain():
+    import paper_2512_00093_gb300 as rm
+    for bad in (0, -1, 900000001):
+        with pytest.raises(rm.RanmarError):
+            rm.seed(bad)
+
+
+def test_host_argument_checks(lib):
+    """Calls rejected by host checks return before any CUDA call."""
+    L, _ = lib
+    vp = ctypes.c_void_p
+    fake = vp(0x10000)          # never dereferenced: every call below fails a host check
+    assert L.ranmar_jump(None, 1, None, fake, 1, fake, 4, None, None) == -1
+    assert L.ranmar_jump(fake, 1, None, fake, 0, vp(0x20000), 4, None, None) == -2
+    assert L.ranmar_jump(fake, 1, None, fake, 6, vp(0x20000), 4, None, None) == -2
+    assert L.ranmar_jump(fake, 0, None, fake, 1, vp(0x20000), 4, None, None) == -2
+    assert L.ranmar_jump(fake, 4, None, fake, 1, vp(0x10000 + 400), 4, None, None) == -1  # overlap
+    assert L.ranmar_jump(vp(0x10008), 1, None, fake, 1, vp(0x20000), 4, None, None) == -1  # align
+    assert L.ranmar_jump(None, 0, None, None, 0, None, 0, None, None) == 0                  # n = 0
+    J = (ctypes.c_uint32 * 5)(0, 0, 0, 0, 1 << 31)                                          # 2^159
+    assert L.ranmar_partition(fake, J, 5, 1, vp(0x20000), 2, None) == -2                    # 2*2^159
+    assert L.ranmar_partition(fake, J, 6, 0, vp(0x20000), 1, None) == -2
+    assert L.ranmar_generate_u24(None, 1, fake, 1, fake, 10, None, None) == -1
+    assert L.ranmar_generate_u24(fake, 0, fake, 1, fake, 10, None, None) == -2
+    assert L.ranmar_generate_u24(fake, 1, fake, 0, fake, 10, None, None) == 0
+    assert L.ranmar_generate_f32(fake, 1, fake, 1, vp(0x20002), 10, None, None) == -1
+    assert L.ranmar_generate_plain_u24(None, 10, fake, 1, None) == -1
+    assert L.ranmar_generate_plain_u24(fake, 10, None, 1, None) == -1
+
+
+def test_workload_recipes():
+    from paper_2512_00093_gb300 import workloads as wl
+    lens = wl.BatchedUneven().lengths(200000)
+    assert lens.min() >= 64 and lens.max() <= 65536
+    # log-uniform on [64, 65536]: mean 64 * 1023 / ln 1024 ~ 9446
+    assert abs(lens.mean() / 9446.0 - 1.0) < 0.02
+    rows = wl.Partitioned().verify_rows()
+    assert len(set(rows.tolist())) == 256 and rows.max() < 65536
