@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-extras", action="store_true", help="skip the side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--streams", type=int, default=65536,
+                   help="streams per GPU (65536 is the benchmark; smaller for profiling)")
     return p.parse_args()
 
 
@@ -207,7 +209,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
 
     w = Partitioned()
-    n, count = w.n_streams, w.count
+    n, count = args.streams, w.count
     k0 = rank * n                      # each rank: its own disjoint block of streams
     exps = [(k0 + i) * w.J for i in range(n)]
     stream = torch.cuda.current_stream()
@@ -327,8 +329,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "partitioned: seed 12345, 65536 streams at k*2^40 "
-                               "(k = rank*65536 + 0..65535), 4096 u24 outputs each, "
+        "config": {"workload": f"partitioned: seed 12345, {n} streams at k*2^40 "
+                               f"(k = rank*{n} + 0..{n - 1}), 4096 u24 outputs each, "
                                "write-back; step = jump + generate",
                    "streams_per_gpu": n, "outputs_per_stream": count, "J": "2^40",
                    "l2": "flushed (2x L2 buffer write) between timed steps; "
