@@ -108,7 +108,7 @@ int ranmar_seed(int32_t seed, ranmar_state_t *h_out);
  * i the kernel forms P = t^{E_i} mod (t^97 + t^64 - 1) over Z/2^24 by
  * left-to-right square-and-multiply, applies x P(A) as sum_j b_j x_{j+k},
  * and sets c = (c_base - E_i d) mod m, pos = pos_base + E_i mod 2^64.
- * One 32-lane warp serves 32 streams, one stream per lane.
+ * One 32-lane warp serves 16 streams, two lanes per stream.
  * d_out must not overlap d_base.  n = 0 is a no-op.
  * Errors: RANMAR_EINVAL (null pointer with n > 0, misaligned states,
  * overlapping in/out), RANMAR_ERANGE (exp_words not in 1..5, n_base = 0, or

@@ -1,34 +1,57 @@
 // jump.cuh -- batched jump-ahead (Sec. 3.1, Sec. 3.2).
 //
 // For each stream: P_E(t) = t^E mod phi(t), phi = t^97 + t^64 - 1 over
-// Z/2^24, by left-to-right square-and-multiply (a 1 bit multiplies by t, a
-// shift plus one fix-up); then the new state word k = sum_i b_i x_{i+k+1}
-// (x extended by 96 steps of the recurrence), which equals the Horner form
-// u P_E(A) of Sec. 3.1; then c_E = (c - E d) mod m (Sec. 3.2).
+// Z/2^24, by left-to-right square-and-multiply (a 1 bit multiplies by t: a
+// shift plus the fold t^97 = 1 - t^64); then the new state word k =
+// sum_i b_i x_{i+k+1} (x extended by the recurrence), which is the Horner
+// form u P_E(A) of Sec. 3.1; then c_E = (c - E d) mod m (Sec. 3.2).
 //
-// Mapping: one stream per LANE, 32 streams per warp.  Every lane runs the
-// same instruction stream on its own polynomial (no divergence), so the
-// 97x97 products are register-blocked 8x8 tiles of 32-bit multiply-adds
-// (mul.lo wraps mod 2^32, which is exact mod 2^24; masks only at the end).
-// Each lane owns a private slice of shared memory: the polynomial a (104
-// words, zero padded to 13 blocks of 8) and the 208-word product buffer,
-// which is reused for the extended state window during the application.
-// The slice stride is 324 words (= 4 mod 32) so that 16-byte loads of the
-// 32 lanes fall in distinct bank groups.
+// Mapping: TWO lanes per stream, 16 streams per warp, one warp per CTA.  Every
+// pair runs the same instruction stream on its own polynomial, so the 97x97
+// products are register-blocked 8x8 tiles of 32-bit multiply-adds (mul.lo
+// wraps mod 2^32, exact mod 2^24; masks only at the end).  Within a tile the
+// pair splits the rows: lane g takes rows 4g..4g+3 against all 8 columns
+// (32 multiply-adds into 11 accumulators).
+//
+// Squaring a(t)^2, in place: tiles (I, J), I <= J, of 8-coefficient blocks
+// are summed along the anti-diagonal s = I + J (outputs 8s .. 8s+14), walking
+// s DOWN from 24 to 0.  Off-diagonal tiles are summed and doubled; the
+// diagonal tile (I = J) is then added as a full 8x8 product (its off-diagonal
+// pairs twice, its squares once).  After anti-diagonal s the product block
+// s+1 (coefficients 8s+8 .. 8s+15) is complete, and block s+1 of `a` is no
+// longer read (anti-diagonals <= s use blocks <= s), so:
+//   * blocks >= 12 (degree >= 96) go to a 128-word region R (R[k-96] = c_k);
+//   * blocks <= 12 are reduced at once and written into `a` itself:
+//       a_n = c_n + h_n[n<=95] - h_{n+33}[n<=62] + h_{n+66}[n<=29]
+//             - h_{n-64}[n>=64] + h_{n-31}[n>=64] - h_{n+2}[64<=n<=93]
+//     with h_j = c_{97+j} (t^k = t^{k-97} - t^{k-33} applied until the
+//     degree is below 97; every high block is complete before the first low
+//     one, because s walks down).
+// A multiplication by t shifts the written index by one; the word that lands
+// on t^97 is folded back at the end.  After each anti-diagonal the pair
+// swaps 4 partial sums by shuffle.
+//
+// Application: the extended window X(0..207) is consumed through the same
+// 128-word region used as a ring (window X[8K .. 8K+111] for output block K,
+// 16 new words per round computed by the recurrence).
+//
+// Shared memory per stream: a (104 words, 13 zero-padded blocks of 8) + R
+// (128 words); stride 232 = 8 mod 32, so that the 16-byte loads of a quarter
+// warp (4 streams x 2 lanes) fall in 8 distinct bank groups.  14,848 B per
+// CTA.
 #pragma once
 
 #include "ranmar_device.cuh"
 
 namespace ranmar {
 
-constexpr int kPolyWords = 104;   // 13 blocks of 8 >= 97
-constexpr int kProdWords = 208;   // 193 product words + tile overhang
-constexpr int kLaneWords = 324;   // per-lane slice stride (4 mod 32)
-constexpr int kJumpWarpsPerBlock = 1;
-constexpr size_t kJumpSmemBytes =
-    sizeof(uint32_t) * kLaneWords * 32 * kJumpWarpsPerBlock;
-static_assert(kPolyWords + kProdWords <= kLaneWords, "slice");
-static_assert(kLaneWords % 32 == 4, "bank spread");
+constexpr int kPolyWords = 104;    // 13 blocks of 8 >= 97
+constexpr int kRingWords = 128;    // high product words / application ring
+constexpr int kStreamWords = 232;  // per-stream slice stride (8 mod 32)
+constexpr int kJumpStreamsPerWarp = 16;
+constexpr size_t kJumpSmemBytes = sizeof(uint32_t) * kStreamWords * kJumpStreamsPerWarp;
+static_assert(kPolyWords + kRingWords <= kStreamWords, "slice");
+static_assert(kStreamWords % 32 == 8, "bank spread");
 
 struct ExpParams {
   uint32_t J[kMaxExpWords];  // partition mode: E = (k0 + i) * J
@@ -36,86 +59,118 @@ struct ExpParams {
   uint64_t k0;
 };
 
-__device__ __forceinline__ void load8(const uint32_t* p, uint32_t (&v)[8]) {
+struct Quad {
+  uint32_t v[4];
+};
+struct Oct {
+  uint32_t v[8];
+};
+
+__device__ __forceinline__ Quad lds4(const uint32_t* p) {
+  const uint4 t = *reinterpret_cast<const uint4*>(p);
+  return Quad{{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ Oct lds8(const uint32_t* p) {
   const uint4 lo = *reinterpret_cast<const uint4*>(p);
   const uint4 hi = *reinterpret_cast<const uint4*>(p + 4);
-  v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
-  v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+  return Oct{{lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w}};
 }
 
-__device__ __forceinline__ void store8(uint32_t* p, const uint32_t (&v)[8]) {
-  *reinterpret_cast<uint4*>(p) = make_uint4(v[0], v[1], v[2], v[3]);
-  *reinterpret_cast<uint4*>(p + 4) = make_uint4(v[4], v[5], v[6], v[7]);
-}
-
-// c[0..192] = a(t)^2, with the symmetric products of tiles (I, J), I <= J,
-// summed along the anti-diagonal s = I + J (outputs 8s .. 8s+14) in
-// registers; the upper 7 outputs carry into the next anti-diagonal.
-__device__ __forceinline__ void poly_square(const uint32_t* __restrict__ a,
-                                            uint32_t* __restrict__ c) {
-  uint32_t carry[7];
+// acc[p + q] += r[p] * col[q]: rows of this lane (4) x columns (8).
+__device__ __forceinline__ void tile_mac(uint32_t (&acc)[11], const Quad& r, const Oct& col) {
 #pragma unroll
-  for (int r = 0; r < 7; ++r) carry[r] = 0;
+  for (int p = 0; p < 4; ++p) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[p + q] += r.v[p] * col.v[q];
+  }
+}
+
+// Reduced coefficients n = 8b + 4g + k (k < 4, n <= 96) of a completed
+// product block, written to a[n + shift].
+__device__ __forceinline__ void reduce_block(uint32_t* __restrict__ a,
+                                             const uint32_t* __restrict__ R, int b, unsigned g,
+                                             const uint32_t (&cv)[4], uint32_t shift) {
+  const uint32_t* h = R + 1;  // h_j = c_{97+j}
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int n = 8 * b + 4 * static_cast<int>(g) + k;
+    if (n <= 96) {
+      uint32_t v = cv[k];
+      if (n <= 95) v += h[n];
+      if (n <= 62) v -= h[n + 33];
+      if (n <= 29) v += h[n + 66];
+      if (n >= 64) {
+        v += h[n - 31] - h[n - 64];
+        if (n <= 93) v -= h[n + 2];
+      }
+      a[n + shift] = v;
+    }
+  }
+}
+
+// a = a^2 t^shift mod phi, in place (lanes g = 0, 1 of the pair cooperate).
+__device__ __forceinline__ void square_reduce_pair(uint32_t* __restrict__ a,
+                                                   uint32_t* __restrict__ R, uint32_t shift,
+                                                   unsigned g) {
+  uint32_t pend[4] = {0u, 0u, 0u, 0u};  // low half of the previous anti-diagonal
+  const uint32_t* arow = a + 4 * g;
+  const uint32_t keep0 = g ? 0u : ~0u;
 #pragma unroll 1
-  for (int s = 0; s <= 24; ++s) {
-    uint32_t acc[15];
+  for (int s = 24; s >= 0; --s) {
+    uint32_t acc[11];
 #pragma unroll
-    for (int r = 0; r < 15; ++r) acc[r] = 0;
+    for (int r = 0; r < 11; ++r) acc[r] = 0;
     const int ilo = s > 12 ? s - 12 : 0;
     const int ihi = s >> 1;
+    const bool even = (s & 1) == 0;
+    const int iend = even ? ihi : ihi + 1;  // off-diagonal tiles: I in [ilo, iend)
+    if (ilo < iend) {
+      Quad r0 = lds4(arow + 8 * ilo), r1;
+      Oct c0 = lds8(a + 8 * (s - ilo)), c1;
+      int I = ilo;
 #pragma unroll 1
-    for (int I = ilo; I <= ihi; ++I) {
-      const int J = s - I;
-      uint32_t ai[8], aj[8];
-      load8(a + 8 * I, ai);
-      if (I == J) {
-#pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          acc[2 * p] += ai[p] * ai[p];
-          const uint32_t a2 = ai[p] << 1;
-#pragma unroll
-          for (int q = p + 1; q < 8; ++q) acc[p + q] += a2 * ai[q];
+      for (; I + 1 < iend; I += 2) {  // operands one tile ahead, ping-pong
+        r1 = lds4(arow + 8 * (I + 1));
+        c1 = lds8(a + 8 * (s - I - 1));
+        tile_mac(acc, r0, c0);
+        if (I + 2 < iend) {
+          r0 = lds4(arow + 8 * (I + 2));
+          c0 = lds8(a + 8 * (s - I - 2));
         }
-      } else {
-        load8(a + 8 * J, aj);
-#pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          const uint32_t a2 = ai[p] << 1;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) acc[p + q] += a2 * aj[q];
-        }
+        tile_mac(acc, r1, c1);
       }
+      if (I < iend) tile_mac(acc, r0, c0);
+#pragma unroll
+      for (int k = 0; k < 11; ++k) acc[k] += acc[k];
     }
-    uint32_t lo[8];
-#pragma unroll
-    for (int r = 0; r < 7; ++r) lo[r] = acc[r] + carry[r];
-    lo[7] = acc[7];
-    store8(c + 8 * s, lo);
-#pragma unroll
-    for (int r = 0; r < 7; ++r) carry[r] = acc[8 + r];
-  }
-}
+    if (even) tile_mac(acc, lds4(arow + 8 * ihi), lds8(a + 8 * ihi));
 
-// a = (c mod phi) * t^shift, shift in {0, 1}; c holds 193 words on entry.
-// t^k = t^(k-97) - t^(k-33) for k >= 97, applied from the top.
-__device__ __forceinline__ void poly_reduce_into(uint32_t* __restrict__ c,
-                                                 uint32_t* __restrict__ a, uint32_t shift) {
-#pragma unroll 4
-  for (int k = 2 * kR - 2; k >= kR; --k) {
-    const uint32_t h = c[k];
-    c[k - kR] += h;
-    c[k - kS] -= h;
+    // Lane 0 holds outputs 0..10 of this anti-diagonal, lane 1 outputs 4..14.
+    // Block s+1 = outputs 8..14 here + the low half of anti-diagonal s+1.
+    uint32_t out[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t recv = __shfl_xor_sync(kFull, acc[4 + k], 1);
+      out[k] = (k < 3 ? acc[8 + k] : 0u) + pend[k] + (recv & keep0);
+      pend[k] = acc[k] + (recv & ~keep0);
+    }
+    const int b = s + 1;
+    if (b <= 24) {
+      if (b >= 12)
+        *reinterpret_cast<uint4*>(R + 8 * b - 96 + 4 * g) = make_uint4(out[0], out[1], out[2], out[3]);
+      if (b <= 12) reduce_block(a, R, b, g, out, shift);
+    }
+    __syncwarp();
   }
-  // Multiplying by t moves word n to n+1; word 97 then folds back as
-  // t^97 = 1 - t^64.
-#pragma unroll 4
-  for (int n = 0; n < kR; ++n) a[n + shift] = c[n];
-  if (shift) {
+  reduce_block(a, R, 0, g, pend, shift);
+  __syncwarp();
+  if (shift && g == 0) {  // fold t^97 = 1 - t^64
     const uint32_t top = a[kR];
     a[0] = top;
     a[64] -= top;
     a[kR] = 0;
   }
+  __syncwarp();
 }
 
 __device__ __forceinline__ uint32_t exp_word(const uint32_t (&E)[kMaxExpWords], int w) {
@@ -154,8 +209,8 @@ __device__ __forceinline__ uint32_t exp_mod_m(const uint32_t (&E)[kMaxExpWords])
 }
 
 // E += J * m * 2^(32 shift) (multi-word), truncated to kMaxExpWords.
-__device__ __forceinline__ void exp_mul_add(uint32_t (&E)[kMaxExpWords],
-                                            const uint32_t* J, uint32_t m, int shift) {
+__device__ __forceinline__ void exp_mul_add(uint32_t (&E)[kMaxExpWords], const uint32_t* J,
+                                            uint32_t m, int shift) {
   uint64_t carry = 0;
 #pragma unroll
   for (int w = 0; w < kMaxExpWords; ++w) {
@@ -167,14 +222,15 @@ __device__ __forceinline__ void exp_mul_add(uint32_t (&E)[kMaxExpWords],
   }
 }
 
-// state_out = f^E(base) for one lane's stream; all lanes of the warp call
-// it together (the bit loop is warp-uniform).
-__device__ __forceinline__ void jump_one(const ranmar_state_t* __restrict__ base,
-                                         const uint32_t (&E)[kMaxExpWords], bool active,
-                                         ranmar_state_t* __restrict__ dst,
-                                         uint32_t* __restrict__ a, uint32_t* __restrict__ c) {
+// dst = f^E(base) for the stream of this lane pair; all 32 lanes of the warp
+// call it together (the bit loop is warp-uniform).
+__device__ __forceinline__ void jump_pair(const ranmar_state_t* __restrict__ base,
+                                          const uint32_t (&E)[kMaxExpWords], bool active,
+                                          ranmar_state_t* __restrict__ dst,
+                                          uint32_t* __restrict__ a, uint32_t* __restrict__ R,
+                                          unsigned g) {
   const int nb = active ? exp_bitlen(E) : 0;
-  const int L = __reduce_max_sync(kFull, static_cast<unsigned>(nb));
+  const int L = static_cast<int>(__reduce_max_sync(kFull, static_cast<unsigned>(nb)));
 
   // Leading (up to) six bits: P = t^v0 with v0 < 64 < 97 is a monomial.
   uint32_t v0;
@@ -187,57 +243,81 @@ __device__ __forceinline__ void jump_one(const ranmar_state_t* __restrict__ base
     p = L - 7;
   }
   if (!active) v0 = 0;
-#pragma unroll 4
-  for (int n = 0; n < kPolyWords; ++n) a[n] = 0;
-  a[v0] = 1;
+  for (int n = static_cast<int>(g); n < kPolyWords; n += 2) a[n] = (n == static_cast<int>(v0));
+  __syncwarp();
 
 #pragma unroll 1
   for (; p >= 0; --p) {
     const uint32_t bit = active ? exp_bit(E, p) : 0u;
-    poly_square(a, c);
-    poly_reduce_into(c, a, bit);
+    square_reduce_pair(a, R, bit, g);
   }
 
-  // Application: X(0..96) = base x, X(97..192) by the recurrence, zero pad.
-  uint32_t* X = c;
+  // Application through a 128-word ring of the extended window X: X(0..96)
+  // is the base state, X(q) = X(q-97) - X(q-33) beyond.  Round m handles
+  // output blocks K = 2m + g, whose windows are X[8K .. 8K+111]; between
+  // rounds 16 new words replace the 16 oldest (each depends only on words
+  // still in the ring).
+  uint32_t* ring = R;
   const uint32_t* bx = base->x;
-#pragma unroll 4
-  for (int q = 0; q < kR; ++q) X[q] = bx[q];
-#pragma unroll 4
-  for (int q = kR; q < 2 * kR - 1; ++q) X[q] = X[q - kR] - X[q - kS];
-#pragma unroll
-  for (int q = 2 * kR - 1; q < kProdWords; ++q) X[q] = 0;
+  for (int q = static_cast<int>(g); q < kR; q += 2) ring[q] = bx[q];
+  __syncwarp();
+  for (int q = kR + static_cast<int>(g); q < kRingWords; q += 2) ring[q] = ring[q - kR] - ring[q - kS];
+  __syncwarp();
 
   uint32_t* ox = dst->x;
 #pragma unroll 1
-  for (int K = 0; K < 13; ++K) {
-    uint32_t acc[8];
+  for (int m = 0; m < 7; ++m) {
+    const int K = 2 * m + static_cast<int>(g);
+    if (K < 13) {
+      uint32_t acc[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) acc[r] = 0;
+      for (int r = 0; r < 8; ++r) acc[r] = 0;
+      Oct b = lds8(a);
+      Oct w0 = lds8(ring + ((8 * K) & (kRingWords - 1)));
+      Oct w1 = lds8(ring + ((8 * K + 8) & (kRingWords - 1)));
 #pragma unroll 1
-    for (int I = 0; I < 13; ++I) {
-      uint32_t b[8], w0[8], w1[8];
-      load8(a + 8 * I, b);
-      load8(X + 8 * (I + K), w0);
-      load8(X + 8 * (I + K) + 8, w1);
+      for (int I = 0; I < 13; ++I) {
+        Oct bn = b, n1 = w1;
+        if (I + 1 < 13) {
+          bn = lds8(a + 8 * (I + 1));
+          n1 = lds8(ring + ((8 * (I + 1 + K) + 8) & (kRingWords - 1)));
+        }
 #pragma unroll
-      for (int p2 = 0; p2 < 8; ++p2) {
+        for (int p2 = 0; p2 < 8; ++p2) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const int idx = p2 + r;
-          const uint32_t xv = idx < 8 ? w0[idx & 7] : w1[idx & 7];
-          acc[r] += b[p2] * xv;
+          for (int r = 0; r < 8; ++r) {
+            const int idx = p2 + r;
+            acc[r] += b.v[p2] * (idx < 8 ? w0.v[idx & 7] : w1.v[idx & 7]);
+          }
+        }
+        b = bn;
+        w0 = w1;
+        w1 = n1;
+      }
+      if (active) {
+        if (K < 12) {
+          uint4* o4 = reinterpret_cast<uint4*>(ox + 8 * K);
+          o4[0] = make_uint4(acc[0] & kMask24, acc[1] & kMask24, acc[2] & kMask24,
+                             acc[3] & kMask24);
+          o4[1] = make_uint4(acc[4] & kMask24, acc[5] & kMask24, acc[6] & kMask24,
+                             acc[7] & kMask24);
+        } else {
+          ox[96] = acc[0] & kMask24;
         }
       }
     }
-    if (active) {
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-        if (8 * K + r < kR) ox[8 * K + r] = acc[r] & kMask24;
+    __syncwarp();
+    if (m < 6) {
+      for (int j = static_cast<int>(g); j < 16; j += 2) {
+        const int q = 16 * m + kRingWords + j;
+        ring[q & (kRingWords - 1)] =
+            ring[(q - kR) & (kRingWords - 1)] - ring[(q - kS) & (kRingWords - 1)];
+      }
+      __syncwarp();
     }
   }
 
-  if (active) {
+  if (active && g == 0) {
     const uint32_t e = exp_mod_m(E);
     // (c - e d) mod m = (c + (m - e) d) mod m, non-negative residue.
     const uint64_t cn =
@@ -249,18 +329,18 @@ __device__ __forceinline__ void jump_one(const ranmar_state_t* __restrict__ base
 
 // mode 0: E_i from d_exp (exp_words per stream), base d_base[base_idx[i]].
 // mode 1: E_i = (k0 + i) * J, base d_base[0].
-__global__ void __launch_bounds__(32 * kJumpWarpsPerBlock) jump_kernel(
+__global__ void __launch_bounds__(32) jump_kernel(
     const ranmar_state_t* __restrict__ d_base, uint64_t n_base,
     const uint32_t* __restrict__ d_base_idx, const uint32_t* __restrict__ d_exp,
     uint32_t exp_words, ExpParams part, int mode, ranmar_state_t* __restrict__ d_out,
     uint64_t n, uint32_t* status) {
   extern __shared__ __align__(16) uint32_t smem[];
   const unsigned lane = threadIdx.x & 31;
-  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  uint32_t* slice = smem + threadIdx.x * kLaneWords;
-  uint32_t* a = slice;
-  uint32_t* c = slice + kPolyWords;
-  (void)lane;
+  const unsigned g = lane & 1;
+  const unsigned slot = lane >> 1;
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * kJumpStreamsPerWarp + slot;
+  uint32_t* a = smem + slot * kStreamWords;
+  uint32_t* R = a + kPolyWords;
 
   bool active = i < n;
   uint32_t E[kMaxExpWords];
@@ -275,7 +355,7 @@ __global__ void __launch_bounds__(32 * kJumpWarpsPerBlock) jump_kernel(
         if (w < static_cast<int>(exp_words)) E[w] = ew[w];
       const uint32_t bi = d_base_idx ? d_base_idx[i] : 0u;
       if (bi >= n_base) {
-        flag_status(status, RANMAR_ST_BAD_INDEX);
+        if (g == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
         active = false;
       } else {
         base = d_base + bi;
@@ -286,7 +366,7 @@ __global__ void __launch_bounds__(32 * kJumpWarpsPerBlock) jump_kernel(
       exp_mul_add(E, part.J, static_cast<uint32_t>(k >> 32), 1);
     }
   }
-  jump_one(base, E, active, d_out + (active ? i : 0), a, c);
+  jump_pair(base, E, active, d_out + (active ? i : 0), a, R, g);
 }
 
 }  // namespace ranmar

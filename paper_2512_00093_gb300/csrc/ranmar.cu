@@ -95,13 +95,12 @@ int launch_jump(const ranmar_state_t* base, size_t n_base, const uint32_t* base_
                 const uint32_t* exp, uint32_t exp_words, const ranmar::ExpParams& part,
                 int mode, ranmar_state_t* out, size_t n, uint32_t* status,
                 ranmar_stream_t stream) {
-  const uint64_t threads = 32 * ranmar::kJumpWarpsPerBlock;
-  const uint64_t blocks = (n + threads - 1) / threads;
+  const uint64_t per_cta = ranmar::kJumpStreamsPerWarp;   // one warp per CTA
+  const uint64_t blocks = (n + per_cta - 1) / per_cta;
   if (blocks > 0x7FFFFFFFull) return RANMAR_ERANGE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  ranmar::jump_kernel<<<static_cast<unsigned>(blocks), static_cast<unsigned>(threads),
-                        ranmar::kJumpSmemBytes, s>>>(base, n_base, base_idx, exp, exp_words,
-                                                     part, mode, out, n, status);
+  ranmar::jump_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kJumpSmemBytes, s>>>(
+      base, n_base, base_idx, exp, exp_words, part, mode, out, n, status);
   return check_launch();
 }
 
