@@ -168,6 +168,94 @@ int ranmar_generate_plain_f32(ranmar_state_t *d_state, uint64_t count,
                               float *d_out, int write_back,
                               ranmar_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Persistent batch path: many streams of uneven lengths in one launch.
+ * (Sec. 1 partitioning applied to a batch; Algorithm 2 per stream.)
+ * ------------------------------------------------------------------------ */
+
+/* Opaque handle: owns a device workspace on the device that was current at
+ * creation (queue counter and prefix-sum scratch).  Calls that use one
+ * handle must be ordered on one stream; use one handle per concurrent
+ * stream. */
+typedef struct ranmar_batch ranmar_batch_t;
+
+/* Launch configuration of the persistent kernel. */
+typedef struct ranmar_batch_config {
+    int32_t lanes_per_stream;   /* 32, 16, 8 or 4 = outputs per group step */
+    int32_t threads_per_cta;    /* multiple of 32, 32..1024 */
+    int32_t ctas_per_sm;        /* resident CTAs per SM; 0 = as many as fit */
+    int32_t chunk;              /* descriptors taken per queue pull, >= 1 */
+} ranmar_batch_config_t;
+
+/* ranmar_batch_create -- allocates the workspace (cudaMalloc) for batches of
+ * up to `capacity` streams on the current device.  The default config is
+ * {32, 256, 0, 1}.  Errors: RANMAR_EINVAL (out NULL), RANMAR_ERANGE
+ * (capacity 0 or >= 2^32), RANMAR_ENOMEM, RANMAR_ECUDA. */
+int ranmar_batch_create(size_t capacity, ranmar_batch_t **out);
+
+/* Frees the workspace (synchronizes the device first).  NULL is a no-op. */
+int ranmar_batch_destroy(ranmar_batch_t *b);
+
+/* Set / read the persistent-kernel config.  RANMAR_EINVAL for a config
+ * outside the ranges above. */
+int ranmar_batch_set_config(ranmar_batch_t *b, const ranmar_batch_config_t *cfg);
+int ranmar_batch_get_config(const ranmar_batch_t *b, ranmar_batch_config_t *cfg);
+
+/* ranmar_batch_pack -- from per-stream counts (d_counts[i], device) builds
+ * d_desc[i] = {state_idx i, flags, out_offset = sum_{j<i} counts[j],
+ * count = counts[i]} (outputs packed back to back by an exclusive prefix
+ * sum on the device), optionally d_order (a permutation of 0..n-1 visiting
+ * streams longest first, by floor(log2(count)) bucket; NULL to skip) and
+ * optionally *d_total (device, sum of all counts; NULL to skip).
+ * Errors: RANMAR_EINVAL (NULL b/d_counts/d_desc with n > 0, b on another
+ * device), RANMAR_ERANGE (n > capacity). */
+int ranmar_batch_pack(ranmar_batch_t *b, const uint64_t *d_counts, size_t n,
+                      uint32_t flags, ranmar_desc_t *d_desc, uint32_t *d_order,
+                      uint64_t *d_total, ranmar_stream_t stream);
+
+/* ranmar_batch_generate_u24 / _f32 -- the same outputs as
+ * ranmar_generate_u24/_f32 for the same descriptors, from one persistent
+ * launch: groups of lanes_per_stream lanes pull `chunk` descriptors at a
+ * time from a device queue, in d_order's order (NULL = index order).  The
+ * queue counter is reset on `stream` before the launch (capturable in a
+ * CUDA graph).  Errors as ranmar_generate_u24, plus RANMAR_EINVAL for a NULL
+ * or foreign-device handle.  Device: RANMAR_ST_BAD_INDEX also for
+ * d_order[t] >= n_desc. */
+int ranmar_batch_generate_u24(ranmar_batch_t *b, ranmar_state_t *d_states, size_t n_states,
+                              const ranmar_desc_t *d_desc, size_t n_desc,
+                              const uint32_t *d_order, uint32_t *d_out, size_t out_len,
+                              uint32_t *d_status, ranmar_stream_t stream);
+int ranmar_batch_generate_f32(ranmar_batch_t *b, ranmar_state_t *d_states, size_t n_states,
+                              const ranmar_desc_t *d_desc, size_t n_desc,
+                              const uint32_t *d_order, float *d_out, size_t out_len,
+                              uint32_t *d_status, ranmar_stream_t stream);
+
+/* ranmar_batch_tune -- autotuner: times every candidate config (group
+ * width 32/16/8, 128/256/512 threads, chunk 1/8, all resident CTAs) on this
+ * batch (write-back disabled, so the states are not advanced; the outputs
+ * are written, with their correct values), keeps the fastest in the handle
+ * and returns its time in *best_ms (may be NULL).  Synchronizes `stream`.
+ * f32 != 0 tunes the float kernel.  Errors as ranmar_batch_generate_u24. */
+int ranmar_batch_tune(ranmar_batch_t *b, int f32, ranmar_state_t *d_states, size_t n_states,
+                      const ranmar_desc_t *d_desc, size_t n_desc, const uint32_t *d_order,
+                      void *d_out, size_t out_len, ranmar_stream_t stream, float *best_ms);
+
+/* ------------------------------------------------------------------------
+ * CUDA graphs: capture a sequence of the calls above on one stream and
+ * replay it with one launch (buffers and arguments are frozen at capture).
+ * ------------------------------------------------------------------------ */
+typedef struct ranmar_graph ranmar_graph_t;
+
+/* Starts capturing `stream` (thread-local capture mode).  The legacy NULL
+ * stream cannot be captured: RANMAR_EINVAL. */
+int ranmar_graph_begin(ranmar_stream_t stream);
+/* Ends the capture and instantiates it into *out. */
+int ranmar_graph_end(ranmar_stream_t stream, ranmar_graph_t **out);
+/* Replays the captured work on `stream`. */
+int ranmar_graph_launch(const ranmar_graph_t *g, ranmar_stream_t stream);
+/* Frees the graph.  NULL is a no-op. */
+int ranmar_graph_destroy(ranmar_graph_t *g);
+
 /* Name of a return code (static string, never NULL). */
 const char *ranmar_strerror(int code);
 

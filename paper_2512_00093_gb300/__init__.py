@@ -5,8 +5,8 @@ The compute path is libranmar (CUDA, sm_103a), reached through the C ABI in
 include/ranmar.h; this package is its thin binding plus the build step.
 """
 from .binding import (  # noqa: F401
-    DESC_WRITE_BACK, MAX_EXP_WORDS, R, ST_BAD_INDEX, ST_OUT_RANGE, STATE_WORDS,
-    RanmarError, abi_version, exps_tensor, generate_f32, generate_plain_f32,
-    generate_plain_u24, generate_u24, jump, lib_path, make_desc, partition, seed,
-    state_words_np, words,
+    DESC_WRITE_BACK, MAX_EXP_WORDS, R, ST_BAD_INDEX, ST_OUT_RANGE, STATE_WORDS, Batch,
+    BatchConfig, Graph, RanmarError, abi_version, capture, exps_tensor, generate_f32,
+    generate_plain_f32, generate_plain_u24, generate_u24, jump, lib_path, make_desc,
+    partition, seed, shape_bucket, state_words_np, tune_cached, words,
 )

@@ -37,6 +37,15 @@ class RanmarError(RuntimeError):
         self.code = code
 
 
+class BatchConfig(ctypes.Structure):
+    """ranmar_batch_config_t."""
+    _fields_ = [("lanes_per_stream", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.lanes_per_stream, self.threads_per_cta, self.ctas_per_sm, self.chunk)
+
+
 _L: ctypes.CDLL | None = None
 _vp = ctypes.c_void_p
 _sz = ctypes.c_size_t
@@ -56,9 +65,26 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         getattr(lib, name).argtypes = [_vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp]
     for name in ("ranmar_generate_plain_u24", "ranmar_generate_plain_f32"):
         getattr(lib, name).argtypes = [_vp, _u64, _vp, ctypes.c_int, _vp]
+    lib.ranmar_batch_create.argtypes = [_sz, ctypes.POINTER(_vp)]
+    lib.ranmar_batch_destroy.argtypes = [_vp]
+    lib.ranmar_batch_set_config.argtypes = [_vp, ctypes.POINTER(BatchConfig)]
+    lib.ranmar_batch_get_config.argtypes = [_vp, ctypes.POINTER(BatchConfig)]
+    lib.ranmar_batch_pack.argtypes = [_vp, _vp, _sz, _u32, _vp, _vp, _vp, _vp]
+    for name in ("ranmar_batch_generate_u24", "ranmar_batch_generate_f32"):
+        getattr(lib, name).argtypes = [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp, _vp]
+    lib.ranmar_batch_tune.argtypes = [_vp, ctypes.c_int, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp,
+                                      ctypes.POINTER(ctypes.c_float)]
+    lib.ranmar_graph_begin.argtypes = [_vp]
+    lib.ranmar_graph_end.argtypes = [_vp, ctypes.POINTER(_vp)]
+    lib.ranmar_graph_launch.argtypes = [_vp, _vp]
+    lib.ranmar_graph_destroy.argtypes = [_vp]
     for name in ("ranmar_seed", "ranmar_jump", "ranmar_partition", "ranmar_generate_u24",
                  "ranmar_generate_f32", "ranmar_generate_plain_u24",
-                 "ranmar_generate_plain_f32"):
+                 "ranmar_generate_plain_f32", "ranmar_batch_create", "ranmar_batch_destroy",
+                 "ranmar_batch_set_config", "ranmar_batch_get_config", "ranmar_batch_pack",
+                 "ranmar_batch_generate_u24", "ranmar_batch_generate_f32", "ranmar_batch_tune",
+                 "ranmar_graph_begin", "ranmar_graph_end", "ranmar_graph_launch",
+                 "ranmar_graph_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -225,3 +251,176 @@ def generate_plain_f32(state, count: int, out, write_back: bool = True, stream=N
 def state_words_np(states: torch.Tensor) -> np.ndarray:
     """(n, 100) int32 tensor -> (n, 100) uint32 numpy view on the host."""
     return states.reshape(-1, STATE_WORDS).cpu().numpy().view(np.uint32)
+
+
+# ---------------------------------------------------------------------------
+# persistent batch path
+# ---------------------------------------------------------------------------
+class Batch:
+    """ranmar_batch_t: workspace of the persistent path on the current device."""
+
+    def __init__(self, capacity: int):
+        h = ctypes.c_void_p()
+        _check(_lib().ranmar_batch_create(int(capacity), ctypes.byref(h)), "ranmar_batch_create")
+        self._h = h
+        self.capacity = int(capacity)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().ranmar_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def config(self) -> tuple:
+        c = BatchConfig()
+        _check(_lib().ranmar_batch_get_config(self._h, ctypes.byref(c)), "ranmar_batch_get_config")
+        return c.as_tuple()
+
+    @config.setter
+    def config(self, cfg) -> None:
+        c = BatchConfig(*[int(v) for v in cfg])
+        _check(_lib().ranmar_batch_set_config(self._h, ctypes.byref(c)), "ranmar_batch_set_config")
+
+    def pack(self, counts: torch.Tensor, flags: int = 0, order: bool = True, stream=None):
+        """ranmar_batch_pack: counts (n,) int64 -> (desc (n,3) int64, order (n,) int32 or
+        None, total (1,) int64), all on the device."""
+        _need(counts, torch.int64, "counts")
+        n = counts.numel()
+        desc = torch.empty((n, DESC_WORDS64), dtype=torch.int64, device=counts.device)
+        ordt = torch.empty(n, dtype=torch.int32, device=counts.device) if order else None
+        total = torch.empty(1, dtype=torch.int64, device=counts.device)
+        _check(_lib().ranmar_batch_pack(self._h, _ptr(counts), n, int(flags), _ptr(desc),
+                                        _ptr(ordt), _ptr(total), _stream(stream)),
+               "ranmar_batch_pack")
+        return desc, ordt, total
+
+    def _gen(self, fn, dtype, states, desc, out, order, status, stream):
+        states = states.reshape(-1, STATE_WORDS)
+        _need(states, torch.int32, "states")
+        _need(desc, torch.int64, "desc")
+        _need(out, dtype, "out")
+        if order is not None:
+            _need(order, torch.int32, "order")
+        if status is not None:
+            _need(status, torch.int32, "status")
+        _check(getattr(_lib(), fn)(self._h, _ptr(states), states.shape[0], _ptr(desc),
+                                   desc.shape[0], _ptr(order), _ptr(out), out.numel(),
+                                   _ptr(status), _stream(stream)), fn)
+        return out
+
+    def generate_u24(self, states, desc, out, order=None, status=None, stream=None):
+        """ranmar_batch_generate_u24 (persistent kernel, tuned config)."""
+        return self._gen("ranmar_batch_generate_u24", torch.int32, states, desc, out, order,
+                         status, stream)
+
+    def generate_f32(self, states, desc, out, order=None, status=None, stream=None):
+        """ranmar_batch_generate_f32 (persistent kernel, tuned config)."""
+        return self._gen("ranmar_batch_generate_f32", torch.float32, states, desc, out, order,
+                         status, stream)
+
+    def tune(self, states, desc, out, order=None, stream=None):
+        """ranmar_batch_tune: times the candidate configs on this batch (states are
+        not advanced) and keeps the fastest.  Returns (config, best_ms)."""
+        states = states.reshape(-1, STATE_WORDS)
+        f32 = out.dtype == torch.float32
+        ms = ctypes.c_float(0.0)
+        _check(_lib().ranmar_batch_tune(self._h, int(f32), _ptr(states), states.shape[0],
+                                        _ptr(desc), desc.shape[0], _ptr(order), _ptr(out),
+                                        out.numel(), _stream(stream), ctypes.byref(ms)),
+               "ranmar_batch_tune")
+        return self.config, ms.value
+
+
+def _cache_path() -> str:
+    return os.environ.get("RANMAR_AUTOTUNE_CACHE",
+                          os.path.join(os.path.dirname(LIB), "autotune.json"))
+
+
+def shape_bucket(n: int, total: int, f32: bool) -> str:
+    """Autotune cache key part: log2 of the stream count and of the mean length."""
+    mean = max(1, total // max(1, n))
+    return f"{'f32' if f32 else 'u24'}|n2^{max(0, n.bit_length() - 1)}|len2^{mean.bit_length() - 1}"
+
+
+def tune_cached(batch: "Batch", states, desc, out, order=None, total: int | None = None,
+                stream=None):
+    """Autotuner with a JSON cache keyed by (GPU name, kernel, shape bucket): a hit
+    sets the stored config, a miss runs ranmar_batch_tune and stores the result."""
+    import json
+    n = desc.shape[0]
+    if total is None:
+        total = int(desc[:, 2].sum().item())
+    key = "|".join([torch.cuda.get_device_name(), "generate_persistent",
+                    shape_bucket(n, total, out.dtype == torch.float32)])
+    path = _cache_path()
+    cache = {}
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    if key in cache:
+        batch.config = tuple(cache[key]["config"])
+        return batch.config, cache[key]["ms"], True
+    cfg, ms = batch.tune(states, desc, out, order, stream)
+    cache[key] = {"config": list(cfg), "ms": ms}
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return cfg, ms, False
+
+
+# ---------------------------------------------------------------------------
+# CUDA graphs
+# ---------------------------------------------------------------------------
+class Graph:
+    """ranmar_graph_t: a captured sequence of library calls, replayed with one launch."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def launch(self, stream=None):
+        _check(_lib().ranmar_graph_launch(self._h, _stream(stream)), "ranmar_graph_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().ranmar_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class capture:
+    """Context manager: capture the library calls issued on `stream` (a non-default
+    torch.cuda.Stream) into a Graph: `with capture(s) as cap: ...; cap.graph.launch(s)`."""
+
+    def __init__(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        self.graph: Graph | None = None
+
+    def __enter__(self):
+        _check(_lib().ranmar_graph_begin(_stream(self.stream)), "ranmar_graph_begin")
+        return self
+
+    def __exit__(self, et, ev, tb):
+        h = ctypes.c_void_p()
+        rc = _lib().ranmar_graph_end(_stream(self.stream), ctypes.byref(h))
+        if et is None:
+            _check(rc, "ranmar_graph_end")
+            self.graph = Graph(h)
+        return False

@@ -1,0 +1,143 @@
+// batch.cuh -- packing a batch of uneven streams for the persistent kernel.
+//
+// From per-stream counts the device builds the descriptors (output offsets =
+// exclusive prefix sum of the counts, so the outputs are packed back to
+// back) and a longest-first visiting order (streams bucketed by
+// floor(log2(count)), buckets in decreasing order), which keeps the
+// persistent kernel's tail short.  The order within a bucket is whatever the
+// atomics give; it does not affect any output, because every descriptor
+// writes only its own slice.
+//
+// Prefix sum: three passes over tiles of kScanTile counts -- tile sums,
+// one-CTA scan of the tile sums, then the tile-local scans -- with the tile
+// sums in the batch workspace.
+#pragma once
+
+#include "ranmar_device.cuh"
+
+namespace ranmar {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = 4;
+constexpr int kScanTile = kScanThreads * kScanPerThread;  // 1024 counts per CTA
+constexpr int kBuckets = 65;                               // 0, or floor(log2(count)) + 1
+
+// Exclusive scan of one value per thread across the CTA; returns the
+// exclusive prefix and writes the CTA total to *total.
+__device__ __forceinline__ uint64_t cta_exclusive_scan(uint64_t v, uint64_t* total) {
+  __shared__ uint64_t warp_sums[kScanThreads / 32];
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t t = __shfl_up_sync(kFull, inc, d);
+    if (lane >= static_cast<unsigned>(d)) inc += t;
+  }
+  if (lane == 31) warp_sums[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t t = __shfl_up_sync(kFull, w, d);
+      if (lane >= static_cast<unsigned>(d)) w += t;
+    }
+    if (lane < kScanThreads / 32) warp_sums[lane] = w;  // inclusive warp prefix
+  }
+  __syncthreads();
+  const uint64_t before = warp ? warp_sums[warp - 1] : 0;
+  *total = warp_sums[kScanThreads / 32 - 1];
+  __syncthreads();
+  return before + inc - v;
+}
+
+__device__ __forceinline__ int count_bucket(uint64_t c) {
+  return c ? 64 - __clzll(static_cast<long long>(c)) : 0;  // 0 for empty, else log2 + 1
+}
+
+// Pass 1: sum of each tile of counts; also the bucket histogram.
+__global__ void __launch_bounds__(kScanThreads) pack_tile_sums(const uint64_t* __restrict__ counts,
+                                                               uint64_t n,
+                                                               uint64_t* __restrict__ tile_sums,
+                                                               uint32_t* __restrict__ hist) {
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanTile;
+  uint64_t s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanPerThread; ++j) {
+    const uint64_t i = base + static_cast<uint64_t>(j) * kScanThreads + threadIdx.x;
+    if (i < n) {
+      const uint64_t c = counts[i];
+      s += c;
+      atomicAdd(&hist[count_bucket(c)], 1u);
+    }
+  }
+  uint64_t total;
+  (void)cta_exclusive_scan(s, &total);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// Pass 2 (one CTA): exclusive scan of the tile sums in place; *grand_total
+// receives the sum of all counts.  Also turns the bucket histogram into
+// start positions, largest bucket first (cursor[b] = first slot of bucket b).
+__global__ void __launch_bounds__(kScanThreads) pack_scan_tiles(uint64_t* __restrict__ tile_sums,
+                                                                uint64_t n_tiles,
+                                                                uint64_t* __restrict__ grand_total,
+                                                                const uint32_t* __restrict__ hist,
+                                                                uint32_t* __restrict__ cursor) {
+  uint64_t carry = 0;
+#pragma unroll 1
+  for (uint64_t b0 = 0; b0 < n_tiles; b0 += kScanThreads) {
+    const uint64_t i = b0 + threadIdx.x;
+    const uint64_t v = i < n_tiles ? tile_sums[i] : 0;
+    uint64_t total;
+    const uint64_t ex = cta_exclusive_scan(v, &total);
+    if (i < n_tiles) tile_sums[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) {
+    *grand_total = carry;
+    uint32_t pos = 0;
+    for (int b = kBuckets - 1; b >= 0; --b) {
+      cursor[b] = pos;
+      pos += hist[b];
+    }
+  }
+}
+
+// Pass 3: descriptors with packed offsets, and the longest-first order.
+__global__ void __launch_bounds__(kScanThreads) pack_write(const uint64_t* __restrict__ counts,
+                                                           uint64_t n,
+                                                           const uint64_t* __restrict__ tile_off,
+                                                           uint32_t flags,
+                                                           ranmar_desc_t* __restrict__ desc,
+                                                           uint32_t* __restrict__ cursor,
+                                                           uint32_t* __restrict__ order) {
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanTile;
+  // Thread t owns counts base + 4t .. 4t+3 so that its local scan is serial.
+  uint64_t c[kScanPerThread];
+  uint64_t s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanPerThread; ++j) {
+    const uint64_t i = base + static_cast<uint64_t>(threadIdx.x) * kScanPerThread + j;
+    c[j] = i < n ? counts[i] : 0;
+    s += c[j];
+  }
+  uint64_t total;
+  uint64_t off = tile_off[blockIdx.x] + cta_exclusive_scan(s, &total);
+#pragma unroll
+  for (int j = 0; j < kScanPerThread; ++j) {
+    const uint64_t i = base + static_cast<uint64_t>(threadIdx.x) * kScanPerThread + j;
+    if (i < n) {
+      ranmar_desc_t d;
+      d.state_idx = static_cast<uint32_t>(i);
+      d.flags = flags;
+      d.out_offset = off;
+      d.count = c[j];
+      desc[i] = d;
+      if (order) order[atomicAdd(&cursor[count_bucket(c[j])], 1u)] = static_cast<uint32_t>(i);
+    }
+    off += c[j];
+  }
+}
+
+}  // namespace ranmar

@@ -1,18 +1,20 @@
-// generate.cuh -- warp-step generation of RANMAR outputs (Algorithm 2).
+// generate.cuh -- group-step generation of RANMAR outputs (Algorithm 2).
 //
-// One warp owns one stream.  With the state as a sequence X(q), the new word
-// X(q) = X(q-97) - X(q-33) only depends on words at least 33 positions back,
-// so the 32 lanes compute 32 consecutive words per step.  Because 97 and 33
-// are both 1 mod 32, the two inputs of lane L sit at lane L-1 of blocks b-3
-// and b-1.  The window is therefore kept ROTATED by one lane: register
-// R_b[L] = X(32b + L - 1), lane 0 taking the last word of the previous block
-// from a carry.  A step is then
-//     X(32b + L) = R_{b-3}[L] - R_{b-1}[L]          (no data movement)
-//     R_b[L]     = shfl(X, L - 1), lane 0 <- carry  (one shuffle)
-// and the 97 state words are exactly R_{b-3}, R_{b-2}, R_{b-1} and the carry.
-// c_n of each lane comes in closed form (Sec. 3.2): lane L of step b uses
-// c_{32b+L+1} = (c_{32b} - (L+1) d) mod m.  Output (X - c) mod 2^24 is stored
-// coalesced (32 consecutive words per warp store, streaming hint).
+// A group of W lanes (W = 32, 16, 8 or 4) owns one stream.  With the state as
+// a sequence X(q), the new word X(q) = X(q-97) - X(q-33) only depends on
+// words at least 33 positions back, so the W lanes compute W consecutive
+// words per step.  97 = (96/W) W + 1 and 33 = (32/W) W + 1, so the two
+// inputs of lane L sit at lane L-1 of blocks b - 96/W and b - 32/W.  The
+// window is therefore kept ROTATED by one lane: register R_b[L] =
+// X(Wb + L - 1), lane 0 taking the last word of the previous block from a
+// carry.  A step is then
+//     X(Wb + L) = R_{b-96/W}[L] - R_{b-32/W}[L]     (no data movement)
+//     R_b[L]    = shfl(X, L - 1), lane 0 <- carry   (one shuffle)
+// and the 97 state words are exactly the 96/W ring registers of the group
+// plus the carry.  c_n of each lane comes in closed form (Sec. 3.2): lane L
+// of step b uses c_{Wb+L+1} = (c_{Wb} - (L+1) d) mod m.  Output
+// (X - c) mod 2^24 is stored coalesced (W consecutive words per step,
+// streaming hint).
 #pragma once
 
 #include "ranmar_device.cuh"
@@ -31,91 +33,106 @@ __device__ __forceinline__ void store_output(void* out, uint64_t idx, uint32_t y
 
 struct LaneConsts {
   uint32_t delta_lane;  // (L + 1) d mod m
-  uint32_t delta32;     // 32 d mod m
+  uint32_t delta_w;     // W d mod m
 };
 
-__device__ __forceinline__ LaneConsts lane_consts(unsigned lane) {
-  return LaneConsts{mul_d_mod_m(lane + 1), mul_d_mod_m(32)};
-}
-
-// One 32-word step; `older` holds R_{b-3} on entry and R_b on exit,
-// `newer` holds R_{b-1}.
-template <bool F32>
-__device__ __forceinline__ void warp_step(uint32_t& older, uint32_t newer, uint32_t& carry,
-                                          uint32_t& cb, const LaneConsts& k, unsigned lane,
-                                          void* out, uint64_t& o) {
-  const uint32_t xv = older - newer;               // X(32b + L), kept mod 2^32
-  const uint32_t cl = sub_mod_m(cb, k.delta_lane);  // c_{32b+L+1}
-  store_output<F32>(out, o, (xv - cl) & kMask24);
-  o += 32;
-  cb = sub_mod_m(cb, k.delta32);
-  const uint32_t t = __shfl_sync(kFull, xv, (lane + 31) & 31);
-  older = (lane == 0) ? carry : t;
-  carry = t;
+template <int W>
+__device__ __forceinline__ LaneConsts lane_consts(unsigned gl) {
+  return LaneConsts{mul_d_mod_m(gl + 1), mul_d_mod_m(W)};
 }
 
 // Generates `count` outputs of *st into out[out_base + n], n < count, and
-// optionally writes the advanced state back.  Called by all 32 lanes.
-template <bool F32>
+// optionally writes the advanced state back.  Called by the W lanes of one
+// group (gl = lane within the group, gmask = the group's lane mask).
+template <int W, bool F32>
 __device__ void generate_stream(ranmar_state_t* st, uint64_t count, void* out, uint64_t out_base,
-                                bool write_back, unsigned lane, const LaneConsts& k) {
+                                bool write_back, unsigned gl, unsigned gmask,
+                                const LaneConsts& k) {
+  constexpr int NR = 96 / W;  // ring registers: blocks b-NR .. b-1
+  constexpr int Q = 32 / W;   // the newer input is block b-Q
+  static_assert(NR * W == 96 && Q * W == 32, "group width");
   const uint32_t* xs = st->x;
-  uint32_t s0 = xs[lane];       // R_{-3}[L] = X(-97 + L)
-  uint32_t s1 = xs[32 + lane];  // R_{-2}[L]
-  uint32_t s2 = xs[64 + lane];  // R_{-1}[L]
-  uint32_t carry = xs[96];      // X(-1)
-  uint32_t cb = st->c;          // c_0 of this call
+  uint32_t r[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) r[j] = xs[W * j + gl];  // R_{j-NR}[L] = X(W(j-NR) + L - 1)
+  uint32_t carry = xs[96];                               // X(-1)
+  uint32_t cb = st->c;
   const uint64_t pos0 = st->pos;
 
-  const uint64_t nblk = count >> 5;
-  const unsigned rem = static_cast<unsigned>(count & 31);
-  uint64_t o = out_base + lane;
+  const uint64_t nblk = count / W;
+  const unsigned rem = static_cast<unsigned>(count % W);
+  uint64_t o = out_base + gl;
+  const unsigned src = (gl + W - 1) % W;
+
+  // One step producing R_b into `older` (= R_{b-NR} on entry).
+  auto step = [&](uint32_t& older, uint32_t newer) {
+    const uint32_t xv = older - newer;                  // X(Wb + L), kept mod 2^32
+    const uint32_t cl = sub_mod_m(cb, k.delta_lane);    // c_{Wb+L+1}
+    store_output<F32>(out, o, (xv - cl) & kMask24);
+    o += W;
+    cb = sub_mod_m(cb, k.delta_w);
+    const uint32_t t = __shfl_sync(gmask, xv, src, W);
+    older = (gl == 0) ? carry : t;
+    carry = t;
+  };
 
   uint64_t b = 0;
 #pragma unroll 1
-  for (; b + 3 <= nblk; b += 3) {
-    warp_step<F32>(s0, s2, carry, cb, k, lane, out, o);
-    warp_step<F32>(s1, s0, carry, cb, k, lane, out, o);
-    warp_step<F32>(s2, s1, carry, cb, k, lane, out, o);
+  for (; b + NR <= nblk; b += NR) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) step(r[j], r[(j + NR - Q) % NR]);
   }
-  const unsigned left = static_cast<unsigned>(nblk - b);
-  if (left >= 1) warp_step<F32>(s0, s2, carry, cb, k, lane, out, o);
-  if (left >= 2) warp_step<F32>(s1, s0, carry, cb, k, lane, out, o);
-
-  // Canonical roles after B = nblk full blocks: R_{B-3}, R_{B-2}, R_{B-1}.
-  uint32_t rm3, rm2, rm1;
-  if (left == 0) {
-    rm3 = s0; rm2 = s1; rm1 = s2;
-  } else if (left == 1) {
-    rm3 = s1; rm2 = s2; rm1 = s0;
-  } else {
-    rm3 = s2; rm2 = s0; rm1 = s1;
+  // Remaining blocks: step, then shift the ring so that r[0] stays oldest.
+#pragma unroll 1
+  for (; b < nblk; ++b) {
+    step(r[0], r[NR - Q]);
+    const uint32_t nw = r[0];
+#pragma unroll
+    for (int j = 0; j + 1 < NR; ++j) r[j] = r[j + 1];
+    r[NR - 1] = nw;
   }
 
   // Ragged tail: one more block with masked stores.
   uint32_t xb = 0;
   uint32_t c_end = cb;
   if (rem != 0) {
-    xb = rm3 - rm1;  // X(32B + L)
+    xb = r[0] - r[NR - Q];  // X(WB + L)
     const uint32_t cl = sub_mod_m(cb, k.delta_lane);
-    if (lane < rem) store_output<F32>(out, o, (xb - cl) & kMask24);
-    c_end = __shfl_sync(kFull, cl, rem - 1);
+    if (gl < rem) store_output<F32>(out, o, (xb - cl) & kMask24);
+    c_end = __shfl_sync(gmask, cl, rem - 1, W);
   }
 
   if (!write_back) return;
-  __syncwarp();
-  // Positions relative to 32B: rm3 = X(L-97), rm2 = X(L-65), rm1 = X(L-33),
-  // carry (lane 0) = X(-1), xb = X(L).  New state word q = X(rem - 97 + q).
+  __syncwarp(gmask);
+  // Positions relative to WB: r[j] = X(Wj + L - 97), carry (lane 0) = X(-1),
+  // xb = X(L).  New state word q = X(rem - 97 + q).
   uint32_t* xw = st->x;
-  if (lane >= rem) xw[lane - rem] = rm3 & kMask24;
-  xw[lane + 32 - rem] = rm2 & kMask24;
-  xw[lane + 64 - rem] = rm1 & kMask24;
-  if (lane == 0) xw[96 - rem] = carry & kMask24;
-  if (lane < rem) xw[lane + 97 - rem] = xb & kMask24;
-  if (lane == 0) {
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int q = W * j + static_cast<int>(gl) - static_cast<int>(rem);
+    if (q >= 0) xw[q] = r[j] & kMask24;
+  }
+  if (gl == 0) xw[96 - rem] = carry & kMask24;
+  if (gl < rem) xw[gl + 97 - rem] = xb & kMask24;
+  if (gl == 0) {
     st->c = c_end;
     st->pos = pos0 + count;
   }
+}
+
+// Checks one descriptor on the device; returns false (and flags the status
+// word from the group's first lane) when it must be skipped.
+__device__ __forceinline__ bool desc_ok(const ranmar_desc_t& d, uint64_t n_states,
+                                        uint64_t out_len, uint32_t* status, unsigned gl) {
+  if (d.state_idx >= n_states) {
+    if (gl == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
+    return false;
+  }
+  if (d.count > out_len || d.out_offset > out_len - d.count) {
+    if (gl == 0) flag_status(status, RANMAR_ST_OUT_RANGE);
+    return false;
+  }
+  return true;
 }
 
 // Batch of descriptors, one warp per descriptor (grid-stride over warps).
@@ -127,20 +144,54 @@ __global__ void __launch_bounds__(256) generate_desc_kernel(
   const unsigned lane = threadIdx.x & 31;
   const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-  const LaneConsts k = lane_consts(lane);
+  const LaneConsts k = lane_consts<32>(lane);
 #pragma unroll 1
   for (uint64_t w = warp; w < n_desc; w += nwarps) {
     const ranmar_desc_t d = desc[w];
-    if (d.state_idx >= n_states) {
-      if (lane == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
-      continue;
+    if (!desc_ok(d, n_states, out_len, status, lane)) continue;
+    generate_stream<32, F32>(states + d.state_idx, d.count, out, d.out_offset,
+                             (d.flags & RANMAR_DESC_WRITE_BACK) != 0, lane, kFull, k);
+  }
+}
+
+// Persistent batch kernel: groups of W lanes pull `chunk` descriptors at a
+// time from an atomic queue (*queue must be 0 at launch), in the order
+// given by `order` (e.g. longest first) or in index order when it is null.
+// `allow_write_back` = 0 ignores the write-back flags (used while tuning, so
+// that timing runs leave the states untouched).
+template <int W, bool F32>
+__global__ void generate_persistent_kernel(ranmar_state_t* __restrict__ states,
+                                           uint64_t n_states,
+                                           const ranmar_desc_t* __restrict__ desc,
+                                           uint64_t n_desc, const uint32_t* __restrict__ order,
+                                           void* out, uint64_t out_len, uint32_t* status,
+                                           unsigned long long* queue, uint32_t chunk,
+                                           int allow_write_back) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gl = lane % W;
+  const unsigned gbase = lane - gl;
+  const unsigned gmask = (W == 32) ? kFull : (((1u << W) - 1u) << gbase);
+  const LaneConsts k = lane_consts<W>(gl);
+#pragma unroll 1
+  while (true) {
+    unsigned long long base = 0;
+    if (gl == 0) base = atomicAdd(queue, static_cast<unsigned long long>(chunk));
+    base = __shfl_sync(gmask, base, gbase);
+    if (base >= n_desc) break;
+    const uint64_t end = min(static_cast<uint64_t>(base) + chunk, n_desc);
+#pragma unroll 1
+    for (uint64_t t = base; t < end; ++t) {
+      const uint64_t di = order ? order[t] : t;
+      if (di >= n_desc) {
+        if (gl == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
+        continue;
+      }
+      const ranmar_desc_t d = desc[di];
+      if (!desc_ok(d, n_states, out_len, status, gl)) continue;
+      generate_stream<W, F32>(states + d.state_idx, d.count, out, d.out_offset,
+                              allow_write_back && (d.flags & RANMAR_DESC_WRITE_BACK) != 0, gl,
+                              gmask, k);
     }
-    if (d.count > out_len || d.out_offset > out_len - d.count) {
-      if (lane == 0) flag_status(status, RANMAR_ST_OUT_RANGE);
-      continue;
-    }
-    generate_stream<F32>(states + d.state_idx, d.count, out, d.out_offset,
-                         (d.flags & RANMAR_DESC_WRITE_BACK) != 0, lane, k);
   }
 }
 
@@ -149,7 +200,7 @@ template <bool F32>
 __global__ void __launch_bounds__(32) generate_plain_kernel(ranmar_state_t* st, uint64_t count,
                                                             void* out, int write_back) {
   const unsigned lane = threadIdx.x & 31;
-  generate_stream<F32>(st, count, out, 0, write_back != 0, lane, lane_consts(lane));
+  generate_stream<32, F32>(st, count, out, 0, write_back != 0, lane, kFull, lane_consts<32>(lane));
 }
 
 }  // namespace ranmar

@@ -5,11 +5,32 @@
 // jump.cuh (Sec. 3.1 / 3.2 jump-ahead).
 #include <cstdio>
 #include <cstring>
+#include <new>
 
 #include "ranmar.h"
 #include "ranmar_device.cuh"
 #include "generate.cuh"
 #include "jump.cuh"
+#include "batch.cuh"
+
+// Batch handle: the workspace of the persistent path on one device.
+struct ranmar_batch {
+  int device;
+  int num_sms;
+  size_t capacity;             // streams the workspace can pack
+  unsigned char* ws;           // device workspace (one cudaMalloc)
+  unsigned long long* queue;   // work-queue counter of the persistent kernel
+  uint64_t* total;             // grand total of a pack
+  uint32_t* hist;              // bucket histogram
+  uint32_t* cursor;            // bucket cursors
+  uint64_t* tile_sums;         // ceil(capacity / 1024) tile sums
+  ranmar_batch_config_t cfg;
+};
+
+struct ranmar_graph {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
 
 namespace {
 
@@ -102,6 +123,96 @@ int launch_jump(const ranmar_state_t* base, size_t n_base, const uint32_t* base_
   ranmar::jump_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kJumpSmemBytes, s>>>(
       base, n_base, base_idx, exp, exp_words, part, mode, out, n, status);
   return check_launch();
+}
+
+template <int W, bool F32>
+int persistent_occupancy(int threads) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &nb, ranmar::generate_persistent_kernel<W, F32>, threads, 0);
+  return nb;
+}
+
+template <int W, bool F32>
+void persistent_launch(unsigned grid, unsigned threads, cudaStream_t s, ranmar_state_t* states,
+                       size_t n_states, const ranmar_desc_t* desc, size_t n_desc,
+                       const uint32_t* order, void* out, size_t out_len, uint32_t* status,
+                       unsigned long long* queue, uint32_t chunk, int allow_wb) {
+  ranmar::generate_persistent_kernel<W, F32><<<grid, threads, 0, s>>>(
+      states, n_states, desc, n_desc, order, out, out_len, status, queue, chunk, allow_wb);
+}
+
+bool config_ok(const ranmar_batch_config_t& c) {
+  const int w = c.lanes_per_stream;
+  return (w == 32 || w == 16 || w == 8 || w == 4) && c.threads_per_cta >= 32 &&
+         c.threads_per_cta <= 1024 && c.threads_per_cta % 32 == 0 && c.ctas_per_sm >= 0 &&
+         c.ctas_per_sm <= 64 && c.chunk >= 1;
+}
+
+bool on_device(const ranmar_batch* b) {
+  int dev = -1;
+  return b && cudaGetDevice(&dev) == cudaSuccess && dev == b->device;
+}
+
+// Enqueues queue reset + persistent kernel with config c.
+int run_persistent(ranmar_batch* b, const ranmar_batch_config_t& c, bool f32,
+                   ranmar_state_t* states, size_t n_states, const ranmar_desc_t* desc,
+                   size_t n_desc, const uint32_t* order, void* out, size_t out_len,
+                   uint32_t* status, cudaStream_t s, int allow_wb) {
+  const int W = c.lanes_per_stream, T = c.threads_per_cta;
+  int occ = 0;
+#define RANMAR_OCC(WW) \
+  occ = f32 ? persistent_occupancy<WW, true>(T) : persistent_occupancy<WW, false>(T)
+  switch (W) {
+    case 32: RANMAR_OCC(32); break;
+    case 16: RANMAR_OCC(16); break;
+    case 8: RANMAR_OCC(8); break;
+    default: RANMAR_OCC(4); break;
+  }
+#undef RANMAR_OCC
+  if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration);
+  const int per_sm = c.ctas_per_sm > 0 ? (c.ctas_per_sm < occ ? c.ctas_per_sm : occ) : occ;
+  // Enough CTAs for the work, at most one resident wave.
+  const uint64_t groups_needed = (n_desc + c.chunk - 1) / c.chunk;
+  const uint64_t groups_per_cta = static_cast<uint64_t>(T / W);
+  uint64_t grid = static_cast<uint64_t>(per_sm) * b->num_sms;
+  const uint64_t need = (groups_needed + groups_per_cta - 1) / groups_per_cta;
+  if (need < grid) grid = need;
+  if (grid < 1) grid = 1;
+  cudaError_t e = cudaMemsetAsync(b->queue, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e);
+#define RANMAR_LAUNCH(WW)                                                                      \
+  do {                                                                                         \
+    if (f32)                                                                                   \
+      persistent_launch<WW, true>(static_cast<unsigned>(grid), T, s, states, n_states, desc,   \
+                                  n_desc, order, out, out_len, status, b->queue, c.chunk,      \
+                                  allow_wb);                                                   \
+    else                                                                                       \
+      persistent_launch<WW, false>(static_cast<unsigned>(grid), T, s, states, n_states, desc,  \
+                                   n_desc, order, out, out_len, status, b->queue, c.chunk,     \
+                                   allow_wb);                                                  \
+  } while (0)
+  switch (W) {
+    case 32: RANMAR_LAUNCH(32); break;
+    case 16: RANMAR_LAUNCH(16); break;
+    case 8: RANMAR_LAUNCH(8); break;
+    default: RANMAR_LAUNCH(4); break;
+  }
+#undef RANMAR_LAUNCH
+  return check_launch();
+}
+
+int batch_generate(ranmar_batch* b, bool f32, ranmar_state_t* states, size_t n_states,
+                   const ranmar_desc_t* desc, size_t n_desc, const uint32_t* order, void* out,
+                   size_t out_len, uint32_t* status, ranmar_stream_t stream) {
+  if (!on_device(b)) return RANMAR_EINVAL;
+  if (n_desc == 0) return RANMAR_OK;
+  if (!states || !desc || !out) return RANMAR_EINVAL;
+  if (n_states == 0) return RANMAR_ERANGE;
+  if (!aligned(states, 16) || !aligned(desc, 8) || !aligned(out, 4) || !aligned(order, 4))
+    return RANMAR_EINVAL;
+  return run_persistent(b, b->cfg, f32, states, n_states, desc, n_desc, order, out, out_len,
+                        status, reinterpret_cast<cudaStream_t>(stream), 1);
 }
 
 }  // namespace
@@ -200,6 +311,209 @@ int ranmar_generate_plain_u24(ranmar_state_t* d_state, uint64_t count, uint32_t*
 int ranmar_generate_plain_f32(ranmar_state_t* d_state, uint64_t count, float* d_out,
                               int write_back, ranmar_stream_t stream) {
   return launch_plain(true, d_state, count, d_out, write_back, stream);
+}
+
+int ranmar_batch_create(size_t capacity, ranmar_batch_t** out) {
+  if (!out) return RANMAR_EINVAL;
+  *out = nullptr;
+  if (capacity == 0 || capacity >= (static_cast<size_t>(1) << 32)) return RANMAR_ERANGE;
+  ranmar_batch* b = new (std::nothrow) ranmar_batch{};
+  if (!b) return RANMAR_ENOMEM;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e);
+  }
+  const size_t n_tiles = (capacity + ranmar::kScanTile - 1) / ranmar::kScanTile;
+  // [0] queue, [8] total, [256] hist (65 words), [768] cursor (65 words),
+  // [1280] tile sums.
+  const size_t bytes = 1280 + n_tiles * sizeof(uint64_t);
+  e = cudaMalloc(&b->ws, bytes);
+  if (e != cudaSuccess) {
+    delete b;
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      return RANMAR_ENOMEM;
+    }
+    return cuda_fail(e);
+  }
+  b->capacity = capacity;
+  b->queue = reinterpret_cast<unsigned long long*>(b->ws);
+  b->total = reinterpret_cast<uint64_t*>(b->ws + 8);
+  b->hist = reinterpret_cast<uint32_t*>(b->ws + 256);
+  b->cursor = reinterpret_cast<uint32_t*>(b->ws + 768);
+  b->tile_sums = reinterpret_cast<uint64_t*>(b->ws + 1280);
+  static_assert(ranmar::kBuckets * sizeof(uint32_t) <= 512, "workspace layout");
+  b->cfg = ranmar_batch_config_t{32, 256, 0, 1};
+  *out = b;
+  return RANMAR_OK;
+}
+
+int ranmar_batch_destroy(ranmar_batch_t* b) {
+  if (!b) return RANMAR_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  const cudaError_t e = cudaFree(b->ws);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete b;
+  return e == cudaSuccess ? RANMAR_OK : cuda_fail(e);
+}
+
+int ranmar_batch_set_config(ranmar_batch_t* b, const ranmar_batch_config_t* cfg) {
+  if (!b || !cfg || !config_ok(*cfg)) return RANMAR_EINVAL;
+  b->cfg = *cfg;
+  return RANMAR_OK;
+}
+
+int ranmar_batch_get_config(const ranmar_batch_t* b, ranmar_batch_config_t* cfg) {
+  if (!b || !cfg) return RANMAR_EINVAL;
+  *cfg = b->cfg;
+  return RANMAR_OK;
+}
+
+int ranmar_batch_pack(ranmar_batch_t* b, const uint64_t* d_counts, size_t n, uint32_t flags,
+                      ranmar_desc_t* d_desc, uint32_t* d_order, uint64_t* d_total,
+                      ranmar_stream_t stream) {
+  if (!on_device(b)) return RANMAR_EINVAL;
+  if (n > b->capacity) return RANMAR_ERANGE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint64_t* total = d_total ? d_total : b->total;
+  if (n == 0) {
+    if (!d_total) return RANMAR_OK;
+    const cudaError_t e = cudaMemsetAsync(d_total, 0, sizeof(uint64_t), s);
+    return e == cudaSuccess ? RANMAR_OK : cuda_fail(e);
+  }
+  if (!d_counts || !d_desc) return RANMAR_EINVAL;
+  if (!aligned(d_counts, 8) || !aligned(d_desc, 8) || !aligned(d_order, 4) ||
+      !aligned(d_total, 8))
+    return RANMAR_EINVAL;
+  const unsigned tiles = static_cast<unsigned>((n + ranmar::kScanTile - 1) / ranmar::kScanTile);
+  cudaError_t e = cudaMemsetAsync(b->hist, 0, 1024, s);   // hist + cursor
+  if (e != cudaSuccess) return cuda_fail(e);
+  ranmar::pack_tile_sums<<<tiles, ranmar::kScanThreads, 0, s>>>(d_counts, n, b->tile_sums,
+                                                                  b->hist);
+  ranmar::pack_scan_tiles<<<1, ranmar::kScanThreads, 0, s>>>(b->tile_sums, tiles, total,
+                                                               b->hist, b->cursor);
+  ranmar::pack_write<<<tiles, ranmar::kScanThreads, 0, s>>>(d_counts, n, b->tile_sums, flags,
+                                                              d_desc, b->cursor, d_order);
+  return check_launch();
+}
+
+int ranmar_batch_generate_u24(ranmar_batch_t* b, ranmar_state_t* d_states, size_t n_states,
+                              const ranmar_desc_t* d_desc, size_t n_desc,
+                              const uint32_t* d_order, uint32_t* d_out, size_t out_len,
+                              uint32_t* d_status, ranmar_stream_t stream) {
+  return batch_generate(b, false, d_states, n_states, d_desc, n_desc, d_order, d_out, out_len,
+                        d_status, stream);
+}
+
+int ranmar_batch_generate_f32(ranmar_batch_t* b, ranmar_state_t* d_states, size_t n_states,
+                              const ranmar_desc_t* d_desc, size_t n_desc,
+                              const uint32_t* d_order, float* d_out, size_t out_len,
+                              uint32_t* d_status, ranmar_stream_t stream) {
+  return batch_generate(b, true, d_states, n_states, d_desc, n_desc, d_order, d_out, out_len,
+                        d_status, stream);
+}
+
+int ranmar_batch_tune(ranmar_batch_t* b, int f32, ranmar_state_t* d_states, size_t n_states,
+                      const ranmar_desc_t* d_desc, size_t n_desc, const uint32_t* d_order,
+                      void* d_out, size_t out_len, ranmar_stream_t stream, float* best_ms) {
+  if (!on_device(b)) return RANMAR_EINVAL;
+  if (n_desc == 0) return RANMAR_OK;
+  if (!d_states || !d_desc || !d_out) return RANMAR_EINVAL;
+  if (n_states == 0) return RANMAR_ERANGE;
+  if (!aligned(d_states, 16) || !aligned(d_desc, 8) || !aligned(d_out, 4) ||
+      !aligned(d_order, 4))
+    return RANMAR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(cudaGetLastError());
+  }
+  const int widths[] = {32, 16, 8};
+  const int threads[] = {128, 256, 512};
+  const int chunks[] = {1, 8};
+  float best = 0.0f;
+  ranmar_batch_config_t best_cfg = b->cfg;
+  int rc = RANMAR_OK;
+  for (int w : widths) {
+    for (int t : threads) {
+      for (int ch : chunks) {
+        const ranmar_batch_config_t c{w, t, 0, ch};
+        float ms_min = -1.0f;
+        for (int rep = 0; rep < 3 && rc == RANMAR_OK; ++rep) {
+          cudaEventRecord(e0, s);
+          rc = run_persistent(b, c, f32 != 0, d_states, n_states, d_desc, n_desc, d_order, d_out,
+                              out_len, nullptr, s, 0);
+          cudaEventRecord(e1, s);
+          const cudaError_t es = cudaEventSynchronize(e1);
+          if (rc == RANMAR_OK && es != cudaSuccess) rc = cuda_fail(es);
+          float ms = 0.0f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0 && (ms_min < 0.0f || ms < ms_min)) ms_min = ms;  // rep 0 warms up
+        }
+        if (rc != RANMAR_OK) break;
+        if (best == 0.0f || ms_min < best) {
+          best = ms_min;
+          best_cfg = c;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != RANMAR_OK) return rc;
+  b->cfg = best_cfg;
+  if (best_ms) *best_ms = best;
+  return RANMAR_OK;
+}
+
+int ranmar_graph_begin(ranmar_stream_t stream) {
+  if (!stream) return RANMAR_EINVAL;
+  const cudaError_t e = cudaStreamBeginCapture(reinterpret_cast<cudaStream_t>(stream),
+                                               cudaStreamCaptureModeThreadLocal);
+  return e == cudaSuccess ? RANMAR_OK : cuda_fail(e);
+}
+
+int ranmar_graph_end(ranmar_stream_t stream, ranmar_graph_t** out) {
+  if (!stream || !out) return RANMAR_EINVAL;
+  *out = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(reinterpret_cast<cudaStream_t>(stream), &g);
+  if (e != cudaSuccess) return cuda_fail(e);
+  ranmar_graph* r = new (std::nothrow) ranmar_graph{g, nullptr};
+  if (!r) {
+    cudaGraphDestroy(g);
+    return RANMAR_ENOMEM;
+  }
+  e = cudaGraphInstantiate(&r->exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    delete r;
+    return cuda_fail(e);
+  }
+  *out = r;
+  return RANMAR_OK;
+}
+
+int ranmar_graph_launch(const ranmar_graph_t* g, ranmar_stream_t stream) {
+  if (!g) return RANMAR_EINVAL;
+  const cudaError_t e = cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? RANMAR_OK : cuda_fail(e);
+}
+
+int ranmar_graph_destroy(ranmar_graph_t* g) {
+  if (!g) return RANMAR_OK;
+  cudaGraphExecDestroy(g->exec);
+  cudaGraphDestroy(g->graph);
+  delete g;
+  return RANMAR_OK;
 }
 
 }  // extern "C"
