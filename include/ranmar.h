@@ -240,6 +240,36 @@ int ranmar_batch_tune(ranmar_batch_t *b, int f32, ranmar_state_t *d_states, size
                       const ranmar_desc_t *d_desc, size_t n_desc, const uint32_t *d_order,
                       void *d_out, size_t out_len, ranmar_stream_t stream, float *best_ms);
 
+/*
+ * ranmar_batch_pack_static -- the same result as ranmar_batch_pack, for
+ * callers that cannot allocate device memory.  Some host programs own the
+ * whole GPU heap through their own allocator (a simulation package or a
+ * caching allocator that reserves device memory up front), so a cudaMalloc
+ * from a library would fail or fragment their pool, and some must not make
+ * allocation calls at all inside their time step.  This variant needs no
+ * ranmar_batch_t: its scratch (tile sums of the prefix sum, the bucket
+ * histogram and cursors) lives in a fixed 9,472-byte array compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  The paper has no counterpart; it is an interface convenience.
+ * Limits and behaviour:
+ *   - n <= RANMAR_PACK_STATIC_MAX streams, else RANMAR_ERANGE (nothing is
+ *     enqueued).
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - All calls share the one array and each call clears the parts that must
+ *     start at zero; two calls whose work overlaps on the GPU (different
+ *     streams, or different host threads) race and give wrong results.
+ *   - The caller still owns d_counts, d_desc, d_order and d_total; nothing
+ *     is allocated or freed.
+ * Errors: RANMAR_EINVAL (NULL d_counts/d_desc with n > 0, misalignment),
+ * RANMAR_ERANGE, RANMAR_ECUDA.
+ */
+#define RANMAR_PACK_STATIC_MAX 1048576
+int ranmar_batch_pack_static(const uint64_t *d_counts, size_t n, uint32_t flags,
+                             ranmar_desc_t *d_desc, uint32_t *d_order, uint64_t *d_total,
+                             ranmar_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * CUDA graphs: capture a sequence of the calls above on one stream and
  * replay it with one launch (buffers and arguments are frozen at capture).

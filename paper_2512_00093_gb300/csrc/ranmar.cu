@@ -5,6 +5,7 @@
 // jump.cuh (Sec. 3.1 / 3.2 jump-ahead).
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "ranmar.h"
@@ -31,6 +32,14 @@ struct ranmar_graph {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
 };
+
+// Scratch of ranmar_batch_pack_static, for callers that cannot allocate:
+// [0] grand total, [256] bucket histogram, [768] bucket cursors, [1280] tile
+// sums for up to RANMAR_PACK_STATIC_MAX streams.  9,472 bytes on every GPU
+// that loads the library, kept until the process exits.
+constexpr size_t kStaticTiles = RANMAR_PACK_STATIC_MAX / ranmar::kScanTile;
+static_assert(RANMAR_PACK_STATIC_MAX % ranmar::kScanTile == 0, "whole tiles");
+static __device__ __align__(256) unsigned char g_pack_static[1280 + kStaticTiles * 8];
 
 namespace {
 
@@ -213,6 +222,29 @@ int batch_generate(ranmar_batch* b, bool f32, ranmar_state_t* states, size_t n_s
     return RANMAR_EINVAL;
   return run_persistent(b, b->cfg, f32, states, n_states, desc, n_desc, order, out, out_len,
                         status, reinterpret_cast<cudaStream_t>(stream), 1);
+}
+
+// Device address of g_pack_static on the current device.  In host code the
+// symbol is only a host-side stand-in, so the address is looked up once per
+// device with cudaGetSymbolAddress (with that device current) and cached.
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned char* g_static_addr[kMaxDevices] = {};
+
+int static_scratch(unsigned char** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev < 0 || dev >= kMaxDevices) return RANMAR_EDEVICE;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_pack_static);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_static_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_static_addr[dev];
+  return RANMAR_OK;
 }
 
 }  // namespace
@@ -514,6 +546,39 @@ int ranmar_graph_destroy(ranmar_graph_t* g) {
   cudaGraphDestroy(g->graph);
   delete g;
   return RANMAR_OK;
+}
+
+int ranmar_batch_pack_static(const uint64_t* d_counts, size_t n, uint32_t flags,
+                             ranmar_desc_t* d_desc, uint32_t* d_order, uint64_t* d_total,
+                             ranmar_stream_t stream) {
+  if (n > RANMAR_PACK_STATIC_MAX) return RANMAR_ERANGE;
+  if (n > 0 && (!d_counts || !d_desc)) return RANMAR_EINVAL;
+  if (!aligned(d_counts, 8) || !aligned(d_desc, 8) || !aligned(d_order, 4) ||
+      !aligned(d_total, 8))
+    return RANMAR_EINVAL;
+  unsigned char* ws = nullptr;
+  const int rc = static_scratch(&ws);
+  if (rc != RANMAR_OK) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint64_t* total = d_total ? d_total : reinterpret_cast<uint64_t*>(ws);
+  if (n == 0) {
+    if (!d_total) return RANMAR_OK;
+    const cudaError_t e = cudaMemsetAsync(d_total, 0, sizeof(uint64_t), s);
+    return e == cudaSuccess ? RANMAR_OK : cuda_fail(e);
+  }
+  uint32_t* hist = reinterpret_cast<uint32_t*>(ws + 256);
+  uint32_t* cursor = reinterpret_cast<uint32_t*>(ws + 768);
+  uint64_t* tile_sums = reinterpret_cast<uint64_t*>(ws + 1280);
+  // The array keeps the previous call's contents: clear histogram + cursors.
+  cudaError_t e = cudaMemsetAsync(hist, 0, 1024, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const unsigned tiles = static_cast<unsigned>((n + ranmar::kScanTile - 1) / ranmar::kScanTile);
+  ranmar::pack_tile_sums<<<tiles, ranmar::kScanThreads, 0, s>>>(d_counts, n, tile_sums, hist);
+  ranmar::pack_scan_tiles<<<1, ranmar::kScanThreads, 0, s>>>(tile_sums, tiles, total, hist,
+                                                               cursor);
+  ranmar::pack_write<<<tiles, ranmar::kScanThreads, 0, s>>>(d_counts, n, tile_sums, flags, d_desc,
+                                                              cursor, d_order);
+  return check_launch();
 }
 
 }  // extern "C"
