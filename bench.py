@@ -394,27 +394,96 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
                           "tmacs_per_s": macs / (ms * 1e-3) / 1e12,
                           "alu_frac": macs / (ms * 1e-3) / 1e12 / alu_peak}
 
-    # batched (one launch) vs one plain launch per stream, uneven lengths
+    # Batched uneven workload at full size: 10^6 streams at k*2^64, lengths
+    # log-uniform in [64, 65536] (seed 7), f32 packed by prefix sum.  One step
+    # = partition jump + device pack + one persistent generate (autotuned),
+    # replayed as a captured CUDA graph.  Comparator: one plain launch per
+    # stream (generation only), timed on a sample of streams.
     bu = BatchedUneven()
-    ns = 4096
-    lens = bu.lengths(ns)
-    offs = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    ns = bu.n_streams
+    lens = bu.lengths()
     total = int(lens.sum())
-    stb = rm.partition(rm.seed(bu.seed).to(dev), bu.J, 0, ns)
+    base = rm.seed(bu.seed).to(dev)
+    counts = torch.as_tensor(lens, device=dev)
+    b = rm.Batch(ns)
+    stb = torch.empty((ns, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+    rm.partition(base, bu.J, 0, ns, out=stb)
+    desc, order, tot_t = b.pack(counts)
     outf = torch.empty(total, dtype=torch.float32, device=dev)
-    desc = rm.make_desc(np.arange(ns), offs, lens, 0, device=dev)
-    ms_b = timed(lambda: rm.generate_f32(stb, desc, outf))
-    rows = [stb[i] for i in range(ns)]
-    views = [outf[int(offs[i]):int(offs[i] + lens[i])] for i in range(ns)]
+    cfg, tune_ms, cached = rm.tune_cached(b, stb, desc, outf, order, total)
+    ms_gen = timed(lambda: b.generate_f32(stb, desc, outf, order=order))
+    ms_jump = timed(lambda: rm.partition(base, bu.J, 0, ns, out=stb))
+    ms_pack = timed(lambda: b.pack(counts))
+    gs = torch.cuda.Stream()
+    gs.wait_stream(stream)
+    desc_g = torch.empty_like(desc)
+    ord_g = torch.empty_like(order)
+    import paper_2512_00093_gb300.binding as bd
+    with rm.capture(gs) as cap:
+        rm.partition(base, bu.J, 0, ns, out=stb, stream=gs)
+        bd._check(bd._lib().ranmar_batch_pack(b._h, counts.data_ptr(), ns, 0, desc_g.data_ptr(),
+                                              ord_g.data_ptr(), None, gs.cuda_stream), "pack")
+        b.generate_f32(stb, desc_g, outf, order=ord_g, stream=gs)
+
+    def graph_step():
+        cap.graph.launch(gs)
+    stream.wait_stream(gs)
+    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    graph_step()
+    gs.synchronize()
+    best_g = float("inf")
+    for _ in range(5):
+        ga.record(gs)
+        graph_step()
+        gb.record(gs)
+        gs.synchronize()
+        best_g = min(best_g, ga.elapsed_time(gb))
+    cap.graph.close()
+    gen_bytes = total * 4 + ns * (400 + 24 + 4)
+    # plain comparator on a sample: generation only, one launch per stream
+    samp = 4096
+    rows = [stb[i] for i in range(samp)]
+    offs = np.concatenate([[0], np.cumsum(lens[:samp])[:-1]])
+    views = [outf[int(offs[i]):int(offs[i] + lens[i])] for i in range(samp)]
 
     def plain():
-        for i in range(ns):
+        for i in range(samp):
             rm.generate_plain_f32(rows[i], int(lens[i]), views[i], write_back=False)
-    ms_p = timed(plain, reps=2)
-    res["batched_vs_plain"] = {"streams": ns, "outputs": total, "batched_ms": ms_b,
-                               "plain_ms": ms_p, "speedup": ms_p / ms_b,
-                               "batched_outputs_per_s": total / (ms_b * 1e-3),
-                               "plain_outputs_per_s": total / (ms_p * 1e-3)}
+    ms_plain = timed(plain, reps=2)
+    ps = torch.cuda.Stream()
+    ps.wait_stream(stream)
+    with rm.capture(ps) as pcap:
+        for i in range(samp):
+            rm.generate_plain_f32(rows[i], int(lens[i]), views[i], write_back=False, stream=ps)
+    stream.wait_stream(ps)
+    pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pcap.graph.launch(ps)
+    ps.synchronize()
+    pa.record(ps)
+    pcap.graph.launch(ps)
+    pb.record(ps)
+    ps.synchronize()
+    ms_plain_graph = pa.elapsed_time(pb)
+    pcap.graph.close()
+    samp_out = int(lens[:samp].sum())
+    res["batched_uneven"] = {
+        "streams": ns, "outputs": total, "dtype": "f32",
+        "config": {"lanes_per_stream": cfg[0], "threads_per_cta": cfg[1], "ctas_per_sm": cfg[2],
+                   "chunk": cfg[3], "tuned_ms": tune_ms, "from_cache": cached},
+        "jump_ms": ms_jump, "pack_ms": ms_pack, "generate_ms": ms_gen,
+        "graph_step_ms": best_g, "step_outputs_per_s": total / (best_g * 1e-3),
+        "generate_outputs_per_s": total / (ms_gen * 1e-3),
+        "generate_hbm_gbs": gen_bytes / (ms_gen * 1e-3) / 1e9,
+        "generate_hbm_frac": gen_bytes / (ms_gen * 1e-3) / 1e9 / hbm_peak,
+        "plain_sample_streams": samp, "plain_sample_outputs": samp_out,
+        "plain_python_ms": ms_plain, "plain_graph_ms": ms_plain_graph,
+        "plain_outputs_per_s": samp_out / (ms_plain_graph * 1e-3),
+        "speedup_vs_plain_graph": (total / (ms_gen * 1e-3)) / (samp_out / (ms_plain_graph * 1e-3)),
+        "speedup_vs_plain_python": (total / (ms_gen * 1e-3)) / (samp_out / (ms_plain * 1e-3)),
+    }
+    del outf, stb, desc, order, desc_g, ord_g
+    b.close()
+    torch.cuda.empty_cache()
 
     # probes: write-only HBM ceiling and IMAD ceiling on this GPU
     try:
