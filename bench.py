@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-extras", action="store_true", help="skip the side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--serve-seconds", type=float, default=5.0,
+                   help="duration of the serving run (the recipe's full run is 60 s)")
     p.add_argument("--streams", type=int, default=65536,
                    help="streams per GPU (65536 is the benchmark; smaller for profiling)")
     return p.parse_args()
@@ -349,6 +351,7 @@ def run_ours(args):
 
     if not args.no_extras:
         result["extras"] = extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak)
+        result["extras"]["serving"] = serving(rm, torch, args.serve_seconds)
         if world == 1:
             ns, el = oracle_sample(args.cpu_seconds, 0, w)
             result["cpu_baseline"] = {
@@ -504,6 +507,45 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
                          "imad_tops": SMS * 8 * 256 * iters * 16 / (ms_i * 1e-3) / 1e12}
     except OSError as e:
         res["probes"] = {"error": str(e)}
+    return res
+
+
+def serving(rm, torch, seconds):
+    """Poisson request stream (20k req/s, seed 11; seed U{1..10^4}, k U{0..2^20},
+    J = 2^48, count log-uniform 10^3..10^7, u24/f32 with p = 1/2) served in real
+    time with continuous batching under a 40 GB state+output budget; outputs
+    consumed by the on-device checksum.  Comparator: every request alone with
+    plain launches, on the first requests of the same stream."""
+    from oracle import oracle
+    from paper_2512_00093_gb300.serve import Engine, make_requests
+    from paper_2512_00093_gb300.workloads import Serving
+    w = Serving()
+    t, seeds, ks, counts, f32 = w.requests(duration=seconds)
+    reqs = make_requests(t, seeds, ks, counts, f32, w.J)
+    eng = Engine(budget_bytes=40 << 30)
+    summ = eng.run(reqs, realtime=True, max_wait=seconds * 10 + 60)
+    o = oracle()
+    rng = np.random.default_rng(12)
+    small = [r for r in reqs if r.count <= 20000]
+    pick = [small[i] for i in rng.choice(len(small), min(24, len(small)), replace=False)]
+    ok = 0
+    for r in pick:
+        y = o.stream(r.seed, r.k * r.J + r.offset, r.count)
+        if r.f32:
+            y = (y.astype(np.float64) / 16777216.0).astype(np.float32).view(np.uint32)
+        ok += int(rm.checksum_np(y) == r.checksum)
+    res = {"offered_req_per_s": w.rate, "seconds": seconds, **summ,
+           "iterations": eng.stats["iterations"], "segments": eng.stats["segments"],
+           "jumps": eng.stats["jumps"], "resumed": eng.stats["resumed"],
+           "evicted": eng.stats["evicted"], "verified": f"{ok}/{len(pick)} sampled requests",
+           "budget_gb": 40}
+    nplain = min(len(reqs), 2000)
+    plain = make_requests(t[:nplain], seeds[:nplain], ks[:nplain], counts[:nplain],
+                          f32[:nplain], w.J)
+    ps = eng.run_plain(plain, realtime=True, max_wait=seconds * 10 + 120)
+    res["plain_per_request"] = {**ps, "note": f"first {nplain} requests, each alone: one jump "
+                                              "launch + one one-warp generation launch"}
+    eng.close()
     return res
 
 

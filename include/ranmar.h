@@ -122,6 +122,23 @@ int ranmar_jump(const ranmar_state_t *d_base, size_t n_base,
                 uint32_t *d_status, ranmar_stream_t stream);
 
 /*
+ * ranmar_jump_scatter -- ranmar_jump with per-stream destinations:
+ * d_dst[d_dst_idx[i]] = f^{E_i}(d_base[d_base_idx[i]]) (d_base_idx NULL =
+ * base 0).  For state pools that are read and written in place (a serving
+ * engine's resident states): d_base and d_dst may be the same array, but in
+ * one call no destination index may equal another destination or any base
+ * index used by the call (those would race; not checked).
+ * Errors: as ranmar_jump (RANMAR_ERANGE also for n_dst = 0).  Device:
+ * RANMAR_ST_BAD_INDEX for d_base_idx[i] >= n_base or d_dst_idx[i] >= n_dst
+ * (that stream is skipped).
+ */
+int ranmar_jump_scatter(const ranmar_state_t *d_base, size_t n_base,
+                        const uint32_t *d_base_idx,
+                        const uint32_t *d_exp, uint32_t exp_words,
+                        ranmar_state_t *d_dst, size_t n_dst, const uint32_t *d_dst_idx,
+                        size_t n, uint32_t *d_status, ranmar_stream_t stream);
+
+/*
  * ranmar_partition -- stream partitioning of Sec. 1: d_out[i] is the start
  * of block k = k0 + i of length J of the sequence that starts at *d_base,
  * i.e. f^{kJ}(base), computed as in ranmar_jump with E = (k0 + i) J formed
@@ -285,6 +302,36 @@ int ranmar_graph_end(ranmar_stream_t stream, ranmar_graph_t **out);
 int ranmar_graph_launch(const ranmar_graph_t *g, ranmar_stream_t stream);
 /* Frees the graph.  NULL is a no-op. */
 int ranmar_graph_destroy(ranmar_graph_t *g);
+
+/* ------------------------------------------------------------------------
+ * Output checksums (serving: outputs are consumed on the device).
+ * ------------------------------------------------------------------------ */
+
+/* One checksum work item: words data[offset .. offset+count), whose first
+ * word has index index0 within its request; added into results[result]. */
+typedef struct ranmar_sum_item {
+    uint64_t offset;
+    uint64_t count;
+    uint64_t index0;
+    uint32_t result;
+    uint32_t pad;
+} ranmar_sum_item_t;   /* 32 bytes */
+
+/*
+ * ranmar_checksum -- for each item: results[item.result] += sum_i
+ * data[offset + i] * (2 (index0 + i) + 1) mod 2^64 (32-bit words: the u24
+ * values or the float32 bit patterns).  Items of one request split at any
+ * boundaries sum to the same total.  The caller zeroes d_results first.
+ * Not part of the paper's method: it lets a server consume outputs on the
+ * device and check them against a reference.
+ * Errors: RANMAR_EINVAL (NULL pointer with n_items > 0, misalignment).
+ * Device: RANMAR_ST_OUT_RANGE for an item outside data_len or n_results
+ * (skipped).
+ */
+int ranmar_checksum(const uint32_t *d_data, size_t data_len,
+                    const ranmar_sum_item_t *d_items, size_t n_items,
+                    uint64_t *d_results, size_t n_results,
+                    uint32_t *d_status, ranmar_stream_t stream);
 
 /* Name of a return code (static string, never NULL). */
 const char *ranmar_strerror(int code);

@@ -74,6 +74,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         getattr(lib, name).argtypes = [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp, _vp]
     lib.ranmar_batch_tune.argtypes = [_vp, ctypes.c_int, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp,
                                       ctypes.POINTER(ctypes.c_float)]
+    lib.ranmar_jump_scatter.argtypes = [_vp, _sz, _vp, _vp, _u32, _vp, _sz, _vp, _sz, _vp, _vp]
+    lib.ranmar_checksum.argtypes = [_vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp]
     lib.ranmar_graph_begin.argtypes = [_vp]
     lib.ranmar_graph_end.argtypes = [_vp, ctypes.POINTER(_vp)]
     lib.ranmar_graph_launch.argtypes = [_vp, _vp]
@@ -84,7 +86,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
                  "ranmar_batch_set_config", "ranmar_batch_get_config", "ranmar_batch_pack",
                  "ranmar_batch_generate_u24", "ranmar_batch_generate_f32", "ranmar_batch_tune",
                  "ranmar_graph_begin", "ranmar_graph_end", "ranmar_graph_launch",
-                 "ranmar_graph_destroy"):
+                 "ranmar_graph_destroy", "ranmar_jump_scatter", "ranmar_checksum"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -175,6 +177,46 @@ def jump(base: torch.Tensor, exps: torch.Tensor, base_idx: torch.Tensor | None =
     _check(_lib().ranmar_jump(_ptr(base), base.shape[0], _ptr(base_idx), _ptr(exps), nw,
                               _ptr(out), n, _ptr(status), _stream(stream)), "ranmar_jump")
     return out
+
+
+def jump_scatter(base: torch.Tensor, exps: torch.Tensor, dst: torch.Tensor,
+                 dst_idx: torch.Tensor, base_idx: torch.Tensor | None = None,
+                 status: torch.Tensor | None = None, stream=None, n: int | None = None) -> None:
+    """ranmar_jump_scatter: dst[dst_idx[i]] = f^{E_i}(base[base_idx[i]]) for i < n."""
+    base = base.reshape(-1, STATE_WORDS)
+    dst = dst.reshape(-1, STATE_WORDS)
+    _need(base, torch.int32, "base")
+    _need(dst, torch.int32, "dst")
+    _need(exps, torch.int32, "exps")
+    _need(dst_idx, torch.int32, "dst_idx")
+    if base_idx is not None:
+        _need(base_idx, torch.int32, "base_idx")
+    nw = exps.shape[1]
+    n = exps.shape[0] if n is None else int(n)
+    _check(_lib().ranmar_jump_scatter(_ptr(base), base.shape[0], _ptr(base_idx), _ptr(exps), nw,
+                                      _ptr(dst), dst.shape[0], _ptr(dst_idx), n, _ptr(status),
+                                      _stream(stream)), "ranmar_jump_scatter")
+
+
+def checksum(data: torch.Tensor, items: torch.Tensor, results: torch.Tensor,
+             status: torch.Tensor | None = None, stream=None, n: int | None = None) -> None:
+    """ranmar_checksum over (n, 4) int64 items [offset, count, index0, result]."""
+    if data.dtype not in (torch.int32, torch.float32):
+        raise TypeError("data must be int32 or float32")
+    _need(items, torch.int64, "items")
+    _need(results, torch.int64, "results")
+    n = items.shape[0] if n is None else int(n)
+    _check(_lib().ranmar_checksum(_ptr(data), data.numel(), _ptr(items), n, _ptr(results),
+                                  results.numel(), _ptr(status), _stream(stream)),
+           "ranmar_checksum")
+
+
+def checksum_np(words_u32: np.ndarray, index0: int = 0) -> int:
+    """The same weighted checksum on the host (for checking results)."""
+    w = np.asarray(words_u32).view(np.uint32).astype(np.uint64)
+    i = np.arange(index0, index0 + w.size, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return int(np.sum(w * (np.uint64(2) * i + np.uint64(1)), dtype=np.uint64))
 
 
 def partition(base: torch.Tensor, J: int, k0: int, n: int, out: torch.Tensor | None = None,

@@ -329,11 +329,13 @@ __device__ __forceinline__ void jump_pair(const ranmar_state_t* __restrict__ bas
 
 // mode 0: E_i from d_exp (exp_words per stream), base d_base[base_idx[i]].
 // mode 1: E_i = (k0 + i) * J, base d_base[0].
+// d_dst_idx (mode 0 only, may be null): stream i is written to
+// d_out[d_dst_idx[i]] (index < n_dst) instead of d_out[i].
 __global__ void __launch_bounds__(32) jump_kernel(
     const ranmar_state_t* __restrict__ d_base, uint64_t n_base,
     const uint32_t* __restrict__ d_base_idx, const uint32_t* __restrict__ d_exp,
     uint32_t exp_words, ExpParams part, int mode, ranmar_state_t* __restrict__ d_out,
-    uint64_t n, uint32_t* status) {
+    uint64_t n, uint32_t* status, const uint32_t* __restrict__ d_dst_idx, uint64_t n_dst) {
   extern __shared__ __align__(16) uint32_t smem[];
   const unsigned lane = threadIdx.x & 31;
   const unsigned g = lane & 1;
@@ -366,7 +368,15 @@ __global__ void __launch_bounds__(32) jump_kernel(
       exp_mul_add(E, part.J, static_cast<uint32_t>(k >> 32), 1);
     }
   }
-  jump_pair(base, E, active, d_out + (active ? i : 0), a, R, g);
+  uint64_t di = i;
+  if (active && d_dst_idx) {
+    di = d_dst_idx[i];
+    if (di >= n_dst) {
+      if (g == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
+      active = false;
+    }
+  }
+  jump_pair(base, E, active, d_out + (active ? di : 0), a, R, g);
 }
 
 }  // namespace ranmar

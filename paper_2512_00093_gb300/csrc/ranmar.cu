@@ -86,6 +86,28 @@ struct SeedBits {
   }
 };
 
+// Weighted checksum of 32-bit words: result[item.result] +=
+// sum_i word[offset + i] * (2 (index0 + i) + 1) mod 2^64, one CTA per item.
+__global__ void __launch_bounds__(256) checksum_kernel(const uint32_t* __restrict__ data,
+                                                      const ranmar_sum_item_t* __restrict__ items,
+                                                      uint64_t n_items, uint64_t data_len,
+                                                      unsigned long long* __restrict__ results,
+                                                      uint64_t n_results, uint32_t* status) {
+  for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const ranmar_sum_item_t w = items[it];
+    if (w.result >= n_results || w.count > data_len || w.offset > data_len - w.count) {
+      if (threadIdx.x == 0) ranmar::flag_status(status, RANMAR_ST_OUT_RANGE);
+      continue;
+    }
+    unsigned long long acc = 0;
+    for (uint64_t i = threadIdx.x; i < w.count; i += blockDim.x)
+      acc += static_cast<unsigned long long>(data[w.offset + i]) * (2ull * (w.index0 + i) + 1ull);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(ranmar::kFull, acc, d);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&results[w.result], acc);
+  }
+}
+
 int launch_generate(bool f32, ranmar_state_t* states, size_t n_states, const ranmar_desc_t* desc,
                     size_t n_desc, void* out, size_t out_len, uint32_t* status,
                     ranmar_stream_t stream) {
@@ -124,13 +146,13 @@ int launch_plain(bool f32, ranmar_state_t* st, uint64_t count, void* out, int wr
 int launch_jump(const ranmar_state_t* base, size_t n_base, const uint32_t* base_idx,
                 const uint32_t* exp, uint32_t exp_words, const ranmar::ExpParams& part,
                 int mode, ranmar_state_t* out, size_t n, uint32_t* status,
-                ranmar_stream_t stream) {
+                ranmar_stream_t stream, const uint32_t* dst_idx = nullptr, size_t n_dst = 0) {
   const uint64_t per_cta = ranmar::kJumpStreamsPerWarp;   // one warp per CTA
   const uint64_t blocks = (n + per_cta - 1) / per_cta;
   if (blocks > 0x7FFFFFFFull) return RANMAR_ERANGE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   ranmar::jump_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kJumpSmemBytes, s>>>(
-      base, n_base, base_idx, exp, exp_words, part, mode, out, n, status);
+      base, n_base, base_idx, exp, exp_words, part, mode, out, n, status, dst_idx, n_dst);
   return check_launch();
 }
 
@@ -578,6 +600,36 @@ int ranmar_batch_pack_static(const uint64_t* d_counts, size_t n, uint32_t flags,
                                                                cursor);
   ranmar::pack_write<<<tiles, ranmar::kScanThreads, 0, s>>>(d_counts, n, tile_sums, flags, d_desc,
                                                               cursor, d_order);
+  return check_launch();
+}
+
+int ranmar_jump_scatter(const ranmar_state_t* d_base, size_t n_base, const uint32_t* d_base_idx,
+                        const uint32_t* d_exp, uint32_t exp_words, ranmar_state_t* d_dst,
+                        size_t n_dst, const uint32_t* d_dst_idx, size_t n, uint32_t* d_status,
+                        ranmar_stream_t stream) {
+  if (n == 0) return RANMAR_OK;
+  if (!d_base || !d_exp || !d_dst || !d_dst_idx) return RANMAR_EINVAL;
+  if (exp_words < 1 || exp_words > RANMAR_MAX_EXP_WORDS || n_base == 0 || n_dst == 0)
+    return RANMAR_ERANGE;
+  if (!aligned(d_base, 16) || !aligned(d_dst, 16) || !aligned(d_exp, 4) ||
+      !aligned(d_dst_idx, 4) || !aligned(d_base_idx, 4))
+    return RANMAR_EINVAL;
+  ranmar::ExpParams part{};
+  return launch_jump(d_base, n_base, d_base_idx, d_exp, exp_words, part, 0, d_dst, n, d_status,
+                     stream, d_dst_idx, n_dst);
+}
+
+int ranmar_checksum(const uint32_t* d_data, size_t data_len, const ranmar_sum_item_t* d_items,
+                    size_t n_items, uint64_t* d_results, size_t n_results, uint32_t* d_status,
+                    ranmar_stream_t stream) {
+  if (n_items == 0) return RANMAR_OK;
+  if (!d_data || !d_items || !d_results) return RANMAR_EINVAL;
+  if (!aligned(d_data, 4) || !aligned(d_items, 8) || !aligned(d_results, 8)) return RANMAR_EINVAL;
+  const uint64_t grid = n_items < (1u << 20) ? n_items : (1u << 20);
+  checksum_kernel<<<static_cast<unsigned>(grid), 256, 0,
+                    reinterpret_cast<cudaStream_t>(stream)>>>(
+      d_data, d_items, n_items, data_len, reinterpret_cast<unsigned long long*>(d_results),
+      n_results, d_status);
   return check_launch();
 }
 

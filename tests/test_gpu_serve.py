@@ -1,0 +1,95 @@
+"""GPU serving tests: every request's outputs (through the device checksum)
+equal the oracle's, and each result is the same alone and in the mix.
+Tolerance 0."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+J48 = 1 << 48
+
+
+@pytest.fixture(scope="module")
+def rm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_00093_gb300 as rm
+    return rm
+
+
+def mixed_requests(n, seed, seeds=5, ks=6, cmax=120_000, duration=0.2):
+    """A Poisson-like request list with few distinct streams, so that many
+    requests resume a stream that earlier requests consumed."""
+    from paper_2512_00093_gb300.serve import make_requests
+    rng = np.random.default_rng(seed)
+    t = np.sort(rng.random(n) * duration)
+    sd = rng.integers(1, seeds + 1, n)
+    k = rng.integers(0, ks, n)
+    c = np.floor(10.0 ** (1 + np.log10(cmax / 10) * rng.random(n))).astype(np.int64)
+    c[:8] = [1, 31, 32, 33, 4095, 4096, 4097, 8192 + 5]
+    f32 = rng.random(n) < 0.5
+    return make_requests(t, sd, k, c, f32, J48)
+
+
+def expected_checksum(orc, rm, r):
+    y = orc.stream(r.seed, r.k * r.J + r.offset, r.count)
+    if r.f32:
+        y = (y.astype(np.float64) / 16777216.0).astype(np.float32).view(np.uint32)
+    return rm.checksum_np(y)
+
+
+def check_all(orc, rm, reqs):
+    bad = [r.rid for r in reqs if r.checksum != expected_checksum(orc, rm, r)]
+    assert not bad, f"checksum mismatch for requests {bad[:10]}"
+
+
+def test_checksum_kernel_matches_host(rm):
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(1)
+    data = torch.as_tensor(rng.integers(0, 1 << 24, 100_000).astype(np.int32), device=dev)
+    items = torch.tensor([[0, 40_000, 0, 0], [40_000, 60_000, 40_000, 0], [5, 7, 3, 1]],
+                         dtype=torch.int64, device=dev)
+    res = torch.zeros(2, dtype=torch.int64, device=dev)
+    rm.checksum(data, items, res)
+    torch.cuda.synchronize()
+    h = data.cpu().numpy()
+    got = res.cpu().numpy().astype(np.uint64)
+    assert int(got[0]) == rm.checksum_np(h)                 # split items sum to the whole
+    assert int(got[1]) == rm.checksum_np(h[5:12], index0=3)
+
+
+def test_serving_mix_matches_oracle_and_alone(rm, orc):
+    from paper_2512_00093_gb300.serve import Engine, Request
+    reqs = mixed_requests(260, 7)
+    # small segments, few segments per iteration and a tiny state pool: many
+    # iterations, multi-segment requests, pool jumps, resumes and evictions
+    eng = Engine(budget_bytes=64 << 20, seg=4096, state_entries=96,
+                 max_segments_per_iter=48, max_inflight=3)
+    summary = eng.run(reqs, realtime=False)
+    assert summary["requests"] == len(reqs)
+    assert eng.stats["resumed"] > 0 and eng.stats["evicted"] > 0
+    check_all(orc, rm, reqs)
+    eng.close()
+    # each of a sample, alone in a fresh engine, with its offset as admitted
+    for r in [reqs[i] for i in (0, 3, 7, 40, 100, 200, 259)]:
+        solo = Request(0, 0.0, r.seed, r.k, r.J, r.count, r.f32, offset=r.offset)
+        e2 = Engine(budget_bytes=64 << 20, seg=4096, state_entries=96)
+        e2.run([solo], realtime=False)
+        e2.close()
+        assert solo.checksum == r.checksum, r.rid
+
+
+def test_serving_realtime_and_plain(rm, orc):
+    from paper_2512_00093_gb300.serve import Engine
+    reqs = mixed_requests(150, 9, seeds=40, ks=1000, duration=0.15)
+    eng = Engine(budget_bytes=256 << 20, seg=1 << 14, state_entries=4096)
+    s = eng.run(reqs, realtime=True)
+    assert s["p50_ms"] is not None and s["p99_ms"] >= s["p50_ms"]
+    check_all(orc, rm, reqs)
+    got = [r.checksum for r in reqs]
+    for r in reqs:
+        r.checksum, r.done = -1, -1.0
+    eng.run_plain(reqs, realtime=True)
+    assert [r.checksum for r in reqs] == got
+    eng.close()

@@ -1,0 +1,54 @@
+"""Host-side logic of the serving engine (no GPU): resume offsets, exponent
+rows, the output allocator, and the request recipe."""
+import numpy as np
+
+from paper_2512_00093_gb300.serve import FirstFit, Request, assign_offsets, exp_rows
+from paper_2512_00093_gb300.workloads import Serving
+
+
+def test_offsets_follow_arrival_order():
+    reqs = [Request(i, 0.1 * i, s, k, 1 << 48, c, False)
+            for i, (s, k, c) in enumerate([(1, 0, 10), (1, 1, 5), (1, 0, 7), (2, 0, 3),
+                                           (1, 0, 1), (1, 1, 2)])]
+    assign_offsets(reqs)
+    assert [r.offset for r in reqs] == [0, 0, 10, 0, 17, 5]
+
+
+def test_exp_rows_multiword_and_carry():
+    seg = 1 << 16
+    for base in [0, 1, (1 << 64) - 5, (1 << 96) - 1, ((1 << 20) - 1) * (1 << 48) + 10**7,
+                 (1 << 159) + 3]:
+        rows = exp_rows(base, 9, seg)
+        for q in range(9):
+            e = base + q * seg
+            assert [int(x) for x in rows[q]] == [(e >> (32 * w)) & 0xFFFFFFFF for w in range(5)]
+
+
+def test_firstfit_alignment_reuse_and_coalescing():
+    rng = np.random.default_rng(0)
+    f = FirstFit(1 << 20, align=32)
+    live = []
+    for step in range(2000):
+        if live and rng.random() < 0.45:
+            f.free(*live.pop(int(rng.integers(len(live)))))
+        else:
+            r = f.alloc(int(rng.integers(1, 5000)))
+            if r is not None:
+                assert r[0] % 32 == 0 and r[1] % 32 == 0
+                for a, n in live:
+                    assert r[0] + r[1] <= a or a + n <= r[0], "overlap"
+                live.append(r)
+    for r in live:
+        f.free(*r)
+    assert f.starts == [0] and f.lens == [1 << 20] and f.used == 0
+
+
+def test_serving_recipe():
+    t, seeds, ks, counts, f32 = Serving().requests(duration=2.0)
+    assert abs(len(t) / 2.0 / 20000 - 1) < 0.02
+    assert np.all(np.diff(t) >= 0) and t.min() >= 0 and t.max() <= 2.0
+    assert seeds.min() >= 1 and seeds.max() <= 10**4 and ks.max() <= 1 << 20
+    assert counts.min() >= 1000 and counts.max() <= 10**7
+    # log-uniform 10^3..10^7: mean (10^7 - 10^3) / (4 ln 10) ~ 1.09e6
+    assert abs(counts.mean() / 1.085e6 - 1) < 0.1
+    assert abs(f32.mean() - 0.5) < 0.02
