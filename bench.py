@@ -79,7 +79,22 @@ def dense_squarings(e: int) -> int:
 
 
 def jump_macs(exps) -> int:
+    """Multiply-adds of left-to-right square-and-multiply + application."""
     return sum(dense_squarings(int(e)) * SQ_MACS + APPLY_MACS for e in exps)
+
+
+def table_macs(exps) -> int:
+    """Multiply-adds of the fixed-base table jump: one full 97x97 product per
+    nonzero base-256 digit after the first, + the application."""
+    tot = 0
+    for e in exps:
+        e = int(e)
+        nz = 0
+        while e:
+            nz += (e & 0xFF) != 0
+            e >>= 8
+        tot += max(0, nz - 1) * APPLY_MACS + APPLY_MACS
+    return tot
 
 
 def source_sha(*names) -> str:
@@ -221,9 +236,14 @@ def run_ours(args):
     out = torch.empty(n * count, dtype=torch.int32, device=dev)
     desc = rm.make_desc(np.arange(n), np.arange(n) * count, count, rm.DESC_WRITE_BACK, device=dev)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    # fixed-base power table (built once per device; depends only on phi)
+    torch.cuda.synchronize()
+    tb0 = time.perf_counter()
+    table = rm.Table()
+    table_build_ms = (time.perf_counter() - tb0) * 1e3
 
     def step():
-        rm.partition(base, w.J, k0, n, out=states)
+        table.partition(base, w.J, k0, n, out=states)
         rm.generate_u24(states, desc, out)
 
     for _ in range(args.warmup):
@@ -240,7 +260,7 @@ def run_ours(args):
     for s in range(K):
         flush.fill_(s & 0xFF)          # L2 flush outside the timed events
         ev[s][0].record(stream)
-        rm.partition(base, w.J, k0, n, out=states)
+        table.partition(base, w.J, k0, n, out=states)
         ev[s][1].record(stream)
         rm.generate_u24(states, desc, out)
         ev[s][2].record(stream)
@@ -264,7 +284,7 @@ def run_ours(args):
     e2e_steps = max(3, min(K, 10))
     for _ in range(2):
         d_base.copy_(h_base, non_blocking=True)
-        rm.partition(d_base, w.J, k0, n, out=states)
+        table.partition(d_base, w.J, k0, n, out=states)
         rm.generate_u24(states, desc, out)
         h_out.copy_(out, non_blocking=True)
     torch.cuda.synchronize()
@@ -274,7 +294,7 @@ def run_ours(args):
     e0.record(stream)
     for _ in range(e2e_steps):
         d_base.copy_(h_base, non_blocking=True)
-        rm.partition(d_base, w.J, k0, n, out=states)
+        table.partition(d_base, w.J, k0, n, out=states)
         rm.generate_u24(states, desc, out)
         h_out.copy_(out, non_blocking=True)
     e1.record(stream)
@@ -285,6 +305,20 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_e2e = float(t.item())
     ok_e2e = bool(np.array_equal(h_out[:count].numpy(), out[:count].cpu().numpy()))
+    # the paper's left-to-right square-and-multiply on the same streams
+    sm_states = torch.empty_like(states)
+    rm.partition(base, w.J, k0, n, out=sm_states)
+    torch.cuda.synchronize()
+    same_states = bool(torch.equal(sm_states, table.partition(base, w.J, k0, n)))
+    sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sm_ms = float("inf")
+    for _ in range(3):
+        sa.record(stream)
+        rm.partition(base, w.J, k0, n, out=sm_states)
+        sb.record(stream)
+        torch.cuda.synchronize()
+        sm_ms = min(sm_ms, sa.elapsed_time(sb))
+    del sm_states
 
     if rank != 0:
         if dist:
@@ -306,10 +340,11 @@ def run_ours(args):
     jump_ms = statistics.mean(t_jump)
     gen_ms = statistics.mean(t_gen)
     gen_bytes = n * count * 4 + n * (400 + 400 + 24)
-    jmacs = jump_macs(exps)
-    jump_sha = source_sha("jump.cuh", "ranmar_device.cuh")
+    jmacs = table_macs(exps)
+    smacs = jump_macs(exps)
+    jump_sha = source_sha("jump.cuh", "jump_table.cuh", "ranmar_device.cuh")
     gen_sha = source_sha("generate.cuh", "ranmar_device.cuh")
-    tj = traffic_for("jump_kernel", jump_sha)
+    tj = traffic_for("jump_table_kernel", jump_sha)
     tg = traffic_for("generate_desc_kernel", gen_sha)
     roof_gen = {"kernel": "generate_desc_kernel<u24>", "bound": "hbm",
                 "achieved": gen_bytes / (gen_ms * 1e-3) / 1e9, "peak": hbm_peak,
@@ -318,7 +353,7 @@ def run_ours(args):
                 "algorithmic_bytes": gen_bytes,
                 "traffic": tg["bytes_per_launch"] if tg else None,
                 "avg_launch_ms": gen_ms}
-    roof_jump = {"kernel": "jump_kernel (partition)", "bound": "alu",
+    roof_jump = {"kernel": "jump_table_kernel (partition, fixed-base table)", "bound": "alu",
                  "achieved": jmacs / (jump_ms * 1e-3) / 1e12, "peak": alu_peak,
                  "unit": "Tmul-add/s", "frac": jmacs / (jump_ms * 1e-3) / 1e12 / alu_peak,
                  "peak_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {sm_max:.0f} MHz",
@@ -340,6 +375,13 @@ def run_ours(args):
         "roofline": dominant, "roofline_generate": roof_gen, "roofline_jump": roof_jump,
         "jump_ms": jump_ms, "generate_ms": gen_ms,
         "jumps_per_s": n / (jump_ms * 1e-3),
+        "jump_method": "fixed-base table (8-bit windows, shared by all streams)",
+        "table_build_ms": table_build_ms,
+        "jump_square_multiply": {
+            "ms": sm_ms, "jumps_per_s": n / (sm_ms * 1e-3),
+            "alu_frac": smacs / (sm_ms * 1e-3) / 1e12 / alu_peak,
+            "states_identical_to_table_jump": same_states,
+            "note": "the paper's left-to-right square-and-multiply, per stream"},
         "generate_outputs_per_s": n * count / (gen_ms * 1e-3),
         "clocks": clk,
         "e2e": {"value": world * n * count / (ms_e2e * 1e-3), "unit": UNIT,
@@ -386,16 +428,23 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
             best = min(best, a.elapsed_time(b))
         return best
 
-    # large jumps
+    # large jumps (J = 2^120 + 12345, E = k J up to 2^134): both methods
     lj = LargeJumps()
+    table = rm.Table()
     base = rm.seed(lj.seed).to(dev)
     st = torch.empty((lj.n_streams, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+    exps_l = [k * lj.J for k in range(lj.n_streams)]
     ms = timed(lambda: rm.partition(base, lj.J, 0, lj.n_streams, out=st))
-    macs = jump_macs([k * lj.J for k in range(lj.n_streams)])
-    res["large_jumps"] = {"streams": lj.n_streams, "J": "2^120+12345", "ms": ms,
-                          "jumps_per_s": lj.n_streams / (ms * 1e-3),
-                          "tmacs_per_s": macs / (ms * 1e-3) / 1e12,
-                          "alu_frac": macs / (ms * 1e-3) / 1e12 / alu_peak}
+    macs = jump_macs(exps_l)
+    ms_t = timed(lambda: table.partition(base, lj.J, 0, lj.n_streams, out=st))
+    macs_t = table_macs(exps_l)
+    res["large_jumps"] = {"streams": lj.n_streams, "J": "2^120+12345",
+                          "square_multiply": {"ms": ms, "jumps_per_s": lj.n_streams / (ms * 1e-3),
+                                              "tmacs_per_s": macs / (ms * 1e-3) / 1e12,
+                                              "alu_frac": macs / (ms * 1e-3) / 1e12 / alu_peak},
+                          "table": {"ms": ms_t, "jumps_per_s": lj.n_streams / (ms_t * 1e-3),
+                                    "tmacs_per_s": macs_t / (ms_t * 1e-3) / 1e12,
+                                    "alu_frac": macs_t / (ms_t * 1e-3) / 1e12 / alu_peak}}
 
     # Batched uneven workload at full size: 10^6 streams at k*2^64, lengths
     # log-uniform in [64, 65536] (seed 7), f32 packed by prefix sum.  One step
@@ -410,12 +459,12 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
     counts = torch.as_tensor(lens, device=dev)
     b = rm.Batch(ns)
     stb = torch.empty((ns, rm.STATE_WORDS), dtype=torch.int32, device=dev)
-    rm.partition(base, bu.J, 0, ns, out=stb)
+    table.partition(base, bu.J, 0, ns, out=stb)
     desc, order, tot_t = b.pack(counts)
     outf = torch.empty(total, dtype=torch.float32, device=dev)
     cfg, tune_ms, cached = rm.tune_cached(b, stb, desc, outf, order, total)
     ms_gen = timed(lambda: b.generate_f32(stb, desc, outf, order=order))
-    ms_jump = timed(lambda: rm.partition(base, bu.J, 0, ns, out=stb))
+    ms_jump = timed(lambda: table.partition(base, bu.J, 0, ns, out=stb))
     ms_pack = timed(lambda: b.pack(counts))
     gs = torch.cuda.Stream()
     gs.wait_stream(stream)
@@ -423,7 +472,7 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
     ord_g = torch.empty_like(order)
     import paper_2512_00093_gb300.binding as bd
     with rm.capture(gs) as cap:
-        rm.partition(base, bu.J, 0, ns, out=stb, stream=gs)
+        table.partition(base, bu.J, 0, ns, out=stb, stream=gs)
         bd._check(bd._lib().ranmar_batch_pack(b._h, counts.data_ptr(), ns, 0, desc_g.data_ptr(),
                                               ord_g.data_ptr(), None, gs.cuda_stream), "pack")
         b.generate_f32(stb, desc_g, outf, order=ord_g, stream=gs)

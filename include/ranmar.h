@@ -186,6 +186,45 @@ int ranmar_generate_plain_f32(ranmar_state_t *d_state, uint64_t count,
                               ranmar_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Fixed-base table jump: the same states as ranmar_jump / ranmar_partition.
+ * (Sec. 3.1: t^E mod phi, here as the product of precomputed powers.)
+ * ------------------------------------------------------------------------ */
+
+/* Opaque handle: T[j][d] = t^{d 2^{8j}} mod phi (j < 20, d < 256) on one
+ * device, 5,120 rows of 100 words (2,048,000 bytes).  The table depends only
+ * on phi = t^97 + t^64 - 1, not on seeds or jump sizes. */
+typedef struct ranmar_table ranmar_table_t;
+
+/* Allocates (cudaMalloc) and builds the table on the current device by
+ * left-to-right square-and-multiply of each row's exponent; synchronous
+ * (a few ms).  Errors: RANMAR_EINVAL, RANMAR_ENOMEM, RANMAR_ECUDA. */
+int ranmar_table_create(ranmar_table_t **out);
+/* Frees the table (synchronizes its device).  NULL is a no-op. */
+int ranmar_table_destroy(ranmar_table_t *t);
+/* Device address of the rows (row j*256 + d, 100 words each), for checks. */
+int ranmar_table_rows(const ranmar_table_t *t, const uint32_t **d_rows);
+
+/*
+ * ranmar_jump_tab -- d_dst[d_dst_idx ? d_dst_idx[i] : i] = f^{E_i}(base_i)
+ * exactly as ranmar_jump / ranmar_jump_scatter, with t^{E_i} mod phi formed
+ * as the product of the table rows of E_i's nonzero base-256 digits (one
+ * general polynomial product per digit after the first) instead of
+ * bitlen(E_i) squarings.  Without d_dst_idx the destinations are d_dst[0..n)
+ * (n_dst >= n, no overlap with d_base); with it the scatter rules of
+ * ranmar_jump_scatter apply.  Errors: as ranmar_jump / ranmar_jump_scatter,
+ * plus RANMAR_EINVAL for a NULL table or a table of another device.
+ */
+int ranmar_jump_tab(const ranmar_table_t *t, const ranmar_state_t *d_base, size_t n_base,
+                    const uint32_t *d_base_idx, const uint32_t *d_exp, uint32_t exp_words,
+                    ranmar_state_t *d_dst, size_t n_dst, const uint32_t *d_dst_idx,
+                    size_t n, uint32_t *d_status, ranmar_stream_t stream);
+
+/* ranmar_partition_tab -- ranmar_partition with the table jump. */
+int ranmar_partition_tab(const ranmar_table_t *t, const ranmar_state_t *d_base,
+                         const uint32_t *h_J, uint32_t J_words, uint64_t k0,
+                         ranmar_state_t *d_out, size_t n, ranmar_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Persistent batch path: many streams of uneven lengths in one launch.
  * (Sec. 1 partitioning applied to a batch; Algorithm 2 per stream.)
  * ------------------------------------------------------------------------ */

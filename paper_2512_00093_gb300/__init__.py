@@ -9,5 +9,5 @@ from .binding import (  # noqa: F401
     BatchConfig, Graph, RanmarError, abi_version, capture, checksum, checksum_np, exps_tensor,
     generate_f32, jump_scatter,
     generate_plain_f32, generate_plain_u24, generate_u24, jump, lib_path, make_desc,
-    partition, seed, shape_bucket, state_words_np, tune_cached, words,
+    partition, seed, shape_bucket, state_words_np, Table, tune_cached, words,
 )

@@ -76,6 +76,11 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
                                       ctypes.POINTER(ctypes.c_float)]
     lib.ranmar_jump_scatter.argtypes = [_vp, _sz, _vp, _vp, _u32, _vp, _sz, _vp, _sz, _vp, _vp]
     lib.ranmar_checksum.argtypes = [_vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp]
+    lib.ranmar_table_create.argtypes = [ctypes.POINTER(_vp)]
+    lib.ranmar_table_destroy.argtypes = [_vp]
+    lib.ranmar_table_rows.argtypes = [_vp, ctypes.POINTER(_vp)]
+    lib.ranmar_jump_tab.argtypes = [_vp, _vp, _sz, _vp, _vp, _u32, _vp, _sz, _vp, _sz, _vp, _vp]
+    lib.ranmar_partition_tab.argtypes = [_vp, _vp, _vp, _u32, _u64, _vp, _sz, _vp]
     lib.ranmar_graph_begin.argtypes = [_vp]
     lib.ranmar_graph_end.argtypes = [_vp, ctypes.POINTER(_vp)]
     lib.ranmar_graph_launch.argtypes = [_vp, _vp]
@@ -86,7 +91,9 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
                  "ranmar_batch_set_config", "ranmar_batch_get_config", "ranmar_batch_pack",
                  "ranmar_batch_generate_u24", "ranmar_batch_generate_f32", "ranmar_batch_tune",
                  "ranmar_graph_begin", "ranmar_graph_end", "ranmar_graph_launch",
-                 "ranmar_graph_destroy", "ranmar_jump_scatter", "ranmar_checksum"):
+                 "ranmar_graph_destroy", "ranmar_jump_scatter", "ranmar_checksum",
+                 "ranmar_table_create", "ranmar_table_destroy", "ranmar_table_rows",
+                 "ranmar_jump_tab", "ranmar_partition_tab"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -466,3 +473,77 @@ class capture:
             _check(rc, "ranmar_graph_end")
             self.graph = Graph(h)
         return False
+
+
+# ---------------------------------------------------------------------------
+# fixed-base table jump
+# ---------------------------------------------------------------------------
+class Table:
+    """ranmar_table_t: T[j][d] = t^{d 2^{8j}} mod phi on the current device."""
+
+    ROWS, ROW_WORDS = 20 * 256, 100
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(_lib().ranmar_table_create(ctypes.byref(h)), "ranmar_table_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().ranmar_table_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def jump(self, base: torch.Tensor, exps: torch.Tensor, base_idx=None, out=None,
+             dst_idx=None, status=None, stream=None, n: int | None = None) -> torch.Tensor:
+        """ranmar_jump_tab: out[dst_idx[i] or i] = f^{E_i}(base[base_idx[i]])."""
+        base = base.reshape(-1, STATE_WORDS)
+        _need(base, torch.int32, "base")
+        _need(exps, torch.int32, "exps")
+        nw = exps.shape[1]
+        n = exps.shape[0] if n is None else int(n)
+        if out is None:
+            out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=base.device)
+        out2 = out.reshape(-1, STATE_WORDS)
+        _need(out2, torch.int32, "out")
+        for t, nm in ((base_idx, "base_idx"), (dst_idx, "dst_idx")):
+            if t is not None:
+                _need(t, torch.int32, nm)
+        _check(_lib().ranmar_jump_tab(self._h, _ptr(base), base.shape[0], _ptr(base_idx),
+                                      _ptr(exps), nw, _ptr(out2), out2.shape[0], _ptr(dst_idx),
+                                      n, _ptr(status), _stream(stream)), "ranmar_jump_tab")
+        return out
+
+    def partition(self, base: torch.Tensor, J: int, k0: int, n: int, out=None,
+                  stream=None) -> torch.Tensor:
+        """ranmar_partition_tab: out[i] = f^{(k0+i) J}(base)."""
+        base = base.reshape(-1, STATE_WORDS)
+        _need(base, torch.int32, "base")
+        if out is None:
+            out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=base.device)
+        _need(out, torch.int32, "out")
+        jw = np.array(words(int(J)), dtype=np.uint32)
+        _check(_lib().ranmar_partition_tab(self._h, _ptr(base), jw.ctypes.data, len(jw),
+                                           int(k0), _ptr(out), int(n), _stream(stream)),
+               "ranmar_partition_tab")
+        return out
+
+    def rows_tensor(self) -> torch.Tensor:
+        """The table rows as a (5120, 100) int32 CUDA tensor view (no copy)."""
+        p = ctypes.c_void_p()
+        _check(_lib().ranmar_table_rows(self._h, ctypes.byref(p)), "ranmar_table_rows")
+        return _wrap_device_ptr(p.value, self.ROWS * self.ROW_WORDS).view(self.ROWS,
+                                                                           self.ROW_WORDS)
+
+
+def _wrap_device_ptr(ptr: int, n_int32: int) -> torch.Tensor:
+    """A torch view of library-owned device memory (int32 elements)."""
+    class _Holder:
+        __cuda_array_interface__ = {"shape": (n_int32,), "typestr": "<i4",
+                                    "data": (ptr, False), "version": 2}
+    return torch.as_tensor(_Holder(), device="cuda")

@@ -108,12 +108,18 @@ __device__ __forceinline__ void reduce_block(uint32_t* __restrict__ a,
   }
 }
 
-// a = a^2 t^shift mod phi, in place (lanes g = 0, 1 of the pair cooperate).
-__device__ __forceinline__ void square_reduce_pair(uint32_t* __restrict__ a,
-                                                   uint32_t* __restrict__ R, uint32_t shift,
-                                                   unsigned g) {
+// In place, with the lanes g = 0, 1 of the pair cooperating:
+//   kSquare:  a = a^2 t^shift mod phi          (b unused)
+//   !kSquare: a = a b mod phi (shift must be 0; b is not modified)
+// `mask` holds the lanes taking part (both lanes of every participating pair).
+template <bool kSquare>
+__device__ __forceinline__ void product_reduce_pair(uint32_t* __restrict__ a,
+                                                    const uint32_t* __restrict__ b,
+                                                    uint32_t* __restrict__ R, uint32_t shift,
+                                                    unsigned g, unsigned mask) {
   uint32_t pend[4] = {0u, 0u, 0u, 0u};  // low half of the previous anti-diagonal
   const uint32_t* arow = a + 4 * g;
+  const uint32_t* bcol = kSquare ? a : b;
   const uint32_t keep0 = g ? 0u : ~0u;
 #pragma unroll 1
   for (int s = 24; s >= 0; --s) {
@@ -121,56 +127,63 @@ __device__ __forceinline__ void square_reduce_pair(uint32_t* __restrict__ a,
 #pragma unroll
     for (int r = 0; r < 11; ++r) acc[r] = 0;
     const int ilo = s > 12 ? s - 12 : 0;
-    const int ihi = s >> 1;
-    const bool even = (s & 1) == 0;
-    const int iend = even ? ihi : ihi + 1;  // off-diagonal tiles: I in [ilo, iend)
+    // squaring: off-diagonal tiles I < J, i.e. I in [ilo, iend); general: all I
+    const int iend = kSquare ? ((s & 1) ? (s >> 1) + 1 : (s >> 1)) : (s < 12 ? s : 12) + 1;
     if (ilo < iend) {
       Quad r0 = lds4(arow + 8 * ilo), r1;
-      Oct c0 = lds8(a + 8 * (s - ilo)), c1;
+      Oct c0 = lds8(bcol + 8 * (s - ilo)), c1;
       int I = ilo;
 #pragma unroll 1
       for (; I + 1 < iend; I += 2) {  // operands one tile ahead, ping-pong
         r1 = lds4(arow + 8 * (I + 1));
-        c1 = lds8(a + 8 * (s - I - 1));
+        c1 = lds8(bcol + 8 * (s - I - 1));
         tile_mac(acc, r0, c0);
         if (I + 2 < iend) {
           r0 = lds4(arow + 8 * (I + 2));
-          c0 = lds8(a + 8 * (s - I - 2));
+          c0 = lds8(bcol + 8 * (s - I - 2));
         }
         tile_mac(acc, r1, c1);
       }
       if (I < iend) tile_mac(acc, r0, c0);
+      if (kSquare) {
 #pragma unroll
-      for (int k = 0; k < 11; ++k) acc[k] += acc[k];
+        for (int k = 0; k < 11; ++k) acc[k] += acc[k];
+      }
     }
-    if (even) tile_mac(acc, lds4(arow + 8 * ihi), lds8(a + 8 * ihi));
+    if (kSquare && (s & 1) == 0) tile_mac(acc, lds4(arow + 4 * s), lds8(a + 4 * s));
 
     // Lane 0 holds outputs 0..10 of this anti-diagonal, lane 1 outputs 4..14.
     // Block s+1 = outputs 8..14 here + the low half of anti-diagonal s+1.
     uint32_t out[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const uint32_t recv = __shfl_xor_sync(kFull, acc[4 + k], 1);
+      const uint32_t recv = __shfl_xor_sync(mask, acc[4 + k], 1);
       out[k] = (k < 3 ? acc[8 + k] : 0u) + pend[k] + (recv & keep0);
       pend[k] = acc[k] + (recv & ~keep0);
     }
-    const int b = s + 1;
-    if (b <= 24) {
-      if (b >= 12)
-        *reinterpret_cast<uint4*>(R + 8 * b - 96 + 4 * g) = make_uint4(out[0], out[1], out[2], out[3]);
-      if (b <= 12) reduce_block(a, R, b, g, out, shift);
+    const int bb = s + 1;
+    if (bb <= 24) {
+      if (bb >= 12)
+        *reinterpret_cast<uint4*>(R + 8 * bb - 96 + 4 * g) = make_uint4(out[0], out[1], out[2], out[3]);
+      if (bb <= 12) reduce_block(a, R, bb, g, out, shift);
     }
-    __syncwarp();
+    __syncwarp(mask);
   }
   reduce_block(a, R, 0, g, pend, shift);
-  __syncwarp();
-  if (shift && g == 0) {  // fold t^97 = 1 - t^64
+  __syncwarp(mask);
+  if (kSquare && shift && g == 0) {  // fold t^97 = 1 - t^64
     const uint32_t top = a[kR];
     a[0] = top;
     a[64] -= top;
     a[kR] = 0;
   }
-  __syncwarp();
+  __syncwarp(mask);
+}
+
+__device__ __forceinline__ void square_reduce_pair(uint32_t* __restrict__ a,
+                                                   uint32_t* __restrict__ R, uint32_t shift,
+                                                   unsigned g) {
+  product_reduce_pair<true>(a, a, R, shift, g, kFull);
 }
 
 __device__ __forceinline__ uint32_t exp_word(const uint32_t (&E)[kMaxExpWords], int w) {
@@ -222,13 +235,12 @@ __device__ __forceinline__ void exp_mul_add(uint32_t (&E)[kMaxExpWords], const u
   }
 }
 
-// dst = f^E(base) for the stream of this lane pair; all 32 lanes of the warp
-// call it together (the bit loop is warp-uniform).
-__device__ __forceinline__ void jump_pair(const ranmar_state_t* __restrict__ base,
-                                          const uint32_t (&E)[kMaxExpWords], bool active,
-                                          ranmar_state_t* __restrict__ dst,
-                                          uint32_t* __restrict__ a, uint32_t* __restrict__ R,
-                                          unsigned g) {
+// a = t^E mod phi for the stream of this lane pair by left-to-right
+// square-and-multiply; all 32 lanes of the warp call it together (the bit
+// loop is warp-uniform: it runs over the longest exponent of the warp).
+__device__ __forceinline__ void poly_power_pair(const uint32_t (&E)[kMaxExpWords], bool active,
+                                                uint32_t* __restrict__ a,
+                                                uint32_t* __restrict__ R, unsigned g) {
   const int nb = active ? exp_bitlen(E) : 0;
   const int L = static_cast<int>(__reduce_max_sync(kFull, static_cast<unsigned>(nb)));
 
@@ -251,12 +263,19 @@ __device__ __forceinline__ void jump_pair(const ranmar_state_t* __restrict__ bas
     const uint32_t bit = active ? exp_bit(E, p) : 0u;
     square_reduce_pair(a, R, bit, g);
   }
+}
 
-  // Application through a 128-word ring of the extended window X: X(0..96)
-  // is the base state, X(q) = X(q-97) - X(q-33) beyond.  Round m handles
-  // output blocks K = 2m + g, whose windows are X[8K .. 8K+111]; between
-  // rounds 16 new words replace the 16 oldest (each depends only on words
-  // still in the ring).
+// dst = x P(A) with P = a (97 coefficients, zero padded), and the c / pos
+// jump by E.  The extended window X is consumed through the 128-word region
+// R used as a ring: X(0..96) is the base state, X(q) = X(q-97) - X(q-33)
+// beyond.  Round m handles output blocks K = 2m + g, whose windows are
+// X[8K .. 8K+111]; between rounds 16 new words replace the 16 oldest (each
+// depends only on words still in the ring).
+__device__ __forceinline__ void apply_pair(const ranmar_state_t* __restrict__ base,
+                                           const uint32_t (&E)[kMaxExpWords], bool active,
+                                           ranmar_state_t* __restrict__ dst,
+                                           const uint32_t* __restrict__ a,
+                                           uint32_t* __restrict__ R, unsigned g) {
   uint32_t* ring = R;
   const uint32_t* bx = base->x;
   for (int q = static_cast<int>(g); q < kR; q += 2) ring[q] = bx[q];
@@ -327,6 +346,35 @@ __device__ __forceinline__ void jump_pair(const ranmar_state_t* __restrict__ bas
   }
 }
 
+// dst = f^E(base) for the stream of this lane pair.
+__device__ __forceinline__ void jump_pair(const ranmar_state_t* __restrict__ base,
+                                          const uint32_t (&E)[kMaxExpWords], bool active,
+                                          ranmar_state_t* __restrict__ dst,
+                                          uint32_t* __restrict__ a, uint32_t* __restrict__ R,
+                                          unsigned g) {
+  poly_power_pair(E, active, a, R, g);
+  apply_pair(base, E, active, dst, a, R, g);
+}
+
+// Exponent of stream i: mode 0 reads it from d_exp, mode 1 forms (k0 + i) J.
+__device__ __forceinline__ void load_exponent(uint32_t (&E)[kMaxExpWords], int mode,
+                                              const uint32_t* __restrict__ d_exp,
+                                              uint32_t exp_words, const ExpParams& part,
+                                              uint64_t i) {
+#pragma unroll
+  for (int w = 0; w < kMaxExpWords; ++w) E[w] = 0;
+  if (mode == 0) {
+    const uint32_t* ew = d_exp + i * exp_words;
+#pragma unroll
+    for (int w = 0; w < kMaxExpWords; ++w)
+      if (w < static_cast<int>(exp_words)) E[w] = ew[w];
+  } else {
+    const uint64_t k = part.k0 + i;
+    exp_mul_add(E, part.J, static_cast<uint32_t>(k), 0);
+    exp_mul_add(E, part.J, static_cast<uint32_t>(k >> 32), 1);
+  }
+}
+
 // mode 0: E_i from d_exp (exp_words per stream), base d_base[base_idx[i]].
 // mode 1: E_i = (k0 + i) * J, base d_base[0].
 // d_dst_idx (mode 0 only, may be null): stream i is written to
@@ -346,26 +394,15 @@ __global__ void __launch_bounds__(32) jump_kernel(
 
   bool active = i < n;
   uint32_t E[kMaxExpWords];
-#pragma unroll
-  for (int w = 0; w < kMaxExpWords; ++w) E[w] = 0;
+  load_exponent(E, active ? mode : 0, d_exp, active ? exp_words : 0, part, i);
   const ranmar_state_t* base = d_base;
-  if (active) {
-    if (mode == 0) {
-      const uint32_t* ew = d_exp + i * exp_words;
-#pragma unroll
-      for (int w = 0; w < kMaxExpWords; ++w)
-        if (w < static_cast<int>(exp_words)) E[w] = ew[w];
-      const uint32_t bi = d_base_idx ? d_base_idx[i] : 0u;
-      if (bi >= n_base) {
-        if (g == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
-        active = false;
-      } else {
-        base = d_base + bi;
-      }
+  if (active && mode == 0) {
+    const uint32_t bi = d_base_idx ? d_base_idx[i] : 0u;
+    if (bi >= n_base) {
+      if (g == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
+      active = false;
     } else {
-      const uint64_t k = part.k0 + i;
-      exp_mul_add(E, part.J, static_cast<uint32_t>(k), 0);
-      exp_mul_add(E, part.J, static_cast<uint32_t>(k >> 32), 1);
+      base = d_base + bi;
     }
   }
   uint64_t di = i;

@@ -1,0 +1,134 @@
+// jump_table.cuh -- jump-ahead with a fixed-base power table.
+//
+// The base of the exponentiation is always t, so every power t^{d 2^{8j}}
+// mod phi can be computed once and shared by all streams (fixed-base
+// windowed exponentiation).  With E = sum_j d_j 2^{8j} (base-256 digits,
+// j < 20 for E < 2^160):
+//     t^E mod phi = prod_{j : d_j != 0} T[j][d_j]   (mod phi),
+// where T[j][d] = t^{d 2^{8j}} mod phi.  The table depends on nothing but
+// phi (not on the seed, J or k); it has 20 x 256 rows of 100 words (97
+// coefficients, 3 zeros), about 2 MB, which stays in L2.  A stream then needs
+// (number of nonzero digits - 1) general products instead of bitlen(E)
+// squarings: one product for E = k 2^40 with k < 2^16, at most 19 for any
+// 160-bit E.  The result P_E is the same polynomial the left-to-right
+// square-and-multiply gives (it is unique), so the jumped states are
+// bit-identical.  The table rows themselves are built by that
+// square-and-multiply (poly_power_pair), with the exponent d 2^{8j}.
+#pragma once
+
+#include "jump.cuh"
+
+namespace ranmar {
+
+constexpr int kTabWindowBits = 8;
+constexpr int kTabWindows = 32 * kMaxExpWords / kTabWindowBits;  // 20
+constexpr int kTabDigits = 1 << kTabWindowBits;                  // 256
+constexpr int kTabRows = kTabWindows * kTabDigits;               // 5120
+constexpr int kTabRowWords = 100;                                // 97 + 3 zeros
+constexpr size_t kTabBytes = sizeof(uint32_t) * kTabRowWords * kTabRows;
+// per-stream slice of the table jump: a (104) + b (104) + R (128) = 336 words,
+// stride 344 = 24 mod 32 (16-byte loads of a quarter warp: 8 distinct groups)
+constexpr int kTabStreamWords = 344;
+constexpr size_t kTabSmemBytes = sizeof(uint32_t) * kTabStreamWords * kJumpStreamsPerWarp;
+static_assert(kTabStreamWords % 32 == 24, "bank spread");
+
+// Row (j * 256 + d) = t^{d 2^{8j}} mod phi, canonical 24-bit coefficients
+// 0..96, then zeros.
+__global__ void __launch_bounds__(32) table_build_kernel(uint32_t* __restrict__ table) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned g = lane & 1, slot = lane >> 1;
+  const int row = blockIdx.x * kJumpStreamsPerWarp + static_cast<int>(slot);
+  const bool active = row < kTabRows;
+  uint32_t* a = smem + slot * kStreamWords;
+  uint32_t* R = a + kPolyWords;
+  uint32_t E[kMaxExpWords];
+#pragma unroll
+  for (int w = 0; w < kMaxExpWords; ++w) E[w] = 0;
+  if (active) {
+    const int j = row / kTabDigits, d = row % kTabDigits;
+    const int bit = kTabWindowBits * j;  // d * 2^bit, d < 256, bit + 8 <= 160
+    const uint64_t v = static_cast<uint64_t>(d) << (bit & 31);
+    const int w0 = bit >> 5;
+    E[w0] = static_cast<uint32_t>(v);
+    if (w0 + 1 < kMaxExpWords) E[w0 + 1] = static_cast<uint32_t>(v >> 32);
+  }
+  poly_power_pair(E, active, a, R, g);
+  if (active) {
+    uint32_t* dst = table + static_cast<size_t>(row) * kTabRowWords;
+    for (int q = static_cast<int>(g); q < kTabRowWords; q += 2) dst[q] = q < kR ? (a[q] & kMask24) : 0u;
+  }
+}
+
+__device__ __forceinline__ uint32_t exp_digit(const uint32_t (&E)[kMaxExpWords], int j) {
+  return (exp_word(E, j >> 2) >> (8 * (j & 3))) & 0xFFu;
+}
+
+// Copies one 100-word table row (25 x 16 bytes) into shared memory.
+__device__ __forceinline__ void copy_row(uint32_t* __restrict__ dst,
+                                         const uint32_t* __restrict__ src, unsigned g) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  for (int q = static_cast<int>(g); q < kTabRowWords / 4; q += 2) d4[q] = __ldg(s4 + q);
+}
+
+// Same contract as jump_kernel (modes 0 and 1, optional destination
+// indices), with P_E from the table.
+__global__ void __launch_bounds__(32) jump_table_kernel(
+    const uint32_t* __restrict__ table, const ranmar_state_t* __restrict__ d_base,
+    uint64_t n_base, const uint32_t* __restrict__ d_base_idx,
+    const uint32_t* __restrict__ d_exp, uint32_t exp_words, ExpParams part, int mode,
+    ranmar_state_t* __restrict__ d_out, uint64_t n, uint32_t* status,
+    const uint32_t* __restrict__ d_dst_idx, uint64_t n_dst) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned g = lane & 1, slot = lane >> 1;
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * kJumpStreamsPerWarp + slot;
+  uint32_t* a = smem + slot * kTabStreamWords;
+  uint32_t* b = a + kPolyWords;
+  uint32_t* R = b + kPolyWords;
+
+  bool active = i < n;
+  uint32_t E[kMaxExpWords];
+  load_exponent(E, active ? mode : 0, d_exp, active ? exp_words : 0, part, i);
+  const ranmar_state_t* base = d_base;
+  if (active && mode == 0) {
+    const uint32_t bi = d_base_idx ? d_base_idx[i] : 0u;
+    if (bi >= n_base) {
+      if (g == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
+      active = false;
+    } else {
+      base = d_base + bi;
+    }
+  }
+  uint64_t di = i;
+  if (active && d_dst_idx) {
+    di = d_dst_idx[i];
+    if (di >= n_dst) {
+      if (g == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
+      active = false;
+    }
+  }
+
+  // a = 1 (t^0), b zero padded
+  for (int q = static_cast<int>(g); q < 2 * kPolyWords; q += 2) a[q] = (q == 0);
+  __syncwarp();
+  bool have = false;
+#pragma unroll 1
+  for (int j = 0; j < kTabWindows; ++j) {
+    const uint32_t d = active ? exp_digit(E, j) : 0u;
+    const bool first = d != 0 && !have;
+    const bool mul = d != 0 && have;
+    const uint32_t* row = table + static_cast<size_t>(j * kTabDigits + d) * kTabRowWords;
+    if (first) copy_row(a, row, g);
+    if (mul) copy_row(b, row, g);
+    const unsigned mmask = __ballot_sync(kFull, mul);
+    __syncwarp();
+    if (mul) product_reduce_pair<false>(a, b, R, 0u, g, mmask);
+    __syncwarp();
+    have = have || d != 0;
+  }
+  apply_pair(base, E, active, d_out + (active ? di : 0), a, R, g);
+}
+
+}  // namespace ranmar

@@ -13,6 +13,7 @@
 #include "generate.cuh"
 #include "jump.cuh"
 #include "batch.cuh"
+#include "jump_table.cuh"
 
 // Batch handle: the workspace of the persistent path on one device.
 struct ranmar_batch {
@@ -26,6 +27,12 @@ struct ranmar_batch {
   uint32_t* cursor;            // bucket cursors
   uint64_t* tile_sums;         // ceil(capacity / 1024) tile sums
   ranmar_batch_config_t cfg;
+};
+
+// Fixed-base power table on one device.
+struct ranmar_table {
+  int device;
+  uint32_t* rows;   // kTabRows x kTabRowWords
 };
 
 struct ranmar_graph {
@@ -631,6 +638,119 @@ int ranmar_checksum(const uint32_t* d_data, size_t data_len, const ranmar_sum_it
       d_data, d_items, n_items, data_len, reinterpret_cast<unsigned long long*>(d_results),
       n_results, d_status);
   return check_launch();
+}
+
+int ranmar_table_create(ranmar_table_t** out) {
+  if (!out) return RANMAR_EINVAL;
+  *out = nullptr;
+  ranmar_table* t = new (std::nothrow) ranmar_table{};
+  if (!t) return RANMAR_ENOMEM;
+  cudaError_t e = cudaGetDevice(&t->device);
+  if (e == cudaSuccess) e = cudaMalloc(&t->rows, ranmar::kTabBytes);
+  if (e != cudaSuccess) {
+    delete t;
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      return RANMAR_ENOMEM;
+    }
+    return cuda_fail(e);
+  }
+  cudaStream_t s = nullptr;
+  e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    const unsigned blocks = (ranmar::kTabRows + ranmar::kJumpStreamsPerWarp - 1) /
+                            ranmar::kJumpStreamsPerWarp;
+    ranmar::table_build_kernel<<<blocks, 32, ranmar::kJumpSmemBytes, s>>>(t->rows);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  if (e != cudaSuccess) {
+    cudaFree(t->rows);
+    delete t;
+    return cuda_fail(e);
+  }
+  *out = t;
+  return RANMAR_OK;
+}
+
+int ranmar_table_destroy(ranmar_table_t* t) {
+  if (!t) return RANMAR_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(t->device);
+  cudaDeviceSynchronize();
+  const cudaError_t e = cudaFree(t->rows);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete t;
+  return e == cudaSuccess ? RANMAR_OK : cuda_fail(e);
+}
+
+int ranmar_table_rows(const ranmar_table_t* t, const uint32_t** d_rows) {
+  if (!t || !d_rows) return RANMAR_EINVAL;
+  *d_rows = t->rows;
+  return RANMAR_OK;
+}
+
+static int launch_jump_table(const ranmar_table_t* t, const ranmar_state_t* base, size_t n_base,
+                             const uint32_t* base_idx, const uint32_t* exp, uint32_t exp_words,
+                             const ranmar::ExpParams& part, int mode, ranmar_state_t* out,
+                             size_t n, uint32_t* status, ranmar_stream_t stream,
+                             const uint32_t* dst_idx, size_t n_dst) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != t->device) return RANMAR_EINVAL;
+  const uint64_t blocks = (n + ranmar::kJumpStreamsPerWarp - 1) / ranmar::kJumpStreamsPerWarp;
+  if (blocks > 0x7FFFFFFFull) return RANMAR_ERANGE;
+  ranmar::jump_table_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kTabSmemBytes,
+                              reinterpret_cast<cudaStream_t>(stream)>>>(
+      t->rows, base, n_base, base_idx, exp, exp_words, part, mode, out, n, status, dst_idx,
+      n_dst);
+  return check_launch();
+}
+
+int ranmar_jump_tab(const ranmar_table_t* t, const ranmar_state_t* d_base, size_t n_base,
+                    const uint32_t* d_base_idx, const uint32_t* d_exp, uint32_t exp_words,
+                    ranmar_state_t* d_dst, size_t n_dst, const uint32_t* d_dst_idx, size_t n,
+                    uint32_t* d_status, ranmar_stream_t stream) {
+  if (!t) return RANMAR_EINVAL;
+  if (n == 0) return RANMAR_OK;
+  if (!d_base || !d_exp || !d_dst) return RANMAR_EINVAL;
+  if (exp_words < 1 || exp_words > RANMAR_MAX_EXP_WORDS || n_base == 0) return RANMAR_ERANGE;
+  if (d_dst_idx ? n_dst == 0 : n_dst < n) return RANMAR_ERANGE;
+  if (!aligned(d_base, 16) || !aligned(d_dst, 16) || !aligned(d_exp, 4) ||
+      !aligned(d_base_idx, 4) || !aligned(d_dst_idx, 4))
+    return RANMAR_EINVAL;
+  if (!d_dst_idx &&
+      overlaps(d_base, n_base * sizeof(ranmar_state_t), d_dst, n * sizeof(ranmar_state_t)))
+    return RANMAR_EINVAL;
+  ranmar::ExpParams part{};
+  return launch_jump_table(t, d_base, n_base, d_base_idx, d_exp, exp_words, part, 0, d_dst, n,
+                           d_status, stream, d_dst_idx, n_dst);
+}
+
+int ranmar_partition_tab(const ranmar_table_t* t, const ranmar_state_t* d_base,
+                         const uint32_t* h_J, uint32_t J_words, uint64_t k0,
+                         ranmar_state_t* d_out, size_t n, ranmar_stream_t stream) {
+  if (!t) return RANMAR_EINVAL;
+  if (n == 0) return RANMAR_OK;
+  if (!d_base || !h_J || !d_out) return RANMAR_EINVAL;
+  if (J_words < 1 || J_words > RANMAR_MAX_EXP_WORDS) return RANMAR_ERANGE;
+  if (!aligned(d_base, 16) || !aligned(d_out, 16)) return RANMAR_EINVAL;
+  if (overlaps(d_base, sizeof(ranmar_state_t), d_out, n * sizeof(ranmar_state_t)))
+    return RANMAR_EINVAL;
+  if (n - 1 > UINT64_MAX - k0) return RANMAR_ERANGE;
+  const uint64_t kmax = k0 + (n - 1);
+  int jbits = 0;
+  for (int w = 0; w < static_cast<int>(J_words); ++w)
+    if (h_J[w]) jbits = 32 * w + 32 - __builtin_clz(h_J[w]);
+  const int kbits = kmax ? 64 - __builtin_clzll(kmax) : 0;
+  if (jbits + kbits > 32 * RANMAR_MAX_EXP_WORDS) return RANMAR_ERANGE;
+  ranmar::ExpParams part{};
+  for (uint32_t w = 0; w < J_words; ++w) part.J[w] = h_J[w];
+  part.J_words = J_words;
+  part.k0 = k0;
+  return launch_jump_table(t, d_base, 1, nullptr, nullptr, 0, part, 1, d_out, n, nullptr, stream,
+                           nullptr, n);
 }
 
 }  // extern "C"

@@ -164,8 +164,11 @@ class Engine:
     def __init__(self, budget_bytes: int = 40 << 30, seg: int = 1 << 16,
                  state_entries: int = 1 << 18, max_seeds: int = 10**4 + 1,
                  result_slots: int = 1 << 17, max_segments_per_iter: int = 8192,
-                 max_inflight: int = 4, device="cuda"):
+                 max_inflight: int = 4, device="cuda", use_table: bool = True):
         self.dev = torch.device(device)
+        # fixed-base table jump (bit-identical to square-and-multiply, far fewer
+        # multiply-adds per segment start); use_table=False keeps the latter
+        self.table = bd.Table() if use_table else None
         self.seg = seg
         self.max_segs = max_segments_per_iter
         self.max_inflight = max_inflight
@@ -312,11 +315,9 @@ class Engine:
             if n:
                 pair[1][:n].copy_(pair[0][:n], non_blocking=True)
         if nj:
-            bd.jump_scatter(self.base, st.exps[1], self.pool, st.dst_idx[1],
-                            base_idx=st.base_idx[1], status=self.status, stream=s, n=nj)
+            self._jump(self.base, st.exps[1], st.dst_idx[1], st.base_idx[1], nj)
         if npj:
-            bd.jump_scatter(self.pool, st.pexps[1], self.pool, st.pdst_idx[1],
-                            base_idx=st.pbase_idx[1], status=self.status, stream=s, n=npj)
+            self._jump(self.pool, st.pexps[1], st.pdst_idx[1], st.pbase_idx[1], npj)
         if nu:
             self.batch.generate_u24(self.pool, st.desc_u[1][:nu], self.out, status=self.status,
                                     stream=s)
@@ -334,6 +335,14 @@ class Engine:
         self.stats["segments"] += nseg_tot
         self.stats["jumps"] += nj + npj
         return {"event": ev, "reqs": reqs, "t0": t0_event, "slots": (lo_s, hi_s)}
+
+    def _jump(self, base, exps, dst_idx, base_idx, n):
+        if self.table is not None:
+            self.table.jump(base, exps, base_idx=base_idx, out=self.pool, dst_idx=dst_idx,
+                            status=self.status, stream=self.stream, n=n)
+        else:
+            bd.jump_scatter(base, exps, self.pool, dst_idx, base_idx=base_idx,
+                            status=self.status, stream=self.stream, n=n)
 
     def retire(self, it: dict) -> None:
         it["event"].synchronize()
@@ -452,6 +461,8 @@ class Engine:
 
     def close(self):
         self.batch.close()
+        if self.table is not None:
+            self.table.close()
 
 
 def summarize(reqs) -> dict:

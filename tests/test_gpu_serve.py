@@ -65,7 +65,7 @@ def test_serving_mix_matches_oracle_and_alone(rm, orc):
     # small segments, few segments per iteration and a tiny state pool: many
     # iterations, multi-segment requests, pool jumps, resumes and evictions
     eng = Engine(budget_bytes=64 << 20, seg=4096, state_entries=96,
-                 max_segments_per_iter=48, max_inflight=3)
+                 max_segments_per_iter=48, max_inflight=3, use_table=False)
     summary = eng.run(reqs, realtime=False)
     assert summary["requests"] == len(reqs)
     assert eng.stats["resumed"] > 0 and eng.stats["evicted"] > 0
@@ -74,7 +74,7 @@ def test_serving_mix_matches_oracle_and_alone(rm, orc):
     # each of a sample, alone in a fresh engine, with its offset as admitted
     for r in [reqs[i] for i in (0, 3, 7, 40, 100, 200, 259)]:
         solo = Request(0, 0.0, r.seed, r.k, r.J, r.count, r.f32, offset=r.offset)
-        e2 = Engine(budget_bytes=64 << 20, seg=4096, state_entries=96)
+        e2 = Engine(budget_bytes=64 << 20, seg=4096, state_entries=96, use_table=True)
         e2.run([solo], realtime=False)
         e2.close()
         assert solo.checksum == r.checksum, r.rid
