@@ -11,10 +11,10 @@
 //     X(Wb + L) = R_{b-96/W}[L] - R_{b-32/W}[L]     (no data movement)
 //     R_b[L]    = shfl(X, L - 1), lane 0 <- carry   (one shuffle)
 // and the 97 state words are exactly the 96/W ring registers of the group
-// plus the carry.  c_n of each lane comes in closed form (Sec. 3.2): lane L
-// of step b uses c_{Wb+L+1} = (c_{Wb} - (L+1) d) mod m.  Output
-// (X - c) mod 2^24 is stored coalesced (W consecutive words per step,
-// streaming hint).
+// plus the carry.  c_n of each lane starts in closed form (Sec. 3.2): lane L
+// begins at c_{L+1} = (c_0 - (L+1) d) mod m and every step moves it by W
+// transitions, c <- (c - W d) mod m.  Output (X - c) mod 2^24 is stored
+// coalesced (W consecutive words per step, streaming hint).
 #pragma once
 
 #include "ranmar_device.cuh"
@@ -22,13 +22,28 @@
 namespace ranmar {
 
 template <bool F32>
-__device__ __forceinline__ void store_output(void* out, uint64_t idx, uint32_t y) {
+struct OutT {
+  using type = uint32_t;
+};
+template <>
+struct OutT<true> {
+  using type = float;
+};
+
+template <bool F32>
+__device__ __forceinline__ void store_output(typename OutT<F32>::type* p, uint32_t y) {
   if constexpr (F32) {
     // y < 2^24 converts exactly; the power-of-two scale is exact (Sec. 4).
-    __stcs(static_cast<float*>(out) + idx, __uint2float_rn(y) * (1.0f / 16777216.0f));
+    __stcs(p, __uint2float_rn(y) * (1.0f / 16777216.0f));
   } else {
-    __stcs(static_cast<uint32_t*>(out) + idx, y);
+    __stcs(p, y);
   }
+}
+
+// (c - delta) mod m for c, delta in [0, m): min(c - delta, c + (m - delta)) --
+// exactly one of the two is below m (the other wrapped past 2^32 or is >= m).
+__device__ __forceinline__ uint32_t step_c(uint32_t c, uint32_t delta, uint32_t m_minus_delta) {
+  return min(c - delta, c + m_minus_delta);
 }
 
 struct LaneConsts {
@@ -43,7 +58,8 @@ __device__ __forceinline__ LaneConsts lane_consts(unsigned gl) {
 
 // Generates `count` outputs of *st into out[out_base + n], n < count, and
 // optionally writes the advanced state back.  Called by the W lanes of one
-// group (gl = lane within the group, gmask = the group's lane mask).
+// group (gl = lane within the group, gmask = the group's lane mask).  Each
+// lane carries its own c: c_{Wb+L+1} for the step b it is on.
 template <int W, bool F32>
 __device__ void generate_stream(ranmar_state_t* st, uint64_t count, void* out, uint64_t out_base,
                                 bool write_back, unsigned gl, unsigned gmask,
@@ -51,26 +67,28 @@ __device__ void generate_stream(ranmar_state_t* st, uint64_t count, void* out, u
   constexpr int NR = 96 / W;  // ring registers: blocks b-NR .. b-1
   constexpr int Q = 32 / W;   // the newer input is block b-Q
   static_assert(NR * W == 96 && Q * W == 32, "group width");
+  using T = typename OutT<F32>::type;
   const uint32_t* xs = st->x;
   uint32_t r[NR];
 #pragma unroll
   for (int j = 0; j < NR; ++j) r[j] = xs[W * j + gl];  // R_{j-NR}[L] = X(W(j-NR) + L - 1)
   uint32_t carry = xs[96];                               // X(-1)
-  uint32_t cb = st->c;
+  const uint32_t c0 = st->c;
   const uint64_t pos0 = st->pos;
+  uint32_t cl = sub_mod_m(c0, k.delta_lane);             // c_{L+1}
+  const uint32_t dw = k.delta_w, mdw = kModM - k.delta_w;
 
   const uint64_t nblk = count / W;
   const unsigned rem = static_cast<unsigned>(count % W);
-  uint64_t o = out_base + gl;
+  T* p = static_cast<T*>(out) + out_base + gl;
   const unsigned src = (gl + W - 1) % W;
 
-  // One step producing R_b into `older` (= R_{b-NR} on entry).
-  auto step = [&](uint32_t& older, uint32_t newer) {
-    const uint32_t xv = older - newer;                  // X(Wb + L), kept mod 2^32
-    const uint32_t cl = sub_mod_m(cb, k.delta_lane);    // c_{Wb+L+1}
-    store_output<F32>(out, o, (xv - cl) & kMask24);
-    o += W;
-    cb = sub_mod_m(cb, k.delta_w);
+  // One step producing R_b into `older` (= R_{b-NR} on entry); the output
+  // goes to p[off].
+  auto step = [&](uint32_t& older, uint32_t newer, int off) {
+    const uint32_t xv = older - newer;        // X(Wb + L), kept mod 2^32
+    store_output<F32>(p + off, (xv - cl) & kMask24);
+    cl = step_c(cl, dw, mdw);
     const uint32_t t = __shfl_sync(gmask, xv, src, W);
     older = (gl == 0) ? carry : t;
     carry = t;
@@ -80,12 +98,14 @@ __device__ void generate_stream(ranmar_state_t* st, uint64_t count, void* out, u
 #pragma unroll 1
   for (; b + NR <= nblk; b += NR) {
 #pragma unroll
-    for (int j = 0; j < NR; ++j) step(r[j], r[(j + NR - Q) % NR]);
+    for (int j = 0; j < NR; ++j) step(r[j], r[(j + NR - Q) % NR], W * j);
+    p += W * NR;
   }
   // Remaining blocks: step, then shift the ring so that r[0] stays oldest.
 #pragma unroll 1
   for (; b < nblk; ++b) {
-    step(r[0], r[NR - Q]);
+    step(r[0], r[NR - Q], 0);
+    p += W;
     const uint32_t nw = r[0];
 #pragma unroll
     for (int j = 0; j + 1 < NR; ++j) r[j] = r[j + 1];
@@ -94,12 +114,9 @@ __device__ void generate_stream(ranmar_state_t* st, uint64_t count, void* out, u
 
   // Ragged tail: one more block with masked stores.
   uint32_t xb = 0;
-  uint32_t c_end = cb;
   if (rem != 0) {
     xb = r[0] - r[NR - Q];  // X(WB + L)
-    const uint32_t cl = sub_mod_m(cb, k.delta_lane);
-    if (gl < rem) store_output<F32>(out, o, (xb - cl) & kMask24);
-    c_end = __shfl_sync(gmask, cl, rem - 1, W);
+    if (gl < rem) store_output<F32>(p, (xb - cl) & kMask24);
   }
 
   if (!write_back) return;
@@ -115,7 +132,9 @@ __device__ void generate_stream(ranmar_state_t* st, uint64_t count, void* out, u
   if (gl == 0) xw[96 - rem] = carry & kMask24;
   if (gl < rem) xw[gl + 97 - rem] = xb & kMask24;
   if (gl == 0) {
-    st->c = c_end;
+    // c after `count` transitions, in closed form (Sec. 3.2)
+    const uint64_t e = count % kModM;
+    st->c = static_cast<uint32_t>((static_cast<uint64_t>(c0) + (kModM - e) * kD) % kModM);
     st->pos = pos0 + count;
   }
 }
