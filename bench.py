@@ -225,9 +225,10 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
+    from paper_2512_00093_gb300.shard import max_over_ranks, shard
     w = Partitioned()
-    n, count = args.streams, w.count
-    k0 = rank * n                      # each rank: its own disjoint block of streams
+    count = w.count
+    k0, n = shard(rank, world, args.streams)   # disjoint blocks of streams per rank
     exps = [(k0 + i) * w.J for i in range(n)]
     stream = torch.cuda.current_stream()
 
@@ -270,11 +271,7 @@ def run_ours(args):
     clk = clocks.stop()
     t_jump = [ev[s][0].elapsed_time(ev[s][1]) for s in range(K)]
     t_gen = [ev[s][1].elapsed_time(ev[s][2]) for s in range(K)]
-    ms_step = (sum(t_jump) + sum(t_gen)) / K
-    if dist:
-        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks((sum(t_jump) + sum(t_gen)) / K, dist, dev)
     value = world * n * count / (ms_step * 1e-3)
 
     # ---- end to end through the public API with host buffers ------------
@@ -299,11 +296,7 @@ def run_ours(args):
         h_out.copy_(out, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1) / e2e_steps
-    if dist:
-        t = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist, dev)
     ok_e2e = bool(np.array_equal(h_out[:count].numpy(), out[:count].cpu().numpy()))
     # the paper's left-to-right square-and-multiply on the same streams
     sm_states = torch.empty_like(states)
