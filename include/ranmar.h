@@ -172,6 +172,26 @@ int ranmar_generate_f32(ranmar_state_t *d_states, size_t n_states,
                         uint32_t *d_status, ranmar_stream_t stream);
 
 /*
+ * ranmar_generate_alg1_f32 / _f64 -- Algorithm 1 (Sec. 4, the floating-point
+ * form LAMMPS uses) over the same descriptors: the lagged Fibonacci words,
+ * the arithmetic sequence and the output are computed as reals in [0, 1)
+ * with the "if negative, add 1 (or cm)" fix-ups, in float or double.  Every
+ * value is a multiple of 2^-24, so both are exact and equal
+ * ranmar_generate_f32's outputs (the integer form times 2^-24, Sec. 3.1);
+ * they exist to compare the cost of the two forms on the GPU (Table 1).
+ * The state format (and write-back) is the integer one.  Errors as
+ * ranmar_generate_u24 (d_out aligned to its element size).
+ */
+int ranmar_generate_alg1_f32(ranmar_state_t *d_states, size_t n_states,
+                             const ranmar_desc_t *d_desc, size_t n_desc,
+                             float *d_out, size_t out_len,
+                             uint32_t *d_status, ranmar_stream_t stream);
+int ranmar_generate_alg1_f64(ranmar_state_t *d_states, size_t n_states,
+                             const ranmar_desc_t *d_desc, size_t n_desc,
+                             double *d_out, size_t out_len,
+                             uint32_t *d_status, ranmar_stream_t stream);
+
+/*
  * ranmar_generate_plain_u24 / _f32 -- Algorithm 2 for ONE stream in one
  * launch of one warp: `count` outputs of *d_state into d_out[0..count); if
  * write_back != 0 the state is advanced in place.  This is the

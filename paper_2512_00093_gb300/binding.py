@@ -74,6 +74,9 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         getattr(lib, name).argtypes = [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp, _vp]
     lib.ranmar_batch_tune.argtypes = [_vp, ctypes.c_int, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp,
                                       ctypes.POINTER(ctypes.c_float)]
+    for name in ("ranmar_generate_alg1_f32", "ranmar_generate_alg1_f64"):
+        getattr(lib, name).argtypes = [_vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp]
+        getattr(lib, name).restype = ctypes.c_int
     lib.ranmar_jump_scatter.argtypes = [_vp, _sz, _vp, _vp, _u32, _vp, _sz, _vp, _sz, _vp, _vp]
     lib.ranmar_checksum.argtypes = [_vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp]
     lib.ranmar_table_create.argtypes = [ctypes.POINTER(_vp)]
@@ -271,6 +274,16 @@ def generate_u24(states, desc, out, status=None, stream=None):
 def generate_f32(states, desc, out, status=None, stream=None):
     """ranmar_generate_f32 over a descriptor batch; out is float32 in [0, 1)."""
     return _generate("ranmar_generate_f32", torch.float32, states, desc, out, status, stream)
+
+
+def generate_alg1_f32(states, desc, out, status=None, stream=None):
+    """ranmar_generate_alg1_f32: Algorithm 1 in float; out is float32."""
+    return _generate("ranmar_generate_alg1_f32", torch.float32, states, desc, out, status, stream)
+
+
+def generate_alg1_f64(states, desc, out, status=None, stream=None):
+    """ranmar_generate_alg1_f64: Algorithm 1 in double; out is float64."""
+    return _generate("ranmar_generate_alg1_f64", torch.float64, states, desc, out, status, stream)
 
 
 def generate_plain_u24(state, count: int, out, write_back: bool = True, stream=None):

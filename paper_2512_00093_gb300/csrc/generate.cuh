@@ -139,6 +139,88 @@ __device__ void generate_stream(ranmar_state_t* st, uint64_t count, void* out, u
   }
 }
 
+// Algorithm 1 (Sec. 4, the LAMMPS floating-point form) with the same warp
+// mapping (W = 32): the LFG words are reals in [0, 1) (x = u 2^-24),
+//     y = x_{q-97} - x_{q-33}; if y < 0: y += 1
+//     c = c - 32 cd; if c < 0: c += cm            (32 transitions per step)
+//     out = y - c; if out < 0: out += 1
+// in floating type F (float or double).  Every value is a multiple of 2^-24
+// in [0, 1) (the per-lane offsets (L+1) cd mod cm and 32 cd mod cm are formed
+// in integers, then scaled), so float and double are exact and both equal
+// the integer form times 2^-24 (Sec. 3.1, the isomorphism sigma).  The state
+// stays in its integer format at the boundary.
+template <typename F>
+__device__ void generate_stream_alg1(ranmar_state_t* st, uint64_t count, F* out, bool write_back,
+                                     unsigned lane, const LaneConsts& k) {
+  const F S = static_cast<F>(1.0 / 16777216.0);
+  const uint32_t* xs = st->x;
+  F r0 = static_cast<F>(xs[lane]) * S;   // R_{-3}
+  F r1 = static_cast<F>(xs[32 + lane]) * S;
+  F r2 = static_cast<F>(xs[64 + lane]) * S;
+  F carry = static_cast<F>(xs[96]) * S;
+  const uint32_t c0 = st->c;
+  const uint64_t pos0 = st->pos;
+  F cl = static_cast<F>(sub_mod_m(c0, k.delta_lane)) * S;  // c_{L+1}
+  const F dw = static_cast<F>(k.delta_w) * S;
+  const F cm = static_cast<F>(kModM) * S;
+  const F one = static_cast<F>(1);
+  const uint64_t nblk = count >> 5;
+  const unsigned rem = static_cast<unsigned>(count & 31);
+  F* p = out + lane;
+  const unsigned src = (lane + 31) & 31;
+
+  auto step = [&](F& older, F newer, int off) {
+    F y = older - newer;
+    if (y < 0) y += one;
+    F o = y - cl;
+    if (o < 0) o += one;
+    __stcs(p + off, o);
+    cl -= dw;
+    if (cl < 0) cl += cm;
+    const F t = __shfl_sync(kFull, y, src);
+    older = (lane == 0) ? carry : t;
+    carry = t;
+  };
+
+  uint64_t b = 0;
+#pragma unroll 1
+  for (; b + 3 <= nblk; b += 3) {
+    step(r0, r2, 0);
+    step(r1, r0, 32);
+    step(r2, r1, 64);
+    p += 96;
+  }
+  const unsigned left = static_cast<unsigned>(nblk - b);
+  if (left >= 1) { step(r0, r2, 0); p += 32; }
+  if (left >= 2) { step(r1, r0, 0); p += 32; }
+  F rm3, rm2, rm1;
+  if (left == 0) { rm3 = r0; rm2 = r1; rm1 = r2; }
+  else if (left == 1) { rm3 = r1; rm2 = r2; rm1 = r0; }
+  else { rm3 = r2; rm2 = r0; rm1 = r1; }
+  F xb = 0;
+  if (rem != 0) {
+    xb = rm3 - rm1;
+    if (xb < 0) xb += one;
+    F o = xb - cl;
+    if (o < 0) o += one;
+    if (lane < rem) __stcs(p, o);
+  }
+  if (!write_back) return;
+  __syncwarp();
+  const F U = static_cast<F>(16777216.0);
+  uint32_t* xw = st->x;
+  if (lane >= rem) xw[lane - rem] = static_cast<uint32_t>(rm3 * U);
+  xw[lane + 32 - rem] = static_cast<uint32_t>(rm2 * U);
+  xw[lane + 64 - rem] = static_cast<uint32_t>(rm1 * U);
+  if (lane == 0) xw[96 - rem] = static_cast<uint32_t>(carry * U);
+  if (lane < rem) xw[lane + 97 - rem] = static_cast<uint32_t>(xb * U);
+  if (lane == 0) {
+    const uint64_t e = count % kModM;
+    st->c = static_cast<uint32_t>((static_cast<uint64_t>(c0) + (kModM - e) * kD) % kModM);
+    st->pos = pos0 + count;
+  }
+}
+
 // Checks one descriptor on the device; returns false (and flags the status
 // word from the group's first lane) when it must be skipped.
 __device__ __forceinline__ bool desc_ok(const ranmar_desc_t& d, uint64_t n_states,
@@ -170,6 +252,25 @@ __global__ void __launch_bounds__(256) generate_desc_kernel(
     if (!desc_ok(d, n_states, out_len, status, lane)) continue;
     generate_stream<32, F32>(states + d.state_idx, d.count, out, d.out_offset,
                              (d.flags & RANMAR_DESC_WRITE_BACK) != 0, lane, kFull, k);
+  }
+}
+
+// Algorithm 1 over a batch of descriptors (one warp per descriptor).
+template <typename F>
+__global__ void __launch_bounds__(256) generate_alg1_kernel(
+    ranmar_state_t* __restrict__ states, uint64_t n_states,
+    const ranmar_desc_t* __restrict__ desc, uint64_t n_desc, F* out, uint64_t out_len,
+    uint32_t* status) {
+  const unsigned lane = threadIdx.x & 31;
+  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  const LaneConsts k = lane_consts<32>(lane);
+#pragma unroll 1
+  for (uint64_t w = warp; w < n_desc; w += nwarps) {
+    const ranmar_desc_t d = desc[w];
+    if (!desc_ok(d, n_states, out_len, status, lane)) continue;
+    generate_stream_alg1<F>(states + d.state_idx, d.count, out + d.out_offset,
+                            (d.flags & RANMAR_DESC_WRITE_BACK) != 0, lane, k);
   }
 }
 

@@ -276,6 +276,22 @@ int static_scratch(unsigned char** out) {
   return RANMAR_OK;
 }
 
+template <typename F>
+int launch_alg1(ranmar_state_t* states, size_t n_states, const ranmar_desc_t* desc,
+                       size_t n_desc, F* out, size_t out_len, uint32_t* status,
+                       ranmar_stream_t stream) {
+  if (n_desc == 0) return RANMAR_OK;
+  if (!states || !desc || !out) return RANMAR_EINVAL;
+  if (n_states == 0) return RANMAR_ERANGE;
+  if (!aligned(states, 16) || !aligned(desc, 8) || !aligned(out, sizeof(F))) return RANMAR_EINVAL;
+  uint64_t blocks = (n_desc + 7) / 8;
+  if (blocks > (1u << 20)) blocks = 1u << 20;
+  ranmar::generate_alg1_kernel<F><<<static_cast<unsigned>(blocks), 256, 0,
+                                    reinterpret_cast<cudaStream_t>(stream)>>>(
+      states, n_states, desc, n_desc, out, out_len, status);
+  return check_launch();
+}
+
 }  // namespace
 
 extern "C" {
@@ -751,6 +767,19 @@ int ranmar_partition_tab(const ranmar_table_t* t, const ranmar_state_t* d_base,
   part.k0 = k0;
   return launch_jump_table(t, d_base, 1, nullptr, nullptr, 0, part, 1, d_out, n, nullptr, stream,
                            nullptr, n);
+}
+
+int ranmar_generate_alg1_f32(ranmar_state_t* d_states, size_t n_states,
+                             const ranmar_desc_t* d_desc, size_t n_desc, float* d_out,
+                             size_t out_len, uint32_t* d_status, ranmar_stream_t stream) {
+  return launch_alg1<float>(d_states, n_states, d_desc, n_desc, d_out, out_len, d_status, stream);
+}
+
+int ranmar_generate_alg1_f64(ranmar_state_t* d_states, size_t n_states,
+                             const ranmar_desc_t* d_desc, size_t n_desc, double* d_out,
+                             size_t out_len, uint32_t* d_status, ranmar_stream_t stream) {
+  return launch_alg1<double>(d_states, n_states, d_desc, n_desc, d_out, out_len, d_status,
+                             stream);
 }
 
 }  // extern "C"
