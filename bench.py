@@ -440,6 +440,16 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
     macs = jump_macs(exps_l)
     ms_t = timed(lambda: table.partition(base, lj.J, 0, lj.n_streams, out=st))
     macs_t = table_macs(exps_l)
+    red = rm.JUMP_REDUCE_PERIOD
+    ms_tr = timed(lambda: rm.partition_ex(base, lj.J, 0, lj.n_streams, table=table, flags=red,
+                                          out=st))
+    ms_sr = timed(lambda: rm.partition_ex(base, lj.J, 0, lj.n_streams, table=None, flags=red,
+                                          out=st))
+    res["large_jumps_period_reduced"] = {
+        "note": "labelled variant, not the paper's method: the polynomial part uses "
+                "E mod (2^97 - 1) 2^23 (the order of t); identical states",
+        "table": {"ms": ms_tr, "jumps_per_s": lj.n_streams / (ms_tr * 1e-3)},
+        "square_multiply": {"ms": ms_sr, "jumps_per_s": lj.n_streams / (ms_sr * 1e-3)}}
     res["large_jumps"] = {"streams": lj.n_streams, "J": "2^120+12345",
                           "square_multiply": {"ms": ms, "jumps_per_s": lj.n_streams / (ms * 1e-3),
                                               "tmacs_per_s": macs / (ms * 1e-3) / 1e12,

@@ -244,6 +244,26 @@ int ranmar_partition_tab(const ranmar_table_t *t, const ranmar_state_t *d_base,
                          const uint32_t *h_J, uint32_t J_words, uint64_t k0,
                          ranmar_state_t *d_out, size_t n, ranmar_stream_t stream);
 
+/* Flag of ranmar_partition_ex: the polynomial part of each jump uses
+ * E mod T, T = (2^97 - 1) 2^23 = 2^120 - 2^23, the multiplicative order of t
+ * modulo phi over Z/2^24 (t^T = 1, so t^E = t^(E mod T)); c still uses
+ * E mod m (Sec. 3.2).  The jumped states are identical; long exponents (the
+ * paper's J ~ 2^120) get much shorter.  Not in the paper (which jumps with
+ * the unreduced E); the period follows from its Sec. 2 (about 2^144 in all,
+ * 2^120 of it from the lagged Fibonacci part). */
+#define RANMAR_JUMP_REDUCE_PERIOD 1u
+
+/*
+ * ranmar_partition_ex -- ranmar_partition (t == NULL: square-and-multiply)
+ * or ranmar_partition_tab (t != NULL) with flags (0 or
+ * RANMAR_JUMP_REDUCE_PERIOD).  Errors: as those, plus RANMAR_EINVAL for an
+ * unknown flag.
+ */
+int ranmar_partition_ex(const ranmar_table_t *t, const ranmar_state_t *d_base,
+                        const uint32_t *h_J, uint32_t J_words, uint64_t k0,
+                        ranmar_state_t *d_out, size_t n, uint32_t flags,
+                        ranmar_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Persistent batch path: many streams of uneven lengths in one launch.
  * (Sec. 1 partitioning applied to a batch; Algorithm 2 per stream.)

@@ -84,6 +84,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_table_rows.argtypes = [_vp, ctypes.POINTER(_vp)]
     lib.ranmar_jump_tab.argtypes = [_vp, _vp, _sz, _vp, _vp, _u32, _vp, _sz, _vp, _sz, _vp, _vp]
     lib.ranmar_partition_tab.argtypes = [_vp, _vp, _vp, _u32, _u64, _vp, _sz, _vp]
+    lib.ranmar_partition_ex.argtypes = [_vp, _vp, _vp, _u32, _u64, _vp, _sz, _u32, _vp]
+    lib.ranmar_partition_ex.restype = ctypes.c_int
     lib.ranmar_graph_begin.argtypes = [_vp]
     lib.ranmar_graph_end.argtypes = [_vp, ctypes.POINTER(_vp)]
     lib.ranmar_graph_launch.argtypes = [_vp, _vp]
@@ -240,6 +242,25 @@ def partition(base: torch.Tensor, J: int, k0: int, n: int, out: torch.Tensor | N
     jw = np.array(words(int(J)), dtype=np.uint32)
     _check(_lib().ranmar_partition(_ptr(base), jw.ctypes.data, len(jw), int(k0), _ptr(out),
                                    int(n), _stream(stream)), "ranmar_partition")
+    return out
+
+
+JUMP_REDUCE_PERIOD = 1
+
+
+def partition_ex(base: torch.Tensor, J: int, k0: int, n: int, table=None, flags: int = 0,
+                 out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """ranmar_partition_ex: partition with the table (or square-and-multiply when
+    table is None) and optional JUMP_REDUCE_PERIOD."""
+    base = base.reshape(-1, STATE_WORDS)
+    _need(base, torch.int32, "base")
+    if out is None:
+        out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=base.device)
+    _need(out, torch.int32, "out")
+    jw = np.array(words(int(J)), dtype=np.uint32)
+    _check(_lib().ranmar_partition_ex(table._h if table is not None else None, _ptr(base),
+                                      jw.ctypes.data, len(jw), int(k0), _ptr(out), int(n),
+                                      int(flags), _stream(stream)), "ranmar_partition_ex")
     return out
 
 

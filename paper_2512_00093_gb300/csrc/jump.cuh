@@ -56,6 +56,7 @@ static_assert(kStreamWords % 32 == 8, "bank spread");
 struct ExpParams {
   uint32_t J[kMaxExpWords];  // partition mode: E = (k0 + i) * J
   uint32_t J_words;
+  uint32_t flags;            // RANMAR_JUMP_REDUCE_PERIOD
   uint64_t k0;
 };
 
@@ -235,6 +236,36 @@ __device__ __forceinline__ void exp_mul_add(uint32_t (&E)[kMaxExpWords], const u
   }
 }
 
+// E mod T for T = (2^97 - 1) 2^23 = 2^120 - 2^23, the multiplicative order of
+// t modulo phi over Z/2^24 (so t^E = t^(E mod T) and the polynomial part of a
+// jump may use the reduced exponent; c needs E mod m instead).  Two folds of
+// 2^120 = 2^23 (mod T) bring E below 2^120, then one conditional
+// subtraction of T.
+__device__ __forceinline__ void reduce_period(uint32_t (&E)[kMaxExpWords]) {
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const uint64_t hi = (static_cast<uint64_t>(E[4]) << 8) | (E[3] >> 24);  // bits 120..159
+    if (hi != 0) {
+      E[3] &= 0x00FFFFFFu;
+      E[4] = 0;
+      const uint64_t add = hi << 23;  // < 2^63
+      uint64_t t = static_cast<uint64_t>(E[0]) + static_cast<uint32_t>(add);
+      E[0] = static_cast<uint32_t>(t);
+      t = (t >> 32) + E[1] + static_cast<uint32_t>(add >> 32);
+      E[1] = static_cast<uint32_t>(t);
+      t = (t >> 32) + E[2];
+      E[2] = static_cast<uint32_t>(t);
+      t = (t >> 32) + E[3];
+      E[3] = static_cast<uint32_t>(t);
+    }
+  }
+  if (E[3] == 0x00FFFFFFu && E[2] == 0xFFFFFFFFu && E[1] == 0xFFFFFFFFu &&
+      E[0] >= 0xFF800000u) {  // T <= E < 2^120
+    E[0] -= 0xFF800000u;
+    E[1] = E[2] = E[3] = 0;
+  }
+}
+
 // a = t^E mod phi for the stream of this lane pair by left-to-right
 // square-and-multiply; all 32 lanes of the warp call it together (the bit
 // loop is warp-uniform: it runs over the longest exponent of the warp).
@@ -347,12 +378,15 @@ __device__ __forceinline__ void apply_pair(const ranmar_state_t* __restrict__ ba
 }
 
 // dst = f^E(base) for the stream of this lane pair.
+// Ep is the exponent of the polynomial part (E itself, or E mod T), E the
+// full exponent (for c and pos).
 __device__ __forceinline__ void jump_pair(const ranmar_state_t* __restrict__ base,
+                                          const uint32_t (&Ep)[kMaxExpWords],
                                           const uint32_t (&E)[kMaxExpWords], bool active,
                                           ranmar_state_t* __restrict__ dst,
                                           uint32_t* __restrict__ a, uint32_t* __restrict__ R,
                                           unsigned g) {
-  poly_power_pair(E, active, a, R, g);
+  poly_power_pair(Ep, active, a, R, g);
   apply_pair(base, E, active, dst, a, R, g);
 }
 
@@ -413,7 +447,11 @@ __global__ void __launch_bounds__(32) jump_kernel(
       active = false;
     }
   }
-  jump_pair(base, E, active, d_out + (active ? di : 0), a, R, g);
+  uint32_t Ep[kMaxExpWords];
+#pragma unroll
+  for (int w = 0; w < kMaxExpWords; ++w) Ep[w] = E[w];
+  if (part.flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
+  jump_pair(base, Ep, E, active, d_out + (active ? di : 0), a, R, g);
 }
 
 }  // namespace ranmar

@@ -110,13 +110,18 @@ __global__ void __launch_bounds__(32) jump_table_kernel(
     }
   }
 
+  uint32_t Ep[kMaxExpWords];
+#pragma unroll
+  for (int w = 0; w < kMaxExpWords; ++w) Ep[w] = E[w];
+  if (part.flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
+
   // a = 1 (t^0), b zero padded
   for (int q = static_cast<int>(g); q < 2 * kPolyWords; q += 2) a[q] = (q == 0);
   __syncwarp();
   bool have = false;
 #pragma unroll 1
   for (int j = 0; j < kTabWindows; ++j) {
-    const uint32_t d = active ? exp_digit(E, j) : 0u;
+    const uint32_t d = active ? exp_digit(Ep, j) : 0u;
     const bool first = d != 0 && !have;
     const bool mul = d != 0 && have;
     const uint32_t* row = table + static_cast<size_t>(j * kTabDigits + d) * kTabRowWords;

@@ -782,4 +782,32 @@ int ranmar_generate_alg1_f64(ranmar_state_t* d_states, size_t n_states,
                              stream);
 }
 
+int ranmar_partition_ex(const ranmar_table_t* t, const ranmar_state_t* d_base, const uint32_t* h_J,
+                        uint32_t J_words, uint64_t k0, ranmar_state_t* d_out, size_t n,
+                        uint32_t flags, ranmar_stream_t stream) {
+  if (flags & ~static_cast<uint32_t>(RANMAR_JUMP_REDUCE_PERIOD)) return RANMAR_EINVAL;
+  if (n == 0) return RANMAR_OK;
+  if (!d_base || !h_J || !d_out) return RANMAR_EINVAL;
+  if (J_words < 1 || J_words > RANMAR_MAX_EXP_WORDS) return RANMAR_ERANGE;
+  if (!aligned(d_base, 16) || !aligned(d_out, 16)) return RANMAR_EINVAL;
+  if (overlaps(d_base, sizeof(ranmar_state_t), d_out, n * sizeof(ranmar_state_t)))
+    return RANMAR_EINVAL;
+  if (n - 1 > UINT64_MAX - k0) return RANMAR_ERANGE;
+  const uint64_t kmax = k0 + (n - 1);
+  int jbits = 0;
+  for (int w = 0; w < static_cast<int>(J_words); ++w)
+    if (h_J[w]) jbits = 32 * w + 32 - __builtin_clz(h_J[w]);
+  const int kbits = kmax ? 64 - __builtin_clzll(kmax) : 0;
+  if (jbits + kbits > 32 * RANMAR_MAX_EXP_WORDS) return RANMAR_ERANGE;
+  ranmar::ExpParams part{};
+  for (uint32_t w = 0; w < J_words; ++w) part.J[w] = h_J[w];
+  part.J_words = J_words;
+  part.k0 = k0;
+  part.flags = flags;
+  if (t)
+    return launch_jump_table(t, d_base, 1, nullptr, nullptr, 0, part, 1, d_out, n, nullptr,
+                             stream, nullptr, n);
+  return launch_jump(d_base, 1, nullptr, nullptr, 0, part, 1, d_out, n, nullptr, stream);
+}
+
 }  // extern "C"

@@ -77,3 +77,26 @@ def test_partition_tab_full_size_equals_square_and_multiply(rm, table, which):
     b = rm.partition(base, w.J, 0, w.n_streams)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("use_table", [True, False])
+def test_period_reduction_gives_identical_states(rm, table, use_table):
+    """E mod T (T = (2^97 - 1) 2^23, the order of t) for the polynomial part:
+    same states as the unreduced jump, for J around and beyond 2^120."""
+    from paper_2512_00093_gb300.workloads import LargeJumps
+    dev = torch.device("cuda:0")
+    t = table if use_table else None
+    w = LargeJumps()
+    base = rm.seed(w.seed).to(dev)
+    n = w.n_streams if use_table else 2048
+    a = rm.partition_ex(base, w.J, 0, n, table=t, flags=rm.JUMP_REDUCE_PERIOD)
+    b = rm.partition_ex(base, w.J, 0, n, table=t, flags=0)
+    T = ((1 << 97) - 1) << 23
+    for J, k0, cnt in [(T, 0, 64), (T - 1, 5, 64), ((1 << 159) - 1, 0, 2),
+                       ((1 << 130) + 7, 1000, 64), (12345, 3, 64)]:
+        x = rm.partition_ex(base, J, k0, cnt, table=t, flags=rm.JUMP_REDUCE_PERIOD)
+        y = rm.partition_ex(base, J, k0, cnt, table=t, flags=0)
+        torch.cuda.synchronize()
+        assert torch.equal(x, y), (J, k0)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
