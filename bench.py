@@ -229,7 +229,6 @@ def run_ours(args):
     w = Partitioned()
     count = w.count
     k0, n = shard(rank, world, args.streams)   # disjoint blocks of streams per rank
-    exps = [(k0 + i) * w.J for i in range(n)]
     stream = torch.cuda.current_stream()
 
     base = rm.seed(w.seed).to(dev)
@@ -243,14 +242,20 @@ def run_ours(args):
     table = rm.Table()
     table_build_ms = (time.perf_counter() - tb0) * 1e3
 
-    def step():
-        table.partition(base, w.J, k0, n, out=states)
+    # Each step is one full pass (jump + generate) over a fresh batch of
+    # streams: batch i of rank r is k = (i * world + r) * n + 0..n-1.
+    def k0_of(i):
+        return (i * world + rank) * n
+
+    def serial_step(i):
+        table.partition(base, w.J, k0_of(i), n, out=states)
         rm.generate_u24(states, desc, out)
 
-    for _ in range(args.warmup):
-        step()
+    for i in range(args.warmup):
+        serial_step(i)
     torch.cuda.synchronize()
 
+    # ---- serial steps: per-kernel times for the roofline ---------------------
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     clocks = Clocks(local)
@@ -258,60 +263,114 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    for s in range(K):
-        flush.fill_(s & 0xFF)          # L2 flush outside the timed events
-        ev[s][0].record(stream)
-        table.partition(base, w.J, k0, n, out=states)
-        ev[s][1].record(stream)
+    for i in range(K):
+        flush.fill_(i & 0xFF)          # L2 flush outside the timed events
+        ev[i][0].record(stream)
+        table.partition(base, w.J, k0_of(i), n, out=states)
+        ev[i][1].record(stream)
         rm.generate_u24(states, desc, out)
-        ev[s][2].record(stream)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    t_jump = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
+    t_gen = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
+    serial_ms = max_over_ranks((sum(t_jump) + sum(t_gen)) / K, dist, dev)
+
+    # ---- pipelined steps (the measured throughput): the jump of batch i+1
+    # (integer pipe) runs on its own stream while batch i generates (HBM),
+    # states double-buffered; every step still jumps and generates its batch.
+    sJ, sG = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    bufs = [states, torch.empty_like(states)]
+
+    def pipeline(first, steps, d_base=None, h2d=None, d2h=None):
+        evJ, evG, evD = [], [], []
+        for j in range(steps):
+            i = first + j
+            buf = bufs[j % 2]
+            if j >= 2:
+                sJ.wait_event(evG[j - 2])          # batch j-2 finished reading buf
+            with torch.cuda.stream(sJ):
+                src = base
+                if h2d is not None:                 # end to end: inputs from the host
+                    src = d_base[j % 2]
+                    src.copy_(h2d, non_blocking=True)
+                table.partition(src, w.J, k0_of(i), n, out=buf, stream=sJ)
+            e = torch.cuda.Event()
+            e.record(sJ)
+            evJ.append(e)
+            sG.wait_event(e)
+            o = out if d2h is None else d2h[1][j % 2]
+            if d2h is not None and j >= 2:
+                sG.wait_event(evD[j - 2])          # host copy of batch j-2 done
+            rm.generate_u24(buf, desc, o, stream=sG)
+            g = torch.cuda.Event()
+            g.record(sG)
+            evG.append(g)
+            if d2h is not None:
+                sD = d2h[2]
+                sD.wait_event(g)
+                with torch.cuda.stream(sD):
+                    d2h[0][j % 2].copy_(o, non_blocking=True)
+                dd = torch.cuda.Event()
+                dd.record(sD)
+                evD.append(dd)
+        return (evD or evG)[-1]
+
+    torch.cuda.synchronize()
+    pipeline(K, 2)                                 # warm the two streams
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(sJ)
+    last = pipeline(K + 2, K)
+    sG.wait_event(last)
+    t1.record(sG)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    t_jump = [ev[s][0].elapsed_time(ev[s][1]) for s in range(K)]
-    t_gen = [ev[s][1].elapsed_time(ev[s][2]) for s in range(K)]
-    ms_step = max_over_ranks((sum(t_jump) + sum(t_gen)) / K, dist, dev)
+    ms_step = max_over_ranks(t0.elapsed_time(t1) / K, dist, dev)
     value = world * n * count / (ms_step * 1e-3)
 
-    # ---- end to end through the public API with host buffers ------------
+    # ---- end to end through the public API with host buffers: the seeded base
+    # state copied in from pinned memory and the whole 1 GiB result copied back
+    # to pinned memory every step, on a third stream, double-buffered.
     h_base = rm.seed(w.seed).pin_memory()
-    h_out = torch.empty(n * count, dtype=torch.int32).pin_memory()
-    d_base = torch.empty_like(base)
+    d_bases = [torch.empty_like(base), torch.empty_like(base)]
+    h_outs = [torch.empty(n * count, dtype=torch.int32).pin_memory() for _ in range(2)]
+    d_outs = [out, torch.empty_like(out)]
+    sD = torch.cuda.Stream(dev)
     e2e_steps = max(3, min(K, 10))
-    for _ in range(2):
-        d_base.copy_(h_base, non_blocking=True)
-        table.partition(d_base, w.J, k0, n, out=states)
-        rm.generate_u24(states, desc, out)
-        h_out.copy_(out, non_blocking=True)
+    d2h = (h_outs, d_outs, sD)
+    pipeline(2 * K + 2, 2, d_bases, h_base, d2h)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        d_base.copy_(h_base, non_blocking=True)
-        table.partition(d_base, w.J, k0, n, out=states)
-        rm.generate_u24(states, desc, out)
-        h_out.copy_(out, non_blocking=True)
-    e1.record(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(sJ)
+    last = pipeline(2 * K + 4, e2e_steps, d_bases, h_base, d2h)
+    sJ.wait_event(last)
+    e1.record(sJ)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist, dev)
-    ok_e2e = bool(np.array_equal(h_out[:count].numpy(), out[:count].cpu().numpy()))
+    ok_e2e = bool(np.array_equal(h_outs[(e2e_steps - 1) % 2][:count].numpy(),
+                                 d_outs[(e2e_steps - 1) % 2][:count].cpu().numpy()))
+    del d_outs[1], h_outs
     # the paper's left-to-right square-and-multiply on the same streams
     sm_states = torch.empty_like(states)
-    rm.partition(base, w.J, k0, n, out=sm_states)
+    rm.partition(base, w.J, k0_of(0), n, out=sm_states)
     torch.cuda.synchronize()
-    same_states = bool(torch.equal(sm_states, table.partition(base, w.J, k0, n)))
+    same_states = bool(torch.equal(sm_states, table.partition(base, w.J, k0_of(0), n)))
     sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sm_ms = float("inf")
     for _ in range(3):
         sa.record(stream)
-        rm.partition(base, w.J, k0, n, out=sm_states)
+        rm.partition(base, w.J, k0_of(0), n, out=sm_states)
         sb.record(stream)
         torch.cuda.synchronize()
         sm_ms = min(sm_ms, sa.elapsed_time(sb))
     del sm_states
+    exps = [(k0_of(i) + q) * w.J for i in range(K) for q in range(0, n, 97)]
 
     if rank != 0:
         if dist:
@@ -333,8 +392,10 @@ def run_ours(args):
     jump_ms = statistics.mean(t_jump)
     gen_ms = statistics.mean(t_gen)
     gen_bytes = n * count * 4 + n * (400 + 400 + 24)
-    jmacs = table_macs(exps)
-    smacs = jump_macs(exps)
+    # algorithmic multiply-adds of one launch (the K serial batches, sampled every
+    # 97th stream and scaled to n streams per launch)
+    jmacs = table_macs(exps) * n / (len(exps) / K) / K
+    smacs = jump_macs([(k0_of(0) + q) * w.J for q in range(0, n, 97)]) * n / len(range(0, n, 97))
     jump_sha = source_sha("jump.cuh", "jump_table.cuh", "ranmar_device.cuh")
     gen_sha = source_sha("generate.cuh", "ranmar_device.cuh")
     tj = traffic_for("jump_table_kernel", jump_sha)
@@ -359,12 +420,15 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"partitioned: seed 12345, {n} streams at k*2^40 "
-                               f"(k = rank*{n} + 0..{n - 1}), 4096 u24 outputs each, "
-                               "write-back; step = jump + generate",
+        "config": {"workload": f"partitioned: seed 12345, {n} streams per step at k*2^40 "
+                               f"(step i of rank r: k = (i*N + r)*{n} + 0..{n - 1}), 4096 u24 "
+                               "outputs each, write-back; step = table jump + generate, "
+                               "jump of step i+1 overlapped with generation of step i",
                    "streams_per_gpu": n, "outputs_per_stream": count, "J": "2^40",
-                   "l2": "flushed (2x L2 buffer write) between timed steps; "
-                         "each step also writes 1.07 GB"},
+                   "l2": "inputs/outputs larger than L2: every step writes 1.07 GB (8x L2); "
+                         "the serial per-kernel timing flushes L2 (258 MB write) between steps"},
+        "serial_ms_per_step": serial_ms,
+        "serial_outputs_per_s": world * n * count / (serial_ms * 1e-3),
         "roofline": dominant, "roofline_generate": roof_gen, "roofline_jump": roof_jump,
         "jump_ms": jump_ms, "generate_ms": gen_ms,
         "jumps_per_s": n / (jump_ms * 1e-3),
@@ -379,7 +443,10 @@ def run_ours(args):
         "clocks": clk,
         "e2e": {"value": world * n * count / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 400, "d2h_bytes_per_step": n * count * 4,
-                "ms_per_step": ms_e2e, "checked": ok_e2e},
+                "ms_per_step": ms_e2e, "checked": ok_e2e,
+                "note": "binding calls with the base state from pinned host memory and the "
+                        "whole result copied to pinned host memory every step (copies on "
+                        "their own stream, double-buffered)"},
         "gpu_launches": 2 * K,
         "library": rbuild.LIB,
     }

@@ -221,6 +221,12 @@ typedef struct ranmar_table ranmar_table_t;
 int ranmar_table_create(ranmar_table_t **out);
 /* Frees the table (synchronizes its device).  NULL is a no-op. */
 int ranmar_table_destroy(ranmar_table_t *t);
+/* Caps the table-jump launches at ctas_per_sm resident CTAs per SM (the
+ * kernel then strides over the remaining streams), leaving SM resources to
+ * work running concurrently on another stream (e.g. generation of the
+ * previous batch).  0 (the default) launches one CTA per 16 streams.
+ * Errors: RANMAR_EINVAL (NULL, or outside 0..64). */
+int ranmar_table_set_ctas_per_sm(ranmar_table_t *t, int ctas_per_sm);
 /* Device address of the rows (row j*256 + d, 100 words each), for checks. */
 int ranmar_table_rows(const ranmar_table_t *t, const uint32_t **d_rows);
 

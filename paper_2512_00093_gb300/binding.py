@@ -82,6 +82,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_table_create.argtypes = [ctypes.POINTER(_vp)]
     lib.ranmar_table_destroy.argtypes = [_vp]
     lib.ranmar_table_rows.argtypes = [_vp, ctypes.POINTER(_vp)]
+    lib.ranmar_table_set_ctas_per_sm.argtypes = [_vp, ctypes.c_int]
+    lib.ranmar_table_set_ctas_per_sm.restype = ctypes.c_int
     lib.ranmar_jump_tab.argtypes = [_vp, _vp, _sz, _vp, _vp, _u32, _vp, _sz, _vp, _sz, _vp, _vp]
     lib.ranmar_partition_tab.argtypes = [_vp, _vp, _vp, _u32, _u64, _vp, _sz, _vp]
     lib.ranmar_partition_ex.argtypes = [_vp, _vp, _vp, _u32, _u64, _vp, _sz, _u32, _vp]
@@ -532,6 +534,10 @@ class Table:
             self.close()
         except Exception:
             pass
+
+    def set_ctas_per_sm(self, k: int) -> None:
+        """ranmar_table_set_ctas_per_sm (0 = full grid)."""
+        _check(_lib().ranmar_table_set_ctas_per_sm(self._h, int(k)), "ranmar_table_set_ctas_per_sm")
 
     def jump(self, base: torch.Tensor, exps: torch.Tensor, base_idx=None, out=None,
              dst_idx=None, status=None, stream=None, n: int | None = None) -> torch.Tensor:

@@ -83,10 +83,15 @@ __global__ void __launch_bounds__(32) jump_table_kernel(
   extern __shared__ __align__(16) uint32_t smem[];
   const unsigned lane = threadIdx.x & 31;
   const unsigned g = lane & 1, slot = lane >> 1;
-  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * kJumpStreamsPerWarp + slot;
   uint32_t* a = smem + slot * kTabStreamWords;
   uint32_t* b = a + kPolyWords;
   uint32_t* R = b + kPolyWords;
+  const uint64_t groups = (n + kJumpStreamsPerWarp - 1) / kJumpStreamsPerWarp;
+  // grid-stride over groups of 16 streams (the grid may be smaller than the
+  // work, e.g. to leave SM resources to a concurrent generation kernel)
+#pragma unroll 1
+  for (uint64_t grp = blockIdx.x; grp < groups; grp += gridDim.x) {
+  const uint64_t i = grp * kJumpStreamsPerWarp + slot;
 
   bool active = i < n;
   uint32_t E[kMaxExpWords];
@@ -134,6 +139,8 @@ __global__ void __launch_bounds__(32) jump_table_kernel(
     have = have || d != 0;
   }
   apply_pair(base, E, active, d_out + (active ? di : 0), a, R, g);
+  __syncwarp();
+  }
 }
 
 }  // namespace ranmar

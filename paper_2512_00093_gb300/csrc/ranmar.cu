@@ -32,7 +32,9 @@ struct ranmar_batch {
 // Fixed-base power table on one device.
 struct ranmar_table {
   int device;
-  uint32_t* rows;   // kTabRows x kTabRowWords
+  uint32_t* rows;     // kTabRows x kTabRowWords
+  int num_sms;
+  int ctas_per_sm;    // 0 = one CTA per group of 16 streams (full grid)
 };
 
 struct ranmar_graph {
@@ -662,6 +664,8 @@ int ranmar_table_create(ranmar_table_t** out) {
   ranmar_table* t = new (std::nothrow) ranmar_table{};
   if (!t) return RANMAR_ENOMEM;
   cudaError_t e = cudaGetDevice(&t->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, t->device);
   if (e == cudaSuccess) e = cudaMalloc(&t->rows, ranmar::kTabBytes);
   if (e != cudaSuccess) {
     delete t;
@@ -702,6 +706,12 @@ int ranmar_table_destroy(ranmar_table_t* t) {
   return e == cudaSuccess ? RANMAR_OK : cuda_fail(e);
 }
 
+int ranmar_table_set_ctas_per_sm(ranmar_table_t* t, int ctas_per_sm) {
+  if (!t || ctas_per_sm < 0 || ctas_per_sm > 64) return RANMAR_EINVAL;
+  t->ctas_per_sm = ctas_per_sm;
+  return RANMAR_OK;
+}
+
 int ranmar_table_rows(const ranmar_table_t* t, const uint32_t** d_rows) {
   if (!t || !d_rows) return RANMAR_EINVAL;
   *d_rows = t->rows;
@@ -715,8 +725,12 @@ static int launch_jump_table(const ranmar_table_t* t, const ranmar_state_t* base
                              const uint32_t* dst_idx, size_t n_dst) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != t->device) return RANMAR_EINVAL;
-  const uint64_t blocks = (n + ranmar::kJumpStreamsPerWarp - 1) / ranmar::kJumpStreamsPerWarp;
-  if (blocks > 0x7FFFFFFFull) return RANMAR_ERANGE;
+  uint64_t blocks = (n + ranmar::kJumpStreamsPerWarp - 1) / ranmar::kJumpStreamsPerWarp;
+  if (t->ctas_per_sm > 0) {
+    const uint64_t cap = static_cast<uint64_t>(t->ctas_per_sm) * t->num_sms;
+    if (blocks > cap) blocks = cap;   // the kernel strides over the rest
+  }
+  if (blocks > 0x7FFFFFFFull) blocks = 0x7FFFFFFFull;
   ranmar::jump_table_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kTabSmemBytes,
                               reinterpret_cast<cudaStream_t>(stream)>>>(
       t->rows, base, n_base, base_idx, exp, exp_words, part, mode, out, n, status, dst_idx,
