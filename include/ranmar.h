@@ -57,6 +57,7 @@ extern "C" {
 /* Bits OR-ed into *d_status by kernels. */
 #define RANMAR_ST_BAD_INDEX 1u    /* state or base index out of range       */
 #define RANMAR_ST_OUT_RANGE 2u    /* out_offset + count beyond out_len      */
+#define RANMAR_ST_BAD_SEED 4u     /* seed outside 1..900000000              */
 
 /* Descriptor flags. */
 #define RANMAR_DESC_WRITE_BACK 1u /* store the advanced state after output  */
@@ -100,6 +101,16 @@ typedef struct CUstream_st *ranmar_stream_t;   /* == cudaStream_t */
  * seed bound of Sec. 1; seed 0 would make seed - 1 negative).
  */
 int ranmar_seed(int32_t seed, ranmar_state_t *h_out);
+
+/*
+ * ranmar_seed_batch -- Algorithm 3 on the device for many seeds at once (one
+ * thread per seed): d_out[i] = the seeded state of d_seeds[i], identical to
+ * ranmar_seed.  Errors: RANMAR_EINVAL (NULL with n > 0, misaligned d_out).
+ * Device: RANMAR_ST_BAD_SEED for a seed outside 1..900000000 (that d_out[i]
+ * is left untouched).
+ */
+int ranmar_seed_batch(const int32_t *d_seeds, size_t n, ranmar_state_t *d_out,
+                      uint32_t *d_status, ranmar_stream_t stream);
 
 /*
  * ranmar_jump -- Sec. 3.1 and Sec. 3.2: d_out[i] = f^{E_i}(base), where base

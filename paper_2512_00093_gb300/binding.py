@@ -24,6 +24,7 @@ MAX_EXP_WORDS = 5
 DESC_WRITE_BACK = 1
 ST_BAD_INDEX = 1
 ST_OUT_RANGE = 2
+ST_BAD_SEED = 4
 
 OK, EINVAL, ERANGE, ECUDA, ENOMEM, EDEVICE = 0, -1, -2, -3, -4, -5
 
@@ -77,6 +78,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     for name in ("ranmar_generate_alg1_f32", "ranmar_generate_alg1_f64"):
         getattr(lib, name).argtypes = [_vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp]
         getattr(lib, name).restype = ctypes.c_int
+    lib.ranmar_seed_batch.argtypes = [_vp, _sz, _vp, _vp, _vp]
+    lib.ranmar_seed_batch.restype = ctypes.c_int
     lib.ranmar_jump_scatter.argtypes = [_vp, _sz, _vp, _vp, _u32, _vp, _sz, _vp, _sz, _vp, _vp]
     lib.ranmar_checksum.argtypes = [_vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp]
     lib.ranmar_table_create.argtypes = [ctypes.POINTER(_vp)]
@@ -171,6 +174,22 @@ def seed(seed: int) -> torch.Tensor:
     buf = np.zeros(STATE_WORDS, np.uint32)
     _check(_lib().ranmar_seed(int(seed), buf.ctypes.data), "ranmar_seed")
     return torch.from_numpy(buf.view(np.int32).copy())
+
+
+def seed_batch(seeds: torch.Tensor, out: torch.Tensor | None = None,
+               status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """ranmar_seed_batch: Algorithm 3 on the device; seeds is (n,) int32 CUDA."""
+    _need(seeds, torch.int32, "seeds")
+    n = seeds.numel()
+    if out is None:
+        out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=seeds.device)
+    out2 = out.reshape(-1, STATE_WORDS)
+    _need(out2, torch.int32, "out")
+    if status is not None:
+        _need(status, torch.int32, "status")
+    _check(_lib().ranmar_seed_batch(_ptr(seeds), n, _ptr(out2), _ptr(status), _stream(stream)),
+           "ranmar_seed_batch")
+    return out
 
 
 def jump(base: torch.Tensor, exps: torch.Tensor, base_idx: torch.Tensor | None = None,

@@ -95,6 +95,41 @@ struct SeedBits {
   }
 };
 
+// Algorithm 3 (Appendix A) on the device: one thread per seed, the same two
+// sub-generators as the host SeedBits, 97 x 24 bit draws, then the LAMMPS
+// ring order (x_1..x_97 = u_97, ..., u_1), c = 362436, pos = 0.
+__global__ void __launch_bounds__(128) seed_kernel(const int32_t* __restrict__ seeds, uint64_t n,
+                                                   ranmar_state_t* __restrict__ out,
+                                                   uint32_t* status) {
+  const uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int32_t seed = seeds[t];
+  if (seed < 1 || seed > 900000000) {
+    ranmar::flag_status(status, RANMAR_ST_BAD_SEED);
+    return;
+  }
+  const int32_t ij = (seed - 1) / 30082;
+  const int32_t kl = (seed - 1) - 30082 * ij;
+  int32_t i = (ij / 177) % 177 + 2, j = ij % 177 + 2, k = (kl / 169) % 178 + 1, l = kl % 169;
+  uint32_t* x = out[t].x;
+#pragma unroll 1
+  for (int w = 0; w < ranmar::kR; ++w) {
+    uint32_t v = 0;
+#pragma unroll 4
+    for (int b = 23; b >= 0; --b) {
+      const int32_t m = (((i * j) % 179) * k) % 179;
+      i = j;
+      j = k;
+      k = m;
+      l = (53 * l + 1) % 169;
+      if ((l * m) % 64 >= 32) v |= 1u << b;
+    }
+    x[ranmar::kR - 1 - w] = v;  // u_{w+1} is x_{97-w}
+  }
+  out[t].c = ranmar::kC0;
+  out[t].pos = 0;
+}
+
 // Weighted checksum of 32-bit words: result[item.result] +=
 // sum_i word[offset + i] * (2 (index0 + i) + 1) mod 2^64, one CTA per item.
 __global__ void __launch_bounds__(256) checksum_kernel(const uint32_t* __restrict__ data,
@@ -822,6 +857,18 @@ int ranmar_partition_ex(const ranmar_table_t* t, const ranmar_state_t* d_base, c
     return launch_jump_table(t, d_base, 1, nullptr, nullptr, 0, part, 1, d_out, n, nullptr,
                              stream, nullptr, n);
   return launch_jump(d_base, 1, nullptr, nullptr, 0, part, 1, d_out, n, nullptr, stream);
+}
+
+int ranmar_seed_batch(const int32_t* d_seeds, size_t n, ranmar_state_t* d_out, uint32_t* d_status,
+                      ranmar_stream_t stream) {
+  if (n == 0) return RANMAR_OK;
+  if (!d_seeds || !d_out) return RANMAR_EINVAL;
+  if (!aligned(d_seeds, 4) || !aligned(d_out, 16)) return RANMAR_EINVAL;
+  const uint64_t blocks = (n + 127) / 128;
+  if (blocks > 0x7FFFFFFFull) return RANMAR_ERANGE;
+  seed_kernel<<<static_cast<unsigned>(blocks), 128, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      d_seeds, n, d_out, d_status);
+  return check_launch();
 }
 
 }  // extern "C"

@@ -29,6 +29,7 @@ from __future__ import annotations
 import bisect
 import collections
 import dataclasses
+import gc
 import time
 
 import numpy as np
@@ -88,6 +89,21 @@ def exp_rows(base: int, ns: int, seg: int) -> np.ndarray:
             for w in range(2, bd.MAX_EXP_WORDS):
                 out[rows, w] = (h >> (32 * (w - 2))) & 0xFFFFFFFF
     return out
+
+
+def add_rows(out: np.ndarray, base: np.ndarray, add: np.ndarray) -> None:
+    """out[i] = base[i] + add[i] as 5-word little-endian integers (add < 2^64)."""
+    lo = base[:, 0].astype(np.uint64) | (base[:, 1].astype(np.uint64) << np.uint64(32))
+    with np.errstate(over="ignore"):
+        s = lo + add
+    carry = (s < lo).astype(np.uint64)
+    out[:, 0] = (s & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    out[:, 1] = (s >> np.uint64(32)).astype(np.uint32)
+    c = carry
+    for w in range(2, base.shape[1]):
+        v = base[:, w].astype(np.uint64) + c
+        out[:, w] = (v & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+        c = v >> np.uint64(32)
 
 
 class FirstFit:
@@ -152,6 +168,7 @@ class _Staging:
         self.desc_u = mk((cap, 3), torch.int64)
         self.desc_f = mk((cap, 3), torch.int64)
         self.items = mk((cap, 4), torch.int64)
+        self.seeds = mk((cap,), torch.int32)
 
     def ensure(self, n):
         if n > self.cap:
@@ -192,7 +209,8 @@ class Engine:
         # one staging set per possible in-flight iteration: pinned buffers are
         # read by asynchronous copies, so a set is reused only after the event
         # of the iteration that last used it has completed
-        self.stages = [_Staging(self.dev, 4096) for _ in range(max_inflight + 1)]
+        cap = max(4096, max_segments_per_iter)   # never grown (pinned allocation) mid-run
+        self.stages = [_Staging(self.dev, cap) for _ in range(max_inflight + 1)]
         self.stage_ev = [None] * (max_inflight + 1)
         self.stream = torch.cuda.current_stream(self.dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.dev)
@@ -244,12 +262,28 @@ class Engine:
         return out
 
     # --- one iteration -------------------------------------------------------
-    def _seed_rows(self, reqs):
-        new = [r.seed for r in reqs if r.seed not in self.seed_row]
-        for sd in dict.fromkeys(new):
-            row = len(self.seed_row)
-            self.seed_row[sd] = row
-            self.base[row].copy_(bd.seed(sd), non_blocking=False)
+    def _seed_rows(self, reqs, st=None):
+        """Rows of the base-state table for the seeds of `reqs`; new seeds are
+        seeded on the device (Algorithm 3, one launch for all of them)."""
+        new = list(dict.fromkeys(r.seed for r in reqs if r.seed not in self.seed_row))
+        if not new:
+            return
+        r0 = len(self.seed_row)
+        for i, sd in enumerate(new):
+            self.seed_row[sd] = r0 + i
+        m = len(new)
+        if st is None:
+            sd_dev = torch.tensor(new, dtype=torch.int32, device=self.dev)
+        else:
+            st.seeds[0][:m] = torch.tensor(new, dtype=torch.int32)
+            st.seeds[1][:m].copy_(st.seeds[0][:m], non_blocking=True)
+            sd_dev = st.seeds[1][:m]
+        bd.seed_batch(sd_dev, out=self.base[r0:r0 + m], status=self.status, stream=self.stream)
+
+    def preload_seeds(self, seeds) -> None:
+        """Seed a known range of seeds up front (engine set-up)."""
+        self._seed_rows([Request(0, 0.0, int(sd), 0, 1, 1, False) for sd in seeds])
+        torch.cuda.synchronize(self.dev)
 
     def _slots(self, n: int) -> int:
         """n consecutive result slots (never wrapping inside one iteration)."""
@@ -261,57 +295,76 @@ class Engine:
         return lo
 
     def enqueue(self, reqs: list, t0_event) -> dict:
-        self._seed_rows(reqs)
-        nseg_tot = sum(self._nseg(r) for r in reqs)
+        nreq = len(reqs)
+        seg = self.seg
+        counts = np.fromiter((r.count for r in reqs), dtype=np.int64, count=nreq)
+        nseg = np.maximum(1, (counts + seg - 1) // seg)
+        ntot = int(nseg.sum())
         si = self.stats["iterations"] % len(self.stages)
         if self.stage_ev[si] is not None:
             self.stage_ev[si].synchronize()
         st = self.stages[si]
-        st.ensure(nseg_tot)
-        ex_h, bi_h, di_h = st.exps[0].numpy(), st.base_idx[0].numpy(), st.dst_idx[0].numpy()
-        pex_h, pbi_h, pdi_h = st.pexps[0].numpy(), st.pbase_idx[0].numpy(), st.pdst_idx[0].numpy()
-        du_h, df_h, it_h = st.desc_u[0].numpy(), st.desc_f[0].numpy(), st.items[0].numpy()
-        nj = npj = nu = nf = ni = 0
-        seg = self.seg
-        lo_s = self._slots(len(reqs))
+        st.ensure(max(ntot, nreq))
+        self._seed_rows(reqs, st)
+        lo_s = self._slots(nreq)
         for q, r in enumerate(reqs):
-            ns = self._nseg(r)
             r._slot = lo_s + q
-            region, ents = r._region[0], r._ents
-            j = np.arange(ns, dtype=np.int64)
-            cnt = np.maximum(0, np.minimum(seg, r.count - j * seg))
-            offs = region + j * seg
-            if r._resume:       # segment 0 is the resident state; the others jump from it
-                if ns > 1:
-                    pex_h[npj:npj + ns - 1] = exp_rows(0, ns, seg)[1:].view(np.int32)
-                    pbi_h[npj:npj + ns - 1] = ents[0]
-                    pdi_h[npj:npj + ns - 1] = ents[1:]
-                    npj += ns - 1
-            else:               # every segment jumps from the seed's base state
-                ex_h[nj:nj + ns] = exp_rows(r.k * r.J + r.offset, ns, seg).view(np.int32)
-                bi_h[nj:nj + ns] = self.seed_row[r.seed]
-                di_h[nj:nj + ns] = ents
-                nj += ns
-            # descriptors: only the last segment writes its state back
-            flags = np.zeros(ns, dtype=np.int64)
-            flags[-1] = bd.DESC_WRITE_BACK
-            tgt, n0 = (df_h, nf) if r.f32 else (du_h, nu)
-            tgt[n0:n0 + ns, 0] = np.asarray(ents, dtype=np.int64) | (flags << 32)
-            tgt[n0:n0 + ns, 1] = offs
-            tgt[n0:n0 + ns, 2] = cnt
-            if r.f32:
-                nf += ns
-            else:
-                nu += ns
-            it_h[ni:ni + ns, 0] = offs
-            it_h[ni:ni + ns, 1] = cnt
-            it_h[ni:ni + ns, 2] = j * seg
-            it_h[ni:ni + ns, 3] = r._slot
-            ni += ns
+        # per-segment arrays
+        sreq = np.repeat(np.arange(nreq), nseg)
+        starts = np.cumsum(nseg) - nseg
+        j = np.arange(ntot, dtype=np.int64) - np.repeat(starts, nseg)
+        cnt = np.maximum(0, np.minimum(seg, counts[sreq] - j * seg))
+        region = np.fromiter((r._region[0] for r in reqs), dtype=np.int64, count=nreq)
+        offs = region[sreq] + j * seg
+        ents = np.fromiter((e for r in reqs for e in r._ents), dtype=np.int64, count=ntot)
+        last = j == nseg[sreq] - 1
+        f32 = np.fromiter((r.f32 for r in reqs), dtype=bool, count=nreq)[sreq]
+        resume = np.fromiter((r._resume for r in reqs), dtype=bool, count=nreq)[sreq]
+        # jumps from the seed's base state: E = k J + offset + j seg
+        sj = ~resume
+        nj = int(sj.sum())
+        if nj:
+            rq = sreq[sj]
+            basew = np.zeros((nreq, bd.MAX_EXP_WORDS), dtype=np.uint32)
+            for q, r in enumerate(reqs):
+                if not r._resume:
+                    e = r.k * r.J + r.offset
+                    basew[q] = [(e >> (32 * w)) & 0xFFFFFFFF for w in range(bd.MAX_EXP_WORDS)]
+            add_rows(st.exps[0].numpy()[:nj].view(np.uint32), basew[rq],
+                     (j[sj] * seg).astype(np.uint64))
+            st.base_idx[0].numpy()[:nj] = np.fromiter((self.seed_row[reqs[q].seed] for q in rq),
+                                                      dtype=np.int32, count=nj)
+            st.dst_idx[0].numpy()[:nj] = ents[sj]
+        # jumps from a resumed resident state by j seg (segments j >= 1)
+        pj = resume & (j > 0)
+        npj = int(pj.sum())
+        if npj:
+            e = (j[pj] * seg).astype(np.uint64)
+            pe = st.pexps[0].numpy()[:npj].view(np.uint32)
+            pe[:] = 0
+            pe[:, 0] = (e & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+            pe[:, 1] = (e >> np.uint64(32)).astype(np.uint32)
+            first_ent = ents[starts]                      # segment 0 of each request
+            st.pbase_idx[0].numpy()[:npj] = first_ent[sreq[pj]]
+            st.pdst_idx[0].numpy()[:npj] = ents[pj]
+        # generation descriptors (write back only the last segment's state)
+        flags = last.astype(np.int64) * bd.DESC_WRITE_BACK
+        d_all = np.stack([ents | (flags << 32), offs, cnt], axis=1)
+        nu = int((~f32).sum())
+        nf = ntot - nu
+        if nu:
+            st.desc_u[0].numpy()[:nu] = d_all[~f32]
+        if nf:
+            st.desc_f[0].numpy()[:nf] = d_all[f32]
+        it = st.items[0].numpy()
+        it[:ntot, 0] = offs
+        it[:ntot, 1] = cnt
+        it[:ntot, 2] = j * seg
+        it[:ntot, 3] = lo_s + sreq
         s = self.stream
         for pair, n in ((st.exps, nj), (st.base_idx, nj), (st.dst_idx, nj), (st.pexps, npj),
                         (st.pbase_idx, npj), (st.pdst_idx, npj), (st.desc_u, nu),
-                        (st.desc_f, nf), (st.items, ni)):
+                        (st.desc_f, nf), (st.items, ntot)):
             if n:
                 pair[1][:n].copy_(pair[0][:n], non_blocking=True)
         if nj:
@@ -324,15 +377,16 @@ class Engine:
         if nf:
             self.batch.generate_f32(self.pool, st.desc_f[1][:nf], self.outf, status=self.status,
                                     stream=s)
-        hi_s = lo_s + len(reqs)
+        hi_s = lo_s + nreq
         self.results[lo_s:hi_s].zero_()
-        bd.checksum(self.out, st.items[1][:ni], self.results, status=self.status, stream=s, n=ni)
+        bd.checksum(self.out, st.items[1][:ntot], self.results, status=self.status, stream=s,
+                    n=ntot)
         self.results_host[lo_s:hi_s].copy_(self.results[lo_s:hi_s], non_blocking=True)
         ev = torch.cuda.Event(enable_timing=True)
         ev.record(s)
         self.stage_ev[si] = ev
         self.stats["iterations"] += 1
-        self.stats["segments"] += nseg_tot
+        self.stats["segments"] += ntot
         self.stats["jumps"] += nj + npj
         return {"event": ev, "reqs": reqs, "t0": t0_event, "slots": (lo_s, hi_s)}
 
@@ -373,6 +427,17 @@ class Engine:
         available at once."""
         waiting: collections.deque = collections.deque()
         inflight: collections.deque = collections.deque()
+        i = 0
+        # no collector pauses inside the latency-measured loop
+        gc_was = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(reqs, realtime, max_wait, waiting, inflight)
+        finally:
+            if gc_was:
+                gc.enable()
+
+    def _run(self, reqs, realtime, max_wait, waiting, inflight) -> dict:
         i = 0
         torch.cuda.synchronize(self.dev)
         t0 = torch.cuda.Event(enable_timing=True)

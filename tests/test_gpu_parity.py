@@ -261,3 +261,22 @@ def test_large_jumps_sampled(rm, dev, orc):
         assert np.array_equal(st[r, :97], xr) and st[r, 97] == cr, int(r)
         ref, _, _ = orc.generate(xr, cr, w.count)
         assert np.array_equal(got[r], ref), int(r)
+
+
+def test_device_seeding_matches_oracle(rm, dev, orc):
+    rng = np.random.default_rng(17)
+    seeds = np.concatenate([[1, 2, 12345, 54217138, 900000000, 30082, 30083],
+                            rng.integers(1, 900000001, 300)]).astype(np.int32)
+    out = rm.seed_batch(torch.as_tensor(seeds, device=dev))
+    torch.cuda.synchronize()
+    got = st_np(out)
+    for i, sd in enumerate(seeds):
+        x, c = orc.seeded_state(int(sd))
+        assert np.array_equal(got[i, :97], x) and got[i, 97] == c and pos_of(got[i]) == 0, sd
+    bad = torch.tensor([5, 0, -3, 900000001, 7], dtype=torch.int32, device=dev)
+    o2 = torch.full((5, 100), -9, dtype=torch.int32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rm.seed_batch(bad, out=o2, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) & rm.ST_BAD_SEED
+    assert (o2[1:4] == -9).all() and not (o2[0] == -9).all() and not (o2[4] == -9).all()
