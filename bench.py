@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--serve-seconds", type=float, default=5.0,
                    help="duration of the serving run (the recipe's full run is 60 s)")
+    p.add_argument("--case", choices=["partitioned", "uneven", "large"], default="partitioned",
+                   help="partitioned = the benchmark; uneven / large run only that workload's "
+                        "step (for profiling) and print a line for it")
     p.add_argument("--streams", type=int, default=65536,
                    help="streams per GPU (65536 is the benchmark; smaller for profiling)")
     return p.parse_args()
@@ -705,10 +708,59 @@ def serving(rm, torch, seconds):
     return res
 
 
+def run_case(args):
+    """One workload's step only (jump + generate), for profiling: uneven =
+    persistent batch kernel on log-uniform lengths, large = J = 2^120 + 12345
+    (square-and-multiply and table jumps, 1,024 outputs each)."""
+    import torch
+    import paper_2512_00093_gb300 as rm
+    from paper_2512_00093_gb300.workloads import BatchedUneven, LargeJumps
+    dev = torch.device("cuda", 0)
+    n = args.streams
+    table = rm.Table()
+    if args.case == "uneven":
+        w = BatchedUneven()
+        lens = w.lengths(n)
+        base = rm.seed(w.seed).to(dev)
+        b = rm.Batch(n)
+        counts = torch.as_tensor(lens, device=dev)
+        states = torch.empty((n, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+        out = torch.empty(int(lens.sum()), dtype=torch.float32, device=dev)
+
+        def step():
+            table.partition(base, w.J, 0, n, out=states)
+            desc, order, _ = b.pack(counts)
+            b.generate_f32(states, desc, out, order=order)
+    else:
+        w = LargeJumps()
+        base = rm.seed(w.seed).to(dev)
+        states = torch.empty((n, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+        out = torch.empty(n * w.count, dtype=torch.int32, device=dev)
+        desc = rm.make_desc(np.arange(n), np.arange(n) * w.count, w.count, 0, device=dev)
+
+        def step():
+            rm.partition(base, w.J, 0, n, out=states)
+            table.partition(base, w.J, 0, n, out=states)
+            rm.generate_u24(states, desc, out)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        step()
+    e.record()
+    torch.cuda.synchronize()
+    emit({"case": args.case, "streams": n, "ms_per_step": a.elapsed_time(e) / args.steps})
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case != "partitioned":
+        return run_case(args)
     return run_ours(args)
 
 
