@@ -87,16 +87,30 @@ __device__ __forceinline__ void tile_mac(uint32_t (&acc)[11], const Quad& r, con
 }
 
 // Reduced coefficients n = 8b + 4g + k (k < 4, n <= 96) of a completed
-// product block, written to a[n + shift].
-__device__ __forceinline__ void reduce_block(uint32_t* __restrict__ a,
-                                             const uint32_t* __restrict__ R, int b, unsigned g,
-                                             const uint32_t (&cv)[4], uint32_t shift) {
+// product block, written to a[n + shift].  Blocks 0-2, 4-6 and 8-10 have one
+// fixed set of terms for all their coefficients; the four blocks that
+// straddle a range boundary (3, 7, 11, 12) test each coefficient.
+enum ReduceTerms { kLow3 = 0, kLow2 = 1, kHigh4 = 2, kGeneric = 3 };
+
+template <int kTerms>
+__device__ __forceinline__ void reduce_block_t(uint32_t* __restrict__ a,
+                                               const uint32_t* __restrict__ R, int b,
+                                               unsigned g, const uint32_t (&cv)[4],
+                                               uint32_t shift) {
   const uint32_t* h = R + 1;  // h_j = c_{97+j}
+  const int n0 = 8 * b + 4 * static_cast<int>(g);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const int n = 8 * b + 4 * static_cast<int>(g) + k;
-    if (n <= 96) {
-      uint32_t v = cv[k];
+    const int n = n0 + k;
+    uint32_t v = cv[k];
+    if (kTerms == kLow3) {          // n <= 23
+      v += h[n] - h[n + 33] + h[n + 66];
+    } else if (kTerms == kLow2) {   // 32 <= n <= 55
+      v += h[n] - h[n + 33];
+    } else if (kTerms == kHigh4) {  // 64 <= n <= 87
+      v += h[n] - h[n - 64] + h[n - 31] - h[n + 2];
+    } else {
+      if (n > 96) continue;
       if (n <= 95) v += h[n];
       if (n <= 62) v -= h[n + 33];
       if (n <= 29) v += h[n + 66];
@@ -104,9 +118,22 @@ __device__ __forceinline__ void reduce_block(uint32_t* __restrict__ a,
         v += h[n - 31] - h[n - 64];
         if (n <= 93) v -= h[n + 2];
       }
-      a[n + shift] = v;
     }
+    a[n + shift] = v;
   }
+}
+
+__device__ __forceinline__ void reduce_block(uint32_t* __restrict__ a,
+                                             const uint32_t* __restrict__ R, int b, unsigned g,
+                                             const uint32_t (&cv)[4], uint32_t shift) {
+  if (b <= 2)
+    reduce_block_t<kLow3>(a, R, b, g, cv, shift);
+  else if (b >= 4 && b <= 6)
+    reduce_block_t<kLow2>(a, R, b, g, cv, shift);
+  else if (b >= 8 && b <= 10)
+    reduce_block_t<kHigh4>(a, R, b, g, cv, shift);
+  else
+    reduce_block_t<kGeneric>(a, R, b, g, cv, shift);
 }
 
 // In place, with the lanes g = 0, 1 of the pair cooperating:
@@ -286,7 +313,10 @@ __device__ __forceinline__ void poly_power_pair(const uint32_t (&E)[kMaxExpWords
     p = L - 7;
   }
   if (!active) v0 = 0;
-  for (int n = static_cast<int>(g); n < kPolyWords; n += 2) a[n] = (n == static_cast<int>(v0));
+  for (int q = static_cast<int>(g); q < kPolyWords / 4; q += 2)
+    reinterpret_cast<uint4*>(a)[q] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
+  if (g == 0) a[v0] = 1u;
   __syncwarp();
 
 #pragma unroll 1
@@ -322,27 +352,22 @@ __device__ __forceinline__ void apply_pair(const ranmar_state_t* __restrict__ ba
       uint32_t acc[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) acc[r] = 0;
-      Oct b = lds8(a);
-      Oct w0 = lds8(ring + ((8 * K) & (kRingWords - 1)));
-      Oct w1 = lds8(ring + ((8 * K + 8) & (kRingWords - 1)));
-#pragma unroll 1
+      // 13 tiles, fully unrolled so that the sliding window (blocks I+K and
+      // I+K+1 of X) and the coefficient blocks are renamed, not moved.
+      Oct w[14];
+      w[0] = lds8(ring + ((8 * K) & (kRingWords - 1)));
+#pragma unroll
       for (int I = 0; I < 13; ++I) {
-        Oct bn = b, n1 = w1;
-        if (I + 1 < 13) {
-          bn = lds8(a + 8 * (I + 1));
-          n1 = lds8(ring + ((8 * (I + 1 + K) + 8) & (kRingWords - 1)));
-        }
+        const Oct b = lds8(a + 8 * I);
+        w[I + 1] = lds8(ring + ((8 * (I + 1 + K)) & (kRingWords - 1)));
 #pragma unroll
         for (int p2 = 0; p2 < 8; ++p2) {
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const int idx = p2 + r;
-            acc[r] += b.v[p2] * (idx < 8 ? w0.v[idx & 7] : w1.v[idx & 7]);
+            acc[r] += b.v[p2] * (idx < 8 ? w[I].v[idx & 7] : w[I + 1].v[idx & 7]);
           }
         }
-        b = bn;
-        w0 = w1;
-        w1 = n1;
       }
       if (active) {
         if (K < 12) {

@@ -121,11 +121,16 @@ __global__ void __launch_bounds__(32) jump_table_kernel(
   if (part.flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
 
   // a = 1 (t^0), b zero padded
-  for (int q = static_cast<int>(g); q < 2 * kPolyWords; q += 2) a[q] = (q == 0);
+  for (int q = static_cast<int>(g); q < 2 * kPolyWords / 4; q += 2)
+    reinterpret_cast<uint4*>(a)[q] = make_uint4(q == 0 ? 1u : 0u, 0u, 0u, 0u);
   __syncwarp();
+  // digit positions up to the highest nonzero digit of the warp's exponents
+  const int nbits = active ? exp_bitlen(Ep) : 0;
+  const int nwin = (static_cast<int>(__reduce_max_sync(kFull, static_cast<unsigned>(nbits))) +
+                    kTabWindowBits - 1) / kTabWindowBits;
   bool have = false;
 #pragma unroll 1
-  for (int j = 0; j < kTabWindows; ++j) {
+  for (int j = 0; j < nwin; ++j) {
     const uint32_t d = active ? exp_digit(Ep, j) : 0u;
     const bool first = d != 0 && !have;
     const bool mul = d != 0 && have;
