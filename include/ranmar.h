@@ -429,6 +429,16 @@ int ranmar_checksum(const uint32_t *d_data, size_t data_len,
                     uint64_t *d_results, size_t n_results,
                     uint32_t *d_status, ranmar_stream_t stream);
 
+/*
+ * ranmar_host_device_pointer -- the device address of pinned (page-locked)
+ * host memory, for generating straight into host memory: the kernels then
+ * store over the CPU-GPU link instead of a separate device-to-host copy.
+ * The memory must stay pinned while kernels use it.  Errors: RANMAR_EINVAL
+ * (NULL, or memory that is not pinned: RANMAR_ECUDA), RANMAR_EDEVICE (the
+ * device cannot map host memory).
+ */
+int ranmar_host_device_pointer(void *h_ptr, void **d_ptr);
+
 /* Name of a return code (static string, never NULL). */
 const char *ranmar_strerror(int code);
 

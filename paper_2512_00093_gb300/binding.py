@@ -78,6 +78,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     for name in ("ranmar_generate_alg1_f32", "ranmar_generate_alg1_f64"):
         getattr(lib, name).argtypes = [_vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp]
         getattr(lib, name).restype = ctypes.c_int
+    lib.ranmar_host_device_pointer.argtypes = [_vp, ctypes.POINTER(_vp)]
+    lib.ranmar_host_device_pointer.restype = ctypes.c_int
     lib.ranmar_seed_batch.argtypes = [_vp, _sz, _vp, _vp, _vp]
     lib.ranmar_seed_batch.restype = ctypes.c_int
     lib.ranmar_jump_scatter.argtypes = [_vp, _sz, _vp, _vp, _u32, _vp, _sz, _vp, _sz, _vp, _vp]
@@ -296,15 +298,37 @@ def make_desc(state_idx, out_offset, count, flags=DESC_WRITE_BACK, device="cuda"
     return torch.from_numpy(d.view(np.int64)).to(device)
 
 
+def host_device_pointer(t: torch.Tensor) -> int:
+    """ranmar_host_device_pointer: device address of a pinned CPU tensor."""
+    if t.is_cuda or not t.is_pinned():
+        raise ValueError("needs a pinned CPU tensor")
+    p = ctypes.c_void_p()
+    _check(_lib().ranmar_host_device_pointer(t.data_ptr(), ctypes.byref(p)),
+           "ranmar_host_device_pointer")
+    return int(p.value)
+
+
+def _out_ptr(out: torch.Tensor, dtype, name: str) -> int:
+    """Device address of an output tensor: CUDA memory, or pinned host memory
+    (written over the CPU-GPU link)."""
+    if out.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {out.dtype}")
+    if not out.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if out.is_cuda:
+        return out.data_ptr()
+    return host_device_pointer(out)
+
+
 def _generate(fn: str, out_dtype, states, desc, out, status, stream):
     states = states.reshape(-1, STATE_WORDS)
     _need(states, torch.int32, "states")
     _need(desc, torch.int64, "desc")
-    _need(out, out_dtype, "out")
+    optr = _out_ptr(out, out_dtype, "out")
     if status is not None:
         _need(status, torch.int32, "status")
     _check(getattr(_lib(), fn)(_ptr(states), states.shape[0], _ptr(desc), desc.shape[0],
-                               _ptr(out), out.numel(), _ptr(status), _stream(stream)), fn)
+                               optr, out.numel(), _ptr(status), _stream(stream)), fn)
     return out
 
 

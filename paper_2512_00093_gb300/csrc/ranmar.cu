@@ -871,4 +871,20 @@ int ranmar_seed_batch(const int32_t* d_seeds, size_t n, ranmar_state_t* d_out, u
   return check_launch();
 }
 
+int ranmar_host_device_pointer(void* h_ptr, void** d_ptr) {
+  if (!h_ptr || !d_ptr) return RANMAR_EINVAL;
+  *d_ptr = nullptr;
+  int dev = -1, mapped = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mapped, cudaDevAttrCanMapHostMemory, dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (!mapped) return RANMAR_EDEVICE;
+  e = cudaHostGetDevicePointer(d_ptr, h_ptr, 0);
+  if (e != cudaSuccess) {
+    *d_ptr = nullptr;
+    return cuda_fail(e);
+  }
+  return RANMAR_OK;
+}
+
 }  // extern "C"

@@ -280,3 +280,19 @@ def test_device_seeding_matches_oracle(rm, dev, orc):
     torch.cuda.synchronize()
     assert int(status.item()) & rm.ST_BAD_SEED
     assert (o2[1:4] == -9).all() and not (o2[0] == -9).all() and not (o2[4] == -9).all()
+
+
+def test_generate_into_pinned_host_memory(rm, dev, orc):
+    """Outputs stored straight into pinned host memory over the CPU-GPU link
+    (ranmar_host_device_pointer) equal the device-memory outputs."""
+    states = rm.partition(seeded(rm, 12345, dev), 1 << 40, 7, 64)
+    count = 1000 + 7
+    desc = rm.make_desc(np.arange(64), np.arange(64) * count, count, 0, device=dev)
+    h = torch.full((64 * count,), -1, dtype=torch.int32).pin_memory()
+    d = torch.empty(64 * count, dtype=torch.int32, device=dev)
+    rm.generate_u24(states, desc, h)
+    rm.generate_u24(states, desc, d)
+    torch.cuda.synchronize()
+    assert torch.equal(h, d.cpu())
+    ref = orc.stream(12345, 9 * (1 << 40), count)
+    assert np.array_equal(h[2 * count:3 * count].numpy().view(np.uint32), ref)
