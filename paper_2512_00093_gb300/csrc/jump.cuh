@@ -6,22 +6,27 @@
 // sum_i b_i x_{i+k+1} (x extended by the recurrence), which is the Horner
 // form u P_E(A) of Sec. 3.1; then c_E = (c - E d) mod m (Sec. 3.2).
 //
-// Mapping: TWO lanes per stream, 16 streams per warp, one warp per CTA.  Every
-// pair runs the same instruction stream on its own polynomial, so the 97x97
-// products are register-blocked 8x8 tiles of 32-bit multiply-adds (mul.lo
-// wraps mod 2^32, exact mod 2^24; masks only at the end).  Within a tile the
-// pair splits the rows: lane g takes rows 4g..4g+3 against all 8 columns
-// (32 multiply-adds into 11 accumulators).
+// Mapping: TWO lanes per stream (lanes L and L + 16 of the warp), 16 streams
+// per warp, one warp per CTA.  Every pair runs the same instruction stream on
+// its own polynomial.  A polynomial is held as six 16-coefficient blocks
+// (coefficients 0..95) plus coefficient 96 alone:
+//     a = a' + a_96 t^96,  a b = a'b' + t^96 (a_96 b' + b_96 a') + a_96 b_96 t^192,
+// so the 97x97 product is 6x6 register-blocked 16x16 tiles of 32-bit
+// multiply-adds (mul.lo wraps mod 2^32, exact mod 2^24; masks only at the
+// end) plus a rank-1 correction of the coefficients 96..192.  Within a tile
+// the pair splits the rows: lane g takes rows 8g..8g+7 against all 16
+// columns (128 multiply-adds into 23 accumulators).
 //
-// Squaring a(t)^2, in place: tiles (I, J), I <= J, of 8-coefficient blocks
-// are summed along the anti-diagonal s = I + J (outputs 8s .. 8s+14), walking
-// s DOWN from 24 to 0.  Off-diagonal tiles are summed and doubled; the
-// diagonal tile (I = J) is then added as a full 8x8 product (its off-diagonal
-// pairs twice, its squares once).  After anti-diagonal s the product block
-// s+1 (coefficients 8s+8 .. 8s+15) is complete, and block s+1 of `a` is no
-// longer read (anti-diagonals <= s use blocks <= s), so:
-//   * blocks >= 12 (degree >= 96) go to a 128-word region R (R[k-96] = c_k);
-//   * blocks <= 12 are reduced at once and written into `a` itself:
+// In place, anti-diagonal by anti-diagonal: tiles (I, J) with I + J = s
+// produce the outputs 16s .. 16s+30; s walks DOWN from 10 to 0 (squaring:
+// tiles I < J summed and doubled, then the diagonal tile I = J added as a
+// full product).  After anti-diagonal s the product block s+1 (coefficients
+// 16s+16 .. 16s+31) is complete, and block s+1 of `a` is no longer read
+// (anti-diagonals <= s use blocks <= s), so:
+//   * blocks >= 6 (degree >= 96) get the rank-1 correction and go to a
+//     128-word region R (R[k-96] = c_k; R[96] = c_192 = a_96 b_96);
+//   * blocks <= 5 and coefficient 96 are reduced at once and written into
+//     `a` itself:
 //       a_n = c_n + h_n[n<=95] - h_{n+33}[n<=62] + h_{n+66}[n<=29]
 //             - h_{n-64}[n>=64] + h_{n-31}[n>=64] - h_{n+2}[64<=n<=93]
 //     with h_j = c_{97+j} (t^k = t^{k-97} - t^{k-33} applied until the
@@ -29,29 +34,30 @@
 //     one, because s walks down).
 // A multiplication by t shifts the written index by one; the word that lands
 // on t^97 is folded back at the end.  After each anti-diagonal the pair
-// swaps 4 partial sums by shuffle.
+// swaps 8 partial sums by shuffle.
 //
-// Application: the extended window X(0..207) is consumed through the same
-// 128-word region used as a ring (window X[8K .. 8K+111] for output block K,
-// 16 new words per round computed by the recurrence).
+// Application: the extended window X(0..192) is consumed through the same
+// 128-word region used as a ring (window X(16K .. 16K+111) for output block
+// K, 32 new words per round computed by the recurrence).
 //
-// Shared memory per stream: a (104 words, 13 zero-padded blocks of 8) + R
-// (128 words); stride 232 = 8 mod 32, so that the 16-byte loads of a quarter
-// warp (4 streams x 2 lanes) fall in 8 distinct bank groups.  14,848 B per
-// CTA.
+// Shared memory per stream: a (100 words: blocks, coefficient 96, the t^97
+// word of a shifted square, padding) + R (128 words); stride 228 = 4 mod 32,
+// so that the 16-byte loads of a quarter warp (8 streams, same half) fall in
+// 8 distinct bank groups.  14,592 B per CTA.
 #pragma once
 
 #include "ranmar_device.cuh"
 
 namespace ranmar {
 
-constexpr int kPolyWords = 104;    // 13 blocks of 8 >= 97
+constexpr int kPolyWords = 100;    // 6 x 16 coefficients, a_96, t^97 word, 2 pad
 constexpr int kRingWords = 128;    // high product words / application ring
-constexpr int kStreamWords = 232;  // per-stream slice stride (8 mod 32)
+constexpr int kStreamWords = 228;  // per-stream slice stride (4 mod 32)
 constexpr int kJumpStreamsPerWarp = 16;
+constexpr int kPairXor = 16;       // the two lanes of a stream: L and L + 16
 constexpr size_t kJumpSmemBytes = sizeof(uint32_t) * kStreamWords * kJumpStreamsPerWarp;
 static_assert(kPolyWords + kRingWords <= kStreamWords, "slice");
-static_assert(kStreamWords % 32 == 8, "bank spread");
+static_assert(kStreamWords % 32 == 4, "bank spread");
 
 struct ExpParams {
   uint32_t J[kMaxExpWords];  // partition mode: E = (k0 + i) * J
@@ -60,80 +66,104 @@ struct ExpParams {
   uint64_t k0;
 };
 
-struct Quad {
-  uint32_t v[4];
-};
 struct Oct {
   uint32_t v[8];
 };
+struct Hex {
+  uint32_t v[16];
+};
 
-__device__ __forceinline__ Quad lds4(const uint32_t* p) {
+__device__ __forceinline__ void lds4_to(uint32_t* d, const uint32_t* p) {
   const uint4 t = *reinterpret_cast<const uint4*>(p);
-  return Quad{{t.x, t.y, t.z, t.w}};
+  d[0] = t.x;
+  d[1] = t.y;
+  d[2] = t.z;
+  d[3] = t.w;
 }
 __device__ __forceinline__ Oct lds8(const uint32_t* p) {
-  const uint4 lo = *reinterpret_cast<const uint4*>(p);
-  const uint4 hi = *reinterpret_cast<const uint4*>(p + 4);
-  return Oct{{lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w}};
+  Oct o;
+  lds4_to(o.v, p);
+  lds4_to(o.v + 4, p + 4);
+  return o;
+}
+__device__ __forceinline__ Hex lds16(const uint32_t* p) {
+  Hex h;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) lds4_to(h.v + 4 * q, p + 4 * q);
+  return h;
+}
+__device__ __forceinline__ void st4(uint32_t* p, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+  *reinterpret_cast<uint4*>(p) = make_uint4(x, y, z, w);
 }
 
-// acc[p + q] += r[p] * col[q]: rows of this lane (4) x columns (8).
-__device__ __forceinline__ void tile_mac(uint32_t (&acc)[11], const Quad& r, const Oct& col) {
+// acc[p + q] += r[p] * col[q]: this lane's 8 rows x the block's 16 columns.
+__device__ __forceinline__ void tile_mac(uint32_t (&acc)[23], const Oct& r, const Hex& col) {
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < 8; ++p) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[p + q] += r.v[p] * col.v[q];
+    for (int q = 0; q < 16; ++q) acc[p + q] += r.v[p] * col.v[q];
   }
 }
 
-// Reduced coefficients n = 8b + 4g + k (k < 4, n <= 96) of a completed
-// product block, written to a[n + shift].  Blocks 0-2, 4-6 and 8-10 have one
-// fixed set of terms for all their coefficients; the four blocks that
-// straddle a range boundary (3, 7, 11, 12) test each coefficient.
-enum ReduceTerms { kLow3 = 0, kLow2 = 1, kHigh4 = 2, kGeneric = 3 };
-
-template <int kTerms>
-__device__ __forceinline__ void reduce_block_t(uint32_t* __restrict__ a,
-                                               const uint32_t* __restrict__ R, int b,
-                                               unsigned g, const uint32_t (&cv)[4],
-                                               uint32_t shift) {
-  const uint32_t* h = R + 1;  // h_j = c_{97+j}
-  const int n0 = 8 * b + 4 * static_cast<int>(g);
+// v[j] += h_{n+kOff} (kAdd) or -= (otherwise) for the lane's coefficients
+// n = 16 kB + 8g + j, j < 8, with kLo <= n <= kHi; h_i = c_{97+i} = R[i+1].
+// The 8 words come from 16-byte loads of R at the rounded-down index (Rg =
+// R + 8g) and are selected at compile time.
+template <int kB, int kOff, int kLo, int kHi, bool kAdd>
+__device__ __forceinline__ void add_term(uint32_t (&v)[8], const uint32_t* __restrict__ Rg,
+                                         unsigned g) {
+  constexpr int n_first = 16 * kB, n_last = 16 * kB + 15;
+  if constexpr (kHi >= n_first && kLo <= n_last) {
+    constexpr int w = 16 * kB + kOff + 1;  // R index of j = 0 for g = 0
+    constexpr int d = w & 3;
+    static_assert(w - d >= 0 && w - d + 8 + 12 <= kRingWords, "R window");
+    const uint32_t* p = Rg + (w - d);
+    uint32_t t[12];
+    lds4_to(t, p);
+    lds4_to(t + 4, p + 4);
+    if constexpr (d != 0) lds4_to(t + 8, p + 8);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int n = n0 + k;
-    uint32_t v = cv[k];
-    if (kTerms == kLow3) {          // n <= 23
-      v += h[n] - h[n + 33] + h[n + 66];
-    } else if (kTerms == kLow2) {   // 32 <= n <= 55
-      v += h[n] - h[n + 33];
-    } else if (kTerms == kHigh4) {  // 64 <= n <= 87
-      v += h[n] - h[n - 64] + h[n - 31] - h[n + 2];
-    } else {
-      if (n > 96) continue;
-      if (n <= 95) v += h[n];
-      if (n <= 62) v -= h[n + 33];
-      if (n <= 29) v += h[n + 66];
-      if (n >= 64) {
-        v += h[n - 31] - h[n - 64];
-        if (n <= 93) v -= h[n + 2];
-      }
+    for (int j = 0; j < 8; ++j) {
+      const int n0 = 16 * kB + j, n1 = n0 + 8;
+      const bool ok0 = kLo <= n0 && n0 <= kHi;
+      const bool ok1 = kLo <= n1 && n1 <= kHi;
+      if (!ok0 && !ok1) continue;
+      uint32_t x = t[d + j];
+      if (ok0 != ok1) x = ((g != 0) ? ok1 : ok0) ? x : 0u;
+      v[j] = kAdd ? v[j] + x : v[j] - x;
     }
-    a[n + shift] = v;
   }
 }
 
-__device__ __forceinline__ void reduce_block(uint32_t* __restrict__ a,
-                                             const uint32_t* __restrict__ R, int b, unsigned g,
-                                             const uint32_t (&cv)[4], uint32_t shift) {
-  if (b <= 2)
-    reduce_block_t<kLow3>(a, R, b, g, cv, shift);
-  else if (b >= 4 && b <= 6)
-    reduce_block_t<kLow2>(a, R, b, g, cv, shift);
-  else if (b >= 8 && b <= 10)
-    reduce_block_t<kHigh4>(a, R, b, g, cv, shift);
-  else
-    reduce_block_t<kGeneric>(a, R, b, g, cv, shift);
+// Reduces the lane's 8 coefficients of the completed low product block kB
+// (n = 16 kB + 8g + j) and writes them to a[n + shift].
+template <int kB>
+__device__ __forceinline__ void reduce_low(uint32_t* __restrict__ a,
+                                           const uint32_t* __restrict__ R, unsigned g,
+                                           uint32_t (&v)[8], uint32_t shift) {
+  const uint32_t* Rg = R + 8 * g;
+  add_term<kB, 0, 0, 95, true>(v, Rg, g);
+  add_term<kB, 33, 0, 62, false>(v, Rg, g);
+  add_term<kB, 66, 0, 29, true>(v, Rg, g);
+  add_term<kB, -64, 64, 96, false>(v, Rg, g);
+  add_term<kB, -31, 64, 96, true>(v, Rg, g);
+  add_term<kB, 2, 64, 93, false>(v, Rg, g);
+  uint32_t* dst = a + 16 * kB + 8 * g + shift;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) dst[j] = v[j];
+}
+
+__device__ __forceinline__ void reduce_low_dispatch(int B, uint32_t* __restrict__ a,
+                                                    const uint32_t* __restrict__ R, unsigned g,
+                                                    uint32_t (&v)[8], uint32_t shift) {
+  switch (B) {
+    case 0: reduce_low<0>(a, R, g, v, shift); break;
+    case 1: reduce_low<1>(a, R, g, v, shift); break;
+    case 2: reduce_low<2>(a, R, g, v, shift); break;
+    case 3: reduce_low<3>(a, R, g, v, shift); break;
+    case 4: reduce_low<4>(a, R, g, v, shift); break;
+    default: reduce_low<5>(a, R, g, v, shift); break;
+  }
 }
 
 // In place, with the lanes g = 0, 1 of the pair cooperating:
@@ -145,59 +175,82 @@ __device__ __forceinline__ void product_reduce_pair(uint32_t* __restrict__ a,
                                                     const uint32_t* __restrict__ b,
                                                     uint32_t* __restrict__ R, uint32_t shift,
                                                     unsigned g, unsigned mask) {
-  uint32_t pend[4] = {0u, 0u, 0u, 0u};  // low half of the previous anti-diagonal
-  const uint32_t* arow = a + 4 * g;
+  const uint32_t* arow = a + 8 * g;
   const uint32_t* bcol = kSquare ? a : b;
-  const uint32_t keep0 = g ? 0u : ~0u;
-#pragma unroll 1
-  for (int s = 24; s >= 0; --s) {
-    uint32_t acc[11];
+  const uint32_t a96 = a[96];
+  const uint32_t b96 = kSquare ? a96 : b[96];
+  if (g == 0) R[96] = a96 * b96;  // c_192
+  uint32_t pend[8];  // low half of the previous anti-diagonal
 #pragma unroll
-    for (int r = 0; r < 11; ++r) acc[r] = 0;
-    const int ilo = s > 12 ? s - 12 : 0;
+  for (int k = 0; k < 8; ++k) pend[k] = 0;
+#pragma unroll 1
+  for (int s = 10; s >= 0; --s) {
+    uint32_t acc[23];
+#pragma unroll
+    for (int r = 0; r < 23; ++r) acc[r] = 0;
+    const int ilo = s > 5 ? s - 5 : 0;
     // squaring: off-diagonal tiles I < J, i.e. I in [ilo, iend); general: all I
-    const int iend = kSquare ? ((s & 1) ? (s >> 1) + 1 : (s >> 1)) : (s < 12 ? s : 12) + 1;
+    const int iend = kSquare ? (s + 1) >> 1 : (s < 5 ? s : 5) + 1;
     if (ilo < iend) {
-      Quad r0 = lds4(arow + 8 * ilo), r1;
-      Oct c0 = lds8(bcol + 8 * (s - ilo)), c1;
+      Oct r0 = lds8(arow + 16 * ilo), r1;
+      Hex c0 = lds16(bcol + 16 * (s - ilo)), c1;
       int I = ilo;
 #pragma unroll 1
       for (; I + 1 < iend; I += 2) {  // operands one tile ahead, ping-pong
-        r1 = lds4(arow + 8 * (I + 1));
-        c1 = lds8(bcol + 8 * (s - I - 1));
+        r1 = lds8(arow + 16 * (I + 1));
+        c1 = lds16(bcol + 16 * (s - I - 1));
         tile_mac(acc, r0, c0);
         if (I + 2 < iend) {
-          r0 = lds4(arow + 8 * (I + 2));
-          c0 = lds8(bcol + 8 * (s - I - 2));
+          r0 = lds8(arow + 16 * (I + 2));
+          c0 = lds16(bcol + 16 * (s - I - 2));
         }
         tile_mac(acc, r1, c1);
       }
       if (I < iend) tile_mac(acc, r0, c0);
       if (kSquare) {
 #pragma unroll
-        for (int k = 0; k < 11; ++k) acc[k] += acc[k];
+        for (int k = 0; k < 23; ++k) acc[k] += acc[k];
       }
     }
-    if (kSquare && (s & 1) == 0) tile_mac(acc, lds4(arow + 4 * s), lds8(a + 4 * s));
+    if (kSquare && (s & 1) == 0) tile_mac(acc, lds8(arow + 8 * s), lds16(a + 8 * s));
 
-    // Lane 0 holds outputs 0..10 of this anti-diagonal, lane 1 outputs 4..14.
-    // Block s+1 = outputs 8..14 here + the low half of anti-diagonal s+1.
-    uint32_t out[4];
+    // Lane g holds outputs 16s + 8g + r, r < 23.  Block s+1 (16s+16 ..
+    // 16s+31): lane 0 takes 16..23 (its own 16..22 and lane 1's 16..23),
+    // lane 1 takes 24..31 (its own only).  The low half of anti-diagonal s
+    // stays pending for block s: lane 0 holds 0..7 (its own only), lane 1
+    // 8..15 (its own and lane 0's).  So each lane sends its accumulators
+    // 8..15 to the other.
+    uint32_t out[8];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t recv = __shfl_xor_sync(mask, acc[4 + k], 1);
-      out[k] = (k < 3 ? acc[8 + k] : 0u) + pend[k] + (recv & keep0);
-      pend[k] = acc[k] + (recv & ~keep0);
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t recv = __shfl_xor_sync(mask, acc[8 + k], kPairXor);
+      out[k] = (k < 7 ? acc[16 + k] : 0u) + pend[k] + (g ? 0u : recv);
+      pend[k] = acc[k] + (g ? recv : 0u);
     }
-    const int bb = s + 1;
-    if (bb <= 24) {
-      if (bb >= 12)
-        *reinterpret_cast<uint4*>(R + 8 * bb - 96 + 4 * g) = make_uint4(out[0], out[1], out[2], out[3]);
-      if (bb <= 12) reduce_block(a, R, bb, g, out, shift);
+    const int B = s + 1;
+    if (B >= 6) {
+      // rank-1 part: c_k += a_96 b_{k-96} + b_96 a_{k-96}, k = 16B + 8g + j
+      const int i0 = 16 * (B - 6) + 8 * static_cast<int>(g);
+      const Oct x = lds8(a + i0);
+      if (kSquare) {
+        const uint32_t a2 = a96 + a96;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[j] += a2 * x.v[j];
+      } else {
+        const Oct y = lds8(b + i0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[j] += a96 * y.v[j] + b96 * x.v[j];
+      }
+      st4(R + i0, out[0], out[1], out[2], out[3]);
+      st4(R + i0 + 4, out[4], out[5], out[6], out[7]);
+      // coefficient 96: c_96 + h_65 - h_32 (h_j = c_{97+j} = R[j+1])
+      if (B == 6 && g == 0) a[96 + shift] = out[0] + R[66] - R[33];
+    } else {
+      reduce_low_dispatch(B, a, R, g, out, shift);
     }
     __syncwarp(mask);
   }
-  reduce_block(a, R, 0, g, pend, shift);
+  reduce_low<0>(a, R, g, pend, shift);
   __syncwarp(mask);
   if (kSquare && shift && g == 0) {  // fold t^97 = 1 - t^64
     const uint32_t top = a[kR];
@@ -326,73 +379,95 @@ __device__ __forceinline__ void poly_power_pair(const uint32_t (&E)[kMaxExpWords
   }
 }
 
-// dst = x P(A) with P = a (97 coefficients, zero padded), and the c / pos
-// jump by E.  The extended window X is consumed through the 128-word region
-// R used as a ring: X(0..96) is the base state, X(q) = X(q-97) - X(q-33)
-// beyond.  Round m handles output blocks K = 2m + g, whose windows are
-// X[8K .. 8K+111]; between rounds 16 new words replace the 16 oldest (each
-// depends only on words still in the ring).
+// dst = x P(A) with P = a (97 coefficients), and the c / pos jump by E.
+// The extended window X is consumed through the 128-word region R used as a
+// ring: X(0..96) is the base state, X(q) = X(q-97) - X(q-33) beyond.  Round m
+// (m < 3) handles output blocks K = 2m + g (outputs 16K .. 16K+15), whose
+// windows are X(16K .. 16K+111): six 16x16 tiles plus the rank-1 column of
+// a_96 (X(96+16K .. 111+16K), the last window block).  Between rounds 32 new
+// words replace the 32 oldest: every lane reads the words its new ones
+// depend on before any lane writes.  Output 96 is a plain dot product of a
+// with X(96..192).
 __device__ __forceinline__ void apply_pair(const ranmar_state_t* __restrict__ base,
                                            const uint32_t (&E)[kMaxExpWords], bool active,
                                            ranmar_state_t* __restrict__ dst,
                                            const uint32_t* __restrict__ a,
                                            uint32_t* __restrict__ R, unsigned g) {
+  constexpr int kRM = kRingWords - 1;
   uint32_t* ring = R;
-  const uint32_t* bx = base->x;
-  for (int q = static_cast<int>(g); q < kR; q += 2) ring[q] = bx[q];
+  const uint32_t* bx = base->x;  // 16-byte aligned (checked on the host)
+  for (int q = static_cast<int>(g); q < 24; q += 2)
+    reinterpret_cast<uint4*>(ring)[q] = reinterpret_cast<const uint4*>(bx)[q];
+  if (g == 0) ring[96] = bx[96];
   __syncwarp();
   for (int q = kR + static_cast<int>(g); q < kRingWords; q += 2) ring[q] = ring[q - kR] - ring[q - kS];
   __syncwarp();
 
+  const uint32_t b96 = a[96];
   uint32_t* ox = dst->x;
 #pragma unroll 1
-  for (int m = 0; m < 7; ++m) {
+  for (int m = 0; m < 3; ++m) {
     const int K = 2 * m + static_cast<int>(g);
-    if (K < 13) {
-      uint32_t acc[8];
+    uint32_t acc[16];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) acc[r] = 0;
-      // 13 tiles, fully unrolled so that the sliding window (blocks I+K and
-      // I+K+1 of X) and the coefficient blocks are renamed, not moved.
-      Oct w[14];
-      w[0] = lds8(ring + ((8 * K) & (kRingWords - 1)));
+    for (int r = 0; r < 16; ++r) acc[r] = 0;
+    // six tiles, fully unrolled so that the sliding window (blocks I+K and
+    // I+K+1 of X) and the coefficient blocks are renamed, not moved
+    Hex w0 = lds16(ring + ((16 * K) & kRM));
 #pragma unroll
-      for (int I = 0; I < 13; ++I) {
-        const Oct b = lds8(a + 8 * I);
-        w[I + 1] = lds8(ring + ((8 * (I + 1 + K)) & (kRingWords - 1)));
+    for (int I = 0; I < 6; ++I) {
+      const Hex bb = lds16(a + 16 * I);
+      const Hex w1 = lds16(ring + ((16 * (I + 1 + K)) & kRM));
 #pragma unroll
-        for (int p2 = 0; p2 < 8; ++p2) {
+      for (int p2 = 0; p2 < 16; ++p2) {
 #pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const int idx = p2 + r;
-            acc[r] += b.v[p2] * (idx < 8 ? w[I].v[idx & 7] : w[I + 1].v[idx & 7]);
-          }
+        for (int r = 0; r < 16; ++r) {
+          const int idx = p2 + r;
+          acc[r] += bb.v[p2] * (idx < 16 ? w0.v[idx] : w1.v[idx - 16]);
         }
       }
-      if (active) {
-        if (K < 12) {
-          uint4* o4 = reinterpret_cast<uint4*>(ox + 8 * K);
-          o4[0] = make_uint4(acc[0] & kMask24, acc[1] & kMask24, acc[2] & kMask24,
-                             acc[3] & kMask24);
-          o4[1] = make_uint4(acc[4] & kMask24, acc[5] & kMask24, acc[6] & kMask24,
-                             acc[7] & kMask24);
-        } else {
-          ox[96] = acc[0] & kMask24;
-        }
-      }
+      w0 = w1;
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) acc[r] += b96 * w0.v[r];
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        st4(ox + 16 * K + 4 * q, acc[4 * q] & kMask24, acc[4 * q + 1] & kMask24,
+            acc[4 * q + 2] & kMask24, acc[4 * q + 3] & kMask24);
     }
     __syncwarp();
-    if (m < 6) {
-      for (int j = static_cast<int>(g); j < 16; j += 2) {
-        const int q = 16 * m + kRingWords + j;
-        ring[q & (kRingWords - 1)] =
-            ring[(q - kR) & (kRingWords - 1)] - ring[(q - kS) & (kRingWords - 1)];
-      }
+    if (m < 2) {
+      // X(q) for q = 32m + 128 + 16g + j, j < 16, into the slots of X(q - 128)
+      uint32_t nx[16];
+      const int q0 = 32 * m + kRingWords + 16 * static_cast<int>(g);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        nx[j] = ring[(q0 + j - kR) & kRM] - ring[(q0 + j - kS) & kRM];
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        st4(ring + ((q0 + 4 * q) & kRM), nx[4 * q], nx[4 * q + 1], nx[4 * q + 2], nx[4 * q + 3]);
       __syncwarp();
     }
   }
+  // output 96 = sum_i a_i X(96 + i); the ring holds X(64..191), and
+  // X(192) = X(95) - X(159).  Lane 0 takes blocks 0..2 and a_96, lane 1
+  // blocks 3..5.
+  uint32_t part = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int I = 3 * static_cast<int>(g) + i;
+    const Hex bb = lds16(a + 16 * I);
+    const Hex xx = lds16(ring + ((96 + 16 * I) & kRM));
+#pragma unroll
+    for (int p2 = 0; p2 < 16; ++p2) part += bb.v[p2] * xx.v[p2];
+  }
+  if (g == 0) part += b96 * (ring[95] - ring[159 & kRM]);
+  part += __shfl_xor_sync(kFull, part, kPairXor);
 
   if (active && g == 0) {
+    ox[96] = part & kMask24;
     const uint32_t e = exp_mod_m(E);
     // (c - e d) mod m = (c + (m - e) d) mod m, non-negative residue.
     const uint64_t cn =
@@ -438,15 +513,15 @@ __device__ __forceinline__ void load_exponent(uint32_t (&E)[kMaxExpWords], int m
 // mode 1: E_i = (k0 + i) * J, base d_base[0].
 // d_dst_idx (mode 0 only, may be null): stream i is written to
 // d_out[d_dst_idx[i]] (index < n_dst) instead of d_out[i].
-__global__ void __launch_bounds__(32) jump_kernel(
+__global__ void __launch_bounds__(32, 12) jump_kernel(
     const ranmar_state_t* __restrict__ d_base, uint64_t n_base,
     const uint32_t* __restrict__ d_base_idx, const uint32_t* __restrict__ d_exp,
     uint32_t exp_words, ExpParams part, int mode, ranmar_state_t* __restrict__ d_out,
     uint64_t n, uint32_t* status, const uint32_t* __restrict__ d_dst_idx, uint64_t n_dst) {
   extern __shared__ __align__(16) uint32_t smem[];
   const unsigned lane = threadIdx.x & 31;
-  const unsigned g = lane & 1;
-  const unsigned slot = lane >> 1;
+  const unsigned g = lane >> 4;
+  const unsigned slot = lane & 15;
   const uint64_t i = static_cast<uint64_t>(blockIdx.x) * kJumpStreamsPerWarp + slot;
   uint32_t* a = smem + slot * kStreamWords;
   uint32_t* R = a + kPolyWords;

@@ -26,18 +26,25 @@ constexpr int kTabDigits = 1 << kTabWindowBits;                  // 256
 constexpr int kTabRows = kTabWindows * kTabDigits;               // 5120
 constexpr int kTabRowWords = 100;                                // 97 + 3 zeros
 constexpr size_t kTabBytes = sizeof(uint32_t) * kTabRowWords * kTabRows;
-// per-stream slice of the table jump: a (104) + b (104) + R (128) = 336 words,
-// stride 344 = 24 mod 32 (16-byte loads of a quarter warp: 8 distinct groups)
-constexpr int kTabStreamWords = 344;
+// Per-stream slice of the table jump: a (100 words) at 0, R at 100, the table
+// row b (100 words) at 200.  A product reads R only up to word 99 and writes
+// it only up to word 96, so b may start at R + 100; the application's
+// 128-word ring overlaps the start of b, which it no longer needs.  300
+// words, stride 324 = 4 mod 32 (16-byte loads of a quarter warp: 8 distinct
+// groups).
+constexpr int kTabRowOffset = kPolyWords + 100;
+constexpr int kTabStreamWords = 324;
 constexpr size_t kTabSmemBytes = sizeof(uint32_t) * kTabStreamWords * kJumpStreamsPerWarp;
-static_assert(kTabStreamWords % 32 == 24, "bank spread");
+static_assert(kTabRowOffset + kTabRowWords <= kTabStreamWords, "slice");
+static_assert(kPolyWords + kRingWords <= kTabStreamWords, "slice");
+static_assert(kTabStreamWords % 32 == 4, "bank spread");
 
 // Row (j * 256 + d) = t^{d 2^{8j}} mod phi, canonical 24-bit coefficients
 // 0..96, then zeros.
 __global__ void __launch_bounds__(32) table_build_kernel(uint32_t* __restrict__ table) {
   extern __shared__ __align__(16) uint32_t smem[];
   const unsigned lane = threadIdx.x & 31;
-  const unsigned g = lane & 1, slot = lane >> 1;
+  const unsigned g = lane >> 4, slot = lane & 15;
   const int row = blockIdx.x * kJumpStreamsPerWarp + static_cast<int>(slot);
   const bool active = row < kTabRows;
   uint32_t* a = smem + slot * kStreamWords;
@@ -82,10 +89,10 @@ __global__ void __launch_bounds__(32) jump_table_kernel(
     const uint32_t* __restrict__ d_dst_idx, uint64_t n_dst) {
   extern __shared__ __align__(16) uint32_t smem[];
   const unsigned lane = threadIdx.x & 31;
-  const unsigned g = lane & 1, slot = lane >> 1;
+  const unsigned g = lane >> 4, slot = lane & 15;
   uint32_t* a = smem + slot * kTabStreamWords;
-  uint32_t* b = a + kPolyWords;
-  uint32_t* R = b + kPolyWords;
+  uint32_t* R = a + kPolyWords;
+  uint32_t* b = a + kTabRowOffset;
   const uint64_t groups = (n + kJumpStreamsPerWarp - 1) / kJumpStreamsPerWarp;
   // grid-stride over groups of 16 streams (the grid may be smaller than the
   // work, e.g. to leave SM resources to a concurrent generation kernel)
@@ -120,8 +127,8 @@ __global__ void __launch_bounds__(32) jump_table_kernel(
   for (int w = 0; w < kMaxExpWords; ++w) Ep[w] = E[w];
   if (part.flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
 
-  // a = 1 (t^0), b zero padded
-  for (int q = static_cast<int>(g); q < 2 * kPolyWords / 4; q += 2)
+  // a = 1 (t^0); b is always a whole copied row
+  for (int q = static_cast<int>(g); q < kPolyWords / 4; q += 2)
     reinterpret_cast<uint4*>(a)[q] = make_uint4(q == 0 ? 1u : 0u, 0u, 0u, 0u);
   __syncwarp();
   // digit positions up to the highest nonzero digit of the warp's exponents
