@@ -188,10 +188,30 @@ def pin_first_step_is_F1(o):
     assert int(out[0]) == (new - ca) & 0xFFFFFF
 
 
+def pin_jump_linear_brute(o):
+    """The x part of f^E is linear over Z/2^24 (x' = x A^E, Sec. 3.1): by
+    brute-force stepping alone, the jumped x of any state is the sum of the
+    jumped unit states weighted by its words, mod 2^24.  (A jump of a block
+    of states by one fixed E is therefore one matrix product.)"""
+    rng = np.random.default_rng(17)
+    for E in (1, 64, 150, 1000):
+        M = np.zeros((R, R), np.uint64)
+        for i in range(R):
+            e = np.zeros(R, np.uint32)
+            e[i] = 1
+            M[i] = o.brute_jump(e, 0, E)[0]
+        for _ in range(2):
+            x = rng.integers(0, 1 << 24, R).astype(np.uint32)
+            xb, _ = o.brute_jump(x, 5, E)
+            xs = [int(v) for v in x]
+            lin = [sum(xs[i] * int(M[i, w]) for i in range(R)) & 0xFFFFFF for w in range(R)]
+            assert xb.tolist() == lin, E
+
+
 PINS = [pin_james, pin_seed_int_float, pin_alg1_alg2, pin_brute, pin_special,
         pin_cayley_hamilton, pin_horner_dot, pin_composition, pin_order,
         pin_large_jump_brute, pin_c_closed_form, pin_stream_blocks,
-        pin_first_step_is_F1]
+        pin_first_step_is_F1, pin_jump_linear_brute]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=lambda f: f.__name__)
@@ -213,6 +233,27 @@ def test_brute_force_to_1e7(orc):
         xj, cj = orc.jump(x, c, J)
         xb, cb = orc.brute_jump(x, c, J)
         assert np.array_equal(xj, xb) and cj == cb, J
+
+
+def test_radix_blocks_by_jump_matrices(orc):
+    """Stream k + rR of (seed, J) = stream k times the matrix of the jump by
+    rRJ (rows: unit states jumped by the oracle's polynomial method); the
+    composition the GPU partition plan uses level by level."""
+    J = 1 << 40
+    x0, c0 = orc.seeded_state(12345)
+    for r, Rr, k in [(1, 16, 777), (15, 16, 0), (3, 256, 5)]:
+        E = r * Rr * J
+        M = np.zeros((R, R), np.uint64)
+        for i in range(R):
+            e = np.zeros(R, np.uint32)
+            e[i] = 1
+            M[i] = orc.jump(e, 0, E)[0]
+        xs, cs = orc.jump(x0, c0, k * J)
+        xd, cd = orc.jump(x0, c0, (k + r * Rr) * J)
+        v = [int(a) for a in xs]
+        lin = [sum(v[i] * int(M[i, w]) for i in range(R)) & 0xFFFFFF for w in range(R)]
+        assert xd.tolist() == lin
+        assert cd == orc.c_jump(cs, E)
 
 
 def test_regression_values(orc):
