@@ -6,7 +6,8 @@ states sit at k*J for J = 2^40, each producing 4,096 consecutive 24-bit
 outputs into a row-per-stream [65,536 x 4,096] uint32 array.  One step is one
 pass of the whole path: the jump of every stream (t^{kJ} mod phi, the
 linear combination of the 97 words, c in closed form) and the generation of
-all 2^28 outputs with the state written back.  Inputs are synthetic (the
+all 2^28 outputs with the state written back, as one fused launch
+(ranmar_partition_generate_u24); the two-call path is timed beside it.  Inputs are synthetic (the
 paper uses none).  `value` is outputs/s over the whole job.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
@@ -278,56 +279,25 @@ def run_ours(args):
     t_gen = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
     serial_ms = max_over_ranks((sum(t_jump) + sum(t_gen)) / K, dist, dev)
 
-    # ---- pipelined steps (the measured throughput): the jump of batch i+1
-    # (integer pipe) runs on its own stream while batch i generates (HBM),
-    # states double-buffered; every step still jumps and generates its batch.
-    sJ, sG = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    # ---- timed steps (the measured throughput): one fused launch per step
+    # (ranmar_partition_generate_u24).  Each CTA jumps its 16 streams with the
+    # table and then generates them, so on every SM the integer-bound jumps of
+    # some CTAs overlap the HBM-bound stores of others.  Every step jumps and
+    # generates a fresh batch of streams (k0 advances), states double-buffered.
     bufs = [states, torch.empty_like(states)]
-
-    def pipeline(first, steps, d_base=None, h2d=None, d2h=None):
-        evJ, evG, evD = [], [], []
-        for j in range(steps):
-            i = first + j
-            buf = bufs[j % 2]
-            if j >= 2:
-                sJ.wait_event(evG[j - 2])          # batch j-2 finished reading buf
-            with torch.cuda.stream(sJ):
-                src = base
-                if h2d is not None:                 # end to end: inputs from the host
-                    src = d_base[j % 2]
-                    src.copy_(h2d, non_blocking=True)
-                table.partition(src, w.J, k0_of(i), n, out=buf, stream=sJ)
-            e = torch.cuda.Event()
-            e.record(sJ)
-            evJ.append(e)
-            sG.wait_event(e)
-            o = out if d2h is None else d2h[1][j % 2]
-            if d2h is not None and j >= 2:
-                sG.wait_event(evD[j - 2])          # host copy of batch j-2 done
-            rm.generate_u24(buf, desc, o, stream=sG)
-            g = torch.cuda.Event()
-            g.record(sG)
-            evG.append(g)
-            if d2h is not None:
-                sD = d2h[2]
-                sD.wait_event(g)
-                with torch.cuda.stream(sD):
-                    d2h[0][j % 2].copy_(o, non_blocking=True)
-                dd = torch.cuda.Event()
-                dd.record(sD)
-                evD.append(dd)
-        return (evD or evG)[-1]
-
-    torch.cuda.synchronize()
-    pipeline(K, 2)                                 # warm the two streams
+    out2 = out.view(n, count)
+    for j in range(3):
+        table.partition_generate(base, w.J, k0_of(K + j), n, count, states=bufs[j % 2],
+                                 out=out2, stream=stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(sJ)
-    last = pipeline(K + 2, K)
-    sG.wait_event(last)
-    t1.record(sG)
+    t0.record(stream)
+    for j in range(K):
+        table.partition_generate(base, w.J, k0_of(K + 3 + j), n, count, states=bufs[j % 2],
+                                 out=out2, stream=stream)
+    t1.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -335,29 +305,83 @@ def run_ours(args):
     ms_step = max_over_ranks(t0.elapsed_time(t1) / K, dist, dev)
     value = world * n * count / (ms_step * 1e-3)
 
-    # ---- end to end through the public API with host buffers: the seeded base
-    # state copied in from pinned memory and the whole 1 GiB result copied back
-    # to pinned memory every step, on a third stream, double-buffered.
+    # ---- the same steps as two calls (table partition on one stream, then
+    # generation on another), the jump of batch i+1 overlapping the
+    # generation of batch i; reported beside the fused step.
+    sJ, sG = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def pipeline(first, steps):
+        evG = []
+        for j in range(steps):
+            buf = bufs[j % 2]
+            if j >= 2:
+                sJ.wait_event(evG[j - 2])          # batch j-2 finished reading buf
+            table.partition(base, w.J, k0_of(first + j), n, out=buf, stream=sJ)
+            e = torch.cuda.Event()
+            e.record(sJ)
+            sG.wait_event(e)
+            rm.generate_u24(buf, desc, out, stream=sG)
+            g = torch.cuda.Event()
+            g.record(sG)
+            evG.append(g)
+        return evG[-1]
+
+    torch.cuda.synchronize()
+    pipeline(2 * K + 3, 2)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(sJ)
+    last = pipeline(2 * K + 5, K)
+    sG.wait_event(last)
+    p1.record(sG)
+    torch.cuda.synchronize()
+    ms_two = max_over_ranks(p0.elapsed_time(p1) / K, dist, dev)
+
+    # ---- end to end through the public API with host buffers: every step
+    # copies the seeded base state in from pinned memory, runs the fused call
+    # and copies the whole 1 GiB result back to pinned memory (copies on their
+    # own stream, double-buffered).
     h_base = rm.seed(w.seed).pin_memory()
     d_bases = [torch.empty_like(base), torch.empty_like(base)]
-    h_outs = [torch.empty(n * count, dtype=torch.int32).pin_memory() for _ in range(2)]
-    d_outs = [out, torch.empty_like(out)]
-    sD = torch.cuda.Stream(dev)
-    e2e_steps = max(3, min(K, 10))
-    d2h = (h_outs, d_outs, sD)
-    pipeline(2 * K + 2, 2, d_bases, h_base, d2h)
+    h_outs = [torch.empty((n, count), dtype=torch.int32).pin_memory() for _ in range(2)]
+    d_outs = [out2, torch.empty_like(out2)]
+    sF, sD = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def e2e_steps(first, steps):
+        evF, evD = [], []
+        for j in range(steps):
+            b = j % 2
+            if j >= 2:
+                sF.wait_event(evD[j - 2])          # host copy of batch j-2 done
+            with torch.cuda.stream(sF):
+                d_bases[b].copy_(h_base, non_blocking=True)
+            table.partition_generate(d_bases[b], w.J, k0_of(first + j), n, count,
+                                     states=bufs[b], out=d_outs[b], stream=sF)
+            f = torch.cuda.Event()
+            f.record(sF)
+            evF.append(f)
+            sD.wait_event(f)
+            with torch.cuda.stream(sD):
+                h_outs[b].copy_(d_outs[b], non_blocking=True)
+            dd = torch.cuda.Event()
+            dd.record(sD)
+            evD.append(dd)
+        return evD[-1]
+
+    n_e2e = max(3, min(K, 10))
+    e2e_steps(3 * K + 5, 2)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(sJ)
-    last = pipeline(2 * K + 4, e2e_steps, d_bases, h_base, d2h)
-    sJ.wait_event(last)
-    e1.record(sJ)
+    e0.record(sF)
+    last = e2e_steps(3 * K + 7, n_e2e)
+    sF.wait_event(last)
+    e1.record(sF)
     torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist, dev)
-    ok_e2e = bool(np.array_equal(h_outs[(e2e_steps - 1) % 2][:count].numpy(),
-                                 d_outs[(e2e_steps - 1) % 2][:count].cpu().numpy()))
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / n_e2e, dist, dev)
+    lastb = (n_e2e - 1) % 2
+    ok_e2e = bool(np.array_equal(h_outs[lastb][:2].numpy(), d_outs[lastb][:2].cpu().numpy()))
     del d_outs[1], h_outs
     # the paper's left-to-right square-and-multiply on the same streams
     sm_states = torch.empty_like(states)
@@ -417,7 +441,26 @@ def run_ours(args):
                  "algorithmic_macs": jmacs,
                  "traffic": tj["bytes_per_launch"] if tj else None,
                  "avg_launch_ms": jump_ms}
-    dominant = roof_jump if jump_ms >= gen_ms else roof_gen
+    # the fused kernel of the timed steps: HBM-store bound (outputs + final
+    # states), with its multiply-adds reported beside
+    exps_f = [(k0_of(K + 3 + j) + q) * w.J for j in range(K) for q in range(0, n, 97)]
+    fmacs = table_macs(exps_f) * n / (len(exps_f) / K) / K
+    fused_bytes = n * count * 4 + n * 400
+    fused_sha = source_sha("jump.cuh", "jump_table.cuh", "generate.cuh", "partition_generate.cuh",
+                           "ranmar_device.cuh")
+    tf = traffic_for("partition_generate_kernel", fused_sha)
+    roof_fused = {"kernel": "partition_generate_kernel<u24> (table jump + generation, fused)",
+                  "bound": "hbm",
+                  "achieved": fused_bytes / (ms_step * 1e-3) / 1e9, "peak": hbm_peak,
+                  "unit": "GB/s", "frac": fused_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak,
+                  "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                  "algorithmic_bytes": fused_bytes,
+                  "traffic": tf["bytes_per_launch"] if tf else None,
+                  "avg_launch_ms": ms_step,
+                  "alu": {"algorithmic_macs": fmacs,
+                          "achieved": fmacs / (ms_step * 1e-3) / 1e12, "peak": alu_peak,
+                          "unit": "Tmul-add/s",
+                          "frac": fmacs / (ms_step * 1e-3) / 1e12 / alu_peak}}
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -425,14 +468,16 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": f"partitioned: seed 12345, {n} streams per step at k*2^40 "
                                f"(step i of rank r: k = (i*N + r)*{n} + 0..{n - 1}), 4096 u24 "
-                               "outputs each, write-back; step = table jump + generate, "
-                               "jump of step i+1 overlapped with generation of step i",
+                               "outputs each, write-back; step = one fused launch: table "
+                               "jump of every stream + generation",
                    "streams_per_gpu": n, "outputs_per_stream": count, "J": "2^40",
                    "l2": "inputs/outputs larger than L2: every step writes 1.07 GB (8x L2); "
                          "the serial per-kernel timing flushes L2 (258 MB write) between steps"},
         "serial_ms_per_step": serial_ms,
         "serial_outputs_per_s": world * n * count / (serial_ms * 1e-3),
-        "roofline": dominant, "roofline_generate": roof_gen, "roofline_jump": roof_jump,
+        "two_kernel_pipelined_ms_per_step": ms_two,
+        "two_kernel_outputs_per_s": world * n * count / (ms_two * 1e-3),
+        "roofline": roof_fused, "roofline_generate": roof_gen, "roofline_jump": roof_jump,
         "jump_ms": jump_ms, "generate_ms": gen_ms,
         "jumps_per_s": n / (jump_ms * 1e-3),
         "jump_method": "fixed-base table (8-bit windows, shared by all streams)",
@@ -447,10 +492,10 @@ def run_ours(args):
         "e2e": {"value": world * n * count / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 400, "d2h_bytes_per_step": n * count * 4,
                 "ms_per_step": ms_e2e, "checked": ok_e2e,
-                "note": "binding calls with the base state from pinned host memory and the "
-                        "whole result copied to pinned host memory every step (copies on "
-                        "their own stream, double-buffered)"},
-        "gpu_launches": 2 * K,
+                "note": "the fused binding call with the base state from pinned host memory "
+                        "and the whole result copied to pinned host memory every step "
+                        "(copies on their own stream, double-buffered)"},
+        "gpu_launches": K,
         "library": rbuild.LIB,
     }
 
@@ -645,6 +690,32 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
                   "fewer instructions per output (and f64 doubles the bytes)")
     res["float_vs_modular"] = fv
     del o32, o64, st0
+
+    # partition plan: radix-16 levels of jump matrices (one integer GEMM per
+    # level) against the per-stream table jump, same states
+    try:
+        pw = Partitioned()
+        pbase = rm.seed(pw.seed).to(dev)
+        tb = time.perf_counter()
+        plan = rm.Plan(table, pw.J, pw.n_streams)
+        plan_build = (time.perf_counter() - tb) * 1e3
+        pst = torch.empty((pw.n_streams, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+        ms_p = timed(lambda: plan.partition(pbase, 0, pw.n_streams, out=pst))
+        ms_t = timed(lambda: table.partition(pbase, pw.J, 0, pw.n_streams, out=pst))
+        same = bool(torch.equal(plan.partition(pbase, 0, pw.n_streams),
+                                table.partition(pbase, pw.J, 0, pw.n_streams)))
+        levels = {str(m): timed(lambda m=m: plan.partition(pbase, 0, m, out=pst))
+                  for m in (16, 256, 4096)}
+        res["partition_plan"] = {
+            "streams": pw.n_streams, "build_ms": plan_build, "ms": ms_p,
+            "table_jump_ms": ms_t, "states_identical": same,
+            "ms_for_first_streams": levels,
+            "macs_per_stream": 97 * 97,
+            "note": "16 streams by the table jump, then 3 levels x -> x M_{r 16^(t+1) J}"}
+        plan.close()
+        del pst
+    except Exception as e:  # noqa: BLE001
+        res["partition_plan"] = {"error": f"{type(e).__name__}: {e}"}
 
     # probes: write-only HBM ceiling and IMAD ceiling on this GPU
     try:

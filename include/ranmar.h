@@ -281,6 +281,71 @@ int ranmar_partition_ex(const ranmar_table_t *t, const ranmar_state_t *d_base,
                         ranmar_state_t *d_out, size_t n, uint32_t flags,
                         ranmar_stream_t stream);
 
+/*
+ * Partition plan: stream partitioning (Sec. 1) of one base state into
+ * consecutive blocks k = k0 + i of length J, computed level by level with
+ * jump matrices.  The x part of a jump is linear over Z/2^24 (x' = x A^E,
+ * Sec. 3.1), so the jump of many states by one fixed E is one matrix
+ * product; row i of the 97x97 matrix M_E is the x part of the unit state
+ * e_i jumped by E (the polynomial method of Sec. 3.1, via the table).  A
+ * plan holds M_E for E = r 16^(t+1) J, r = 1..15, t < levels (levels =
+ * ceil(log16(max_n / 16))), about 0.65 MB per level on the device.
+ *
+ * ranmar_plan_create: builds the matrices on the current device (which must
+ * be the table's) and returns when they are ready (synchronous).  The plan
+ * keeps a pointer to *t, which must outlive it.  Errors: RANMAR_EINVAL
+ * (null pointer, table of another device), RANMAR_ERANGE (J_words not in
+ * 1..5, max_n not in 1..2^32, 15 16^levels J >= 2^160), RANMAR_ENOMEM,
+ * RANMAR_ECUDA.
+ */
+typedef struct ranmar_plan ranmar_plan_t;
+int ranmar_plan_create(const ranmar_table_t *t, const uint32_t *h_J, uint32_t J_words,
+                       size_t max_n, ranmar_plan_t **out);
+int ranmar_plan_destroy(ranmar_plan_t *p);
+
+/*
+ * ranmar_partition_plan -- the same states as ranmar_partition with the
+ * plan's J: d_out[i] = f^{(k0+i) J}(*d_base), i < n <= max_n.  The first 16
+ * streams are jumped directly with the table; then level t derives streams
+ * r 16^(t+1) + i from streams i < 16^(t+1) by x <- x M_{r 16^(t+1) J} (one
+ * blocked integer GEMM per level, 9,409 multiply-adds per stream against a
+ * matrix shared by all streams of the level), c by the closed form of
+ * Sec. 3.2.  Asynchronous on `stream`.  Errors: RANMAR_EINVAL (null
+ * pointer, misalignment, d_out overlapping *d_base, plan of another
+ * device), RANMAR_ERANGE (n > max_n, (k0 + n - 1) J >= 2^160).
+ */
+int ranmar_partition_plan(const ranmar_plan_t *p, const ranmar_state_t *d_base, uint64_t k0,
+                          size_t n, ranmar_state_t *d_out, ranmar_stream_t stream);
+
+/*
+ * ranmar_partition_generate_u24 / ranmar_partition_generate_f32 -- stream
+ * partitioning (Sec. 1) and generation (Algorithm 2) fused in one kernel.
+ * Stream i (block k = k0 + i of length J of the sequence that starts at
+ * *d_base) is jumped to f^{kJ}(base) with the table (as
+ * ranmar_partition_tab), then its first `count` outputs go to
+ * d_out[i count .. (i+1) count) (u24 in uint32, or u24 * 2^-24 as float,
+ * exact), and d_states[i] receives f^{kJ + count}(base), the state after
+ * those outputs (for resume).  flags: 0 or RANMAR_JUMP_REDUCE_PERIOD.
+ * d_states holds n states (the caller's, 16-byte aligned, not overlapping
+ * *d_base); d_out holds n * count elements (aligned to the element size).
+ * Same results as ranmar_partition_tab followed by ranmar_generate_* with
+ * WRITE_BACK descriptors (state i, offset i count); one launch instead of
+ * two, so that jumps and stores overlap on each SM.
+ * Errors: RANMAR_EINVAL (null pointer with n > 0, misalignment, overlap,
+ * unknown flag, table of another device), RANMAR_ERANGE (J_words not in
+ * 1..5, (k0 + n - 1) J >= 2^160, n * count overflowing size_t).
+ */
+int ranmar_partition_generate_u24(const ranmar_table_t *t, const ranmar_state_t *d_base,
+                                  const uint32_t *h_J, uint32_t J_words, uint64_t k0,
+                                  size_t n, uint64_t count, uint32_t flags,
+                                  ranmar_state_t *d_states, uint32_t *d_out,
+                                  ranmar_stream_t stream);
+int ranmar_partition_generate_f32(const ranmar_table_t *t, const ranmar_state_t *d_base,
+                                  const uint32_t *h_J, uint32_t J_words, uint64_t k0,
+                                  size_t n, uint64_t count, uint32_t flags,
+                                  ranmar_state_t *d_states, float *d_out,
+                                  ranmar_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Persistent batch path: many streams of uneven lengths in one launch.
  * (Sec. 1 partitioning applied to a batch; Algorithm 2 per stream.)

@@ -87,12 +87,19 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_table_create.argtypes = [ctypes.POINTER(_vp)]
     lib.ranmar_table_destroy.argtypes = [_vp]
     lib.ranmar_table_rows.argtypes = [_vp, ctypes.POINTER(_vp)]
+    lib.ranmar_plan_create.argtypes = [_vp, _vp, _u32, _sz, ctypes.POINTER(_vp)]
+    lib.ranmar_plan_destroy.argtypes = [_vp]
+    lib.ranmar_partition_plan.argtypes = [_vp, _vp, _u64, _sz, _vp, _vp]
+    lib.ranmar_partition_plan.restype = ctypes.c_int
     lib.ranmar_table_set_ctas_per_sm.argtypes = [_vp, ctypes.c_int]
     lib.ranmar_table_set_ctas_per_sm.restype = ctypes.c_int
     lib.ranmar_jump_tab.argtypes = [_vp, _vp, _sz, _vp, _vp, _u32, _vp, _sz, _vp, _sz, _vp, _vp]
     lib.ranmar_partition_tab.argtypes = [_vp, _vp, _vp, _u32, _u64, _vp, _sz, _vp]
     lib.ranmar_partition_ex.argtypes = [_vp, _vp, _vp, _u32, _u64, _vp, _sz, _u32, _vp]
     lib.ranmar_partition_ex.restype = ctypes.c_int
+    for nm in ("ranmar_partition_generate_u24", "ranmar_partition_generate_f32"):
+        getattr(lib, nm).argtypes = [_vp, _vp, _vp, _u32, _u64, _sz, _u64, _u32, _vp, _vp, _vp]
+        getattr(lib, nm).restype = ctypes.c_int
     lib.ranmar_graph_begin.argtypes = [_vp]
     lib.ranmar_graph_end.argtypes = [_vp, ctypes.POINTER(_vp)]
     lib.ranmar_graph_launch.argtypes = [_vp, _vp]
@@ -616,12 +623,76 @@ class Table:
                "ranmar_partition_tab")
         return out
 
+    def partition_generate(self, base: torch.Tensor, J: int, k0: int, n: int, count: int,
+                           states=None, out=None, f32: bool = False, flags: int = 0,
+                           stream=None):
+        """ranmar_partition_generate_u24 / _f32: stream i = k0 + i jumped to
+        f^{(k0+i) J}(base) and its first `count` outputs written to out[i] (an
+        (n, count) int32 or float32 tensor); states[i] = the state after them.
+        Returns (states, out)."""
+        base = base.reshape(-1, STATE_WORDS)
+        _need(base, torch.int32, "base")
+        dt = torch.float32 if f32 else torch.int32
+        if states is None:
+            states = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=base.device)
+        if out is None:
+            out = torch.empty((n, count), dtype=dt, device=base.device)
+        _need(states, torch.int32, "states")
+        optr = _out_ptr(out, dt, "out")
+        if states.numel() < n * STATE_WORDS or out.numel() < n * count:
+            raise ValueError("states / out too small")
+        jw = np.array(words(int(J)), dtype=np.uint32)
+        fn = "ranmar_partition_generate_f32" if f32 else "ranmar_partition_generate_u24"
+        _check(getattr(_lib(), fn)(self._h, _ptr(base), jw.ctypes.data, len(jw), int(k0),
+                                   int(n), int(count), int(flags), _ptr(states), optr,
+                                   _stream(stream)), fn)
+        return states, out
+
     def rows_tensor(self) -> torch.Tensor:
         """The table rows as a (5120, 100) int32 CUDA tensor view (no copy)."""
         p = ctypes.c_void_p()
         _check(_lib().ranmar_table_rows(self._h, ctypes.byref(p)), "ranmar_table_rows")
         return _wrap_device_ptr(p.value, self.ROWS * self.ROW_WORDS).view(self.ROWS,
                                                                            self.ROW_WORDS)
+
+
+class Plan:
+    """ranmar_plan_t: jump matrices M_{r 16^(t+1) J} for partitions of block
+    length J into up to max_n streams (built on the table's device)."""
+
+    def __init__(self, table: "Table", J: int, max_n: int):
+        jw = np.array(words(int(J)), dtype=np.uint32)
+        h = ctypes.c_void_p()
+        _check(_lib().ranmar_plan_create(table._h, jw.ctypes.data, len(jw), int(max_n),
+                                         ctypes.byref(h)), "ranmar_plan_create")
+        self._h = h
+        self._table = table       # the plan points at the table
+        self.J, self.max_n = int(J), int(max_n)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().ranmar_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def partition(self, base: torch.Tensor, k0: int, n: int, out=None,
+                  stream=None) -> torch.Tensor:
+        """ranmar_partition_plan: out[i] = f^{(k0+i) J}(base)."""
+        base = base.reshape(-1, STATE_WORDS)
+        _need(base, torch.int32, "base")
+        if out is None:
+            out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=base.device)
+        _need(out, torch.int32, "out")
+        if out.numel() < n * STATE_WORDS:
+            raise ValueError("out too small")
+        _check(_lib().ranmar_partition_plan(self._h, _ptr(base), int(k0), int(n), _ptr(out),
+                                            _stream(stream)), "ranmar_partition_plan")
+        return out
 
 
 def _wrap_device_ptr(ptr: int, n_int32: int) -> torch.Tensor:

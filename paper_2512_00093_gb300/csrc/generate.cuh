@@ -56,70 +56,84 @@ __device__ __forceinline__ LaneConsts lane_consts(unsigned gl) {
   return LaneConsts{mul_d_mod_m(gl + 1), mul_d_mod_m(W)};
 }
 
-// Generates `count` outputs of *st into out[out_base + n], n < count, and
-// optionally writes the advanced state back.  Called by the W lanes of one
-// group (gl = lane within the group, gmask = the group's lane mask).  Each
-// lane carries its own c: c_{Wb+L+1} for the step b it is on.
+// Registers of one stream on its group of W lanes: the rotated ring, the
+// carry (lane 0: the last word of the previous block), this lane's c and the
+// output pointer.
 template <int W, bool F32>
-__device__ void generate_stream(ranmar_state_t* st, uint64_t count, void* out, uint64_t out_base,
-                                bool write_back, unsigned gl, unsigned gmask,
-                                const LaneConsts& k) {
-  constexpr int NR = 96 / W;  // ring registers: blocks b-NR .. b-1
-  constexpr int Q = 32 / W;   // the newer input is block b-Q
+struct GenCtx {
+  static constexpr int NR = 96 / W;  // ring registers: blocks b-NR .. b-1
+  static constexpr int Q = 32 / W;   // the newer input is block b-Q
   static_assert(NR * W == 96 && Q * W == 32, "group width");
   using T = typename OutT<F32>::type;
-  const uint32_t* xs = st->x;
   uint32_t r[NR];
-#pragma unroll
-  for (int j = 0; j < NR; ++j) r[j] = xs[W * j + gl];  // R_{j-NR}[L] = X(W(j-NR) + L - 1)
-  uint32_t carry = xs[96];                               // X(-1)
-  const uint32_t c0 = st->c;
-  const uint64_t pos0 = st->pos;
-  uint32_t cl = sub_mod_m(c0, k.delta_lane);             // c_{L+1}
-  const uint32_t dw = k.delta_w, mdw = kModM - k.delta_w;
+  uint32_t carry;
+  uint32_t cl;  // c_{Wb+L+1} for the step b the lane is on
+  T* p;
+};
 
+template <int W, bool F32>
+__device__ __forceinline__ void gen_load(GenCtx<W, F32>& g, const ranmar_state_t* st, void* out,
+                                         uint64_t out_base, unsigned gl, const LaneConsts& k) {
+  const uint32_t* xs = st->x;
+#pragma unroll
+  for (int j = 0; j < GenCtx<W, F32>::NR; ++j) g.r[j] = xs[W * j + gl];  // R_{j-NR}[L] = X(W(j-NR) + L - 1)
+  g.carry = xs[96];                                                       // X(-1)
+  g.cl = sub_mod_m(st->c, k.delta_lane);                                  // c_{L+1}
+  g.p = static_cast<typename GenCtx<W, F32>::T*>(out) + out_base + gl;
+}
+
+// Step j of a ring turn: R_b into r[j] (= R_{b-NR} on entry), output to p[W j].
+template <int W, bool F32>
+__device__ __forceinline__ void gen_step(GenCtx<W, F32>& g, int j, unsigned gl, unsigned gmask,
+                                         unsigned src, uint32_t dw, uint32_t mdw) {
+  constexpr int NR = GenCtx<W, F32>::NR, Q = GenCtx<W, F32>::Q;
+  const uint32_t xv = g.r[j] - g.r[(j + NR - Q) % NR];  // X(Wb + L), kept mod 2^32
+  store_output<F32>(g.p + W * j, (xv - g.cl) & kMask24);
+  g.cl = step_c(g.cl, dw, mdw);
+  const uint32_t t = __shfl_sync(gmask, xv, src, W);
+  g.r[j] = (gl == 0) ? g.carry : t;
+  g.carry = t;
+}
+
+// Continues the stream from block b0 (a multiple of NR; the context holds
+// R_{b0-NR} .. R_{b0-1}) to `count` outputs, then optionally writes the
+// advanced state back.
+template <int W, bool F32>
+__device__ void gen_finish(GenCtx<W, F32>& g, ranmar_state_t* st, uint64_t count, uint64_t b0,
+                           bool write_back, unsigned gl, unsigned gmask, const LaneConsts& k) {
+  constexpr int NR = GenCtx<W, F32>::NR, Q = GenCtx<W, F32>::Q;
   const uint64_t nblk = count / W;
   const unsigned rem = static_cast<unsigned>(count % W);
-  T* p = static_cast<T*>(out) + out_base + gl;
   const unsigned src = (gl + W - 1) % W;
-
-  // One step producing R_b into `older` (= R_{b-NR} on entry); the output
-  // goes to p[off].
-  auto step = [&](uint32_t& older, uint32_t newer, int off) {
-    const uint32_t xv = older - newer;        // X(Wb + L), kept mod 2^32
-    store_output<F32>(p + off, (xv - cl) & kMask24);
-    cl = step_c(cl, dw, mdw);
-    const uint32_t t = __shfl_sync(gmask, xv, src, W);
-    older = (gl == 0) ? carry : t;
-    carry = t;
-  };
-
-  uint64_t b = 0;
+  const uint32_t dw = k.delta_w, mdw = kModM - k.delta_w;
+  uint64_t b = b0;
 #pragma unroll 1
   for (; b + NR <= nblk; b += NR) {
 #pragma unroll
-    for (int j = 0; j < NR; ++j) step(r[j], r[(j + NR - Q) % NR], W * j);
-    p += W * NR;
+    for (int j = 0; j < NR; ++j) gen_step<W, F32>(g, j, gl, gmask, src, dw, mdw);
+    g.p += W * NR;
   }
   // Remaining blocks: step, then shift the ring so that r[0] stays oldest.
 #pragma unroll 1
   for (; b < nblk; ++b) {
-    step(r[0], r[NR - Q], 0);
-    p += W;
-    const uint32_t nw = r[0];
+    gen_step<W, F32>(g, 0, gl, gmask, src, dw, mdw);
+    g.p += W;
+    const uint32_t nw = g.r[0];
 #pragma unroll
-    for (int j = 0; j + 1 < NR; ++j) r[j] = r[j + 1];
-    r[NR - 1] = nw;
+    for (int j = 0; j + 1 < NR; ++j) g.r[j] = g.r[j + 1];
+    g.r[NR - 1] = nw;
   }
 
   // Ragged tail: one more block with masked stores.
   uint32_t xb = 0;
   if (rem != 0) {
-    xb = r[0] - r[NR - Q];  // X(WB + L)
-    if (gl < rem) store_output<F32>(p, (xb - cl) & kMask24);
+    xb = g.r[0] - g.r[NR - Q];  // X(WB + L)
+    if (gl < rem) store_output<F32>(g.p, (xb - g.cl) & kMask24);
   }
 
   if (!write_back) return;
+  const uint32_t c0 = st->c;
+  const uint64_t pos0 = st->pos;
   __syncwarp(gmask);
   // Positions relative to WB: r[j] = X(Wj + L - 97), carry (lane 0) = X(-1),
   // xb = X(L).  New state word q = X(rem - 97 + q).
@@ -127,16 +141,70 @@ __device__ void generate_stream(ranmar_state_t* st, uint64_t count, void* out, u
 #pragma unroll
   for (int j = 0; j < NR; ++j) {
     const int q = W * j + static_cast<int>(gl) - static_cast<int>(rem);
-    if (q >= 0) xw[q] = r[j] & kMask24;
+    if (q >= 0) xw[q] = g.r[j] & kMask24;
   }
-  if (gl == 0) xw[96 - rem] = carry & kMask24;
+  if (gl == 0) xw[96 - rem] = g.carry & kMask24;
   if (gl < rem) xw[gl + 97 - rem] = xb & kMask24;
+  __syncwarp(gmask);
   if (gl == 0) {
     // c after `count` transitions, in closed form (Sec. 3.2)
     const uint64_t e = count % kModM;
     st->c = static_cast<uint32_t>((static_cast<uint64_t>(c0) + (kModM - e) * kD) % kModM);
     st->pos = pos0 + count;
   }
+}
+
+// Generates `count` outputs of *st into out[out_base + n], n < count, and
+// optionally writes the advanced state back.  Called by the W lanes of one
+// group (gl = lane within the group, gmask = the group's lane mask).
+template <int W, bool F32>
+__device__ void generate_stream(ranmar_state_t* st, uint64_t count, void* out, uint64_t out_base,
+                                bool write_back, unsigned gl, unsigned gmask,
+                                const LaneConsts& k) {
+  GenCtx<W, F32> g;
+  gen_load<W, F32>(g, st, out, out_base, gl, k);
+  gen_finish<W, F32>(g, st, count, 0, write_back, gl, gmask, k);
+}
+
+// S streams on one group at once: their steps are independent dependency
+// chains (shuffle -> subtract -> shuffle), so interleaving them hides the
+// chain latency with S times fewer resident warps.  The blocks all S have
+// (rounded down to whole ring turns) run interleaved; each stream then
+// finishes alone.  ok[s] = false skips stream s (and the interleaved part).
+template <int W, bool F32, int S>
+__device__ void generate_streams(ranmar_state_t* const (&st)[S], const uint64_t (&count)[S],
+                                 void* out, const uint64_t (&out_base)[S],
+                                 const bool (&write_back)[S], const bool (&ok)[S], unsigned gl,
+                                 unsigned gmask, const LaneConsts& k) {
+  constexpr int NR = GenCtx<W, F32>::NR;
+  GenCtx<W, F32> g[S];
+  bool all = true;
+  uint64_t common = ~0ull;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    all = all && ok[s];
+    if (ok[s]) {
+      gen_load<W, F32>(g[s], st[s], out, out_base[s], gl, k);
+      common = min(common, count[s] / W);
+    }
+  }
+  if (!all) common = 0;
+  common -= common % NR;
+  const unsigned src = (gl + W - 1) % W;
+  const uint32_t dw = k.delta_w, mdw = kModM - k.delta_w;
+#pragma unroll 1
+  for (uint64_t b = 0; b < common; b += NR) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) gen_step<W, F32>(g[s], j, gl, gmask, src, dw, mdw);
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) g[s].p += W * NR;
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+    if (ok[s]) gen_finish<W, F32>(g[s], st[s], count[s], common, write_back[s], gl, gmask, k);
 }
 
 // Algorithm 1 (Sec. 4, the LAMMPS floating-point form) with the same warp
@@ -274,9 +342,18 @@ __global__ void __launch_bounds__(256) generate_alg1_kernel(
   }
 }
 
+// Streams a group interleaves in the persistent kernel: 4 for whole warps
+// (3 ring registers each), 2 for half warps (6 each), 1 for narrower groups
+// (whose rings are 12 or 24 registers).
+template <int W>
+__host__ __device__ constexpr int persistent_ilp() {
+  return W == 32 ? 4 : (W == 16 ? 2 : 1);
+}
+
 // Persistent batch kernel: groups of W lanes pull `chunk` descriptors at a
 // time from an atomic queue (*queue must be 0 at launch), in the order
-// given by `order` (e.g. longest first) or in index order when it is null.
+// given by `order` (e.g. longest first) or in index order when it is null,
+// and generate them persistent_ilp<W>() at a time (interleaved).
 // `allow_write_back` = 0 ignores the write-back flags (used while tuning, so
 // that timing runs leave the states untouched).
 template <int W, bool F32>
@@ -287,6 +364,7 @@ __global__ void generate_persistent_kernel(ranmar_state_t* __restrict__ states,
                                            void* out, uint64_t out_len, uint32_t* status,
                                            unsigned long long* queue, uint32_t chunk,
                                            int allow_write_back) {
+  constexpr int S = persistent_ilp<W>();
   const unsigned lane = threadIdx.x & 31;
   const unsigned gl = lane % W;
   const unsigned gbase = lane - gl;
@@ -300,17 +378,31 @@ __global__ void generate_persistent_kernel(ranmar_state_t* __restrict__ states,
     if (base >= n_desc) break;
     const uint64_t end = min(static_cast<uint64_t>(base) + chunk, n_desc);
 #pragma unroll 1
-    for (uint64_t t = base; t < end; ++t) {
-      const uint64_t di = order ? order[t] : t;
-      if (di >= n_desc) {
-        if (gl == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
-        continue;
+    for (uint64_t t0 = base; t0 < end; t0 += S) {
+      ranmar_state_t* st[S];
+      uint64_t cnt[S], ob[S];
+      bool wb[S], ok[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const uint64_t t = t0 + s;
+        st[s] = states;
+        cnt[s] = ob[s] = 0;
+        wb[s] = ok[s] = false;
+        if (t >= end) continue;
+        const uint64_t di = order ? order[t] : t;
+        if (di >= n_desc) {
+          if (gl == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
+          continue;
+        }
+        const ranmar_desc_t d = desc[di];
+        if (!desc_ok(d, n_states, out_len, status, gl)) continue;
+        st[s] = states + d.state_idx;
+        cnt[s] = d.count;
+        ob[s] = d.out_offset;
+        wb[s] = allow_write_back && (d.flags & RANMAR_DESC_WRITE_BACK) != 0;
+        ok[s] = true;
       }
-      const ranmar_desc_t d = desc[di];
-      if (!desc_ok(d, n_states, out_len, status, gl)) continue;
-      generate_stream<W, F32>(states + d.state_idx, d.count, out, d.out_offset,
-                              allow_write_back && (d.flags & RANMAR_DESC_WRITE_BACK) != 0, gl,
-                              gmask, k);
+      generate_streams<W, F32, S>(st, cnt, out, ob, wb, ok, gl, gmask, k);
     }
   }
 }

@@ -79,6 +79,49 @@ __device__ __forceinline__ void copy_row(uint32_t* __restrict__ dst,
   for (int q = static_cast<int>(g); q < kTabRowWords / 4; q += 2) d4[q] = __ldg(s4 + q);
 }
 
+// dst = f^E(base) for the stream of this lane pair, P_E from the table (all
+// 32 lanes call it; `active` false for lanes without a stream).  Slice: a at
+// 0, R at kPolyWords, the row b at kTabRowOffset.
+__device__ __forceinline__ void table_jump_pair(const uint32_t* __restrict__ table,
+                                                const ranmar_state_t* __restrict__ base,
+                                                const uint32_t (&E)[kMaxExpWords],
+                                                uint32_t flags, bool active,
+                                                ranmar_state_t* __restrict__ dst,
+                                                uint32_t* __restrict__ a, unsigned g) {
+  uint32_t* R = a + kPolyWords;
+  uint32_t* b = a + kTabRowOffset;
+  uint32_t Ep[kMaxExpWords];
+#pragma unroll
+  for (int w = 0; w < kMaxExpWords; ++w) Ep[w] = E[w];
+  if (flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
+
+  // a = 1 (t^0); b is always a whole copied row
+  for (int q = static_cast<int>(g); q < kPolyWords / 4; q += 2)
+    reinterpret_cast<uint4*>(a)[q] = make_uint4(q == 0 ? 1u : 0u, 0u, 0u, 0u);
+  __syncwarp();
+  // digit positions up to the highest nonzero digit of the warp's exponents
+  const int nbits = active ? exp_bitlen(Ep) : 0;
+  const int nwin = (static_cast<int>(__reduce_max_sync(kFull, static_cast<unsigned>(nbits))) +
+                    kTabWindowBits - 1) / kTabWindowBits;
+  bool have = false;
+#pragma unroll 1
+  for (int j = 0; j < nwin; ++j) {
+    const uint32_t d = active ? exp_digit(Ep, j) : 0u;
+    const bool first = d != 0 && !have;
+    const bool mul = d != 0 && have;
+    const uint32_t* row = table + static_cast<size_t>(j * kTabDigits + d) * kTabRowWords;
+    if (first) copy_row(a, row, g);
+    if (mul) copy_row(b, row, g);
+    const unsigned mmask = __ballot_sync(kFull, mul);
+    __syncwarp();
+    if (mul) product_reduce_pair<false>(a, b, R, 0u, g, mmask);
+    __syncwarp();
+    have = have || d != 0;
+  }
+  apply_pair(base, E, active, dst, a, R, g);
+  __syncwarp();
+}
+
 // Same contract as jump_kernel (modes 0 and 1, optional destination
 // indices), with P_E from the table.
 __global__ void __launch_bounds__(32) jump_table_kernel(
@@ -91,8 +134,6 @@ __global__ void __launch_bounds__(32) jump_table_kernel(
   const unsigned lane = threadIdx.x & 31;
   const unsigned g = lane >> 4, slot = lane & 15;
   uint32_t* a = smem + slot * kTabStreamWords;
-  uint32_t* R = a + kPolyWords;
-  uint32_t* b = a + kTabRowOffset;
   const uint64_t groups = (n + kJumpStreamsPerWarp - 1) / kJumpStreamsPerWarp;
   // grid-stride over groups of 16 streams (the grid may be smaller than the
   // work, e.g. to leave SM resources to a concurrent generation kernel)
@@ -122,36 +163,7 @@ __global__ void __launch_bounds__(32) jump_table_kernel(
     }
   }
 
-  uint32_t Ep[kMaxExpWords];
-#pragma unroll
-  for (int w = 0; w < kMaxExpWords; ++w) Ep[w] = E[w];
-  if (part.flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
-
-  // a = 1 (t^0); b is always a whole copied row
-  for (int q = static_cast<int>(g); q < kPolyWords / 4; q += 2)
-    reinterpret_cast<uint4*>(a)[q] = make_uint4(q == 0 ? 1u : 0u, 0u, 0u, 0u);
-  __syncwarp();
-  // digit positions up to the highest nonzero digit of the warp's exponents
-  const int nbits = active ? exp_bitlen(Ep) : 0;
-  const int nwin = (static_cast<int>(__reduce_max_sync(kFull, static_cast<unsigned>(nbits))) +
-                    kTabWindowBits - 1) / kTabWindowBits;
-  bool have = false;
-#pragma unroll 1
-  for (int j = 0; j < nwin; ++j) {
-    const uint32_t d = active ? exp_digit(Ep, j) : 0u;
-    const bool first = d != 0 && !have;
-    const bool mul = d != 0 && have;
-    const uint32_t* row = table + static_cast<size_t>(j * kTabDigits + d) * kTabRowWords;
-    if (first) copy_row(a, row, g);
-    if (mul) copy_row(b, row, g);
-    const unsigned mmask = __ballot_sync(kFull, mul);
-    __syncwarp();
-    if (mul) product_reduce_pair<false>(a, b, R, 0u, g, mmask);
-    __syncwarp();
-    have = have || d != 0;
-  }
-  apply_pair(base, E, active, d_out + (active ? di : 0), a, R, g);
-  __syncwarp();
+  table_jump_pair(table, base, E, part.flags, active, d_out + (active ? di : 0), a, g);
   }
 }
 

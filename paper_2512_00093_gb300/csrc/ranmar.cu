@@ -14,6 +14,8 @@
 #include "jump.cuh"
 #include "batch.cuh"
 #include "jump_table.cuh"
+#include "partition_generate.cuh"
+#include "plan.cuh"
 
 // Batch handle: the workspace of the persistent path on one device.
 struct ranmar_batch {
@@ -35,6 +37,18 @@ struct ranmar_table {
   uint32_t* rows;     // kTabRows x kTabRowWords
   int num_sms;
   int ctas_per_sm;    // 0 = one CTA per group of 16 streams (full grid)
+};
+
+struct ranmar_plan {
+  int device;
+  const ranmar_table_t* table;  // not owned
+  uint32_t J[RANMAR_MAX_EXP_WORDS];
+  uint32_t J_words;
+  size_t max_n;
+  int levels;          // level t turns 16^(t+1) known streams into 16^(t+2)
+  uint32_t* mats;      // levels x 15 x 97 x 112: M_{r 16^(t+1) J}
+  uint32_t* ced;       // levels x 15: (E mod m) d mod m
+  uint64_t* pose;      // levels x 15: E mod 2^64
 };
 
 struct ranmar_graph {
@@ -326,6 +340,56 @@ int launch_alg1(ranmar_state_t* states, size_t n_states, const ranmar_desc_t* de
   ranmar::generate_alg1_kernel<F><<<static_cast<unsigned>(blocks), 256, 0,
                                     reinterpret_cast<cudaStream_t>(stream)>>>(
       states, n_states, desc, n_desc, out, out_len, status);
+  return check_launch();
+}
+
+// Validates a partition request (E = (k0 + i) J for i < n must fit in
+// RANMAR_MAX_EXP_WORDS words) and fills the kernel parameters.
+int partition_params(const uint32_t* h_J, uint32_t J_words, uint64_t k0, size_t n,
+                     uint32_t flags, ranmar::ExpParams& part) {
+  if (flags & ~static_cast<uint32_t>(RANMAR_JUMP_REDUCE_PERIOD)) return RANMAR_EINVAL;
+  if (J_words < 1 || J_words > RANMAR_MAX_EXP_WORDS) return RANMAR_ERANGE;
+  if (n - 1 > UINT64_MAX - k0) return RANMAR_ERANGE;
+  const uint64_t kmax = k0 + (n - 1);
+  int jbits = 0;
+  for (int w = 0; w < static_cast<int>(J_words); ++w)
+    if (h_J[w]) jbits = 32 * w + 32 - __builtin_clz(h_J[w]);
+  const int kbits = kmax ? 64 - __builtin_clzll(kmax) : 0;
+  if (jbits + kbits > 32 * RANMAR_MAX_EXP_WORDS) return RANMAR_ERANGE;
+  part = ranmar::ExpParams{};
+  for (uint32_t w = 0; w < J_words; ++w) part.J[w] = h_J[w];
+  part.J_words = J_words;
+  part.k0 = k0;
+  part.flags = flags;
+  return RANMAR_OK;
+}
+
+template <bool F32>
+int launch_partition_generate(const ranmar_table_t* t, const ranmar_state_t* d_base,
+                              const uint32_t* h_J, uint32_t J_words, uint64_t k0, size_t n,
+                              uint64_t count, uint32_t flags, ranmar_state_t* d_states,
+                              void* d_out, ranmar_stream_t stream) {
+  if (!t || (flags & ~static_cast<uint32_t>(RANMAR_JUMP_REDUCE_PERIOD))) return RANMAR_EINVAL;
+  if (n == 0) return RANMAR_OK;
+  if (!d_base || !h_J || !d_states || (count > 0 && !d_out)) return RANMAR_EINVAL;
+  if (!aligned(d_base, 16) || !aligned(d_states, 16) || !aligned(d_out, 4)) return RANMAR_EINVAL;
+  if (count > 0 && n > SIZE_MAX / 4 / count) return RANMAR_ERANGE;
+  if (overlaps(d_base, sizeof(ranmar_state_t), d_states, n * sizeof(ranmar_state_t)))
+    return RANMAR_EINVAL;
+  if (count > 0 && (overlaps(d_base, sizeof(ranmar_state_t), d_out, n * count * 4) ||
+                    overlaps(d_states, n * sizeof(ranmar_state_t), d_out, n * count * 4)))
+    return RANMAR_EINVAL;
+  ranmar::ExpParams part;
+  const int rc = partition_params(h_J, J_words, k0, n, flags, part);
+  if (rc != RANMAR_OK) return rc;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != t->device) return RANMAR_EINVAL;
+  uint64_t blocks = (n + ranmar::kJumpStreamsPerWarp - 1) / ranmar::kJumpStreamsPerWarp;
+  if (blocks > 0x7FFFFFFFull) blocks = 0x7FFFFFFFull;
+  ranmar::partition_generate_kernel<F32>
+      <<<static_cast<unsigned>(blocks), 32, ranmar::kTabSmemBytes,
+         reinterpret_cast<cudaStream_t>(stream)>>>(t->rows, d_base, part, d_states, n, count,
+                                                    d_out);
   return check_launch();
 }
 
@@ -816,6 +880,194 @@ int ranmar_partition_tab(const ranmar_table_t* t, const ranmar_state_t* d_base,
   part.k0 = k0;
   return launch_jump_table(t, d_base, 1, nullptr, nullptr, 0, part, 1, d_out, n, nullptr, stream,
                            nullptr, n);
+}
+
+
+int ranmar_partition_generate_u24(const ranmar_table_t* t, const ranmar_state_t* d_base,
+                                  const uint32_t* h_J, uint32_t J_words, uint64_t k0, size_t n,
+                                  uint64_t count, uint32_t flags, ranmar_state_t* d_states,
+                                  uint32_t* d_out, ranmar_stream_t stream) {
+  return launch_partition_generate<false>(t, d_base, h_J, J_words, k0, n, count, flags, d_states,
+                                          d_out, stream);
+}
+
+int ranmar_partition_generate_f32(const ranmar_table_t* t, const ranmar_state_t* d_base,
+                                  const uint32_t* h_J, uint32_t J_words, uint64_t k0, size_t n,
+                                  uint64_t count, uint32_t flags, ranmar_state_t* d_states,
+                                  float* d_out, ranmar_stream_t stream) {
+  return launch_partition_generate<true>(t, d_base, h_J, J_words, k0, n, count, flags, d_states,
+                                         d_out, stream);
+}
+
+int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_words,
+                       size_t max_n, ranmar_plan_t** out) {
+  if (!out) return RANMAR_EINVAL;
+  *out = nullptr;
+  if (!t || !h_J) return RANMAR_EINVAL;
+  if (J_words < 1 || J_words > RANMAR_MAX_EXP_WORDS || max_n == 0 || max_n > (1ull << 32))
+    return RANMAR_ERANGE;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != t->device) return RANMAR_EINVAL;
+  int levels = 0;
+  for (uint64_t known = ranmar::kPlanBase; known < max_n; known *= ranmar::kPlanRadix) ++levels;
+  ranmar_plan* p = new (std::nothrow) ranmar_plan{};
+  if (!p) return RANMAR_ENOMEM;
+  p->device = dev;
+  p->table = t;
+  for (uint32_t w = 0; w < J_words; ++w) p->J[w] = h_J[w];
+  p->J_words = J_words;
+  p->max_n = max_n;
+  p->levels = levels;
+  if (levels == 0) {
+    *out = p;
+    return RANMAR_OK;
+  }
+  // Exponents E = r 16^(t+1) J (r = 1..15), one per matrix; each matrix row i
+  // is the unit state e_i jumped by E.
+  const int nmat = 15 * levels;
+  const size_t nrows = static_cast<size_t>(nmat) * RANMAR_R;
+  uint32_t* hexp = new (std::nothrow) uint32_t[nrows * RANMAR_MAX_EXP_WORDS];
+  uint32_t* hidx = new (std::nothrow) uint32_t[nrows];
+  uint32_t* hced = new (std::nothrow) uint32_t[nmat];
+  uint64_t* hpos = new (std::nothrow) uint64_t[nmat];
+  ranmar_state_t* hunit = new (std::nothrow) ranmar_state_t[RANMAR_R];
+  int rc = (hexp && hidx && hced && hpos && hunit) ? RANMAR_OK : RANMAR_ENOMEM;
+  for (int m = 0; rc == RANMAR_OK && m < nmat; ++m) {
+    const int tl = m / 15, r = m % 15 + 1;
+    uint64_t mult = static_cast<uint64_t>(r);
+    for (int q = 0; q <= tl; ++q) mult *= ranmar::kPlanRadix;
+    uint32_t E[RANMAR_MAX_EXP_WORDS] = {0, 0, 0, 0, 0};
+    unsigned __int128 carry = 0;
+    for (int w = 0; w < RANMAR_MAX_EXP_WORDS; ++w) {
+      const unsigned __int128 v =
+          static_cast<unsigned __int128>(w < static_cast<int>(J_words) ? h_J[w] : 0u) * mult + carry;
+      E[w] = static_cast<uint32_t>(v);
+      carry = v >> 32;
+    }
+    if (carry != 0) {
+      rc = RANMAR_ERANGE;
+      break;
+    }
+    uint64_t em = 0;  // E mod m by Horner over 32-bit words
+    for (int w = RANMAR_MAX_EXP_WORDS - 1; w >= 0; --w) em = ((em << 32) | E[w]) % ranmar::kModM;
+    hced[m] = static_cast<uint32_t>((em * ranmar::kD) % ranmar::kModM);
+    hpos[m] = (static_cast<uint64_t>(E[1]) << 32) | E[0];
+    for (int i = 0; i < RANMAR_R; ++i) {
+      const size_t q = static_cast<size_t>(m) * RANMAR_R + i;
+      hidx[q] = static_cast<uint32_t>(i);
+      for (int w = 0; w < RANMAR_MAX_EXP_WORDS; ++w) hexp[q * RANMAR_MAX_EXP_WORDS + w] = E[w];
+    }
+  }
+  if (rc == RANMAR_OK) {
+    std::memset(hunit, 0, sizeof(ranmar_state_t) * RANMAR_R);
+    for (int i = 0; i < RANMAR_R; ++i) hunit[i].x[i] = 1u;
+  }
+  ranmar_state_t *dunit = nullptr, *djumped = nullptr;
+  uint32_t *dexp = nullptr, *didx = nullptr;
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (rc == RANMAR_OK) {
+    e = cudaMalloc(&p->mats, nrows * ranmar::kPlanCols * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&p->ced, nmat * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&p->pose, nmat * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&dunit, RANMAR_R * sizeof(ranmar_state_t));
+    if (e == cudaSuccess) e = cudaMalloc(&djumped, nrows * sizeof(ranmar_state_t));
+    if (e == cudaSuccess) e = cudaMalloc(&dexp, nrows * RANMAR_MAX_EXP_WORDS * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&didx, nrows * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->ced, hced, nmat * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->pose, hpos, nmat * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dunit, hunit, RANMAR_R * sizeof(ranmar_state_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dexp, hexp, nrows * RANMAR_MAX_EXP_WORDS * sizeof(uint32_t),
+                          cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(didx, hidx, nrows * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ranmar::plan_level_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(ranmar::kPlanSmemBytes));
+    if (e == cudaSuccess) {
+      ranmar::ExpParams none{};
+      const int jr = launch_jump_table(t, dunit, RANMAR_R, didx, dexp, RANMAR_MAX_EXP_WORDS, none,
+                                       0, djumped, nrows, nullptr,
+                                       reinterpret_cast<ranmar_stream_t>(s), nullptr, nrows);
+      if (jr != RANMAR_OK) e = cudaErrorLaunchFailure;
+    }
+    if (e == cudaSuccess) {
+      ranmar::plan_pack_kernel<<<1024, 128, 0, s>>>(djumped, p->mats, nrows);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (s) cudaStreamDestroy(s);
+    if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? RANMAR_ENOMEM : cuda_fail(e);
+  }
+  cudaFree(dunit);
+  cudaFree(djumped);
+  cudaFree(dexp);
+  cudaFree(didx);
+  delete[] hexp;
+  delete[] hidx;
+  delete[] hced;
+  delete[] hpos;
+  delete[] hunit;
+  if (rc != RANMAR_OK) {
+    cudaFree(p->mats);
+    cudaFree(p->ced);
+    cudaFree(p->pose);
+    delete p;
+    if (rc == RANMAR_ENOMEM) cudaGetLastError();
+    return rc;
+  }
+  *out = p;
+  return RANMAR_OK;
+}
+
+int ranmar_plan_destroy(ranmar_plan_t* p) {
+  if (!p) return RANMAR_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(p->device);
+  cudaFree(p->mats);
+  cudaFree(p->ced);
+  cudaFree(p->pose);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete p;
+  return RANMAR_OK;
+}
+
+int ranmar_partition_plan(const ranmar_plan_t* p, const ranmar_state_t* d_base, uint64_t k0,
+                          size_t n, ranmar_state_t* d_out, ranmar_stream_t stream) {
+  if (!p) return RANMAR_EINVAL;
+  if (n == 0) return RANMAR_OK;
+  if (!d_base || !d_out) return RANMAR_EINVAL;
+  if (n > p->max_n) return RANMAR_ERANGE;
+  if (!aligned(d_base, 16) || !aligned(d_out, 16)) return RANMAR_EINVAL;
+  if (overlaps(d_base, sizeof(ranmar_state_t), d_out, n * sizeof(ranmar_state_t)))
+    return RANMAR_EINVAL;
+  ranmar::ExpParams part;
+  const int rc = partition_params(p->J, p->J_words, k0, n, 0, part);
+  if (rc != RANMAR_OK) return rc;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return RANMAR_EINVAL;
+  const size_t n0 = n < static_cast<size_t>(ranmar::kPlanBase) ? n : ranmar::kPlanBase;
+  int jr = launch_jump_table(p->table, d_base, 1, nullptr, nullptr, 0, part, 1, d_out, n0, nullptr,
+                             stream, nullptr, n0);
+  if (jr != RANMAR_OK) return jr;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint64_t R = ranmar::kPlanBase;
+  for (int tl = 0; tl < p->levels && R < n; ++tl, R *= ranmar::kPlanRadix) {
+    const dim3 grid(static_cast<unsigned>((R + ranmar::kPlanRows - 1) / ranmar::kPlanRows), 15);
+    ranmar::plan_level_kernel<<<grid, ranmar::kPlanThreads, ranmar::kPlanSmemBytes, s>>>(
+        d_out, R, n, p->mats + static_cast<size_t>(tl) * 15 * RANMAR_R * ranmar::kPlanCols,
+        p->ced + tl * 15, p->pose + tl * 15);
+    const int lr = check_launch();
+    if (lr != RANMAR_OK) return lr;
+  }
+  return RANMAR_OK;
 }
 
 int ranmar_generate_alg1_f32(ranmar_state_t* d_states, size_t n_states,

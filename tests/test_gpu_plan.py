@@ -1,0 +1,80 @@
+"""GPU parity of the partition plan (radix-16 levels of jump matrices): the
+states equal the table partition's and the oracle's, bit for bit, for
+stream counts that end inside every level, and the plan's host checks."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_00093_gb300 as rm
+    return rm
+
+
+@pytest.fixture(scope="module")
+def table(rm):
+    t = rm.Table()
+    yield t
+    t.close()
+
+
+@pytest.mark.parametrize("J", [1 << 40, (1 << 64) + 12345, (1 << 120) + 12345])
+def test_plan_equals_table_partition(rm, table, orc, J):
+    dev = torch.device("cuda:0")
+    base = rm.seed(12345).to(dev)
+    plan = rm.Plan(table, J, 70000)
+    for n, k0 in [(1, 0), (15, 3), (16, 0), (17, 9), (255, 1), (256, 0), (257, 4),
+                  (4095, 7), (4097, 0), (65536, 123), (70000, 1 << 20)]:
+        a = plan.partition(base, k0, n)
+        b = table.partition(base, J, k0, n)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), (n, k0)
+    # a sample against the oracle directly
+    st = rm.state_words_np(a)
+    x0, c0 = orc.seeded_state(12345)
+    for i in [0, 15, 16, 255, 256, 4095, 4096, 65535, 65536, 69999]:
+        xr, cr = orc.jump(x0, c0, ((1 << 20) + i) * J)
+        assert np.array_equal(st[i, :97], xr) and st[i, 97] == cr, i
+        pos = int(st[i, 98]) | (int(st[i, 99]) << 32)
+        assert pos == (((1 << 20) + i) * J) % (1 << 64), i
+    plan.close()
+
+
+def test_plan_other_seeds_and_resume(rm, table, orc):
+    dev = torch.device("cuda:0")
+    J = 1 << 48
+    plan = rm.Plan(table, J, 300)
+    for s in (1, 54217138, 900000000):
+        base = rm.seed(s).to(dev)
+        a = plan.partition(base, 77, 300)
+        b = table.partition(base, J, 77, 300)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), s
+    # a non-seeded base (an advanced state with its own c and pos)
+    base = table.partition(rm.seed(5).to(dev), 12345, 9, 1)
+    a = plan.partition(base, 2, 300)
+    b = table.partition(base, J, 2, 300)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    plan.close()
+
+
+def test_plan_host_checks(rm, table):
+    dev = torch.device("cuda:0")
+    base = rm.seed(3).to(dev)
+    plan = rm.Plan(table, 1 << 40, 1000)
+    with pytest.raises(rm.RanmarError):
+        plan.partition(base, 0, 1001)                # n > max_n
+    with pytest.raises(rm.RanmarError):
+        plan.partition(base, (1 << 64) - 1, 2)       # k0 + n - 1 overflows
+    with pytest.raises(rm.RanmarError):
+        rm.Plan(table, (1 << 159), 1 << 20)          # 15 16^4 J >= 2^160
+    out = torch.empty((4, 100), dtype=torch.int32, device=dev)
+    with pytest.raises(rm.RanmarError):
+        plan.partition(out[0:1], 0, 4, out=out)      # output overlaps the base
+    plan.close()
