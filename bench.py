@@ -6,8 +6,11 @@ states sit at k*J for J = 2^40, each producing 4,096 consecutive 24-bit
 outputs into a row-per-stream [65,536 x 4,096] uint32 array.  One step is one
 pass of the whole path: the jump of every stream (t^{kJ} mod phi, the
 linear combination of the 97 words, c in closed form) and the generation of
-all 2^28 outputs with the state written back, as one fused launch
-(ranmar_partition_generate_u24); the two-call path is timed beside it.  Inputs are synthetic (the
+all 2^28 outputs with the state written back: 16 streams by the table jump
+(on a side stream, overlapping the previous step's generation), the rest by
+the partition plan's radix-16 levels of jump matrices on the tensor cores,
+then the generation; the fused one-launch path and the two-call path are
+timed beside it.  Inputs are synthetic (the
 paper uses none).  `value` is outputs/s over the whole job.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
@@ -279,35 +282,108 @@ def run_ours(args):
     t_gen = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
     serial_ms = max_over_ranks((sum(t_jump) + sum(t_gen)) / K, dist, dev)
 
-    # ---- timed steps (the measured throughput): one fused launch per step
-    # (ranmar_partition_generate_u24).  Each CTA jumps its 16 streams with the
-    # table and then generates them, so on every SM the integer-bound jumps of
-    # some CTAs overlap the HBM-bound stores of others.  Every step jumps and
-    # generates a fresh batch of streams (k0 advances), states double-buffered.
+    # ---- timed steps (the measured throughput): partition plan + generation.
+    # Per step: the first 16 streams by the table jump (on a high-priority
+    # side stream, so that it runs while the previous step generates), the
+    # other streams by the plan's radix-16 levels of jump matrices on the
+    # tensor cores (ranmar_plan_expand), then the generation of all 2^28
+    # outputs with write-back.  Every step jumps and generates a fresh batch
+    # of streams (k0 advances); states double-buffered.
     bufs = [states, torch.empty_like(states)]
     out2 = out.view(n, count)
-    for j in range(3):
-        table.partition_generate(base, w.J, k0_of(K + j), n, count, states=bufs[j % 2],
-                                 out=out2, stream=stream)
+    tp0 = time.perf_counter()
+    plan = rm.Plan(table, w.J, n)
+    plan_build_ms = (time.perf_counter() - tp0) * 1e3
+    side = torch.cuda.Stream(dev, priority=-1)
+    main_s = torch.cuda.Stream(dev)
+    sD = torch.cuda.Stream(dev)
+
+    def plan_steps(first, steps, d_base=None, h_base=None, d2h=None):
+        evG, evD = [], []
+        for j in range(steps):
+            b = j % 2
+            buf = bufs[b]
+            if j >= 2:
+                side.wait_event(evG[j - 2])          # batch j-2 finished with buf
+            src = base
+            if h_base is not None:                   # end to end: inputs from the host
+                src = d_base[b]
+                with torch.cuda.stream(side):
+                    src.copy_(h_base, non_blocking=True)
+            table.partition(src, w.J, k0_of(first + j), 16, out=buf[:16], stream=side)
+            e = torch.cuda.Event()
+            e.record(side)
+            main_s.wait_event(e)
+            plan.expand(buf, n, stream=main_s)
+            o = out2
+            if d2h is not None:
+                o = d2h[1][b]
+                if j >= 2:
+                    main_s.wait_event(evD[j - 2])    # host copy of batch j-2 done
+            rm.generate_u24(buf, desc, o, stream=main_s)
+            g = torch.cuda.Event()
+            g.record(main_s)
+            evG.append(g)
+            if d2h is not None:
+                sD.wait_event(g)
+                with torch.cuda.stream(sD):
+                    d2h[0][b].copy_(o, non_blocking=True)
+                dd = torch.cuda.Event()
+                dd.record(sD)
+                evD.append(dd)
+        return (evD or evG)[-1]
+
+    torch.cuda.synchronize()
+    plan_steps(K, 3)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for j in range(K):
-        table.partition_generate(base, w.J, k0_of(K + 3 + j), n, count, states=bufs[j % 2],
-                                 out=out2, stream=stream)
-    t1.record(stream)
+    t0.record(side)
+    last = plan_steps(K + 3, K)
+    main_s.wait_event(last)
+    t1.record(main_s)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clk = clocks.stop()
     ms_step = max_over_ranks(t0.elapsed_time(t1) / K, dist, dev)
     value = world * n * count / (ms_step * 1e-3)
+    plan_status = plan.status()
+    # the states of the last timed batch equal the per-stream table jump's
+    # (before their write-back: recompute that batch's start states)
+    chk = plan.partition(base, k0_of(K + 3 + K - 1), n)
+    plan_ok = bool(torch.equal(chk, table.partition(base, w.J, k0_of(K + 3 + K - 1), n)))
+    del chk
+    # expand alone (the tensor-core levels), for the roofline
+    ex0, ex1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    exp_ms = float("inf")
+    for _ in range(5):
+        flush.fill_(7)
+        ex0.record(stream)
+        plan.expand(bufs[0], n, stream=stream)
+        ex1.record(stream)
+        torch.cuda.synchronize()
+        exp_ms = min(exp_ms, ex0.elapsed_time(ex1))
+
+    # ---- the same steps as one fused launch (ranmar_partition_generate_u24:
+    # each CTA jumps its 16 streams with the table, then generates them)
+    for j in range(2):
+        table.partition_generate(base, w.J, k0_of(2 * K + 3 + j), n, count, states=bufs[j % 2],
+                                 out=out2, stream=stream)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for j in range(K):
+        table.partition_generate(base, w.J, k0_of(2 * K + 5 + j), n, count, states=bufs[j % 2],
+                                 out=out2, stream=stream)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_fused = max_over_ranks(f0.elapsed_time(f1) / K, dist, dev)
 
     # ---- the same steps as two calls (table partition on one stream, then
     # generation on another), the jump of batch i+1 overlapping the
-    # generation of batch i; reported beside the fused step.
+    # generation of batch i
     sJ, sG = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
     def pipeline(first, steps):
@@ -327,57 +403,34 @@ def run_ours(args):
         return evG[-1]
 
     torch.cuda.synchronize()
-    pipeline(2 * K + 3, 2)
+    pipeline(3 * K + 5, 2)
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record(sJ)
-    last = pipeline(2 * K + 5, K)
+    last = pipeline(3 * K + 7, K)
     sG.wait_event(last)
     p1.record(sG)
     torch.cuda.synchronize()
     ms_two = max_over_ranks(p0.elapsed_time(p1) / K, dist, dev)
 
     # ---- end to end through the public API with host buffers: every step
-    # copies the seeded base state in from pinned memory, runs the fused call
+    # copies the seeded base state in from pinned memory, runs the plan step
     # and copies the whole 1 GiB result back to pinned memory (copies on their
-    # own stream, double-buffered).
+    # own streams, double-buffered).
     h_base = rm.seed(w.seed).pin_memory()
     d_bases = [torch.empty_like(base), torch.empty_like(base)]
     h_outs = [torch.empty((n, count), dtype=torch.int32).pin_memory() for _ in range(2)]
     d_outs = [out2, torch.empty_like(out2)]
-    sF, sD = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-
-    def e2e_steps(first, steps):
-        evF, evD = [], []
-        for j in range(steps):
-            b = j % 2
-            if j >= 2:
-                sF.wait_event(evD[j - 2])          # host copy of batch j-2 done
-            with torch.cuda.stream(sF):
-                d_bases[b].copy_(h_base, non_blocking=True)
-            table.partition_generate(d_bases[b], w.J, k0_of(first + j), n, count,
-                                     states=bufs[b], out=d_outs[b], stream=sF)
-            f = torch.cuda.Event()
-            f.record(sF)
-            evF.append(f)
-            sD.wait_event(f)
-            with torch.cuda.stream(sD):
-                h_outs[b].copy_(d_outs[b], non_blocking=True)
-            dd = torch.cuda.Event()
-            dd.record(sD)
-            evD.append(dd)
-        return evD[-1]
-
     n_e2e = max(3, min(K, 10))
-    e2e_steps(3 * K + 5, 2)
+    plan_steps(4 * K + 7, 2, d_bases, h_base, (h_outs, d_outs))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(sF)
-    last = e2e_steps(3 * K + 7, n_e2e)
-    sF.wait_event(last)
-    e1.record(sF)
+    e0.record(side)
+    last = plan_steps(4 * K + 9, n_e2e, d_bases, h_base, (h_outs, d_outs))
+    side.wait_event(last)
+    e1.record(side)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1) / n_e2e, dist, dev)
     lastb = (n_e2e - 1) % 2
@@ -441,43 +494,44 @@ def run_ours(args):
                  "algorithmic_macs": jmacs,
                  "traffic": tj["bytes_per_launch"] if tj else None,
                  "avg_launch_ms": jump_ms}
-    # the fused kernel of the timed steps: HBM-store bound (outputs + final
-    # states), with its multiply-adds reported beside
-    exps_f = [(k0_of(K + 3 + j) + q) * w.J for j in range(K) for q in range(0, n, 97)]
-    fmacs = table_macs(exps_f) * n / (len(exps_f) / K) / K
+    # the tensor-core levels of the plan: algorithmic work = the 97 x 97
+    # multiply-adds of every derived stream, as the fp16 tensor FLOPs of the
+    # six limb products (2 x 6 x 97 x 97 per stream)
+    n_derived = n - 16
+    plan_flops = 2.0 * 6 * 97 * 97 * n_derived
+    tc_peak = peaks.get("bf16_tflops", 1900.0)
+    roof_plan = {"kernel": "plan_level_mma_kernel (3 radix-16 levels, tcgen05, fp16 limbs)",
+                 "bound": "tensor", "achieved": plan_flops / (exp_ms * 1e-3) / 1e12,
+                 "peak": tc_peak, "unit": "TFLOP/s",
+                 "frac": plan_flops / (exp_ms * 1e-3) / 1e12 / tc_peak,
+                 "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops); "
+                                "fp16 has the same nominal dense rate",
+                 "algorithmic_flops": plan_flops, "traffic": None, "avg_launch_ms": exp_ms,
+                 "note": "three dependent launches, latency-bound at this size"}
     fused_bytes = n * count * 4 + n * 400
-    fused_sha = source_sha("jump.cuh", "jump_table.cuh", "generate.cuh", "partition_generate.cuh",
-                           "ranmar_device.cuh")
-    tf = traffic_for("partition_generate_kernel", fused_sha)
-    roof_fused = {"kernel": "partition_generate_kernel<u24> (table jump + generation, fused)",
-                  "bound": "hbm",
-                  "achieved": fused_bytes / (ms_step * 1e-3) / 1e9, "peak": hbm_peak,
-                  "unit": "GB/s", "frac": fused_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak,
-                  "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                  "algorithmic_bytes": fused_bytes,
-                  "traffic": tf["bytes_per_launch"] if tf else None,
-                  "avg_launch_ms": ms_step,
-                  "alu": {"algorithmic_macs": fmacs,
-                          "achieved": fmacs / (ms_step * 1e-3) / 1e12, "peak": alu_peak,
-                          "unit": "Tmul-add/s",
-                          "frac": fmacs / (ms_step * 1e-3) / 1e12 / alu_peak}}
-
+    roof_fused = {"kernel": "partition_generate_kernel<u24>", "bound": "hbm",
+                  "ms": ms_fused, "frac": fused_bytes / (ms_fused * 1e-3) / 1e9 / hbm_peak}
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": f"partitioned: seed 12345, {n} streams per step at k*2^40 "
                                f"(step i of rank r: k = (i*N + r)*{n} + 0..{n - 1}), 4096 u24 "
-                               "outputs each, write-back; step = one fused launch: table "
-                               "jump of every stream + generation",
+                               "outputs each, write-back; step = table jump of 16 streams + "
+                               "radix-16 jump-matrix levels (tensor cores) for the rest + "
+                               "generation",
                    "streams_per_gpu": n, "outputs_per_stream": count, "J": "2^40",
                    "l2": "inputs/outputs larger than L2: every step writes 1.07 GB (8x L2); "
                          "the serial per-kernel timing flushes L2 (258 MB write) between steps"},
         "serial_ms_per_step": serial_ms,
         "serial_outputs_per_s": world * n * count / (serial_ms * 1e-3),
+        "fused_ms_per_step": ms_fused, "fused_outputs_per_s": world * n * count / (ms_fused * 1e-3),
         "two_kernel_pipelined_ms_per_step": ms_two,
         "two_kernel_outputs_per_s": world * n * count / (ms_two * 1e-3),
-        "roofline": roof_fused, "roofline_generate": roof_gen, "roofline_jump": roof_jump,
+        "roofline": roof_gen, "roofline_plan": roof_plan, "roofline_generate": roof_gen,
+        "roofline_jump": roof_jump, "roofline_fused": roof_fused,
+        "plan": {"build_ms": plan_build_ms, "expand_ms": exp_ms, "status": plan_status,
+                 "states_identical_to_table_jump": plan_ok},
         "jump_ms": jump_ms, "generate_ms": gen_ms,
         "jumps_per_s": n / (jump_ms * 1e-3),
         "jump_method": "fixed-base table (8-bit windows, shared by all streams)",
@@ -492,10 +546,10 @@ def run_ours(args):
         "e2e": {"value": world * n * count / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 400, "d2h_bytes_per_step": n * count * 4,
                 "ms_per_step": ms_e2e, "checked": ok_e2e,
-                "note": "the fused binding call with the base state from pinned host memory "
-                        "and the whole result copied to pinned host memory every step "
-                        "(copies on their own stream, double-buffered)"},
-        "gpu_launches": K,
+                "note": "the plan step through the binding, with the base state from pinned "
+                        "host memory and the whole result copied to pinned host memory every "
+                        "step (copies on their own streams, double-buffered)"},
+        "gpu_launches": 5 * K,
         "library": rbuild.LIB,
     }
 

@@ -58,6 +58,8 @@ extern "C" {
 #define RANMAR_ST_BAD_INDEX 1u    /* state or base index out of range       */
 #define RANMAR_ST_OUT_RANGE 2u    /* out_offset + count beyond out_len      */
 #define RANMAR_ST_BAD_SEED 4u     /* seed outside 1..900000000              */
+#define RANMAR_ST_TIMEOUT 8u      /* a bounded device wait ran out (the CTA  */
+                                  /* left its work undone and returned)      */
 
 /* Descriptor flags. */
 #define RANMAR_DESC_WRITE_BACK 1u /* store the advanced state after output  */
@@ -316,6 +318,34 @@ int ranmar_plan_destroy(ranmar_plan_t *p);
  */
 int ranmar_partition_plan(const ranmar_plan_t *p, const ranmar_state_t *d_base, uint64_t k0,
                           size_t n, ranmar_state_t *d_out, ranmar_stream_t stream);
+
+/*
+ * ranmar_plan_expand -- the levels of ranmar_partition_plan alone: given
+ * d_states[i] = f^{(k0+i) J}(base) for i < 16 (any k0, e.g. from
+ * ranmar_partition_tab on another stream), fills d_states[16 .. n).  A no-op
+ * for n <= 16.  Errors: RANMAR_EINVAL (null pointer, misalignment, plan of
+ * another device), RANMAR_ERANGE (n > max_n).
+ */
+int ranmar_plan_expand(const ranmar_plan_t *p, ranmar_state_t *d_states, size_t n,
+                       ranmar_stream_t stream);
+
+/*
+ * How the plan's levels multiply (same results either way):
+ *   RANMAR_PLAN_TENSOR (default): tcgen05 MMAs on fp16 limbs -- every 24-bit
+ *     word split into three balanced 8-bit limbs (exact in fp16), the limb
+ *     products accumulated exactly in fp32 in tensor memory and recombined
+ *     mod 2^24; operands staged in shared memory (the matrix by a bulk async
+ *     copy);
+ *   RANMAR_PLAN_IMAD: blocked 32-bit integer multiply-adds.
+ * ranmar_plan_set_method: RANMAR_EINVAL for an unknown method.
+ * ranmar_plan_status: device pointer to the plan's status word (bit
+ * RANMAR_ST_TIMEOUT if a tensor-core level gave up on a bounded wait; then
+ * the states it was to write are not valid).  Cleared at plan creation.
+ */
+#define RANMAR_PLAN_TENSOR 0
+#define RANMAR_PLAN_IMAD 1
+int ranmar_plan_set_method(ranmar_plan_t *p, int method);
+int ranmar_plan_status(const ranmar_plan_t *p, uint32_t **d_status);
 
 /*
  * ranmar_partition_generate_u24 / ranmar_partition_generate_f32 -- stream

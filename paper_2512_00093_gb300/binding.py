@@ -91,6 +91,10 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_plan_destroy.argtypes = [_vp]
     lib.ranmar_partition_plan.argtypes = [_vp, _vp, _u64, _sz, _vp, _vp]
     lib.ranmar_partition_plan.restype = ctypes.c_int
+    lib.ranmar_plan_set_method.argtypes = [_vp, ctypes.c_int]
+    lib.ranmar_plan_expand.argtypes = [_vp, _vp, _sz, _vp]
+    lib.ranmar_plan_expand.restype = ctypes.c_int
+    lib.ranmar_plan_status.argtypes = [_vp, ctypes.POINTER(_vp)]
     lib.ranmar_table_set_ctas_per_sm.argtypes = [_vp, ctypes.c_int]
     lib.ranmar_table_set_ctas_per_sm.restype = ctypes.c_int
     lib.ranmar_jump_tab.argtypes = [_vp, _vp, _sz, _vp, _vp, _u32, _vp, _sz, _vp, _sz, _vp, _vp]
@@ -679,6 +683,28 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    TENSOR, IMAD = 0, 1
+
+    def set_method(self, method: int) -> None:
+        """ranmar_plan_set_method (Plan.TENSOR or Plan.IMAD)."""
+        _check(_lib().ranmar_plan_set_method(self._h, int(method)), "ranmar_plan_set_method")
+
+    def status(self) -> int:
+        """The plan's device status word (synchronises the device)."""
+        p = ctypes.c_void_p()
+        _check(_lib().ranmar_plan_status(self._h, ctypes.byref(p)), "ranmar_plan_status")
+        torch.cuda.synchronize()
+        return int(_wrap_device_ptr(p.value, 1).item())
+
+    def expand(self, states: torch.Tensor, n: int, stream=None) -> torch.Tensor:
+        """ranmar_plan_expand: states[0..16) given, states[16..n) filled."""
+        _need(states, torch.int32, "states")
+        if states.numel() < n * STATE_WORDS:
+            raise ValueError("states too small")
+        _check(_lib().ranmar_plan_expand(self._h, _ptr(states), int(n), _stream(stream)),
+               "ranmar_plan_expand")
+        return states
 
     def partition(self, base: torch.Tensor, k0: int, n: int, out=None,
                   stream=None) -> torch.Tensor:

@@ -16,6 +16,7 @@
 #include "jump_table.cuh"
 #include "partition_generate.cuh"
 #include "plan.cuh"
+#include "plan_mma.cuh"
 
 // Batch handle: the workspace of the persistent path on one device.
 struct ranmar_batch {
@@ -47,8 +48,12 @@ struct ranmar_plan {
   size_t max_n;
   int levels;          // level t turns 16^(t+1) known streams into 16^(t+2)
   uint32_t* mats;      // levels x 15 x 97 x 112: M_{r 16^(t+1) J}
+  uint8_t* bimg;       // levels x 15 fp16 limb images of the same matrices
   uint32_t* ced;       // levels x 15: (E mod m) d mod m
   uint64_t* pose;      // levels x 15: E mod 2^64
+  uint32_t* status;    // device status word of the tensor-core levels
+  int method;          // RANMAR_PLAN_TENSOR or RANMAR_PLAN_IMAD
+  int num_sms;
 };
 
 struct ranmar_graph {
@@ -918,6 +923,21 @@ int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_
   p->J_words = J_words;
   p->max_n = max_n;
   p->levels = levels;
+  p->method = RANMAR_PLAN_TENSOR;
+  {
+    cudaError_t e0 = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e0 == cudaSuccess) e0 = cudaMalloc(&p->status, sizeof(uint32_t));
+    if (e0 == cudaSuccess) e0 = cudaMemset(p->status, 0, sizeof(uint32_t));
+    if (e0 != cudaSuccess) {
+      cudaFree(p->status);
+      delete p;
+      if (e0 == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return RANMAR_ENOMEM;
+      }
+      return cuda_fail(e0);
+    }
+  }
   if (levels == 0) {
     *out = p;
     return RANMAR_OK;
@@ -968,6 +988,11 @@ int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_
   cudaError_t e = cudaSuccess;
   if (rc == RANMAR_OK) {
     e = cudaMalloc(&p->mats, nrows * ranmar::kPlanCols * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&p->bimg, static_cast<size_t>(nmat) * ranmar::kBImgBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ranmar::plan_level_mma_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(ranmar::kMmaSmemBytes));
     if (e == cudaSuccess) e = cudaMalloc(&p->ced, nmat * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->pose, nmat * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMalloc(&dunit, RANMAR_R * sizeof(ranmar_state_t));
@@ -1001,6 +1026,11 @@ int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_
       ranmar::plan_pack_kernel<<<1024, 128, 0, s>>>(djumped, p->mats, nrows);
       e = cudaGetLastError();
     }
+    if (e == cudaSuccess) {
+      ranmar::plan_bimg_kernel<<<1024, 256, 0, s>>>(djumped, p->bimg,
+                                                    static_cast<uint32_t>(nmat));
+      e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (s) cudaStreamDestroy(s);
     if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? RANMAR_ENOMEM : cuda_fail(e);
@@ -1016,8 +1046,10 @@ int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_
   delete[] hunit;
   if (rc != RANMAR_OK) {
     cudaFree(p->mats);
+    cudaFree(p->bimg);
     cudaFree(p->ced);
     cudaFree(p->pose);
+    cudaFree(p->status);
     delete p;
     if (rc == RANMAR_ENOMEM) cudaGetLastError();
     return rc;
@@ -1032,10 +1064,59 @@ int ranmar_plan_destroy(ranmar_plan_t* p) {
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
   cudaFree(p->mats);
+  cudaFree(p->bimg);
   cudaFree(p->ced);
   cudaFree(p->pose);
+  cudaFree(p->status);
   if (prev >= 0) cudaSetDevice(prev);
   delete p;
+  return RANMAR_OK;
+}
+
+int ranmar_plan_set_method(ranmar_plan_t* p, int method) {
+  if (!p || (method != RANMAR_PLAN_TENSOR && method != RANMAR_PLAN_IMAD)) return RANMAR_EINVAL;
+  p->method = method;
+  return RANMAR_OK;
+}
+
+int ranmar_plan_status(const ranmar_plan_t* p, uint32_t** d_status) {
+  if (!p || !d_status) return RANMAR_EINVAL;
+  *d_status = p->status;
+  return RANMAR_OK;
+}
+
+int ranmar_plan_expand(const ranmar_plan_t* p, ranmar_state_t* d_states, size_t n,
+                       ranmar_stream_t stream) {
+  if (!p) return RANMAR_EINVAL;
+  if (n <= static_cast<size_t>(ranmar::kPlanBase)) return RANMAR_OK;
+  if (!d_states) return RANMAR_EINVAL;
+  if (n > p->max_n) return RANMAR_ERANGE;
+  if (!aligned(d_states, 16)) return RANMAR_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return RANMAR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint64_t R = ranmar::kPlanBase;
+  for (int tl = 0; tl < p->levels && R < n; ++tl, R *= ranmar::kPlanRadix) {
+    if (p->method == RANMAR_PLAN_TENSOR) {
+      // items (tile, r): tiles of 128 source rows, r = 1..r_count with r R < n
+      const uint64_t tiles = (R + ranmar::kMmaM - 1) / ranmar::kMmaM;
+      const uint64_t rc = (n - 1) / R < 15 ? (n - 1) / R : 15;
+      const uint64_t items = tiles * rc;
+      const unsigned grid = static_cast<unsigned>(
+          items < static_cast<uint64_t>(p->num_sms) ? items : static_cast<uint64_t>(p->num_sms));
+      ranmar::plan_level_mma_kernel<<<grid, ranmar::kMmaThreads, ranmar::kMmaSmemBytes, s>>>(
+          d_states, R, n, static_cast<uint32_t>(rc), static_cast<uint32_t>(items),
+          p->bimg + static_cast<size_t>(tl) * 15 * ranmar::kBImgBytes, p->ced + tl * 15,
+          p->pose + tl * 15, p->status);
+    } else {
+      const dim3 grid(static_cast<unsigned>((R + ranmar::kPlanRows - 1) / ranmar::kPlanRows), 15);
+      ranmar::plan_level_kernel<<<grid, ranmar::kPlanThreads, ranmar::kPlanSmemBytes, s>>>(
+          d_states, R, n, p->mats + static_cast<size_t>(tl) * 15 * RANMAR_R * ranmar::kPlanCols,
+          p->ced + tl * 15, p->pose + tl * 15);
+    }
+    const int lr = check_launch();
+    if (lr != RANMAR_OK) return lr;
+  }
   return RANMAR_OK;
 }
 
@@ -1054,20 +1135,10 @@ int ranmar_partition_plan(const ranmar_plan_t* p, const ranmar_state_t* d_base, 
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return RANMAR_EINVAL;
   const size_t n0 = n < static_cast<size_t>(ranmar::kPlanBase) ? n : ranmar::kPlanBase;
-  int jr = launch_jump_table(p->table, d_base, 1, nullptr, nullptr, 0, part, 1, d_out, n0, nullptr,
-                             stream, nullptr, n0);
+  const int jr = launch_jump_table(p->table, d_base, 1, nullptr, nullptr, 0, part, 1, d_out, n0,
+                                   nullptr, stream, nullptr, n0);
   if (jr != RANMAR_OK) return jr;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  uint64_t R = ranmar::kPlanBase;
-  for (int tl = 0; tl < p->levels && R < n; ++tl, R *= ranmar::kPlanRadix) {
-    const dim3 grid(static_cast<unsigned>((R + ranmar::kPlanRows - 1) / ranmar::kPlanRows), 15);
-    ranmar::plan_level_kernel<<<grid, ranmar::kPlanThreads, ranmar::kPlanSmemBytes, s>>>(
-        d_out, R, n, p->mats + static_cast<size_t>(tl) * 15 * RANMAR_R * ranmar::kPlanCols,
-        p->ced + tl * 15, p->pose + tl * 15);
-    const int lr = check_launch();
-    if (lr != RANMAR_OK) return lr;
-  }
-  return RANMAR_OK;
+  return ranmar_plan_expand(p, d_out, n, stream);
 }
 
 int ranmar_generate_alg1_f32(ranmar_state_t* d_states, size_t n_states,

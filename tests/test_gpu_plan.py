@@ -23,11 +23,13 @@ def table(rm):
     t.close()
 
 
+@pytest.mark.parametrize("method", ["tensor", "imad"])
 @pytest.mark.parametrize("J", [1 << 40, (1 << 64) + 12345, (1 << 120) + 12345])
-def test_plan_equals_table_partition(rm, table, orc, J):
+def test_plan_equals_table_partition(rm, table, orc, J, method):
     dev = torch.device("cuda:0")
     base = rm.seed(12345).to(dev)
     plan = rm.Plan(table, J, 70000)
+    plan.set_method(rm.Plan.TENSOR if method == "tensor" else rm.Plan.IMAD)
     for n, k0 in [(1, 0), (15, 3), (16, 0), (17, 9), (255, 1), (256, 0), (257, 4),
                   (4095, 7), (4097, 0), (65536, 123), (70000, 1 << 20)]:
         a = plan.partition(base, k0, n)
@@ -42,6 +44,7 @@ def test_plan_equals_table_partition(rm, table, orc, J):
         assert np.array_equal(st[i, :97], xr) and st[i, 97] == cr, i
         pos = int(st[i, 98]) | (int(st[i, 99]) << 32)
         assert pos == (((1 << 20) + i) * J) % (1 << 64), i
+    assert plan.status() == 0
     plan.close()
 
 
@@ -77,4 +80,27 @@ def test_plan_host_checks(rm, table):
     out = torch.empty((4, 100), dtype=torch.int32, device=dev)
     with pytest.raises(rm.RanmarError):
         plan.partition(out[0:1], 0, 4, out=out)      # output overlaps the base
+    with pytest.raises(rm.RanmarError):
+        plan.set_method(7)
+    plan.close()
+
+
+def test_plan_expand_from_table_rows(rm, table):
+    """expand() from 16 rows computed elsewhere (the table partition on
+    another stream) gives the same states as one partition_plan call."""
+    dev = torch.device("cuda:0")
+    J = 1 << 40
+    base = rm.seed(12345).to(dev)
+    plan = rm.Plan(table, J, 5000)
+    side = torch.cuda.Stream(dev)
+    st = torch.empty((5000, 100), dtype=torch.int32, device=dev)
+    table.partition(base, J, 99, 16, out=st[:16], stream=side)
+    ev = torch.cuda.Event()
+    ev.record(side)
+    torch.cuda.current_stream().wait_event(ev)
+    plan.expand(st, 5000)
+    ref = plan.partition(base, 99, 5000)
+    torch.cuda.synchronize()
+    assert torch.equal(st, ref)
+    assert plan.status() == 0
     plan.close()
