@@ -6,9 +6,9 @@ states sit at k*J for J = 2^40, each producing 4,096 consecutive 24-bit
 outputs into a row-per-stream [65,536 x 4,096] uint32 array.  One step is one
 pass of the whole path: the jump of every stream (t^{kJ} mod phi, the
 linear combination of the 97 words, c in closed form) and the generation of
-all 2^28 outputs with the state written back: 16 streams by the table jump
+all 2^28 outputs with the state written back: 256 streams by the table jump
 (on a side stream, overlapping the previous step's generation), the rest by
-the partition plan's radix-16 levels of jump matrices on the tensor cores,
+the partition plan's radix-256 level of jump matrices on the tensor cores,
 then the generation; the fused one-launch path and the two-call path are
 timed beside it.  Inputs are synthetic (the
 paper uses none).  `value` is outputs/s over the whole job.
@@ -61,7 +61,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--serve-seconds", type=float, default=5.0,
                    help="duration of the serving run (the recipe's full run is 60 s)")
-    p.add_argument("--case", choices=["partitioned", "uneven", "large"], default="partitioned",
+    p.add_argument("--case", choices=["partitioned", "uneven", "large", "plan"],
+                   default="partitioned",
                    help="partitioned = the benchmark; uneven / large run only that workload's "
                         "step (for profiling) and print a line for it")
     p.add_argument("--streams", type=int, default=65536,
@@ -283,18 +284,18 @@ def run_ours(args):
     serial_ms = max_over_ranks((sum(t_jump) + sum(t_gen)) / K, dist, dev)
 
     # ---- timed steps (the measured throughput): partition plan + generation.
-    # Per step: the first 16 streams by the table jump (on a high-priority
-    # side stream, so that it runs while the previous step generates), the
-    # other streams by the plan's radix-16 levels of jump matrices on the
-    # tensor cores (ranmar_plan_expand), then the generation of all 2^28
-    # outputs with write-back.  Every step jumps and generates a fresh batch
+    # Per step: the first 256 streams by the table jump (on a side stream, so
+    # that it runs while the previous step generates), the
+    # other 65,280 by one radix-256 level of jump matrices on the tensor cores
+    # (ranmar_plan_expand), then the generation of all 2^28 outputs with
+    # write-back.  Every step jumps and generates a fresh batch
     # of streams (k0 advances); states double-buffered.
     bufs = [states, torch.empty_like(states)]
     out2 = out.view(n, count)
     tp0 = time.perf_counter()
     plan = rm.Plan(table, w.J, n)
     plan_build_ms = (time.perf_counter() - tp0) * 1e3
-    side = torch.cuda.Stream(dev, priority=-1)
+    side = torch.cuda.Stream(dev)   # default priority: measured faster than high
     main_s = torch.cuda.Stream(dev)
     sD = torch.cuda.Stream(dev)
 
@@ -310,7 +311,8 @@ def run_ours(args):
                 src = d_base[b]
                 with torch.cuda.stream(side):
                     src.copy_(h_base, non_blocking=True)
-            table.partition(src, w.J, k0_of(first + j), 16, out=buf[:16], stream=side)
+            nb = min(rm.Plan.BASE, n)
+            table.partition(src, w.J, k0_of(first + j), nb, out=buf[:nb], stream=side)
             e = torch.cuda.Event()
             e.record(side)
             main_s.wait_event(e)
@@ -497,17 +499,17 @@ def run_ours(args):
     # the tensor-core levels of the plan: algorithmic work = the 97 x 97
     # multiply-adds of every derived stream, as the fp16 tensor FLOPs of the
     # six limb products (2 x 6 x 97 x 97 per stream)
-    n_derived = n - 16
+    n_derived = max(0, n - rm.Plan.BASE)
     plan_flops = 2.0 * 6 * 97 * 97 * n_derived
     tc_peak = peaks.get("bf16_tflops", 1900.0)
-    roof_plan = {"kernel": "plan_level_mma_kernel (3 radix-16 levels, tcgen05, fp16 limbs)",
+    roof_plan = {"kernel": "plan_level_mma_kernel (radix-256 level, tcgen05, fp16 limbs)",
                  "bound": "tensor", "achieved": plan_flops / (exp_ms * 1e-3) / 1e12,
                  "peak": tc_peak, "unit": "TFLOP/s",
                  "frac": plan_flops / (exp_ms * 1e-3) / 1e12 / tc_peak,
                  "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops); "
                                 "fp16 has the same nominal dense rate",
                  "algorithmic_flops": plan_flops, "traffic": None, "avg_launch_ms": exp_ms,
-                 "note": "three dependent launches, latency-bound at this size"}
+                 "note": "one launch (510 tiles x matrices over 152 SMs)"}
     fused_bytes = n * count * 4 + n * 400
     roof_fused = {"kernel": "partition_generate_kernel<u24>", "bound": "hbm",
                   "ms": ms_fused, "frac": fused_bytes / (ms_fused * 1e-3) / 1e9 / hbm_peak}
@@ -517,8 +519,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": f"partitioned: seed 12345, {n} streams per step at k*2^40 "
                                f"(step i of rank r: k = (i*N + r)*{n} + 0..{n - 1}), 4096 u24 "
-                               "outputs each, write-back; step = table jump of 16 streams + "
-                               "radix-16 jump-matrix levels (tensor cores) for the rest + "
+                               "outputs each, write-back; step = table jump of 256 streams + "
+                               "one radix-256 jump-matrix level (tensor cores) for the rest + "
                                "generation",
                    "streams_per_gpu": n, "outputs_per_stream": count, "J": "2^40",
                    "l2": "inputs/outputs larger than L2: every step writes 1.07 GB (8x L2); "
@@ -549,7 +551,7 @@ def run_ours(args):
                 "note": "the plan step through the binding, with the base state from pinned "
                         "host memory and the whole result copied to pinned host memory every "
                         "step (copies on their own streams, double-buffered)"},
-        "gpu_launches": 5 * K,
+        "gpu_launches": 3 * K,
         "library": rbuild.LIB,
     }
 
@@ -759,13 +761,13 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
         same = bool(torch.equal(plan.partition(pbase, 0, pw.n_streams),
                                 table.partition(pbase, pw.J, 0, pw.n_streams)))
         levels = {str(m): timed(lambda m=m: plan.partition(pbase, 0, m, out=pst))
-                  for m in (16, 256, 4096)}
+                  for m in (256, 4096)}
         res["partition_plan"] = {
             "streams": pw.n_streams, "build_ms": plan_build, "ms": ms_p,
             "table_jump_ms": ms_t, "states_identical": same,
             "ms_for_first_streams": levels,
             "macs_per_stream": 97 * 97,
-            "note": "16 streams by the table jump, then 3 levels x -> x M_{r 16^(t+1) J}"}
+            "note": "256 streams by the table jump, then one level x -> x M_{r 256 J}"}
         plan.close()
         del pst
     except Exception as e:  # noqa: BLE001
@@ -836,14 +838,25 @@ def serving(rm, torch, seconds):
 def run_case(args):
     """One workload's step only (jump + generate), for profiling: uneven =
     persistent batch kernel on log-uniform lengths, large = J = 2^120 + 12345
-    (square-and-multiply and table jumps, 1,024 outputs each)."""
+    (square-and-multiply and table jumps, 1,024 outputs each), plan = the
+    partition plan of the partitioned workload alone (256 table jumps + the
+    tensor-core level, no generation)."""
     import torch
     import paper_2512_00093_gb300 as rm
     from paper_2512_00093_gb300.workloads import BatchedUneven, LargeJumps
     dev = torch.device("cuda", 0)
     n = args.streams
     table = rm.Table()
-    if args.case == "uneven":
+    if args.case == "plan":
+        from paper_2512_00093_gb300.workloads import Partitioned
+        w = Partitioned()
+        base = rm.seed(w.seed).to(dev)
+        plan = rm.Plan(table, w.J, n)
+        states = torch.empty((n, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+
+        def step():
+            plan.partition(base, 0, n, out=states)
+    elif args.case == "uneven":
         w = BatchedUneven()
         lens = w.lengths(n)
         base = rm.seed(w.seed).to(dev)

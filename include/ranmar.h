@@ -289,16 +289,19 @@ int ranmar_partition_ex(const ranmar_table_t *t, const ranmar_state_t *d_base,
  * jump matrices.  The x part of a jump is linear over Z/2^24 (x' = x A^E,
  * Sec. 3.1), so the jump of many states by one fixed E is one matrix
  * product; row i of the 97x97 matrix M_E is the x part of the unit state
- * e_i jumped by E (the polynomial method of Sec. 3.1, via the table).  A
- * plan holds M_E for E = r 16^(t+1) J, r = 1..15, t < levels (levels =
- * ceil(log16(max_n / 16))), about 0.65 MB per level on the device.
+ * e_i jumped by E (the polynomial method of Sec. 3.1, via the table).  The
+ * first 256 streams are jumped directly; level 0 takes them to 65,536
+ * (radix 256), each later level multiplies the count by 16.  A plan holds
+ * M_E for E = r R_t J (R_t = streams known before level t, r = 1 .. radix-1)
+ * for the levels max_n needs: 255 matrices (19 MB of device images) for
+ * max_n <= 65,536, 15 more per further level.
  *
  * ranmar_plan_create: builds the matrices on the current device (which must
  * be the table's) and returns when they are ready (synchronous).  The plan
  * keeps a pointer to *t, which must outlive it.  Errors: RANMAR_EINVAL
  * (null pointer, table of another device), RANMAR_ERANGE (J_words not in
- * 1..5, max_n not in 1..2^32, 15 16^levels J >= 2^160), RANMAR_ENOMEM,
- * RANMAR_ECUDA.
+ * 1..5, max_n not in 1..2^32, r R_t J >= 2^160 for a needed matrix),
+ * RANMAR_ENOMEM, RANMAR_ECUDA.
  */
 typedef struct ranmar_plan ranmar_plan_t;
 int ranmar_plan_create(const ranmar_table_t *t, const uint32_t *h_J, uint32_t J_words,
@@ -307,24 +310,24 @@ int ranmar_plan_destroy(ranmar_plan_t *p);
 
 /*
  * ranmar_partition_plan -- the same states as ranmar_partition with the
- * plan's J: d_out[i] = f^{(k0+i) J}(*d_base), i < n <= max_n.  The first 16
- * streams are jumped directly with the table; then level t derives streams
- * r 16^(t+1) + i from streams i < 16^(t+1) by x <- x M_{r 16^(t+1) J} (one
- * blocked integer GEMM per level, 9,409 multiply-adds per stream against a
- * matrix shared by all streams of the level), c by the closed form of
- * Sec. 3.2.  Asynchronous on `stream`.  Errors: RANMAR_EINVAL (null
- * pointer, misalignment, d_out overlapping *d_base, plan of another
- * device), RANMAR_ERANGE (n > max_n, (k0 + n - 1) J >= 2^160).
+ * plan's J: d_out[i] = f^{(k0+i) J}(*d_base), i < n <= max_n.  The first
+ * 256 streams are jumped directly with the table; then each level derives
+ * streams r R + i from streams i < R by x <- x M_{rRJ} (one dense GEMM per
+ * level, 9,409 multiply-adds per stream against a matrix shared by all R
+ * streams), c by the closed form of Sec. 3.2.  Asynchronous on `stream`.
+ * Errors: RANMAR_EINVAL (null pointer, misalignment, d_out overlapping
+ * *d_base, plan of another device), RANMAR_ERANGE (n > max_n,
+ * (k0 + n - 1) J >= 2^160).
  */
 int ranmar_partition_plan(const ranmar_plan_t *p, const ranmar_state_t *d_base, uint64_t k0,
                           size_t n, ranmar_state_t *d_out, ranmar_stream_t stream);
 
 /*
  * ranmar_plan_expand -- the levels of ranmar_partition_plan alone: given
- * d_states[i] = f^{(k0+i) J}(base) for i < 16 (any k0, e.g. from
- * ranmar_partition_tab on another stream), fills d_states[16 .. n).  A no-op
- * for n <= 16.  Errors: RANMAR_EINVAL (null pointer, misalignment, plan of
- * another device), RANMAR_ERANGE (n > max_n).
+ * d_states[i] = f^{(k0+i) J}(base) for i < 256 (any k0, e.g. from
+ * ranmar_partition_tab on another stream), fills d_states[256 .. n).  A
+ * no-op for n <= 256.  Errors: RANMAR_EINVAL (null pointer, misalignment,
+ * plan of another device), RANMAR_ERANGE (n > max_n).
  */
 int ranmar_plan_expand(const ranmar_plan_t *p, ranmar_state_t *d_states, size_t n,
                        ranmar_stream_t stream);

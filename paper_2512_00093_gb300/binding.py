@@ -661,8 +661,11 @@ class Table:
 
 
 class Plan:
-    """ranmar_plan_t: jump matrices M_{r 16^(t+1) J} for partitions of block
-    length J into up to max_n streams (built on the table's device)."""
+    """ranmar_plan_t: jump matrices M_{r R_t J} for partitions of block length
+    J into up to max_n streams (built on the table's device): 256 streams
+    jumped directly, then levels of radix 256, 16, 16, ..."""
+
+    BASE = 256
 
     def __init__(self, table: "Table", J: int, max_n: int):
         jw = np.array(words(int(J)), dtype=np.uint32)
@@ -698,7 +701,7 @@ class Plan:
         return int(_wrap_device_ptr(p.value, 1).item())
 
     def expand(self, states: torch.Tensor, n: int, stream=None) -> torch.Tensor:
-        """ranmar_plan_expand: states[0..16) given, states[16..n) filled."""
+        """ranmar_plan_expand: states[0..256) given, states[256..n) filled."""
         _need(states, torch.int32, "states")
         if states.numel() < n * STATE_WORDS:
             raise ValueError("states too small")

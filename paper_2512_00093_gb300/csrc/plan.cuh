@@ -1,13 +1,14 @@
-// plan.cuh -- stream partitioning (Sec. 1) by radix-16 levels of jump
-// matrices: one dense contraction per level.
+// plan.cuh -- stream partitioning (Sec. 1) by levels of jump matrices: one
+// dense contraction per level.
 //
 // The x part of a jump is linear over Z/2^24 (x' = x A^E, Sec. 3.1), so a
 // jump by a fixed E of many states is one matrix product X' = X M_E, where
 // row i of the 97x97 matrix M_E is the x part of the unit state e_i jumped
 // by E (computed once, with the polynomial method).  For the streams
-// k = k0 + i, i < n, of one base state: the first 16 are jumped directly
-// (the fixed-base table), and level t (R = 16^(t+1) streams known) derives
-// streams r R + i (r = 1..15, i < R) as
+// k = k0 + i, i < n, of one base state: the first 256 are jumped directly
+// (the fixed-base table), and a level with R streams known and radix rho
+// (256 for the first level, 16 after) derives streams r R + i (r = 1 ..
+// rho - 1, i < R) as
 //     x_{k0 + rR + i} = x_{k0 + i} M_{rRJ},   c by the closed form (Sec. 3.2),
 // so every stream costs one 97x97 vector-matrix product (9,409 multiply-
 // adds) against a matrix shared by R streams: a blocked GEMM on the integer
@@ -24,8 +25,13 @@
 
 namespace ranmar {
 
-constexpr int kPlanRadix = 16;
-constexpr int kPlanBase = 16;       // streams jumped directly
+constexpr int kPlanBase = 256;      // streams jumped directly (the table jump)
+constexpr int kPlanRadix0 = 256;    // first level: 256 -> 65,536 streams
+constexpr int kPlanRadix = 16;      // later levels
+constexpr int kPlanMaxLevels = 8;
+
+// Radix of level t.
+__host__ __device__ constexpr int plan_radix(int t) { return t == 0 ? kPlanRadix0 : kPlanRadix; }
 constexpr int kPlanRows = 128;      // source rows per CTA
 constexpr int kPlanCols = 112;      // 97 output words, zero padded (16 x 7)
 constexpr int kPlanAStride = 132;   // words per k of the transposed source rows
@@ -44,7 +50,7 @@ __global__ void plan_pack_kernel(const ranmar_state_t* __restrict__ unit_jumped,
 
 // One level: for r = blockIdx.y + 1 and source rows i = blockIdx.x * 128 +
 // (0..127) < R, st[rR + i] = st[i] advanced by E_r = rRJ (rows >= n are
-// skipped).  mats: the 15 matrices of this level (97 x 112 each); cEd[r-1] =
+// skipped).  mats: the matrices of this level (97 x 112 each); cEd[r-1] =
 // (E_r mod m) d mod m; posE[r-1] = E_r mod 2^64.
 __global__ void __launch_bounds__(kPlanThreads, 2) plan_level_kernel(
     ranmar_state_t* __restrict__ st, uint64_t R, uint64_t n, const uint32_t* __restrict__ mats,

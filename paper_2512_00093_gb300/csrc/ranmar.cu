@@ -46,8 +46,9 @@ struct ranmar_plan {
   uint32_t J[RANMAR_MAX_EXP_WORDS];
   uint32_t J_words;
   size_t max_n;
-  int levels;          // level t turns 16^(t+1) known streams into 16^(t+2)
-  uint32_t* mats;      // levels x 15 x 97 x 112: M_{r 16^(t+1) J}
+  int levels;          // level t: R_t known streams -> R_t * radix(t)
+  int mat_off[ranmar::kPlanMaxLevels];  // first matrix of each level
+  uint32_t* mats;      // per level radix - 1 matrices of 97 x 112: M_{r R_t J}
   uint8_t* bimg;       // levels x 15 fp16 limb images of the same matrices
   uint32_t* ced;       // levels x 15: (E mod m) d mod m
   uint64_t* pose;      // levels x 15: E mod 2^64
@@ -914,7 +915,10 @@ int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != t->device) return RANMAR_EINVAL;
   int levels = 0;
-  for (uint64_t known = ranmar::kPlanBase; known < max_n; known *= ranmar::kPlanRadix) ++levels;
+  {
+    uint64_t known = ranmar::kPlanBase;
+    for (; known < max_n; known *= ranmar::plan_radix(levels)) ++levels;
+  }
   ranmar_plan* p = new (std::nothrow) ranmar_plan{};
   if (!p) return RANMAR_ENOMEM;
   p->device = dev;
@@ -942,9 +946,19 @@ int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_
     *out = p;
     return RANMAR_OK;
   }
-  // Exponents E = r 16^(t+1) J (r = 1..15), one per matrix; each matrix row i
-  // is the unit state e_i jumped by E.
-  const int nmat = 15 * levels;
+  // Exponents E = r R_t J (r = 1 .. radix(t) - 1), one per matrix; each matrix
+  // row i is the unit state e_i jumped by E.
+  int nmat = 0;
+  uint64_t level_known[ranmar::kPlanMaxLevels];
+  {
+    uint64_t known = ranmar::kPlanBase;
+    for (int tl = 0; tl < levels; ++tl) {
+      p->mat_off[tl] = nmat;
+      level_known[tl] = known;
+      nmat += ranmar::plan_radix(tl) - 1;
+      known *= ranmar::plan_radix(tl);
+    }
+  }
   const size_t nrows = static_cast<size_t>(nmat) * RANMAR_R;
   uint32_t* hexp = new (std::nothrow) uint32_t[nrows * RANMAR_MAX_EXP_WORDS];
   uint32_t* hidx = new (std::nothrow) uint32_t[nrows];
@@ -953,9 +967,10 @@ int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_
   ranmar_state_t* hunit = new (std::nothrow) ranmar_state_t[RANMAR_R];
   int rc = (hexp && hidx && hced && hpos && hunit) ? RANMAR_OK : RANMAR_ENOMEM;
   for (int m = 0; rc == RANMAR_OK && m < nmat; ++m) {
-    const int tl = m / 15, r = m % 15 + 1;
-    uint64_t mult = static_cast<uint64_t>(r);
-    for (int q = 0; q <= tl; ++q) mult *= ranmar::kPlanRadix;
+    int tl = 0;
+    while (tl + 1 < levels && m >= p->mat_off[tl + 1]) ++tl;
+    const int r = m - p->mat_off[tl] + 1;
+    const uint64_t mult = static_cast<uint64_t>(r) * level_known[tl];  // < 2^40
     uint32_t E[RANMAR_MAX_EXP_WORDS] = {0, 0, 0, 0, 0};
     unsigned __int128 carry = 0;
     for (int w = 0; w < RANMAR_MAX_EXP_WORDS; ++w) {
@@ -1096,23 +1111,26 @@ int ranmar_plan_expand(const ranmar_plan_t* p, ranmar_state_t* d_states, size_t 
   if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return RANMAR_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   uint64_t R = ranmar::kPlanBase;
-  for (int tl = 0; tl < p->levels && R < n; ++tl, R *= ranmar::kPlanRadix) {
+  for (int tl = 0; tl < p->levels && R < n; R *= ranmar::plan_radix(tl), ++tl) {
+    const uint64_t rmax = static_cast<uint64_t>(ranmar::plan_radix(tl) - 1);
+    const uint64_t rc = (n - 1) / R < rmax ? (n - 1) / R : rmax;  // r = 1..rc: rR < n
+    const int mo = p->mat_off[tl];
     if (p->method == RANMAR_PLAN_TENSOR) {
-      // items (tile, r): tiles of 128 source rows, r = 1..r_count with r R < n
+      // items (tile, r): tiles of 128 source rows
       const uint64_t tiles = (R + ranmar::kMmaM - 1) / ranmar::kMmaM;
-      const uint64_t rc = (n - 1) / R < 15 ? (n - 1) / R : 15;
       const uint64_t items = tiles * rc;
       const unsigned grid = static_cast<unsigned>(
           items < static_cast<uint64_t>(p->num_sms) ? items : static_cast<uint64_t>(p->num_sms));
       ranmar::plan_level_mma_kernel<<<grid, ranmar::kMmaThreads, ranmar::kMmaSmemBytes, s>>>(
           d_states, R, n, static_cast<uint32_t>(rc), static_cast<uint32_t>(items),
-          p->bimg + static_cast<size_t>(tl) * 15 * ranmar::kBImgBytes, p->ced + tl * 15,
-          p->pose + tl * 15, p->status);
+          p->bimg + static_cast<size_t>(mo) * ranmar::kBImgBytes, p->ced + mo, p->pose + mo,
+          p->status);
     } else {
-      const dim3 grid(static_cast<unsigned>((R + ranmar::kPlanRows - 1) / ranmar::kPlanRows), 15);
+      const dim3 grid(static_cast<unsigned>((R + ranmar::kPlanRows - 1) / ranmar::kPlanRows),
+                      static_cast<unsigned>(rc));
       ranmar::plan_level_kernel<<<grid, ranmar::kPlanThreads, ranmar::kPlanSmemBytes, s>>>(
-          d_states, R, n, p->mats + static_cast<size_t>(tl) * 15 * RANMAR_R * ranmar::kPlanCols,
-          p->ced + tl * 15, p->pose + tl * 15);
+          d_states, R, n, p->mats + static_cast<size_t>(mo) * RANMAR_R * ranmar::kPlanCols,
+          p->ced + mo, p->pose + mo);
     }
     const int lr = check_launch();
     if (lr != RANMAR_OK) return lr;

@@ -1,6 +1,7 @@
-"""GPU parity of the partition plan (radix-16 levels of jump matrices): the
-states equal the table partition's and the oracle's, bit for bit, for
-stream counts that end inside every level, and the plan's host checks."""
+"""GPU parity of the partition plan (256 streams by the table jump, then
+levels of jump matrices of radix 256, 16, ...): the states equal the table
+partition's and the oracle's, bit for bit, for stream counts that end
+inside every level, and the plan's host checks."""
 import numpy as np
 import pytest
 import torch
@@ -30,8 +31,8 @@ def test_plan_equals_table_partition(rm, table, orc, J, method):
     base = rm.seed(12345).to(dev)
     plan = rm.Plan(table, J, 70000)
     plan.set_method(rm.Plan.TENSOR if method == "tensor" else rm.Plan.IMAD)
-    for n, k0 in [(1, 0), (15, 3), (16, 0), (17, 9), (255, 1), (256, 0), (257, 4),
-                  (4095, 7), (4097, 0), (65536, 123), (70000, 1 << 20)]:
+    for n, k0 in [(1, 0), (255, 3), (256, 0), (257, 9), (511, 1), (512, 0), (513, 4),
+                  (4097, 7), (65535, 0), (65536, 123), (65537, 5), (70000, 1 << 20)]:
         a = plan.partition(base, k0, n)
         b = table.partition(base, J, k0, n)
         torch.cuda.synchronize()
@@ -39,7 +40,7 @@ def test_plan_equals_table_partition(rm, table, orc, J, method):
     # a sample against the oracle directly
     st = rm.state_words_np(a)
     x0, c0 = orc.seeded_state(12345)
-    for i in [0, 15, 16, 255, 256, 4095, 4096, 65535, 65536, 69999]:
+    for i in [0, 255, 256, 511, 512, 4095, 4096, 65535, 65536, 69999]:
         xr, cr = orc.jump(x0, c0, ((1 << 20) + i) * J)
         assert np.array_equal(st[i, :97], xr) and st[i, 97] == cr, i
         pos = int(st[i, 98]) | (int(st[i, 99]) << 32)
@@ -76,7 +77,7 @@ def test_plan_host_checks(rm, table):
     with pytest.raises(rm.RanmarError):
         plan.partition(base, (1 << 64) - 1, 2)       # k0 + n - 1 overflows
     with pytest.raises(rm.RanmarError):
-        rm.Plan(table, (1 << 159), 1 << 20)          # 15 16^4 J >= 2^160
+        rm.Plan(table, (1 << 159), 1 << 20)          # 15 * 65536 * J >= 2^160
     out = torch.empty((4, 100), dtype=torch.int32, device=dev)
     with pytest.raises(rm.RanmarError):
         plan.partition(out[0:1], 0, 4, out=out)      # output overlaps the base
@@ -86,15 +87,16 @@ def test_plan_host_checks(rm, table):
 
 
 def test_plan_expand_from_table_rows(rm, table):
-    """expand() from 16 rows computed elsewhere (the table partition on
-    another stream) gives the same states as one partition_plan call."""
+    """expand() from the first 256 rows computed elsewhere (the table
+    partition on another stream) gives the same states as one partition_plan
+    call."""
     dev = torch.device("cuda:0")
     J = 1 << 40
     base = rm.seed(12345).to(dev)
     plan = rm.Plan(table, J, 5000)
     side = torch.cuda.Stream(dev)
     st = torch.empty((5000, 100), dtype=torch.int32, device=dev)
-    table.partition(base, J, 99, 16, out=st[:16], stream=side)
+    table.partition(base, J, 99, 256, out=st[:256], stream=side)
     ev = torch.cuda.Event()
     ev.record(side)
     torch.cuda.current_stream().wait_event(ev)
