@@ -631,8 +631,9 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
 
     # Batched uneven workload at full size: 10^6 streams at k*2^64, lengths
     # log-uniform in [64, 65536] (seed 7), f32 packed by prefix sum.  One step
-    # = partition jump + device pack + one persistent generate (autotuned),
-    # replayed as a captured CUDA graph.  Comparator: one plain launch per
+    # = partition (the plan; the per-stream table jump beside it) + device
+    # pack + one persistent generate (autotuned), replayed as a captured CUDA
+    # graph.  Comparator: one plain launch per
     # stream (generation only), timed on a sample of streams.
     bu = BatchedUneven()
     ns = bu.n_streams
@@ -649,31 +650,43 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
     ms_gen = timed(lambda: b.generate_f32(stb, desc, outf, order=order))
     ms_jump = timed(lambda: table.partition(base, bu.J, 0, ns, out=stb))
     ms_pack = timed(lambda: b.pack(counts))
+    # the start states by the partition plan (256 table jumps + levels of
+    # jump matrices on the tensor cores): same states, checked
+    bplan = rm.Plan(table, bu.J, ns)
+    ms_jump_plan = timed(lambda: bplan.partition(base, 0, ns, out=stb))
+    plan_same = bool(torch.equal(bplan.partition(base, 0, ns),
+                                 table.partition(base, bu.J, 0, ns)))
     gs = torch.cuda.Stream()
     gs.wait_stream(stream)
     desc_g = torch.empty_like(desc)
     ord_g = torch.empty_like(order)
     import paper_2512_00093_gb300.binding as bd
-    with rm.capture(gs) as cap:
-        table.partition(base, bu.J, 0, ns, out=stb, stream=gs)
-        bd._check(bd._lib().ranmar_batch_pack(b._h, counts.data_ptr(), ns, 0, desc_g.data_ptr(),
-                                              ord_g.data_ptr(), None, gs.cuda_stream), "pack")
-        b.generate_f32(stb, desc_g, outf, order=ord_g, stream=gs)
 
-    def graph_step():
+    def graph_ms(jump):
+        with rm.capture(gs) as cap:
+            jump()
+            bd._check(bd._lib().ranmar_batch_pack(b._h, counts.data_ptr(), ns, 0,
+                                                  desc_g.data_ptr(), ord_g.data_ptr(), None,
+                                                  gs.cuda_stream), "pack")
+            b.generate_f32(stb, desc_g, outf, order=ord_g, stream=gs)
+        stream.wait_stream(gs)
+        ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         cap.graph.launch(gs)
-    stream.wait_stream(gs)
-    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    graph_step()
-    gs.synchronize()
-    best_g = float("inf")
-    for _ in range(5):
-        ga.record(gs)
-        graph_step()
-        gb.record(gs)
         gs.synchronize()
-        best_g = min(best_g, ga.elapsed_time(gb))
-    cap.graph.close()
+        best = float("inf")
+        for _ in range(5):
+            ga.record(gs)
+            cap.graph.launch(gs)
+            gb.record(gs)
+            gs.synchronize()
+            best = min(best, ga.elapsed_time(gb))
+        cap.graph.close()
+        return best
+
+    best_g = graph_ms(lambda: bplan.partition(base, 0, ns, out=stb, stream=gs))
+    best_g_table = graph_ms(lambda: table.partition(base, bu.J, 0, ns, out=stb, stream=gs))
+    plan_status = bplan.status()
+    bplan.close()
     gen_bytes = total * 4 + ns * (400 + 24 + 4)
     # plain comparator on a sample: generation only, one launch per stream
     samp = 4096
@@ -705,8 +718,11 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
         "streams": ns, "outputs": total, "dtype": "f32",
         "config": {"lanes_per_stream": cfg[0], "threads_per_cta": cfg[1], "ctas_per_sm": cfg[2],
                    "chunk": cfg[3], "tuned_ms": tune_ms, "from_cache": cached},
-        "jump_ms": ms_jump, "pack_ms": ms_pack, "generate_ms": ms_gen,
-        "graph_step_ms": best_g, "step_outputs_per_s": total / (best_g * 1e-3),
+        "jump_ms": ms_jump_plan, "jump_table_ms": ms_jump, "jump_method": "partition plan",
+        "plan_states_identical": plan_same, "plan_status": plan_status,
+        "pack_ms": ms_pack, "generate_ms": ms_gen,
+        "graph_step_ms": best_g, "graph_step_table_jump_ms": best_g_table,
+        "step_outputs_per_s": total / (best_g * 1e-3),
         "generate_outputs_per_s": total / (ms_gen * 1e-3),
         "generate_hbm_gbs": gen_bytes / (ms_gen * 1e-3) / 1e9,
         "generate_hbm_frac": gen_bytes / (ms_gen * 1e-3) / 1e9 / hbm_peak,

@@ -106,3 +106,22 @@ def test_plan_expand_from_table_rows(rm, table):
     assert torch.equal(st, ref)
     assert plan.status() == 0
     plan.close()
+
+
+def test_plan_million_streams_equals_table(rm, table):
+    """10^6 streams (the batched-uneven shape, J = 2^64): the radix-256 level
+    and a radix-16 level, both methods, against the per-stream table jump."""
+    dev = torch.device("cuda:0")
+    J = 1 << 64
+    n = 1_000_000
+    base = rm.seed(12345).to(dev)
+    plan = rm.Plan(table, J, n)
+    ref = table.partition(base, J, 3, n)
+    for method in (rm.Plan.TENSOR, rm.Plan.IMAD):
+        plan.set_method(method)
+        got = plan.partition(base, 3, n)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref), method
+        del got
+    assert plan.status() == 0
+    plan.close()
