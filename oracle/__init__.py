@@ -102,6 +102,19 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.orc_jump.restype = None
     lib.orc_stream.argtypes = [ctypes.c_int32, _u32p, ctypes.c_int, ctypes.c_uint64, _u32p]
     lib.orc_stream.restype = ctypes.c_int
+    lib.orc_lfg_step.argtypes = [_u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
+    lib.orc_lfg_step.restype = None
+    lib.orc_lfg_mulmod.argtypes = [_u32p, _u32p, _u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int]
+    lib.orc_lfg_mulmod.restype = None
+    lib.orc_lfg_pow_t.argtypes = [_u32p, ctypes.c_int, _u32p, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int]
+    lib.orc_lfg_pow_t.restype = None
+    lib.orc_lfg_apply.argtypes = [_u32p, _u32p, _u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.orc_lfg_apply.restype = None
+    lib.orc_lfg_jump.argtypes = [_u32p, _u32p, ctypes.c_int, _u32p, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_int]
+    lib.orc_lfg_jump.restype = None
     return lib
 
 
@@ -252,6 +265,42 @@ class Oracle:
         out = np.zeros(count, np.uint32)
         if self.lib.orc_stream(seed, w, len(w), count, out) != 0:
             raise ValueError(f"seed {seed} outside 1..900000000")
+        return out
+
+    # -- general lags (concluding remarks): x_n = x_{n-r} - x_{n-s} mod 2^e --
+    def lfg_step(self, x: np.ndarray, r: int, s: int, e: int, n: int) -> np.ndarray:
+        """n transitions of the window x (oldest first), brute force."""
+        y = np.ascontiguousarray(x, np.uint32).copy()
+        self.lib.orc_lfg_step(y, r, s, e, n)
+        return y
+
+    def lfg_mulmod(self, a, b, r: int, s: int, e: int, karatsuba: bool = False) -> np.ndarray:
+        """a b mod phi_{r,s} = t^r + t^{r-s} - 1 (classical or Karatsuba product)."""
+        out = np.zeros(r, np.uint32)
+        self.lib.orc_lfg_mulmod(np.ascontiguousarray(a, np.uint32), np.ascontiguousarray(b, np.uint32),
+                                out, r, s, e, int(karatsuba))
+        return out
+
+    def lfg_pow_t(self, E: int, r: int, s: int, e: int, karatsuba: bool = False) -> np.ndarray:
+        """t^E mod phi_{r,s} by left-to-right binary exponentiation."""
+        w = self.words(E)
+        out = np.zeros(r, np.uint32)
+        self.lib.orc_lfg_pow_t(w, len(w), out, r, s, e, int(karatsuba))
+        return out
+
+    def lfg_apply(self, x, p, r: int, s: int, e: int) -> np.ndarray:
+        """x P(A) in the dot-product form (window extended to 2r - 1 words)."""
+        out = np.zeros(r, np.uint32)
+        self.lib.orc_lfg_apply(np.ascontiguousarray(x, np.uint32), np.ascontiguousarray(p, np.uint32),
+                               out, r, s, e)
+        return out
+
+    def lfg_jump(self, x, E: int, r: int, s: int, e: int, karatsuba: bool = False) -> np.ndarray:
+        """The window x jumped by E transitions (polynomial method)."""
+        w = self.words(E)
+        out = np.zeros(r, np.uint32)
+        self.lib.orc_lfg_jump(np.ascontiguousarray(x, np.uint32), w, len(w), out, r, s, e,
+                              int(karatsuba))
         return out
 
 

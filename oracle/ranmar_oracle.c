@@ -387,3 +387,167 @@ int orc_stream(int32_t seed, const uint32_t *E, int nw, uint64_t count,
     orc_generate(x, c, count, out, NULL, NULL);
     return 0;
 }
+
+/* ======================================================================== */
+/* Concluding remarks: the jump for lagged Fibonacci recurrences of general */
+/* order.  x_n = x_{n-r} - x_{n-s} mod 2^e (r > s >= 1, 1 <= e <= 32) has    */
+/* the transition matrix of Sec. 3.1 with characteristic polynomial          */
+/*     phi_{r,s}(t) = t^r + t^{r-s} - 1,   i.e. t^k = t^{k-r} - t^{k-s},     */
+/* and the jump by E is x' = x P_E(A) with P_E = t^E mod phi_{r,s} (for      */
+/* r = 97, s = 33, e = 24 it is the lagged Fibonacci part of RANMAR).  The   */
+/* cost of P_E is one polynomial product per exponent bit: r^2 multiply-adds */
+/* with the classical product, about r^{log2 3} with Karatsuba's (the        */
+/* concluding remarks).  The window x[0..r) is kept oldest first.            */
+/* ======================================================================== */
+static uint32_t lfg_mask(int e) { return e >= 32 ? 0xFFFFFFFFu : ((1u << e) - 1u); }
+
+/* n transitions of the window by the recurrence (brute force). */
+void orc_lfg_step(uint32_t *x, int r, int s, int e, uint64_t n)
+{
+    uint32_t mask = lfg_mask(e);
+    uint32_t *ring = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)r);
+    memcpy(ring, x, sizeof(uint32_t) * (size_t)r);
+    int h = 0;                                   /* ring[h] = oldest word */
+    int q = r - s;                               /* ring[q] = x_{n-s}     */
+    for (uint64_t t = 0; t < n; t++) {
+        uint32_t w = (ring[h] - ring[q]) & mask;
+        ring[h] = w;
+        h = (h + 1 == r) ? 0 : h + 1;
+        q = (q + 1 == r) ? 0 : q + 1;
+    }
+    for (int i = 0; i < r; i++) x[i] = ring[(h + i) % r];
+    free(ring);
+}
+
+/* c[0 .. 2r-1) reduced mod phi_{r,s} from the top: t^k = t^{k-r} - t^{k-s}. */
+static void lfg_reduce(uint32_t *c, int r, int s)
+{
+    for (int k = 2 * r - 2; k >= r; k--) {
+        uint32_t h = c[k];
+        c[k] = 0;
+        c[k - r] += h;
+#if ORC_MUTANT == 13
+        c[k - s] += h;
+#else
+        c[k - s] -= h;
+#endif
+    }
+}
+
+/* Classical product c[0 .. 2n-1) = a b of two n-coefficient polynomials. */
+static void lfg_school(const uint32_t *a, const uint32_t *b, uint32_t *c, int n)
+{
+    memset(c, 0, sizeof(uint32_t) * (size_t)(2 * n));
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) c[i + j] += a[i] * b[j];
+}
+
+/* Karatsuba's product c[0 .. 2n-1) = a b: with a = a0 + t^h a1, b likewise
+ * (h = n/2), a b = z0 + t^h (z1 - z0 - z2) + t^{2h} z2 for z0 = a0 b0,
+ * z2 = a1 b1, z1 = (a0 + a1)(b0 + b1); classical below 16 coefficients. */
+static void lfg_kara(const uint32_t *a, const uint32_t *b, uint32_t *c, int n)
+{
+    if (n <= 16) {
+        lfg_school(a, b, c, n);
+        return;
+    }
+    int h = n / 2, hh = n - h;                   /* a0: h coefficients, a1: hh >= h */
+    uint32_t *sa = (uint32_t *)calloc((size_t)hh, sizeof(uint32_t));
+    uint32_t *sb = (uint32_t *)calloc((size_t)hh, sizeof(uint32_t));
+    uint32_t *a0 = (uint32_t *)calloc((size_t)hh, sizeof(uint32_t));
+    uint32_t *b0 = (uint32_t *)calloc((size_t)hh, sizeof(uint32_t));
+    uint32_t *z0 = (uint32_t *)calloc((size_t)(2 * hh), sizeof(uint32_t));
+    uint32_t *z1 = (uint32_t *)calloc((size_t)(2 * hh), sizeof(uint32_t));
+    uint32_t *z2 = (uint32_t *)calloc((size_t)(2 * hh), sizeof(uint32_t));
+    memcpy(a0, a, sizeof(uint32_t) * (size_t)h);
+    memcpy(b0, b, sizeof(uint32_t) * (size_t)h);
+    for (int i = 0; i < hh; i++) {
+        sa[i] = a0[i] + a[h + i];
+        sb[i] = b0[i] + b[h + i];
+    }
+    lfg_kara(a0, b0, z0, hh);                    /* a0, b0 zero padded to hh */
+    lfg_kara(a + h, b + h, z2, hh);
+    lfg_kara(sa, sb, z1, hh);
+    memset(c, 0, sizeof(uint32_t) * (size_t)(2 * n));
+    for (int i = 0; i < 2 * hh; i++) {
+#if ORC_MUTANT == 12
+        uint32_t mid = z1[i] - z0[i];
+#else
+        uint32_t mid = z1[i] - z0[i] - z2[i];
+#endif
+        if (i < 2 * h) c[i] += z0[i];
+        c[h + i] += mid;
+        if (2 * h + i < 2 * n) c[2 * h + i] += z2[i];
+    }
+    free(sa); free(sb); free(a0); free(b0); free(z0); free(z1); free(z2);
+}
+
+/* out = a b mod phi_{r,s}, classical (karatsuba = 0) or Karatsuba product. */
+void orc_lfg_mulmod(const uint32_t *a, const uint32_t *b, uint32_t *out, int r, int s, int e,
+                    int karatsuba)
+{
+    uint32_t *c = (uint32_t *)calloc((size_t)(2 * r), sizeof(uint32_t));
+    if (karatsuba) lfg_kara(a, b, c, r);
+    else lfg_school(a, b, c, r);
+    lfg_reduce(c, r, s);
+    uint32_t mask = lfg_mask(e);
+    for (int i = 0; i < r; i++) out[i] = c[i] & mask;
+    free(c);
+}
+
+/* P_E = t^E mod phi_{r,s} by left-to-right binary exponentiation (square,
+ * then multiply by t on a 1 bit); E little-endian in nw 32-bit words. */
+void orc_lfg_pow_t(const uint32_t *E, int nw, uint32_t *out, int r, int s, int e, int karatsuba)
+{
+    uint32_t *p = (uint32_t *)calloc((size_t)r, sizeof(uint32_t));
+    uint32_t *t1 = (uint32_t *)calloc((size_t)r, sizeof(uint32_t));
+    uint32_t mask = lfg_mask(e);
+    p[0] = 1;
+    if (r > 1) t1[1] = 1;
+    else t1[0] = 1;
+    for (int w = nw - 1; w >= 0; w--) {
+        for (int bit = 31; bit >= 0; bit--) {
+            int b = (E[w] >> bit) & 1u;
+            orc_lfg_mulmod(p, p, p, r, s, e, karatsuba);
+            if (b) {
+                /* p t: shift up, the word on t^r becomes 1 - t^{r-s} */
+                uint32_t top = p[r - 1];
+                memmove(p + 1, p, sizeof(uint32_t) * (size_t)(r - 1));
+                p[0] = top;
+                p[r - s] = (p[r - s] - top) & mask;
+            }
+        }
+    }
+    memcpy(out, p, sizeof(uint32_t) * (size_t)r);
+    free(p);
+    free(t1);
+}
+
+/* x' = x P(A): new word k = sum_i p_i X_{i+k}, X the window extended by the
+ * recurrence to 2r-1 words (the dot-product form of Sec. 3.1). */
+void orc_lfg_apply(const uint32_t *x, const uint32_t *p, uint32_t *out, int r, int s, int e)
+{
+    uint32_t *X = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(2 * r));
+    memcpy(X, x, sizeof(uint32_t) * (size_t)r);
+    for (int q = r; q < 2 * r - 1; q++) X[q] = X[q - r] - X[q - s];
+    uint32_t mask = lfg_mask(e);
+    for (int k = 0; k < r; k++) {
+        uint32_t acc = 0;
+        for (int i = 0; i < r; i++) acc += p[i] * X[i + k];
+        out[k] = acc & mask;
+    }
+    free(X);
+}
+
+/* The jump by E of the window x (out may alias x). */
+void orc_lfg_jump(const uint32_t *x, const uint32_t *E, int nw, uint32_t *out, int r, int s,
+                  int e, int karatsuba)
+{
+    uint32_t *p = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)r);
+    uint32_t *o = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)r);
+    orc_lfg_pow_t(E, nw, p, r, s, e, karatsuba);
+    orc_lfg_apply(x, p, o, r, s, e);
+    memcpy(out, o, sizeof(uint32_t) * (size_t)r);
+    free(p);
+    free(o);
+}
