@@ -115,6 +115,9 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.orc_lfg_jump.argtypes = [_u32p, _u32p, ctypes.c_int, _u32p, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int]
     lib.orc_lfg_jump.restype = None
+    lib.orc_lfg_generate.argtypes = [_u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_uint64, _u32p]
+    lib.orc_lfg_generate.restype = None
     return lib
 
 
@@ -294,6 +297,13 @@ class Oracle:
         self.lib.orc_lfg_apply(np.ascontiguousarray(x, np.uint32), np.ascontiguousarray(p, np.uint32),
                                out, r, s, e)
         return out
+
+    def lfg_generate(self, x, r: int, s: int, e: int, n: int):
+        """(the next n words of the recurrence, the advanced window)."""
+        y = np.ascontiguousarray(x, np.uint32).copy()
+        out = np.zeros(max(n, 1), np.uint32)
+        self.lib.orc_lfg_generate(y, r, s, e, n, out)
+        return out[:n], y
 
     def lfg_jump(self, x, E: int, r: int, s: int, e: int, karatsuba: bool = False) -> np.ndarray:
         """The window x jumped by E transitions (polynomial method)."""

@@ -551,3 +551,22 @@ void orc_lfg_jump(const uint32_t *x, const uint32_t *E, int nw, uint32_t *out, i
     free(p);
     free(o);
 }
+
+/* The next n words of the recurrence after the window x (brute force); x is
+ * advanced by n transitions. */
+void orc_lfg_generate(uint32_t *x, int r, int s, int e, uint64_t n, uint32_t *out)
+{
+    uint32_t mask = lfg_mask(e);
+    uint32_t *ring = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)r);
+    memcpy(ring, x, sizeof(uint32_t) * (size_t)r);
+    int h = 0, q = r - s;
+    for (uint64_t t = 0; t < n; t++) {
+        uint32_t w = (ring[h] - ring[q]) & mask;
+        out[t] = w;
+        ring[h] = w;
+        h = (h + 1 == r) ? 0 : h + 1;
+        q = (q + 1 == r) ? 0 : q + 1;
+    }
+    for (int i = 0; i < r; i++) x[i] = ring[(h + i) % r];
+    free(ring);
+}

@@ -71,7 +71,19 @@ def pin_lfg_composition(o):
                               o.lfg_jump(x, a + b, r, s, e, karatsuba=True))
 
 
-PINS = [pin_lfg_brute, pin_lfg_ranmar, pin_lfg_karatsuba, pin_lfg_special, pin_lfg_composition]
+def pin_lfg_generate_ranmar(o):
+    """At RANMAR's lags the generated words are Algorithm 2's LFG words: its
+    outputs plus c_n mod 2^24 (Algorithm 2 outputs x_{96+n} - c_n)."""
+    x, c = o.seeded_state(12345)
+    words, after = o.lfg_generate(x, 97, 33, 24, 500)
+    out, xa, _ = o.generate(x, c, 500)
+    cs = np.array([o.c_step(c, n + 1) for n in range(500)], np.int64)
+    assert np.array_equal((out.astype(np.int64) + cs) & 0xFFFFFF, words.astype(np.int64))
+    assert np.array_equal(after, xa)
+
+
+PINS = [pin_lfg_brute, pin_lfg_ranmar, pin_lfg_karatsuba, pin_lfg_special, pin_lfg_composition,
+        pin_lfg_generate_ranmar]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=lambda f: f.__name__)
