@@ -789,6 +789,41 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
     except Exception as e:  # noqa: BLE001
         res["partition_plan"] = {"error": f"{type(e).__name__}: {e}"}
 
+    # general lags (the concluding remarks): the jump of x_n = x_{n-r} - x_{n-s}
+    # mod 2^e for growing r, classical vs Karatsuba squarings (64-bit
+    # exponents with the top bit set: 63 squarings each)
+    try:
+        lag = {}
+        rng = np.random.default_rng(1)
+        for (r, s_, e) in [(97, 33, 24), (607, 273, 24), (1279, 418, 32), (2048, 1029, 24)]:
+            nl = 4096 if r < 1000 else 1216
+            xl = torch.as_tensor(rng.integers(0, 1 << e, (nl, r), dtype=np.uint64)
+                                 .astype(np.uint32).view(np.int32), device=dev)
+            exl = rm.exps_tensor([int(v) | (1 << 63) for v in rng.integers(0, 1 << 62, nl,
+                                                                          dtype=np.uint64)],
+                                 2, device=dev)
+            idl = torch.arange(nl, dtype=torch.int32, device=dev)
+            ol = torch.empty_like(xl)
+            row = {"streams": nl}
+            for name, m in [("classical", rm.LFG_CLASSICAL), ("karatsuba", rm.LFG_KARATSUBA)] + \
+                    [(f"karatsuba_L{L}", rm.LFG_KARATSUBA_LEVELS(L)) for L in (1, 2, 3)]:
+                try:
+                    L = rm.lfg_karatsuba_levels(r, s_, e, m)
+                    ms_l = timed(lambda m=m: rm.lfg_jump(r, s_, e, xl, exl, base_idx=idl, out=ol,
+                                                         method=m), reps=2)
+                    M = -(-r // (1 << L))
+                    macs = nl * (63 * (3 ** L) * M * M + r * r)
+                    row[name] = {"levels": L, "ms": ms_l, "jumps_per_s": nl / (ms_l * 1e-3),
+                                 "leaf_macs_per_s": macs / (ms_l * 1e-3),
+                                 "alu_frac": macs / (ms_l * 1e-3) / 1e12 / alu_peak}
+                except rm.RanmarError:
+                    row[name] = None
+            lag[f"r{r}_s{s_}_e{e}"] = row
+            del xl, exl, idl, ol
+        res["general_lags"] = lag
+    except Exception as ex_:  # noqa: BLE001
+        res["general_lags"] = {"error": f"{type(ex_).__name__}: {ex_}"}
+
     # probes: write-only HBM ceiling and IMAD ceiling on this GPU
     try:
         P = ctypes.CDLL(rbuild.PROBE_LIB)

@@ -350,6 +350,58 @@ int ranmar_plan_expand(const ranmar_plan_t *p, ranmar_state_t *d_states, size_t 
 int ranmar_plan_set_method(ranmar_plan_t *p, int method);
 int ranmar_plan_status(const ranmar_plan_t *p, uint32_t **d_status);
 
+/* ------------------------------------------------------------------------
+ * Lagged Fibonacci recurrences of general order (the concluding remarks):
+ * x_n = x_{n-r} - x_{n-s} mod 2^e, 2 <= r <= 2048, 1 <= s < r, 1 <= e <= 32;
+ * for r = 97, s = 33, e = 24 the lagged Fibonacci part of RANMAR.  A state is
+ * the window x_{n-r} .. x_{n-1}, r uint32 words, oldest first.  The jump by E
+ * is x' = x P_E(A), P_E = t^E mod (t^r + t^{r-s} - 1) by binary
+ * exponentiation (Sec. 3.1 with general lags), each squaring by the
+ * classical product (r^2 multiply-adds) or by Karatsuba's (3^L products of
+ * r/2^L coefficients with L levels, about r^{log2 3} for deep splits).
+ * ------------------------------------------------------------------------ */
+#define RANMAR_LFG_CLASSICAL 0
+#define RANMAR_LFG_KARATSUBA 1                 /* depth chosen by the library */
+#define RANMAR_LFG_KARATSUBA_LEVELS(L) (16 + (L))  /* exactly L = 1..6 levels */
+
+/*
+ * ranmar_lfg_jump -- d_out[i] = the window d_x[d_base_idx[i]] (or d_x[0]
+ * when d_base_idx is NULL) jumped by E_i = d_exp[i * exp_words ..]
+ * (little-endian 32-bit words, exp_words in 1..5).  d_x holds n_base windows
+ * of r words, d_out n windows (must not overlap d_x).  One CTA per stream.
+ * Errors: RANMAR_EINVAL (r, s, e or method out of range, null pointer,
+ * misalignment, overlap), RANMAR_ERANGE (exp_words, n_base = 0, the shape
+ * does not fit on the device).  Device: RANMAR_ST_BAD_INDEX for
+ * d_base_idx[i] >= n_base (that stream is skipped).
+ */
+int ranmar_lfg_jump(uint32_t r, uint32_t s, uint32_t e, int method, const uint32_t *d_x,
+                    size_t n_base, const uint32_t *d_base_idx, const uint32_t *d_exp,
+                    uint32_t exp_words, uint32_t *d_out, size_t n, uint32_t *d_status,
+                    ranmar_stream_t stream);
+
+/*
+ * ranmar_lfg_generate -- for each of the n windows d_x[i] (r words), the
+ * next `count` words of the recurrence to d_out[i * count ..] (masked to e
+ * bits), and the window advanced in place.  One warp per stream, min(32, s)
+ * words per step.  Errors: RANMAR_EINVAL (r, s, e out of range, null
+ * pointer, misalignment, overlap), RANMAR_ERANGE (n * count overflows).
+ */
+int ranmar_lfg_generate(uint32_t r, uint32_t s, uint32_t e, uint32_t *d_x, size_t n,
+                        uint64_t count, uint32_t *d_out, ranmar_stream_t stream);
+
+/*
+ * ranmar_lfg_karatsuba_levels -- the number of Karatsuba levels the jump
+ * uses for (r, s, e, method): 0 for the classical product.
+ * RANMAR_LFG_KARATSUBA takes 2 levels for r >= 1024, 1 for 512 <= r < 1024
+ * and the classical product below (the fastest on GB300 in a sweep of r =
+ * 97, 607, 1279, 2048 and depths 0..5: a deeper split saves multiply-adds
+ * but needs more shared memory, so fewer CTAs share an SM).
+ * RANMAR_EINVAL for arguments out of range or an explicit depth that does
+ * not fit (leaves of at least 8 coefficients within 200 KB of shared
+ * memory).
+ */
+int ranmar_lfg_karatsuba_levels(uint32_t r, uint32_t s, uint32_t e, int method);
+
 /*
  * ranmar_partition_generate_u24 / ranmar_partition_generate_f32 -- stream
  * partitioning (Sec. 1) and generation (Algorithm 2) fused in one kernel.

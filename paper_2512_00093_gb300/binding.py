@@ -92,6 +92,13 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_partition_plan.argtypes = [_vp, _vp, _u64, _sz, _vp, _vp]
     lib.ranmar_partition_plan.restype = ctypes.c_int
     lib.ranmar_plan_set_method.argtypes = [_vp, ctypes.c_int]
+    lib.ranmar_lfg_jump.argtypes = [_u32, _u32, _u32, ctypes.c_int, _vp, _sz, _vp, _vp, _u32, _vp,
+                                    _sz, _vp, _vp]
+    lib.ranmar_lfg_jump.restype = ctypes.c_int
+    lib.ranmar_lfg_generate.argtypes = [_u32, _u32, _u32, _vp, _sz, _u64, _vp, _vp]
+    lib.ranmar_lfg_generate.restype = ctypes.c_int
+    lib.ranmar_lfg_karatsuba_levels.argtypes = [_u32, _u32, _u32, ctypes.c_int]
+    lib.ranmar_lfg_karatsuba_levels.restype = ctypes.c_int
     lib.ranmar_plan_expand.argtypes = [_vp, _vp, _sz, _vp]
     lib.ranmar_plan_expand.restype = ctypes.c_int
     lib.ranmar_plan_status.argtypes = [_vp, ctypes.POINTER(_vp)]
@@ -658,6 +665,56 @@ class Table:
         _check(_lib().ranmar_table_rows(self._h, ctypes.byref(p)), "ranmar_table_rows")
         return _wrap_device_ptr(p.value, self.ROWS * self.ROW_WORDS).view(self.ROWS,
                                                                            self.ROW_WORDS)
+
+
+LFG_CLASSICAL, LFG_KARATSUBA = 0, 1
+
+
+def LFG_KARATSUBA_LEVELS(L: int) -> int:
+    """Method code for Karatsuba with exactly L levels (1..6)."""
+    return 16 + int(L)
+
+
+def lfg_jump(r: int, s: int, e: int, x: torch.Tensor, exps: torch.Tensor, base_idx=None,
+             out=None, method: int = LFG_KARATSUBA, status=None, stream=None) -> torch.Tensor:
+    """ranmar_lfg_jump: out[i] = window x[base_idx[i] or 0] (r words, oldest
+    first) of x_n = x_{n-r} - x_{n-s} mod 2^e, jumped by exps[i] (words)."""
+    x = x.reshape(-1, r)
+    _need(x, torch.int32, "x")
+    _need(exps, torch.int32, "exps")
+    n, nw = exps.shape
+    if out is None:
+        out = torch.empty((n, r), dtype=torch.int32, device=x.device)
+    _need(out, torch.int32, "out")
+    if base_idx is not None:
+        _need(base_idx, torch.int32, "base_idx")
+    _check(_lib().ranmar_lfg_jump(r, s, e, int(method), _ptr(x), x.shape[0], _ptr(base_idx),
+                                  _ptr(exps), nw, _ptr(out), n, _ptr(status), _stream(stream)),
+           "ranmar_lfg_jump")
+    return out
+
+
+def lfg_generate(r: int, s: int, e: int, x: torch.Tensor, count: int, out=None,
+                 stream=None) -> torch.Tensor:
+    """ranmar_lfg_generate: the next `count` words of each window (x advanced
+    in place); returns out (n, count)."""
+    x = x.reshape(-1, r)
+    _need(x, torch.int32, "x")
+    n = x.shape[0]
+    if out is None:
+        out = torch.empty((n, count), dtype=torch.int32, device=x.device)
+    _need(out, torch.int32, "out")
+    _check(_lib().ranmar_lfg_generate(r, s, e, _ptr(x), n, int(count), _ptr(out), _stream(stream)),
+           "ranmar_lfg_generate")
+    return out
+
+
+def lfg_karatsuba_levels(r: int, s: int, e: int, method: int = LFG_KARATSUBA) -> int:
+    """ranmar_lfg_karatsuba_levels (0 = classical product)."""
+    v = _lib().ranmar_lfg_karatsuba_levels(r, s, e, int(method))
+    if v < 0:
+        raise RanmarError(v, "ranmar_lfg_karatsuba_levels")
+    return v
 
 
 class Plan:

@@ -3,6 +3,7 @@
 // Host side: argument checks, Algorithm 3 seeding, launch configuration and
 // CUDA error mapping.  Device side: generate.cuh (Algorithm 2 warp step) and
 // jump.cuh (Sec. 3.1 / 3.2 jump-ahead).
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -17,6 +18,7 @@
 #include "partition_generate.cuh"
 #include "plan.cuh"
 #include "plan_mma.cuh"
+#include "lfg.cuh"
 
 // Batch handle: the workspace of the persistent path on one device.
 struct ranmar_batch {
@@ -397,6 +399,68 @@ int launch_partition_generate(const ranmar_table_t* t, const ranmar_state_t* d_b
          reinterpret_cast<cudaStream_t>(stream)>>>(t->rows, d_base, part, d_states, n, count,
                                                     d_out);
   return check_launch();
+}
+
+// Shape of a general-lag jump; false for arguments out of range.
+constexpr size_t kLfgSmemMax = 200 * 1024;
+
+bool lfg_shape(uint32_t r, uint32_t s, uint32_t e, int method, ranmar::LfgShape& sh) {
+  if (r < 2 || r > static_cast<uint32_t>(ranmar::kLfgMaxR) || s < 1 || s >= r || e < 1 || e > 32)
+    return false;
+  // method: classical, Karatsuba with an automatic depth, or Karatsuba with
+  // exactly L levels (RANMAR_LFG_KARATSUBA_LEVELS(L), L = 1..6)
+  int want_L = -1;
+  if (method == RANMAR_LFG_KARATSUBA) want_L = 0;
+  else if (method >= RANMAR_LFG_KARATSUBA_LEVELS(1) && method <= RANMAR_LFG_KARATSUBA_LEVELS(6))
+    want_L = method - RANMAR_LFG_KARATSUBA_LEVELS(0);
+  else if (method != RANMAR_LFG_CLASSICAL) return false;
+  sh = ranmar::LfgShape{};
+  sh.r = static_cast<int>(r);
+  sh.s = static_cast<int>(s);
+  sh.mask = e == 32 ? 0xFFFFFFFFu : ((1u << e) - 1u);
+  const int R = sh.r;
+  const int xwin = ranmar::lfg_sk(2 * R + 3) + 1;   // the skewed extended window
+  auto a4 = [](int w) { return (w + 3) & ~3; };
+  if (want_L == 0) want_L = R >= 1024 ? 2 : (R >= 512 ? 1 : -1);  // measured on GB300
+  if (want_L > 0) {
+    for (int L = 6; L >= 1; --L) {
+      if (L != want_L) continue;
+      const int M = (R + (1 << L) - 1) >> L;
+      if (M < 8) continue;
+      int p3 = 1;
+      for (int q = 0; q < L; ++q) p3 *= 3;
+      const int opnd = ranmar::lfg_opnd_words(M);
+      const int size_a = a4(std::max(p3 * 2 * M, xwin));
+      const int size_b = a4((p3 / 3) * 4 * M);
+      const int N = M << L;
+      const int words = a4(N) + p3 * opnd + size_a + size_b;
+      if (static_cast<size_t>(words) * 4 > kLfgSmemMax) continue;
+      sh.L = L;
+      sh.M = M;
+      sh.N = N;
+      sh.pow3L = p3;
+      sh.opnd = opnd;
+      sh.off_p = 0;
+      sh.off_ops = a4(N);
+      sh.off_a = sh.off_ops + p3 * opnd;
+      sh.off_b = sh.off_a + size_a;
+      sh.words = sh.off_b + size_b;
+      return true;
+    }
+    return false;   // that depth does not fit
+  }
+  // the classical product (also Karatsuba's fallback when no level fits)
+  sh.L = 0;
+  sh.M = R;
+  sh.N = R;
+  sh.pow3L = 1;
+  sh.opnd = ranmar::lfg_opnd_words(R);
+  sh.off_p = 0;
+  sh.off_ops = a4(R);
+  sh.off_a = sh.off_ops + sh.opnd;
+  sh.off_b = sh.off_a + a4(std::max(2 * R, xwin));
+  sh.words = sh.off_b;
+  return true;
 }
 
 }  // namespace
@@ -1157,6 +1221,68 @@ int ranmar_partition_plan(const ranmar_plan_t* p, const ranmar_state_t* d_base, 
                                    nullptr, stream, nullptr, n0);
   if (jr != RANMAR_OK) return jr;
   return ranmar_plan_expand(p, d_out, n, stream);
+}
+
+int ranmar_lfg_karatsuba_levels(uint32_t r, uint32_t s, uint32_t e, int method) {
+  ranmar::LfgShape sh;
+  if (!lfg_shape(r, s, e, method, sh)) return RANMAR_EINVAL;
+  return sh.L;
+}
+
+int ranmar_lfg_jump(uint32_t r, uint32_t s, uint32_t e, int method, const uint32_t* d_x,
+                    size_t n_base, const uint32_t* d_base_idx, const uint32_t* d_exp,
+                    uint32_t exp_words, uint32_t* d_out, size_t n, uint32_t* d_status,
+                    ranmar_stream_t stream) {
+  ranmar::LfgShape sh;
+  if (!lfg_shape(r, s, e, method, sh)) return RANMAR_EINVAL;
+  if (n == 0) return RANMAR_OK;
+  if (!d_x || !d_exp || !d_out) return RANMAR_EINVAL;
+  if (exp_words < 1 || exp_words > RANMAR_MAX_EXP_WORDS || n_base == 0) return RANMAR_ERANGE;
+  if (!aligned(d_x, 4) || !aligned(d_out, 4) || !aligned(d_exp, 4) || !aligned(d_base_idx, 4))
+    return RANMAR_EINVAL;
+  if (overlaps(d_x, n_base * r * sizeof(uint32_t), d_out, n * r * sizeof(uint32_t)))
+    return RANMAR_EINVAL;
+  const size_t smem = static_cast<size_t>(sh.words) * sizeof(uint32_t);
+  cudaError_t ce = cudaFuncSetAttribute(ranmar::lfg_jump_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        static_cast<int>(smem));
+  if (ce != cudaSuccess) return cuda_fail(ce);
+  int dev = -1, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ranmar::lfg_jump_kernel,
+                                                    ranmar::kLfgThreads, smem) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  if (per < 1) return RANMAR_ERANGE;
+  uint64_t grid = static_cast<uint64_t>(sms) * per;
+  if (grid > n) grid = n;
+  ranmar::lfg_jump_kernel<<<static_cast<unsigned>(grid), ranmar::kLfgThreads, smem,
+                            reinterpret_cast<cudaStream_t>(stream)>>>(
+      sh, d_x, n_base, d_base_idx, d_exp, exp_words, d_out, n, d_status);
+  return check_launch();
+}
+
+int ranmar_lfg_generate(uint32_t r, uint32_t s, uint32_t e, uint32_t* d_x, size_t n,
+                        uint64_t count, uint32_t* d_out, ranmar_stream_t stream) {
+  ranmar::LfgShape sh;
+  if (!lfg_shape(r, s, e, RANMAR_LFG_CLASSICAL, sh)) return RANMAR_EINVAL;
+  if (n == 0 || count == 0) return RANMAR_OK;
+  if (!d_x || !d_out) return RANMAR_EINVAL;
+  if (!aligned(d_x, 4) || !aligned(d_out, 4)) return RANMAR_EINVAL;
+  if (count > SIZE_MAX / 4 / n) return RANMAR_ERANGE;
+  if (overlaps(d_x, n * r * sizeof(uint32_t), d_out, n * count * sizeof(uint32_t)))
+    return RANMAR_EINVAL;
+  const size_t smem = static_cast<size_t>(ranmar::kLfgGenWarps) * r * sizeof(uint32_t);
+  cudaError_t ce = cudaFuncSetAttribute(ranmar::lfg_generate_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        static_cast<int>(smem));
+  if (ce != cudaSuccess) return cuda_fail(ce);
+  uint64_t grid = (n + ranmar::kLfgGenWarps - 1) / ranmar::kLfgGenWarps;
+  if (grid > (1u << 20)) grid = 1u << 20;
+  ranmar::lfg_generate_kernel<<<static_cast<unsigned>(grid), 32 * ranmar::kLfgGenWarps, smem,
+                                reinterpret_cast<cudaStream_t>(stream)>>>(
+      static_cast<int>(r), static_cast<int>(s), sh.mask, d_x, n, count, d_out);
+  return check_launch();
 }
 
 int ranmar_generate_alg1_f32(ranmar_state_t* d_states, size_t n_states,
