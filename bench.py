@@ -628,6 +628,21 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
                           "table": {"ms": ms_t, "jumps_per_s": lj.n_streams / (ms_t * 1e-3),
                                     "tmacs_per_s": macs_t / (ms_t * 1e-3) / 1e12,
                                     "alu_frac": macs_t / (ms_t * 1e-3) / 1e12 / alu_peak}}
+    # the same 16,384 jumps by the partition plan (256 table jumps + one
+    # tensor-core level of jump matrices); states checked identical
+    try:
+        tb = time.perf_counter()
+        lplan = rm.Plan(table, lj.J, lj.n_streams)
+        lbuild = (time.perf_counter() - tb) * 1e3
+        ms_p = timed(lambda: lplan.partition(base, 0, lj.n_streams, out=st))
+        same = bool(torch.equal(lplan.partition(base, 0, lj.n_streams),
+                                table.partition(base, lj.J, 0, lj.n_streams)))
+        res["large_jumps"]["plan"] = {"ms": ms_p, "jumps_per_s": lj.n_streams / (ms_p * 1e-3),
+                                      "build_ms": lbuild, "states_identical": same,
+                                      "status": lplan.status()}
+        lplan.close()
+    except Exception as ex_:  # noqa: BLE001
+        res["large_jumps"]["plan"] = {"error": f"{type(ex_).__name__}: {ex_}"}
 
     # Batched uneven workload at full size: 10^6 streams at k*2^64, lengths
     # log-uniform in [64, 65536] (seed 7), f32 packed by prefix sum.  One step
