@@ -778,8 +778,8 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
     res["float_vs_modular"] = fv
     del o32, o64, st0
 
-    # partition plan: radix-16 levels of jump matrices (one integer GEMM per
-    # level) against the per-stream table jump, same states
+    # partition plan: 256 table jumps + one radix-256 level of jump matrices
+    # on the tensor cores, against the per-stream table jump, same states
     try:
         pw = Partitioned()
         pbase = rm.seed(pw.seed).to(dev)
