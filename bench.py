@@ -186,6 +186,30 @@ def oracle_sample(seconds: float, start_k: int, w):
             return n, el
 
 
+def oracle_sample_threads(seconds: float, start_k: int, w, threads: int):
+    """The same oracle on `threads` host threads at once, each on its own
+    consecutive streams (the C calls run without the interpreter lock, and
+    the oracle keeps no mutable global state).  Returns (streams, seconds)."""
+    import concurrent.futures as cf
+    from oracle import oracle
+    o = oracle()
+
+    def work(t):
+        n = 0
+        t0 = time.perf_counter()
+        k = start_k + t * 1_000_000
+        while True:
+            o.stream(w.seed, (k + n) * w.J, w.count)
+            n += 1
+            if time.perf_counter() - t0 >= seconds and n >= 2:
+                return n
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        ns = list(ex.map(work, range(threads)))
+    return sum(ns), time.perf_counter() - t0
+
+
 def run_reference(args):
     from paper_2512_00093_gb300.workloads import Partitioned
     rank, world, _ = dist_env()
@@ -482,6 +506,8 @@ def run_ours(args):
     gen_sha = source_sha("generate.cuh", "ranmar_device.cuh")
     tj = traffic_for("jump_table_kernel", jump_sha)
     tg = traffic_for("generate_desc_kernel", gen_sha)
+    tp = traffic_for("plan_level_mma_kernel",
+                     source_sha("plan_mma.cuh", "plan.cuh", "ranmar_device.cuh"))
     roof_gen = {"kernel": "generate_desc_kernel<u24>", "bound": "hbm",
                 "achieved": gen_bytes / (gen_ms * 1e-3) / 1e9, "peak": hbm_peak,
                 "unit": "GB/s", "frac": gen_bytes / (gen_ms * 1e-3) / 1e9 / hbm_peak,
@@ -508,7 +534,8 @@ def run_ours(args):
                  "frac": plan_flops / (exp_ms * 1e-3) / 1e12 / tc_peak,
                  "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops); "
                                 "fp16 has the same nominal dense rate",
-                 "algorithmic_flops": plan_flops, "traffic": None, "avg_launch_ms": exp_ms,
+                 "algorithmic_flops": plan_flops,
+                 "traffic": tp["bytes_per_launch"] if tp else None, "avg_launch_ms": exp_ms,
                  "note": "one launch (510 tiles x matrices over 152 SMs)"}
     fused_bytes = n * count * 4 + n * 400
     roof_fused = {"kernel": "partition_generate_kernel<u24>", "bound": "hbm",
@@ -574,6 +601,13 @@ def run_ours(args):
                 "kind": "oracle",
                 "sample": f"{ns} streams of this workload (jump + 4096 outputs), "
                           f"{el:.1f} s, single-threaded C oracle on the host"}
+            threads = os.cpu_count() or 1
+            ns, el = oracle_sample_threads(args.cpu_seconds / 2, 10_000_000, w, threads)
+            result["cpu_baseline_all_cores"] = {
+                "value": ns * count / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+                "note": "reported only: the same oracle over streams on every host core",
+                "sample": f"{ns} streams of this workload (jump + 4096 outputs), "
+                          f"{el:.1f} s, {threads} threads"}
     emit(result)
     if dist:
         dist.barrier()
