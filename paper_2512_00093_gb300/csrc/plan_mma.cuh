@@ -3,22 +3,24 @@
 //
 // Exact integer arithmetic on fp16 inputs: every 24-bit word v is split
 // into three balanced 8-bit limbs, v = v0 + 2^8 v1 + 2^16 v2 (mod 2^24),
-// v_i in [-128, 127] (exact in fp16).  With K = 97 terms per dot product the
-// four accumulators
-//     D0 = A0 B0,  D1 = A0 B1 + A1 B0,  D2a = A0 B2 + A2 B0,  D2b = A1 B1
-// (and every partial sum of them) stay below 2 * 97 * 2^14 < 2^22 in
-// magnitude, so the fp32 accumulation is exact, each value converts to an
-// integer by one add of 1.5 * 2^23 (its bits are then 0x4B400000 + D), and
+// v_i in [-128, 127] (exact in fp16).  Along K, A holds [A0 | A1 | A2] and
+// B holds [B2 | B1 | B0], each limb block 104 wide (97 padded), then 8 zero
+// columns (K = 320).  The product sums with equal K positions give the
+// weight-2^16 terms A0 B2 + A1 B1 + A2 B0, split at K = 160 into D2a and
+// D2b; A's K positions [0, 208) against B's [104, 312) give D1 = A0 B1 +
+// A1 B0, and [0, 112) against [208, 320) give D0 = A0 B0 (the last 8 B
+// columns are zero).  Every accumulator sums at most 194 products of
+// magnitude <= 2^14, so it and its partial sums stay below 2^22: the fp32
+// accumulation is exact, each value converts to an integer by one add of
+// 1.5 * 2^23 (its bits are then 0x4B400000 + D), and
 //     x'_w = (D0 + 2^8 D1 + 2^16 (D2a + D2b)) mod 2^24.
-// A holds [A0 | A1 | A2] along K (3 x 112, 97 padded), B holds [B2 | B1 |
-// B0]: each accumulator is a sum of K ranges of the two images.
 //
 // Tile: 128 source rows (M, one TMEM lane each) x 112 output words (N) x
-// 336 (K): 42 MMAs of 128x112x16 per (tile, r).  A CTA of 256 threads owns
+// 320 (K): 40 MMAs of 128x112x16 per (tile, r).  A CTA of 256 threads owns
 // a balanced contiguous range of (tile, r) items.  Per tile, one bulk async
 // copy (TMA) brings the 128 consecutive source states (51 KB) into a staging
 // buffer, from which the warps build the limb image.  Per item, a bulk copy
-// brings the B image (75 KB, precomputed at plan creation), one thread
+// brings the B image (70 KB, precomputed at plan creation), one thread
 // issues the MMAs, the eight warps read the accumulators back (warps w and
 // w+4 share TMEM lanes 32(w%4).. and split the columns), recombine the limbs
 // and assemble the 128 new states in the staging buffer, and one bulk async
@@ -43,27 +45,28 @@ namespace ranmar {
 
 constexpr int kMmaM = 128;              // rows per tile = TMEM lanes
 constexpr int kMmaN = 112;              // output words, 97 padded
-constexpr int kLimbK = 112;             // K per limb, 97 padded
-constexpr int kMmaK = 3 * kLimbK;       // 336
+constexpr int kLimbK = 104;             // K per limb block, 97 padded to 8
+constexpr int kMmaK = 320;              // 3 limb blocks + 8 zero columns
 constexpr int kMmaThreads = 256;
 constexpr uint32_t kTmemCols = 512;     // D0 at 0, D1 at 128, D2a at 256, D2b at 384
 constexpr uint32_t kMagicBits = 0x4B400000u;  // bits of 1.5 * 2^23
 // kMagicBits (1 + 2^8 + 2 * 2^16): the bias of b0 + 2^8 b1 + 2^16 (b2a + b2b)
 constexpr uint32_t kMagicMix = kMagicBits + (kMagicBits << 8) + (kMagicBits << 17);
-constexpr uint32_t kAImgBytes = kMmaM * kMmaK * 2;   // 86,016
+constexpr uint32_t kAImgBytes = kMmaM * kMmaK * 2;   // 81,920
 constexpr uint32_t kStageBytes = kMmaM * sizeof(ranmar_state_t);  // 51,200
-constexpr uint32_t kBImgBytes = kMmaN * kMmaK * 2;   // 75,264
+constexpr uint32_t kBImgBytes = kMmaN * kMmaK * 2;   // 71,680
 constexpr uint32_t kALbo = (kMmaM / 8) * 128;        // 2048
 constexpr uint32_t kBLbo = (kMmaN / 8) * 128;        // 1792
 constexpr uint32_t kCoreSbo = 128;
-// Operand images, the staging buffer, then barriers and the TMEM address.
-// The descriptors only reach inside the images (A start at most 40 LBO plus
-// one LBO and 15 SBO; B at most 40 LBO plus one LBO and 13 SBO).
+constexpr int kKGroups = kMmaK / 8;     // 40 core matrices along K
+// Operand images, the staging buffer, then barriers and the TMEM address:
+// 204,864 B, so that a 20,736 B CTA of the table jump fits beside it on an
+// SM.  An MMA reads K groups g, g + 1 from its start; the starts below reach
+// at most group 38 (A and B), i.e. inside the images.
 constexpr size_t kMmaSmemBytes = kAImgBytes + kBImgBytes + kStageBytes + 64;
 static_assert(kMmaSmemBytes <= 232448, "smem");
-static_assert(41 * kALbo + 15 * kCoreSbo + 128 <= kAImgBytes &&
-                  41 * kBLbo + 13 * kCoreSbo + 128 <= kBImgBytes,
-              "descriptor reach");
+static_assert(kKGroups * kALbo == kAImgBytes && kKGroups * kBLbo == kBImgBytes, "images");
+static_assert(kLimbK % 8 == 0 && 3 * kLimbK + 8 == kMmaK && kMmaK % 16 == 0, "K layout");
 constexpr uint32_t kMbarSpinLimit = 1u << 22;
 static_assert(kBImgBytes % 32 == 0, "two 16-byte aligned halves");
 
@@ -131,8 +134,9 @@ __device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes
 __device__ __forceinline__ void bulk_wait_read() {
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
-__device__ __forceinline__ void bulk_wait_all() {
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+// A hint that brings `bytes` (a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -166,6 +170,34 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
       : "memory");
 }
 
+// D[tmem] (+)= A B with the descriptors advanced by the constants kAOff /
+// kBOff (added inside the statement, so that the 42 descriptors of an item
+// are not all held in registers).
+template <uint32_t kAOff, uint32_t kBOff>
+__device__ __forceinline__ void mma_f16_at(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n .reg .b64 da, db;\n setp.ne.b32 p, %4, 0;\n"
+      " add.s64 da, %1, %5;\n add.s64 db, %2, %6;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kMmaIdesc), "r"(accumulate), "n"(kAOff), "n"(kBOff)
+      : "memory");
+}
+
+// kSteps MMAs (16 K each) from the K group (8 columns) kA of A and kB of B
+// on, into the accumulator at d (the first one overwrites it when `first`).
+// Step j starts 2 j groups further: a constant added to the descriptor's
+// start-address field (shared-memory addresses stay below 2^18).
+template <int kSteps, int kA, int kB, int kJ = 0>
+__device__ __forceinline__ void mma_run(uint32_t d, uint64_t ad, uint64_t bd, bool first) {
+  if constexpr (kJ < kSteps) {
+    static_assert(kA + 2 * kJ + 1 < kKGroups && kB + 2 * kJ + 1 < kKGroups, "K reach");
+    mma_f16_at<(((kA + 2u * kJ) * kALbo) >> 4), (((kB + 2u * kJ) * kBLbo) >> 4)>(
+        d, ad, bd, (first && kJ == 0) ? 0u : 1u);
+    mma_run<kSteps, kA, kB, kJ + 1>(d, ad, bd, first);
+  }
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::
                    "r"(bar)
@@ -182,22 +214,53 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld1(uint32_t taddr, uint32_t (&v)[1]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v[0]) : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-
-// Balanced 8-bit limbs of a 24-bit word: v = l0 + 2^8 l1 + 2^16 l2 (mod 2^24).
-__device__ __forceinline__ void limbs3(uint32_t v, int (&l)[3]) {
-  l[0] = static_cast<int>((v & 0xFFu) ^ 0x80u) - 0x80;
-  const uint32_t v1 = (v - static_cast<uint32_t>(l[0])) >> 8;
-  l[1] = static_cast<int>((v1 & 0xFFu) ^ 0x80u) - 0x80;
-  const uint32_t v2 = (v1 - static_cast<uint32_t>(l[1])) >> 8;
-  l[2] = static_cast<int>((v2 & 0xFFu) ^ 0x80u) - 0x80;
+// The registers of a tcgen05.ld hold their values only after the wait; an
+// empty statement that "rewrites" them, placed after tmem_ld_wait, keeps the
+// compiler from reading them earlier.
+__device__ __forceinline__ void tmem_regs_fence(uint32_t (&v)[16]) {
+  asm volatile(""
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]));
+}
+__device__ __forceinline__ void tmem_regs_fence(uint32_t (&v)[1]) {
+  asm volatile("" : "+r"(v[0]));
 }
 
-__device__ __forceinline__ uint32_t pack_half2(int a, int b) {
-  const __half2 h = __halves2half2(__int2half_rn(a), __int2half_rn(b));
-  return *reinterpret_cast<const uint32_t*>(&h);
+// Output word j of the four accumulators D0, D1, D2a, D2b (fp32 bits):
+// |D| < 2^22, so D + 1.5 * 2^23 is exact and its bits are 0x4B400000 + D;
+// x' = (D0 + 2^8 D1 + 2^16 (D2a + D2b)) mod 2^24.
+template <int kW>
+__device__ __forceinline__ uint32_t limb_sum(const uint32_t (&f)[4][kW], int j) {
+  const uint32_t b0 = __float_as_uint(__uint_as_float(f[0][j]) + 12582912.0f);
+  const uint32_t b1 = __float_as_uint(__uint_as_float(f[1][j]) + 12582912.0f);
+  const uint32_t b2 = __float_as_uint(__uint_as_float(f[2][j]) + 12582912.0f) +
+                      __float_as_uint(__uint_as_float(f[3][j]) + 12582912.0f);
+  return (b0 + (b1 << 8) + (b2 << 16) - kMagicMix) & kMask24;
+}
+
+// Balanced 8-bit limbs of two 24-bit words as fp16 pairs: h[s] = (limb s of
+// a, limb s of b), v = l0 + 2^8 l1 + 2^16 l2 (mod 2^24), l_s in [-128, 127].
+// (v + 0x808080) mod 2^24 has the bytes l_s + 128 (the balanced digits are
+// unique); a byte u placed under the high byte 0x64 is the fp16 1024 + u,
+// and one packed subtraction of 1152 leaves l_s (every value is exact).
+__device__ __forceinline__ void limb_pairs(uint32_t a, uint32_t b, uint32_t (&h)[3]) {
+  const uint32_t wa = ((a + 0x808080u) & kMask24) | 0x64000000u;
+  const uint32_t wb = ((b + 0x808080u) & kMask24) | 0x64000000u;
+  const __half2 bias = __float2half2_rn(1152.0f);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    // result bytes: byte s of wa, 0x64, byte s of wb, 0x64
+    const uint32_t bits = __byte_perm(wa, wb, s | (3u << 4) | ((4u + s) << 8) | (7u << 12));
+    const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&bits), bias);
+    h[s] = *reinterpret_cast<const uint32_t*>(&v);
+  }
 }
 
 // Byte offset of element (row, k) in an operand image with `groups` 8-row
@@ -206,9 +269,9 @@ __host__ __device__ constexpr uint32_t img_off(uint32_t row, uint32_t k, uint32_
   return ((k / 8) * groups + row / 8) * 128 + (row % 8) * 16 + (k % 8) * 2;
 }
 
-// B image of one matrix: element (n, k') = limb (2 - k'/112) of M[k'%112][n]
-// (0 beyond 97 in either index), so that K holds [B2 | B1 | B0].  One thread
-// per (matrix, n, k-pair).
+// B image of one matrix: element (n, k') = limb (2 - k'/104) of M[k'%104][n]
+// for k' < 312 (0 beyond 97 in either index), 0 for k' >= 312, so that K
+// holds [B2 | B1 | B0 | 0].  One thread per (matrix, n, k-pair).
 __global__ void plan_bimg_kernel(const ranmar_state_t* __restrict__ unit_jumped,
                                  uint8_t* __restrict__ bimg, uint32_t nmat) {
   const uint64_t total = static_cast<uint64_t>(nmat) * kMmaN * (kLimbK / 2);
@@ -217,26 +280,29 @@ __global__ void plan_bimg_kernel(const ranmar_state_t* __restrict__ unit_jumped,
     const uint32_t mat = static_cast<uint32_t>(q / (kMmaN * (kLimbK / 2)));
     const uint32_t rem = static_cast<uint32_t>(q % (kMmaN * (kLimbK / 2)));
     const uint32_t nn = rem / (kLimbK / 2), k = 2 * (rem % (kLimbK / 2));
-    int la[3] = {0, 0, 0}, lb[3] = {0, 0, 0};
+    uint32_t va = 0, vb = 0;
     if (nn < static_cast<uint32_t>(kR)) {
       const ranmar_state_t* rows = unit_jumped + static_cast<size_t>(mat) * kR;
-      if (k < static_cast<uint32_t>(kR)) limbs3(rows[k].x[nn], la);
-      if (k + 1 < static_cast<uint32_t>(kR)) limbs3(rows[k + 1].x[nn], lb);
+      if (k < static_cast<uint32_t>(kR)) va = rows[k].x[nn];
+      if (k + 1 < static_cast<uint32_t>(kR)) vb = rows[k + 1].x[nn];
     }
+    uint32_t h[3];
+    limb_pairs(va, vb, h);
     uint8_t* img = bimg + static_cast<size_t>(mat) * kBImgBytes;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
       const uint32_t kk = s * kLimbK + k;
-      *reinterpret_cast<uint32_t*>(img + img_off(nn, kk, kMmaN / 8)) =
-          pack_half2(la[2 - s], lb[2 - s]);
+      *reinterpret_cast<uint32_t*>(img + img_off(nn, kk, kMmaN / 8)) = h[2 - s];
     }
+    if (k == 0)  // the 8 zero columns after the limb blocks
+      *reinterpret_cast<uint4*>(img + img_off(nn, 3 * kLimbK, kMmaN / 8)) = make_uint4(0, 0, 0, 0);
   }
 }
 
 // One level on the tensor cores: items q = tile * r_count + (r - 1), tile <
 // ceil(R / 128), r = 1..r_count; st[rR + i] = st[i] advanced by E_r for
-// source rows i < R of the tile with rR + i < n.  bimg: this level's 15 B
-// images; cEd / posE as in plan_level_kernel.
+// source rows i < R of the tile with rR + i < n.  bimg: this level's B
+// images (one per r); cEd / posE as in plan_level_kernel.
 __global__ void __launch_bounds__(kMmaThreads, 1) plan_level_mma_kernel(
     ranmar_state_t* __restrict__ st, uint64_t R, uint64_t n, uint32_t r_count, uint32_t items,
     const uint8_t* __restrict__ bimg, const uint32_t* __restrict__ cEd,
@@ -256,18 +322,6 @@ __global__ void __launch_bounds__(kMmaThreads, 1) plan_level_mma_kernel(
       static_cast<uint32_t>(static_cast<uint64_t>(blockIdx.x + 1) * items / gridDim.x);
   if (q0 >= q1) return;
 
-  if (tid == 0) {
-    mbar_init(bar_b, 1);
-    mbar_init(bar_m, 1);
-    mbar_init(bar_s, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) tmem_alloc(smem_addr(tmem_slot), kTmemCols);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-
   auto load_b = [&](uint32_t q) {
     const uint32_t r = q % r_count + 1;
     const uint8_t* src = bimg + static_cast<size_t>(r - 1) * kBImgBytes;
@@ -275,11 +329,43 @@ __global__ void __launch_bounds__(kMmaThreads, 1) plan_level_mma_kernel(
     bulk_g2s(smem_addr(B), src, kBImgBytes / 2, bar_b);
     bulk_g2s(smem_addr(B) + kBImgBytes / 2, src + kBImgBytes / 2, kBImgBytes / 2, bar_b);
   };
+  // source rows of a tile into the staging buffer
+  auto load_src = [&](uint64_t tile) {
+    const uint64_t i0 = tile * kMmaM;
+    const uint32_t bytes = static_cast<uint32_t>(R - i0 < kMmaM ? R - i0 : kMmaM) *
+                           static_cast<uint32_t>(sizeof(ranmar_state_t));
+    mbar_expect_tx(bar_s, bytes);
+    bulk_g2s(smem_addr(stage), st + i0, bytes, bar_s);
+  };
 
-  if (tid == 0) load_b(q0);
+  // Thread 0 starts the copies of the first tile and the first B image at
+  // once (they run under the TMEM allocation) and asks L2 for the CTA's
+  // other B images and, if its range reaches a second tile, those rows.
+  if (tid == 0) {
+    mbar_init(bar_b, 1);
+    mbar_init(bar_m, 1);
+    mbar_init(bar_s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    load_src(q0 / r_count);
+    load_b(q0);
+    for (uint32_t q = q0 + 1; q < q1; ++q)
+      prefetch_l2(bimg + static_cast<size_t>(q % r_count) * kBImgBytes, kBImgBytes);
+    const uint64_t t_last = (q1 - 1) / r_count;
+    if (t_last != q0 / r_count) {
+      const uint64_t i0 = t_last * kMmaM;
+      prefetch_l2(st + i0, static_cast<uint32_t>(R - i0 < kMmaM ? R - i0 : kMmaM) *
+                               static_cast<uint32_t>(sizeof(ranmar_state_t)));
+    }
+  }
+  if (warp == 0) tmem_alloc(smem_addr(tmem_slot), kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
   uint32_t ph_b = 0, ph_m = 0, ph_s = 0;  // ph_b: thread 0 only
   bool ok = true;
-  bool b_in_flight = true, mma_in_flight = false, s_in_flight = false;  // thread 0's view
+  bool b_in_flight = true, mma_in_flight = false, s_in_flight = true;  // thread 0's view
   int64_t cur_tile = -1;
   uint32_t src_c = 0;  // warps 0-3: c and pos of this thread's source row
   uint64_t src_pos = 0;
@@ -292,13 +378,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1) plan_level_mma_kernel(
     const uint64_t i0 = tile * kMmaM;
     const uint32_t nsrc = static_cast<uint32_t>(R - i0 < kMmaM ? R - i0 : kMmaM);
     if (static_cast<int64_t>(tile) != cur_tile) {
-      // the tile's source states into the staging buffer (after the last
-      // store has read it)
-      if (tid == 0) {
+      // the tile's source states into the staging buffer (the first tile's
+      // copy is already in flight; a later one waits until the last store
+      // has read the buffer)
+      if (tid == 0 && cur_tile >= 0) {
         bulk_wait_read();
-        mbar_expect_tx(bar_s, nsrc * static_cast<uint32_t>(sizeof(ranmar_state_t)));
-        bulk_g2s(smem_addr(stage), st + i0, nsrc * static_cast<uint32_t>(sizeof(ranmar_state_t)),
-                 bar_s);
+        load_src(tile);
         s_in_flight = true;
       }
       const bool s_ok = mbar_wait(bar_s, ph_s);
@@ -307,7 +392,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1) plan_level_mma_kernel(
       ph_s ^= 1;
       if (tid == 0) s_in_flight = false;
       // A image: warp w converts core matrices (mg, kg) with mg = w, w+8;
-      // lane l -> row mg*8 + (l & 7), k pair 2 (l >> 3).
+      // lane l -> row mg*8 + (l & 7), k pair 2 (l >> 3); then the 8 zero
+      // columns after the limb blocks.
+      if (tid < kMmaM)
+        *reinterpret_cast<uint4*>(A + img_off(tid, 3 * kLimbK, kMmaM / 8)) = make_uint4(0, 0, 0, 0);
 #pragma unroll 1
       for (uint32_t mg = warp; mg < kMmaM / 8; mg += kMmaThreads / 32) {
         const uint32_t row = mg * 8 + (lane & 7);
@@ -321,13 +409,11 @@ __global__ void __launch_bounds__(kMmaThreads, 1) plan_level_mma_kernel(
             v = *reinterpret_cast<const uint2*>(x + k);
             if (k + 1 >= static_cast<uint32_t>(kR)) v.y = 0u;
           }
-          int la[3], lb[3];
-          limbs3(v.x, la);
-          limbs3(v.y, lb);
+          uint32_t h[3];
+          limb_pairs(v.x, v.y, h);
 #pragma unroll
           for (int s = 0; s < 3; ++s)
-            *reinterpret_cast<uint32_t*>(A + img_off(row, s * kLimbK + k, kMmaM / 8)) =
-                pack_half2(la[s], lb[s]);
+            *reinterpret_cast<uint32_t*>(A + img_off(row, s * kLimbK + k, kMmaM / 8)) = h[s];
         }
       }
       if (warp < 4 && m < nsrc) {
@@ -345,24 +431,17 @@ __global__ void __launch_bounds__(kMmaThreads, 1) plan_level_mma_kernel(
         b_in_flight = false;
         ph_b ^= 1;
         tc_fence_after();
-        const uint32_t a0 = smem_addr(A), b0 = smem_addr(B);
-        // K ranges (units of 16): limb images A = [A0 | A1 | A2], B = [B2 | B1
-        // | B0], 7 steps per limb.  D2a (col 256) = A0 B2 + A2 B0, D2b (col
-        // 384) = A1 B1, D1 (col 128) = A0 B1 + A1 B0, D0 (col 0) = A0 B0.
-        constexpr uint32_t L = kLimbK / 16;
-        auto run = [&](uint32_t dcol, uint32_t astep, uint32_t bstep, uint32_t nsteps,
-                       bool first) {
-#pragma unroll 1
-          for (uint32_t s2 = 0; s2 < nsteps; ++s2)
-            mma_f16(tmem + dcol, mma_desc(a0 + 2 * (astep + s2) * kALbo, kALbo, kCoreSbo),
-                    mma_desc(b0 + 2 * (bstep + s2) * kBLbo, kBLbo, kCoreSbo),
-                    (first && s2 == 0) ? 0u : 1u);
-        };
-        run(256, 0, 0, L, true);          // A0 B2
-        run(256, 2 * L, 2 * L, L, false); // A2 B0
-        run(384, L, L, L, true);          // A1 B1
-        run(128, 0, L, 2 * L, true);      // A0 B1 + A1 B0
-        run(0, 0, 2 * L, L, true);        // A0 B0
+        // K groups of 8 (limb blocks of 13 groups: A = [A0 | A1 | A2 | 0], B
+        // = [B2 | B1 | B0 | 0]).  D2a (col 256) and D2b (col 384): equal K
+        // positions, groups 0-19 and 20-39; D1 (col 128): A groups 0-25
+        // against B groups 13-38; D0 (col 0): A 0-13 against B 26-39.
+        const uint64_t ad = mma_desc(smem_addr(A), kALbo, kCoreSbo);
+        const uint64_t bd = mma_desc(smem_addr(B), kBLbo, kCoreSbo);
+        constexpr int G = kLimbK / 8;                    // 13
+        mma_run<10, 0, 0>(tmem + 256, ad, bd, true);     // D2a
+        mma_run<10, 20, 20>(tmem + 384, ad, bd, true);   // D2b
+        mma_run<G, 0, G>(tmem + 128, ad, bd, true);      // D1 = A0 B1 + A1 B0
+        mma_run<7, 0, 2 * G>(tmem, ad, bd, true);        // D0 = A0 B0
         mma_commit(bar_m);
         mma_in_flight = true;
       }
@@ -384,43 +463,59 @@ __global__ void __launch_bounds__(kMmaThreads, 1) plan_level_mma_kernel(
       bulk_wait_read();  // the previous item's store has read the staging buffer
     }
     __syncthreads();
-    // read-back: warps w and w+4 read TMEM lanes 32(w%4).. (tile rows) and
-    // split the 7 column chunks (4 + 3); the states go to staging row m
-    // destination rows rR + i0 + (0 .. ndst): a prefix of the tile (i < R and
-    // rR + i < n), possibly empty
+    // read-back: warps w and w+4 read TMEM lanes 32(w%4).. (tile rows);
+    // warp w < 4 takes the column chunks 0-2 and column 96, warp w + 4 the
+    // chunks 3-5 (16 columns each).  All loads of a phase are issued before
+    // the one wait.  The states go to staging row m; destination rows rR +
+    // i0 + (0 .. ndst): a prefix of the tile (i < R and rR + i < n),
+    // possibly empty.
     const uint64_t dst0 = static_cast<uint64_t>(r) * R + i0;
     const uint32_t ndst =
         dst0 >= n ? 0u
                   : static_cast<uint32_t>(min(static_cast<uint64_t>(nsrc), n - dst0));
     uint32_t* srow = reinterpret_cast<uint32_t*>(stage) + m * (sizeof(ranmar_state_t) / 4);
     const uint32_t lane_base = tmem + ((quarter * 32u) << 16);
-    const int c_lo = warp < 4 ? 0 : 4, c_hi = warp < 4 ? 4 : kMmaN / 16;
-#pragma unroll 1
-    for (int c = c_lo; c < c_hi; ++c) {
-      uint32_t f0[16], f1[16], f2[16], f3[16];
-      tmem_ld16(lane_base + 16 * c, f0);
-      tmem_ld16(lane_base + 128 + 16 * c, f1);
-      tmem_ld16(lane_base + 256 + 16 * c, f2);
-      tmem_ld16(lane_base + 384 + 16 * c, f3);
-      tmem_ld_wait();
-      uint32_t w[16];
+    const int c0 = warp < 4 ? 0 : 3;
+    {
+      uint32_t f[2][4][16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        // |D| < 2^22: D + 1.5 * 2^23 is exact and its bits are 0x4B400000 + D
-        const uint32_t b0 = __float_as_uint(__uint_as_float(f0[j]) + 12582912.0f);
-        const uint32_t b1 = __float_as_uint(__uint_as_float(f1[j]) + 12582912.0f);
-        const uint32_t b2 = __float_as_uint(__uint_as_float(f2[j]) + 12582912.0f) +
-                            __float_as_uint(__uint_as_float(f3[j]) + 12582912.0f);
-        w[j] = (b0 + (b1 << 8) + (b2 << 16) - kMagicMix) & kMask24;
-      }
-      if (c < kMmaN / 16 - 1) {
-        uint4* o4 = reinterpret_cast<uint4*>(srow + 16 * c);
+      for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) tmem_ld16(lane_base + 128 * d + 16 * (c0 + cc), f[cc][d]);
+      tmem_ld_wait();
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) tmem_regs_fence(f[cc][d]);
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        uint4* o4 = reinterpret_cast<uint4*>(srow + 16 * (c0 + cc));
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          o4[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
-      } else {
-        srow[96] = w[0];
+          o4[j] = make_uint4(limb_sum(f[cc], 4 * j), limb_sum(f[cc], 4 * j + 1),
+                             limb_sum(f[cc], 4 * j + 2), limb_sum(f[cc], 4 * j + 3));
       }
+    }
+    {
+      uint32_t f[4][16], g[4][1];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) tmem_ld16(lane_base + 128 * d + 16 * (c0 + 2), f[d]);
+      if (warp < 4) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) tmem_ld1(lane_base + 128 * d + 96, g[d]);
+      }
+      tmem_ld_wait();
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        tmem_regs_fence(f[d]);
+        tmem_regs_fence(g[d]);
+      }
+      uint4* o4 = reinterpret_cast<uint4*>(srow + 16 * (c0 + 2));
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        o4[j] = make_uint4(limb_sum(f, 4 * j), limb_sum(f, 4 * j + 1), limb_sum(f, 4 * j + 2),
+                           limb_sum(f, 4 * j + 3));
+      if (warp < 4) srow[96] = limb_sum(g, 0);
     }
     if (warp < 4) {
       ranmar_state_t* so = reinterpret_cast<ranmar_state_t*>(srow);
@@ -440,7 +535,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1) plan_level_mma_kernel(
     if (s_in_flight) mbar_wait(bar_s, ph_s);
     if (mma_in_flight) mbar_wait(bar_m, ph_m);
   }
-  if (tid == 0) bulk_wait_all();
+  // the staging buffer must outlive the reads of the last store; its writes
+  // complete with the grid
+  if (tid == 0) bulk_wait_read();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
