@@ -341,6 +341,11 @@ int ranmar_plan_expand(const ranmar_plan_t *p, ranmar_state_t *d_states, size_t 
  *     copy);
  *   RANMAR_PLAN_IMAD: blocked 32-bit integer multiply-adds.
  * ranmar_plan_set_method: RANMAR_EINVAL for an unknown method.
+ * ranmar_plan_set_ctas: the number of CTAs a tensor-core level launches (one
+ *   CTA per SM at most, each taking a balanced range of (tile, matrix)
+ *   items); 0 (the default) = one per SM.  Fewer CTAs leave the other SMs
+ *   to work on another stream at the same time (e.g. the generation of the
+ *   previous batch).  RANMAR_EINVAL above 65535.
  * ranmar_plan_status: device pointer to the plan's status word (bit
  * RANMAR_ST_TIMEOUT if a tensor-core level gave up on a bounded wait; then
  * the states it was to write are not valid).  Cleared at plan creation.
@@ -348,6 +353,7 @@ int ranmar_plan_expand(const ranmar_plan_t *p, ranmar_state_t *d_states, size_t 
 #define RANMAR_PLAN_TENSOR 0
 #define RANMAR_PLAN_IMAD 1
 int ranmar_plan_set_method(ranmar_plan_t *p, int method);
+int ranmar_plan_set_ctas(ranmar_plan_t *p, unsigned ctas);
 int ranmar_plan_status(const ranmar_plan_t *p, uint32_t **d_status);
 
 /* ------------------------------------------------------------------------

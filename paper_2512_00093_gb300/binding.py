@@ -92,6 +92,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_partition_plan.argtypes = [_vp, _vp, _u64, _sz, _vp, _vp]
     lib.ranmar_partition_plan.restype = ctypes.c_int
     lib.ranmar_plan_set_method.argtypes = [_vp, ctypes.c_int]
+    lib.ranmar_plan_set_ctas.argtypes = [_vp, ctypes.c_uint]
     lib.ranmar_lfg_jump.argtypes = [_u32, _u32, _u32, ctypes.c_int, _vp, _sz, _vp, _vp, _u32, _vp,
                                     _sz, _vp, _vp]
     lib.ranmar_lfg_jump.restype = ctypes.c_int
@@ -749,6 +750,10 @@ class Plan:
     def set_method(self, method: int) -> None:
         """ranmar_plan_set_method (Plan.TENSOR or Plan.IMAD)."""
         _check(_lib().ranmar_plan_set_method(self._h, int(method)), "ranmar_plan_set_method")
+
+    def set_ctas(self, ctas: int) -> None:
+        """ranmar_plan_set_ctas: CTAs of a tensor-core level (0 = one per SM)."""
+        _check(_lib().ranmar_plan_set_ctas(self._h, int(ctas)), "ranmar_plan_set_ctas")
 
     def status(self) -> int:
         """The plan's device status word (synchronises the device)."""

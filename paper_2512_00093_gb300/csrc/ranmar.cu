@@ -51,12 +51,13 @@ struct ranmar_plan {
   int levels;          // level t: R_t known streams -> R_t * radix(t)
   int mat_off[ranmar::kPlanMaxLevels];  // first matrix of each level
   uint32_t* mats;      // per level radix - 1 matrices of 97 x 112: M_{r R_t J}
-  uint8_t* bimg;       // levels x 15 fp16 limb images of the same matrices
-  uint32_t* ced;       // levels x 15: (E mod m) d mod m
-  uint64_t* pose;      // levels x 15: E mod 2^64
+  uint8_t* bimg;       // fp16 limb images of the same matrices
+  uint32_t* ced;       // per matrix: (E mod m) d mod m
+  uint64_t* pose;      // per matrix: E mod 2^64
   uint32_t* status;    // device status word of the tensor-core levels
   int method;          // RANMAR_PLAN_TENSOR or RANMAR_PLAN_IMAD
   int num_sms;
+  unsigned ctas;       // CTAs of a tensor-core level (0: one per SM)
 };
 
 struct ranmar_graph {
@@ -1158,6 +1159,12 @@ int ranmar_plan_set_method(ranmar_plan_t* p, int method) {
   return RANMAR_OK;
 }
 
+int ranmar_plan_set_ctas(ranmar_plan_t* p, unsigned ctas) {
+  if (!p || ctas > 65535u) return RANMAR_EINVAL;
+  p->ctas = ctas;
+  return RANMAR_OK;
+}
+
 int ranmar_plan_status(const ranmar_plan_t* p, uint32_t** d_status) {
   if (!p || !d_status) return RANMAR_EINVAL;
   *d_status = p->status;
@@ -1183,8 +1190,8 @@ int ranmar_plan_expand(const ranmar_plan_t* p, ranmar_state_t* d_states, size_t 
       // items (tile, r): tiles of 128 source rows
       const uint64_t tiles = (R + ranmar::kMmaM - 1) / ranmar::kMmaM;
       const uint64_t items = tiles * rc;
-      const unsigned grid = static_cast<unsigned>(
-          items < static_cast<uint64_t>(p->num_sms) ? items : static_cast<uint64_t>(p->num_sms));
+      const uint64_t want = p->ctas ? p->ctas : static_cast<uint64_t>(p->num_sms);
+      const unsigned grid = static_cast<unsigned>(items < want ? items : want);
       ranmar::plan_level_mma_kernel<<<grid, ranmar::kMmaThreads, ranmar::kMmaSmemBytes, s>>>(
           d_states, R, n, static_cast<uint32_t>(rc), static_cast<uint32_t>(items),
           p->bimg + static_cast<size_t>(mo) * ranmar::kBImgBytes, p->ced + mo, p->pose + mo,

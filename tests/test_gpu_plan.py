@@ -86,6 +86,25 @@ def test_plan_host_checks(rm, table):
     plan.close()
 
 
+@pytest.mark.parametrize("ctas", [1, 3, 7, 32, 151, 600])
+def test_plan_ctas(rm, table, ctas):
+    """A tensor-core level on fewer (or more) CTAs than SMs: every CTA takes a
+    balanced range of (tile, matrix) items; the states do not change."""
+    dev = torch.device("cuda:0")
+    J = 1 << 40
+    base = rm.seed(12345).to(dev)
+    plan = rm.Plan(table, J, 70000)
+    ref = table.partition(base, J, 7, 70000)
+    plan.set_ctas(ctas)
+    got = plan.partition(base, 7, 70000)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+    assert plan.status() == 0
+    with pytest.raises(rm.RanmarError):
+        plan.set_ctas(70000)
+    plan.close()
+
+
 def test_plan_expand_from_table_rows(rm, table):
     """expand() from the first 256 rows computed elsewhere (the table
     partition on another stream) gives the same states as one partition_plan

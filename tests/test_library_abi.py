@@ -85,6 +85,8 @@ def test_host_argument_checks(lib):
     assert L.ranmar_generate_f32(fake, 1, fake, 1, vp(0x20002), 10, None, None) == -1
     assert L.ranmar_generate_plain_u24(None, 10, fake, 1, None) == -1
     assert L.ranmar_generate_plain_u24(fake, 10, None, 1, None) == -1
+    L.ranmar_plan_set_ctas.argtypes = [ctypes.c_void_p, ctypes.c_uint]
+    assert L.ranmar_plan_set_ctas(None, 4) == -1
 
 
 def test_workload_recipes():
