@@ -42,6 +42,23 @@ sys.path.insert(0, ROOT)
 
 METRIC = "outputs/s & HBM fraction; jumps/s at J≈2^120; batched vs per-stream launch"
 UNIT = "outputs/s"
+# The paper's own single-CPU measurements (Sec. 4): Table 1, seconds for
+# 10^9 outputs (floating point as in LAMMPS, 24-bit modular), and Table 2,
+# microseconds for t^J mod phi with NTL.  Context beside the measured
+# numbers, not a target.
+PAPER_CPUS = ["Apple M2 Pro", "Raspberry Pi 4B (Cortex-A72, 1.5 GHz)",
+              "Threadripper 3970X (3.7 GHz)", "Core i7-14700F (5.3 GHz)"]
+PAPER_TABLE1_S = {"float": [3.30, 16.60, 8.45, 3.31], "modular": [1.27, 6.14, 2.07, 1.01]}
+PAPER_TABLE2_US = {"2^64-1": [1347, 10395, 946, 2702], "2^120-1": [2556, 21411, 1946, 4697]}
+
+
+def paper_cpu_context() -> dict:
+    return {"note": "the paper's single-CPU numbers (Tables 1-2), context only",
+            "cpus": PAPER_CPUS,
+            "modular_outputs_per_s": [1e9 / t for t in PAPER_TABLE1_S["modular"]],
+            "modular_speedup_vs_float": [f / q for f, q in zip(PAPER_TABLE1_S["float"],
+                                                                PAPER_TABLE1_S["modular"])],
+            "poly_powers_per_s_J_2^120-1": [1e6 / t for t in PAPER_TABLE2_US["2^120-1"]]}
 L2_BYTES = 129 * 2**20
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
@@ -580,6 +597,7 @@ def run_ours(args):
                         "step (copies on their own streams, double-buffered)"},
         "gpu_launches": 3 * K,
         "library": rbuild.LIB,
+        "paper_cpu_context": paper_cpu_context(),
     }
 
     if not args.no_extras:
