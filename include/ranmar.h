@@ -60,6 +60,8 @@ extern "C" {
 #define RANMAR_ST_BAD_SEED 4u     /* seed outside 1..900000000              */
 #define RANMAR_ST_TIMEOUT 8u      /* a bounded device wait ran out (the CTA  */
                                   /* left its work undone and returned)      */
+#define RANMAR_ST_OVERLAP 16u     /* a generation would leave its stream     */
+                                  /* (ranmar_check_overlap; not an error)    */
 
 /* Descriptor flags. */
 #define RANMAR_DESC_WRITE_BACK 1u /* store the advanced state after output  */
@@ -183,6 +185,28 @@ int ranmar_generate_f32(ranmar_state_t *d_states, size_t n_states,
                         const ranmar_desc_t *d_desc, size_t n_desc,
                         float *d_out, size_t out_len,
                         uint32_t *d_status, ranmar_stream_t stream);
+
+/*
+ * ranmar_check_overlap -- the non-overlap condition of the partition
+ * (Sec. 1): stream k of (base, J) owns the transitions [kJ, (k+1)J), so
+ * `count` outputs from a state at position pos stay inside it iff off = pos
+ * - kJ satisfies off <= J and count <= J - off.  For each descriptor i (its
+ * state d_states[state_idx] as it is BEFORE the generation, d_k[i] the
+ * stream index that state belongs to) a generation that would leave the
+ * stream OR-s RANMAR_ST_OVERLAP into *d_status.  Nothing is refused or
+ * changed: such outputs are still RANMAR outputs, only no longer disjoint
+ * from stream k+1's.  off is computed mod 2^64 (the state keeps pos mod
+ * 2^64), exact while the true offset is below 2^64; for J >= 2^64 only off
+ * + count > 2^64 is flagged.  h_J: J as J_words little-endian 32-bit words.
+ * Errors: RANMAR_EINVAL (a null pointer with n_desc > 0, d_status NULL,
+ * misaligned states, descriptors or d_k), RANMAR_ERANGE (J_words not in
+ * 1..5, J = 0, n_states = 0 with n_desc > 0).  Device: RANMAR_ST_BAD_INDEX
+ * for state_idx >= n_states.
+ */
+int ranmar_check_overlap(const ranmar_state_t *d_states, size_t n_states,
+                         const ranmar_desc_t *d_desc, size_t n_desc,
+                         const uint64_t *d_k, const uint32_t *h_J, uint32_t J_words,
+                         uint32_t *d_status, ranmar_stream_t stream);
 
 /*
  * ranmar_generate_alg1_f32 / _f64 -- Algorithm 1 (Sec. 4, the floating-point

@@ -25,6 +25,8 @@ DESC_WRITE_BACK = 1
 ST_BAD_INDEX = 1
 ST_OUT_RANGE = 2
 ST_BAD_SEED = 4
+ST_TIMEOUT = 8
+ST_OVERLAP = 16
 
 OK, EINVAL, ERANGE, ECUDA, ENOMEM, EDEVICE = 0, -1, -2, -3, -4, -5
 
@@ -64,6 +66,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_partition.argtypes = [_vp, _vp, _u32, _u64, _vp, _sz, _vp]
     for name in ("ranmar_generate_u24", "ranmar_generate_f32"):
         getattr(lib, name).argtypes = [_vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp]
+    lib.ranmar_check_overlap.argtypes = [_vp, _sz, _vp, _sz, _vp, _vp, _u32, _vp, _vp]
     for name in ("ranmar_generate_plain_u24", "ranmar_generate_plain_f32"):
         getattr(lib, name).argtypes = [_vp, _u64, _vp, ctypes.c_int, _vp]
     lib.ranmar_batch_create.argtypes = [_sz, ctypes.POINTER(_vp)]
@@ -354,6 +357,24 @@ def _generate(fn: str, out_dtype, states, desc, out, status, stream):
 def generate_u24(states, desc, out, status=None, stream=None):
     """ranmar_generate_u24 over a descriptor batch; out is int32 (24-bit values)."""
     return _generate("ranmar_generate_u24", torch.int32, states, desc, out, status, stream)
+
+
+def check_overlap(states, desc, k, J: int, status=None, stream=None) -> torch.Tensor:
+    """ranmar_check_overlap: ORs ST_OVERLAP into `status` ((1,) int32, created
+    zeroed when None) for every descriptor whose generation would leave its
+    stream k[i] of spacing J (the states as they are before generating)."""
+    states = states.reshape(-1, STATE_WORDS)
+    _need(states, torch.int32, "states")
+    _need(desc, torch.int64, "desc")
+    _need(k, torch.int64, "k")
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=states.device)
+    _need(status, torch.int32, "status")
+    jw = np.array(words(int(J)), dtype=np.uint32)
+    _check(_lib().ranmar_check_overlap(_ptr(states), states.shape[0], _ptr(desc), desc.shape[0],
+                                       _ptr(k), jw.ctypes.data, len(jw), _ptr(status),
+                                       _stream(stream)), "ranmar_check_overlap")
+    return status
 
 
 def generate_f32(states, desc, out, status=None, stream=None):

@@ -19,6 +19,7 @@
 #include "plan.cuh"
 #include "plan_mma.cuh"
 #include "lfg.cuh"
+#include "overlap.cuh"
 
 // Batch handle: the workspace of the persistent path on one device.
 struct ranmar_batch {
@@ -550,6 +551,32 @@ int ranmar_generate_f32(ranmar_state_t* d_states, size_t n_states, const ranmar_
                         ranmar_stream_t stream) {
   return launch_generate(true, d_states, n_states, d_desc, n_desc, d_out, out_len, d_status,
                          stream);
+}
+
+int ranmar_check_overlap(const ranmar_state_t* d_states, size_t n_states,
+                         const ranmar_desc_t* d_desc, size_t n_desc, const uint64_t* d_k,
+                         const uint32_t* h_J, uint32_t J_words, uint32_t* d_status,
+                         ranmar_stream_t stream) {
+  if (!h_J) return RANMAR_EINVAL;
+  if (J_words < 1 || J_words > RANMAR_MAX_EXP_WORDS) return RANMAR_ERANGE;
+  bool zero = true, big = false;
+  for (uint32_t w = 0; w < J_words; ++w) {
+    zero = zero && h_J[w] == 0;
+    big = big || (w >= 2 && h_J[w] != 0);
+  }
+  if (zero) return RANMAR_ERANGE;
+  if (n_desc == 0) return RANMAR_OK;
+  if (!d_states || !d_desc || !d_k || !d_status) return RANMAR_EINVAL;
+  if (n_states == 0) return RANMAR_ERANGE;
+  if (!aligned(d_states, 16) || !aligned(d_desc, 8) || !aligned(d_k, 8)) return RANMAR_EINVAL;
+  const uint64_t J_lo = static_cast<uint64_t>(h_J[0]) |
+                        (J_words > 1 ? static_cast<uint64_t>(h_J[1]) << 32 : 0ull);
+  uint64_t blocks = (n_desc + 255) / 256;
+  if (blocks > (1u << 20)) blocks = 1u << 20;
+  ranmar::overlap_check_kernel<<<static_cast<unsigned>(blocks), 256, 0,
+                                 reinterpret_cast<cudaStream_t>(stream)>>>(
+      d_states, n_states, d_desc, n_desc, d_k, J_lo, big ? 1 : 0, d_status);
+  return check_launch();
 }
 
 int ranmar_generate_plain_u24(ranmar_state_t* d_state, uint64_t count, uint32_t* d_out,

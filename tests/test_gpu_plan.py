@@ -144,3 +144,41 @@ def test_plan_million_streams_equals_table(rm, table):
         del got
     assert plan.status() == 0
     plan.close()
+
+
+def test_partitioned_full_size_bench_path(rm, table, orc):
+    """The benchmark's step at full size (65,536 streams x 4,096 u24 outputs,
+    J = 2^40, a batch that starts at k0 = 5 * 65,536): the first 256 streams
+    by the table jump on a side stream, the tensor-core level for the rest,
+    then generation with write-back; 256 sampled rows and their advanced
+    states against the oracle."""
+    from paper_2512_00093_gb300.workloads import Partitioned
+    w = Partitioned()
+    dev = torch.device("cuda:0")
+    n, count, k0 = w.n_streams, w.count, 5 * w.n_streams
+    base = rm.seed(w.seed).to(dev)
+    plan = rm.Plan(table, w.J, n)
+    states = torch.empty((n, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+    out = torch.empty((n, count), dtype=torch.int32, device=dev)
+    desc = rm.make_desc(np.arange(n), np.arange(n) * count, count, rm.DESC_WRITE_BACK,
+                        device=dev)
+    side, main = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    table.partition(base, w.J, k0, 256, out=states[:256], stream=side)
+    ev = torch.cuda.Event()
+    ev.record(side)
+    main.wait_event(ev)
+    plan.expand(states, n, stream=main)
+    rm.generate_u24(states, desc, out, stream=main)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    rows = w.verify_rows()
+    got = out[torch.as_tensor(rows, device=dev)].cpu().numpy().view(np.uint32)
+    after = rm.state_words_np(states)
+    x0, c0 = orc.seeded_state(w.seed)
+    for q, (r, row) in enumerate(zip(rows, got)):
+        E = (k0 + int(r)) * w.J
+        assert np.array_equal(row, orc.stream(w.seed, E, count)), int(r)
+        if q % 32 == 0:
+            xs, cs = orc.jump(x0, c0, E + count)
+            assert np.array_equal(after[r, :97], xs) and after[r, 97] == cs, int(r)
+    plan.close()

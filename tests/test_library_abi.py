@@ -87,6 +87,20 @@ def test_host_argument_checks(lib):
     assert L.ranmar_generate_plain_u24(fake, 10, None, 1, None) == -1
     L.ranmar_plan_set_ctas.argtypes = [ctypes.c_void_p, ctypes.c_uint]
     assert L.ranmar_plan_set_ctas(None, 4) == -1
+    L.ranmar_check_overlap.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                       ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]
+    jw = np.array([1000], dtype=np.uint32)
+    zero = np.array([0, 0], dtype=np.uint32)
+    d = jw.ctypes.data
+    assert L.ranmar_check_overlap(fake, 1, fake, 1, fake, None, 1, fake, None) == -1  # J null
+    assert L.ranmar_check_overlap(fake, 1, fake, 1, fake, d, 0, fake, None) == -2     # words
+    assert L.ranmar_check_overlap(fake, 1, fake, 1, fake, d, 6, fake, None) == -2
+    assert L.ranmar_check_overlap(fake, 1, fake, 1, fake, zero.ctypes.data, 2, fake,
+                                  None) == -2                                          # J = 0
+    assert L.ranmar_check_overlap(None, 0, None, 0, None, d, 1, None, None) == 0     # n = 0
+    assert L.ranmar_check_overlap(fake, 1, fake, 1, fake, d, 1, None, None) == -1    # status
+    assert L.ranmar_check_overlap(fake, 0, fake, 1, fake, d, 1, fake, None) == -2    # n_states
 
 
 def test_workload_recipes():
