@@ -55,6 +55,13 @@ class Request:
     def key(self):
         return (self.seed, self.k, self.J)
 
+    @property
+    def overlaps(self) -> bool:
+        """The request runs past the end (k+1)J of its stream (Sec. 1): its
+        outputs are still served, but they are no longer disjoint from
+        stream k+1's."""
+        return self.offset + self.count > self.J
+
 
 def assign_offsets(reqs) -> None:
     """Resume semantics: offset = sum of counts of earlier arrivals of the stream."""
@@ -538,4 +545,5 @@ def summarize(reqs) -> dict:
             "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
             "mean_ms": float(lat.mean() * 1e3) if lat.size else None,
-            "span_s": span, "outputs_per_s": outs / span if span > 0 else None}
+            "span_s": span, "outputs_per_s": outs / span if span > 0 else None,
+            "overlapping_requests": sum(1 for r in reqs if r.overlaps)}

@@ -2,6 +2,7 @@
 rows, the output allocator, and the request recipe."""
 import numpy as np
 
+from paper_2512_00093_gb300 import serve
 from paper_2512_00093_gb300.serve import FirstFit, Request, assign_offsets, exp_rows
 from paper_2512_00093_gb300.workloads import Serving
 
@@ -52,3 +53,17 @@ def test_serving_recipe():
     # log-uniform 10^3..10^7: mean (10^7 - 10^3) / (4 ln 10) ~ 1.09e6
     assert abs(counts.mean() / 1.085e6 - 1) < 0.1
     assert abs(f32.mean() - 0.5) < 0.02
+
+
+def test_overlap_flag_in_summary():
+    """A request that runs past (k+1)J of its stream is served and counted as
+    overlapping (Sec. 1); the requests before it are not."""
+    J = 100
+    reqs = serve.make_requests(np.array([0.0, 0.1, 0.2, 0.3]), np.array([7, 7, 7, 8]),
+                               np.array([3, 3, 3, 3]), np.array([60, 40, 1, 101]),
+                               np.array([False] * 4), J)
+    assert [r.offset for r in reqs] == [0, 60, 100, 0]
+    assert [r.overlaps for r in reqs] == [False, False, True, True]
+    for r in reqs:
+        r.done = r.t + 0.001
+    assert serve.summarize(reqs)["overlapping_requests"] == 2
