@@ -59,6 +59,15 @@ __device__ __forceinline__ LaneConsts lane_consts(unsigned gl) {
 // Registers of one stream on its group of W lanes: the rotated ring, the
 // carry (lane 0: the last word of the previous block), this lane's c and the
 // output pointer.
+//
+// Store alignment: a step writes W consecutive outputs.  When the stream's
+// output offset is not a multiple of W (a = out_base mod W, packed uneven
+// batches), every such store would straddle two W-word windows.  The
+// realigned mode rotates each step's outputs by a lanes (one more shuffle):
+// lane L stores the output of lane (L - a) mod W, taken from the current
+// step for L >= a and from the previous step (`up`) for L < a, so every
+// store fills one aligned window; the first window (lanes below a skip it)
+// and the last one or two are partial.
 template <int W, bool F32>
 struct GenCtx {
   static constexpr int NR = 96 / W;  // ring registers: blocks b-NR .. b-1
@@ -67,11 +76,16 @@ struct GenCtx {
   using T = typename OutT<F32>::type;
   uint32_t r[NR];
   uint32_t carry;
-  uint32_t cl;  // c_{Wb+L+1} for the step b the lane is on
-  T* p;
+  uint32_t cl;     // c_{Wb+L+1} for the step b the lane is on
+  T* p;            // out + (out_base - a) + L (a = 0 unless realigned)
+  unsigned ssrc;   // the lane whose output this lane stores when realigned, (L - a) mod W
+  bool lo;         // realigned: L < a (stores the previous step's output)
+  uint32_t up;     // realigned: this lane's rotated output of the previous step
 };
 
-template <int W, bool F32>
+// kRealign: prepare realigned stores (p at the aligned window, ssrc, lo);
+// otherwise p = out + out_base + L and the stores are never realigned.
+template <int W, bool F32, bool kRealign>
 __device__ __forceinline__ void gen_load(GenCtx<W, F32>& g, const ranmar_state_t* st, void* out,
                                          uint64_t out_base, unsigned gl, const LaneConsts& k) {
   const uint32_t* xs = st->x;
@@ -79,26 +93,51 @@ __device__ __forceinline__ void gen_load(GenCtx<W, F32>& g, const ranmar_state_t
   for (int j = 0; j < GenCtx<W, F32>::NR; ++j) g.r[j] = xs[W * j + gl];  // R_{j-NR}[L] = X(W(j-NR) + L - 1)
   g.carry = xs[96];                                                       // X(-1)
   g.cl = sub_mod_m(st->c, k.delta_lane);                                  // c_{L+1}
-  g.p = static_cast<typename GenCtx<W, F32>::T*>(out) + out_base + gl;
+  const unsigned a = kRealign ? static_cast<unsigned>(out_base % W) : 0u;  // same on the group
+  g.ssrc = (gl + W - a) % W;
+  g.lo = gl < a;
+  g.up = 0;
+  g.p = static_cast<typename GenCtx<W, F32>::T*>(out) + (out_base - a) + gl;
 }
 
-// Step j of a ring turn: R_b into r[j] (= R_{b-NR} on entry), output to p[W j].
-template <int W, bool F32>
+// Step j of a ring turn: R_b into r[j] (= R_{b-NR} on entry), the outputs to
+// window p[W j].  kRot: realigned stores; kFirst: the stream's first step
+// (in the realigned mode the lanes below a have nothing to store yet).
+template <int W, bool F32, bool kRot, bool kFirst>
 __device__ __forceinline__ void gen_step(GenCtx<W, F32>& g, int j, unsigned gl, unsigned gmask,
                                          unsigned src, uint32_t dw, uint32_t mdw) {
   constexpr int NR = GenCtx<W, F32>::NR, Q = GenCtx<W, F32>::Q;
   const uint32_t xv = g.r[j] - g.r[(j + NR - Q) % NR];  // X(Wb + L), kept mod 2^32
-  store_output<F32>(g.p + W * j, (xv - g.cl) & kMask24);
+  const uint32_t y = (xv - g.cl) & kMask24;
+  if constexpr (kRot) {
+    const uint32_t u = __shfl_sync(gmask, y, g.ssrc, W);
+    const uint32_t v = g.lo ? g.up : u;
+    g.up = u;
+    if (!(kFirst && g.lo)) store_output<F32>(g.p + W * j, v);
+  } else {
+    store_output<F32>(g.p + W * j, y);
+  }
   g.cl = step_c(g.cl, dw, mdw);
   const uint32_t t = __shfl_sync(gmask, xv, src, W);
   g.r[j] = (gl == 0) ? g.carry : t;
   g.carry = t;
 }
 
+// One ring turn of steps (the first step of the stream when kFirst).
+template <int W, bool F32, bool kRot, bool kFirst>
+__device__ __forceinline__ void gen_turn(GenCtx<W, F32>& g, unsigned gl, unsigned gmask,
+                                         unsigned src, uint32_t dw, uint32_t mdw) {
+  constexpr int NR = GenCtx<W, F32>::NR;
+  gen_step<W, F32, kRot, kFirst>(g, 0, gl, gmask, src, dw, mdw);
+#pragma unroll
+  for (int j = 1; j < NR; ++j) gen_step<W, F32, kRot, false>(g, j, gl, gmask, src, dw, mdw);
+  g.p += W * NR;
+}
+
 // Continues the stream from block b0 (a multiple of NR; the context holds
 // R_{b0-NR} .. R_{b0-1}) to `count` outputs, then optionally writes the
 // advanced state back.
-template <int W, bool F32>
+template <int W, bool F32, bool kRot>
 __device__ void gen_finish(GenCtx<W, F32>& g, ranmar_state_t* st, uint64_t count, uint64_t b0,
                            bool write_back, unsigned gl, unsigned gmask, const LaneConsts& k) {
   constexpr int NR = GenCtx<W, F32>::NR, Q = GenCtx<W, F32>::Q;
@@ -107,16 +146,19 @@ __device__ void gen_finish(GenCtx<W, F32>& g, ranmar_state_t* st, uint64_t count
   const unsigned src = (gl + W - 1) % W;
   const uint32_t dw = k.delta_w, mdw = kModM - k.delta_w;
   uint64_t b = b0;
-#pragma unroll 1
-  for (; b + NR <= nblk; b += NR) {
-#pragma unroll
-    for (int j = 0; j < NR; ++j) gen_step<W, F32>(g, j, gl, gmask, src, dw, mdw);
-    g.p += W * NR;
+  if (kRot && b == 0 && nblk >= NR) {
+    gen_turn<W, F32, kRot, true>(g, gl, gmask, src, dw, mdw);
+    b = NR;
   }
+#pragma unroll 1
+  for (; b + NR <= nblk; b += NR) gen_turn<W, F32, kRot, false>(g, gl, gmask, src, dw, mdw);
   // Remaining blocks: step, then shift the ring so that r[0] stays oldest.
 #pragma unroll 1
   for (; b < nblk; ++b) {
-    gen_step<W, F32>(g, 0, gl, gmask, src, dw, mdw);
+    if (kRot && b == 0)
+      gen_step<W, F32, kRot, true>(g, 0, gl, gmask, src, dw, mdw);
+    else
+      gen_step<W, F32, kRot, false>(g, 0, gl, gmask, src, dw, mdw);
     g.p += W;
     const uint32_t nw = g.r[0];
 #pragma unroll
@@ -126,8 +168,18 @@ __device__ void gen_finish(GenCtx<W, F32>& g, ranmar_state_t* st, uint64_t count
 
   // Ragged tail: one more block with masked stores.
   uint32_t xb = 0;
-  if (rem != 0) {
-    xb = g.r[0] - g.r[NR - Q];  // X(WB + L)
+  if (rem != 0) xb = g.r[0] - g.r[NR - Q];  // X(WB + L)
+  if constexpr (kRot) {
+    // window nblk: lanes below a hold the last full step's outputs (position
+    // W nblk - a + L), the others the tail's (W nblk + L - a); window nblk+1:
+    // lanes below a, the tail's positions W (nblk + 1) + L - a
+    const uint32_t ut = __shfl_sync(gmask, (xb - g.cl) & kMask24, g.ssrc, W);
+    const int a = static_cast<int>((gl + W - g.ssrc) % W);
+    const int64_t rel = static_cast<int64_t>(W * nblk) + static_cast<int>(gl) - a;
+    if (rel >= 0 && rel < static_cast<int64_t>(count)) store_output<F32>(g.p, g.lo ? g.up : ut);
+    if (g.lo && W + static_cast<int>(gl) - a < static_cast<int>(rem))
+      store_output<F32>(g.p + W, ut);
+  } else {
     if (gl < rem) store_output<F32>(g.p, (xb - g.cl) & kMask24);
   }
 
@@ -157,54 +209,98 @@ __device__ void gen_finish(GenCtx<W, F32>& g, ranmar_state_t* st, uint64_t count
 // Generates `count` outputs of *st into out[out_base + n], n < count, and
 // optionally writes the advanced state back.  Called by the W lanes of one
 // group (gl = lane within the group, gmask = the group's lane mask).
-template <int W, bool F32>
+// kRealign: realigned stores for offsets that are not multiples of W (the
+// persistent batch kernel, whose packed outputs start anywhere); the
+// one-warp-per-descriptor and fused kernels store unrealigned, which keeps
+// their register count (and occupancy) of the aligned case.
+template <int W, bool F32, bool kRealign = false>
 __device__ void generate_stream(ranmar_state_t* st, uint64_t count, void* out, uint64_t out_base,
                                 bool write_back, unsigned gl, unsigned gmask,
                                 const LaneConsts& k) {
   GenCtx<W, F32> g;
-  gen_load<W, F32>(g, st, out, out_base, gl, k);
-  gen_finish<W, F32>(g, st, count, 0, write_back, gl, gmask, k);
+  gen_load<W, F32, kRealign>(g, st, out, out_base, gl, k);
+  if (kRealign && g.ssrc != gl)
+    gen_finish<W, F32, kRealign>(g, st, count, 0, write_back, gl, gmask, k);
+  else
+    gen_finish<W, F32, false>(g, st, count, 0, write_back, gl, gmask, k);
+}
+
+// The interleaved part of generate_streams: `common` blocks (whole ring
+// turns) of all S streams, their steps alternating.
+template <int W, bool F32, int S, bool kRot>
+__device__ __forceinline__ void gen_interleaved(GenCtx<W, F32> (&g)[S], uint64_t common,
+                                                unsigned gl, unsigned gmask, unsigned src,
+                                                uint32_t dw, uint32_t mdw) {
+  constexpr int NR = GenCtx<W, F32>::NR;
+  uint64_t b = 0;
+  if (kRot && common > 0) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) gen_step<W, F32, kRot, true>(g[s], 0, gl, gmask, src, dw, mdw);
+#pragma unroll
+    for (int j = 1; j < NR; ++j) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) gen_step<W, F32, kRot, false>(g[s], j, gl, gmask, src, dw, mdw);
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) g[s].p += W * NR;
+    b = NR;
+  }
+#pragma unroll 1
+  for (; b < common; b += NR) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) gen_step<W, F32, kRot, false>(g[s], j, gl, gmask, src, dw, mdw);
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) g[s].p += W * NR;
+  }
 }
 
 // S streams on one group at once: their steps are independent dependency
 // chains (shuffle -> subtract -> shuffle), so interleaving them hides the
 // chain latency with S times fewer resident warps.  The blocks all S have
-// (rounded down to whole ring turns) run interleaved; each stream then
-// finishes alone.  ok[s] = false skips stream s (and the interleaved part).
-template <int W, bool F32, int S>
+// (rounded down to whole ring turns) run interleaved (realigned for all S
+// when any of them needs it: with a = 0 that mode stores the same words);
+// each stream then finishes alone.  ok[s] = false skips stream s (and the
+// interleaved part).
+template <int W, bool F32, int S, bool kRealign = false>
 __device__ void generate_streams(ranmar_state_t* const (&st)[S], const uint64_t (&count)[S],
                                  void* out, const uint64_t (&out_base)[S],
                                  const bool (&write_back)[S], const bool (&ok)[S], unsigned gl,
                                  unsigned gmask, const LaneConsts& k) {
   constexpr int NR = GenCtx<W, F32>::NR;
   GenCtx<W, F32> g[S];
-  bool all = true;
+  bool all = true, rot = false;
   uint64_t common = ~0ull;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     all = all && ok[s];
     if (ok[s]) {
-      gen_load<W, F32>(g[s], st[s], out, out_base[s], gl, k);
+      gen_load<W, F32, kRealign>(g[s], st[s], out, out_base[s], gl, k);
       common = min(common, count[s] / W);
+      rot = rot || g[s].ssrc != gl;
     }
   }
   if (!all) common = 0;
   common -= common % NR;
   const unsigned src = (gl + W - 1) % W;
   const uint32_t dw = k.delta_w, mdw = kModM - k.delta_w;
-#pragma unroll 1
-  for (uint64_t b = 0; b < common; b += NR) {
+  if (kRealign && rot)
+    gen_interleaved<W, F32, S, kRealign>(g, common, gl, gmask, src, dw, mdw);
+  else
+    gen_interleaved<W, F32, S, false>(g, common, gl, gmask, src, dw, mdw);
 #pragma unroll
-    for (int j = 0; j < NR; ++j) {
-#pragma unroll
-      for (int s = 0; s < S; ++s) gen_step<W, F32>(g[s], j, gl, gmask, src, dw, mdw);
-    }
-#pragma unroll
-    for (int s = 0; s < S; ++s) g[s].p += W * NR;
+  for (int s = 0; s < S; ++s) {
+    if (!ok[s]) continue;
+    // a stream that ran realigned from block 0 continues realigned (its
+    // last window is still pending in `up`); one with a = 0 has nothing
+    // pending either way
+    if (kRealign && g[s].ssrc != gl)
+      gen_finish<W, F32, kRealign>(g[s], st[s], count[s], common, write_back[s], gl, gmask, k);
+    else
+      gen_finish<W, F32, false>(g[s], st[s], count[s], common, write_back[s], gl, gmask, k);
   }
-#pragma unroll
-  for (int s = 0; s < S; ++s)
-    if (ok[s]) gen_finish<W, F32>(g[s], st[s], count[s], common, write_back[s], gl, gmask, k);
 }
 
 // Algorithm 1 (Sec. 4, the LAMMPS floating-point form) with the same warp
@@ -402,7 +498,7 @@ __global__ void generate_persistent_kernel(ranmar_state_t* __restrict__ states,
         wb[s] = allow_write_back && (d.flags & RANMAR_DESC_WRITE_BACK) != 0;
         ok[s] = true;
       }
-      generate_streams<W, F32, S>(st, cnt, out, ob, wb, ok, gl, gmask, k);
+      generate_streams<W, F32, S, true>(st, cnt, out, ob, wb, ok, gl, gmask, k);
     }
   }
 }
