@@ -451,8 +451,15 @@ class Engine:
         t0.record(self.stream)
         h0 = time.perf_counter()
         n = len(reqs)
+        t_prev = time.perf_counter()
+        max_loop = 0.0
         while i < n or waiting or inflight:
-            now = time.perf_counter() - h0
+            t_now = time.perf_counter()
+            max_loop = max(max_loop, t_now - t_prev)   # host time of one loop turn
+            if t_now - t_prev > 0.01:
+                self.stats["slow_loops"] += 1
+            t_prev = t_now
+            now = t_now - h0
             if now > max_wait:
                 raise RuntimeError("serving run exceeded its time limit")
             while i < n and (not realtime or reqs[i].t <= now):
@@ -473,6 +480,7 @@ class Engine:
                 if wait > 0:
                     time.sleep(min(wait, 2e-4))
         torch.cuda.synchronize(self.dev)
+        self.stats["max_loop_ms"] = max(self.stats["max_loop_ms"], int(max_loop * 1e3))
         st = int(self.status.item())
         if st:
             raise RuntimeError(f"device status bits {st}")
