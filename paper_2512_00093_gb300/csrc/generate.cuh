@@ -93,11 +93,18 @@ __device__ __forceinline__ void gen_load(GenCtx<W, F32>& g, const ranmar_state_t
   for (int j = 0; j < GenCtx<W, F32>::NR; ++j) g.r[j] = xs[W * j + gl];  // R_{j-NR}[L] = X(W(j-NR) + L - 1)
   g.carry = xs[96];                                                       // X(-1)
   g.cl = sub_mod_m(st->c, k.delta_lane);                                  // c_{L+1}
-  const unsigned a = kRealign ? static_cast<unsigned>(out_base % W) : 0u;  // same on the group
-  g.ssrc = (gl + W - a) % W;
-  g.lo = gl < a;
+  using T = typename GenCtx<W, F32>::T;
   g.up = 0;
-  g.p = static_cast<typename GenCtx<W, F32>::T*>(out) + (out_base - a) + gl;
+  if constexpr (kRealign) {
+    const unsigned a = static_cast<unsigned>(out_base % W);  // the same on the whole group
+    g.ssrc = (gl + W - a) % W;
+    g.lo = gl < a;
+    g.p = static_cast<T*>(out) + (out_base - a) + gl;
+  } else {
+    g.ssrc = gl;
+    g.lo = false;
+    g.p = static_cast<T*>(out) + out_base + gl;
+  }
 }
 
 // Step j of a ring turn: R_b into r[j] (= R_{b-NR} on entry), the outputs to
