@@ -378,6 +378,28 @@ int ranmar_plan_expand(const ranmar_plan_t *p, ranmar_state_t *d_states, size_t 
 #define RANMAR_PLAN_IMAD 1
 int ranmar_plan_set_method(ranmar_plan_t *p, int method);
 int ranmar_plan_set_ctas(ranmar_plan_t *p, unsigned ctas);
+
+/*
+ * ranmar_debug_set_wait_limit -- a test hook for the timeout path of the
+ * bounded device waits of the tensor-core plan levels: with iterations > 0
+ * the first wait of every CTA is made on a barrier that nothing completes,
+ * probed without blocking at most `iterations` times, so that it runs out
+ * without faulting or hanging anything (0 restores normal operation).  A
+ * CTA whose wait ran out flags RANMAR_ST_TIMEOUT in the plan's status word,
+ * still waits (bounded) for its own copies and MMAs in flight, frees its
+ * tensor memory and returns.  Synchronizes the
+ * device before and after.  Errors: RANMAR_ECUDA.
+ */
+int ranmar_debug_set_wait_limit(uint32_t iterations);
+
+/*
+ * ranmar_debug_fail_next -- host-side failure injection for tests: the next
+ * entry point that launches a kernel returns `code` (a RANMAR_E* value, or 0
+ * to clear) once, as if its launch had failed; the kernel itself was still
+ * enqueued and runs normally.  Errors: RANMAR_EINVAL for a code that is not
+ * 0 or a RANMAR_E* value.
+ */
+int ranmar_debug_fail_next(int code);
 int ranmar_plan_status(const ranmar_plan_t *p, uint32_t **d_status);
 
 /* ------------------------------------------------------------------------

@@ -7,6 +7,7 @@ include/ranmar.h; this package is its thin binding plus the build step.
 from .binding import (  # noqa: F401
     DESC_WRITE_BACK, MAX_EXP_WORDS, R, ST_BAD_INDEX, ST_OUT_RANGE, STATE_WORDS, Batch,
     BatchConfig, Graph, RanmarError, abi_version, capture, check_overlap, checksum, checksum_np,
+    debug_fail_next, debug_set_wait_limit,
     exps_tensor, ST_OVERLAP, ST_TIMEOUT,
     JUMP_REDUCE_PERIOD, generate_alg1_f32, generate_alg1_f64, generate_f32, jump_scatter,
     partition_ex,

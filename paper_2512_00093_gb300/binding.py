@@ -96,6 +96,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_partition_plan.restype = ctypes.c_int
     lib.ranmar_plan_set_method.argtypes = [_vp, ctypes.c_int]
     lib.ranmar_plan_set_ctas.argtypes = [_vp, ctypes.c_uint]
+    lib.ranmar_debug_set_wait_limit.argtypes = [_u32]
+    lib.ranmar_debug_fail_next.argtypes = [ctypes.c_int]
     lib.ranmar_lfg_jump.argtypes = [_u32, _u32, _u32, ctypes.c_int, _vp, _sz, _vp, _vp, _u32, _vp,
                                     _sz, _vp, _vp]
     lib.ranmar_lfg_jump.restype = ctypes.c_int
@@ -357,6 +359,18 @@ def _generate(fn: str, out_dtype, states, desc, out, status, stream):
 def generate_u24(states, desc, out, status=None, stream=None):
     """ranmar_generate_u24 over a descriptor batch; out is int32 (24-bit values)."""
     return _generate("ranmar_generate_u24", torch.int32, states, desc, out, status, stream)
+
+
+def debug_set_wait_limit(iterations: int) -> None:
+    """ranmar_debug_set_wait_limit: non-blocking probes before a device wait of
+    the tensor-core plan levels gives up (0 = the default bounded wait); for
+    tests of the timeout path."""
+    _check(_lib().ranmar_debug_set_wait_limit(int(iterations)), "ranmar_debug_set_wait_limit")
+
+
+def debug_fail_next(code: int) -> None:
+    """ranmar_debug_fail_next: the next launching call returns `code` once."""
+    _check(_lib().ranmar_debug_fail_next(int(code)), "ranmar_debug_fail_next")
 
 
 def check_overlap(states, desc, k, J: int, status=None, stream=None) -> torch.Tensor:

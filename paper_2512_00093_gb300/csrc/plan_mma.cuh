@@ -108,10 +108,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kMbarSpinLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
+// Non-blocking probe of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// A test of the timeout path (set only by ranmar_debug_set_wait_limit):
+// when n > 0, the first wait of every CTA is made on a barrier that nothing
+// completes, probed without blocking at most n times.
+__device__ uint32_t g_wait_limit = 0;
+
+// Bounded wait for the phase with the given parity (blocking polls, or
+// non-blocking probes when `probe`); false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          uint32_t limit = kMbarSpinLimit, bool probe = false) {
+  for (uint32_t it = 0; it < limit; ++it)
+    if (probe ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return true;
   return false;
 }
 
@@ -312,10 +331,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1) plan_level_mma_kernel(
   uint8_t* B = A + kAImgBytes;
   uint8_t* stage = B + kBImgBytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(stage + kStageBytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  const uint32_t bar_x = smem_addr(&bars[3]);  // never completed (the timeout test)
   const uint32_t bar_b = smem_addr(&bars[0]), bar_m = smem_addr(&bars[1]),
                  bar_s = smem_addr(&bars[2]);
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t test_limit = g_wait_limit;
 
   const uint32_t q0 = static_cast<uint32_t>(static_cast<uint64_t>(blockIdx.x) * items / gridDim.x);
   const uint32_t q1 =
@@ -345,6 +366,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) plan_level_mma_kernel(
     mbar_init(bar_b, 1);
     mbar_init(bar_m, 1);
     mbar_init(bar_s, 1);
+    mbar_init(bar_x, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     load_src(q0 / r_count);
     load_b(q0);
@@ -386,7 +408,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) plan_level_mma_kernel(
         load_src(tile);
         s_in_flight = true;
       }
-      const bool s_ok = mbar_wait(bar_s, ph_s);
+      const bool s_ok = test_limit ? mbar_wait(bar_x, 0, test_limit, true)
+                                   : mbar_wait(bar_s, ph_s);
       ok = __syncthreads_and(s_ok);
       if (!ok) break;
       ph_s ^= 1;

@@ -4,10 +4,13 @@
 // CUDA error mapping.  Device side: generate.cuh (Algorithm 2 warp step) and
 // jump.cuh (Sec. 3.1 / 3.2 jump-ahead).
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "ranmar.h"
 #include "ranmar_device.cuh"
@@ -84,10 +87,24 @@ int cuda_fail(cudaError_t e) {
   return RANMAR_ECUDA;
 }
 
+// Host-side failure injection (ranmar_debug_fail_next): the next launch
+// check returns this code once.
+std::atomic<int> g_fail_next{0};
+
 int check_launch() {
   const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? RANMAR_OK : cuda_fail(e);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return g_fail_next.exchange(0);
 }
+
+// A named NVTX range over one entry point (host side: the enqueue), so that
+// a timeline tool shows which call issued which kernels.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -505,6 +522,7 @@ int ranmar_seed(int32_t seed, ranmar_state_t* h_out) {
 int ranmar_jump(const ranmar_state_t* d_base, size_t n_base, const uint32_t* d_base_idx,
                 const uint32_t* d_exp, uint32_t exp_words, ranmar_state_t* d_out, size_t n,
                 uint32_t* d_status, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_jump");
   if (n == 0) return RANMAR_OK;
   if (!d_base || !d_exp || !d_out) return RANMAR_EINVAL;
   if (exp_words < 1 || exp_words > RANMAR_MAX_EXP_WORDS || n_base == 0) return RANMAR_ERANGE;
@@ -518,6 +536,7 @@ int ranmar_jump(const ranmar_state_t* d_base, size_t n_base, const uint32_t* d_b
 
 int ranmar_partition(const ranmar_state_t* d_base, const uint32_t* h_J, uint32_t J_words,
                      uint64_t k0, ranmar_state_t* d_out, size_t n, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_partition");
   if (n == 0) return RANMAR_OK;
   if (!d_base || !h_J || !d_out) return RANMAR_EINVAL;
   if (J_words < 1 || J_words > RANMAR_MAX_EXP_WORDS) return RANMAR_ERANGE;
@@ -542,6 +561,7 @@ int ranmar_partition(const ranmar_state_t* d_base, const uint32_t* h_J, uint32_t
 int ranmar_generate_u24(ranmar_state_t* d_states, size_t n_states, const ranmar_desc_t* d_desc,
                         size_t n_desc, uint32_t* d_out, size_t out_len, uint32_t* d_status,
                         ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_generate_u24");
   return launch_generate(false, d_states, n_states, d_desc, n_desc, d_out, out_len, d_status,
                          stream);
 }
@@ -549,6 +569,7 @@ int ranmar_generate_u24(ranmar_state_t* d_states, size_t n_states, const ranmar_
 int ranmar_generate_f32(ranmar_state_t* d_states, size_t n_states, const ranmar_desc_t* d_desc,
                         size_t n_desc, float* d_out, size_t out_len, uint32_t* d_status,
                         ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_generate_f32");
   return launch_generate(true, d_states, n_states, d_desc, n_desc, d_out, out_len, d_status,
                          stream);
 }
@@ -557,6 +578,7 @@ int ranmar_check_overlap(const ranmar_state_t* d_states, size_t n_states,
                          const ranmar_desc_t* d_desc, size_t n_desc, const uint64_t* d_k,
                          const uint32_t* h_J, uint32_t J_words, uint32_t* d_status,
                          ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_check_overlap");
   if (!h_J) return RANMAR_EINVAL;
   if (J_words < 1 || J_words > RANMAR_MAX_EXP_WORDS) return RANMAR_ERANGE;
   bool zero = true, big = false;
@@ -654,6 +676,7 @@ int ranmar_batch_get_config(const ranmar_batch_t* b, ranmar_batch_config_t* cfg)
 int ranmar_batch_pack(ranmar_batch_t* b, const uint64_t* d_counts, size_t n, uint32_t flags,
                       ranmar_desc_t* d_desc, uint32_t* d_order, uint64_t* d_total,
                       ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_batch_pack");
   if (!on_device(b)) return RANMAR_EINVAL;
   if (n > b->capacity) return RANMAR_ERANGE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -683,6 +706,7 @@ int ranmar_batch_generate_u24(ranmar_batch_t* b, ranmar_state_t* d_states, size_
                               const ranmar_desc_t* d_desc, size_t n_desc,
                               const uint32_t* d_order, uint32_t* d_out, size_t out_len,
                               uint32_t* d_status, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_batch_generate_u24");
   return batch_generate(b, false, d_states, n_states, d_desc, n_desc, d_order, d_out, out_len,
                         d_status, stream);
 }
@@ -691,6 +715,7 @@ int ranmar_batch_generate_f32(ranmar_batch_t* b, ranmar_state_t* d_states, size_
                               const ranmar_desc_t* d_desc, size_t n_desc,
                               const uint32_t* d_order, float* d_out, size_t out_len,
                               uint32_t* d_status, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_batch_generate_f32");
   return batch_generate(b, true, d_states, n_states, d_desc, n_desc, d_order, d_out, out_len,
                         d_status, stream);
 }
@@ -698,6 +723,7 @@ int ranmar_batch_generate_f32(ranmar_batch_t* b, ranmar_state_t* d_states, size_
 int ranmar_batch_tune(ranmar_batch_t* b, int f32, ranmar_state_t* d_states, size_t n_states,
                       const ranmar_desc_t* d_desc, size_t n_desc, const uint32_t* d_order,
                       void* d_out, size_t out_len, ranmar_stream_t stream, float* best_ms) {
+  NvtxRange nvtx_("ranmar_batch_tune");
   if (!on_device(b)) return RANMAR_EINVAL;
   if (n_desc == 0) return RANMAR_OK;
   if (!d_states || !d_desc || !d_out) return RANMAR_EINVAL;
@@ -829,6 +855,7 @@ int ranmar_jump_scatter(const ranmar_state_t* d_base, size_t n_base, const uint3
                         const uint32_t* d_exp, uint32_t exp_words, ranmar_state_t* d_dst,
                         size_t n_dst, const uint32_t* d_dst_idx, size_t n, uint32_t* d_status,
                         ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_jump_scatter");
   if (n == 0) return RANMAR_OK;
   if (!d_base || !d_exp || !d_dst || !d_dst_idx) return RANMAR_EINVAL;
   if (exp_words < 1 || exp_words > RANMAR_MAX_EXP_WORDS || n_base == 0 || n_dst == 0)
@@ -844,6 +871,7 @@ int ranmar_jump_scatter(const ranmar_state_t* d_base, size_t n_base, const uint3
 int ranmar_checksum(const uint32_t* d_data, size_t data_len, const ranmar_sum_item_t* d_items,
                     size_t n_items, uint64_t* d_results, size_t n_results, uint32_t* d_status,
                     ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_checksum");
   if (n_items == 0) return RANMAR_OK;
   if (!d_data || !d_items || !d_results) return RANMAR_EINVAL;
   if (!aligned(d_data, 4) || !aligned(d_items, 8) || !aligned(d_results, 8)) return RANMAR_EINVAL;
@@ -856,6 +884,7 @@ int ranmar_checksum(const uint32_t* d_data, size_t data_len, const ranmar_sum_it
 }
 
 int ranmar_table_create(ranmar_table_t** out) {
+  NvtxRange nvtx_("ranmar_table_create");
   if (!out) return RANMAR_EINVAL;
   *out = nullptr;
   ranmar_table* t = new (std::nothrow) ranmar_table{};
@@ -939,6 +968,7 @@ int ranmar_jump_tab(const ranmar_table_t* t, const ranmar_state_t* d_base, size_
                     const uint32_t* d_base_idx, const uint32_t* d_exp, uint32_t exp_words,
                     ranmar_state_t* d_dst, size_t n_dst, const uint32_t* d_dst_idx, size_t n,
                     uint32_t* d_status, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_jump_tab");
   if (!t) return RANMAR_EINVAL;
   if (n == 0) return RANMAR_OK;
   if (!d_base || !d_exp || !d_dst) return RANMAR_EINVAL;
@@ -958,6 +988,7 @@ int ranmar_jump_tab(const ranmar_table_t* t, const ranmar_state_t* d_base, size_
 int ranmar_partition_tab(const ranmar_table_t* t, const ranmar_state_t* d_base,
                          const uint32_t* h_J, uint32_t J_words, uint64_t k0,
                          ranmar_state_t* d_out, size_t n, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_partition_tab");
   if (!t) return RANMAR_EINVAL;
   if (n == 0) return RANMAR_OK;
   if (!d_base || !h_J || !d_out) return RANMAR_EINVAL;
@@ -985,6 +1016,7 @@ int ranmar_partition_generate_u24(const ranmar_table_t* t, const ranmar_state_t*
                                   const uint32_t* h_J, uint32_t J_words, uint64_t k0, size_t n,
                                   uint64_t count, uint32_t flags, ranmar_state_t* d_states,
                                   uint32_t* d_out, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_partition_generate_u24");
   return launch_partition_generate<false>(t, d_base, h_J, J_words, k0, n, count, flags, d_states,
                                           d_out, stream);
 }
@@ -993,12 +1025,14 @@ int ranmar_partition_generate_f32(const ranmar_table_t* t, const ranmar_state_t*
                                   const uint32_t* h_J, uint32_t J_words, uint64_t k0, size_t n,
                                   uint64_t count, uint32_t flags, ranmar_state_t* d_states,
                                   float* d_out, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_partition_generate_f32");
   return launch_partition_generate<true>(t, d_base, h_J, J_words, k0, n, count, flags, d_states,
                                          d_out, stream);
 }
 
 int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_words,
                        size_t max_n, ranmar_plan_t** out) {
+  NvtxRange nvtx_("ranmar_plan_create");
   if (!out) return RANMAR_EINVAL;
   *out = nullptr;
   if (!t || !h_J) return RANMAR_EINVAL;
@@ -1192,6 +1226,19 @@ int ranmar_plan_set_ctas(ranmar_plan_t* p, unsigned ctas) {
   return RANMAR_OK;
 }
 
+int ranmar_debug_fail_next(int code) {
+  if (code > 0 || code < RANMAR_EDEVICE) return RANMAR_EINVAL;
+  g_fail_next.store(code);
+  return RANMAR_OK;
+}
+
+int ranmar_debug_set_wait_limit(uint32_t iterations) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(ranmar::g_wait_limit, &iterations, sizeof(iterations));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? RANMAR_OK : cuda_fail(e);
+}
+
 int ranmar_plan_status(const ranmar_plan_t* p, uint32_t** d_status) {
   if (!p || !d_status) return RANMAR_EINVAL;
   *d_status = p->status;
@@ -1200,6 +1247,7 @@ int ranmar_plan_status(const ranmar_plan_t* p, uint32_t** d_status) {
 
 int ranmar_plan_expand(const ranmar_plan_t* p, ranmar_state_t* d_states, size_t n,
                        ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_plan_expand");
   if (!p) return RANMAR_EINVAL;
   if (n <= static_cast<size_t>(ranmar::kPlanBase)) return RANMAR_OK;
   if (!d_states) return RANMAR_EINVAL;
@@ -1238,6 +1286,7 @@ int ranmar_plan_expand(const ranmar_plan_t* p, ranmar_state_t* d_states, size_t 
 
 int ranmar_partition_plan(const ranmar_plan_t* p, const ranmar_state_t* d_base, uint64_t k0,
                           size_t n, ranmar_state_t* d_out, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_partition_plan");
   if (!p) return RANMAR_EINVAL;
   if (n == 0) return RANMAR_OK;
   if (!d_base || !d_out) return RANMAR_EINVAL;
@@ -1267,6 +1316,7 @@ int ranmar_lfg_jump(uint32_t r, uint32_t s, uint32_t e, int method, const uint32
                     size_t n_base, const uint32_t* d_base_idx, const uint32_t* d_exp,
                     uint32_t exp_words, uint32_t* d_out, size_t n, uint32_t* d_status,
                     ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_lfg_jump");
   ranmar::LfgShape sh;
   if (!lfg_shape(r, s, e, method, sh)) return RANMAR_EINVAL;
   if (n == 0) return RANMAR_OK;
@@ -1298,6 +1348,7 @@ int ranmar_lfg_jump(uint32_t r, uint32_t s, uint32_t e, int method, const uint32
 
 int ranmar_lfg_generate(uint32_t r, uint32_t s, uint32_t e, uint32_t* d_x, size_t n,
                         uint64_t count, uint32_t* d_out, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_lfg_generate");
   ranmar::LfgShape sh;
   if (!lfg_shape(r, s, e, RANMAR_LFG_CLASSICAL, sh)) return RANMAR_EINVAL;
   if (n == 0 || count == 0) return RANMAR_OK;
@@ -1322,12 +1373,14 @@ int ranmar_lfg_generate(uint32_t r, uint32_t s, uint32_t e, uint32_t* d_x, size_
 int ranmar_generate_alg1_f32(ranmar_state_t* d_states, size_t n_states,
                              const ranmar_desc_t* d_desc, size_t n_desc, float* d_out,
                              size_t out_len, uint32_t* d_status, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_generate_alg1_f32");
   return launch_alg1<float>(d_states, n_states, d_desc, n_desc, d_out, out_len, d_status, stream);
 }
 
 int ranmar_generate_alg1_f64(ranmar_state_t* d_states, size_t n_states,
                              const ranmar_desc_t* d_desc, size_t n_desc, double* d_out,
                              size_t out_len, uint32_t* d_status, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_generate_alg1_f64");
   return launch_alg1<double>(d_states, n_states, d_desc, n_desc, d_out, out_len, d_status,
                              stream);
 }
@@ -1335,6 +1388,7 @@ int ranmar_generate_alg1_f64(ranmar_state_t* d_states, size_t n_states,
 int ranmar_partition_ex(const ranmar_table_t* t, const ranmar_state_t* d_base, const uint32_t* h_J,
                         uint32_t J_words, uint64_t k0, ranmar_state_t* d_out, size_t n,
                         uint32_t flags, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_partition_ex");
   if (flags & ~static_cast<uint32_t>(RANMAR_JUMP_REDUCE_PERIOD)) return RANMAR_EINVAL;
   if (n == 0) return RANMAR_OK;
   if (!d_base || !h_J || !d_out) return RANMAR_EINVAL;
@@ -1362,6 +1416,7 @@ int ranmar_partition_ex(const ranmar_table_t* t, const ranmar_state_t* d_base, c
 
 int ranmar_seed_batch(const int32_t* d_seeds, size_t n, ranmar_state_t* d_out, uint32_t* d_status,
                       ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_seed_batch");
   if (n == 0) return RANMAR_OK;
   if (!d_seeds || !d_out) return RANMAR_EINVAL;
   if (!aligned(d_seeds, 4) || !aligned(d_out, 16)) return RANMAR_EINVAL;

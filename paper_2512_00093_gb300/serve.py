@@ -302,6 +302,12 @@ class Engine:
         return lo
 
     def enqueue(self, reqs: list, t0_event) -> dict:
+        # one NVTX range per iteration (timeline tools show it beside the
+        # library's own ranges)
+        with torch.cuda.nvtx.range(f"serve.enqueue[{len(reqs)}]"):
+            return self._enqueue(reqs, t0_event)
+
+    def _enqueue(self, reqs: list, t0_event) -> dict:
         nreq = len(reqs)
         seg = self.seg
         counts = np.fromiter((r.count for r in reqs), dtype=np.int64, count=nreq)
@@ -406,6 +412,10 @@ class Engine:
                             status=self.status, stream=self.stream, n=n)
 
     def retire(self, it: dict) -> None:
+        with torch.cuda.nvtx.range("serve.retire"):
+            self._retire(it)
+
+    def _retire(self, it: dict) -> None:
         it["event"].synchronize()
         done = it["t0"].elapsed_time(it["event"]) * 1e-3
         lo_s, hi_s = it["slots"]

@@ -296,3 +296,18 @@ def test_generate_into_pinned_host_memory(rm, dev, orc):
     assert torch.equal(h, d.cpu())
     ref = orc.stream(12345, 9 * (1 << 40), count)
     assert np.array_equal(h[2 * count:3 * count].numpy().view(np.uint32), ref)
+
+
+def test_injected_launch_failure(rm, dev):
+    """ranmar_debug_fail_next makes the next launching call return its code
+    once (RanmarError in the binding); the call after it succeeds."""
+    st = rm.partition(seeded(rm, 3, dev), 1000, 0, 2)
+    out = torch.empty(100, dtype=torch.int32, device=dev)
+    desc = rm.make_desc(np.array([0]), np.array([0]), 100, 0, device=dev)
+    rm.debug_fail_next(rm.binding.ECUDA)
+    with pytest.raises(rm.RanmarError) as ei:
+        rm.generate_u24(st, desc, out)
+    assert ei.value.code == rm.binding.ECUDA
+    rm.generate_u24(st, desc, out)
+    torch.cuda.synchronize()
+

@@ -105,6 +105,35 @@ def test_plan_ctas(rm, table, ctas):
     plan.close()
 
 
+def test_plan_timeout_path(rm, table):
+    """Failure detection without a fault: with the first wait of every CTA of
+    the tensor-core level made on a barrier that nothing completes (one
+    non-blocking probe), the level gives up, flags
+    RANMAR_ST_TIMEOUT and returns (its CTAs drain their own copies and MMAs
+    first); the context stays usable and a fresh plan gives the right
+    states."""
+    dev = torch.device("cuda:0")
+    J = 1 << 40
+    base = rm.seed(3).to(dev)
+    plan = rm.Plan(table, J, 5000)
+    torch.cuda.synchronize()
+    rm.debug_set_wait_limit(1)
+    try:
+        plan.partition(base, 0, 5000)
+        torch.cuda.synchronize()
+        assert plan.status() & rm.ST_TIMEOUT
+    finally:
+        rm.debug_set_wait_limit(0)
+    plan.close()
+    plan = rm.Plan(table, J, 5000)
+    got = plan.partition(base, 0, 5000)
+    ref = table.partition(base, J, 0, 5000)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+    assert plan.status() == 0
+    plan.close()
+
+
 def test_plan_expand_from_table_rows(rm, table):
     """expand() from the first 256 rows computed elsewhere (the table
     partition on another stream) gives the same states as one partition_plan

@@ -93,3 +93,26 @@ def test_serving_realtime_and_plain(rm, orc):
     eng.run_plain(reqs, realtime=True)
     assert [r.checksum for r in reqs] == got
     eng.close()
+
+
+def test_serving_injected_failure_then_recovers(rm, orc):
+    """Failure detection on the host: a library call that fails in the middle
+    of a serving run (injected with ranmar_debug_fail_next) ends the run with
+    an exception instead of a hang; the context stays usable and a new
+    engine serves the same requests correctly."""
+    from paper_2512_00093_gb300.serve import Engine, assign_offsets
+    reqs = mixed_requests(60, 21, seeds=3, ks=4, cmax=50_000, duration=0.05)
+    eng = Engine(budget_bytes=64 << 20, seg=4096, state_entries=256)
+    rm.debug_fail_next(rm.binding.ECUDA)
+    with pytest.raises(rm.RanmarError) as ei:
+        eng.run(reqs, realtime=False)
+    assert ei.value.code == rm.binding.ECUDA
+    torch.cuda.synchronize()
+    eng.close()
+    for r in reqs:
+        r.checksum, r.done = -1, -1.0
+    assign_offsets(reqs)
+    eng = Engine(budget_bytes=64 << 20, seg=4096, state_entries=256)
+    eng.run(reqs, realtime=False)
+    check_all(orc, rm, reqs)
+    eng.close()

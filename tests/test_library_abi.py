@@ -86,6 +86,9 @@ def test_host_argument_checks(lib):
     assert L.ranmar_generate_plain_u24(None, 10, fake, 1, None) == -1
     assert L.ranmar_generate_plain_u24(fake, 10, None, 1, None) == -1
     L.ranmar_plan_set_ctas.argtypes = [ctypes.c_void_p, ctypes.c_uint]
+    L.ranmar_debug_fail_next.argtypes = [ctypes.c_int]
+    assert L.ranmar_debug_fail_next(1) == -1 and L.ranmar_debug_fail_next(-6) == -1
+    assert L.ranmar_debug_fail_next(0) == 0
     assert L.ranmar_plan_set_ctas(None, 4) == -1
     L.ranmar_check_overlap.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                                        ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
