@@ -60,6 +60,9 @@ __global__ void __launch_bounds__(kScanThreads) pack_tile_sums(const uint64_t* _
                                                                uint64_t n,
                                                                uint64_t* __restrict__ tile_sums,
                                                                uint32_t* __restrict__ hist) {
+  __shared__ uint32_t local[kBuckets];  // this tile's histogram (one global add per bucket)
+  for (int b = threadIdx.x; b < kBuckets; b += kScanThreads) local[b] = 0;
+  __syncthreads();
   const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanTile;
   uint64_t s = 0;
 #pragma unroll
@@ -68,12 +71,14 @@ __global__ void __launch_bounds__(kScanThreads) pack_tile_sums(const uint64_t* _
     if (i < n) {
       const uint64_t c = counts[i];
       s += c;
-      atomicAdd(&hist[count_bucket(c)], 1u);
+      atomicAdd(&local[count_bucket(c)], 1u);
     }
   }
   uint64_t total;
-  (void)cta_exclusive_scan(s, &total);
+  (void)cta_exclusive_scan(s, &total);  // its barriers also complete the histogram
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+  for (int b = threadIdx.x; b < kBuckets; b += kScanThreads)
+    if (local[b]) atomicAdd(&hist[b], local[b]);
 }
 
 // Pass 2 (one CTA): exclusive scan of the tile sums in place; *grand_total
@@ -134,9 +139,34 @@ __global__ void __launch_bounds__(kScanThreads) pack_write(const uint64_t* __res
       d.out_offset = off;
       d.count = c[j];
       desc[i] = d;
-      if (order) order[atomicAdd(&cursor[count_bucket(c[j])], 1u)] = static_cast<uint32_t>(i);
     }
     off += c[j];
+  }
+  if (!order) return;  // uniform over the CTA
+  // The order: the tile reserves one range per bucket with a single global
+  // add (from its own histogram), then places its streams inside the range
+  // with shared-memory counters.
+  __shared__ uint32_t cnt[kBuckets], start[kBuckets];
+  for (int b = threadIdx.x; b < kBuckets; b += kScanThreads) cnt[b] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kScanPerThread; ++j) {
+    const uint64_t i = base + static_cast<uint64_t>(threadIdx.x) * kScanPerThread + j;
+    if (i < n) atomicAdd(&cnt[count_bucket(c[j])], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kBuckets; b += kScanThreads) {
+    start[b] = cnt[b] ? atomicAdd(&cursor[b], cnt[b]) : 0u;
+    cnt[b] = 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kScanPerThread; ++j) {
+    const uint64_t i = base + static_cast<uint64_t>(threadIdx.x) * kScanPerThread + j;
+    if (i < n) {
+      const int b = count_bucket(c[j]);
+      order[start[b] + atomicAdd(&cnt[b], 1u)] = static_cast<uint32_t>(i);
+    }
   }
 }
 
