@@ -680,8 +680,10 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
                           "table": {"ms": ms_t, "jumps_per_s": lj.n_streams / (ms_t * 1e-3),
                                     "tmacs_per_s": macs_t / (ms_t * 1e-3) / 1e12,
                                     "alu_frac": macs_t / (ms_t * 1e-3) / 1e12 / alu_peak}}
-    # the same 16,384 jumps by the partition plan (256 table jumps + one
-    # tensor-core level of jump matrices); states checked identical
+    # the same 16,384 jumps by the partition plan (the first 256 by the
+    # plan's table of the powers of t^J, then one tensor-core level of jump
+    # matrices), and all of them by that table (P_{kJ} over the digits of k);
+    # states checked identical
     try:
         tb = time.perf_counter()
         lplan = rm.Plan(table, lj.J, lj.n_streams)
@@ -692,6 +694,17 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
         res["large_jumps"]["plan"] = {"ms": ms_p, "jumps_per_s": lj.n_streams / (ms_p * 1e-3),
                                       "build_ms": lbuild, "states_identical": same,
                                       "status": lplan.status()}
+        ms_j = timed(lambda: lplan.jump(base, 0, lj.n_streams, out=st))
+        same_j = bool(torch.equal(lplan.jump(base, 0, lj.n_streams),
+                                  table.partition(base, lj.J, 0, lj.n_streams)))
+        macs_j = table_macs(list(range(lj.n_streams)))
+        res["large_jumps"]["powers_of_tJ"] = {
+            "ms": ms_j, "jumps_per_s": lj.n_streams / (ms_j * 1e-3),
+            "tmacs_per_s": macs_j / (ms_j * 1e-3) / 1e12,
+            "alu_frac": macs_j / (ms_j * 1e-3) / 1e12 / alu_peak,
+            "states_identical": same_j,
+            "note": "every stream by the plan's table of the powers of t^J: (nonzero base-256 "
+                    "digits of k) - 1 products + the application"}
         lplan.close()
     except Exception as ex_:  # noqa: BLE001
         res["large_jumps"]["plan"] = {"error": f"{type(ex_).__name__}: {ex_}"}
@@ -721,6 +734,7 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
     # jump matrices on the tensor cores): same states, checked
     bplan = rm.Plan(table, bu.J, ns)
     ms_jump_plan = timed(lambda: bplan.partition(base, 0, ns, out=stb))
+    ms_jump_tj = timed(lambda: bplan.jump(base, 0, ns, out=stb))
     plan_same = bool(torch.equal(bplan.partition(base, 0, ns),
                                  table.partition(base, bu.J, 0, ns)))
     gs = torch.cuda.Stream()
@@ -785,7 +799,8 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
         "streams": ns, "outputs": total, "dtype": "f32",
         "config": {"lanes_per_stream": cfg[0], "threads_per_cta": cfg[1], "ctas_per_sm": cfg[2],
                    "chunk": cfg[3], "tuned_ms": tune_ms, "from_cache": cached},
-        "jump_ms": ms_jump_plan, "jump_table_ms": ms_jump, "jump_method": "partition plan",
+        "jump_ms": ms_jump_plan, "jump_table_ms": ms_jump, "jump_powers_of_tJ_ms": ms_jump_tj,
+        "jump_method": "partition plan",
         "plan_states_identical": plan_same, "plan_status": plan_status,
         "pack_ms": ms_pack, "generate_ms": ms_gen,
         "graph_step_ms": best_g, "graph_step_table_jump_ms": best_g_table,

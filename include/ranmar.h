@@ -321,7 +321,9 @@ int ranmar_partition_ex(const ranmar_table_t *t, const ranmar_state_t *d_base,
  * max_n <= 65,536, 15 more per further level.
  *
  * ranmar_plan_create: builds the matrices on the current device (which must
- * be the table's) and returns when they are ready (synchronous).  The plan
+ * be the table's), and a table of the powers of t^J (rows t^{d 2^{8j} J}
+ * for the base-256 digits d of k, j < W with W = min(8, (160 - bitlen J)/8)),
+ * and returns when they are ready (synchronous).  The plan
  * keeps a pointer to *t, which must outlive it.  Errors: RANMAR_EINVAL
  * (null pointer, table of another device), RANMAR_ERANGE (J_words not in
  * 1..5, max_n not in 1..2^32, r R_t J >= 2^160 for a needed matrix),
@@ -335,7 +337,9 @@ int ranmar_plan_destroy(ranmar_plan_t *p);
 /*
  * ranmar_partition_plan -- the same states as ranmar_partition with the
  * plan's J: d_out[i] = f^{(k0+i) J}(*d_base), i < n <= max_n.  The first
- * 256 streams are jumped directly with the table; then each level derives
+ * 256 streams are jumped directly: by the plan's table of the powers of t^J
+ * when it covers k0 + 255 (P_{kJ} from the digits of k: no product for
+ * k < 256, at most one for k < 2^16), else by the fixed-base table; then each level derives
  * streams r R + i from streams i < R by x <- x M_{rRJ} (one dense GEMM per
  * level, 9,409 multiply-adds per stream against a matrix shared by all R
  * streams), c by the closed form of Sec. 3.2.  Asynchronous on `stream`.
@@ -355,6 +359,20 @@ int ranmar_partition_plan(const ranmar_plan_t *p, const ranmar_state_t *d_base, 
  */
 int ranmar_plan_expand(const ranmar_plan_t *p, ranmar_state_t *d_states, size_t n,
                        ranmar_stream_t stream);
+
+/*
+ * ranmar_plan_jump -- every stream by the plan's table of the powers of t^J
+ * (Sec. 1 start states, the polynomial method of Sec. 3.1 with the product
+ * over the base-256 digits of k instead of those of kJ): d_out[i] =
+ * f^{(k0+i) J}(*d_base), i < n (any n), (nonzero digits of k) - 1 products
+ * and the application per stream.  The same states as ranmar_partition.
+ * Asynchronous on `stream`.  Errors: RANMAR_EINVAL (null pointer,
+ * misalignment, d_out overlapping *d_base, plan of another device),
+ * RANMAR_ERANGE ((k0 + n - 1) J >= 2^160, or k0 + n - 1 >= 256^W, W the
+ * table's windows).
+ */
+int ranmar_plan_jump(const ranmar_plan_t *p, const ranmar_state_t *d_base, uint64_t k0,
+                     size_t n, ranmar_state_t *d_out, ranmar_stream_t stream);
 
 /*
  * How the plan's levels multiply (same results either way):

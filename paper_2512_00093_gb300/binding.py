@@ -96,6 +96,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_partition_plan.restype = ctypes.c_int
     lib.ranmar_plan_set_method.argtypes = [_vp, ctypes.c_int]
     lib.ranmar_plan_set_ctas.argtypes = [_vp, ctypes.c_uint]
+    lib.ranmar_plan_jump.argtypes = [_vp, _vp, _u64, _sz, _vp, _vp]
     lib.ranmar_debug_set_wait_limit.argtypes = [_u32]
     lib.ranmar_debug_fail_next.argtypes = [ctypes.c_int]
     lib.ranmar_lfg_jump.argtypes = [_u32, _u32, _u32, ctypes.c_int, _vp, _sz, _vp, _vp, _u32, _vp,
@@ -805,6 +806,21 @@ class Plan:
         _check(_lib().ranmar_plan_expand(self._h, _ptr(states), int(n), _stream(stream)),
                "ranmar_plan_expand")
         return states
+
+    def jump(self, base: torch.Tensor, k0: int, n: int, out=None,
+             stream=None) -> torch.Tensor:
+        """ranmar_plan_jump: out[i] = f^{(k0+i) J}(base), every stream by the
+        plan's table of the powers of t^J."""
+        base = base.reshape(-1, STATE_WORDS)
+        _need(base, torch.int32, "base")
+        if out is None:
+            out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=base.device)
+        _need(out, torch.int32, "out")
+        if out.numel() < n * STATE_WORDS:
+            raise ValueError("out too small")
+        _check(_lib().ranmar_plan_jump(self._h, _ptr(base), int(k0), int(n), _ptr(out),
+                                       _stream(stream)), "ranmar_plan_jump")
+        return out
 
     def partition(self, base: torch.Tensor, k0: int, n: int, out=None,
                   stream=None) -> torch.Tensor:

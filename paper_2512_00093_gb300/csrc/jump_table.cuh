@@ -14,6 +14,11 @@
 // square-and-multiply gives (it is unique), so the jumped states are
 // bit-identical.  The table rows themselves are built by that
 // square-and-multiply (poly_power_pair), with the exponent d 2^{8j}.
+//
+// For the streams of one partition (E = kJ) a second table, of the powers of
+// t^J (rows t^{d 2^{8j} J}, built from the first), lets the product run over
+// the digits of k instead of those of kJ (jtable_build_kernel,
+// jump_jtable_kernel).
 #pragma once
 
 #include "jump.cuh"
@@ -79,34 +84,28 @@ __device__ __forceinline__ void copy_row(uint32_t* __restrict__ dst,
   for (int q = static_cast<int>(g); q < kTabRowWords / 4; q += 2) d4[q] = __ldg(s4 + q);
 }
 
-// dst = f^E(base) for the stream of this lane pair, P_E from the table (all
-// 32 lanes call it; `active` false for lanes without a stream).  Slice: a at
-// 0, R at kPolyWords, the row b at kTabRowOffset.
-__device__ __forceinline__ void table_jump_pair(const uint32_t* __restrict__ table,
-                                                const ranmar_state_t* __restrict__ base,
-                                                const uint32_t (&E)[kMaxExpWords],
-                                                uint32_t flags, bool active,
-                                                ranmar_state_t* __restrict__ dst,
+// a = prod over the nonzero base-256 digits d_j of D of table row (j, d_j):
+// P_D for the fixed-base table (rows t^{d 2^{8j}}), P_{D J} for a table of
+// the powers of t^J (rows t^{d 2^{8j} J}).  All 32 lanes call it; `active`
+// false for lanes without a stream.  Slice: a at 0, R at kPolyWords, the
+// row b at kTabRowOffset.
+__device__ __forceinline__ void table_poly_pair(const uint32_t* __restrict__ table,
+                                                const uint32_t (&D)[kMaxExpWords], bool active,
                                                 uint32_t* __restrict__ a, unsigned g) {
   uint32_t* R = a + kPolyWords;
   uint32_t* b = a + kTabRowOffset;
-  uint32_t Ep[kMaxExpWords];
-#pragma unroll
-  for (int w = 0; w < kMaxExpWords; ++w) Ep[w] = E[w];
-  if (flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
-
   // a = 1 (t^0); b is always a whole copied row
   for (int q = static_cast<int>(g); q < kPolyWords / 4; q += 2)
     reinterpret_cast<uint4*>(a)[q] = make_uint4(q == 0 ? 1u : 0u, 0u, 0u, 0u);
   __syncwarp();
   // digit positions up to the highest nonzero digit of the warp's exponents
-  const int nbits = active ? exp_bitlen(Ep) : 0;
+  const int nbits = active ? exp_bitlen(D) : 0;
   const int nwin = (static_cast<int>(__reduce_max_sync(kFull, static_cast<unsigned>(nbits))) +
                     kTabWindowBits - 1) / kTabWindowBits;
   bool have = false;
 #pragma unroll 1
   for (int j = 0; j < nwin; ++j) {
-    const uint32_t d = active ? exp_digit(Ep, j) : 0u;
+    const uint32_t d = active ? exp_digit(D, j) : 0u;
     const bool first = d != 0 && !have;
     const bool mul = d != 0 && have;
     const uint32_t* row = table + static_cast<size_t>(j * kTabDigits + d) * kTabRowWords;
@@ -118,8 +117,80 @@ __device__ __forceinline__ void table_jump_pair(const uint32_t* __restrict__ tab
     __syncwarp();
     have = have || d != 0;
   }
-  apply_pair(base, E, active, dst, a, R, g);
+}
+
+// dst = f^E(base) for the stream of this lane pair, P_E from the fixed-base
+// table (of E, or of E reduced by the period of t when flagged).
+__device__ __forceinline__ void table_jump_pair(const uint32_t* __restrict__ table,
+                                                const ranmar_state_t* __restrict__ base,
+                                                const uint32_t (&E)[kMaxExpWords],
+                                                uint32_t flags, bool active,
+                                                ranmar_state_t* __restrict__ dst,
+                                                uint32_t* __restrict__ a, unsigned g) {
+  uint32_t Ep[kMaxExpWords];
+#pragma unroll
+  for (int w = 0; w < kMaxExpWords; ++w) Ep[w] = E[w];
+  if (flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
+  table_poly_pair(table, Ep, active, a, g);
+  apply_pair(base, E, active, dst, a, a + kPolyWords, g);
   __syncwarp();
+}
+
+// A table of the powers of t^J for one J (Sec. 1: the partition's start
+// states are f^{kJ}(base), so P_{kJ} = prod over the base-256 digits d_j of k
+// of t^{d_j 2^{8j} J}): rows (j, d) = t^{d 2^{8j} J} mod phi for j < windows,
+// built from the fixed-base table.  Stream k then costs (nonzero digits of
+// k) - 1 products instead of (nonzero digits of kJ) - 1: none for k < 256,
+// at most one for k < 2^16, whatever the size of J.
+__global__ void __launch_bounds__(32) jtable_build_kernel(const uint32_t* __restrict__ table,
+                                                          ExpParams part, int windows,
+                                                          uint32_t* __restrict__ jtable) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned g = lane >> 4, slot = lane & 15;
+  const int row = blockIdx.x * kJumpStreamsPerWarp + static_cast<int>(slot);
+  const bool active = row < windows * kTabDigits;
+  uint32_t* a = smem + slot * kTabStreamWords;
+  uint32_t E[kMaxExpWords];
+#pragma unroll
+  for (int w = 0; w < kMaxExpWords; ++w) E[w] = 0;
+  if (active) {
+    // E = d 2^{8j} J: d 2^{(8j) mod 32} < 2^32 at word (8j) / 32
+    const int j = row / kTabDigits, d = row % kTabDigits;
+    exp_mul_add(E, part.J, static_cast<uint32_t>(d) << ((8 * j) & 31), (8 * j) >> 5);
+  }
+  table_poly_pair(table, E, active, a, g);
+  if (active) {
+    uint32_t* dst = jtable + static_cast<size_t>(row) * kTabRowWords;
+    for (int q = static_cast<int>(g); q < kTabRowWords; q += 2) dst[q] = q < kR ? (a[q] & kMask24) : 0u;
+  }
+}
+
+// Partition by a table of the powers of t^J: stream i of the call is
+// k = k0 + i, P_{kJ} from the digits of k, c and pos from E = kJ.
+__global__ void __launch_bounds__(32) jump_jtable_kernel(
+    const uint32_t* __restrict__ jtable, const ranmar_state_t* __restrict__ d_base,
+    ExpParams part, ranmar_state_t* __restrict__ d_out, uint64_t n) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned g = lane >> 4, slot = lane & 15;
+  uint32_t* a = smem + slot * kTabStreamWords;
+  const uint64_t groups = (n + kJumpStreamsPerWarp - 1) / kJumpStreamsPerWarp;
+#pragma unroll 1
+  for (uint64_t grp = blockIdx.x; grp < groups; grp += gridDim.x) {
+    const uint64_t i = grp * kJumpStreamsPerWarp + slot;
+    const bool active = i < n;
+    uint32_t E[kMaxExpWords], K[kMaxExpWords];
+    load_exponent(E, 1, nullptr, 0, part, active ? i : 0);
+    const uint64_t k = part.k0 + (active ? i : 0);
+#pragma unroll
+    for (int w = 0; w < kMaxExpWords; ++w) K[w] = 0;
+    K[0] = static_cast<uint32_t>(k);
+    K[1] = static_cast<uint32_t>(k >> 32);
+    table_poly_pair(jtable, K, active, a, g);
+    apply_pair(d_base, E, active, d_out + (active ? i : 0), a, a + kPolyWords, g);
+    __syncwarp();
+  }
 }
 
 // Same contract as jump_kernel (modes 0 and 1, optional destination

@@ -62,6 +62,8 @@ struct ranmar_plan {
   int method;          // RANMAR_PLAN_TENSOR or RANMAR_PLAN_IMAD
   int num_sms;
   unsigned ctas;       // CTAs of a tensor-core level (0: one per SM)
+  uint32_t* jtable;    // powers of t^J: rows (j, d) = t^{d 2^{8j} J}, j < jt_windows
+  int jt_windows;      // base-256 digits of k it covers (0: none)
 };
 
 struct ranmar_graph {
@@ -1068,6 +1070,44 @@ int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_
       return cuda_fail(e0);
     }
   }
+  {
+    // the table of the powers of t^J: windows j with 255 * 2^{8j} J < 2^160,
+    // at most the 8 windows of a 64-bit k
+    int jbits = 0;
+    for (uint32_t w = 0; w < J_words; ++w)
+      if (h_J[w]) jbits = 32 * static_cast<int>(w) + 32 - __builtin_clz(h_J[w]);
+    const int W = std::min(8, (32 * RANMAR_MAX_EXP_WORDS - jbits) / 8);
+    cudaError_t e0 = cudaSuccess;
+    cudaStream_t s0 = nullptr;
+    if (W > 0) {
+      const int rows = W * ranmar::kTabDigits;
+      e0 = cudaMalloc(&p->jtable, sizeof(uint32_t) * ranmar::kTabRowWords * rows);
+      if (e0 == cudaSuccess) e0 = cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking);
+      if (e0 == cudaSuccess) {
+        ranmar::ExpParams jp{};
+        for (uint32_t w = 0; w < J_words; ++w) jp.J[w] = h_J[w];
+        jp.J_words = J_words;
+        ranmar::jtable_build_kernel<<<(rows + ranmar::kJumpStreamsPerWarp - 1) /
+                                          ranmar::kJumpStreamsPerWarp,
+                                      32, ranmar::kTabSmemBytes, s0>>>(t->rows, jp, W,
+                                                                       p->jtable);
+        e0 = cudaGetLastError();
+      }
+      if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(s0);
+      if (s0) cudaStreamDestroy(s0);
+    }
+    if (e0 != cudaSuccess) {
+      cudaFree(p->jtable);
+      cudaFree(p->status);
+      delete p;
+      if (e0 == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return RANMAR_ENOMEM;
+      }
+      return cuda_fail(e0);
+    }
+    p->jt_windows = W;
+  }
   if (levels == 0) {
     *out = p;
     return RANMAR_OK;
@@ -1191,6 +1231,7 @@ int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_
     cudaFree(p->ced);
     cudaFree(p->pose);
     cudaFree(p->status);
+    cudaFree(p->jtable);
     delete p;
     if (rc == RANMAR_ENOMEM) cudaGetLastError();
     return rc;
@@ -1209,6 +1250,7 @@ int ranmar_plan_destroy(ranmar_plan_t* p) {
   cudaFree(p->ced);
   cudaFree(p->pose);
   cudaFree(p->status);
+  cudaFree(p->jtable);
   if (prev >= 0) cudaSetDevice(prev);
   delete p;
   return RANMAR_OK;
@@ -1284,6 +1326,39 @@ int ranmar_plan_expand(const ranmar_plan_t* p, ranmar_state_t* d_states, size_t 
   return RANMAR_OK;
 }
 
+// Streams k0 .. k0+n-1 by the plan's table of the powers of t^J, when it
+// covers k0 + n - 1 (else RANMAR_ERANGE, nothing launched).
+static int launch_jtable_partition(const ranmar_plan_t* p, const ranmar_state_t* d_base,
+                                   const ranmar::ExpParams& part, size_t n,
+                                   ranmar_state_t* d_out, ranmar_stream_t stream) {
+  const uint64_t kmax = part.k0 + (n - 1);
+  const int kbits = kmax ? 64 - __builtin_clzll(kmax) : 0;
+  if (!p->jtable || kbits > 8 * p->jt_windows) return RANMAR_ERANGE;
+  uint64_t blocks = (n + ranmar::kJumpStreamsPerWarp - 1) / ranmar::kJumpStreamsPerWarp;
+  if (blocks > 0x7FFFFFFFull) blocks = 0x7FFFFFFFull;
+  ranmar::jump_jtable_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kTabSmemBytes,
+                               reinterpret_cast<cudaStream_t>(stream)>>>(p->jtable, d_base,
+                                                                         part, d_out, n);
+  return check_launch();
+}
+
+int ranmar_plan_jump(const ranmar_plan_t* p, const ranmar_state_t* d_base, uint64_t k0,
+                     size_t n, ranmar_state_t* d_out, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_plan_jump");
+  if (!p) return RANMAR_EINVAL;
+  if (n == 0) return RANMAR_OK;
+  if (!d_base || !d_out) return RANMAR_EINVAL;
+  if (!aligned(d_base, 16) || !aligned(d_out, 16)) return RANMAR_EINVAL;
+  if (overlaps(d_base, sizeof(ranmar_state_t), d_out, n * sizeof(ranmar_state_t)))
+    return RANMAR_EINVAL;
+  ranmar::ExpParams part;
+  const int rc = partition_params(p->J, p->J_words, k0, n, 0, part);
+  if (rc != RANMAR_OK) return rc;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return RANMAR_EINVAL;
+  return launch_jtable_partition(p, d_base, part, n, d_out, stream);
+}
+
 int ranmar_partition_plan(const ranmar_plan_t* p, const ranmar_state_t* d_base, uint64_t k0,
                           size_t n, ranmar_state_t* d_out, ranmar_stream_t stream) {
   NvtxRange nvtx_("ranmar_partition_plan");
@@ -1300,8 +1375,12 @@ int ranmar_partition_plan(const ranmar_plan_t* p, const ranmar_state_t* d_base, 
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return RANMAR_EINVAL;
   const size_t n0 = n < static_cast<size_t>(ranmar::kPlanBase) ? n : ranmar::kPlanBase;
-  const int jr = launch_jump_table(p->table, d_base, 1, nullptr, nullptr, 0, part, 1, d_out, n0,
-                                   nullptr, stream, nullptr, n0);
+  // the first streams by the table of the powers of t^J where it covers
+  // them, else by the fixed-base table
+  int jr = launch_jtable_partition(p, d_base, part, n0, d_out, stream);
+  if (jr == RANMAR_ERANGE)
+    jr = launch_jump_table(p->table, d_base, 1, nullptr, nullptr, 0, part, 1, d_out, n0,
+                           nullptr, stream, nullptr, n0);
   if (jr != RANMAR_OK) return jr;
   return ranmar_plan_expand(p, d_out, n, stream);
 }

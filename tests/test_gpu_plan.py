@@ -211,3 +211,52 @@ def test_partitioned_full_size_bench_path(rm, table, orc):
             xs, cs = orc.jump(x0, c0, E + count)
             assert np.array_equal(after[r, :97], xs) and after[r, 97] == cs, int(r)
     plan.close()
+
+
+@pytest.mark.parametrize("J", [3, 10**6, 1 << 40, (1 << 64) + 12345, (1 << 120) + 12345,
+                               (1 << 140) + 7])
+def test_plan_jump_by_powers_of_tJ(rm, table, orc, J):
+    """ranmar_plan_jump (P_{kJ} over the base-256 digits of k, from the plan's
+    table of the powers of t^J) gives the fixed-base table's states, and the
+    oracle's on a sample; streams past the table's windows are refused."""
+    dev = torch.device("cuda:0")
+    base = rm.seed(12345).to(dev)
+    plan = rm.Plan(table, J, 300)
+    W = min(8, (160 - J.bit_length()) // 8)
+    x0, c0 = orc.seeded_state(12345)
+    for k0, n in [(0, 1), (0, 300), (255, 3), (12345, 700), ((1 << 31) + 5, 33),
+                  ((1 << 63) - 40, 40)]:
+        kmax = k0 + n - 1
+        if kmax.bit_length() + J.bit_length() > 160:
+            continue
+        if kmax.bit_length() > 8 * W:
+            with pytest.raises(rm.RanmarError):
+                plan.jump(base, k0, n)
+            continue
+        got = plan.jump(base, k0, n)
+        ref = table.partition(base, J, k0, n)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref), (J, k0, n)
+        st = rm.state_words_np(got)
+        for i in {0, n - 1}:
+            xs, cs = orc.jump(x0, c0, (k0 + i) * J)
+            assert np.array_equal(st[i, :97], xs) and st[i, 97] == cs
+    plan.close()
+
+
+def test_plan_base_falls_back_to_fixed_table(rm, table):
+    """J = 2^150: the table of the powers of t^J has one window (k < 256), so
+    the first streams of a batch at k0 = 5 come from the fixed-base table;
+    the states are the same."""
+    dev = torch.device("cuda:0")
+    J = 1 << 150
+    base = rm.seed(9).to(dev)
+    plan = rm.Plan(table, J, 300)
+    got = plan.partition(base, 5, 300)
+    ref = table.partition(base, J, 5, 300)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+    with pytest.raises(rm.RanmarError):
+        plan.jump(base, 5, 300)
+    assert torch.equal(plan.jump(base, 0, 256), table.partition(base, J, 0, 256))
+    plan.close()
