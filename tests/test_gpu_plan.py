@@ -245,18 +245,19 @@ def test_plan_jump_by_powers_of_tJ(rm, table, orc, J):
 
 
 def test_plan_base_falls_back_to_fixed_table(rm, table):
-    """J = 2^150: the table of the powers of t^J has one window (k < 256), so
-    the first streams of a batch at k0 = 5 come from the fixed-base table;
-    the states are the same."""
+    """J = 2^140: the table of the powers of t^J has two windows (k < 2^16),
+    so the first streams of a batch at k0 = 65,500 (k up to 65,799) come
+    from the fixed-base table; the states are the same, and ranmar_plan_jump
+    refuses those k."""
     dev = torch.device("cuda:0")
-    J = 1 << 150
+    J = 1 << 140
     base = rm.seed(9).to(dev)
     plan = rm.Plan(table, J, 300)
-    got = plan.partition(base, 5, 300)
-    ref = table.partition(base, J, 5, 300)
+    got = plan.partition(base, 65500, 300)
+    ref = table.partition(base, J, 65500, 300)
     torch.cuda.synchronize()
     assert torch.equal(got, ref)
     with pytest.raises(rm.RanmarError):
-        plan.jump(base, 5, 300)
+        plan.jump(base, 65500, 300)
     assert torch.equal(plan.jump(base, 0, 256), table.partition(base, J, 0, 256))
     plan.close()
