@@ -730,7 +730,7 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
     ms_gen = timed(lambda: b.generate_f32(stb, desc, outf, order=order))
     ms_jump = timed(lambda: table.partition(base, bu.J, 0, ns, out=stb))
     ms_pack = timed(lambda: b.pack(counts))
-    # the start states by the partition plan (256 table jumps + levels of
+    # the start states by the partition plan (256 from the powers of t^J + levels of
     # jump matrices on the tensor cores): same states, checked
     bplan = rm.Plan(table, bu.J, ns)
     ms_jump_plan = timed(lambda: bplan.partition(base, 0, ns, out=stb))
@@ -845,7 +845,7 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
     res["float_vs_modular"] = fv
     del o32, o64, st0
 
-    # partition plan: 256 table jumps + one radix-256 level of jump matrices
+    # partition plan: 256 from the powers of t^J + one radix-256 level of jump matrices
     # on the tensor cores, against the per-stream table jump, same states
     try:
         pw = Partitioned()
@@ -865,7 +865,7 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
             "table_jump_ms": ms_t, "states_identical": same,
             "ms_for_first_streams": levels,
             "macs_per_stream": 97 * 97,
-            "note": "256 streams by the table jump, then one level x -> x M_{r 256 J}"}
+            "note": "256 streams from the plan's powers of t^J, then one level x -> x M_{r 256 J}"}
         plan.close()
         del pst
     except Exception as e:  # noqa: BLE001
@@ -972,7 +972,7 @@ def run_case(args):
     """One workload's step only (jump + generate), for profiling: uneven =
     persistent batch kernel on log-uniform lengths, large = J = 2^120 + 12345
     (square-and-multiply and table jumps, 1,024 outputs each), plan = the
-    partition plan of the partitioned workload alone (256 table jumps + the
+    partition plan of the partitioned workload alone (256 from the powers of t^J + the
     tensor-core level, no generation)."""
     import torch
     import paper_2512_00093_gb300 as rm
