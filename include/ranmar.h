@@ -612,7 +612,8 @@ typedef struct ranmar_graph ranmar_graph_t;
 /* Starts capturing `stream` (thread-local capture mode).  The legacy NULL
  * stream cannot be captured: RANMAR_EINVAL. */
 int ranmar_graph_begin(ranmar_stream_t stream);
-/* Ends the capture and instantiates it into *out. */
+/* Ends the capture, instantiates it into *out and uploads it to the device
+ * (synchronizes `stream`). */
 int ranmar_graph_end(ranmar_stream_t stream, ranmar_graph_t **out);
 /* Replays the captured work on `stream`. */
 int ranmar_graph_launch(const ranmar_graph_t *g, ranmar_stream_t stream);

@@ -797,7 +797,11 @@ int ranmar_graph_end(ranmar_stream_t stream, ranmar_graph_t** out) {
     return RANMAR_ENOMEM;
   }
   e = cudaGraphInstantiate(&r->exec, g, 0);
+  // upload now, so that the first launch does not pay for it
+  if (e == cudaSuccess) e = cudaGraphUpload(r->exec, reinterpret_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) {
+    if (r->exec) cudaGraphExecDestroy(r->exec);
     cudaGraphDestroy(g);
     delete r;
     return cuda_fail(e);
