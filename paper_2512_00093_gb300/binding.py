@@ -781,7 +781,7 @@ class Plan:
         except Exception:
             pass
 
-    TENSOR, IMAD = 0, 1
+    TENSOR, IMAD, TENSOR_PIPELINED = 0, 1, 2
 
     def set_method(self, method: int) -> None:
         """ranmar_plan_set_method (Plan.TENSOR or Plan.IMAD)."""

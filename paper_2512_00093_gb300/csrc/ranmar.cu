@@ -21,6 +21,7 @@
 #include "partition_generate.cuh"
 #include "plan.cuh"
 #include "plan_mma.cuh"
+#include "plan_mma2.cuh"
 #include "lfg.cuh"
 #include "overlap.cuh"
 
@@ -1178,6 +1179,10 @@ int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_
       e = cudaFuncSetAttribute(ranmar::plan_level_mma_kernel,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(ranmar::kMmaSmemBytes));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ranmar::plan_level_mma2_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(ranmar::kM2SmemBytes));
     if (e == cudaSuccess) e = cudaMalloc(&p->ced, nmat * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->pose, nmat * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMalloc(&dunit, RANMAR_R * sizeof(ranmar_state_t));
@@ -1261,7 +1266,9 @@ int ranmar_plan_destroy(ranmar_plan_t* p) {
 }
 
 int ranmar_plan_set_method(ranmar_plan_t* p, int method) {
-  if (!p || (method != RANMAR_PLAN_TENSOR && method != RANMAR_PLAN_IMAD)) return RANMAR_EINVAL;
+  if (!p || (method != RANMAR_PLAN_TENSOR && method != RANMAR_PLAN_IMAD &&
+             method != RANMAR_PLAN_TENSOR_PIPELINED))
+    return RANMAR_EINVAL;
   p->method = method;
   return RANMAR_OK;
 }
@@ -1307,7 +1314,16 @@ int ranmar_plan_expand(const ranmar_plan_t* p, ranmar_state_t* d_states, size_t 
     const uint64_t rmax = static_cast<uint64_t>(ranmar::plan_radix(tl) - 1);
     const uint64_t rc = (n - 1) / R < rmax ? (n - 1) / R : rmax;  // r = 1..rc: rR < n
     const int mo = p->mat_off[tl];
-    if (p->method == RANMAR_PLAN_TENSOR) {
+    if (p->method == RANMAR_PLAN_TENSOR_PIPELINED) {
+      const uint64_t tiles = (R + ranmar::kMmaM - 1) / ranmar::kMmaM;
+      const uint64_t items = tiles * rc;
+      const uint64_t want = p->ctas ? p->ctas : static_cast<uint64_t>(p->num_sms);
+      const unsigned grid = static_cast<unsigned>(items < want ? items : want);
+      ranmar::plan_level_mma2_kernel<<<grid, ranmar::kM2Threads, ranmar::kM2SmemBytes, s>>>(
+          d_states, R, n, static_cast<uint32_t>(rc), static_cast<uint32_t>(items),
+          p->bimg + static_cast<size_t>(mo) * ranmar::kBImgBytes, p->ced + mo, p->pose + mo,
+          p->status);
+    } else if (p->method == RANMAR_PLAN_TENSOR) {
       // items (tile, r): tiles of 128 source rows
       const uint64_t tiles = (R + ranmar::kMmaM - 1) / ranmar::kMmaM;
       const uint64_t items = tiles * rc;

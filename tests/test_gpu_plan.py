@@ -24,13 +24,16 @@ def table(rm):
     t.close()
 
 
-@pytest.mark.parametrize("method", ["tensor", "imad"])
+METHODS = {"tensor": 0, "imad": 1, "tensor_pipelined": 2}
+
+
+@pytest.mark.parametrize("method", list(METHODS))
 @pytest.mark.parametrize("J", [1 << 40, (1 << 64) + 12345, (1 << 120) + 12345])
 def test_plan_equals_table_partition(rm, table, orc, J, method):
     dev = torch.device("cuda:0")
     base = rm.seed(12345).to(dev)
     plan = rm.Plan(table, J, 70000)
-    plan.set_method(rm.Plan.TENSOR if method == "tensor" else rm.Plan.IMAD)
+    plan.set_method(METHODS[method])
     for n, k0 in [(1, 0), (255, 3), (256, 0), (257, 9), (511, 1), (512, 0), (513, 4),
                   (4097, 7), (65535, 0), (65536, 123), (65537, 5), (70000, 1 << 20)]:
         a = plan.partition(base, k0, n)
