@@ -558,8 +558,8 @@ def run_ours(args):
     gen_sha = source_sha("generate.cuh", "ranmar_device.cuh")
     tj = traffic_for("jump_table_kernel", jump_sha)
     tg = traffic_for("generate_desc_kernel", gen_sha)
-    tp = traffic_for("plan_level_mma_kernel",
-                     source_sha("plan_mma.cuh", "plan.cuh", "ranmar_device.cuh"))
+    tp = traffic_for("plan_level_mma2_kernel",
+                     source_sha("plan_mma2.cuh", "plan_mma.cuh", "plan.cuh", "ranmar_device.cuh"))
     roof_gen = {"kernel": "generate_desc_kernel<u24>", "bound": "hbm",
                 "achieved": gen_bytes / (gen_ms * 1e-3) / 1e9, "peak": hbm_peak,
                 "unit": "GB/s", "frac": gen_bytes / (gen_ms * 1e-3) / 1e9 / hbm_peak,
@@ -580,7 +580,8 @@ def run_ours(args):
     n_derived = max(0, n - rm.Plan.BASE)
     plan_flops = 2.0 * 6 * 97 * 97 * n_derived
     tc_peak = peaks.get("bf16_tflops", 1900.0)
-    roof_plan = {"kernel": "plan_level_mma_kernel (radix-256 level, tcgen05, fp16 limbs)",
+    roof_plan = {"kernel": "plan_level_mma2_kernel (radix-256 level, tcgen05, fp16 limbs, "
+                           "A in tensor memory, items pipelined)",
                  "bound": "tensor", "achieved": plan_flops / (exp_ms * 1e-3) / 1e12,
                  "peak": tc_peak, "unit": "TFLOP/s",
                  "frac": plan_flops / (exp_ms * 1e-3) / 1e12 / tc_peak,

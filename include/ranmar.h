@@ -376,16 +376,17 @@ int ranmar_plan_jump(const ranmar_plan_t *p, const ranmar_state_t *d_base, uint6
 
 /*
  * How the plan's levels multiply (same results either way):
- *   RANMAR_PLAN_TENSOR (default): tcgen05 MMAs on fp16 limbs -- every 24-bit
+ *   RANMAR_PLAN_TENSOR: tcgen05 MMAs on fp16 limbs -- every 24-bit
  *     word split into three balanced 8-bit limbs (exact in fp16), the limb
  *     products accumulated exactly in fp32 in tensor memory and recombined
  *     mod 2^24; operands staged in shared memory (the matrix by a bulk async
  *     copy);
  *   RANMAR_PLAN_IMAD: blocked 32-bit integer multiply-adds;
- *   RANMAR_PLAN_TENSOR_PIPELINED: tcgen05 MMAs with the limb image of the
- *     source rows in tensor memory, the whole weight-2^16 sum in one
- *     accumulator, two B images in shared memory and the MMAs of the next
- *     (tile, matrix) item running while the current one is read back.
+ *   RANMAR_PLAN_TENSOR_PIPELINED (default): tcgen05 MMAs on the same limbs,
+ *     with the limb image of the source rows in tensor memory, the whole
+ *     weight-2^16 sum in one accumulator, two B images in shared memory and
+ *     the MMAs of the next (tile, matrix) item running while the current one
+ *     is read back.
  * ranmar_plan_set_method: RANMAR_EINVAL for an unknown method.
  * ranmar_plan_set_ctas: the number of CTAs a tensor-core level launches (one
  *   CTA per SM at most, each taking a balanced range of (tile, matrix)

@@ -784,7 +784,8 @@ class Plan:
     TENSOR, IMAD, TENSOR_PIPELINED = 0, 1, 2
 
     def set_method(self, method: int) -> None:
-        """ranmar_plan_set_method (Plan.TENSOR or Plan.IMAD)."""
+        """ranmar_plan_set_method (Plan.TENSOR_PIPELINED, the default,
+        Plan.TENSOR or Plan.IMAD)."""
         _check(_lib().ranmar_plan_set_method(self._h, int(method)), "ranmar_plan_set_method")
 
     def set_ctas(self, ctas: int) -> None:

@@ -34,6 +34,8 @@
 //   aready    the tile's A image is in tensor memory  (8 arrivals)
 //   src       the tile's source rows have landed      (copy, tx count)
 //   drain     every MMA of the CTA is complete        (tcgen05.commit)
+//   x         never completed: with a wait limit set for the timeout test,
+//             each role's first wait is a bounded probe of it
 // The 256 reading threads also meet at named barrier 1 (bar.red.and, so
 // that a timeout seen by any of them is seen by all of them).
 #pragma once
@@ -118,11 +120,13 @@ __global__ void __launch_bounds__(kM2Threads, 1) plan_level_mma2_kernel(
   uint8_t* Bs = reinterpret_cast<uint8_t*>(smem);  // two B images
   uint8_t* stage = Bs + 2 * static_cast<size_t>(kBImgBytes);
   uint64_t* bars = reinterpret_cast<uint64_t*>(stage + kStageBytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 13);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14);
+  static_assert(14 * sizeof(uint64_t) + sizeof(uint32_t) <= 128, "barrier area");
   const uint32_t bfull0 = smem_addr(&bars[0]), bempty0 = smem_addr(&bars[2]);
   const uint32_t dfull0 = smem_addr(&bars[4]), dempty0 = smem_addr(&bars[7]);
   const uint32_t aready = smem_addr(&bars[10]), bar_src = smem_addr(&bars[11]);
-  const uint32_t bar_drain = smem_addr(&bars[12]);
+  const uint32_t bar_drain = smem_addr(&bars[12]), bar_x = smem_addr(&bars[13]);
+  const uint32_t test_limit = g_wait_limit;
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   const uint32_t q0 = static_cast<uint32_t>(static_cast<uint64_t>(blockIdx.x) * items / gridDim.x);
@@ -152,6 +156,7 @@ __global__ void __launch_bounds__(kM2Threads, 1) plan_level_mma2_kernel(
     for (int b = 7; b < 11; ++b) mbar_init(smem_addr(&bars[b]), kM2Workers / 32);  // dempty, aready
     mbar_init(bar_src, 1);
     mbar_init(bar_drain, 1);
+    mbar_init(bar_x, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     load_src(q0 / r_count);  // the first tile's rows, under the allocation
   }
@@ -173,20 +178,16 @@ __global__ void __launch_bounds__(kM2Threads, 1) plan_level_mma2_kernel(
         load_b(q0 + 1, 1);
         pend |= 2u;
       }
+      // the CTA's later B images into L2 now, so that their copies into
+      // shared memory, issued while the tensor core works, are short
+      for (uint32_t qq = q0 + 2; qq < q1; ++qq)
+        prefetch_l2(bimg + static_cast<size_t>(qq % r_count) * kBImgBytes, kBImgBytes);
       uint32_t tiles_seen = 0;
       int64_t cur_tile = -1;
       bool issued = false;
+      if (test_limit) ok = mbar_wait(bar_x, 0, test_limit, true);
       for (uint32_t t = 0; t < count && ok; ++t) {
         const uint32_t q = q0 + t, s = t & 1u;
-        if (t >= 1 && t + 1 < count) {
-          // item t+1 uses the slot of item t-1, free once its MMAs are done
-          const uint32_t so = (t - 1) & 1u;
-          ok = mbar_wait(bempty0 + 8 * so, ((t - 1) >> 1) & 1u);
-          if (!ok) break;
-          load_b(q + 1, so);
-          pend |= 1u << so;
-          pend_par = (pend_par & ~(1u << so)) | ((((t + 1) >> 1) & 1u) << so);
-        }
         const int64_t tile = static_cast<int64_t>(q / r_count);
         if (tile != cur_tile) {
           ok = mbar_wait(aready, tiles_seen & 1u);
@@ -209,6 +210,17 @@ __global__ void __launch_bounds__(kM2Threads, 1) plan_level_mma2_kernel(
         mma_run_ta<20, 0>(tmem + kM2D2, tmem, bd);
         issued = true;
         mma_commit(dfull0 + 8 * 2);
+        if (t >= 1 && t + 1 < count) {
+          // item t+1 takes the slot of item t-1, free once its MMAs are done
+          // (by now, behind this item's D2 group): its copy then lands while
+          // the rest of this item is multiplied
+          const uint32_t so = (t - 1) & 1u;
+          ok = mbar_wait(bempty0 + 8 * so, ((t - 1) >> 1) & 1u);
+          if (!ok) break;
+          load_b(q + 1, so);
+          pend |= 1u << so;
+          pend_par = (pend_par & ~(1u << so)) | ((((t + 1) >> 1) & 1u) << so);
+        }
         if (t >= 1) {
           ok = mbar_wait(dempty0 + 8 * 1, (t - 1) & 1u);
           if (!ok) break;
@@ -263,7 +275,8 @@ __global__ void __launch_bounds__(kM2Threads, 1) plan_level_mma2_kernel(
             src_pending = true;
           }
         }
-        const bool s_ok = mbar_wait(bar_src, changes & 1u);
+        const bool s_ok = test_limit ? mbar_wait(bar_x, 0, test_limit, true)
+                                     : mbar_wait(bar_src, changes & 1u);
         ok = workers_sync_and(s_ok);
         if (!ok) break;
         if (tid == 0) src_pending = false;

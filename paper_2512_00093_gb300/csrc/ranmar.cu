@@ -1060,7 +1060,7 @@ int ranmar_plan_create(const ranmar_table_t* t, const uint32_t* h_J, uint32_t J_
   p->J_words = J_words;
   p->max_n = max_n;
   p->levels = levels;
-  p->method = RANMAR_PLAN_TENSOR;
+  p->method = RANMAR_PLAN_TENSOR_PIPELINED;
   {
     cudaError_t e0 = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e0 == cudaSuccess) e0 = cudaMalloc(&p->status, sizeof(uint32_t));

@@ -108,7 +108,8 @@ def test_plan_ctas(rm, table, ctas):
     plan.close()
 
 
-def test_plan_timeout_path(rm, table):
+@pytest.mark.parametrize("method", ["tensor", "tensor_pipelined"])
+def test_plan_timeout_path(rm, table, method):
     """Failure detection without a fault: with the first wait of every CTA of
     the tensor-core level made on a barrier that nothing completes (one
     non-blocking probe), the level gives up, flags
@@ -119,6 +120,7 @@ def test_plan_timeout_path(rm, table):
     J = 1 << 40
     base = rm.seed(3).to(dev)
     plan = rm.Plan(table, J, 5000)
+    plan.set_method(METHODS[method])
     torch.cuda.synchronize()
     rm.debug_set_wait_limit(1)
     try:
@@ -129,6 +131,7 @@ def test_plan_timeout_path(rm, table):
         rm.debug_set_wait_limit(0)
     plan.close()
     plan = rm.Plan(table, J, 5000)
+    plan.set_method(METHODS[method])
     got = plan.partition(base, 0, 5000)
     ref = table.partition(base, J, 0, 5000)
     torch.cuda.synchronize()
