@@ -264,6 +264,24 @@ int ranmar_table_destroy(ranmar_table_t *t);
  * previous batch).  0 (the default) launches one CTA per 16 streams.
  * Errors: RANMAR_EINVAL (NULL, or outside 0..64). */
 int ranmar_table_set_ctas_per_sm(ranmar_table_t *t, int ctas_per_sm);
+/* Lanes per stream of the table jumps (Sec. 3.1; same results either way):
+ *   RANMAR_JUMP_MAP_AUTO (default): a warp per stream for batches of at most
+ *     RANMAR_JUMP_WARP_AUTO_MAX streams, two lanes per stream above;
+ *   RANMAR_JUMP_MAP_PAIR: two lanes per stream, 16 streams per warp (the
+ *     97 x 97 products register-tiled in 16 x 16 blocks; the most work per
+ *     SM, for batches that fill the GPU);
+ *   RANMAR_JUMP_MAP_WARP: one warp per stream (each lane forms a few
+ *     product coefficients and output words; the shortest time per stream,
+ *     for small batches such as the first streams of a partition plan or
+ *     the segment jumps of a serving iteration).
+ * ranmar_table_set_jump_mapping sets it for the table's jumps and
+ * partitions, ranmar_plan_set_jump_mapping for the plan's jumps by the
+ * powers of t^J.  Errors: RANMAR_EINVAL (NULL, unknown mapping). */
+#define RANMAR_JUMP_MAP_AUTO 0
+#define RANMAR_JUMP_MAP_PAIR 1
+#define RANMAR_JUMP_MAP_WARP 2
+#define RANMAR_JUMP_WARP_AUTO_MAX 2048
+int ranmar_table_set_jump_mapping(ranmar_table_t *t, int map);
 /* Device address of the rows (row j*256 + d, 100 words each), for checks. */
 int ranmar_table_rows(const ranmar_table_t *t, const uint32_t **d_rows);
 
@@ -402,6 +420,7 @@ int ranmar_plan_jump(const ranmar_plan_t *p, const ranmar_state_t *d_base, uint6
 #define RANMAR_PLAN_TENSOR_PIPELINED 2
 int ranmar_plan_set_method(ranmar_plan_t *p, int method);
 int ranmar_plan_set_ctas(ranmar_plan_t *p, unsigned ctas);
+int ranmar_plan_set_jump_mapping(ranmar_plan_t *p, int map);
 
 /*
  * ranmar_debug_set_wait_limit -- a test hook for the timeout path of the

@@ -111,6 +111,10 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_plan_status.argtypes = [_vp, ctypes.POINTER(_vp)]
     lib.ranmar_table_set_ctas_per_sm.argtypes = [_vp, ctypes.c_int]
     lib.ranmar_table_set_ctas_per_sm.restype = ctypes.c_int
+    lib.ranmar_table_set_jump_mapping.argtypes = [_vp, ctypes.c_int]
+    lib.ranmar_table_set_jump_mapping.restype = ctypes.c_int
+    lib.ranmar_plan_set_jump_mapping.argtypes = [_vp, ctypes.c_int]
+    lib.ranmar_plan_set_jump_mapping.restype = ctypes.c_int
     lib.ranmar_jump_tab.argtypes = [_vp, _vp, _sz, _vp, _vp, _u32, _vp, _sz, _vp, _sz, _vp, _vp]
     lib.ranmar_partition_tab.argtypes = [_vp, _vp, _vp, _u32, _u64, _vp, _sz, _vp]
     lib.ranmar_partition_ex.argtypes = [_vp, _vp, _vp, _u32, _u64, _vp, _sz, _u32, _vp]
@@ -294,6 +298,9 @@ def partition(base: torch.Tensor, J: int, k0: int, n: int, out: torch.Tensor | N
 
 
 JUMP_REDUCE_PERIOD = 1
+# ranmar_*_set_jump_mapping: lanes per stream of the table jumps
+JUMP_MAP_AUTO, JUMP_MAP_PAIR, JUMP_MAP_WARP = 0, 1, 2
+JUMP_WARP_AUTO_MAX = 2048
 
 
 def partition_ex(base: torch.Tensor, J: int, k0: int, n: int, table=None, flags: int = 0,
@@ -637,6 +644,12 @@ class Table:
         """ranmar_table_set_ctas_per_sm (0 = full grid)."""
         _check(_lib().ranmar_table_set_ctas_per_sm(self._h, int(k)), "ranmar_table_set_ctas_per_sm")
 
+    def set_jump_mapping(self, m: int) -> None:
+        """ranmar_table_set_jump_mapping (JUMP_MAP_AUTO, JUMP_MAP_PAIR or
+        JUMP_MAP_WARP)."""
+        _check(_lib().ranmar_table_set_jump_mapping(self._h, int(m)),
+               "ranmar_table_set_jump_mapping")
+
     def jump(self, base: torch.Tensor, exps: torch.Tensor, base_idx=None, out=None,
              dst_idx=None, status=None, stream=None, n: int | None = None) -> torch.Tensor:
         """ranmar_jump_tab: out[dst_idx[i] or i] = f^{E_i}(base[base_idx[i]])."""
@@ -791,6 +804,12 @@ class Plan:
     def set_ctas(self, ctas: int) -> None:
         """ranmar_plan_set_ctas: CTAs of a tensor-core level (0 = one per SM)."""
         _check(_lib().ranmar_plan_set_ctas(self._h, int(ctas)), "ranmar_plan_set_ctas")
+
+    def set_jump_mapping(self, m: int) -> None:
+        """ranmar_plan_set_jump_mapping: lanes per stream of the plan's jumps
+        by the powers of t^J (JUMP_MAP_AUTO, JUMP_MAP_PAIR or JUMP_MAP_WARP)."""
+        _check(_lib().ranmar_plan_set_jump_mapping(self._h, int(m)),
+               "ranmar_plan_set_jump_mapping")
 
     def status(self) -> int:
         """The plan's device status word (synchronises the device)."""

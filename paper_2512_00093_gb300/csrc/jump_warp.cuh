@@ -1,0 +1,229 @@
+// jump_warp.cuh -- table jump with a whole warp per stream, for small batches.
+//
+// The pair kernels (jump_table_kernel, jump_jtable_kernel) give each stream
+// two lanes, which is efficient when the batch fills the GPU but leaves a
+// batch of a few hundred streams (the first streams of a partition plan, the
+// segment jumps of a serving iteration) on a handful of SMs for ~20 us.
+// Here a warp owns one stream, with the same arithmetic (Sec. 3.1: P_E = the
+// product of the table rows of the nonzero digits, then the new state word
+// k = sum_i p_i x_{i+k}; Sec. 3.2: the c jump):
+//   * product c = a b (193 coefficients): lane l forms c_n for n = l + 32r,
+//     r < 6, as sum_{i<97} a_i b_{n-i} over a copy of b with 96 zeros on
+//     either side (no bounds tests; twice the multiply-adds of the triangle,
+//     but one broadcast load, one conflict-free load and one multiply-add
+//     each), c_192 = a_96 b_96;
+//   * reduction mod phi: t^k = t^{k-97} - t^{k-33} for k from 192 down to 97
+//     in three blocks [160, 192], [127, 159], [97, 126]: the targets of a
+//     block lie below it and are distinct, so each block is one parallel
+//     step;
+//   * application: the window X(0..192) (X(0..96) = the state, then the
+//     recurrence in three parallel rounds of at most 33 words), lane l forms
+//     outputs l, l + 32, l + 64 as dot products with broadcast p_i, and
+//     output 96 is a lane-strided dot product summed over the warp.
+// Arithmetic is mod 2^32 (exact mod 2^24), masked when stored.
+#pragma once
+
+#include "jump_table.cuh"
+
+namespace ranmar {
+
+constexpr int kWarpJumpWarps = 4;  // warps (streams in flight) per CTA
+// Per-warp slice (words): a = P (100) at 0; b with zero margins at 100
+// (b_0 at 196, 288 words: indices n - i in [-96, 191]); the product c
+// (193) or the window X (193) at 388.
+constexpr int kWjA = 0, kWjBz = 100, kWjB0 = kWjBz + 96, kWjC = 388, kWjWords = 584;
+constexpr size_t kWarpJumpSmemBytes = sizeof(uint32_t) * kWjWords * kWarpJumpWarps;
+static_assert(kWjB0 + 192 <= kWjC && kWjC + 196 <= kWjWords, "slice");
+static_assert(kWjWords % 4 == 0 && kWjB0 % 4 == 0 && kWjC % 4 == 0, "16-byte rows");
+
+// Copies one 100-word table row (25 x 16 bytes) into shared memory.
+__device__ __forceinline__ void copy_row_warp(uint32_t* __restrict__ dst,
+                                              const uint32_t* __restrict__ src, unsigned lane) {
+  if (lane < kTabRowWords / 4)
+    reinterpret_cast<uint4*>(dst)[lane] = __ldg(reinterpret_cast<const uint4*>(src) + lane);
+}
+
+// a = a b mod phi; b sits at bz + 96 with zeros at bz[0..95] and
+// bz[193..287] (a table row's words 97..99 are zero); c is scratch.
+__device__ __forceinline__ void poly_mulmod_warp(uint32_t* __restrict__ a,
+                                                 const uint32_t* __restrict__ bz,
+                                                 uint32_t* __restrict__ c, unsigned lane) {
+  const uint32_t* b0 = bz + 96;
+  uint32_t acc[6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) acc[r] = 0;
+#pragma unroll 4
+  for (int i = 0; i < kR; ++i) {
+    const uint32_t ai = a[i];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) acc[r] += ai * b0[static_cast<int>(lane) + 32 * r - i];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 6; ++r) c[lane + 32 * r] = acc[r];
+  if (lane == 0) c[192] = a[96] * b0[96];
+  __syncwarp();
+  // fold the coefficients 192 .. 97, one block of distinct targets at a time
+#pragma unroll
+  for (int blk = 0; blk < 3; ++blk) {
+    const int hi = blk == 0 ? 192 : (blk == 1 ? 159 : 126);
+    const int lo = blk == 0 ? 160 : (blk == 1 ? 127 : 97);
+    for (int k = hi - static_cast<int>(lane); k >= lo; k -= 32) {
+      const uint32_t v = c[k];
+      c[k - kR] += v;
+      c[k - kS] -= v;
+    }
+    __syncwarp();
+  }
+  for (int n = static_cast<int>(lane); n < kR; n += 32) a[n] = c[n];
+  __syncwarp();
+}
+
+// a = prod over the nonzero base-256 digits d_j of D of table row (j, d_j)
+// (the fixed-base table, or a table of the powers of t^J); a = 1 for D = 0.
+// D is the same in every lane.
+__device__ __forceinline__ void table_poly_warp(const uint32_t* __restrict__ table,
+                                                const uint32_t (&D)[kMaxExpWords],
+                                                uint32_t* __restrict__ s, unsigned lane) {
+  uint32_t* a = s + kWjA;
+  for (int q = static_cast<int>(lane); q < kR; q += 32) a[q] = q == 0 ? 1u : 0u;
+  __syncwarp();
+  const int nwin = (exp_bitlen(D) + kTabWindowBits - 1) / kTabWindowBits;
+  bool have = false;
+#pragma unroll 1
+  for (int j = 0; j < nwin; ++j) {
+    const uint32_t d = exp_digit(D, j);
+    if (d == 0) continue;
+    const uint32_t* row = table + static_cast<size_t>(j * kTabDigits + d) * kTabRowWords;
+    if (!have) {
+      copy_row_warp(a, row, lane);
+      __syncwarp();
+    } else {
+      copy_row_warp(s + kWjB0, row, lane);
+      __syncwarp();
+      poly_mulmod_warp(a, s + kWjBz, s + kWjC, lane);
+    }
+    have = true;
+  }
+}
+
+// dst = x P(A) with P = s[kWjA..], and the c / pos jump by E.
+__device__ __forceinline__ void apply_warp(const ranmar_state_t* __restrict__ base,
+                                           const uint32_t (&E)[kMaxExpWords],
+                                           ranmar_state_t* __restrict__ dst,
+                                           uint32_t* __restrict__ s, unsigned lane) {
+  const uint32_t* a = s + kWjA;
+  uint32_t* X = s + kWjC;
+  // X(0..99) from the state's 25 leading 16-byte words (words 97..99 are c
+  // and pos; the recurrence overwrites them)
+  if (lane < 25)
+    reinterpret_cast<uint4*>(X)[lane] = reinterpret_cast<const uint4*>(base->x)[lane];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int qend = kR + kS * (r + 1) < 2 * kR - 1 ? kR + kS * (r + 1) : 2 * kR - 1;
+    for (int q = kR + kS * r + static_cast<int>(lane); q < qend; q += 32)
+      X[q] = X[q - kR] - X[q - kS];
+    __syncwarp();
+  }
+  uint32_t acc0 = 0, acc1 = 0, acc2 = 0;
+#pragma unroll 4
+  for (int i = 0; i < kR; ++i) {
+    const uint32_t ai = a[i];
+    acc0 += ai * X[i + lane];
+    acc1 += ai * X[i + lane + 32];
+    acc2 += ai * X[i + lane + 64];
+  }
+  uint32_t p96 = 0;
+  for (int i = static_cast<int>(lane); i < kR; i += 32) p96 += a[i] * X[96 + i];
+  p96 = __reduce_add_sync(kFull, p96);
+  uint32_t* ox = dst->x;
+  ox[lane] = acc0 & kMask24;
+  ox[lane + 32] = acc1 & kMask24;
+  ox[lane + 64] = acc2 & kMask24;
+  if (lane == 0) {
+    ox[96] = p96 & kMask24;
+    const uint32_t e = exp_mod_m(E);
+    // (c - e d) mod m = (c + (m - e) d) mod m, non-negative residue.
+    const uint64_t cn =
+        (static_cast<uint64_t>(base->c) + static_cast<uint64_t>(kModM - e) * kD) % kModM;
+    dst->c = static_cast<uint32_t>(cn);
+    dst->pos = base->pos + (static_cast<uint64_t>(E[1]) << 32 | E[0]);
+  }
+  __syncwarp();
+}
+
+// Zero margins of the b copy (set once per CTA; rows land only at b_0).
+__device__ __forceinline__ void zero_margins_warp(uint32_t* __restrict__ s, unsigned lane) {
+  for (int q = static_cast<int>(lane); q < 96; q += 32) s[kWjBz + q] = 0u;
+  for (int q = kWjB0 + 97 + static_cast<int>(lane); q < kWjC; q += 32) s[q] = 0u;
+  __syncwarp();
+}
+
+// Same contract as jump_table_kernel, one warp per stream.
+__global__ void __launch_bounds__(32 * kWarpJumpWarps) jump_table_warp_kernel(
+    const uint32_t* __restrict__ table, const ranmar_state_t* __restrict__ d_base,
+    uint64_t n_base, const uint32_t* __restrict__ d_base_idx,
+    const uint32_t* __restrict__ d_exp, uint32_t exp_words, ExpParams part, int mode,
+    ranmar_state_t* __restrict__ d_out, uint64_t n, uint32_t* status,
+    const uint32_t* __restrict__ d_dst_idx, uint64_t n_dst) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* s = smem + w * kWjWords;
+  zero_margins_warp(s, lane);
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kWarpJumpWarps;
+#pragma unroll 1
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * kWarpJumpWarps + w; i < n; i += stride) {
+    uint32_t E[kMaxExpWords];
+    load_exponent(E, mode, d_exp, exp_words, part, i);
+    const ranmar_state_t* base = d_base;
+    if (mode == 0) {
+      const uint32_t bi = d_base_idx ? d_base_idx[i] : 0u;
+      if (bi >= n_base) {
+        if (lane == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
+        continue;
+      }
+      base = d_base + bi;
+    }
+    uint64_t di = i;
+    if (d_dst_idx) {
+      di = d_dst_idx[i];
+      if (di >= n_dst) {
+        if (lane == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
+        continue;
+      }
+    }
+    uint32_t Ep[kMaxExpWords];
+#pragma unroll
+    for (int q = 0; q < kMaxExpWords; ++q) Ep[q] = E[q];
+    if (part.flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
+    table_poly_warp(table, Ep, s, lane);
+    apply_warp(base, E, d_out + di, s, lane);
+  }
+}
+
+// Same contract as jump_jtable_kernel (stream i: k = k0 + i, P_{kJ} from the
+// digits of k in a table of the powers of t^J), one warp per stream.
+__global__ void __launch_bounds__(32 * kWarpJumpWarps) jump_jtable_warp_kernel(
+    const uint32_t* __restrict__ jtable, const ranmar_state_t* __restrict__ d_base,
+    ExpParams part, ranmar_state_t* __restrict__ d_out, uint64_t n) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* s = smem + w * kWjWords;
+  zero_margins_warp(s, lane);
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kWarpJumpWarps;
+#pragma unroll 1
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * kWarpJumpWarps + w; i < n; i += stride) {
+    uint32_t E[kMaxExpWords], K[kMaxExpWords];
+    load_exponent(E, 1, nullptr, 0, part, i);
+    const uint64_t k = part.k0 + i;
+#pragma unroll
+    for (int q = 0; q < kMaxExpWords; ++q) K[q] = 0;
+    K[0] = static_cast<uint32_t>(k);
+    K[1] = static_cast<uint32_t>(k >> 32);
+    table_poly_warp(jtable, K, s, lane);
+    apply_warp(d_base, E, d_out + i, s, lane);
+  }
+}
+
+}  // namespace ranmar

@@ -18,6 +18,7 @@
 #include "jump.cuh"
 #include "batch.cuh"
 #include "jump_table.cuh"
+#include "jump_warp.cuh"
 #include "partition_generate.cuh"
 #include "plan.cuh"
 #include "plan_mma.cuh"
@@ -45,6 +46,7 @@ struct ranmar_table {
   uint32_t* rows;     // kTabRows x kTabRowWords
   int num_sms;
   int ctas_per_sm;    // 0 = one CTA per group of 16 streams (full grid)
+  int jump_map;       // RANMAR_JUMP_MAP_*: lanes per stream of the table jumps
 };
 
 struct ranmar_plan {
@@ -65,6 +67,7 @@ struct ranmar_plan {
   unsigned ctas;       // CTAs of a tensor-core level (0: one per SM)
   uint32_t* jtable;    // powers of t^J: rows (j, d) = t^{d 2^{8j} J}, j < jt_windows
   int jt_windows;      // base-256 digits of k it covers (0: none)
+  int jump_map;        // RANMAR_JUMP_MAP_*: lanes per stream of its jumps
 };
 
 struct ranmar_graph {
@@ -945,10 +948,30 @@ int ranmar_table_set_ctas_per_sm(ranmar_table_t* t, int ctas_per_sm) {
   return RANMAR_OK;
 }
 
+int ranmar_table_set_jump_mapping(ranmar_table_t* t, int map) {
+  if (!t || map < RANMAR_JUMP_MAP_AUTO || map > RANMAR_JUMP_MAP_WARP) return RANMAR_EINVAL;
+  t->jump_map = map;
+  return RANMAR_OK;
+}
+
+int ranmar_plan_set_jump_mapping(ranmar_plan_t* p, int map) {
+  if (!p || map < RANMAR_JUMP_MAP_AUTO || map > RANMAR_JUMP_MAP_WARP) return RANMAR_EINVAL;
+  p->jump_map = map;
+  return RANMAR_OK;
+}
+
 int ranmar_table_rows(const ranmar_table_t* t, const uint32_t** d_rows) {
   if (!t || !d_rows) return RANMAR_EINVAL;
   *d_rows = t->rows;
   return RANMAR_OK;
+}
+
+// Two lanes per stream fill the GPU from a few thousand streams on; below
+// that a warp per stream finishes sooner.
+static bool use_warp_jump(int map, size_t n) {
+  if (map == RANMAR_JUMP_MAP_WARP) return true;
+  if (map == RANMAR_JUMP_MAP_PAIR) return false;
+  return n <= RANMAR_JUMP_WARP_AUTO_MAX;
 }
 
 static int launch_jump_table(const ranmar_table_t* t, const ranmar_state_t* base, size_t n_base,
@@ -958,12 +981,22 @@ static int launch_jump_table(const ranmar_table_t* t, const ranmar_state_t* base
                              const uint32_t* dst_idx, size_t n_dst) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != t->device) return RANMAR_EINVAL;
-  uint64_t blocks = (n + ranmar::kJumpStreamsPerWarp - 1) / ranmar::kJumpStreamsPerWarp;
+  const bool warp = use_warp_jump(t->jump_map, n);
+  const uint64_t per_cta = warp ? ranmar::kWarpJumpWarps : ranmar::kJumpStreamsPerWarp;
+  uint64_t blocks = (n + per_cta - 1) / per_cta;
   if (t->ctas_per_sm > 0) {
     const uint64_t cap = static_cast<uint64_t>(t->ctas_per_sm) * t->num_sms;
     if (blocks > cap) blocks = cap;   // the kernel strides over the rest
   }
   if (blocks > 0x7FFFFFFFull) blocks = 0x7FFFFFFFull;
+  if (warp) {
+    ranmar::jump_table_warp_kernel<<<static_cast<unsigned>(blocks), 32 * ranmar::kWarpJumpWarps,
+                                     ranmar::kWarpJumpSmemBytes,
+                                     reinterpret_cast<cudaStream_t>(stream)>>>(
+        t->rows, base, n_base, base_idx, exp, exp_words, part, mode, out, n, status, dst_idx,
+        n_dst);
+    return check_launch();
+  }
   ranmar::jump_table_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kTabSmemBytes,
                               reinterpret_cast<cudaStream_t>(stream)>>>(
       t->rows, base, n_base, base_idx, exp, exp_words, part, mode, out, n, status, dst_idx,
@@ -1354,8 +1387,17 @@ static int launch_jtable_partition(const ranmar_plan_t* p, const ranmar_state_t*
   const uint64_t kmax = part.k0 + (n - 1);
   const int kbits = kmax ? 64 - __builtin_clzll(kmax) : 0;
   if (!p->jtable || kbits > 8 * p->jt_windows) return RANMAR_ERANGE;
-  uint64_t blocks = (n + ranmar::kJumpStreamsPerWarp - 1) / ranmar::kJumpStreamsPerWarp;
+  const bool warp = use_warp_jump(p->jump_map, n);
+  const uint64_t per_cta = warp ? ranmar::kWarpJumpWarps : ranmar::kJumpStreamsPerWarp;
+  uint64_t blocks = (n + per_cta - 1) / per_cta;
   if (blocks > 0x7FFFFFFFull) blocks = 0x7FFFFFFFull;
+  if (warp) {
+    ranmar::jump_jtable_warp_kernel<<<static_cast<unsigned>(blocks), 32 * ranmar::kWarpJumpWarps,
+                                      ranmar::kWarpJumpSmemBytes,
+                                      reinterpret_cast<cudaStream_t>(stream)>>>(
+        p->jtable, d_base, part, d_out, n);
+    return check_launch();
+  }
   ranmar::jump_jtable_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kTabSmemBytes,
                                reinterpret_cast<cudaStream_t>(stream)>>>(p->jtable, d_base,
                                                                          part, d_out, n);
