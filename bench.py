@@ -691,6 +691,28 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
             best = min(best, a.elapsed_time(b))
         return best
 
+    def graph_timed(fn_s, reps=5, per=20):
+        """Device time per call: `per` calls captured into one CUDA graph and
+        replayed (no host launch latency between the events)."""
+        gs = torch.cuda.Stream(dev)
+        fn_s(gs)
+        torch.cuda.synchronize()
+        with rm.capture(gs) as cap:
+            for _ in range(per):
+                fn_s(gs)
+        cap.graph.launch(gs)
+        gs.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(gs)
+            cap.graph.launch(gs)
+            b.record(gs)
+            gs.synchronize()
+            best = min(best, a.elapsed_time(b) / per)
+        cap.graph.close()
+        return best
+
     # large jumps (J = 2^120 + 12345, E = k J up to 2^134): both methods
     lj = LargeJumps()
     table = rm.Table()
@@ -729,9 +751,15 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
         ms_p = timed(lambda: lplan.partition(base, 0, lj.n_streams, out=st))
         same = bool(torch.equal(lplan.partition(base, 0, lj.n_streams),
                                 table.partition(base, lj.J, 0, lj.n_streams)))
+        gms_p = graph_timed(lambda s_: lplan.partition(base, 0, lj.n_streams, out=st, stream=s_))
         res["large_jumps"]["plan"] = {"ms": ms_p, "jumps_per_s": lj.n_streams / (ms_p * 1e-3),
+                                      "graph_ms": gms_p,
+                                      "graph_jumps_per_s": lj.n_streams / (gms_p * 1e-3),
                                       "build_ms": lbuild, "states_identical": same,
-                                      "status": lplan.status()}
+                                      "status": lplan.status(),
+                                      "note": "ms: one call between CUDA events (host launch "
+                                              "latency included); graph_ms: device time per "
+                                              "call, 20 calls replayed from a CUDA graph"}
         ms_j = timed(lambda: lplan.jump(base, 0, lj.n_streams, out=st))
         same_j = bool(torch.equal(lplan.jump(base, 0, lj.n_streams),
                                   table.partition(base, lj.J, 0, lj.n_streams)))

@@ -280,7 +280,7 @@ int ranmar_table_set_ctas_per_sm(ranmar_table_t *t, int ctas_per_sm);
 #define RANMAR_JUMP_MAP_AUTO 0
 #define RANMAR_JUMP_MAP_PAIR 1
 #define RANMAR_JUMP_MAP_WARP 2
-#define RANMAR_JUMP_WARP_AUTO_MAX 2048
+#define RANMAR_JUMP_WARP_AUTO_MAX 8192
 int ranmar_table_set_jump_mapping(ranmar_table_t *t, int map);
 /* Device address of the rows (row j*256 + d, 100 words each), for checks. */
 int ranmar_table_rows(const ranmar_table_t *t, const uint32_t **d_rows);

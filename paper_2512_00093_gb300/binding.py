@@ -300,7 +300,7 @@ def partition(base: torch.Tensor, J: int, k0: int, n: int, out: torch.Tensor | N
 JUMP_REDUCE_PERIOD = 1
 # ranmar_*_set_jump_mapping: lanes per stream of the table jumps
 JUMP_MAP_AUTO, JUMP_MAP_PAIR, JUMP_MAP_WARP = 0, 1, 2
-JUMP_WARP_AUTO_MAX = 2048
+JUMP_WARP_AUTO_MAX = 8192
 
 
 def partition_ex(base: torch.Tensor, J: int, k0: int, n: int, table=None, flags: int = 0,

@@ -7,19 +7,21 @@
 // Here a warp owns one stream, with the same arithmetic (Sec. 3.1: P_E = the
 // product of the table rows of the nonzero digits, then the new state word
 // k = sum_i p_i x_{i+k}; Sec. 3.2: the c jump):
-//   * product c = a b (193 coefficients): lane l forms c_n for n = l + 32r,
-//     r < 6, as sum_{i<97} a_i b_{n-i} over a copy of b with 96 zeros on
-//     either side (no bounds tests; twice the multiply-adds of the triangle,
-//     but one broadcast load, one conflict-free load and one multiply-add
-//     each), c_192 = a_96 b_96;
+//   * product c = a b (193 coefficients): lane l forms c_n for n = 6l ..
+//     6l+5 as sum_{i<97} a_i b_{n-i} over a copy of b with 96 zeros on
+//     either side (no bounds tests; twice the multiply-adds of the
+//     triangle), its six b words in registers sliding by one word per step
+//     (one shared-memory load per six multiply-adds, the a_i broadcast four
+//     at a time), c_192 = a_96 b_96;
 //   * reduction mod phi: t^k = t^{k-97} - t^{k-33} for k from 192 down to 97
 //     in three blocks [160, 192], [127, 159], [97, 126]: the targets of a
 //     block lie below it and are distinct, so each block is one parallel
 //     step;
 //   * application: the window X(0..192) (X(0..96) = the state, then the
 //     recurrence in three parallel rounds of at most 33 words), lane l forms
-//     outputs l, l + 32, l + 64 as dot products with broadcast p_i, and
-//     output 96 is a lane-strided dot product summed over the warp.
+//     outputs 3l .. 3l+2 with a sliding window of three X words (one load
+//     per three multiply-adds), and output 96 is a lane-strided dot product
+//     summed over the warp.
 // Arithmetic is mod 2^32 (exact mod 2^24), masked when stored.
 #pragma once
 
@@ -45,22 +47,42 @@ __device__ __forceinline__ void copy_row_warp(uint32_t* __restrict__ dst,
 
 // a = a b mod phi; b sits at bz + 96 with zeros at bz[0..95] and
 // bz[193..287] (a table row's words 97..99 are zero); c is scratch.
+// Lane l forms c_n for n = 6l .. 6l+5 with a sliding window: at step i its
+// six registers hold b_{6l+j-i}, and step i+1 shifts them by one and loads
+// the single new word b_{6l-i-1} (rows of b 24 bytes apart per lane: at most
+// two lanes per bank).
 __device__ __forceinline__ void poly_mulmod_warp(uint32_t* __restrict__ a,
                                                  const uint32_t* __restrict__ bz,
                                                  uint32_t* __restrict__ c, unsigned lane) {
   const uint32_t* b0 = bz + 96;
-  uint32_t acc[6];
+  const int n0 = 6 * static_cast<int>(lane);
+  uint32_t acc[6], w[6];
 #pragma unroll
-  for (int r = 0; r < 6; ++r) acc[r] = 0;
-#pragma unroll 4
-  for (int i = 0; i < kR; ++i) {
-    const uint32_t ai = a[i];
+  for (int j = 0; j < 6; ++j) {
+    acc[j] = 0;
+    w[j] = b0[n0 + j];
+  }
 #pragma unroll
-    for (int r = 0; r < 6; ++r) acc[r] += ai * b0[static_cast<int>(lane) + 32 * r - i];
+  for (int i4 = 0; i4 < kR; i4 += 4) {
+    const uint4 a4 = *reinterpret_cast<const uint4*>(a + i4);  // a[96..99] for the last
+    const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int i = i4 + e;
+      if (i < kR) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc[j] += av[e] * w[j];
+        if (i + 1 < kR) {
+#pragma unroll
+          for (int j = 5; j >= 1; --j) w[j] = w[j - 1];
+          w[0] = b0[n0 - i - 1];
+        }
+      }
+    }
   }
   __syncwarp();
 #pragma unroll
-  for (int r = 0; r < 6; ++r) c[lane + 32 * r] = acc[r];
+  for (int j = 0; j < 6; ++j) c[n0 + j] = acc[j];
   if (lane == 0) c[192] = a[96] * b0[96];
   __syncwarp();
   // fold the coefficients 192 .. 97, one block of distinct targets at a time
@@ -126,21 +148,39 @@ __device__ __forceinline__ void apply_warp(const ranmar_state_t* __restrict__ ba
       X[q] = X[q - kR] - X[q - kS];
     __syncwarp();
   }
-  uint32_t acc0 = 0, acc1 = 0, acc2 = 0;
-#pragma unroll 4
-  for (int i = 0; i < kR; ++i) {
-    const uint32_t ai = a[i];
-    acc0 += ai * X[i + lane];
-    acc1 += ai * X[i + lane + 32];
-    acc2 += ai * X[i + lane + 64];
+  // lane l: outputs 3l .. 3l+2, window registers X(3l + j + i) slid by one
+  // word per step (3l mod 32 is distinct over the warp: no bank conflicts)
+  const int k0 = 3 * static_cast<int>(lane);
+  uint32_t acc[3], w[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    acc[j] = 0;
+    w[j] = X[k0 + j];
+  }
+#pragma unroll
+  for (int i4 = 0; i4 < kR; i4 += 4) {
+    const uint4 a4 = *reinterpret_cast<const uint4*>(a + i4);
+    const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int i = i4 + e;
+      if (i < kR) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) acc[j] += av[e] * w[j];
+        if (i + 1 < kR) {
+          w[0] = w[1];
+          w[1] = w[2];
+          w[2] = X[k0 + 3 + i];
+        }
+      }
+    }
   }
   uint32_t p96 = 0;
   for (int i = static_cast<int>(lane); i < kR; i += 32) p96 += a[i] * X[96 + i];
   p96 = __reduce_add_sync(kFull, p96);
   uint32_t* ox = dst->x;
-  ox[lane] = acc0 & kMask24;
-  ox[lane + 32] = acc1 & kMask24;
-  ox[lane + 64] = acc2 & kMask24;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) ox[k0 + j] = acc[j] & kMask24;
   if (lane == 0) {
     ox[96] = p96 & kMask24;
     const uint32_t e = exp_mod_m(E);

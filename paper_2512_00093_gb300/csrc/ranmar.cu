@@ -966,8 +966,8 @@ int ranmar_table_rows(const ranmar_table_t* t, const uint32_t** d_rows) {
   return RANMAR_OK;
 }
 
-// Two lanes per stream fill the GPU from a few thousand streams on; below
-// that a warp per stream finishes sooner.
+// Two lanes per stream do less work per output and win once the batch is
+// around ten thousand streams; below that a warp per stream finishes sooner.
 static bool use_warp_jump(int map, size_t n) {
   if (map == RANMAR_JUMP_MAP_WARP) return true;
   if (map == RANMAR_JUMP_MAP_PAIR) return false;
