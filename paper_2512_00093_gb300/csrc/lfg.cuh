@@ -9,8 +9,10 @@
 // r^2 multiply-adds each with the classical product, about r^{log2 3} with
 // Karatsuba's -- the trade-off the concluding remarks describe.
 //
-// One CTA of 256 threads jumps one stream (grid-stride over streams); every
-// step is CTA-parallel, in shared memory:
+// One CTA jumps one stream (grid-stride over streams), with 64 to 256
+// threads by the width of its widest step (the host's choice: a small r
+// leaves room for more streams per SM); every step is CTA-parallel, in
+// shared memory:
 //   * classical squaring: the operand, skewed (word q at q + q/32, so that
 //     the stride-4 sliding-window loads of 32 lanes hit distinct banks), and
 //     blocks of 4 consecutive outputs per thread, Sum_i a_i a_{k-i} with the

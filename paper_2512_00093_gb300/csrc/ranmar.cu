@@ -1453,6 +1453,21 @@ int ranmar_lfg_karatsuba_levels(uint32_t r, uint32_t s, uint32_t e, int method) 
   return sh.L;
 }
 
+// Threads of a jump CTA (one stream per CTA): enough for the widest
+// CTA-parallel step (the 4-output blocks of the leaf squarings, of the
+// application), in whole warps, at least 64 and at most kLfgThreads; a small
+// r then leaves room for more streams per SM instead of idle warps.  Every
+// thread holds at most ceil(r / threads) <= 8 words in the shift by t.
+static int lfg_jump_threads(const ranmar::LfgShape& sh) {
+  const int sq = sh.pow3L * ((2 * sh.M + 3) / 4);
+  const int ap = (sh.r + 3) / 4;
+  int t = std::max(sq, ap);
+  t = (t + 31) / 32 * 32;
+  t = std::min(ranmar::kLfgThreads, std::max(64, t));
+  while (t < ranmar::kLfgThreads && (sh.r + t - 1) / t > 8) t += 32;
+  return t;
+}
+
 int ranmar_lfg_jump(uint32_t r, uint32_t s, uint32_t e, int method, const uint32_t* d_x,
                     size_t n_base, const uint32_t* d_base_idx, const uint32_t* d_exp,
                     uint32_t exp_words, uint32_t* d_out, size_t n, uint32_t* d_status,
@@ -1468,6 +1483,7 @@ int ranmar_lfg_jump(uint32_t r, uint32_t s, uint32_t e, int method, const uint32
   if (overlaps(d_x, n_base * r * sizeof(uint32_t), d_out, n * r * sizeof(uint32_t)))
     return RANMAR_EINVAL;
   const size_t smem = static_cast<size_t>(sh.words) * sizeof(uint32_t);
+  const int threads = lfg_jump_threads(sh);
   cudaError_t ce = cudaFuncSetAttribute(ranmar::lfg_jump_kernel,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         static_cast<int>(smem));
@@ -1475,13 +1491,13 @@ int ranmar_lfg_jump(uint32_t r, uint32_t s, uint32_t e, int method, const uint32
   int dev = -1, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ranmar::lfg_jump_kernel,
-                                                    ranmar::kLfgThreads, smem) != cudaSuccess)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ranmar::lfg_jump_kernel, threads,
+                                                    smem) != cudaSuccess)
     return cuda_fail(cudaGetLastError());
   if (per < 1) return RANMAR_ERANGE;
   uint64_t grid = static_cast<uint64_t>(sms) * per;
   if (grid > n) grid = n;
-  ranmar::lfg_jump_kernel<<<static_cast<unsigned>(grid), ranmar::kLfgThreads, smem,
+  ranmar::lfg_jump_kernel<<<static_cast<unsigned>(grid), threads, smem,
                             reinterpret_cast<cudaStream_t>(stream)>>>(
       sh, d_x, n_base, d_base_idx, d_exp, exp_words, d_out, n, d_status);
   return check_launch();
