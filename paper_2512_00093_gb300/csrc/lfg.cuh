@@ -362,4 +362,161 @@ __global__ void __launch_bounds__(32 * kLfgGenWarps) lfg_generate_kernel(
   }
 }
 
+// ---------------------------------------------------------------------------
+// Jump with a warp per stream, classical squaring, r <= kLfgWarpMaxR.
+//
+// The same steps as lfg_jump_kernel (left-to-right binary exponentiation,
+// reduction in blocks of s, the application over the extended window), with
+// the CTA-wide steps replaced by warp-wide ones, so that small lags (r = 97:
+// 49 four-output blocks per squaring) do not leave most of a CTA idle:
+//   * squaring: lane l forms c_n for n = 8l .. 8l+7 as Sum_{i < R4} a_i
+//     a_{n-i} (R4 = r rounded up to 4; a is zero outside [0, r), stored with
+//     128 zero words below and up to 256 above, so there are no bounds
+//     tests), its eight a words in registers sliding down by one per step:
+//     one shared-memory load per eight multiply-adds; the operand is skewed
+//     (word q at q + q/32) so that the stride-8 loads of a warp hit distinct
+//     banks (lanes 0 and 31 can share one);
+//   * application: lane l forms outputs 4l .. 4l+3 over the skewed window,
+//     sliding up by one word per step.
+constexpr int kLfgWarpMaxR = 128;
+constexpr int kLfgWarpWarps = 4;                  // streams per CTA
+// per-warp slice (words): the operand a (logical -128 .. 255, skewed), the
+// product / the extended window
+constexpr int kLfgWA = 0;
+constexpr int kLfgWAWords = ((lfg_sk(384 - 1) + 1) + 3) & ~3;   // 396
+constexpr int kLfgWC = kLfgWAWords;
+constexpr int kLfgWCWords = ((lfg_sk(2 * kLfgWarpMaxR + 8) + 1) + 3) & ~3;
+constexpr int kLfgWWords = kLfgWC + kLfgWCWords;
+constexpr size_t kLfgWarpSmemBytes = sizeof(uint32_t) * kLfgWWords * kLfgWarpWarps;
+static_assert(kLfgWAWords >= lfg_sk(383) + 1 && kLfgWCWords >= 256, "warp slice");
+
+// a_m, m in [-128, 256): the skewed slot of logical index m
+__device__ __forceinline__ int lfg_wa(int m) { return lfg_sk(m + 128); }
+
+__global__ void __launch_bounds__(32 * kLfgWarpWarps) lfg_jump_warp_kernel(
+    int r, int s, uint32_t mask, const uint32_t* __restrict__ d_x, uint64_t n_base,
+    const uint32_t* __restrict__ d_base_idx, const uint32_t* __restrict__ d_exp,
+    uint32_t exp_words, uint32_t* __restrict__ d_out, uint64_t n, uint32_t* status) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int lane = static_cast<int>(threadIdx.x & 31), w = static_cast<int>(threadIdx.x >> 5);
+  uint32_t* A = smem + w * kLfgWWords + kLfgWA;
+  uint32_t* C = smem + w * kLfgWWords + kLfgWC;
+  const int R4 = (r + 3) & ~3;
+  for (int q = lane; q < kLfgWAWords; q += 32) A[q] = 0u;
+  __syncwarp();
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kLfgWarpWarps;
+#pragma unroll 1
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * kLfgWarpWarps + w; i < n; i += stride) {
+    uint32_t E[kMaxExpWords];
+#pragma unroll
+    for (int q = 0; q < kMaxExpWords; ++q)
+      E[q] = q < static_cast<int>(exp_words) ? d_exp[i * exp_words + q] : 0u;
+    const uint32_t bi = d_base_idx ? d_base_idx[i] : 0u;
+    if (bi >= n_base) {
+      if (lane == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
+      continue;
+    }
+    int nbits = 0;
+#pragma unroll
+    for (int q = 0; q < kMaxExpWords; ++q)
+      if (E[q] != 0) nbits = 32 * q + 32 - __clz(E[q]);
+    // leading bits while the value stays below r: P = t^v
+    uint32_t v = 0;
+    int pos = nbits - 1;
+    while (pos >= 0) {
+      const uint32_t bit = (E[pos >> 5] >> (pos & 31)) & 1u;
+      if (2 * v + bit >= static_cast<uint32_t>(r)) break;
+      v = 2 * v + bit;
+      --pos;
+    }
+    for (int q = lane; q < r; q += 32) A[lfg_wa(q)] = q == static_cast<int>(v) ? 1u : 0u;
+    __syncwarp();
+#pragma unroll 1
+    for (; pos >= 0; --pos) {
+      // c = a^2 (c_n for n = 8 lane + j)
+      const int n0 = 8 * lane;
+      uint32_t acc[8], win[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        acc[j] = 0u;
+        win[j] = A[lfg_wa(n0 + j)];
+      }
+#pragma unroll 1
+      for (int i0 = 0; i0 < R4; i0 += 4) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int ii = i0 + e;
+          const uint32_t ai = A[lfg_wa(ii)];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[j] += ai * win[j];
+#pragma unroll
+          for (int j = 7; j >= 1; --j) win[j] = win[j - 1];
+          win[0] = A[lfg_wa(n0 - ii - 1)];   // logical index >= -128
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) C[n0 + j] = acc[j];
+      __syncwarp();
+      // mod phi from the top, blocks of s (t^k = t^{k-r} - t^{k-s})
+      for (int top = 2 * r - 2; top >= r; top -= s) {
+        const int bot = max(r, top - s + 1);
+        for (int k = bot + lane; k <= top; k += 32) C[k - s] -= C[k];
+        __syncwarp();
+        for (int k = bot + lane; k <= top; k += 32) C[k - r] += C[k];
+        __syncwarp();
+      }
+      // a = c mod phi, times t on a 1 bit (shift; the word on t^r folds back
+      // as 1 - t^{r-s}), masked
+      const bool bit = (E[pos >> 5] >> (pos & 31)) & 1u;
+      const uint32_t topw = C[r - 1];
+      for (int q = lane; q < r; q += 32) {
+        uint32_t x = C[q];
+        if (bit) {
+          x = q == 0 ? topw : C[q - 1];
+          if (q == r - s) x -= topw;
+        }
+        A[lfg_wa(q)] = x & mask;
+      }
+      __syncwarp();
+    }
+    // application: X_q = x_q (q < r), X_q = X_{q-r} - X_{q-s} up to 2r - 2,
+    // zeros above (read only against zero coefficients); out_k = Sum_i p_i X_{i+k}
+    const uint32_t* x = d_x + static_cast<uint64_t>(bi) * r;
+    for (int q = lane; q < r; q += 32) C[lfg_sk(q)] = x[q];
+    for (int q = 2 * r - 1 + lane; q < 2 * kLfgWarpMaxR + 8; q += 32) C[lfg_sk(q)] = 0u;
+    __syncwarp();
+    for (int q0 = r; q0 < 2 * r - 1; q0 += s) {
+      const int q1 = min(2 * r - 1, q0 + s);
+      for (int q = q0 + lane; q < q1; q += 32) C[lfg_sk(q)] = C[lfg_sk(q - r)] - C[lfg_sk(q - s)];
+      __syncwarp();
+    }
+    const int k0 = 4 * lane;
+    uint32_t acc[4], win[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      acc[j] = 0u;
+      win[j] = C[lfg_sk(k0 + j)];
+    }
+#pragma unroll 1
+    for (int i0 = 0; i0 < R4; i0 += 4) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int ii = i0 + e;
+        const uint32_t pi = A[lfg_wa(ii)];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j] += pi * win[j];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) win[j] = win[j + 1];
+        win[3] = C[lfg_sk(k0 + ii + 4)];
+      }
+    }
+    uint32_t* o = d_out + i * static_cast<uint64_t>(r);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (k0 + j < r) o[k0 + j] = acc[j] & mask;
+    __syncwarp();
+  }
+}
+
 }  // namespace ranmar

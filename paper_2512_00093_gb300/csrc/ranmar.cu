@@ -1482,6 +1482,16 @@ int ranmar_lfg_jump(uint32_t r, uint32_t s, uint32_t e, int method, const uint32
     return RANMAR_EINVAL;
   if (overlaps(d_x, n_base * r * sizeof(uint32_t), d_out, n * r * sizeof(uint32_t)))
     return RANMAR_EINVAL;
+  if (sh.L == 0 && sh.r <= ranmar::kLfgWarpMaxR) {
+    // a warp per stream (classical squaring)
+    uint64_t blocks = (n + ranmar::kLfgWarpWarps - 1) / ranmar::kLfgWarpWarps;
+    if (blocks > 0x7FFFFFFFull) blocks = 0x7FFFFFFFull;
+    ranmar::lfg_jump_warp_kernel<<<static_cast<unsigned>(blocks), 32 * ranmar::kLfgWarpWarps,
+                                   ranmar::kLfgWarpSmemBytes,
+                                   reinterpret_cast<cudaStream_t>(stream)>>>(
+        sh.r, sh.s, sh.mask, d_x, n_base, d_base_idx, d_exp, exp_words, d_out, n, d_status);
+    return check_launch();
+  }
   const size_t smem = static_cast<size_t>(sh.words) * sizeof(uint32_t);
   const int threads = lfg_jump_threads(sh);
   cudaError_t ce = cudaFuncSetAttribute(ranmar::lfg_jump_kernel,
