@@ -934,6 +934,40 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
             "note": "256 streams from the plan's powers of t^J, then one level x -> x M_{r 256 J}"}
         plan.close()
         del pst
+        # many items per CTA: 256 streams expanded to 2^20 (the radix-256 level,
+        # then a radix-16 level of 7,680 items), each method, L2 flushed before each
+        nb = 1 << 20
+        bplan = rm.Plan(table, pw.J, nb)
+        bst = bplan.partition(pbase, 0, nb)
+        flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
+        ref4k = table.partition(pbase, pw.J, 0, 4096)
+        big = {"streams": nb, "algorithmic_flops": 2.0 * 6 * 97 * 97 * (nb - 256),
+               "note": "CUDA events around ranmar_plan_expand (the states of all 2^20 "
+                       "streams from the first 256), L2 flushed before each; tensor_frac "
+                       "of the measured bf16 burst peak"}
+        tc_peak = peaks.get("bf16_tflops", 1900.0)
+        for mname, mth in [("tensor_pipelined", rm.Plan.TENSOR_PIPELINED),
+                           ("tensor", rm.Plan.TENSOR)]:
+            bplan.set_method(mth)
+
+            def one(bplan=bplan, bst=bst):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                bplan.expand(bst, nb, stream=stream)
+                b0.record(stream)
+                torch.cuda.synchronize()
+                return a0.elapsed_time(b0)
+            one()
+            ms_b = min(one() for _ in range(5))
+            tf = big["algorithmic_flops"] / (ms_b * 1e-3) / 1e12
+            big[mname] = {"ms": ms_b, "tflops": tf, "tensor_frac": tf / tc_peak,
+                          "status": bplan.status(),
+                          "first_4096_identical": bool(torch.equal(bst[:4096], ref4k))}
+        res["partition_plan"]["expand_2p20"] = big
+        bplan.close()
+        del bst, flush
     except Exception as e:  # noqa: BLE001
         res["partition_plan"] = {"error": f"{type(e).__name__}: {e}"}
 
