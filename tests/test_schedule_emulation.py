@@ -1,0 +1,170 @@
+"""CPU emulations of two GPU schedules, checked against the oracle.
+
+These tests replay, in numpy, the exact index arithmetic two kernels use, so
+that a wrong offset, block order or fold step in the design fails on the CPU
+(the GPU parity tests then check the kernels themselves):
+
+* the warp-per-stream table jump (one warp per stream): the product of two
+  polynomials mod phi = t^97 + t^64 - 1 over Z/2^24 (Sec. 3.1) with lane l
+  forming coefficients 6l .. 6l+5 through a sliding window over a
+  zero-padded copy of b, the fold in three blocks of distinct targets, and
+  the application x P(A) (Sec. 3.1, the linear combination of the window)
+  with lane l forming outputs 3l .. 3l+2;
+* the tensor-core plan level: x' = x M mod 2^24 from balanced 8-bit limbs
+  in fp16, with A = [A0 | A1 | A2 | 0] and B = [B2 | B1 | B0 | 0] along
+  K = 320 (limb blocks of 104), D2 over all of K, D1 = A[0, 208) B[104, 312),
+  D0 = A[0, 112) B[208, 320), each accumulator inside the range where fp32
+  sums of integers are exact, and x' = D0 + 2^8 D1 + 2^16 D2 mod 2^24.
+"""
+import numpy as np
+
+R, S = 97, 33
+M32 = (1 << 32) - 1
+MASK = (1 << 24) - 1
+
+
+def u32(v):
+    return int(v) & M32
+
+
+# --- warp-per-stream jump --------------------------------------------------
+def warp_mulmod(a, b):
+    """a b mod phi as the warp kernel schedules it (arithmetic mod 2^32)."""
+    a = [int(v) for v in a] + [0, 0, 0]          # a[97..99]: the row padding
+    bz = [0] * 288                               # b_0 at 96, zeros either side
+    for i in range(R):
+        bz[96 + i] = int(b[i])
+    c = [0] * 193
+    for lane in range(32):
+        n0 = 6 * lane
+        win = [bz[96 + n0 + j] for j in range(6)]
+        acc = [0] * 6
+        for i in range(R):
+            for j in range(6):
+                acc[j] = u32(acc[j] + a[i] * win[j])
+            if i + 1 < R:
+                win = [bz[96 + n0 - i - 1]] + win[:5]
+        for j in range(6):
+            c[n0 + j] = acc[j]
+    c[192] = u32(a[96] * int(b[96]))
+    # fold blocks [160, 192], [127, 159], [97, 126]: all reads of a block
+    # before its writes, targets distinct and below the block
+    for hi, lo in ((192, 160), (159, 127), (126, 97)):
+        ks = list(range(hi, lo - 1, -1))
+        vals = {k: c[k] for k in ks}
+        targets = [k - R for k in ks] + [k - S for k in ks]
+        assert len(set(targets)) == len(targets) and max(targets) < lo
+        for k in ks:
+            c[k - R] = u32(c[k - R] + vals[k])
+            c[k - S] = u32(c[k - S] - vals[k])
+    return np.array([v & MASK for v in c[:R]], dtype=np.uint32)
+
+
+def warp_apply(x, p):
+    """New state words k = sum_i p_i X_{i+k} as the warp kernel schedules it."""
+    X = [int(v) for v in x] + [0] * 96
+    for r in range(3):
+        q0 = R + S * r
+        q1 = min(R + S * (r + 1), 2 * R - 1)
+        src = [(X[q - R], X[q - S]) for q in range(q0, q1)]   # reads first
+        assert all(q - S < q0 for q in range(q0, q1))
+        for q, (u, v) in zip(range(q0, q1), src):
+            X[q] = u32(u - v)
+    p = [int(v) for v in p]
+    out = [0] * R
+    for lane in range(32):
+        k0 = 3 * lane
+        win = [X[k0 + j] for j in range(3)]
+        acc = [0] * 3
+        for i in range(R):
+            for j in range(3):
+                acc[j] = u32(acc[j] + p[i] * win[j])
+            if i + 1 < R:
+                win = win[1:] + [X[k0 + 3 + i]]
+        for j in range(3):
+            out[k0 + j] = acc[j]
+    out[96] = u32(sum(p[i] * X[96 + i] for i in range(R)))
+    return np.array([v & MASK for v in out], dtype=np.uint32)
+
+
+def test_warp_product_schedule_matches_oracle(orc):
+    rng = np.random.default_rng(5)
+    cases = [(1, 1), (96, 1), (97, 0), (12345, 2**40), (2**64 + 7, 2**100 + 3)]
+    cases += [(int(a), int(b)) for a, b in rng.integers(0, 2**62, (4, 2))]
+    for ea, eb in cases:
+        pa, pb = orc.poly_pow_t(ea), orc.poly_pow_t(eb)
+        got = warp_mulmod(pa, pb)
+        assert np.array_equal(got, orc.poly_mulmod(pa, pb)), (ea, eb)
+        assert np.array_equal(got, orc.poly_pow_t(ea + eb)), (ea, eb)   # P_a P_b = P_{a+b}
+    # dense random operands (not powers of t)
+    for _ in range(3):
+        a = rng.integers(0, 1 << 24, R, dtype=np.uint32)
+        b = rng.integers(0, 1 << 24, R, dtype=np.uint32)
+        assert np.array_equal(warp_mulmod(a, b), orc.poly_mulmod(a, b))
+
+
+def test_warp_apply_schedule_matches_oracle(orc):
+    x, c = orc.seeded_state(12345)
+    for e in (0, 1, 33, 96, 97, 10**6, 2**40 + 5):
+        p = orc.poly_pow_t(e)
+        xe, _ = orc.jump(x, c, e)
+        got = warp_apply(x, p)
+        assert np.array_equal(got, xe), e
+        assert np.array_equal(got, orc.apply_dot(x, p)), e
+
+
+# --- tensor-core plan level ------------------------------------------------
+LIMB_K, KTOT, NPAD = 104, 320, 112
+
+
+def limbs(v):
+    """Balanced 8-bit limbs l_0..l_2 of 24-bit words: the bytes of
+    (v + 0x808080) mod 2^24, minus 128; v = sum 2^(8k) l_k mod 2^24."""
+    w = (v.astype(np.int64) + 0x808080) & MASK
+    return [((w >> (8 * k)) & 0xFF) - 128 for k in range(3)]
+
+
+def plan_level_emulated(X, M):
+    """x' = x M mod 2^24 (rows of X: source states; M: 97 x 97 words) through
+    the K = 320 limb layout and the three accumulators."""
+    n = X.shape[0]
+    A = np.zeros((n, KTOT), np.int64)
+    for k, l in enumerate(limbs(X)):              # A = [A0 | A1 | A2 | 0]
+        A[:, LIMB_K * k: LIMB_K * k + R] = l
+    B = np.zeros((KTOT, NPAD), np.int64)
+    ml = limbs(M)                                 # B = [B2 | B1 | B0 | 0]
+    for blk, k in enumerate((2, 1, 0)):
+        B[LIMB_K * blk: LIMB_K * blk + R, :R] = ml[k]
+    D2 = A @ B                                    # A0 B2 + A1 B1 + A2 B0
+    D1 = A[:, :2 * LIMB_K] @ B[LIMB_K:3 * LIMB_K]  # A0 B1 + A1 B0
+    D0 = A[:, :NPAD] @ B[2 * LIMB_K:]             # A0 B0
+    # fp32 accumulation of these integer products is exact below 2^24
+    assert np.abs(D2).max() < 2**23 and np.abs(D1).max() < 2**22 and np.abs(D0).max() < 2**22
+    out = (D0 + (D1 << 8) + (D2 << 16)) & MASK
+    return out[:, :R].astype(np.uint32)
+
+
+def test_plan_limb_layout_matches_modular_product():
+    rng = np.random.default_rng(9)
+    X = rng.integers(0, 1 << 24, (37, R), dtype=np.int64)
+    M = rng.integers(0, 1 << 24, (R, R), dtype=np.int64)
+    X[0] = MASK                                   # extreme words: all limbs 127
+    X[1] = 0x808080                               # all limbs 0
+    X[2] = 0x7F7F7F                               # all limbs -1
+    M[:, 0] = MASK
+    want = np.zeros((X.shape[0], R), np.int64)
+    for j in range(R):                            # exact, then mod 2^24
+        want[:, j] = (X * M[:, j]).sum(axis=1) & MASK
+    assert np.array_equal(plan_level_emulated(X, M), want.astype(np.uint32))
+
+
+def test_plan_limb_layout_is_the_jump(orc):
+    """Rows of M_E = the unit states jumped by E: x M_E is x jumped by E."""
+    E = 2**40 + 77
+    M = np.stack([orc.jump(np.eye(R, dtype=np.uint32)[i], 0, E)[0] for i in range(R)])
+    xs = [orc.seeded_state(s)[0] for s in (12345, 2, 54217138)]
+    X = np.stack(xs).astype(np.int64)
+    got = plan_level_emulated(X, M.astype(np.int64))
+    for i, s in enumerate((12345, 2, 54217138)):
+        x, c = orc.seeded_state(s)
+        assert np.array_equal(got[i], orc.jump(x, c, E)[0])
