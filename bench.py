@@ -740,6 +740,31 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
                           "table": {"ms": ms_t, "jumps_per_s": lj.n_streams / (ms_t * 1e-3),
                                     "tmacs_per_s": macs_t / (ms_t * 1e-3) / 1e12,
                                     "alu_frac": macs_t / (ms_t * 1e-3) / 1e12 / alu_peak}}
+    # the polynomial part alone, t^J mod phi (the paper's Table 2 times one
+    # such power on a CPU): one power (the latency of one warp's chain) and
+    # 16,384 at once (throughput), by the paper's square-and-multiply
+    try:
+        pp = {}
+        for label, Jp in [("2^64-1", (1 << 64) - 1), ("2^120-1", (1 << 120) - 1)]:
+            row = {}
+            for npw in (1, 16384):
+                exq = rm.exps_tensor([Jp] * npw, 5, device=dev)
+                poq = torch.empty((npw, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+                ms_pp = timed(lambda exq=exq, poq=poq: rm.poly_power(exq, out=poq))
+                macs_pp = npw * dense_squarings(Jp) * SQ_MACS
+                row[str(npw)] = {"ms": ms_pp, "powers_per_s": npw / (ms_pp * 1e-3),
+                                 "alu_frac": macs_pp / (ms_pp * 1e-3) / 1e12 / alu_peak}
+            pp["J=" + label] = row
+        pp["paper_cpu_powers_per_s"] = {"J=" + k: [1e6 / t for t in v]
+                                        for k, v in PAPER_TABLE2_US.items()}
+        pp["note"] = ("ranmar_poly_power: P_J = t^J mod (t^97 + t^64 - 1) over Z/2^24 by "
+                      "left-to-right square-and-multiply, 2 lanes per power; the paper's "
+                      "CPU figures (Table 2: M2 Pro, Raspberry Pi 4B, Threadripper 3970X, "
+                      "Core i7-14700F) are context, one power at a time")
+        res["poly_power"] = pp
+    except Exception as ex_:  # noqa: BLE001
+        res["poly_power"] = {"error": f"{type(ex_).__name__}: {ex_}"}
+
     # the same 16,384 jumps by the partition plan (the first 256 by the
     # plan's table of the powers of t^J, then one tensor-core level of jump
     # matrices), and all of them by that table (P_{kJ} over the digits of k);

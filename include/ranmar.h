@@ -137,6 +137,21 @@ int ranmar_jump(const ranmar_state_t *d_base, size_t n_base,
                 uint32_t *d_status, ranmar_stream_t stream);
 
 /*
+ * ranmar_poly_power -- Sec. 3.1, the polynomial part of a jump alone (what
+ * the paper's Table 2 times): d_poly[i] = P_{E_i}(t) = t^{E_i} mod (t^97 +
+ * t^64 - 1) over Z/2^24, by the same left-to-right square-and-multiply as
+ * ranmar_jump, for E_i the little-endian integer d_exp[i*exp_words ..
+ * (i+1)*exp_words) (device).  d_poly (device, n x 100 uint32, caller-owned):
+ * coefficients 0..96 of P_{E_i} (24-bit canonical, coefficient j of t^j),
+ * then three zero words.  Two lanes per exponent, 16 per warp; asynchronous
+ * on `stream`; n = 0 is a no-op.  Errors: RANMAR_EINVAL (NULL with n > 0,
+ * misaligned or overlapping buffers), RANMAR_ERANGE (exp_words not in
+ * 1..RANMAR_MAX_EXP_WORDS, or n too large for one launch).
+ */
+int ranmar_poly_power(const uint32_t *d_exp, uint32_t exp_words, size_t n, uint32_t *d_poly,
+                      ranmar_stream_t stream);
+
+/*
  * ranmar_jump_scatter -- ranmar_jump with per-stream destinations:
  * d_dst[d_dst_idx[i]] = f^{E_i}(d_base[d_base_idx[i]]) (d_base_idx NULL =
  * base 0).  For state pools that are read and written in place (a serving

@@ -13,6 +13,6 @@ from .binding import (  # noqa: F401
     generate_alg1_f32, generate_alg1_f64, generate_f32, jump_scatter,
     partition_ex,
     generate_plain_f32, generate_plain_u24, generate_u24, jump, lib_path, make_desc,
-    partition, seed, seed_batch, ST_BAD_SEED, shape_bucket, state_words_np, Table, Plan,
+    partition, poly_power, seed, seed_batch, ST_BAD_SEED, shape_bucket, state_words_np, Table, Plan,
     LFG_CLASSICAL, LFG_KARATSUBA, LFG_KARATSUBA_LEVELS, lfg_jump, lfg_generate, lfg_karatsuba_levels, tune_cached, words,
 )

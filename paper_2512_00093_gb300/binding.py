@@ -111,6 +111,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_plan_status.argtypes = [_vp, ctypes.POINTER(_vp)]
     lib.ranmar_table_set_ctas_per_sm.argtypes = [_vp, ctypes.c_int]
     lib.ranmar_table_set_ctas_per_sm.restype = ctypes.c_int
+    lib.ranmar_poly_power.argtypes = [_vp, _u32, _sz, _vp, _vp]
+    lib.ranmar_poly_power.restype = ctypes.c_int
     lib.ranmar_table_set_jump_mapping.argtypes = [_vp, ctypes.c_int]
     lib.ranmar_table_set_jump_mapping.restype = ctypes.c_int
     lib.ranmar_plan_set_jump_mapping.argtypes = [_vp, ctypes.c_int]
@@ -240,6 +242,21 @@ def jump(base: torch.Tensor, exps: torch.Tensor, base_idx: torch.Tensor | None =
         _need(status, torch.int32, "status")
     _check(_lib().ranmar_jump(_ptr(base), base.shape[0], _ptr(base_idx), _ptr(exps), nw,
                               _ptr(out), n, _ptr(status), _stream(stream)), "ranmar_jump")
+    return out
+
+
+def poly_power(exps: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """ranmar_poly_power: out[i, :97] = t^{E_i} mod (t^97 + t^64 - 1) over
+    Z/2^24 (out[i, 97:] = 0); exps is (n, w) int32 little-endian words."""
+    _need(exps, torch.int32, "exps")
+    n, nw = exps.shape
+    if out is None:
+        out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=exps.device)
+    _need(out, torch.int32, "out")
+    if out.numel() < n * STATE_WORDS:
+        raise ValueError("out too small")
+    _check(_lib().ranmar_poly_power(_ptr(exps), nw, n, _ptr(out), _stream(stream)),
+           "ranmar_poly_power")
     return out
 
 

@@ -554,4 +554,30 @@ __global__ void __launch_bounds__(32, 12) jump_kernel(
   jump_pair(base, Ep, E, active, d_out + (active ? di : 0), a, R, g);
 }
 
+// P_{E_i} = t^{E_i} mod phi alone (the polynomial part of a jump, Sec. 3.1),
+// by the same square-and-multiply: d_poly[i] = coefficients 0..96 (24-bit),
+// then three zero words.
+__global__ void __launch_bounds__(32, 12) poly_power_kernel(const uint32_t* __restrict__ d_exp,
+                                                            uint32_t exp_words,
+                                                            uint32_t* __restrict__ d_poly,
+                                                            uint64_t n) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned g = lane >> 4;
+  const unsigned slot = lane & 15;
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * kJumpStreamsPerWarp + slot;
+  uint32_t* a = smem + slot * kStreamWords;
+  uint32_t* R = a + kPolyWords;
+  const bool active = i < n;
+  uint32_t E[kMaxExpWords];
+  const ExpParams part{};
+  load_exponent(E, 0, d_exp, active ? exp_words : 0, part, active ? i : 0);
+  poly_power_pair(E, active, a, R, g);
+  __syncwarp();
+  if (active) {
+    uint32_t* dst = d_poly + i * kPolyWords;
+    for (int q = static_cast<int>(g); q < kPolyWords; q += 2) dst[q] = q < kR ? (a[q] & kMask24) : 0u;
+  }
+}
+
 }  // namespace ranmar

@@ -540,6 +540,24 @@ int ranmar_jump(const ranmar_state_t* d_base, size_t n_base, const uint32_t* d_b
                      stream);
 }
 
+int ranmar_poly_power(const uint32_t* d_exp, uint32_t exp_words, size_t n, uint32_t* d_poly,
+                      ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_poly_power");
+  if (n == 0) return RANMAR_OK;
+  if (!d_exp || !d_poly) return RANMAR_EINVAL;
+  if (exp_words < 1 || exp_words > RANMAR_MAX_EXP_WORDS) return RANMAR_ERANGE;
+  if (!aligned(d_exp, 4) || !aligned(d_poly, 4)) return RANMAR_EINVAL;
+  if (overlaps(d_exp, n * exp_words * sizeof(uint32_t), d_poly,
+               n * ranmar::kPolyWords * sizeof(uint32_t)))
+    return RANMAR_EINVAL;
+  const uint64_t blocks = (n + ranmar::kJumpStreamsPerWarp - 1) / ranmar::kJumpStreamsPerWarp;
+  if (blocks > 0x7FFFFFFFull) return RANMAR_ERANGE;
+  ranmar::poly_power_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kJumpSmemBytes,
+                              reinterpret_cast<cudaStream_t>(stream)>>>(d_exp, exp_words, d_poly,
+                                                                        n);
+  return check_launch();
+}
+
 int ranmar_partition(const ranmar_state_t* d_base, const uint32_t* h_J, uint32_t J_words,
                      uint64_t k0, ranmar_state_t* d_out, size_t n, ranmar_stream_t stream) {
   NvtxRange nvtx_("ranmar_partition");

@@ -1,0 +1,51 @@
+"""GPU parity of ranmar_poly_power (Sec. 3.1, the polynomial part of a jump,
+what the paper's Table 2 times): t^E mod (t^97 + t^64 - 1) over Z/2^24 equals
+the oracle's for edge and random exponents up to 2^160 - 1, bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_00093_gb300 as rm
+    return rm
+
+
+def test_poly_power_matches_oracle(rm, orc):
+    from paper_2512_00093_gb300.workloads import random_exponents
+    dev = torch.device("cuda:0")
+    edge = [0, 1, 2, 63, 64, 96, 97, 98, 193, (1 << 64) - 1, (1 << 120) - 1,
+            ((1 << 97) - 1) << 23, (1 << 159) + 3, (1 << 160) - 1]
+    exps = edge + random_exponents(45, 160, seed=8)
+    got = rm.poly_power(rm.exps_tensor(exps, 5, device=dev))
+    torch.cuda.synchronize()
+    g = got.cpu().numpy().view(np.uint32)
+    assert not g[:, 97:].any()
+    for i, e in enumerate(exps):
+        assert np.array_equal(g[i, :97], orc.poly_pow_t(e)), (i, e)
+
+
+def test_poly_power_is_the_jumps_polynomial(rm, orc):
+    """x P_E(A) from the returned coefficients is the jumped state."""
+    dev = torch.device("cuda:0")
+    exps = [5, 10**6, (1 << 64) - 1, (1 << 120) + 12345]
+    p = rm.poly_power(rm.exps_tensor(exps, 5, device=dev)).cpu().numpy().view(np.uint32)
+    x, c = orc.seeded_state(12345)
+    for i, e in enumerate(exps):
+        assert np.array_equal(orc.apply_dot(x, p[i, :97]), orc.jump(x, c, e)[0])
+
+
+def test_poly_power_ragged_batch_and_errors(rm, orc):
+    dev = torch.device("cuda:0")
+    for n in (1, 15, 16, 17, 33):
+        exps = [(1 << 64) - 1 - i for i in range(n)]
+        got = rm.poly_power(rm.exps_tensor(exps, 3, device=dev)).cpu().numpy().view(np.uint32)
+        for i in {0, n - 1}:
+            assert np.array_equal(got[i, :97], orc.poly_pow_t(exps[i]))
+    with pytest.raises(rm.RanmarError):
+        rm.poly_power(torch.zeros((2, 6), dtype=torch.int32, device=dev))   # 6 words

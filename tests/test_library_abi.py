@@ -90,6 +90,12 @@ def test_host_argument_checks(lib):
     assert L.ranmar_debug_fail_next(1) == -1 and L.ranmar_debug_fail_next(-6) == -1
     assert L.ranmar_debug_fail_next(0) == 0
     assert L.ranmar_plan_set_ctas(None, 4) == -1
+    L.ranmar_poly_power.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_size_t,
+                                    ctypes.c_void_p, ctypes.c_void_p]
+    assert L.ranmar_poly_power(None, 1, 1, fake, None) == -1
+    assert L.ranmar_poly_power(fake, 0, 1, vp(0x20000), None) == -2
+    assert L.ranmar_poly_power(fake, 6, 1, vp(0x20000), None) == -2
+    assert L.ranmar_poly_power(None, 1, 0, None, None) == 0                              # n = 0
     L.ranmar_table_set_jump_mapping.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.ranmar_plan_set_jump_mapping.argtypes = [ctypes.c_void_p, ctypes.c_int]
     assert L.ranmar_table_set_jump_mapping(None, 0) == -1
