@@ -123,7 +123,9 @@ int ranmar_seed_batch(const int32_t *d_seeds, size_t n, ranmar_state_t *d_out,
  * i the kernel forms P = t^{E_i} mod (t^97 + t^64 - 1) over Z/2^24 by
  * left-to-right square-and-multiply, applies x P(A) as sum_j b_j x_{j+k},
  * and sets c = (c_base - E_i d) mod m, pos = pos_base + E_i mod 2^64.
- * One 32-lane warp serves 16 streams, two lanes per stream.
+ * One 32-lane warp serves 16 streams, two lanes per stream; a batch of at
+ * most RANMAR_JUMP_WARP_AUTO_MAX streams instead gives each stream a whole
+ * warp (its chain of squarings is then ~8 times shorter).  Same results.
  * d_out must not overlap d_base.  n = 0 is a no-op.
  * Errors: RANMAR_EINVAL (null pointer with n > 0, misaligned states,
  * overlapping in/out), RANMAR_ERANGE (exp_words not in 1..5, n_base = 0, or
@@ -143,7 +145,8 @@ int ranmar_jump(const ranmar_state_t *d_base, size_t n_base,
  * ranmar_jump, for E_i the little-endian integer d_exp[i*exp_words ..
  * (i+1)*exp_words) (device).  d_poly (device, n x 100 uint32, caller-owned):
  * coefficients 0..96 of P_{E_i} (24-bit canonical, coefficient j of t^j),
- * then three zero words.  Two lanes per exponent, 16 per warp; asynchronous
+ * then three zero words.  Two lanes per exponent, 16 per warp (a warp per
+ * exponent up to RANMAR_JUMP_WARP_AUTO_MAX exponents); asynchronous
  * on `stream`; n = 0 is a no-op.  Errors: RANMAR_EINVAL (NULL with n > 0,
  * misaligned or overlapping buffers), RANMAR_ERANGE (exp_words not in
  * 1..RANMAR_MAX_EXP_WORDS, or n too large for one launch).

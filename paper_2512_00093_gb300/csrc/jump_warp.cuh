@@ -266,4 +266,124 @@ __global__ void __launch_bounds__(32 * kWarpJumpWarps) jump_jtable_warp_kernel(
   }
 }
 
+// ---------------------------------------------------------------------------
+// Square-and-multiply with a warp per stream (Sec. 3.1, the paper's method):
+// the same left-to-right exponentiation as poly_power_pair, each squaring a
+// warp product of a with a copy of itself (the symmetric half is not used:
+// in lockstep the lanes would wait for the longest triangle anyway), a 1 bit
+// a shift by t with the fold t^97 = 1 - t^64.  For small batches only: per
+// stream it executes about three times the instructions of the pair kernel,
+// but its chain of ~bitlen(E) squarings is ~8 times shorter.
+
+// a = a^2 t^bit mod phi
+__device__ __forceinline__ void square_times_warp(uint32_t* __restrict__ s, uint32_t bit,
+                                                  unsigned lane) {
+  uint32_t* a = s + kWjA;
+  for (int q = static_cast<int>(lane); q < kR; q += 32) s[kWjB0 + q] = a[q];
+  __syncwarp();
+  poly_mulmod_warp(a, s + kWjBz, s + kWjC, lane);
+  if (bit) {
+    // t a: a_q <- a_{q-1}, a_0 <- a_96, a_64 <- a_63 - a_96
+    const uint32_t top = a[kR - 1];
+    uint32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int q = static_cast<int>(lane) + 32 * k;
+      v[k] = q < kR ? (q == 0 ? top : a[q - 1]) : 0u;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int q = static_cast<int>(lane) + 32 * k;
+      if (q < kR) a[q] = q == kR - kS ? v[k] - top : v[k];
+    }
+    __syncwarp();
+  }
+}
+
+// a = t^E mod phi (a in s[kWjA..]); E is the same in every lane.
+__device__ __forceinline__ void poly_power_warp(const uint32_t (&E)[kMaxExpWords],
+                                                uint32_t* __restrict__ s, unsigned lane) {
+  const int L = exp_bitlen(E);
+  // leading (up to) six bits: t^v0 with v0 < 64 < 97 is a monomial
+  uint32_t v0;
+  int pbit;
+  if (L <= 6) {
+    v0 = E[0] & 63u;
+    pbit = -1;
+  } else {
+    v0 = exp_bits6(E, L - 6);
+    pbit = L - 7;
+  }
+  uint32_t* a = s + kWjA;
+  for (int q = static_cast<int>(lane); q < kR; q += 32) a[q] = q == static_cast<int>(v0) ? 1u : 0u;
+  __syncwarp();
+#pragma unroll 1
+  for (; pbit >= 0; --pbit) square_times_warp(s, exp_bit(E, pbit), lane);
+}
+
+// Same contract as poly_power_kernel, one warp per exponent.
+__global__ void __launch_bounds__(32 * kWarpJumpWarps) poly_power_warp_kernel(
+    const uint32_t* __restrict__ d_exp, uint32_t exp_words, uint32_t* __restrict__ d_poly,
+    uint64_t n) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* s = smem + w * kWjWords;
+  zero_margins_warp(s, lane);
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kWarpJumpWarps;
+  const ExpParams part{};
+#pragma unroll 1
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * kWarpJumpWarps + w; i < n; i += stride) {
+    uint32_t E[kMaxExpWords];
+    load_exponent(E, 0, d_exp, exp_words, part, i);
+    poly_power_warp(E, s, lane);
+    uint32_t* dst = d_poly + i * kPolyWords;
+    for (int q = static_cast<int>(lane); q < kPolyWords; q += 32)
+      dst[q] = q < kR ? (s[kWjA + q] & kMask24) : 0u;
+    __syncwarp();
+  }
+}
+
+// Same contract as jump_kernel (modes 0 and 1, base and destination
+// indices, the period reduction), one warp per stream.
+__global__ void __launch_bounds__(32 * kWarpJumpWarps) jump_warp_kernel(
+    const ranmar_state_t* __restrict__ d_base, uint64_t n_base,
+    const uint32_t* __restrict__ d_base_idx, const uint32_t* __restrict__ d_exp,
+    uint32_t exp_words, ExpParams part, int mode, ranmar_state_t* __restrict__ d_out,
+    uint64_t n, uint32_t* status, const uint32_t* __restrict__ d_dst_idx, uint64_t n_dst) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* s = smem + w * kWjWords;
+  zero_margins_warp(s, lane);
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kWarpJumpWarps;
+#pragma unroll 1
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * kWarpJumpWarps + w; i < n; i += stride) {
+    uint32_t E[kMaxExpWords];
+    load_exponent(E, mode, d_exp, exp_words, part, i);
+    const ranmar_state_t* base = d_base;
+    if (mode == 0) {
+      const uint32_t bi = d_base_idx ? d_base_idx[i] : 0u;
+      if (bi >= n_base) {
+        if (lane == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
+        continue;
+      }
+      base = d_base + bi;
+    }
+    uint64_t di = i;
+    if (d_dst_idx) {
+      di = d_dst_idx[i];
+      if (di >= n_dst) {
+        if (lane == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
+        continue;
+      }
+    }
+    uint32_t Ep[kMaxExpWords];
+#pragma unroll
+    for (int q = 0; q < kMaxExpWords; ++q) Ep[q] = E[q];
+    if (part.flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
+    poly_power_warp(Ep, s, lane);
+    apply_warp(base, E, d_out + di, s, lane);
+  }
+}
+
 }  // namespace ranmar

@@ -238,10 +238,18 @@ int launch_jump(const ranmar_state_t* base, size_t n_base, const uint32_t* base_
                 const uint32_t* exp, uint32_t exp_words, const ranmar::ExpParams& part,
                 int mode, ranmar_state_t* out, size_t n, uint32_t* status,
                 ranmar_stream_t stream, const uint32_t* dst_idx = nullptr, size_t n_dst = 0) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n <= RANMAR_JUMP_WARP_AUTO_MAX) {
+    // a small batch: a warp per stream shortens each stream's chain of squarings
+    const uint64_t wblocks = (n + ranmar::kWarpJumpWarps - 1) / ranmar::kWarpJumpWarps;
+    ranmar::jump_warp_kernel<<<static_cast<unsigned>(wblocks), 32 * ranmar::kWarpJumpWarps,
+                               ranmar::kWarpJumpSmemBytes, s>>>(
+        base, n_base, base_idx, exp, exp_words, part, mode, out, n, status, dst_idx, n_dst);
+    return check_launch();
+  }
   const uint64_t per_cta = ranmar::kJumpStreamsPerWarp;   // one warp per CTA
   const uint64_t blocks = (n + per_cta - 1) / per_cta;
   if (blocks > 0x7FFFFFFFull) return RANMAR_ERANGE;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   ranmar::jump_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kJumpSmemBytes, s>>>(
       base, n_base, base_idx, exp, exp_words, part, mode, out, n, status, dst_idx, n_dst);
   return check_launch();
@@ -550,6 +558,14 @@ int ranmar_poly_power(const uint32_t* d_exp, uint32_t exp_words, size_t n, uint3
   if (overlaps(d_exp, n * exp_words * sizeof(uint32_t), d_poly,
                n * ranmar::kPolyWords * sizeof(uint32_t)))
     return RANMAR_EINVAL;
+  if (n <= RANMAR_JUMP_WARP_AUTO_MAX) {
+    const uint64_t wblocks = (n + ranmar::kWarpJumpWarps - 1) / ranmar::kWarpJumpWarps;
+    ranmar::poly_power_warp_kernel<<<static_cast<unsigned>(wblocks), 32 * ranmar::kWarpJumpWarps,
+                                     ranmar::kWarpJumpSmemBytes,
+                                     reinterpret_cast<cudaStream_t>(stream)>>>(d_exp, exp_words,
+                                                                               d_poly, n);
+    return check_launch();
+  }
   const uint64_t blocks = (n + ranmar::kJumpStreamsPerWarp - 1) / ranmar::kJumpStreamsPerWarp;
   if (blocks > 0x7FFFFFFFull) return RANMAR_ERANGE;
   ranmar::poly_power_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kJumpSmemBytes,

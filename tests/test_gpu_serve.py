@@ -63,8 +63,11 @@ def test_serving_mix_matches_oracle_and_alone(rm, orc):
     from paper_2512_00093_gb300.serve import Engine, Request
     reqs = mixed_requests(260, 7)
     # small segments, few segments per iteration and a tiny state pool: many
-    # iterations, multi-segment requests, pool jumps, resumes and evictions
-    eng = Engine(budget_bytes=64 << 20, seg=4096, state_entries=96,
+    # iterations, multi-segment requests, pool jumps, resumes and evictions.
+    # 40 entries: the 30 distinct streams stay resident once seen, so every
+    # admission of a request of more than 10 segments must evict, however
+    # many iterations happen to be in flight
+    eng = Engine(budget_bytes=64 << 20, seg=4096, state_entries=40,
                  max_segments_per_iter=48, max_inflight=3, use_table=False)
     summary = eng.run(reqs, realtime=False)
     assert summary["requests"] == len(reqs)
