@@ -124,8 +124,8 @@ int ranmar_seed_batch(const int32_t *d_seeds, size_t n, ranmar_state_t *d_out,
  * left-to-right square-and-multiply, applies x P(A) as sum_j b_j x_{j+k},
  * and sets c = (c_base - E_i d) mod m, pos = pos_base + E_i mod 2^64.
  * One 32-lane warp serves 16 streams, two lanes per stream; a batch of at
- * most RANMAR_JUMP_WARP_AUTO_MAX streams instead gives each stream a whole
- * warp (its chain of squarings is then ~8 times shorter).  Same results.
+ * most RANMAR_SQUARE_WARP_AUTO_MAX streams instead gives each stream a whole
+ * warp (its chain of squarings is then ~5 times shorter).  Same results.
  * d_out must not overlap d_base.  n = 0 is a no-op.
  * Errors: RANMAR_EINVAL (null pointer with n > 0, misaligned states,
  * overlapping in/out), RANMAR_ERANGE (exp_words not in 1..5, n_base = 0, or
@@ -146,7 +146,7 @@ int ranmar_jump(const ranmar_state_t *d_base, size_t n_base,
  * (i+1)*exp_words) (device).  d_poly (device, n x 100 uint32, caller-owned):
  * coefficients 0..96 of P_{E_i} (24-bit canonical, coefficient j of t^j),
  * then three zero words.  Two lanes per exponent, 16 per warp (a warp per
- * exponent up to RANMAR_JUMP_WARP_AUTO_MAX exponents); asynchronous
+ * exponent up to RANMAR_SQUARE_WARP_AUTO_MAX exponents); asynchronous
  * on `stream`; n = 0 is a no-op.  Errors: RANMAR_EINVAL (NULL with n > 0,
  * misaligned or overlapping buffers), RANMAR_ERANGE (exp_words not in
  * 1..RANMAR_MAX_EXP_WORDS, or n too large for one launch).
@@ -299,6 +299,10 @@ int ranmar_table_set_ctas_per_sm(ranmar_table_t *t, int ctas_per_sm);
 #define RANMAR_JUMP_MAP_PAIR 1
 #define RANMAR_JUMP_MAP_WARP 2
 #define RANMAR_JUMP_WARP_AUTO_MAX 8192
+/* The square-and-multiply jumps (ranmar_jump, ranmar_jump_scatter,
+ * ranmar_partition, ranmar_partition_ex without a table) and
+ * ranmar_poly_power take a warp per stream up to this many streams. */
+#define RANMAR_SQUARE_WARP_AUTO_MAX 4096
 int ranmar_table_set_jump_mapping(ranmar_table_t *t, int map);
 /* Device address of the rows (row j*256 + d, 100 words each), for checks. */
 int ranmar_table_rows(const ranmar_table_t *t, const uint32_t **d_rows);

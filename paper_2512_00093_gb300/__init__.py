@@ -9,7 +9,7 @@ from .binding import (  # noqa: F401
     BatchConfig, Graph, RanmarError, abi_version, capture, check_overlap, checksum, checksum_np,
     debug_fail_next, debug_set_wait_limit,
     exps_tensor, ST_OVERLAP, ST_TIMEOUT,
-    JUMP_REDUCE_PERIOD, JUMP_MAP_AUTO, JUMP_MAP_PAIR, JUMP_MAP_WARP, JUMP_WARP_AUTO_MAX,
+    JUMP_REDUCE_PERIOD, JUMP_MAP_AUTO, JUMP_MAP_PAIR, JUMP_MAP_WARP, JUMP_WARP_AUTO_MAX, SQUARE_WARP_AUTO_MAX,
     generate_alg1_f32, generate_alg1_f64, generate_f32, jump_scatter,
     partition_ex,
     generate_plain_f32, generate_plain_u24, generate_u24, jump, lib_path, make_desc,

@@ -318,6 +318,7 @@ JUMP_REDUCE_PERIOD = 1
 # ranmar_*_set_jump_mapping: lanes per stream of the table jumps
 JUMP_MAP_AUTO, JUMP_MAP_PAIR, JUMP_MAP_WARP = 0, 1, 2
 JUMP_WARP_AUTO_MAX = 8192
+SQUARE_WARP_AUTO_MAX = 4096    # the same for the square-and-multiply jumps and poly_power
 
 
 def partition_ex(base: torch.Tensor, J: int, k0: int, n: int, table=None, flags: int = 0,

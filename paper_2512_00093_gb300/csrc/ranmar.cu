@@ -239,7 +239,7 @@ int launch_jump(const ranmar_state_t* base, size_t n_base, const uint32_t* base_
                 int mode, ranmar_state_t* out, size_t n, uint32_t* status,
                 ranmar_stream_t stream, const uint32_t* dst_idx = nullptr, size_t n_dst = 0) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (n <= RANMAR_JUMP_WARP_AUTO_MAX) {
+  if (n <= RANMAR_SQUARE_WARP_AUTO_MAX) {
     // a small batch: a warp per stream shortens each stream's chain of squarings
     const uint64_t wblocks = (n + ranmar::kWarpJumpWarps - 1) / ranmar::kWarpJumpWarps;
     ranmar::jump_warp_kernel<<<static_cast<unsigned>(wblocks), 32 * ranmar::kWarpJumpWarps,
@@ -558,7 +558,7 @@ int ranmar_poly_power(const uint32_t* d_exp, uint32_t exp_words, size_t n, uint3
   if (overlaps(d_exp, n * exp_words * sizeof(uint32_t), d_poly,
                n * ranmar::kPolyWords * sizeof(uint32_t)))
     return RANMAR_EINVAL;
-  if (n <= RANMAR_JUMP_WARP_AUTO_MAX) {
+  if (n <= RANMAR_SQUARE_WARP_AUTO_MAX) {
     const uint64_t wblocks = (n + ranmar::kWarpJumpWarps - 1) / ranmar::kWarpJumpWarps;
     ranmar::poly_power_warp_kernel<<<static_cast<unsigned>(wblocks), 32 * ranmar::kWarpJumpWarps,
                                      ranmar::kWarpJumpSmemBytes,

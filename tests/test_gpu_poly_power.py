@@ -52,11 +52,11 @@ def test_poly_power_ragged_batch_and_errors(rm, orc):
 
 
 def test_poly_power_warp_and_pair_mappings_agree(rm):
-    """Batches up to JUMP_WARP_AUTO_MAX take a warp per exponent, larger ones
+    """Batches up to SQUARE_WARP_AUTO_MAX take a warp per exponent, larger ones
     two lanes: the same exponents through both give the same polynomials."""
     from paper_2512_00093_gb300.workloads import random_exponents
     dev = torch.device("cuda:0")
-    n = rm.JUMP_WARP_AUTO_MAX + 1
+    n = rm.SQUARE_WARP_AUTO_MAX + 1
     exps = random_exponents(n, 134, seed=12)
     ex = rm.exps_tensor(exps, 5, device=dev)
     pair = rm.poly_power(ex)                     # n > the switch: two lanes each
@@ -68,7 +68,7 @@ def test_poly_power_warp_and_pair_mappings_agree(rm):
 def test_square_multiply_jump_warp_and_pair_agree(rm):
     dev = torch.device("cuda:0")
     base = rm.seed(77).to(dev)
-    n = rm.JUMP_WARP_AUTO_MAX + 1
+    n = rm.SQUARE_WARP_AUTO_MAX + 1
     for J, flags in [((1 << 120) + 12345, 0), ((1 << 64) - 1, rm.JUMP_REDUCE_PERIOD)]:
         pair = rm.partition_ex(base, J, 3, n, flags=flags)          # square-and-multiply
         warp = rm.partition_ex(base, J, 3, n - 1, flags=flags)
