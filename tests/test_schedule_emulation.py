@@ -103,6 +103,33 @@ def test_warp_product_schedule_matches_oracle(orc):
         assert np.array_equal(warp_mulmod(a, b), orc.poly_mulmod(a, b))
 
 
+def warp_poly_power(e):
+    """t^e mod phi as the warp square-and-multiply schedules it: the leading
+    six bits as a monomial, then per bit a warp square and, on a 1 bit, the
+    shift by t with the fold t^97 = 1 - t^64."""
+    L = e.bit_length()
+    if L <= 6:
+        v0, p = e & 63, -1
+    else:
+        v0, p = (e >> (L - 6)) & 63, L - 7
+    a = np.zeros(R, np.uint32)
+    a[v0] = 1
+    while p >= 0:
+        a = warp_mulmod(a, a.copy())
+        if (e >> p) & 1:
+            top = int(a[R - 1])
+            v = [top] + [int(a[q - 1]) for q in range(1, R)]
+            v[R - S] = u32(v[R - S] - top)
+            a = np.array([x & MASK for x in v], dtype=np.uint32)
+        p -= 1
+    return a
+
+
+def test_warp_square_multiply_schedule_matches_oracle(orc):
+    for e in (0, 1, 63, 64, 65, 96, 97, 1000, 2**40 + 5, 2**64 - 1):
+        assert np.array_equal(warp_poly_power(e), orc.poly_pow_t(e)), e
+
+
 def test_warp_apply_schedule_matches_oracle(orc):
     x, c = orc.seeded_state(12345)
     for e in (0, 1, 33, 96, 97, 10**6, 2**40 + 5):
@@ -115,6 +142,15 @@ def test_warp_apply_schedule_matches_oracle(orc):
 
 # --- tensor-core plan level ------------------------------------------------
 LIMB_K, KTOT, NPAD = 104, 320, 112
+
+
+def test_limb_values():
+    for v, want in [(0x7F7F7F, [127] * 3), (0x7F7F80, [-128] * 3), (0, [0] * 3),
+                    ((1 << 24) - 1, [-1, 0, 0]), (0x123456, None)]:
+        l = [int(x[0]) for x in limbs(np.array([v]))]
+        if want is not None:
+            assert l == want, hex(v)
+        assert (l[0] + 256 * l[1] + 65536 * l[2]) % (1 << 24) == v
 
 
 def limbs(v):
@@ -148,10 +184,12 @@ def test_plan_limb_layout_matches_modular_product():
     rng = np.random.default_rng(9)
     X = rng.integers(0, 1 << 24, (37, R), dtype=np.int64)
     M = rng.integers(0, 1 << 24, (R, R), dtype=np.int64)
-    X[0] = MASK                                   # extreme words: all limbs 127
-    X[1] = 0x808080                               # all limbs 0
-    X[2] = 0x7F7F7F                               # all limbs -1
-    M[:, 0] = MASK
+    X[0] = 0x7F7F7F                               # limbs (127, 127, 127)
+    X[1] = 0x7F7F80                               # limbs (-128, -128, -128)
+    X[2] = 0                                      # limbs (0, 0, 0)
+    X[3] = MASK                                   # limbs (-1, 0, 0): -1 mod 2^24
+    M[:, 0] = 0x7F7F80                            # with X[1]: every product +2^14,
+    M[:, 1] = 0x7F7F7F                            # the accumulators' largest sums
     want = np.zeros((X.shape[0], R), np.int64)
     for j in range(R):                            # exact, then mod 2^24
         want[:, j] = (X * M[:, j]).sum(axis=1) & MASK
