@@ -193,7 +193,8 @@ __device__ __forceinline__ void apply_warp(const ranmar_state_t* __restrict__ ba
   __syncwarp();
 }
 
-// Zero margins of the b copy (set once per CTA; rows land only at b_0).
+// Zero margins of the b copy (set once per warp slice; rows and squared
+// copies land only at b_0 .. b_99).
 __device__ __forceinline__ void zero_margins_warp(uint32_t* __restrict__ s, unsigned lane) {
   for (int q = static_cast<int>(lane); q < 96; q += 32) s[kWjBz + q] = 0u;
   for (int q = kWjB0 + 97 + static_cast<int>(lane); q < kWjC; q += 32) s[q] = 0u;
