@@ -1,6 +1,6 @@
-"""CPU emulations of two GPU schedules, checked against the oracle.
+"""CPU emulations of GPU schedules, checked against the oracle.
 
-These tests replay, in numpy, the exact index arithmetic two kernels use, so
+These tests replay, in numpy, the exact index arithmetic the kernels use, so
 that a wrong offset, block order or fold step in the design fails on the CPU
 (the GPU parity tests then check the kernels themselves):
 
@@ -10,6 +10,9 @@ that a wrong offset, block order or fold step in the design fails on the CPU
   zero-padded copy of b, the fold in three blocks of distinct targets, and
   the application x P(A) (Sec. 3.1, the linear combination of the window)
   with lane l forming outputs 3l .. 3l+2;
+* the lane-pair jump: 16 x 16 tiles along descending anti-diagonals, the
+  pair's partial-sum exchange, the closed-form gather of the folded high
+  half, the ring application;
 * the tensor-core plan level: x' = x M mod 2^24 from balanced 8-bit limbs
   in fp16, with A = [A0 | A1 | A2 | 0] and B = [B2 | B1 | B0 | 0] along
   K = 320 (limb blocks of 104), D2 over all of K, D1 = A[0, 208) B[104, 312),
@@ -138,6 +141,146 @@ def test_warp_apply_schedule_matches_oracle(orc):
         got = warp_apply(x, p)
         assert np.array_equal(got, xe), e
         assert np.array_equal(got, orc.apply_dot(x, p)), e
+
+
+# --- lane-pair jump (two lanes per stream) ---------------------------------
+W32 = 1 << 32
+
+
+def gather_low(c, h, n):
+    """Coefficient n < 97 after folding the high half (h_j = c_{97+j}): the
+    closed form the pair kernel applies to a completed low block,
+    a_n = c_n + h_n - h_{n+33} + h_{n+66} - h_{n-64} + h_{n-31} - h_{n+2}
+    over the ranges in which each term exists."""
+    v = c
+    if n <= 95:
+        v += h(n)
+    if n <= 62:
+        v -= h(n + 33)
+    if n <= 29:
+        v += h(n + 66)
+    if n >= 64:
+        v += h(n - 31) - h(n - 64)
+        if n <= 93:
+            v -= h(n + 2)
+    return v
+
+
+def pair_product(a_in, b_in, square, shift):
+    """a b (or a^2 t^shift) mod phi in the pair kernel's order: anti-diagonals
+    s = I + J of 16 x 16 tiles walked from 10 down to 0, lane g taking rows
+    8g .. 8g+7 of each tile (off-diagonal tiles doubled when squaring), the
+    pair exchanging partial sums, each completed block written at once: high
+    blocks (with the rank-1 a_96 term) to a 128-word region, low blocks through
+    the closed-form gather straight into a."""
+    a = [int(v) for v in a_in] + [0] * 15
+    b = a if square else [int(v) for v in b_in] + [0] * 15
+    a96, b96 = a[96], b[96]
+    reg = [0] * 128                               # reg[k - 96] = c_k
+    reg[96] = (a96 * b96) % W32                   # c_192
+    out_a = list(a)
+
+    def h(j):
+        return reg[j + 1]
+
+    def complete(B, outs):
+        for g in range(2):
+            for jj in range(8):
+                k = 16 * B + 8 * g + jj
+                v = outs[g][jj]
+                if B >= 6 and k <= 191:
+                    i = k - 96
+                    v += 2 * a96 * a[i] if square else a96 * b[i] + b96 * a[i]
+                v %= W32
+                if B >= 6:
+                    reg[k - 96] = v
+                if B <= 6 and k <= 96:
+                    out_a[k + shift] = gather_low(v, h, k) % W32
+
+    pend = [[0] * 8, [0] * 8]
+    for s_ in range(10, -1, -1):
+        acc = [[0] * 23, [0] * 23]
+        ilo, ihi = max(0, s_ - 5), min(s_, 5)
+        for g in range(2):
+            tiles = [(I, s_ - I) for I in range(ilo, ihi + 1)]
+            if square:
+                off = [(I, J) for I, J in tiles if I < J]
+                for I, J in off:
+                    for p in range(8):
+                        for q in range(16):
+                            acc[g][p + q] += a[16 * I + 8 * g + p] * a[16 * J + q]
+                if off:
+                    acc[g] = [2 * v for v in acc[g]]
+                if s_ % 2 == 0:
+                    I = s_ // 2
+                    for p in range(8):
+                        for q in range(16):
+                            acc[g][p + q] += a[16 * I + 8 * g + p] * a[16 * I + q]
+            else:
+                for I, J in tiles:
+                    for p in range(8):
+                        for q in range(16):
+                            acc[g][p + q] += a[16 * I + 8 * g + p] * b[16 * J + q]
+        recv = [[acc[1][8 + j] for j in range(8)], [acc[0][8 + j] for j in range(8)]]
+        outs, newp = [[0] * 8, [0] * 8], [[0] * 8, [0] * 8]
+        for g in range(2):
+            for j in range(8):
+                outs[g][j] = pend[g][j] + (acc[g][16 + j] if j <= 6 else 0) + \
+                    (recv[g][j] if g == 0 else 0)
+                newp[g][j] = acc[g][j] + (recv[g][j] if g == 1 else 0)
+        pend = newp
+        complete(s_ + 1, outs)
+    complete(0, pend)
+    if shift:                                     # the word on t^97: 1 - t^64
+        top = out_a[97]
+        out_a[0] = top
+        out_a[64] -= top
+    return np.array([v % (1 << 24) for v in out_a[:R]], dtype=np.uint32)
+
+
+def pair_apply(p, x):
+    """x P(A) in the pair kernel's order: the window through a 128-word ring,
+    output blocks of 16 as six 16 x 16 tiles plus the a_96 column, 32 new
+    window words per round, output 96 as a plain dot product."""
+    p = [int(v) for v in p] + [0] * 15
+    ring = [0] * 128
+    for q in range(R):
+        ring[q] = int(x[q])
+    for q in range(R, 128):
+        ring[q] = (ring[q - R] - ring[q - S]) % W32
+    out = [0] * R
+    for m in range(3):
+        for g in range(2):
+            K = 2 * m + g
+            acc = [0] * 16
+            for I in range(6):
+                for q in range(16):
+                    for r in range(16):
+                        acc[r] += p[16 * I + q] * ring[(16 * (I + K) + q + r) % 128]
+            for r in range(16):
+                acc[r] += p[96] * ring[(96 + 16 * K + r) % 128]
+                out[16 * K + r] = acc[r] % (1 << 24)
+        if m < 2:
+            for q in range(32 * m + 128, 32 * m + 160):
+                ring[q % 128] = (ring[(q - R) % 128] - ring[(q - S) % 128]) % W32
+    x192 = (ring[(192 - R) % 128] - ring[(192 - S) % 128]) % W32
+    out[96] = (sum(p[i] * ring[(96 + i) % 128] for i in range(96)) + p[96] * x192) % (1 << 24)
+    return np.array(out, dtype=np.uint32)
+
+
+def test_pair_schedule_matches_oracle(orc):
+    rng = np.random.default_rng(11)
+    t = np.zeros(R, np.uint32)
+    t[1] = 1
+    for _ in range(3):
+        a = rng.integers(0, 1 << 24, R).astype(np.uint32)
+        b = rng.integers(0, 1 << 24, R).astype(np.uint32)
+        sq = orc.poly_mulmod(a, a)
+        assert np.array_equal(pair_product(a, None, True, 0), sq)
+        assert np.array_equal(pair_product(a, None, True, 1), orc.poly_mulmod(sq, t))
+        assert np.array_equal(pair_product(a, b, False, 0), orc.poly_mulmod(a, b))
+        x = rng.integers(0, 1 << 24, R).astype(np.uint32)
+        assert np.array_equal(pair_apply(a, x), orc.apply_dot(x, a))
 
 
 # --- tensor-core plan level ------------------------------------------------
