@@ -49,7 +49,9 @@ class Request:
     f32: bool
     offset: int = -1        # outputs of this stream taken by earlier arrivals
     done: float = -1.0      # completion time (GPU clock, seconds from start)
+    host_done: float = -1.0  # when the host saw the completion (host clock, same origin)
     checksum: int = -1      # device checksum of the outputs
+    rejected: bool = False  # larger than the engine could ever hold: refused on arrival
 
     @property
     def key(self):
@@ -205,6 +207,7 @@ class Engine:
         self.out = torch.empty(out_words, dtype=torch.int32, device=self.dev)
         self.outf = self.out.view(torch.float32)
         self.alloc = FirstFit(out_words)
+        self.state_entries = state_entries
         self.free_entries = list(range(state_entries - 1, -1, -1))
         self.resident: collections.OrderedDict = collections.OrderedDict()  # key -> (entry, end)
         self.base = torch.empty((max_seeds, bd.STATE_WORDS), dtype=torch.int32, device=self.dev)
@@ -227,6 +230,14 @@ class Engine:
     def _nseg(self, r: Request) -> int:
         return max(1, (r.count + self.seg - 1) // self.seg)
 
+    def fits_ever(self, r: Request) -> bool:
+        """Whether `r` fits the engine when nothing else is held: its output
+        region in the output pool and its segments' states in the state pool.
+        A request that does not is refused when it reaches the queue head
+        instead of blocking every request behind it."""
+        need = max(self.alloc.align, -(-max(1, r.count) // self.alloc.align) * self.alloc.align)
+        return need <= self.alloc.size and self._nseg(r) <= self.state_entries
+
     def _take_entries(self, n: int):
         while len(self.free_entries) < n and self.resident:
             _, (e, _) = self.resident.popitem(last=False)      # evict least recently used
@@ -241,6 +252,11 @@ class Engine:
         nsegs = 0
         while waiting:
             r = waiting[0]
+            if not self.fits_ever(r):
+                waiting.popleft()
+                r.rejected = True
+                self.stats["rejected"] += 1
+                continue
             ns = self._nseg(r)
             if out and nsegs + ns > self.max_segs:
                 break
@@ -418,10 +434,12 @@ class Engine:
     def _retire(self, it: dict) -> None:
         it["event"].synchronize()
         done = it["t0"].elapsed_time(it["event"]) * 1e-3
+        host_done = time.perf_counter() - self._h0
         lo_s, hi_s = it["slots"]
         host = self.results_host[lo_s:hi_s].numpy().view(np.uint64)
         for r in it["reqs"]:
             r.done = done
+            r.host_done = host_done
             r.checksum = int(host[r._slot - lo_s])
             self.alloc.free(*r._region)
             ents = r._ents
@@ -460,6 +478,7 @@ class Engine:
         t0 = torch.cuda.Event(enable_timing=True)
         t0.record(self.stream)
         h0 = time.perf_counter()
+        self._h0 = h0
         n = len(reqs)
         t_prev = time.perf_counter()
         max_loop = 0.0
@@ -504,6 +523,7 @@ class Engine:
         t0 = torch.cuda.Event(enable_timing=True)
         t0.record(self.stream)
         h0 = time.perf_counter()
+        self._h0 = h0
         s = self.stream
         st_d = torch.empty((1, bd.STATE_WORDS), dtype=torch.int32, device=self.dev)
         one = torch.zeros(1, dtype=torch.int32, device=self.dev)
@@ -515,6 +535,9 @@ class Engine:
                     time.sleep(wait)
             if time.perf_counter() - h0 > max_wait:
                 raise RuntimeError("plain run exceeded its time limit")
+            if not self.fits_ever(r):
+                r.rejected = True
+                continue
             self._seed_rows([r])
             region = self.alloc.alloc(max(1, r.count))
             while region is None and pending:
@@ -546,6 +569,7 @@ class Engine:
         r, ev = item
         ev.synchronize()
         r.done = t0.elapsed_time(ev) * 1e-3
+        r.host_done = time.perf_counter() - self._h0
         r.checksum = int(np.int64(self.results[r._slot].item()).astype(np.uint64))
         self.alloc.free(*r._region)
 
@@ -556,12 +580,21 @@ class Engine:
 
 
 def summarize(reqs) -> dict:
-    lat = np.array([r.done - r.t for r in reqs if r.done >= 0])
-    outs = sum(r.count for r in reqs)
-    span = max(r.done for r in reqs) - min(r.t for r in reqs) if reqs else 0.0
-    return {"requests": len(reqs), "outputs": outs,
-            "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
-            "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
+    """Latency percentiles over the served requests.  `p50_ms`/`p99_ms`: the
+    GPU event that ends the request's iteration minus its arrival (the device
+    is done; the host has not looked yet).  `host_p50_ms`/`host_p99_ms`: the
+    moment the host's scheduler loop saw that event complete, minus arrival
+    (what a caller polling the engine observes)."""
+    served = [r for r in reqs if r.done >= 0 and not r.rejected]
+    lat = np.array([r.done - r.t for r in served])
+    hlat = np.array([r.host_done - r.t for r in served if r.host_done >= 0])
+    outs = sum(r.count for r in served)
+    span = max(r.done for r in served) - min(r.t for r in served) if served else 0.0
+    pct = lambda a, q: float(np.percentile(a, q) * 1e3) if a.size else None
+    return {"requests": len(reqs), "served": len(served),
+            "rejected": sum(1 for r in reqs if r.rejected), "outputs": outs,
+            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
             "mean_ms": float(lat.mean() * 1e3) if lat.size else None,
+            "host_p50_ms": pct(hlat, 50), "host_p99_ms": pct(hlat, 99),
             "span_s": span, "outputs_per_s": outs / span if span > 0 else None,
             "overlapping_requests": sum(1 for r in reqs if r.overlaps)}

@@ -1,5 +1,7 @@
 """Host-side logic of the serving engine (no GPU): resume offsets, exponent
-rows, the output allocator, and the request recipe."""
+rows, the output allocator, admission, and the request recipe."""
+import collections
+
 import numpy as np
 
 from paper_2512_00093_gb300 import serve
@@ -67,3 +69,35 @@ def test_overlap_flag_in_summary():
     for r in reqs:
         r.done = r.t + 0.001
     assert serve.summarize(reqs)["overlapping_requests"] == 2
+
+
+def _bare_engine(out_words, state_entries, seg):
+    """An Engine with only its host-side admission state (no device memory)."""
+    eng = serve.Engine.__new__(serve.Engine)
+    eng.seg, eng.max_segs = seg, 1000
+    eng.alloc = FirstFit(out_words)
+    eng.state_entries = state_entries
+    eng.free_entries = list(range(state_entries - 1, -1, -1))
+    eng.resident = collections.OrderedDict()
+    eng.stats = collections.Counter()
+    return eng
+
+
+def test_admit_refuses_requests_that_can_never_fit():
+    """A request larger than the output pool, or with more segments than the
+    state pool has entries, is refused when it reaches the head of the queue;
+    the requests behind it are admitted instead of waiting behind it."""
+    eng = _bare_engine(out_words=1024, state_entries=4, seg=16)
+    reqs = serve.make_requests(np.array([0.0, 0.1, 0.2, 0.3]), np.array([1, 2, 3, 4]),
+                               np.array([0, 0, 0, 0]), np.array([2000, 100, 30, 64]),
+                               np.array([False] * 4), 1 << 48)
+    waiting = collections.deque(reqs)
+    got = eng.admit(waiting)
+    # 2000 > 1024 output words; 100 outputs = 7 segments > 4 state entries
+    assert [r.rid for r in got] == [2] and [r.rejected for r in reqs] == [True, True, False, False]
+    assert eng.stats["rejected"] == 2
+    assert [r.rid for r in waiting] == [3]          # 64 outputs = 4 segments: waits for entries
+    for r in reqs[2:]:
+        r.done = r.host_done = r.t + 0.001
+    s = serve.summarize(reqs)
+    assert (s["requests"], s["served"], s["rejected"]) == (4, 2, 2)
