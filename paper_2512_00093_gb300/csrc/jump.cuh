@@ -1,14 +1,11 @@
-// jump.cuh -- batched jump-ahead (Sec. 3.1, Sec. 3.2).
+// jump.cuh -- building blocks of the jump-ahead (Sec. 3.1, Sec. 3.2), a
+// lane pair per stream (lanes L and L + 16 of the warp, 16 streams per
+// warp): the exponent arithmetic, the general product a b mod phi(t) of two
+// polynomials (phi = t^97 + t^64 - 1 over Z/2^24), and the application of a
+// jump polynomial to a state.  The squaring of the paper's square-and-
+// multiply and its kernels are in square_mirror.cuh.
 //
-// For each stream: P_E(t) = t^E mod phi(t), phi = t^97 + t^64 - 1 over
-// Z/2^24, by left-to-right square-and-multiply (a 1 bit multiplies by t: a
-// shift plus the fold t^97 = 1 - t^64); then the new state word k =
-// sum_i b_i x_{i+k+1} (x extended by the recurrence), which is the Horner
-// form u P_E(A) of Sec. 3.1; then c_E = (c - E d) mod m (Sec. 3.2).
-//
-// Mapping: TWO lanes per stream (lanes L and L + 16 of the warp), 16 streams
-// per warp, one warp per CTA.  Every pair runs the same instruction stream on
-// its own polynomial.  A polynomial is held as six 16-coefficient blocks
+// General product: a polynomial is held as six 16-coefficient blocks
 // (coefficients 0..95) plus coefficient 96 alone:
 //     a = a' + a_96 t^96,  a b = a'b' + t^96 (a_96 b' + b_96 a') + a_96 b_96 t^192,
 // so the 97x97 product is 6x6 register-blocked 16x16 tiles of 32-bit
@@ -18,11 +15,10 @@
 // columns (128 multiply-adds into 23 accumulators).
 //
 // In place, anti-diagonal by anti-diagonal: tiles (I, J) with I + J = s
-// produce the outputs 16s .. 16s+30; s walks DOWN from 10 to 0 (squaring:
-// tiles I < J summed and doubled, then the diagonal tile I = J added as a
-// full product).  After anti-diagonal s the product block s+1 (coefficients
-// 16s+16 .. 16s+31) is complete, and block s+1 of `a` is no longer read
-// (anti-diagonals <= s use blocks <= s), so:
+// produce the outputs 16s .. 16s+30; s walks DOWN from 10 to 0.  After
+// anti-diagonal s the product block s+1 (coefficients 16s+16 .. 16s+31) is
+// complete, and block s+1 of `a` is no longer read (anti-diagonals <= s use
+// blocks <= s), so:
 //   * blocks >= 6 (degree >= 96) get the rank-1 correction and go to a
 //     128-word region R (R[k-96] = c_k; R[96] = c_192 = a_96 b_96);
 //   * blocks <= 5 and coefficient 96 are reduced at once and written into
@@ -32,25 +28,22 @@
 //     with h_j = c_{97+j} (t^k = t^{k-97} - t^{k-33} applied until the
 //     degree is below 97; every high block is complete before the first low
 //     one, because s walks down).
-// A multiplication by t shifts the written index by one; the word that lands
-// on t^97 is folded back at the end.  After each anti-diagonal the pair
-// swaps 8 partial sums by shuffle.
+// After each anti-diagonal the pair swaps 8 partial sums by shuffle.
 //
 // Application: the extended window X(0..192) is consumed through the same
 // 128-word region used as a ring (window X(16K .. 16K+111) for output block
 // K, 32 new words per round computed by the recurrence).
 //
-// Shared memory per stream: a (100 words: blocks, coefficient 96, the t^97
-// word of a shifted square, padding) + R (128 words); stride 228 = 4 mod 32,
-// so that the 16-byte loads of a quarter warp (8 streams, same half) fall in
-// 8 distinct bank groups.  14,592 B per CTA.
+// Shared memory per stream: a (100 words: blocks, coefficient 96, padding)
+// + R (128 words); stride 228 = 4 mod 32, so that the 16-byte loads of a
+// quarter warp (8 streams, same half) fall in 8 distinct bank groups.
 #pragma once
 
 #include "ranmar_device.cuh"
 
 namespace ranmar {
 
-constexpr int kPolyWords = 100;    // 6 x 16 coefficients, a_96, t^97 word, 2 pad
+constexpr int kPolyWords = 100;    // 6 x 16 coefficients, a_96, 3 pad
 constexpr int kRingWords = 128;    // high product words / application ring
 constexpr int kStreamWords = 228;  // per-stream slice stride (4 mod 32)
 constexpr int kJumpStreamsPerWarp = 16;
@@ -136,11 +129,11 @@ __device__ __forceinline__ void add_term(uint32_t (&v)[8], const uint32_t* __res
 }
 
 // Reduces the lane's 8 coefficients of the completed low product block kB
-// (n = 16 kB + 8g + j) and writes them to a[n + shift].
+// (n = 16 kB + 8g + j) and writes them to a[n].
 template <int kB>
 __device__ __forceinline__ void reduce_low(uint32_t* __restrict__ a,
                                            const uint32_t* __restrict__ R, unsigned g,
-                                           uint32_t (&v)[8], uint32_t shift) {
+                                           uint32_t (&v)[8]) {
   const uint32_t* Rg = R + 8 * g;
   add_term<kB, 0, 0, 95, true>(v, Rg, g);
   add_term<kB, 33, 0, 62, false>(v, Rg, g);
@@ -148,37 +141,34 @@ __device__ __forceinline__ void reduce_low(uint32_t* __restrict__ a,
   add_term<kB, -64, 64, 96, false>(v, Rg, g);
   add_term<kB, -31, 64, 96, true>(v, Rg, g);
   add_term<kB, 2, 64, 93, false>(v, Rg, g);
-  uint32_t* dst = a + 16 * kB + 8 * g + shift;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) dst[j] = v[j];
+  uint32_t* dst = a + 16 * kB + 8 * g;
+  st4(dst, v[0], v[1], v[2], v[3]);
+  st4(dst + 4, v[4], v[5], v[6], v[7]);
 }
 
 __device__ __forceinline__ void reduce_low_dispatch(int B, uint32_t* __restrict__ a,
                                                     const uint32_t* __restrict__ R, unsigned g,
-                                                    uint32_t (&v)[8], uint32_t shift) {
+                                                    uint32_t (&v)[8]) {
   switch (B) {
-    case 0: reduce_low<0>(a, R, g, v, shift); break;
-    case 1: reduce_low<1>(a, R, g, v, shift); break;
-    case 2: reduce_low<2>(a, R, g, v, shift); break;
-    case 3: reduce_low<3>(a, R, g, v, shift); break;
-    case 4: reduce_low<4>(a, R, g, v, shift); break;
-    default: reduce_low<5>(a, R, g, v, shift); break;
+    case 0: reduce_low<0>(a, R, g, v); break;
+    case 1: reduce_low<1>(a, R, g, v); break;
+    case 2: reduce_low<2>(a, R, g, v); break;
+    case 3: reduce_low<3>(a, R, g, v); break;
+    case 4: reduce_low<4>(a, R, g, v); break;
+    default: reduce_low<5>(a, R, g, v); break;
   }
 }
 
-// In place, with the lanes g = 0, 1 of the pair cooperating:
-//   kSquare:  a = a^2 t^shift mod phi          (b unused)
-//   !kSquare: a = a b mod phi (shift must be 0; b is not modified)
-// `mask` holds the lanes taking part (both lanes of every participating pair).
-template <bool kSquare>
+// a = a b mod phi in place (b is not modified), with the lanes g = 0, 1 of
+// the pair cooperating.  `mask` holds the lanes taking part (both lanes of
+// every participating pair).
 __device__ __forceinline__ void product_reduce_pair(uint32_t* __restrict__ a,
                                                     const uint32_t* __restrict__ b,
-                                                    uint32_t* __restrict__ R, uint32_t shift,
-                                                    unsigned g, unsigned mask) {
+                                                    uint32_t* __restrict__ R, unsigned g,
+                                                    unsigned mask) {
   const uint32_t* arow = a + 8 * g;
-  const uint32_t* bcol = kSquare ? a : b;
   const uint32_t a96 = a[96];
-  const uint32_t b96 = kSquare ? a96 : b[96];
+  const uint32_t b96 = b[96];
   if (g == 0) R[96] = a96 * b96;  // c_192
   uint32_t pend[8];  // low half of the previous anti-diagonal
 #pragma unroll
@@ -189,30 +179,22 @@ __device__ __forceinline__ void product_reduce_pair(uint32_t* __restrict__ a,
 #pragma unroll
     for (int r = 0; r < 23; ++r) acc[r] = 0;
     const int ilo = s > 5 ? s - 5 : 0;
-    // squaring: off-diagonal tiles I < J, i.e. I in [ilo, iend); general: all I
-    const int iend = kSquare ? (s + 1) >> 1 : (s < 5 ? s : 5) + 1;
-    if (ilo < iend) {
-      Oct r0 = lds8(arow + 16 * ilo), r1;
-      Hex c0 = lds16(bcol + 16 * (s - ilo)), c1;
-      int I = ilo;
+    const int iend = (s < 5 ? s : 5) + 1;
+    Oct r0 = lds8(arow + 16 * ilo), r1;
+    Hex c0 = lds16(b + 16 * (s - ilo)), c1;
+    int I = ilo;
 #pragma unroll 1
-      for (; I + 1 < iend; I += 2) {  // operands one tile ahead, ping-pong
-        r1 = lds8(arow + 16 * (I + 1));
-        c1 = lds16(bcol + 16 * (s - I - 1));
-        tile_mac(acc, r0, c0);
-        if (I + 2 < iend) {
-          r0 = lds8(arow + 16 * (I + 2));
-          c0 = lds16(bcol + 16 * (s - I - 2));
-        }
-        tile_mac(acc, r1, c1);
+    for (; I + 1 < iend; I += 2) {  // operands one tile ahead, ping-pong
+      r1 = lds8(arow + 16 * (I + 1));
+      c1 = lds16(b + 16 * (s - I - 1));
+      tile_mac(acc, r0, c0);
+      if (I + 2 < iend) {
+        r0 = lds8(arow + 16 * (I + 2));
+        c0 = lds16(b + 16 * (s - I - 2));
       }
-      if (I < iend) tile_mac(acc, r0, c0);
-      if (kSquare) {
-#pragma unroll
-        for (int k = 0; k < 23; ++k) acc[k] += acc[k];
-      }
+      tile_mac(acc, r1, c1);
     }
-    if (kSquare && (s & 1) == 0) tile_mac(acc, lds8(arow + 8 * s), lds16(a + 8 * s));
+    if (I < iend) tile_mac(acc, r0, c0);
 
     // Lane g holds outputs 16s + 8g + r, r < 23.  Block s+1 (16s+16 ..
     // 16s+31): lane 0 takes 16..23 (its own 16..22 and lane 1's 16..23),
@@ -232,39 +214,20 @@ __device__ __forceinline__ void product_reduce_pair(uint32_t* __restrict__ a,
       // rank-1 part: c_k += a_96 b_{k-96} + b_96 a_{k-96}, k = 16B + 8g + j
       const int i0 = 16 * (B - 6) + 8 * static_cast<int>(g);
       const Oct x = lds8(a + i0);
-      if (kSquare) {
-        const uint32_t a2 = a96 + a96;
+      const Oct y = lds8(b + i0);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) out[j] += a2 * x.v[j];
-      } else {
-        const Oct y = lds8(b + i0);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) out[j] += a96 * y.v[j] + b96 * x.v[j];
-      }
+      for (int j = 0; j < 8; ++j) out[j] += a96 * y.v[j] + b96 * x.v[j];
       st4(R + i0, out[0], out[1], out[2], out[3]);
       st4(R + i0 + 4, out[4], out[5], out[6], out[7]);
       // coefficient 96: c_96 + h_65 - h_32 (h_j = c_{97+j} = R[j+1])
-      if (B == 6 && g == 0) a[96 + shift] = out[0] + R[66] - R[33];
+      if (B == 6 && g == 0) a[96] = out[0] + R[66] - R[33];
     } else {
-      reduce_low_dispatch(B, a, R, g, out, shift);
+      reduce_low_dispatch(B, a, R, g, out);
     }
     __syncwarp(mask);
   }
-  reduce_low<0>(a, R, g, pend, shift);
+  reduce_low<0>(a, R, g, pend);
   __syncwarp(mask);
-  if (kSquare && shift && g == 0) {  // fold t^97 = 1 - t^64
-    const uint32_t top = a[kR];
-    a[0] = top;
-    a[64] -= top;
-    a[kR] = 0;
-  }
-  __syncwarp(mask);
-}
-
-__device__ __forceinline__ void square_reduce_pair(uint32_t* __restrict__ a,
-                                                   uint32_t* __restrict__ R, uint32_t shift,
-                                                   unsigned g) {
-  product_reduce_pair<true>(a, a, R, shift, g, kFull);
 }
 
 __device__ __forceinline__ uint32_t exp_word(const uint32_t (&E)[kMaxExpWords], int w) {
@@ -343,39 +306,6 @@ __device__ __forceinline__ void reduce_period(uint32_t (&E)[kMaxExpWords]) {
       E[0] >= 0xFF800000u) {  // T <= E < 2^120
     E[0] -= 0xFF800000u;
     E[1] = E[2] = E[3] = 0;
-  }
-}
-
-// a = t^E mod phi for the stream of this lane pair by left-to-right
-// square-and-multiply; all 32 lanes of the warp call it together (the bit
-// loop is warp-uniform: it runs over the longest exponent of the warp).
-__device__ __forceinline__ void poly_power_pair(const uint32_t (&E)[kMaxExpWords], bool active,
-                                                uint32_t* __restrict__ a,
-                                                uint32_t* __restrict__ R, unsigned g) {
-  const int nb = active ? exp_bitlen(E) : 0;
-  const int L = static_cast<int>(__reduce_max_sync(kFull, static_cast<unsigned>(nb)));
-
-  // Leading (up to) six bits: P = t^v0 with v0 < 64 < 97 is a monomial.
-  uint32_t v0;
-  int p;
-  if (L <= 6) {
-    v0 = E[0] & 63u;
-    p = -1;
-  } else {
-    v0 = exp_bits6(E, L - 6);
-    p = L - 7;
-  }
-  if (!active) v0 = 0;
-  for (int q = static_cast<int>(g); q < kPolyWords / 4; q += 2)
-    reinterpret_cast<uint4*>(a)[q] = make_uint4(0u, 0u, 0u, 0u);
-  __syncwarp();
-  if (g == 0) a[v0] = 1u;
-  __syncwarp();
-
-#pragma unroll 1
-  for (; p >= 0; --p) {
-    const uint32_t bit = active ? exp_bit(E, p) : 0u;
-    square_reduce_pair(a, R, bit, g);
   }
 }
 
@@ -477,19 +407,6 @@ __device__ __forceinline__ void apply_pair(const ranmar_state_t* __restrict__ ba
   }
 }
 
-// dst = f^E(base) for the stream of this lane pair.
-// Ep is the exponent of the polynomial part (E itself, or E mod T), E the
-// full exponent (for c and pos).
-__device__ __forceinline__ void jump_pair(const ranmar_state_t* __restrict__ base,
-                                          const uint32_t (&Ep)[kMaxExpWords],
-                                          const uint32_t (&E)[kMaxExpWords], bool active,
-                                          ranmar_state_t* __restrict__ dst,
-                                          uint32_t* __restrict__ a, uint32_t* __restrict__ R,
-                                          unsigned g) {
-  poly_power_pair(Ep, active, a, R, g);
-  apply_pair(base, E, active, dst, a, R, g);
-}
-
 // Exponent of stream i: mode 0 reads it from d_exp, mode 1 forms (k0 + i) J.
 __device__ __forceinline__ void load_exponent(uint32_t (&E)[kMaxExpWords], int mode,
                                               const uint32_t* __restrict__ d_exp,
@@ -506,77 +423,6 @@ __device__ __forceinline__ void load_exponent(uint32_t (&E)[kMaxExpWords], int m
     const uint64_t k = part.k0 + i;
     exp_mul_add(E, part.J, static_cast<uint32_t>(k), 0);
     exp_mul_add(E, part.J, static_cast<uint32_t>(k >> 32), 1);
-  }
-}
-
-// mode 0: E_i from d_exp (exp_words per stream), base d_base[base_idx[i]].
-// mode 1: E_i = (k0 + i) * J, base d_base[0].
-// d_dst_idx (mode 0 only, may be null): stream i is written to
-// d_out[d_dst_idx[i]] (index < n_dst) instead of d_out[i].
-__global__ void __launch_bounds__(32, 12) jump_kernel(
-    const ranmar_state_t* __restrict__ d_base, uint64_t n_base,
-    const uint32_t* __restrict__ d_base_idx, const uint32_t* __restrict__ d_exp,
-    uint32_t exp_words, ExpParams part, int mode, ranmar_state_t* __restrict__ d_out,
-    uint64_t n, uint32_t* status, const uint32_t* __restrict__ d_dst_idx, uint64_t n_dst) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  const unsigned lane = threadIdx.x & 31;
-  const unsigned g = lane >> 4;
-  const unsigned slot = lane & 15;
-  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * kJumpStreamsPerWarp + slot;
-  uint32_t* a = smem + slot * kStreamWords;
-  uint32_t* R = a + kPolyWords;
-
-  bool active = i < n;
-  uint32_t E[kMaxExpWords];
-  load_exponent(E, active ? mode : 0, d_exp, active ? exp_words : 0, part, i);
-  const ranmar_state_t* base = d_base;
-  if (active && mode == 0) {
-    const uint32_t bi = d_base_idx ? d_base_idx[i] : 0u;
-    if (bi >= n_base) {
-      if (g == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
-      active = false;
-    } else {
-      base = d_base + bi;
-    }
-  }
-  uint64_t di = i;
-  if (active && d_dst_idx) {
-    di = d_dst_idx[i];
-    if (di >= n_dst) {
-      if (g == 0) flag_status(status, RANMAR_ST_BAD_INDEX);
-      active = false;
-    }
-  }
-  uint32_t Ep[kMaxExpWords];
-#pragma unroll
-  for (int w = 0; w < kMaxExpWords; ++w) Ep[w] = E[w];
-  if (part.flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
-  jump_pair(base, Ep, E, active, d_out + (active ? di : 0), a, R, g);
-}
-
-// P_{E_i} = t^{E_i} mod phi alone (the polynomial part of a jump, Sec. 3.1),
-// by the same square-and-multiply: d_poly[i] = coefficients 0..96 (24-bit),
-// then three zero words.
-__global__ void __launch_bounds__(32, 12) poly_power_kernel(const uint32_t* __restrict__ d_exp,
-                                                            uint32_t exp_words,
-                                                            uint32_t* __restrict__ d_poly,
-                                                            uint64_t n) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  const unsigned lane = threadIdx.x & 31;
-  const unsigned g = lane >> 4;
-  const unsigned slot = lane & 15;
-  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * kJumpStreamsPerWarp + slot;
-  uint32_t* a = smem + slot * kStreamWords;
-  uint32_t* R = a + kPolyWords;
-  const bool active = i < n;
-  uint32_t E[kMaxExpWords];
-  const ExpParams part{};
-  load_exponent(E, 0, d_exp, active ? exp_words : 0, part, active ? i : 0);
-  poly_power_pair(E, active, a, R, g);
-  __syncwarp();
-  if (active) {
-    uint32_t* dst = d_poly + i * kPolyWords;
-    for (int q = static_cast<int>(g); q < kPolyWords; q += 2) dst[q] = q < kR ? (a[q] & kMask24) : 0u;
   }
 }
 

@@ -13,7 +13,7 @@
 // 160-bit E.  The result P_E is the same polynomial the left-to-right
 // square-and-multiply gives (it is unique), so the jumped states are
 // bit-identical.  The table rows themselves are built by that
-// square-and-multiply (poly_power_pair), with the exponent d 2^{8j}.
+// square-and-multiply (poly_power_mirror), with the exponent d 2^{8j}.
 //
 // For the streams of one partition (E = kJ) a second table, of the powers of
 // t^J (rows t^{d 2^{8j} J}, built from the first), lets the product run over
@@ -21,7 +21,7 @@
 // jump_jtable_kernel).
 #pragma once
 
-#include "jump.cuh"
+#include "square_mirror.cuh"
 
 namespace ranmar {
 
@@ -52,8 +52,7 @@ __global__ void __launch_bounds__(32) table_build_kernel(uint32_t* __restrict__ 
   const unsigned g = lane >> 4, slot = lane & 15;
   const int row = blockIdx.x * kJumpStreamsPerWarp + static_cast<int>(slot);
   const bool active = row < kTabRows;
-  uint32_t* a = smem + slot * kStreamWords;
-  uint32_t* R = a + kPolyWords;
+  uint32_t* slice = smem + slot * kMirStreamWords;
   uint32_t E[kMaxExpWords];
 #pragma unroll
   for (int w = 0; w < kMaxExpWords; ++w) E[w] = 0;
@@ -65,9 +64,10 @@ __global__ void __launch_bounds__(32) table_build_kernel(uint32_t* __restrict__ 
     E[w0] = static_cast<uint32_t>(v);
     if (w0 + 1 < kMaxExpWords) E[w0 + 1] = static_cast<uint32_t>(v >> 32);
   }
-  poly_power_pair(E, active, a, R, g);
+  poly_power_mirror(E, active, slice, g);
   if (active) {
     uint32_t* dst = table + static_cast<size_t>(row) * kTabRowWords;
+    const uint32_t* a = slice + kMirA;
     for (int q = static_cast<int>(g); q < kTabRowWords; q += 2) dst[q] = q < kR ? (a[q] & kMask24) : 0u;
   }
 }
@@ -113,7 +113,7 @@ __device__ __forceinline__ void table_poly_pair(const uint32_t* __restrict__ tab
     if (mul) copy_row(b, row, g);
     const unsigned mmask = __ballot_sync(kFull, mul);
     __syncwarp();
-    if (mul) product_reduce_pair<false>(a, b, R, 0u, g, mmask);
+    if (mul) product_reduce_pair(a, b, R, g, mmask);
     __syncwarp();
     have = have || d != 0;
   }

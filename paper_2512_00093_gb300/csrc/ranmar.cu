@@ -16,6 +16,7 @@
 #include "ranmar_device.cuh"
 #include "generate.cuh"
 #include "jump.cuh"
+#include "square_mirror.cuh"
 #include "batch.cuh"
 #include "jump_table.cuh"
 #include "jump_warp.cuh"
@@ -250,7 +251,7 @@ int launch_jump(const ranmar_state_t* base, size_t n_base, const uint32_t* base_
   const uint64_t per_cta = ranmar::kJumpStreamsPerWarp;   // one warp per CTA
   const uint64_t blocks = (n + per_cta - 1) / per_cta;
   if (blocks > 0x7FFFFFFFull) return RANMAR_ERANGE;
-  ranmar::jump_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kJumpSmemBytes, s>>>(
+  ranmar::jump_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kMirSmemBytes, s>>>(
       base, n_base, base_idx, exp, exp_words, part, mode, out, n, status, dst_idx, n_dst);
   return check_launch();
 }
@@ -348,6 +349,9 @@ int batch_generate(ranmar_batch* b, bool f32, ranmar_state_t* states, size_t n_s
 // Device address of g_pack_static on the current device.  In host code the
 // symbol is only a host-side stand-in, so the address is looked up once per
 // device with cudaGetSymbolAddress (with that device current) and cached.
+// The cache is not invalidated by cudaDeviceReset (which unloads the module),
+// so a process that resets a device must not call the static pack on it
+// afterwards.
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 unsigned char* g_static_addr[kMaxDevices] = {};
@@ -568,7 +572,7 @@ int ranmar_poly_power(const uint32_t* d_exp, uint32_t exp_words, size_t n, uint3
   }
   const uint64_t blocks = (n + ranmar::kJumpStreamsPerWarp - 1) / ranmar::kJumpStreamsPerWarp;
   if (blocks > 0x7FFFFFFFull) return RANMAR_ERANGE;
-  ranmar::poly_power_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kJumpSmemBytes,
+  ranmar::poly_power_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kMirSmemBytes,
                               reinterpret_cast<cudaStream_t>(stream)>>>(d_exp, exp_words, d_poly,
                                                                         n);
   return check_launch();
@@ -865,6 +869,7 @@ int ranmar_graph_destroy(ranmar_graph_t* g) {
 int ranmar_batch_pack_static(const uint64_t* d_counts, size_t n, uint32_t flags,
                              ranmar_desc_t* d_desc, uint32_t* d_order, uint64_t* d_total,
                              ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_batch_pack_static");
   if (n > RANMAR_PACK_STATIC_MAX) return RANMAR_ERANGE;
   if (n > 0 && (!d_counts || !d_desc)) return RANMAR_EINVAL;
   if (!aligned(d_counts, 8) || !aligned(d_desc, 8) || !aligned(d_order, 4) ||
@@ -950,7 +955,7 @@ int ranmar_table_create(ranmar_table_t** out) {
   if (e == cudaSuccess) {
     const unsigned blocks = (ranmar::kTabRows + ranmar::kJumpStreamsPerWarp - 1) /
                             ranmar::kJumpStreamsPerWarp;
-    ranmar::table_build_kernel<<<blocks, 32, ranmar::kJumpSmemBytes, s>>>(t->rows);
+    ranmar::table_build_kernel<<<blocks, 32, ranmar::kMirSmemBytes, s>>>(t->rows);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaStreamDestroy(s);

@@ -10,9 +10,13 @@ that a wrong offset, block order or fold step in the design fails on the CPU
   zero-padded copy of b, the fold in three blocks of distinct targets, and
   the application x P(A) (Sec. 3.1, the linear combination of the window)
   with lane l forming outputs 3l .. 3l+2;
-* the lane-pair jump: 16 x 16 tiles along descending anti-diagonals, the
-  pair's partial-sum exchange, the closed-form gather of the folded high
-  half, the ring application;
+* the lane-pair general product (table jump): 16 x 16 tiles along
+  descending anti-diagonals, the pair's partial-sum exchange, the
+  closed-form gather of the folded high half, and the ring application;
+* the mirrored lane-pair square of the square-and-multiply: lane 0 forms
+  the low half of x^2 from x, lane 1 the high half from x reversed (the
+  same instructions), output-stationary over symmetric block triangles,
+  then the gather, the shift by t on a 1 bit and both copies written;
 * the tensor-core plan level: x' = x M mod 2^24 from balanced 8-bit limbs
   in fp16, with A = [A0 | A1 | A2 | 0] and B = [B2 | B1 | B0 | 0] along
   K = 320 (limb blocks of 104), D2 over all of K, D1 = A[0, 208) B[104, 312),
@@ -166,15 +170,15 @@ def gather_low(c, h, n):
     return v
 
 
-def pair_product(a_in, b_in, square, shift):
-    """a b (or a^2 t^shift) mod phi in the pair kernel's order: anti-diagonals
-    s = I + J of 16 x 16 tiles walked from 10 down to 0, lane g taking rows
-    8g .. 8g+7 of each tile (off-diagonal tiles doubled when squaring), the
-    pair exchanging partial sums, each completed block written at once: high
-    blocks (with the rank-1 a_96 term) to a 128-word region, low blocks through
-    the closed-form gather straight into a."""
+def pair_product(a_in, b_in):
+    """a b mod phi in the pair kernel's order (the general product of the
+    table jump): anti-diagonals s = I + J of 16 x 16 tiles walked from 10
+    down to 0, lane g taking rows 8g .. 8g+7 of each tile, the pair
+    exchanging partial sums, each completed block written at once: high
+    blocks (with the rank-1 a_96 term) to a 128-word region, low blocks
+    through the closed-form gather straight into a."""
     a = [int(v) for v in a_in] + [0] * 15
-    b = a if square else [int(v) for v in b_in] + [0] * 15
+    b = [int(v) for v in b_in] + [0] * 15
     a96, b96 = a[96], b[96]
     reg = [0] * 128                               # reg[k - 96] = c_k
     reg[96] = (a96 * b96) % W32                   # c_192
@@ -190,37 +194,22 @@ def pair_product(a_in, b_in, square, shift):
                 v = outs[g][jj]
                 if B >= 6 and k <= 191:
                     i = k - 96
-                    v += 2 * a96 * a[i] if square else a96 * b[i] + b96 * a[i]
+                    v += a96 * b[i] + b96 * a[i]
                 v %= W32
                 if B >= 6:
                     reg[k - 96] = v
                 if B <= 6 and k <= 96:
-                    out_a[k + shift] = gather_low(v, h, k) % W32
+                    out_a[k] = gather_low(v, h, k) % W32
 
     pend = [[0] * 8, [0] * 8]
     for s_ in range(10, -1, -1):
         acc = [[0] * 23, [0] * 23]
         ilo, ihi = max(0, s_ - 5), min(s_, 5)
         for g in range(2):
-            tiles = [(I, s_ - I) for I in range(ilo, ihi + 1)]
-            if square:
-                off = [(I, J) for I, J in tiles if I < J]
-                for I, J in off:
-                    for p in range(8):
-                        for q in range(16):
-                            acc[g][p + q] += a[16 * I + 8 * g + p] * a[16 * J + q]
-                if off:
-                    acc[g] = [2 * v for v in acc[g]]
-                if s_ % 2 == 0:
-                    I = s_ // 2
-                    for p in range(8):
-                        for q in range(16):
-                            acc[g][p + q] += a[16 * I + 8 * g + p] * a[16 * I + q]
-            else:
-                for I, J in tiles:
-                    for p in range(8):
-                        for q in range(16):
-                            acc[g][p + q] += a[16 * I + 8 * g + p] * b[16 * J + q]
+            for I, J in [(I, s_ - I) for I in range(ilo, ihi + 1)]:
+                for p in range(8):
+                    for q in range(16):
+                        acc[g][p + q] += a[16 * I + 8 * g + p] * b[16 * J + q]
         recv = [[acc[1][8 + j] for j in range(8)], [acc[0][8 + j] for j in range(8)]]
         outs, newp = [[0] * 8, [0] * 8], [[0] * 8, [0] * 8]
         for g in range(2):
@@ -231,10 +220,6 @@ def pair_product(a_in, b_in, square, shift):
         pend = newp
         complete(s_ + 1, outs)
     complete(0, pend)
-    if shift:                                     # the word on t^97: 1 - t^64
-        top = out_a[97]
-        out_a[0] = top
-        out_a[64] -= top
     return np.array([v % (1 << 24) for v in out_a[:R]], dtype=np.uint32)
 
 
@@ -270,15 +255,11 @@ def pair_apply(p, x):
 
 def test_pair_schedule_matches_oracle(orc):
     rng = np.random.default_rng(11)
-    t = np.zeros(R, np.uint32)
-    t[1] = 1
     for _ in range(3):
         a = rng.integers(0, 1 << 24, R).astype(np.uint32)
         b = rng.integers(0, 1 << 24, R).astype(np.uint32)
-        sq = orc.poly_mulmod(a, a)
-        assert np.array_equal(pair_product(a, None, True, 0), sq)
-        assert np.array_equal(pair_product(a, None, True, 1), orc.poly_mulmod(sq, t))
-        assert np.array_equal(pair_product(a, b, False, 0), orc.poly_mulmod(a, b))
+        assert np.array_equal(pair_product(a, b), orc.poly_mulmod(a, b))
+        assert np.array_equal(pair_product(a, a), orc.poly_mulmod(a, a))
         x = rng.integers(0, 1 << 24, R).astype(np.uint32)
         assert np.array_equal(pair_apply(a, x), orc.apply_dot(x, a))
 
@@ -349,3 +330,144 @@ def test_plan_limb_layout_is_the_jump(orc):
     for i, s in enumerate((12345, 2, 54217138)):
         x, c = orc.seeded_state(s)
         assert np.array_equal(got[i], orc.jump(x, c, E)[0])
+
+
+# --- mirrored lane-pair square (symmetric triangles) ------------------------
+def mirror_block_ops(m):
+    """The 16 x 16 block terms that land in output block m (coefficients
+    16m .. 16m+15) of x^2 for blocks X_0 .. X_5 of x: full blocks products
+    X_I X_J (I < J) contribute their low triangle (p + q <= 15) when
+    I + J = m and their high triangle (p + q >= 16) when I + J = m - 1; the
+    square X_I^2 of one block contributes its cross terms p < q likewise."""
+    low = [(I, m - I) for I in range(6) if I < m - I <= 5]
+    high = [(I, m - 1 - I) for I in range(6) if I < m - 1 - I <= 5]
+    low_sym = [m // 2] if m % 2 == 0 else []
+    high_sym = [(m - 1) // 2] if m % 2 == 1 else []
+    return low, high, low_sym, high_sym
+
+
+def mirror_lane_block(X, m, plant=0):
+    """One lane's output block m of x^2 (x = X_0 .. X_5, 96 coefficients):
+    cross terms once, doubled, then the squares x_p^2 at the even outputs."""
+    low, high, low_sym, high_sym = mirror_block_ops(m)
+    acc = [0] * 16
+    for I, J in low:
+        for p in range(16):
+            for q in range(16 - p):
+                acc[p + q] += X[16 * I + p] * X[16 * J + q]
+    for I, J in high:
+        for p in range(1, 16):
+            for q in range(16 - p, 16):
+                acc[p + q - 16] += X[16 * I + p] * X[16 * J + q]
+    for I in low_sym:
+        for p in range(16):
+            for q in range(p + 1, 16 - p):
+                acc[p + q] += X[16 * I + p] * X[16 * I + q]
+    hs_lo = 15 if plant == 1 else 16               # planted: a wrong triangle edge
+    for I in high_sym:
+        for p in range(16):
+            for q in range(max(p + 1, hs_lo - p), 16):
+                if p + q >= 16:
+                    acc[p + q - 16] += X[16 * I + p] * X[16 * I + q]
+                elif plant == 1:
+                    acc[p + q] += X[16 * I + p] * X[16 * I + q]
+    acc = [2 * v for v in acc]
+    for r in range(0, 16, 2):
+        acc[r] += X[8 * m + r // 2] ** 2
+    return [v % W32 for v in acc]
+
+
+def mirror_square(A, Bv, shift, plant=0):
+    """x^2 t^shift mod phi as the mirrored pair schedules it.  A holds x
+    (coefficients 0..96), Bv the same polynomial reversed (Bv[i] = x_{96-i}).
+    Lane 0 forms c_0..c_95 of c = x^2 from A; lane 1 runs the same
+    instructions on Bv, which gives the reversed top half c_192..c_97
+    (written as Hr[k] = c_{192-k}); c_96 is split between the lanes.  The
+    gather folds the top half in closed form, each lane's 8 outputs per
+    block are rotated by one position for a 1 bit (the missing word from the
+    partner by shuffle), t^97 = 1 - t^64 adds the old a_96 at 0 and
+    subtracts it at 64, and both copies are written."""
+    X = [list(map(int, A)), list(map(int, Bv))]
+    C, Hr = [0] * 96, [0] * 96
+    for g, dst in ((0, C), (1, Hr)):
+        for m in range(6):
+            dst[16 * m: 16 * m + 16] = mirror_lane_block(X[g], m, plant)
+    part = [sum(X[g][24 * g + i] * X[g][96 - 24 * g - i] for i in range(24)) for g in (0, 1)]
+    c96 = (2 * (part[0] + part[1]) + X[0][48] ** 2) % W32
+    assert X[1][48] == X[0][48]
+
+    def h(k):
+        return Hr[95 - k]
+
+    a96 = (c96 + h(65) - h(32)) % W32
+    newA, newB = [0] * 100, [0] * 100
+    prev7 = [0, 0]                                # lane 1's v[7] of the previous block
+    v = [[0] * 8, [0] * 8]
+    for kB in range(6):
+        for g in (0, 1):
+            for j in range(8):
+                n = 16 * kB + 8 * g + j
+                v[g][j] = gather_low(C[n], h, n) % W32
+        recv = [prev7[1], v[0][7]]                # what each lane gets from its partner
+        for g in (0, 1):
+            for j in range(8):
+                pos = 16 * kB + 8 * g + j
+                w = (recv[g] if j == 0 else v[g][j - 1]) if shift else v[g][j]
+                if shift and pos == 0:
+                    w += a96
+                if shift and pos == 64:
+                    w -= a96
+                newA[pos] = w % W32
+                newB[96 - pos] = w % W32
+        prev7 = [v[0][7], v[1][7]]
+    w96 = prev7[1] if shift else a96
+    newA[96] = newB[0] = w96
+    return newA, newB
+
+
+def mirror_poly_power(e, plant=0):
+    L = e.bit_length()
+    if L <= 6:
+        v0, p = e & 63, -1
+    else:
+        v0, p = (e >> (L - 6)) & 63, L - 7
+    A, Bv = [0] * 100, [0] * 100
+    A[v0] = 1
+    Bv[96 - v0] = 1
+    while p >= 0:
+        A, Bv = mirror_square(A, Bv, (e >> p) & 1, plant)
+        p -= 1
+    return np.array([v & MASK for v in A[:R]], dtype=np.uint32), Bv
+
+
+def test_mirror_square_multiply_schedule_matches_oracle(orc):
+    for e in (0, 1, 63, 64, 65, 96, 97, 127, 128, 1000, 2**40 + 5, (1 << 64) - 1,
+              (1 << 120) + 12345):
+        a, Bv = mirror_poly_power(e)
+        assert np.array_equal(a, orc.poly_pow_t(e)), e
+        assert [v & MASK for v in Bv[:R]] == [int(x) for x in a[::-1]], e
+
+
+def test_mirror_square_dense_and_planted_edge(orc):
+    rng = np.random.default_rng(13)
+    t = np.zeros(R, np.uint32)
+    t[1] = 1
+    for _ in range(3):
+        a = rng.integers(0, 1 << 24, R).astype(np.uint32)
+        A = [int(v) for v in a] + [0, 0, 0]
+        Bv = [int(v) for v in a[::-1]] + [0, 0, 0]
+        sq = orc.poly_mulmod(a, a)
+        for shift, want in ((0, sq), (1, orc.poly_mulmod(sq, t))):
+            nA, nB = mirror_square(A, Bv, shift)
+            assert [v & MASK for v in nA[:R]] == [int(x) for x in want]
+            assert [v & MASK for v in nB[:R]] == [int(x) for x in want[::-1]]
+        # the same schedule with the high-triangle edge of a block square off by one
+        bad, _ = mirror_square(A, Bv, 0, plant=1)
+        assert [v & MASK for v in bad[:R]] != [int(x) for x in sq]
+    # the six blocks' terms add up to the symmetric count 97 * 98 / 2 - 1 - 48
+    # (everything but c_96's 49 products), split evenly between the lanes
+    n = 0
+    for m in range(6):
+        low, high, ls, hs = mirror_block_ops(m)
+        n += 136 * len(low) + 120 * len(high) + 64 * len(ls) + 56 * len(hs) + 8
+    assert 2 * n + 49 == 97 * 98 // 2
