@@ -13,14 +13,15 @@
 // c_96 (49) is split between the lanes.
 //
 // A lane forms its outputs block by block (16 coefficients, output block m
-// = coefficients 16m .. 16m+15, m = 0..5), output-stationary, from the
-// 16-coefficient blocks X_0 .. X_5 held in registers: a block pair X_I X_J
-// (I < J) puts its low triangle (p + q <= 15) into block I + J and its high
-// triangle (p + q >= 16) into block I + J + 1; a block square X_I^2 puts its
-// cross terms p < q into blocks 2I and 2I + 1.  Cross terms are summed once,
-// doubled, then the squares x_p^2 are added at the even outputs.  No partial
-// sum crosses lanes.  Lane 0 stores its half to C[n] = c_n and lane 1 to
-// Hr[k] = c_{192-k} (the same store pattern), so that h_j = c_{97+j} =
+// = coefficients 16m .. 16m+15, m = 0..5), output-stationary.  The cross
+// terms x_i x_{n-i} (i < n - i) of block m are taken in chunks of 8 values
+// of i: the chunks i = 8c .. 8c+7 for c < m lie wholly below the diagonal
+// (i < j for every output of the block), each an 8 x 16 parallelogram of
+// 128 multiply-adds with the same code; the chunk at i = 8m holds the
+// diagonal and keeps its terms with u < r/2.  Cross terms are summed once,
+// doubled, then the squares x_{8m+r/2}^2 are added at the even outputs.  No
+// partial sum crosses lanes.  Lane 0 stores its half to C[n] = c_n and lane
+// 1 to Hr[k] = c_{192-k} (the same store pattern), so that h_j = c_{97+j} =
 // Hr[95 - j].
 //
 // Reduction mod phi = t^97 + t^64 - 1 (t^k = t^{k-97} - t^{k-33}) in
@@ -91,37 +92,41 @@ __device__ __forceinline__ void mir_sym_high(uint32_t (&acc)[16], const Hex& x) 
   }
 }
 
-// Output block m of x^2 (coefficients 16m .. 16m+15) from the blocks xb.
-template <int m>
-__device__ __forceinline__ void mir_block(uint32_t (&acc)[16], const Hex (&xb)[6]) {
+// One full chunk of output block m: acc[r] += sum_{u<8} x_{8c+u} w[r-u+8]
+// for r = 0..15, with w[k] = x_{16m-8c-8+k} (24 words); all its terms have
+// i < j.  128 multiply-adds; each accumulator is updated every 16.
+__device__ __forceinline__ void mir_para(uint32_t (&acc)[16], const Oct& x, const Hex& w0,
+                                         const Oct& w1) {
 #pragma unroll
-  for (int r = 0; r < 16; ++r) acc[r] = 0;
+  for (int u = 0; u < 8; ++u) {
 #pragma unroll
-  for (int I = 0; I < 6; ++I) {
-    const int J = m - I;
-    if (I < J && J <= 5) mir_tri_low(acc, xb[I], xb[J]);
-    const int J1 = m - 1 - I;
-    if (I < J1 && J1 <= 5) mir_tri_high(acc, xb[I], xb[J1]);
+    for (int r = 0; r < 16; ++r) {
+      const int k = r - u + 8;  // 1 .. 23
+      acc[r] += x.v[u] * (k < 16 ? w0.v[k] : w1.v[k - 16]);
+    }
   }
-  if constexpr (m % 2 == 0) {
-    mir_sym_low(acc, xb[m / 2]);
-  } else {
-    mir_sym_high(acc, xb[(m - 1) / 2]);
+}
+
+// The last chunk of output block m and the block's end: t = x_{8m} ..
+// x_{8m+15}; the terms with i < j are t_u t_{r-u} for u < r/2.  Then the
+// cross terms are doubled, the squares t_{r/2}^2 added at even r, the block
+// stored to dst + 16m and acc cleared.
+__device__ __forceinline__ void mir_tail(uint32_t (&acc)[16], const Hex& t,
+                                         uint32_t* __restrict__ dst, int m) {
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+#pragma unroll
+    for (int r = 2 * u + 1; r < 16; ++r) acc[r] += t.v[u] * t.v[r - u];
   }
 #pragma unroll
   for (int r = 0; r < 16; ++r) acc[r] += acc[r];
-  constexpr int sb = m / 2, so = 8 * (m % 2);  // x_{8m+u} = block sb, offset so + u
 #pragma unroll
-  for (int u = 0; u < 8; ++u) acc[2 * u] += xb[sb].v[so + u] * xb[sb].v[so + u];
-}
-
-template <int m>
-__device__ __forceinline__ void mir_block_store(uint32_t* __restrict__ dst, const Hex (&xb)[6]) {
-  uint32_t acc[16];
-  mir_block<m>(acc, xb);
+  for (int u = 0; u < 8; ++u) acc[2 * u] += t.v[u] * t.v[u];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < 4; ++q) {
     st4(dst + 16 * m + 4 * q, acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    acc[4 * q] = acc[4 * q + 1] = acc[4 * q + 2] = acc[4 * q + 3] = 0u;
+  }
 }
 
 // v[j] += / -= h_{n+kOff} for the lane's n = 16 kB + 8 g + j, j < 8, with
@@ -208,9 +213,6 @@ __device__ __forceinline__ void square_mirror_pair(uint32_t* __restrict__ slice,
   uint32_t* Hr = slice + kMirH;
   const uint32_t* X = g ? Bv : A;
   uint32_t* dst = g ? Hr : C;
-  Hex xb[6];
-#pragma unroll
-  for (int I = 0; I < 6; ++I) xb[I] = lds16(X + 16 * I);
   // c_96 = 2 sum_{i<48} x_i x_{96-i} + x_48^2: lane g takes i = 24g .. 24g+23
   // of its own copy (for lane 1, xr_i xr_{96-i} = x_{96-i} x_i).
   uint32_t part = 0;
@@ -230,13 +232,38 @@ __device__ __forceinline__ void square_mirror_pair(uint32_t* __restrict__ slice,
       part += l4[3] * h4[1];
     }
   }
-  mir_block_store<0>(dst, xb);
-  mir_block_store<1>(dst, xb);
-  mir_block_store<2>(dst, xb);
-  mir_block_store<3>(dst, xb);
-  mir_block_store<4>(dst, xb);
-  mir_block_store<5>(dst, xb);
-  const uint32_t x48 = xb[3].v[0];          // x_48 (the same word in both copies)
+  // This lane's half, output block by output block: block m = m full chunks
+  // (c = 0 .. m-1) then the last chunk.  Two operand sets (P, Q) alternate so
+  // that the next chunk's words load while the current one multiplies.
+  uint32_t acc[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) acc[r] = 0;
+#pragma unroll 1
+  for (int m = 0; m < 6; ++m) {
+    const uint32_t* wb = X + 16 * m - 8;   // window base of chunk c: wb - 8c
+    int c = 0;
+    if (m > 0) {
+      Oct xp = lds8(X), wp1;
+      Hex wp0 = lds16(wb);
+      wp1 = lds8(wb + 16);
+#pragma unroll 1
+      for (; c + 1 < m; c += 2) {
+        const Oct xq = lds8(X + 8 * (c + 1));
+        const Hex wq0 = lds16(wb - 8 * (c + 1));
+        const Oct wq1 = lds8(wb - 8 * (c + 1) + 16);
+        mir_para(acc, xp, wp0, wp1);
+        if (c + 2 < m) {
+          xp = lds8(X + 8 * (c + 2));
+          wp0 = lds16(wb - 8 * (c + 2));
+          wp1 = lds8(wb - 8 * (c + 2) + 16);
+        }
+        mir_para(acc, xq, wq0, wq1);
+      }
+      if (c < m) mir_para(acc, xp, wp0, wp1);
+    }
+    mir_tail(acc, lds16(X + 8 * m), dst, m);
+  }
+  const uint32_t x48 = X[48];               // x_48 (the same word in both copies)
   const uint32_t c96 =
       2u * (part + __shfl_xor_sync(kFull, part, kPairXor)) + x48 * x48;
   __syncwarp();

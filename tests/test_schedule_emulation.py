@@ -347,8 +347,9 @@ def mirror_block_ops(m):
 
 
 def mirror_lane_block(X, m, plant=0):
-    """One lane's output block m of x^2 (x = X_0 .. X_5, 96 coefficients):
-    cross terms once, doubled, then the squares x_p^2 at the even outputs."""
+    """One lane's output block m of x^2 (x = X_0 .. X_5, 96 coefficients) by
+    16 x 16 block triangles: cross terms once, doubled, then the squares
+    x_p^2 at the even outputs."""
     low, high, low_sym, high_sym = mirror_block_ops(m)
     acc = [0] * 16
     for I, J in low:
@@ -377,6 +378,27 @@ def mirror_lane_block(X, m, plant=0):
     return [v % W32 for v in acc]
 
 
+def mirror_lane_block_chunks(X, m, plant=0):
+    """The same block m as the kernel's loop forms it: m full chunks, each
+    acc[r] += sum_{u<8} x_{8c+u} x_{16m+r-8c-u} (an 8 x 16 parallelogram of
+    the product, i < j throughout), then the chunk at 8m, whose terms with
+    i < j are u < r/2, then doubling and the squares x_{8m+r/2}^2 at even r."""
+    acc = [0] * 16
+    for c in range(m):
+        w = X[16 * m - 8 * c - 8: 16 * m - 8 * c + 16]           # 24 words, w[k] = x_{base+k}
+        for u in range(8):
+            for r in range(16):
+                acc[r] += X[8 * c + u] * w[r - u + 8 - (plant == 1)]
+    t = X[8 * m: 8 * m + 16]
+    for u in range(8):
+        for r in range(2 * u + 1 + (plant == 2), 16):
+            acc[r] += t[u] * t[r - u]
+    acc = [2 * v for v in acc]
+    for r in range(0, 16, 2):
+        acc[r] += t[r // 2] ** 2
+    return [v % W32 for v in acc]
+
+
 def mirror_square(A, Bv, shift, plant=0):
     """x^2 t^shift mod phi as the mirrored pair schedules it.  A holds x
     (coefficients 0..96), Bv the same polynomial reversed (Bv[i] = x_{96-i}).
@@ -391,7 +413,9 @@ def mirror_square(A, Bv, shift, plant=0):
     C, Hr = [0] * 96, [0] * 96
     for g, dst in ((0, C), (1, Hr)):
         for m in range(6):
-            dst[16 * m: 16 * m + 16] = mirror_lane_block(X[g], m, plant)
+            blk = mirror_lane_block_chunks(X[g], m, plant)
+            assert plant or blk == mirror_lane_block(X[g], m)
+            dst[16 * m: 16 * m + 16] = blk
     part = [sum(X[g][24 * g + i] * X[g][96 - 24 * g - i] for i in range(24)) for g in (0, 1)]
     c96 = (2 * (part[0] + part[1]) + X[0][48] ** 2) % W32
     assert X[1][48] == X[0][48]
@@ -461,9 +485,11 @@ def test_mirror_square_dense_and_planted_edge(orc):
             nA, nB = mirror_square(A, Bv, shift)
             assert [v & MASK for v in nA[:R]] == [int(x) for x in want]
             assert [v & MASK for v in nB[:R]] == [int(x) for x in want[::-1]]
-        # the same schedule with the high-triangle edge of a block square off by one
-        bad, _ = mirror_square(A, Bv, 0, plant=1)
-        assert [v & MASK for v in bad[:R]] != [int(x) for x in sq]
+        # the same schedule with the window of the full chunks one word off,
+        # or with the i < j edge of the last chunk off by one
+        for pl in (1, 2):
+            bad, _ = mirror_square(A, Bv, 0, plant=pl)
+            assert [v & MASK for v in bad[:R]] != [int(x) for x in sq]
     # the six blocks' terms add up to the symmetric count 97 * 98 / 2 - 1 - 48
     # (everything but c_96's 49 products), split evenly between the lanes
     n = 0
