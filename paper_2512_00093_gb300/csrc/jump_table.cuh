@@ -46,10 +46,10 @@ static_assert(kTabStreamWords % 32 == 4, "bank spread");
 
 // Row (j * 256 + d) = t^{d 2^{8j}} mod phi, canonical 24-bit coefficients
 // 0..96, then zeros.
-__global__ void __launch_bounds__(32) table_build_kernel(uint32_t* __restrict__ table) {
+__global__ void __launch_bounds__(kMirThreads) table_build_kernel(uint32_t* __restrict__ table) {
   extern __shared__ __align__(16) uint32_t smem[];
   const unsigned lane = threadIdx.x & 31;
-  const unsigned g = lane >> 4, slot = lane & 15;
+  const unsigned g = lane >> 4, slot = lane & 15, w = threadIdx.x >> 5;
   const int row = blockIdx.x * kJumpStreamsPerWarp + static_cast<int>(slot);
   const bool active = row < kTabRows;
   uint32_t* slice = smem + slot * kMirStreamWords;
@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(32) table_build_kernel(uint32_t* __restrict__ 
     E[w0] = static_cast<uint32_t>(v);
     if (w0 + 1 < kMaxExpWords) E[w0 + 1] = static_cast<uint32_t>(v >> 32);
   }
-  poly_power_mirror(E, active, slice, g);
-  if (active) {
+  poly_power_mirror(E, active, slice, g, w);
+  if (active && w == 0) {
     uint32_t* dst = table + static_cast<size_t>(row) * kTabRowWords;
     const uint32_t* a = slice + kMirA;
     for (int q = static_cast<int>(g); q < kTabRowWords; q += 2) dst[q] = q < kR ? (a[q] & kMask24) : 0u;

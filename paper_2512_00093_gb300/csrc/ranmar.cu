@@ -248,10 +248,11 @@ int launch_jump(const ranmar_state_t* base, size_t n_base, const uint32_t* base_
         base, n_base, base_idx, exp, exp_words, part, mode, out, n, status, dst_idx, n_dst);
     return check_launch();
   }
-  const uint64_t per_cta = ranmar::kJumpStreamsPerWarp;   // one warp per CTA
+  const uint64_t per_cta = ranmar::kJumpStreamsPerWarp;   // 16 streams per CTA (two warps)
   const uint64_t blocks = (n + per_cta - 1) / per_cta;
   if (blocks > 0x7FFFFFFFull) return RANMAR_ERANGE;
-  ranmar::jump_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kMirSmemBytes, s>>>(
+  ranmar::jump_kernel<<<static_cast<unsigned>(blocks), ranmar::kMirThreads, ranmar::kMirSmemBytes,
+                        s>>>(
       base, n_base, base_idx, exp, exp_words, part, mode, out, n, status, dst_idx, n_dst);
   return check_launch();
 }
@@ -572,7 +573,8 @@ int ranmar_poly_power(const uint32_t* d_exp, uint32_t exp_words, size_t n, uint3
   }
   const uint64_t blocks = (n + ranmar::kJumpStreamsPerWarp - 1) / ranmar::kJumpStreamsPerWarp;
   if (blocks > 0x7FFFFFFFull) return RANMAR_ERANGE;
-  ranmar::poly_power_kernel<<<static_cast<unsigned>(blocks), 32, ranmar::kMirSmemBytes,
+  ranmar::poly_power_kernel<<<static_cast<unsigned>(blocks), ranmar::kMirThreads,
+                              ranmar::kMirSmemBytes,
                               reinterpret_cast<cudaStream_t>(stream)>>>(d_exp, exp_words, d_poly,
                                                                         n);
   return check_launch();
@@ -955,7 +957,8 @@ int ranmar_table_create(ranmar_table_t** out) {
   if (e == cudaSuccess) {
     const unsigned blocks = (ranmar::kTabRows + ranmar::kJumpStreamsPerWarp - 1) /
                             ranmar::kJumpStreamsPerWarp;
-    ranmar::table_build_kernel<<<blocks, 32, ranmar::kMirSmemBytes, s>>>(t->rows);
+    ranmar::table_build_kernel<<<blocks, ranmar::kMirThreads, ranmar::kMirSmemBytes, s>>>(
+        t->rows);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaStreamDestroy(s);

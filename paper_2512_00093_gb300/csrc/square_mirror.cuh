@@ -35,6 +35,11 @@
 // word pushed to t^97 (the old a_96) folds back as +a_96 at t^0 and -a_96
 // at t^64.  The new polynomial is written forward to A and reversed to Bv.
 //
+// Mapping: a CTA of two warps takes 16 streams; in each warp lanes L and
+// L + 16 are the pair of stream L.  The two warps share each stream's work
+// (different output blocks, then different reduction blocks), so a batch
+// of n streams runs on n/8 warps.
+//
 // All arithmetic is 32-bit and wraps mod 2^32, which is exact mod 2^24;
 // words are masked to 24 bits only when a result leaves the kernel.
 //
@@ -52,9 +57,12 @@ constexpr int kMirA = 0;
 constexpr int kMirB = 100;
 constexpr int kMirC = 200;
 constexpr int kMirH = 296;
+constexpr int kMirC96 = 392;          // c_96, handed from warp 0 to warp 1
 constexpr int kMirStreamWords = 420;
+constexpr int kMirWarps = 2;          // warps per CTA, sharing its 16 streams
+constexpr int kMirThreads = 32 * kMirWarps;
 constexpr size_t kMirSmemBytes = sizeof(uint32_t) * kMirStreamWords * kJumpStreamsPerWarp;
-static_assert(kMirH + 96 <= kMirStreamWords, "slice");
+static_assert(kMirH + 96 <= kMirC96 && kMirC96 < kMirStreamWords, "slice");
 static_assert(kMirC + kRingWords <= kMirStreamWords, "ring inside the slice");
 static_assert(kMirStreamWords % 32 == 4, "bank spread");
 static_assert(kMirB % 4 == 0 && kMirC % 4 == 0 && kMirH % 4 == 0, "16-byte alignment");
@@ -93,16 +101,18 @@ __device__ __forceinline__ void mir_sym_high(uint32_t (&acc)[16], const Hex& x) 
 }
 
 // One full chunk of output block m: acc[r] += sum_{u<8} x_{8c+u} w[r-u+8]
-// for r = 0..15, with w[k] = x_{16m-8c-8+k} (24 words); all its terms have
-// i < j.  128 multiply-adds; each accumulator is updated every 16.
-__device__ __forceinline__ void mir_para(uint32_t (&acc)[16], const Oct& x, const Hex& w0,
-                                         const Oct& w1) {
+// for r = 0..15, with w[k] = x_{16m-8c-8+k} (24 words as three octets:
+// w[0..7] = lo, w[8..15] = mid, w[16..23] = hi); all its terms have i < j.
+// 128 multiply-adds; each accumulator is updated every 16.
+__device__ __forceinline__ void mir_para(uint32_t (&acc)[16], const Oct& x, const Oct& lo,
+                                         const Oct& mid, const Oct& hi) {
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int k = r - u + 8;  // 1 .. 23
-      acc[r] += x.v[u] * (k < 16 ? w0.v[k] : w1.v[k - 16]);
+      const uint32_t w = k < 8 ? lo.v[k] : (k < 16 ? mid.v[k - 8] : hi.v[k - 16]);
+      acc[r] += x.v[u] * w;
     }
   }
 }
@@ -203,20 +213,32 @@ __device__ __forceinline__ void mir_gather(uint32_t* __restrict__ A, uint32_t* _
   br[-7] = w[7];
 }
 
-// x = x^2 t^shift mod phi in place (A forward, Bv reversed), lanes g = 0, 1
-// of the pair cooperating; all 32 lanes of the warp call it together.
+// a_47 of the reduced square (the word below block 3), for warp 1's lane 0
+// at its first block: c_47 + h_47 - h_80 (the other terms of the gather do
+// not reach n = 47).
+__device__ __forceinline__ uint32_t mir_a47(const uint32_t* __restrict__ C,
+                                            const uint32_t* __restrict__ Hr) {
+  return C[47] + Hr[95 - 47] - Hr[95 - 80];
+}
+
+// x = x^2 t^shift mod phi in place (A forward, Bv reversed).  Both warps of
+// the CTA call it for the same 16 streams (lanes g = 0, 1 of each pair in
+// each warp): warp 0 forms output blocks 5 and 3 of each lane's half and
+// c_96, warp 1 blocks 4, 2, 1 and 0 (1,216 and 1,184 multiply-adds per
+// lane); after a CTA barrier warp 0 reduces blocks 0..2 and warp 1 blocks
+// 3..5 and position 96; a second barrier ends the squaring.
 __device__ __forceinline__ void square_mirror_pair(uint32_t* __restrict__ slice, uint32_t shift,
-                                                   unsigned g) {
+                                                   unsigned g, unsigned w) {
   uint32_t* A = slice + kMirA;
   uint32_t* Bv = slice + kMirB;
   uint32_t* C = slice + kMirC;
   uint32_t* Hr = slice + kMirH;
   const uint32_t* X = g ? Bv : A;
   uint32_t* dst = g ? Hr : C;
-  // c_96 = 2 sum_{i<48} x_i x_{96-i} + x_48^2: lane g takes i = 24g .. 24g+23
-  // of its own copy (for lane 1, xr_i xr_{96-i} = x_{96-i} x_i).
-  uint32_t part = 0;
-  {
+  if (w == 0) {
+    // c_96 = 2 sum_{i<48} x_i x_{96-i} + x_48^2: lane g takes i = 24g ..
+    // 24g+23 of its own copy (for lane 1, xr_i xr_{96-i} = x_{96-i} x_i).
+    uint32_t pq[4] = {0u, 0u, 0u, 0u};      // four independent chains
     const uint32_t* lo = X + 24 * g;        // x_{24g + i}
     const uint32_t* hi = X + 72 - 24 * g;   // hi[k] = x_{72 - 24g + k}; x_{96-24g-i} = hi[24 - i]
 #pragma unroll
@@ -226,68 +248,92 @@ __device__ __forceinline__ void square_mirror_pair(uint32_t* __restrict__ slice,
       lds4_to(h4, hi + 20 - 4 * q);       // hi[20-4q .. 23-4q]
       lds4_to(h5, hi + 24 - 4 * q);       // hi[24-4q .. 27-4q]
       // i = 4q + u: x_{96-24g-i} = hi[24 - 4q - u]
-      part += l4[0] * h5[0];
-      part += l4[1] * h4[3];
-      part += l4[2] * h4[2];
-      part += l4[3] * h4[1];
+      pq[0] += l4[0] * h5[0];
+      pq[1] += l4[1] * h4[3];
+      pq[2] += l4[2] * h4[2];
+      pq[3] += l4[3] * h4[1];
     }
+    const uint32_t part = (pq[0] + pq[1]) + (pq[2] + pq[3]);
+    const uint32_t x48 = X[48];             // x_48 (the same word in both copies)
+    const uint32_t c96 = 2u * (part + __shfl_xor_sync(kFull, part, kPairXor)) + x48 * x48;
+    if (g == 0) slice[kMirC96] = c96;
   }
-  // This lane's half, output block by output block: block m = m full chunks
-  // (c = 0 .. m-1) then the last chunk.  Two operand sets (P, Q) alternate so
-  // that the next chunk's words load while the current one multiplies.
+  // This warp's output blocks of the lane's half: block m = m full chunks
+  // (c = 0 .. m-1) then the last chunk.  Chunk c's window is the octets
+  // O(2m-c-1), O(2m-c), O(2m-c+1) (O(k) = x_{8k} .. x_{8k+7}), so the next
+  // chunk needs one new octet: four octet registers rotate (period four, the
+  // loop unrolled by four) and each chunk loads the next chunk's new octet
+  // and x octet O(c+1) while it multiplies.
+  const uint32_t blocks = w ? 0x0124u : 0x35u;   // m, four bits each, first in the low bits
+  const int nblocks = w ? 4 : 2;
   uint32_t acc[16];
 #pragma unroll
   for (int r = 0; r < 16; ++r) acc[r] = 0;
 #pragma unroll 1
-  for (int m = 0; m < 6; ++m) {
-    const uint32_t* wb = X + 16 * m - 8;   // window base of chunk c: wb - 8c
-    int c = 0;
+  for (int k = 0; k < nblocks; ++k) {
+    const int m = static_cast<int>((blocks >> (4 * k)) & 15u);
     if (m > 0) {
-      Oct xp = lds8(X), wp1;
-      Hex wp0 = lds16(wb);
-      wp1 = lds8(wb + 16);
+      const uint32_t* ob = X + 16 * m - 8;   // O(2m-1-c) = ob - 8c
+      Oct w0 = lds8(ob), w1 = lds8(ob + 8), w2 = lds8(ob + 16), w3;
+      Oct x0 = lds8(X), x1;
 #pragma unroll 1
-      for (; c + 1 < m; c += 2) {
-        const Oct xq = lds8(X + 8 * (c + 1));
-        const Hex wq0 = lds16(wb - 8 * (c + 1));
-        const Oct wq1 = lds8(wb - 8 * (c + 1) + 16);
-        mir_para(acc, xp, wp0, wp1);
-        if (c + 2 < m) {
-          xp = lds8(X + 8 * (c + 2));
-          wp0 = lds16(wb - 8 * (c + 2));
-          wp1 = lds8(wb - 8 * (c + 2) + 16);
+      for (int c = 0; c < m; c += 4) {
+        if (c + 1 < m) {
+          w3 = lds8(ob - 8 * (c + 1));
+          x1 = lds8(X + 8 * (c + 1));
         }
-        mir_para(acc, xq, wq0, wq1);
+        mir_para(acc, x0, w0, w1, w2);
+        if (c + 1 >= m) break;
+        if (c + 2 < m) {
+          w2 = lds8(ob - 8 * (c + 2));
+          x0 = lds8(X + 8 * (c + 2));
+        }
+        mir_para(acc, x1, w3, w0, w1);
+        if (c + 2 >= m) break;
+        if (c + 3 < m) {
+          w1 = lds8(ob - 8 * (c + 3));
+          x1 = lds8(X + 8 * (c + 3));
+        }
+        mir_para(acc, x0, w2, w3, w0);
+        if (c + 3 >= m) break;
+        if (c + 4 < m) {
+          w0 = lds8(ob - 8 * (c + 4));
+          x0 = lds8(X + 8 * (c + 4));
+        }
+        mir_para(acc, x1, w1, w2, w3);
       }
-      if (c < m) mir_para(acc, xp, wp0, wp1);
     }
     mir_tail(acc, lds16(X + 8 * m), dst, m);
   }
-  const uint32_t x48 = X[48];               // x_48 (the same word in both copies)
-  const uint32_t c96 =
-      2u * (part + __shfl_xor_sync(kFull, part, kPairXor)) + x48 * x48;
-  __syncwarp();
-  const uint32_t a96 = c96 + Hr[95 - 65] - Hr[95 - 32];
-  uint32_t prev7 = 0, last = 0;
-  mir_gather<0>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-  mir_gather<1>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-  mir_gather<2>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-  mir_gather<3>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-  mir_gather<4>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-  mir_gather<5>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-  if (g) {  // position 96: the old a_95 (lane 1's v[7] of block 5) or a_96
-    const uint32_t w96 = shift ? last : a96;
-    A[96] = w96;
-    Bv[0] = w96;
+  __syncthreads();
+  const uint32_t a96 = slice[kMirC96] + Hr[95 - 65] - Hr[95 - 32];
+  uint32_t last = 0;
+  if (w == 0) {
+    uint32_t prev7 = 0;                      // a_{-1} = 0 below block 0
+    mir_gather<0>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    mir_gather<1>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    mir_gather<2>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+  } else {
+    uint32_t prev7 = g ? mir_a47(C, Hr) : 0u;   // lane 1 hands it to lane 0 at block 3
+    mir_gather<3>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    mir_gather<4>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    mir_gather<5>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    if (g) {  // position 96: the old a_95 (lane 1's v[7] of block 5) or a_96
+      const uint32_t w96 = shift ? last : a96;
+      A[96] = w96;
+      Bv[0] = w96;
+    }
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 // A = t^E mod phi (and Bv its reverse) for the stream of this lane pair by
-// left-to-right square-and-multiply; all 32 lanes of the warp call it
-// together (the bit loop runs over the longest exponent of the warp).
+// left-to-right square-and-multiply; both warps of the CTA call it together
+// (the bit loop runs over the longest exponent of the CTA's 16 streams, the
+// same for both warps).
 __device__ __forceinline__ void poly_power_mirror(const uint32_t (&E)[kMaxExpWords], bool active,
-                                                  uint32_t* __restrict__ slice, unsigned g) {
+                                                  uint32_t* __restrict__ slice, unsigned g,
+                                                  unsigned w) {
   const int nb = active ? exp_bitlen(E) : 0;
   const int L = static_cast<int>(__reduce_max_sync(kFull, static_cast<unsigned>(nb)));
   // Leading (up to) six bits: P = t^v0 with v0 < 64 < 97 is a monomial.
@@ -301,18 +347,18 @@ __device__ __forceinline__ void poly_power_mirror(const uint32_t (&E)[kMaxExpWor
     p = L - 7;
   }
   if (!active) v0 = 0;
-  for (int q = static_cast<int>(g); q < (kMirB + 100) / 4; q += 2)
+  for (int q = static_cast<int>(g + 2 * w); q < (kMirB + 100) / 4; q += 4)
     reinterpret_cast<uint4*>(slice)[q] = make_uint4(0u, 0u, 0u, 0u);
-  __syncwarp();
-  if (g == 0) {
+  __syncthreads();
+  if (g == 0 && w == 0) {
     slice[kMirA + v0] = 1u;
     slice[kMirB + 96 - v0] = 1u;
   }
-  __syncwarp();
+  __syncthreads();
 #pragma unroll 1
   for (; p >= 0; --p) {
     const uint32_t bit = active ? exp_bit(E, p) : 0u;
-    square_mirror_pair(slice, bit, g);
+    square_mirror_pair(slice, bit, g, w);
   }
 }
 
@@ -324,7 +370,7 @@ __device__ __forceinline__ void poly_power_mirror(const uint32_t (&E)[kMaxExpWor
 // dst = f^E(base) per stream: t^Ep mod phi by the square-and-multiply above
 // (Ep = E, or E mod T for RANMAR_JUMP_REDUCE_PERIOD), the application x P(A)
 // through the C/Hr region as its ring, and c / pos by the full E.
-__global__ void __launch_bounds__(32, 8) jump_kernel(
+__global__ void __launch_bounds__(kMirThreads, 7) jump_kernel(
     const ranmar_state_t* __restrict__ d_base, uint64_t n_base,
     const uint32_t* __restrict__ d_base_idx, const uint32_t* __restrict__ d_exp,
     uint32_t exp_words, ExpParams part, int mode, ranmar_state_t* __restrict__ d_out,
@@ -332,6 +378,7 @@ __global__ void __launch_bounds__(32, 8) jump_kernel(
   extern __shared__ __align__(16) uint32_t smem[];
   const unsigned lane = threadIdx.x & 31;
   const unsigned g = lane >> 4;
+  const unsigned w = threadIdx.x >> 5;
   const unsigned slot = lane & 15;
   const uint64_t i = static_cast<uint64_t>(blockIdx.x) * kJumpStreamsPerWarp + slot;
   uint32_t* slice = smem + slot * kMirStreamWords;
@@ -361,20 +408,22 @@ __global__ void __launch_bounds__(32, 8) jump_kernel(
 #pragma unroll
   for (int w = 0; w < kMaxExpWords; ++w) Ep[w] = E[w];
   if (part.flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
-  poly_power_mirror(Ep, active, slice, g);
+  poly_power_mirror(Ep, active, slice, g, w);
+  if (w != 0) return;                        // the application is warp 0's
   apply_pair(base, E, active, d_out + (active ? di : 0), slice + kMirA, slice + kMirC, g);
 }
 
 // P_{E_i} = t^{E_i} mod phi alone (the polynomial part of a jump, Sec. 3.1),
 // by the same square-and-multiply: d_poly[i] = coefficients 0..96 (24-bit),
 // then three zero words.
-__global__ void __launch_bounds__(32, 8) poly_power_kernel(const uint32_t* __restrict__ d_exp,
+__global__ void __launch_bounds__(kMirThreads, 7) poly_power_kernel(const uint32_t* __restrict__ d_exp,
                                                            uint32_t exp_words,
                                                            uint32_t* __restrict__ d_poly,
                                                            uint64_t n) {
   extern __shared__ __align__(16) uint32_t smem[];
   const unsigned lane = threadIdx.x & 31;
   const unsigned g = lane >> 4;
+  const unsigned w = threadIdx.x >> 5;
   const unsigned slot = lane & 15;
   const uint64_t i = static_cast<uint64_t>(blockIdx.x) * kJumpStreamsPerWarp + slot;
   uint32_t* slice = smem + slot * kMirStreamWords;
@@ -382,8 +431,8 @@ __global__ void __launch_bounds__(32, 8) poly_power_kernel(const uint32_t* __res
   uint32_t E[kMaxExpWords];
   const ExpParams part{};
   load_exponent(E, 0, d_exp, active ? exp_words : 0, part, active ? i : 0);
-  poly_power_mirror(E, active, slice, g);
-  if (active) {
+  poly_power_mirror(E, active, slice, g, w);
+  if (active && w == 0) {
     uint32_t* dst = d_poly + i * kPolyWords;
     const uint32_t* a = slice + kMirA;
     for (int q = static_cast<int>(g); q < kPolyWords; q += 2) dst[q] = q < kR ? (a[q] & kMask24) : 0u;
