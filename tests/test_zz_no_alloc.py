@@ -73,3 +73,31 @@ def test_static_pack_matches_handle_pack_twice():
         assert np.array_equal(bits[o], bits[ro])
         assert np.all(np.diff(bits[o]) <= 0)
         b.close()
+
+
+@pytest.mark.gpu
+def test_static_pack_without_order_or_total_and_empty():
+    """d_order = NULL and d_total = NULL give the same descriptors (the total
+    then stays inside the library's array); n = 0 writes *d_total = 0."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_00093_gb300 as rm
+    L = _lib()
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream().cuda_stream
+    n = 3000
+    c = np.floor(64 * 1024.0 ** np.random.default_rng(3).random(n)).astype(np.int64)
+    counts = torch.as_tensor(c, device=dev)
+    b = rm.Batch(n)
+    ref_desc, _, _ = b.pack(counts, order=False)
+    desc = torch.full((n, 3), -1, dtype=torch.int64, device=dev)
+    assert L.ranmar_batch_pack_static(counts.data_ptr(), n, 0, desc.data_ptr(), None, None,
+                                      stream) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(desc, ref_desc)
+    total = torch.full((1,), -1, dtype=torch.int64, device=dev)
+    assert L.ranmar_batch_pack_static(counts.data_ptr(), 0, 0, desc.data_ptr(), None,
+                                      total.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    assert int(total.item()) == 0
+    b.close()
