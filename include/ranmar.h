@@ -123,9 +123,14 @@ int ranmar_seed_batch(const int32_t *d_seeds, size_t n, ranmar_state_t *d_out,
  * i the kernel forms P = t^{E_i} mod (t^97 + t^64 - 1) over Z/2^24 by
  * left-to-right square-and-multiply, applies x P(A) as sum_j b_j x_{j+k},
  * and sets c = (c_base - E_i d) mod m, pos = pos_base + E_i mod 2^64.
- * One 32-lane warp serves 16 streams, two lanes per stream; a batch of at
- * most RANMAR_SQUARE_WARP_AUTO_MAX streams instead gives each stream a whole
- * warp (its chain of squarings is then ~5 times shorter).  Same results.
+ * One 32-lane warp serves 16 streams, two lanes per stream (lane 0 forms
+ * the low half of each square, lane 1 the high half from the reversed
+ * polynomial); a batch of at most RANMAR_SQUARE_WARP_AUTO_MAX streams
+ * instead gives each stream a whole warp.  That cuts the LATENCY of one
+ * squaring about 5 times (each stream's dependent chain is spread over 32
+ * lanes instead of 2), not the work: the warp mapping executes about three
+ * times the instructions per stream, so large batches keep the lane pairs.
+ * Same results either way.
  * d_out must not overlap d_base.  n = 0 is a no-op.
  * Errors: RANMAR_EINVAL (null pointer with n > 0, misaligned states,
  * overlapping in/out), RANMAR_ERANGE (exp_words not in 1..5, n_base = 0, or
@@ -636,7 +641,12 @@ int ranmar_batch_tune(ranmar_batch_t *b, int f32, ranmar_state_t *d_states, size
  *     enqueued).
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before
- *     any stream capture.
+ *     any stream capture.  The address is cached for the life of the
+ *     process and does not survive cudaDeviceReset: after resetting a
+ *     device, do not call this function on it again.
+ *   - d_order may be NULL (descriptors only, no visiting order); d_total
+ *     may be NULL (the grand total then goes only to the internal array).
+ *     n == 0 enqueues nothing except *d_total = 0 when d_total is given.
  *   - All calls share the one array and each call clears the parts that must
  *     start at zero; two calls whose work overlaps on the GPU (different
  *     streams, or different host threads) race and give wrong results.
