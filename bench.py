@@ -76,8 +76,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-extras", action="store_true", help="skip the side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--serve-seconds", type=float, default=5.0,
-                   help="duration of the serving run (the recipe's full run is 60 s)")
+    p.add_argument("--serve-seconds", type=float, default=60.0,
+                   help="duration of the serving run (60 s: the recipe's full request list)")
     p.add_argument("--case", choices=["partitioned", "uneven", "large", "plan"],
                    default="partitioned",
                    help="partitioned = the benchmark; uneven / large run only that workload's "
@@ -258,6 +258,188 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def measure_probes(torch, dev, stream):
+    """Ceilings measured on this GPU in this run, before the timed region:
+    the store-only HBM bandwidth (what generation needs), the 32-bit IMAD
+    rate (what the jump needs), and the two ways results reach host memory:
+    a pinned 1 GiB device-to-host copy, and stores from the SMs straight into
+    pinned host memory (mapped).  Each figure is the mean of back-to-back
+    launches between two CUDA events on `stream`, after one untimed launch."""
+    from paper_2512_00093_gb300 import binding as bd
+    from paper_2512_00093_gb300 import build as rbuild
+    P = ctypes.CDLL(rbuild.PROBE_LIB)
+    P.ranmar_probe_write.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                     ctypes.c_void_p]
+    P.ranmar_probe_imad.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
+                                    ctypes.c_void_p]
+
+    def mean_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    res = {}
+    words = 2**30                                            # 4 GiB per launch
+    buf = torch.empty(words, dtype=torch.int32, device=dev)
+    ms_w = mean_ms(lambda: P.ranmar_probe_write(buf.data_ptr(), words, SMS * 8,
+                                                stream.cuda_stream), 4)
+    res["write_only_gbs"] = 4 * words / (ms_w * 1e-3) / 1e9
+    del buf
+    sink = torch.empty(SMS * 8 * 256, dtype=torch.int32, device=dev)
+    iters = 4096
+    ms_i = mean_ms(lambda: P.ranmar_probe_imad(sink.data_ptr(), SMS * 8, iters,
+                                               stream.cuda_stream), 3)
+    res["imad_tops"] = SMS * 8 * 256 * iters * 16 / (ms_i * 1e-3) / 1e12
+    del sink
+    P.ranmar_probe_dadd.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
+                                    ctypes.c_void_p]
+    dsink = torch.empty(SMS * 8 * 256, dtype=torch.float64, device=dev)
+    diters = 512
+    ms_d = mean_ms(lambda: P.ranmar_probe_dadd(dsink.data_ptr(), SMS * 8, diters,
+                                               stream.cuda_stream), 3)
+    res["dadd_tops"] = SMS * 8 * 256 * diters * 16 / (ms_d * 1e-3) / 1e12
+    del dsink
+    n1g = 2**28                                              # 1 GiB
+    d = torch.empty(n1g, dtype=torch.int32, device=dev)
+    h = torch.empty(n1g, dtype=torch.int32).pin_memory()
+    with torch.cuda.stream(stream):
+        ms_c = mean_ms(lambda: h.copy_(d, non_blocking=True), 3)
+    res["d2h_copy_gbs"] = 4 * n1g / (ms_c * 1e-3) / 1e9
+    hp = bd.host_device_pointer(h)
+    ms_z = mean_ms(lambda: P.ranmar_probe_write(hp, n1g, SMS * 8, stream.cuda_stream), 3)
+    res["zero_copy_write_gbs"] = 4 * n1g / (ms_z * 1e-3) / 1e9
+    res["method"] = ("mean of back-to-back launches: store-only kernel over 4 GiB of HBM (x4); "
+                     "independent mad.lo.u32 chains on 8 CTAs per SM (x3); independent "
+                     "double adds (x3); pinned 1 GiB "
+                     "cudaMemcpyAsync device-to-host (x3); the store-only kernel into 1 GiB of "
+                     "mapped pinned host memory (x3)")
+    del d, h
+    return res
+
+
+def e2e_line(world, n, count, ms_copy, ok_copy, ms_zc, ok_zc, probes) -> dict:
+    """The end-to-end figure: the plan step through the binding with host
+    buffers, by the faster of the two ways results reach host memory, as a
+    fraction of that way's ceiling measured in the same run."""
+    bytes_out = n * count * 4
+    paths = {
+        "copy": {"ms_per_step": ms_copy, "checked": ok_copy,
+                 "link_gbs": probes["d2h_copy_gbs"],
+                 "note": "generation into HBM, then the 1 GiB result copied to pinned host "
+                         "memory on a third stream (double-buffered)"},
+        "zero_copy": {"ms_per_step": ms_zc, "checked": ok_zc,
+                      "link_gbs": probes["zero_copy_write_gbs"],
+                      "note": "generation storing straight into pinned host memory "
+                              "(ranmar_host_device_pointer), no copy"}}
+    for v in paths.values():
+        v["gbs"] = bytes_out / (v["ms_per_step"] * 1e-3) / 1e9
+        v["link_frac"] = v["gbs"] / v["link_gbs"]
+    best = min(paths, key=lambda k: paths[k]["ms_per_step"])
+    b = paths[best]
+    return {"value": world * n * count / (b["ms_per_step"] * 1e-3), "unit": UNIT,
+            "h2d_bytes_per_step": 400, "d2h_bytes_per_step": bytes_out,
+            "ms_per_step": b["ms_per_step"], "checked": b["checked"], "path": best,
+            "link_gbs": max(probes["d2h_copy_gbs"], probes["zero_copy_write_gbs"]),
+            "link_frac": b["gbs"] / max(probes["d2h_copy_gbs"], probes["zero_copy_write_gbs"]),
+            "paths": paths,
+            "note": "the plan step through the binding with the base state copied in from "
+                    "pinned host memory every step and the whole 1 GiB result delivered to "
+                    "pinned host memory every step; bound by the GPU-to-CPU link, whose "
+                    "ceilings (a plain pinned copy, SM stores into mapped host memory) are "
+                    "measured in the same run"}
+
+
+def config4(rm, torch, dev, stream, alu_peak, alu_derived, steps=5) -> dict:
+    """Large jumps as one step of the whole path: 16,384 streams at k*J for
+    J = 2^120 + 12,345 (E = kJ up to 2^134), start states by the paper's
+    left-to-right square-and-multiply, then 1,024 u24 outputs per stream with
+    write-back; step i takes k = i*16,384 + 0..16,383 (fresh streams).  The
+    table, plan and period-reduced jumps are labelled variants beside it."""
+    from paper_2512_00093_gb300.workloads import LargeJumps
+    lj = LargeJumps()
+    n, cnt = lj.n_streams, lj.count
+    base = rm.seed(lj.seed).to(dev)
+    st = torch.empty((n, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+    out = torch.empty(n * cnt, dtype=torch.int32, device=dev)
+    desc = rm.make_desc(np.arange(n), np.arange(n) * cnt, cnt, rm.DESC_WRITE_BACK, device=dev)
+    for i in (steps + 10, steps + 11):               # warm-up on other streams
+        rm.partition(base, lj.J, i * n, n, out=st)
+        rm.generate_u24(st, desc, out)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for i in range(steps):
+        ev[i][0].record(stream)
+        rm.partition(base, lj.J, i * n, n, out=st)
+        ev[i][1].record(stream)
+        rm.generate_u24(st, desc, out)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    step_ms = ev[0][0].elapsed_time(ev[-1][2]) / steps
+    jump_ms = statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for i in range(steps))
+    gen_ms = statistics.mean(ev[i][1].elapsed_time(ev[i][2]) for i in range(steps))
+    exps = [(i * n + k) * lj.J for i in range(steps) for k in range(n)]
+    macs = jump_macs(exps) / steps                   # per step (per launch)
+    res = {"workload": "16,384 streams at k*(2^120 + 12,345), square-and-multiply jump + 1,024 "
+                       "u24 outputs each with write-back; step i: k = i*16,384 + 0..16,383",
+           "steps": steps, "step_ms": step_ms, "jump_ms": jump_ms, "generate_ms": gen_ms,
+           "jumps_per_s": n / (jump_ms * 1e-3), "step_jumps_per_s": n / (step_ms * 1e-3),
+           "outputs_per_s": n * cnt / (step_ms * 1e-3),
+           "roofline_jump": {"kernel": "jump_kernel (square-and-multiply, mirrored lane pairs)",
+                             "bound": "alu", "unit": "Tmul-add/s",
+                             "algorithmic_macs": macs,
+                             "achieved": macs / (jump_ms * 1e-3) / 1e12, "peak": alu_peak,
+                             "frac": macs / (jump_ms * 1e-3) / 1e12 / alu_peak,
+                             "peak_source": "measured in this run: independent mad.lo.u32 chains",
+                             "frac_of_derived": macs / (jump_ms * 1e-3) / 1e12 / alu_derived,
+                             "macs_per_stream": "(bitlen(E) - 7) x 4,753 (symmetric squares) + "
+                                                "9,409 (application)"}}
+    # states of the last step: the same numbers by the fixed-base table jump
+    chk = rm.Table()
+    res["states_identical_to_table_jump"] = bool(torch.equal(
+        rm.partition(base, lj.J, (steps - 1) * n, n),
+        chk.partition(base, lj.J, (steps - 1) * n, n)))
+
+    def best_ms(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t = float("inf")
+        for _ in range(reps):
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = min(t, a.elapsed_time(b))
+        return t
+
+    var = {}
+    ms = best_ms(lambda: chk.partition(base, lj.J, 0, n, out=st))
+    var["table"] = {"jump_ms": ms, "jumps_per_s": n / (ms * 1e-3),
+                    "note": "fixed-base table: products of rows t^{d 2^{8j}} over the base-256 "
+                            "digits of kJ (not the paper's method; identical states)"}
+    lplan = rm.Plan(chk, lj.J, n)
+    ms = best_ms(lambda: lplan.partition(base, 0, n, out=st))
+    var["plan"] = {"jump_ms": ms, "jumps_per_s": n / (ms * 1e-3), "status": lplan.status(),
+                   "note": "partition plan: 256 streams from the powers of t^J, the rest by one "
+                           "tensor-core level of jump matrices (identical states)"}
+    lplan.close()
+    red = rm.JUMP_REDUCE_PERIOD
+    ms = best_ms(lambda: rm.partition_ex(base, lj.J, 0, n, table=None, flags=red, out=st))
+    var["square_multiply_period_reduced"] = {
+        "jump_ms": ms, "jumps_per_s": n / (ms * 1e-3),
+        "note": "the paper's square-and-multiply on E mod (2^97 - 1) 2^23 (the order of t), "
+                "c by E mod m: identical states, about 10 fewer squarings"}
+    res["variants"] = var
+    chk.close()
+    return res
+
+
 def run_ours(args):
     import torch
     import paper_2512_00093_gb300 as rm
@@ -274,10 +456,10 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    from paper_2512_00093_gb300.shard import max_over_ranks, shard
+    from paper_2512_00093_gb300.shard import max_over_ranks, step_k0
     w = Partitioned()
     count = w.count
-    k0, n = shard(rank, world, args.streams)   # disjoint blocks of streams per rank
+    n = args.streams                           # streams per rank and step
     stream = torch.cuda.current_stream()
 
     base = rm.seed(w.seed).to(dev)
@@ -292,9 +474,10 @@ def run_ours(args):
     table_build_ms = (time.perf_counter() - tb0) * 1e3
 
     # Each step is one full pass (jump + generate) over a fresh batch of
-    # streams: batch i of rank r is k = (i * world + r) * n + 0..n-1.
+    # streams: batch i of rank r is k = (i * world + r) * n + 0..n-1, so no
+    # stream index is used twice by any rank or step.
     def k0_of(i):
-        return (i * world + rank) * n
+        return step_k0(i, rank, world, n)
 
     def serial_step(i):
         table.partition(base, w.J, k0_of(i), n, out=states)
@@ -303,6 +486,7 @@ def run_ours(args):
     for i in range(args.warmup):
         serial_step(i)
     torch.cuda.synchronize()
+    probes = measure_probes(torch, dev, stream)    # this GPU's ceilings, before the clock
 
     # ---- serial steps: per-kernel times for the roofline ---------------------
     K = args.steps
@@ -324,6 +508,28 @@ def run_ours(args):
     t_gen = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
     serial_ms = max_over_ranks((sum(t_jump) + sum(t_gen)) / K, dist, dev)
 
+    # ---- the generation kernel alone, back to back: NB launches on NB fresh
+    # batches of states (new streams, jumped beforehand), no flush between
+    # them.  A single flushed launch ends with tens of MB of its outputs still
+    # dirty in L2, written back after its closing event; back to back, each
+    # launch's write-back lands inside the next launch, so the mean per launch
+    # carries it (all but the last launch's tail, 1/NB of it).
+    NB = 8
+    gen_states = [torch.empty_like(states) for _ in range(NB)]
+    for b in range(NB):
+        table.partition(base, w.J, k0_of(8 * K + 60 + b), n, out=gen_states[b])
+    outs_bb = [out, torch.empty_like(out)]
+    rm.generate_u24(gen_states[0].clone(), desc, outs_bb[1])
+    torch.cuda.synchronize()
+    bb0, bb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bb0.record(stream)
+    for b in range(NB):
+        rm.generate_u24(gen_states[b], desc, outs_bb[b % 2])
+    bb1.record(stream)
+    torch.cuda.synchronize()
+    gen_bb_ms = max_over_ranks(bb0.elapsed_time(bb1) / NB, dist, dev)
+    del gen_states, outs_bb[1]
+
     # ---- timed steps (the measured throughput): partition plan + generation.
     # Per step: the first 256 streams by the table jump (on a side stream, so
     # that it runs while the previous step generates), the
@@ -340,7 +546,11 @@ def run_ours(args):
     main_s = torch.cuda.Stream(dev)
     sD = torch.cuda.Stream(dev)
 
-    def plan_steps(first, steps, d_base=None, h_base=None, d2h=None):
+    def plan_steps(first, steps, d_base=None, h_base=None, d2h=None, zc=None):
+        """`steps` plan steps on new batches.  End to end: h_base (pinned) is
+        copied in every step; d2h = (host, device) buffers: generate into HBM,
+        then copy to pinned host memory on a third stream; zc = pinned host
+        buffers the generation stores into directly (mapped, no copy)."""
         evG, evD = [], []
         for j in range(steps):
             b = j % 2
@@ -359,6 +569,8 @@ def run_ours(args):
             main_s.wait_event(e)
             plan.expand(buf, n, stream=main_s)
             o = out2
+            if zc is not None:
+                o = zc[b]
             if d2h is not None:
                 o = d2h[1][b]
                 if j >= 2:
@@ -510,10 +722,28 @@ def run_ours(args):
     side.wait_event(last)
     e1.record(side)
     torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / n_e2e, dist, dev)
+    ms_e2e_copy = max_over_ranks(e0.elapsed_time(e1) / n_e2e, dist, dev)
     lastb = (n_e2e - 1) % 2
-    ok_e2e = bool(np.array_equal(h_outs[lastb][:2].numpy(), d_outs[lastb][:2].cpu().numpy()))
-    del d_outs[1], h_outs
+    ok_copy = bool(np.array_equal(h_outs[lastb][:2].numpy(), d_outs[lastb][:2].cpu().numpy()))
+    del d_outs[1]
+    # the same steps storing straight into pinned host memory (no copy)
+    plan_steps(4 * K + 9 + n_e2e, 2, d_bases, h_base, zc=h_outs)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    z0, z1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    z0.record(side)
+    first_zc = 4 * K + 11 + n_e2e
+    last = plan_steps(first_zc, n_e2e, d_bases, h_base, zc=h_outs)
+    side.wait_event(last)
+    z1.record(side)
+    torch.cuda.synchronize()
+    ms_e2e_zc = max_over_ranks(z0.elapsed_time(z1) / n_e2e, dist, dev)
+    # check: the last zero-copy batch against the same batch generated in HBM
+    plan_steps(first_zc + n_e2e - 1, 1)
+    torch.cuda.synchronize()
+    ok_zc = bool(np.array_equal(h_outs[(n_e2e - 1) % 2][:2].numpy(), out2[:2].cpu().numpy()))
+    del h_outs
     # the paper's left-to-right square-and-multiply on the same streams
     sm_states = torch.empty_like(states)
     rm.partition(base, w.J, k0_of(0), n, out=sm_states)
@@ -543,10 +773,12 @@ def run_ours(args):
             peaks = json.load(f)
     except (OSError, ValueError):
         pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_copy = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    hbm_peak = probes["write_only_gbs"]            # generation only stores
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = SMS * IMAD_PER_CLK_SM * sm_max * 1e6 / 1e12       # T mul-add / s
+    alu_derived = SMS * IMAD_PER_CLK_SM * sm_max * 1e6 / 1e12    # T mul-add / s
+    alu_peak = probes["imad_tops"]                               # measured in this run
     jump_ms = statistics.mean(t_jump)
     gen_ms = statistics.mean(t_gen)
     gen_bytes = n * count * 4 + n * (400 + 400 + 24)
@@ -560,17 +792,33 @@ def run_ours(args):
     tg = traffic_for("generate_desc_kernel", gen_sha)
     tp = traffic_for("plan_level_mma2_kernel",
                      source_sha("plan_mma2.cuh", "plan_mma.cuh", "plan.cuh", "ranmar_device.cuh"))
+    gen_gbs = gen_bytes / (gen_bb_ms * 1e-3) / 1e9
     roof_gen = {"kernel": "generate_desc_kernel<u24>", "bound": "hbm",
-                "achieved": gen_bytes / (gen_ms * 1e-3) / 1e9, "peak": hbm_peak,
-                "unit": "GB/s", "frac": gen_bytes / (gen_ms * 1e-3) / 1e9 / hbm_peak,
-                "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "achieved": gen_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gen_gbs / hbm_peak,
+                "peak_source": "measured in this run: store-only kernel over 4 GiB "
+                               "(mean of 4 back-to-back launches), the generation's own bound",
+                "peak_copy": hbm_copy, "frac_of_copy": gen_gbs / hbm_copy,
+                "peak_copy_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes": gen_bytes,
-                "traffic": tg["bytes_per_launch"] if tg else None,
-                "avg_launch_ms": gen_ms}
+                "avg_launch_ms": gen_bb_ms,
+                "timing": f"mean of {NB} back-to-back launches on fresh batches, no flush "
+                          "between them (each launch's L2 write-back lands in the next)",
+                "flushed_single_launch_ms": gen_ms,
+                "traffic": tg["bytes_per_launch"] if tg else None}
+    if tg and tg.get("duration_us"):
+        ncu_gbs = tg["bytes_per_launch"] / (tg["duration_us"] * 1e-6) / 1e9
+        roof_gen["ncu"] = {"dram_gbs": ncu_gbs, "frac": ncu_gbs / hbm_peak,
+                           "duration_us": tg["duration_us"],
+                           "note": "DRAM bytes read + written during one full-size launch / "
+                                   "its ncu duration (profiles/traffic.json)"}
     roof_jump = {"kernel": "jump_table_kernel (partition, fixed-base table)", "bound": "alu",
                  "achieved": jmacs / (jump_ms * 1e-3) / 1e12, "peak": alu_peak,
                  "unit": "Tmul-add/s", "frac": jmacs / (jump_ms * 1e-3) / 1e12 / alu_peak,
-                 "peak_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {sm_max:.0f} MHz",
+                 "peak_source": "measured in this run: independent mad.lo.u32 chains",
+                 "peak_derived": alu_derived,
+                 "peak_derived_source": f"{SMS} SMs x {IMAD_PER_CLK_SM} IMAD/clk x "
+                                        f"{sm_max:.0f} MHz",
                  "algorithmic_macs": jmacs,
                  "traffic": tj["bytes_per_launch"] if tj else None,
                  "avg_launch_ms": jump_ms}
@@ -592,7 +840,8 @@ def run_ours(args):
                  "note": "one launch (510 tiles x matrices over 152 SMs)"}
     fused_bytes = n * count * 4 + n * 400
     roof_fused = {"kernel": "partition_generate_kernel<u24>", "bound": "hbm",
-                  "ms": ms_fused, "frac": fused_bytes / (ms_fused * 1e-3) / 1e9 / hbm_peak}
+                  "ms": ms_fused, "frac": fused_bytes / (ms_fused * 1e-3) / 1e9 / hbm_peak,
+                  "peak": "in-run store-only"}
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -627,21 +876,21 @@ def run_ours(args):
             "note": "the paper's left-to-right square-and-multiply, per stream"},
         "generate_outputs_per_s": n * count / (gen_ms * 1e-3),
         "clocks": clk,
-        "e2e": {"value": world * n * count / (ms_e2e * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": 400, "d2h_bytes_per_step": n * count * 4,
-                "ms_per_step": ms_e2e, "checked": ok_e2e,
-                "note": "the plan step through the binding, with the base state from pinned "
-                        "host memory and the whole result copied to pinned host memory every "
-                        "step (copies on their own streams, double-buffered)"},
+        "e2e": e2e_line(world, n, count, ms_e2e_copy, ok_copy, ms_e2e_zc, ok_zc, probes),
         "gpu_launches": 3 * K,
         "library": rbuild.LIB,
         "paper_cpu_context": paper_cpu_context(),
     }
 
+    try:
+        result["config4"] = config4(rm, torch, dev, stream, alu_peak, alu_derived)
+    except Exception as e:  # noqa: BLE001
+        result["config4"] = {"error": f"{type(e).__name__}: {e}"}
+    result["probes"] = probes
     if not args.no_extras:
         # side measurements never cost the headline line: errors are recorded
         try:
-            result["extras"] = extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak)
+            result["extras"] = extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak, probes)
         except Exception as e:  # noqa: BLE001
             result["extras"] = {"error": f"{type(e).__name__}: {e}"}
         try:
@@ -671,7 +920,7 @@ def run_ours(args):
     return 0
 
 
-def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
+def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak, probes):
     """Side measurements: large jumps (J = 2^120 + 12345), batched vs one
     launch per stream on the uneven-length shape, and the probe ceilings."""
     from paper_2512_00093_gb300 import build as rbuild
@@ -713,33 +962,17 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
         cap.graph.close()
         return best
 
-    # large jumps (J = 2^120 + 12345, E = k J up to 2^134): both methods
+    # large jumps (J = 2^120 + 12345, E = k J up to 2^134): the paper's
+    # square-and-multiply, the fixed-base table and the period-reduced
+    # variant are timed in the top-level config4 step; here the plan from
+    # graph replay and every stream from the plan's powers of t^J
     lj = LargeJumps()
     table = rm.Table()
     base = rm.seed(lj.seed).to(dev)
     st = torch.empty((lj.n_streams, rm.STATE_WORDS), dtype=torch.int32, device=dev)
-    exps_l = [k * lj.J for k in range(lj.n_streams)]
-    ms = timed(lambda: rm.partition(base, lj.J, 0, lj.n_streams, out=st))
-    macs = jump_macs(exps_l)
-    ms_t = timed(lambda: table.partition(base, lj.J, 0, lj.n_streams, out=st))
-    macs_t = table_macs(exps_l)
-    red = rm.JUMP_REDUCE_PERIOD
-    ms_tr = timed(lambda: rm.partition_ex(base, lj.J, 0, lj.n_streams, table=table, flags=red,
-                                          out=st))
-    ms_sr = timed(lambda: rm.partition_ex(base, lj.J, 0, lj.n_streams, table=None, flags=red,
-                                          out=st))
-    res["large_jumps_period_reduced"] = {
-        "note": "labelled variant, not the paper's method: the polynomial part uses "
-                "E mod (2^97 - 1) 2^23 (the order of t); identical states",
-        "table": {"ms": ms_tr, "jumps_per_s": lj.n_streams / (ms_tr * 1e-3)},
-        "square_multiply": {"ms": ms_sr, "jumps_per_s": lj.n_streams / (ms_sr * 1e-3)}}
     res["large_jumps"] = {"streams": lj.n_streams, "J": "2^120+12345",
-                          "square_multiply": {"ms": ms, "jumps_per_s": lj.n_streams / (ms * 1e-3),
-                                              "tmacs_per_s": macs / (ms * 1e-3) / 1e12,
-                                              "alu_frac": macs / (ms * 1e-3) / 1e12 / alu_peak},
-                          "table": {"ms": ms_t, "jumps_per_s": lj.n_streams / (ms_t * 1e-3),
-                                    "tmacs_per_s": macs_t / (ms_t * 1e-3) / 1e12,
-                                    "alu_frac": macs_t / (ms_t * 1e-3) / 1e12 / alu_peak}}
+                          "note": "square-and-multiply, table and period-reduced jumps: see "
+                                  "config4"}
     # the polynomial part alone, t^J mod phi (the paper's Table 2 times one
     # such power on a CPU): one power (the latency of one warp's chain) and
     # 16,384 at once (throughput), by the paper's square-and-multiply
@@ -930,9 +1163,23 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
         fv[name] = {"ms": ms_f, "outputs_per_s": tot2 / (ms_f * 1e-3)}
     fv["speedup_modular_f32_over_float_f32"] = fv["float_alg1_f32"]["ms"] / fv["modular_f32"]["ms"]
     fv["speedup_modular_f32_over_float_f64"] = fv["float_alg1_f64"]["ms"] / fv["modular_f32"]["ms"]
-    fv["note"] = ("generation of 2^28 outputs; on the GPU both forms are store-bound, "
-                  "so the paper's CPU speedup of the modular form shows up only as "
-                  "fewer instructions per output (and f64 doubles the bytes)")
+    fv["note"] = ("generation of 2^28 outputs.  The integer (Algorithm 2) and float32 "
+                  "(Algorithm 1) forms are both store-bound at the same time, so the paper's "
+                  "CPU speedup of the modular form does not appear on the GPU.  The float64 "
+                  "form is bound by GB300's FP64 rate, not by its bytes (twice the bytes "
+                  "would cost 2x, not ~27x): see fp64_rate")
+    # the FP64 bound: Algorithm 1 in double does about 3 dependent FP64
+    # add/compare/select operations per output on a chip with a small FP64 rate
+    fp64_ops = 6 * tot2      # per output: u_i - u_j, c - cd, uni - c, three conditional adds
+    fv["fp64_rate"] = {"outputs_per_s": fv["float_alg1_f64"]["outputs_per_s"],
+                       "ratio_to_f32": fv["float_alg1_f64"]["ms"] / fv["float_alg1_f32"]["ms"],
+                       "bytes_ratio": 2.0,
+                       "fp64_ops_per_output": 6,
+                       "fp64_adds_per_s": fp64_ops / (fv["float_alg1_f64"]["ms"] * 1e-3),
+                       "probe_dadd_per_s": probes["dadd_tops"] * 1e12,
+                       "bound_ms": fp64_ops / (probes["dadd_tops"] * 1e12) * 1e3,
+                       "note": "bound_ms = 6 double adds per output at the measured FP64 add "
+                               "rate; the f64 kernel's time against it shows the FP64 bound"}
     res["float_vs_modular"] = fv
     del o32, o64, st0
 
@@ -1031,25 +1278,6 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak):
     except Exception as ex_:  # noqa: BLE001
         res["general_lags"] = {"error": f"{type(ex_).__name__}: {ex_}"}
 
-    # probes: write-only HBM ceiling and IMAD ceiling on this GPU
-    try:
-        P = ctypes.CDLL(rbuild.PROBE_LIB)
-        P.ranmar_probe_write.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
-                                         ctypes.c_void_p]
-        P.ranmar_probe_imad.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
-                                        ctypes.c_void_p]
-        buf = torch.empty(2**30, dtype=torch.int32, device=dev)     # 4 GiB
-        ms_w = timed(lambda: P.ranmar_probe_write(buf.data_ptr(), buf.numel(), SMS * 8,
-                                                  stream.cuda_stream))
-        del buf
-        sink = torch.empty(SMS * 8 * 256, dtype=torch.int32, device=dev)
-        iters = 4096
-        ms_i = timed(lambda: P.ranmar_probe_imad(sink.data_ptr(), SMS * 8, iters,
-                                                 stream.cuda_stream))
-        res["probes"] = {"write_only_gbs": 4 * 2**30 / (ms_w * 1e-3) / 1e9,
-                         "imad_tops": SMS * 8 * 256 * iters * 16 / (ms_i * 1e-3) / 1e12}
-    except OSError as e:
-        res["probes"] = {"error": str(e)}
     return res
 
 
@@ -1060,7 +1288,7 @@ def serving(rm, torch, seconds):
     consumed by the on-device checksum.  Comparator: every request alone with
     plain launches, on the first requests of the same stream."""
     from oracle import oracle
-    from paper_2512_00093_gb300.serve import Engine, make_requests
+    from paper_2512_00093_gb300.serve import Engine, make_requests, summarize
     from paper_2512_00093_gb300.workloads import Serving
     w = Serving()
     t, seeds, ks, counts, f32 = w.requests(duration=seconds)
@@ -1083,12 +1311,28 @@ def serving(rm, torch, seconds):
            "jumps": eng.stats["jumps"], "resumed": eng.stats["resumed"],
            "evicted": eng.stats["evicted"], "verified": f"{ok}/{len(pick)} sampled requests",
            "budget_gb": 40}
+    res["latency_note"] = ("p50/p99: the GPU event that ends a request's iteration minus its "
+                           "arrival; host_p50/host_p99: when the scheduler loop saw that event "
+                           "complete, minus arrival")
+    # Comparator on the same requests: the first nplain of the list, each alone
+    # with plain launches, arriving at the recipe's times.  It cannot keep up
+    # with 20k req/s, so its latencies are queueing; its sustained rate is
+    # reported beside the engine's figures for the same requests (taken from
+    # the full run above).
     nplain = min(len(reqs), 2000)
     plain = make_requests(t[:nplain], seeds[:nplain], ks[:nplain], counts[:nplain],
                           f32[:nplain], w.J)
     ps = eng.run_plain(plain, realtime=True, max_wait=seconds * 10 + 120)
-    res["plain_per_request"] = {**ps, "note": f"first {nplain} requests, each alone: one jump "
-                                              "launch + one one-warp generation launch"}
+    ok_plain = sum(int(a.checksum == b.checksum) for a, b in zip(plain, reqs[:nplain]))
+    same = summarize(reqs[:nplain])
+    res["plain_per_request"] = {
+        **ps, "sustained_req_per_s": nplain / ps["span_s"] if ps["span_s"] else None,
+        "saturated": bool(ps["span_s"] and nplain / ps["span_s"] < 0.9 * w.rate),
+        "checksums_equal_engine": f"{ok_plain}/{nplain}",
+        "engine_on_same_requests": same,
+        "note": f"the first {nplain} requests of the same list, each alone: one jump launch + "
+                "one one-warp generation launch; when it cannot sustain the offered rate its "
+                "latencies are queueing"}
     eng.close()
     return res
 

@@ -4,7 +4,8 @@
 // ceiling for generation, which only stores).  ranmar_probe_imad: independent
 // chains of 32-bit multiply-add (the integer-pipe ceiling for the jump).
 // Neither is part of the generator; both are timed by the caller with CUDA
-// events on `stream`.
+// events on `stream`.  ranmar_probe_dadd: independent chains of
+// double-precision adds (the FP64 rate that bounds Algorithm 1 in double).
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -37,6 +38,24 @@ __global__ void __launch_bounds__(256) probe_imad_kernel(uint32_t* __restrict__ 
   if (s == 0x9E3779B9u) sink[t] = s;   // practically never; keeps the chains live
 }
 
+// 16 independent double-precision add chains per thread, `iters` rounds.
+__global__ void __launch_bounds__(256) probe_dadd_kernel(double* __restrict__ sink,
+                                                         uint32_t iters, double step) {
+  double a[16];
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) a[k] = static_cast<double>(t + k) * 0.5;
+#pragma unroll 1
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = a[k] + step;
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) s += a[k];
+  if (s == -1.0) sink[t] = s;   // never (all terms positive); keeps the chains live
+}
+
 }  // namespace
 
 extern "C" {
@@ -52,6 +71,14 @@ int ranmar_probe_write(void* d_out, uint64_t n_words, uint32_t blocks, void* str
 int ranmar_probe_imad(uint32_t* d_sink, uint32_t blocks, uint32_t iters, void* stream) {
   if (!d_sink) return -1;
   probe_imad_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_sink, iters, 7u);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// Double-precision adds issued: blocks * 256 * iters * 16.
+int ranmar_probe_dadd(double* d_sink, uint32_t blocks, uint32_t iters, void* stream) {
+  if (!d_sink) return -1;
+  probe_dadd_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_sink, iters,
+                                                                          0.25);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
