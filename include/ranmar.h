@@ -307,7 +307,7 @@ int ranmar_table_set_ctas_per_sm(ranmar_table_t *t, int ctas_per_sm);
 /* The square-and-multiply jumps (ranmar_jump, ranmar_jump_scatter,
  * ranmar_partition, ranmar_partition_ex without a table) and
  * ranmar_poly_power take a warp per stream up to this many streams. */
-#define RANMAR_SQUARE_WARP_AUTO_MAX 4096
+#define RANMAR_SQUARE_WARP_AUTO_MAX 1536
 int ranmar_table_set_jump_mapping(ranmar_table_t *t, int map);
 /* Device address of the rows (row j*256 + d, 100 words each), for checks. */
 int ranmar_table_rows(const ranmar_table_t *t, const uint32_t **d_rows);
@@ -624,6 +624,53 @@ int ranmar_batch_generate_f32(ranmar_batch_t *b, ranmar_state_t *d_states, size_
 int ranmar_batch_tune(ranmar_batch_t *b, int f32, ranmar_state_t *d_states, size_t n_states,
                       const ranmar_desc_t *d_desc, size_t n_desc, const uint32_t *d_order,
                       void *d_out, size_t out_len, ranmar_stream_t stream, float *best_ms);
+
+/*
+ * ranmar_batch_pack_split -- like ranmar_batch_pack, with every stream
+ * longer than `seg` outputs split into ceil(count / seg) pieces of at most
+ * seg outputs; piece q >= 1 of a stream starts from the stream's state
+ * jumped by q seg (Sec. 3.1: the jump by any E), so that the persistent
+ * kernel's warps share a long stream instead of one warp running it alone.
+ * The outputs of every stream stay where ranmar_batch_pack puts them
+ * (offsets = exclusive prefix sum of the counts).
+ * Inputs: d_counts (device, n uint64, n <= the batch's capacity); seg >= 1;
+ * n_extra = sum over the streams of max(0, ceil(count / seg) - 1), computed
+ * by the caller (which sizes the outputs by it).
+ * Outputs (device, caller-owned):
+ *   d_desc[0 .. n + n_extra): piece 0 of stream i at i (state_idx i), the
+ *     extra pieces in stream order from n on (extra piece e: state_idx
+ *     n + e); only a stream's last piece keeps RANMAR_DESC_WRITE_BACK from
+ *     `flags`;
+ *   d_src[e] = the stream of extra piece e; d_exp[2e], d_exp[2e+1] = the
+ *     little-endian jump exponent q seg of extra piece e;
+ *   *d_total = sum of the counts (may be NULL).
+ * To run a split batch: states d_states[0 .. n + n_extra) with the streams'
+ * states in [0, n); fill [n, n + n_extra) by ranmar_jump_tab(table,
+ * d_states, n, d_src, d_exp, 2, d_states + n, n_extra, NULL, n_extra, ...);
+ * ranmar_batch_generate_* over the n + n_extra descriptors (no order needed:
+ * no piece is longer than seg); with write-back, ranmar_batch_split_finish.
+ * Errors: RANMAR_EINVAL (NULL pointers, seg = 0, n = 0 with n_extra > 0,
+ * misalignment, foreign-device handle), RANMAR_ERANGE (n above capacity,
+ * n + n_extra >= 2^32).  Device: RANMAR_ST_OUT_RANGE in *d_status when the
+ * pieces do not number n_extra (pieces beyond n_extra are not written;
+ * descriptors for missing ones get count 0 and d_src UINT32_MAX).
+ * Not in the paper: load balance for the batched path.
+ */
+int ranmar_batch_pack_split(ranmar_batch_t *b, const uint64_t *d_counts, size_t n, uint64_t seg,
+                            size_t n_extra, uint32_t flags, ranmar_desc_t *d_desc,
+                            uint32_t *d_src, uint32_t *d_exp, uint64_t *d_total,
+                            uint32_t *d_status, ranmar_stream_t stream);
+
+/*
+ * ranmar_batch_split_finish -- after the generation of a split batch with
+ * write-back: copies the advanced state of each split stream's last piece
+ * (d_states[n + e]) back to the stream's own slot d_states[d_src[e]], so
+ * that the states end as ranmar_batch_pack + generate would leave them.
+ * Entries with d_src[e] >= n are skipped.  Asynchronous on `stream`.
+ * Errors: RANMAR_EINVAL (NULL or misaligned with n_extra > 0).
+ */
+int ranmar_batch_split_finish(ranmar_state_t *d_states, size_t n, const uint32_t *d_src,
+                              size_t n_extra, ranmar_stream_t stream);
 
 /*
  * ranmar_batch_pack_static -- the same result as ranmar_batch_pack, for

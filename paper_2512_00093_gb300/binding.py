@@ -74,6 +74,11 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_batch_set_config.argtypes = [_vp, ctypes.POINTER(BatchConfig)]
     lib.ranmar_batch_get_config.argtypes = [_vp, ctypes.POINTER(BatchConfig)]
     lib.ranmar_batch_pack.argtypes = [_vp, _vp, _sz, _u32, _vp, _vp, _vp, _vp]
+    lib.ranmar_batch_pack_split.argtypes = [_vp, _vp, _sz, _u64, _sz, _u32, _vp, _vp, _vp, _vp,
+                                            _vp, _vp]
+    lib.ranmar_batch_pack_split.restype = ctypes.c_int
+    lib.ranmar_batch_split_finish.argtypes = [_vp, _sz, _vp, _sz, _vp]
+    lib.ranmar_batch_split_finish.restype = ctypes.c_int
     for name in ("ranmar_batch_generate_u24", "ranmar_batch_generate_f32"):
         getattr(lib, name).argtypes = [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp, _vp]
     lib.ranmar_batch_tune.argtypes = [_vp, ctypes.c_int, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp,
@@ -318,7 +323,7 @@ JUMP_REDUCE_PERIOD = 1
 # ranmar_*_set_jump_mapping: lanes per stream of the table jumps
 JUMP_MAP_AUTO, JUMP_MAP_PAIR, JUMP_MAP_WARP = 0, 1, 2
 JUMP_WARP_AUTO_MAX = 8192
-SQUARE_WARP_AUTO_MAX = 4096    # the same for the square-and-multiply jumps and poly_power
+SQUARE_WARP_AUTO_MAX = 1536    # the same for the square-and-multiply jumps and poly_power
 
 
 def partition_ex(base: torch.Tensor, J: int, k0: int, n: int, table=None, flags: int = 0,
@@ -507,6 +512,47 @@ class Batch:
                                         _ptr(ordt), _ptr(total), _stream(stream)),
                "ranmar_batch_pack")
         return desc, ordt, total
+
+    @staticmethod
+    def split_extra(counts, seg: int) -> int:
+        """Extra pieces of a split pack: sum over the streams of
+        max(0, ceil(count / seg) - 1) (host counts, numpy or a list)."""
+        c = np.asarray(counts, dtype=np.int64)
+        return int(np.maximum(0, (c - 1) // int(seg)).sum()) if c.size else 0
+
+    def pack_split(self, counts: torch.Tensor, seg: int, n_extra: int, flags: int = 0,
+                   status=None, stream=None):
+        """ranmar_batch_pack_split: counts (n,) int64 on the device, streams longer
+        than seg cut into pieces -> (desc (n + n_extra, 3) int64, src (n_extra,) int32,
+        exps (n_extra, 2) int32, total (1,) int64).  n_extra from split_extra."""
+        _need(counts, torch.int64, "counts")
+        n = counts.numel()
+        dev = counts.device
+        desc = torch.empty((n + n_extra, DESC_WORDS64), dtype=torch.int64, device=dev)
+        src = torch.empty(max(1, n_extra), dtype=torch.int32, device=dev)[:n_extra]
+        exps = torch.empty((max(1, n_extra), 2), dtype=torch.int32, device=dev)[:n_extra]
+        total = torch.empty(1, dtype=torch.int64, device=dev)
+        if status is not None:
+            _need(status, torch.int32, "status")
+        _check(_lib().ranmar_batch_pack_split(self._h, _ptr(counts), n, int(seg), int(n_extra),
+                                              int(flags), _ptr(desc), _ptr(src) if n_extra else None,
+                                              _ptr(exps) if n_extra else None, _ptr(total),
+                                              _ptr(status), _stream(stream)),
+               "ranmar_batch_pack_split")
+        return desc, src, exps, total
+
+    @staticmethod
+    def split_finish(states, n: int, src, stream=None):
+        """ranmar_batch_split_finish: states[src[e]] = states[n + e] for the last
+        piece of each split stream (after a generation with write-back)."""
+        states = states.reshape(-1, STATE_WORDS)
+        _need(states, torch.int32, "states")
+        if src.numel() == 0:
+            return states
+        _need(src, torch.int32, "src")
+        _check(_lib().ranmar_batch_split_finish(_ptr(states), int(n), _ptr(src), src.numel(),
+                                                _stream(stream)), "ranmar_batch_split_finish")
+        return states
 
     def _gen(self, fn, dtype, states, desc, out, order, status, stream):
         states = states.reshape(-1, STATE_WORDS)

@@ -170,4 +170,156 @@ __global__ void __launch_bounds__(kScanThreads) pack_write(const uint64_t* __res
   }
 }
 
+// ---- Splitting long streams into pieces started by extra jumps ----------
+// A stream of count c > seg becomes ceil(c / seg) pieces of at most seg
+// outputs: piece 0 runs from the stream's own state, piece q >= 1 from that
+// state jumped by q seg (Sec. 3.1: a jump by any E), so the persistent kernel
+// never has one warp on a long stream while the others idle.  Layout of the
+// n + n_extra descriptors: piece 0 of stream i at i (state i), the extra
+// pieces in stream order from n on (extra piece e uses state n + e, and
+// src[e] = its stream, exp[e] = q seg as two words).  Only a stream's last
+// piece keeps the write-back flag.
+
+__device__ __forceinline__ uint64_t split_extra(uint64_t c, uint64_t seg) {
+  return c > seg ? (c - 1) / seg : 0;   // ceil(c / seg) - 1
+}
+
+// Pass 1: per-tile sums of the counts and of the extra pieces.
+__global__ void __launch_bounds__(kScanThreads) split_tile_sums(
+    const uint64_t* __restrict__ counts, uint64_t n, uint64_t seg,
+    uint64_t* __restrict__ tile_sums, uint64_t* __restrict__ tile_extra) {
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanTile;
+  uint64_t s = 0, x = 0;
+#pragma unroll
+  for (int j = 0; j < kScanPerThread; ++j) {
+    const uint64_t i = base + static_cast<uint64_t>(j) * kScanThreads + threadIdx.x;
+    if (i < n) {
+      const uint64_t c = counts[i];
+      s += c;
+      x += split_extra(c, seg);
+    }
+  }
+  uint64_t ts, tx;
+  (void)cta_exclusive_scan(s, &ts);
+  (void)cta_exclusive_scan(x, &tx);
+  if (threadIdx.x == 0) {
+    tile_sums[blockIdx.x] = ts;
+    tile_extra[blockIdx.x] = tx;
+  }
+}
+
+// Pass 2 (one CTA): exclusive scans of both tile arrays; *grand_total is the
+// sum of the counts.  If the extra pieces do not number n_extra, the status
+// gets RANMAR_ST_OUT_RANGE and the descriptors the caller sized for pieces
+// that do not exist become empty ones (count 0, stream index UINT32_MAX).
+__global__ void __launch_bounds__(kScanThreads) split_scan_tiles(
+    uint64_t* __restrict__ tile_sums, uint64_t* __restrict__ tile_extra, uint64_t n_tiles,
+    uint64_t n, uint64_t n_extra, uint64_t* __restrict__ grand_total,
+    ranmar_desc_t* __restrict__ desc, uint32_t* __restrict__ src, uint32_t* __restrict__ exp,
+    uint32_t* status) {
+  uint64_t carry = 0, xcarry = 0;
+#pragma unroll 1
+  for (uint64_t b0 = 0; b0 < n_tiles; b0 += kScanThreads) {
+    const uint64_t i = b0 + threadIdx.x;
+    const uint64_t v = i < n_tiles ? tile_sums[i] : 0;
+    const uint64_t w = i < n_tiles ? tile_extra[i] : 0;
+    uint64_t total, xtotal;
+    const uint64_t ex = cta_exclusive_scan(v, &total);
+    const uint64_t xex = cta_exclusive_scan(w, &xtotal);
+    if (i < n_tiles) {
+      tile_sums[i] = carry + ex;
+      tile_extra[i] = xcarry + xex;
+    }
+    carry += total;
+    xcarry += xtotal;
+  }
+  if (threadIdx.x == 0) *grand_total = carry;
+  if (xcarry != n_extra) {
+    if (threadIdx.x == 0) flag_status(status, RANMAR_ST_OUT_RANGE);
+    for (uint64_t e = xcarry + threadIdx.x; e < n_extra; e += kScanThreads) {
+      ranmar_desc_t d;
+      d.state_idx = static_cast<uint32_t>(n + e);
+      d.flags = 0;
+      d.out_offset = 0;
+      d.count = 0;
+      desc[n + e] = d;
+      src[e] = 0xFFFFFFFFu;
+      exp[2 * e] = 0u;
+      exp[2 * e + 1] = 0u;
+    }
+  }
+}
+
+// Pass 3: the pieces' descriptors, and for the extra pieces their stream and
+// jump exponent.
+__global__ void __launch_bounds__(kScanThreads) split_write(
+    const uint64_t* __restrict__ counts, uint64_t n, uint64_t seg, uint64_t n_extra,
+    const uint64_t* __restrict__ tile_off, const uint64_t* __restrict__ tile_xoff, uint32_t flags,
+    ranmar_desc_t* __restrict__ desc, uint32_t* __restrict__ src, uint32_t* __restrict__ exp) {
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanTile;
+  // Thread t owns counts base + 4t .. 4t+3 so that its local scans are serial.
+  uint64_t c[kScanPerThread], x[kScanPerThread];
+  uint64_t s = 0, xs = 0;
+#pragma unroll
+  for (int j = 0; j < kScanPerThread; ++j) {
+    const uint64_t i = base + static_cast<uint64_t>(threadIdx.x) * kScanPerThread + j;
+    c[j] = i < n ? counts[i] : 0;
+    x[j] = split_extra(c[j], seg);
+    s += c[j];
+    xs += x[j];
+  }
+  uint64_t total;
+  uint64_t off = tile_off[blockIdx.x] + cta_exclusive_scan(s, &total);
+  uint64_t xo = tile_xoff[blockIdx.x] + cta_exclusive_scan(xs, &total);
+  const uint32_t no_wb = flags & ~static_cast<uint32_t>(RANMAR_DESC_WRITE_BACK);
+#pragma unroll
+  for (int j = 0; j < kScanPerThread; ++j) {
+    const uint64_t i = base + static_cast<uint64_t>(threadIdx.x) * kScanPerThread + j;
+    if (i < n) {
+      ranmar_desc_t d;
+      d.state_idx = static_cast<uint32_t>(i);
+      d.flags = x[j] ? no_wb : flags;
+      d.out_offset = off;
+      d.count = c[j] < seg ? c[j] : seg;
+      desc[i] = d;
+#pragma unroll 1
+      for (uint64_t q = 1; q <= x[j]; ++q) {
+        const uint64_t e = xo + q - 1;
+        if (e >= n_extra) break;           // flagged by pass 2
+        const uint64_t start = q * seg;
+        const uint64_t left = c[j] - start;
+        d.state_idx = static_cast<uint32_t>(n + e);
+        d.flags = q == x[j] ? flags : no_wb;
+        d.out_offset = off + start;
+        d.count = left < seg ? left : seg;
+        desc[n + e] = d;
+        src[e] = static_cast<uint32_t>(i);
+        exp[2 * e] = static_cast<uint32_t>(start);
+        exp[2 * e + 1] = static_cast<uint32_t>(start >> 32);
+      }
+    }
+    off += c[j];
+    xo += x[j];
+  }
+}
+
+// After the generation: the last piece of every split stream wrote its
+// advanced state to its own slot n + e; copy it back to the stream's slot.
+__global__ void __launch_bounds__(kScanThreads) split_finish(ranmar_state_t* __restrict__ states,
+                                                             uint64_t n,
+                                                             const uint32_t* __restrict__ src,
+                                                             uint64_t n_extra) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t e = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n_extra;
+       e += stride) {
+    const uint32_t i = src[e];
+    if (i >= n) continue;
+    if (e + 1 < n_extra && src[e + 1] == i) continue;   // not the stream's last piece
+    const uint4* from = reinterpret_cast<const uint4*>(states + n + e);
+    uint4* to = reinterpret_cast<uint4*>(states + i);
+#pragma unroll 5
+    for (int q = 0; q < static_cast<int>(sizeof(ranmar_state_t) / 16); ++q) to[q] = from[q];
+  }
+}
+
 }  // namespace ranmar

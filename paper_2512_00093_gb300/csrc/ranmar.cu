@@ -38,6 +38,7 @@ struct ranmar_batch {
   uint32_t* hist;              // bucket histogram
   uint32_t* cursor;            // bucket cursors
   uint64_t* tile_sums;         // ceil(capacity / 1024) tile sums
+  uint64_t* tile_extra;        // the same for the extra pieces of a split pack
   ranmar_batch_config_t cfg;
 };
 
@@ -672,8 +673,8 @@ int ranmar_batch_create(size_t capacity, ranmar_batch_t** out) {
   }
   const size_t n_tiles = (capacity + ranmar::kScanTile - 1) / ranmar::kScanTile;
   // [0] queue, [8] total, [256] hist (65 words), [768] cursor (65 words),
-  // [1280] tile sums.
-  const size_t bytes = 1280 + n_tiles * sizeof(uint64_t);
+  // [1280] tile sums, then the tile sums of the extra pieces (split packs).
+  const size_t bytes = 1280 + 2 * n_tiles * sizeof(uint64_t);
   e = cudaMalloc(&b->ws, bytes);
   if (e != cudaSuccess) {
     delete b;
@@ -689,6 +690,7 @@ int ranmar_batch_create(size_t capacity, ranmar_batch_t** out) {
   b->hist = reinterpret_cast<uint32_t*>(b->ws + 256);
   b->cursor = reinterpret_cast<uint32_t*>(b->ws + 768);
   b->tile_sums = reinterpret_cast<uint64_t*>(b->ws + 1280);
+  b->tile_extra = b->tile_sums + n_tiles;
   static_assert(ranmar::kBuckets * sizeof(uint32_t) <= 512, "workspace layout");
   b->cfg = ranmar_batch_config_t{32, 256, 0, 1};
   *out = b;
@@ -745,6 +747,49 @@ int ranmar_batch_pack(ranmar_batch_t* b, const uint64_t* d_counts, size_t n, uin
                                                                b->hist, b->cursor);
   ranmar::pack_write<<<tiles, ranmar::kScanThreads, 0, s>>>(d_counts, n, b->tile_sums, flags,
                                                               d_desc, b->cursor, d_order);
+  return check_launch();
+}
+
+int ranmar_batch_pack_split(ranmar_batch_t* b, const uint64_t* d_counts, size_t n, uint64_t seg,
+                            size_t n_extra, uint32_t flags, ranmar_desc_t* d_desc,
+                            uint32_t* d_src, uint32_t* d_exp, uint64_t* d_total,
+                            uint32_t* d_status, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_batch_pack_split");
+  if (!on_device(b)) return RANMAR_EINVAL;
+  if (seg == 0) return RANMAR_EINVAL;
+  if (n > b->capacity || n + n_extra >= (static_cast<uint64_t>(1) << 32)) return RANMAR_ERANGE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint64_t* total = d_total ? d_total : b->total;
+  if (n == 0) {
+    if (n_extra) return RANMAR_EINVAL;
+    if (!d_total) return RANMAR_OK;
+    const cudaError_t e = cudaMemsetAsync(d_total, 0, sizeof(uint64_t), s);
+    return e == cudaSuccess ? RANMAR_OK : cuda_fail(e);
+  }
+  if (!d_counts || !d_desc || (n_extra && (!d_src || !d_exp))) return RANMAR_EINVAL;
+  if (!aligned(d_counts, 8) || !aligned(d_desc, 8) || !aligned(d_src, 4) || !aligned(d_exp, 4) ||
+      !aligned(d_total, 8) || !aligned(d_status, 4))
+    return RANMAR_EINVAL;
+  const unsigned tiles = static_cast<unsigned>((n + ranmar::kScanTile - 1) / ranmar::kScanTile);
+  ranmar::split_tile_sums<<<tiles, ranmar::kScanThreads, 0, s>>>(d_counts, n, seg, b->tile_sums,
+                                                                   b->tile_extra);
+  ranmar::split_scan_tiles<<<1, ranmar::kScanThreads, 0, s>>>(
+      b->tile_sums, b->tile_extra, tiles, n, n_extra, total, d_desc, d_src, d_exp, d_status);
+  ranmar::split_write<<<tiles, ranmar::kScanThreads, 0, s>>>(
+      d_counts, n, seg, n_extra, b->tile_sums, b->tile_extra, flags, d_desc, d_src, d_exp);
+  return check_launch();
+}
+
+int ranmar_batch_split_finish(ranmar_state_t* d_states, size_t n, const uint32_t* d_src,
+                              size_t n_extra, ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_batch_split_finish");
+  if (n_extra == 0) return RANMAR_OK;
+  if (!d_states || !d_src) return RANMAR_EINVAL;
+  if (!aligned(d_states, 16) || !aligned(d_src, 4)) return RANMAR_EINVAL;
+  uint64_t blocks = (n_extra + ranmar::kScanThreads - 1) / ranmar::kScanThreads;
+  if (blocks > 65536) blocks = 65536;
+  ranmar::split_finish<<<static_cast<unsigned>(blocks), ranmar::kScanThreads, 0,
+                         reinterpret_cast<cudaStream_t>(stream)>>>(d_states, n, d_src, n_extra);
   return check_launch();
 }
 

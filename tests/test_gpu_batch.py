@@ -185,3 +185,71 @@ def test_batched_uneven_full_size_sampled(rm, dev, orc):
         assert np.array_equal(g, (ref.astype(np.float64) * F).astype(np.float32)), i
     del out
     b.close()
+
+
+@pytest.mark.parametrize("seg", [64, 1000, 4096])
+def test_split_pack_equals_unsplit_batch(rm, dev, orc, seg):
+    """Splitting long streams (ranmar_batch_pack_split, the extra pieces'
+    start states by the table jump by q seg, ranmar_batch_split_finish) gives
+    the same outputs and the same advanced states as the unsplit batch, and
+    the oracle's stream on sampled long streams.  Tolerance 0."""
+    n = 3000
+    c = counts_mix(n, 7)
+    c[20:26] = [seg - 1, seg, seg + 1, 2 * seg, 2 * seg + 1, 65536]
+    J = 1 << 64
+    table = rm.Table()
+    base = rm.seed(12345).to(dev)
+    st0 = table.partition(base, J, 0, n)
+    counts = torch.as_tensor(c, device=dev)
+    total = int(c.sum())
+    b = rm.Batch(n)
+    desc, order, _ = b.pack(counts, flags=rm.DESC_WRITE_BACK)
+    st_u = st0.clone()
+    out_u = torch.full((total,), -1.0, dtype=torch.float32, device=dev)
+    b.generate_f32(st_u, desc, out_u, order=order)
+    n_extra = rm.Batch.split_extra(c, seg)
+    assert n_extra == sum(max(0, -(-int(x) // seg) - 1) for x in c)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    sdesc, src, exps, tot = b.pack_split(counts, seg, n_extra, flags=rm.DESC_WRITE_BACK,
+                                         status=status)
+    st_s = torch.empty((n + n_extra, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+    st_s[:n] = st0
+    if n_extra:
+        table.jump(st_s[:n], exps, base_idx=src, out=st_s[n:], status=status)
+    out_s = torch.full((total,), -1.0, dtype=torch.float32, device=dev)
+    b.generate_f32(st_s, sdesc, out_s, status=status)
+    rm.Batch.split_finish(st_s, n, src)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0 and int(tot.item()) == total
+    d = sdesc.cpu().numpy().view(np.uint64)
+    assert int(d[:, 2].max()) <= seg and int(d[:, 2].sum()) == total
+    assert torch.equal(out_s.view(torch.int32), out_u.view(torch.int32))
+    assert torch.equal(st_s[:n], st_u)
+    offs = np.concatenate([[0], np.cumsum(c)[:-1]])
+    got = out_s.cpu().numpy()
+    for i in (20, 21, 22, 23, 24, 25, int(np.argmax(c))):
+        ref = orc.stream(12345, i * J, int(c[i]))
+        want = (ref.astype(np.float64) * F).astype(np.float32)
+        assert np.array_equal(got[offs[i]: offs[i] + c[i]], want), i
+    b.close()
+    table.close()
+
+
+def test_split_pack_wrong_extra_count_is_flagged(rm, dev):
+    """n_extra that does not match the pieces sets RANMAR_ST_OUT_RANGE; the
+    descriptors sized for missing pieces are empty ones."""
+    c = np.array([10, 300, 5000, 64], dtype=np.int64)
+    seg = 100
+    n_extra = rm.Batch.split_extra(c, seg)          # 2 + 49 = 51
+    counts = torch.as_tensor(c, device=dev)
+    b = rm.Batch(4)
+    for ne in (n_extra - 1, n_extra + 2):
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        desc, src, exps, _ = b.pack_split(counts, seg, ne, status=status)
+        torch.cuda.synchronize()
+        assert int(status.item()) & rm.ST_OUT_RANGE
+        if ne > n_extra:
+            d = desc.cpu().numpy().view(np.uint64)
+            assert np.all(d[4 + n_extra:, 2] == 0)
+            assert np.all(src.cpu().numpy()[n_extra:].view(np.uint32) == 0xFFFFFFFF)
+    b.close()

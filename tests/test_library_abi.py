@@ -124,3 +124,41 @@ def test_workload_recipes():
     assert abs(lens.mean() / 9446.0 - 1.0) < 0.02
     rows = wl.Partitioned().verify_rows()
     assert len(set(rows.tolist())) == 256 and rows.max() < 65536
+
+
+def test_split_extra_counts_pieces():
+    """Batch.split_extra (host): sum of max(0, ceil(c / seg) - 1), by brute force."""
+    from paper_2512_00093_gb300.binding import Batch
+    rng = np.random.default_rng(3)
+    for seg in (1, 7, 64, 4096):
+        c = np.concatenate([[0, 1, seg - 1, seg, seg + 1, 3 * seg], rng.integers(0, 70000, 500)])
+        c = c[c >= 0]
+        want = 0
+        for x in c.tolist():
+            pieces = 0
+            left = x
+            while left > 0:
+                pieces += 1
+                left -= seg
+            want += max(0, pieces - 1)
+        assert Batch.split_extra(c, seg) == want
+    assert Batch.split_extra([], 10) == 0
+
+
+def test_split_entry_points_reject_bad_arguments(lib):
+    """Host checks of the split pack and its finish (no device work)."""
+    L, _ = lib
+    L.ranmar_batch_pack_split.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_uint64, ctypes.c_size_t, ctypes.c_uint32,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.ranmar_batch_split_finish.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                            ctypes.c_size_t, ctypes.c_void_p]
+    fake = ctypes.c_void_p(0x10000)
+    # no batch handle
+    assert L.ranmar_batch_pack_split(None, fake, 4, 16, 0, 0, fake, None, None, None, None,
+                                     None) == -1
+    # finish: nothing to do with n_extra = 0; NULL or misaligned otherwise
+    assert L.ranmar_batch_split_finish(None, 4, None, 0, None) == 0
+    assert L.ranmar_batch_split_finish(None, 4, fake, 3, None) == -1
+    assert L.ranmar_batch_split_finish(ctypes.c_void_p(0x10004), 4, fake, 3, None) == -1
