@@ -221,6 +221,23 @@ __device__ __forceinline__ uint32_t mir_a47(const uint32_t* __restrict__ C,
   return C[47] + Hr[95 - 47] - Hr[95 - 80];
 }
 
+// a_63 of the reduced square (the word below block 4): c_63 + h_63 (63 is
+// past the range of the h_{n+33} term and below that of the n >= 64 terms).
+__device__ __forceinline__ uint32_t mir_a63(const uint32_t* __restrict__ C,
+                                            const uint32_t* __restrict__ Hr) {
+  return C[63] + Hr[95 - 63];
+}
+
+// a_31 (the word below block 2): c_31 + h_31 - h_64 (31 > 29: no h_{n+66}).
+__device__ __forceinline__ uint32_t mir_a31(const uint32_t* __restrict__ C,
+                                            const uint32_t* __restrict__ Hr) {
+  return C[31] + Hr[95 - 31] - Hr[95 - 64];
+}
+
+#ifndef RANMAR_MIR_GATHER_SPLIT
+#define RANMAR_MIR_GATHER_SPLIT 3   // warp 0 reduces blocks 0 .. split-1, warp 1 the rest
+#endif
+
 // x = x^2 t^shift mod phi in place (A forward, Bv reversed).  Both warps of
 // the CTA call it for the same 16 streams (lanes g = 0, 1 of each pair in
 // each warp): warp 0 forms output blocks 5 and 3 of each lane's half and
@@ -308,14 +325,20 @@ __device__ __forceinline__ void square_mirror_pair(uint32_t* __restrict__ slice,
   __syncthreads();
   const uint32_t a96 = slice[kMirC96] + Hr[95 - 65] - Hr[95 - 32];
   uint32_t last = 0;
+  constexpr int kSplit = RANMAR_MIR_GATHER_SPLIT;
+  static_assert(kSplit >= 2 && kSplit <= 4, "gather split");
   if (w == 0) {
     uint32_t prev7 = 0;                      // a_{-1} = 0 below block 0
     mir_gather<0>(A, Bv, C, Hr, g, shift, a96, prev7, last);
     mir_gather<1>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-    mir_gather<2>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    if constexpr (kSplit > 2) mir_gather<2>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    if constexpr (kSplit > 3) mir_gather<3>(A, Bv, C, Hr, g, shift, a96, prev7, last);
   } else {
-    uint32_t prev7 = g ? mir_a47(C, Hr) : 0u;   // lane 1 hands it to lane 0 at block 3
-    mir_gather<3>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    // lane 1 hands lane 0 the word below warp 1's first block
+    uint32_t prev7 = 0;
+    if (g) prev7 = kSplit == 2 ? mir_a31(C, Hr) : kSplit == 3 ? mir_a47(C, Hr) : mir_a63(C, Hr);
+    if constexpr (kSplit <= 2) mir_gather<2>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    if constexpr (kSplit <= 3) mir_gather<3>(A, Bv, C, Hr, g, shift, a96, prev7, last);
     mir_gather<4>(A, Bv, C, Hr, g, shift, a96, prev7, last);
     mir_gather<5>(A, Bv, C, Hr, g, shift, a96, prev7, last);
     if (g) {  // position 96: the old a_95 (lane 1's v[7] of block 5) or a_96
