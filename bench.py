@@ -1091,6 +1091,63 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak, probes):
     best_g = graph_ms(lambda: bplan.partition(base, 0, ns, out=stb, stream=gs))
     best_g_table = graph_ms(lambda: table.partition(base, bu.J, 0, ns, out=stb, stream=gs))
     plan_status = bplan.status()
+
+    # The same step with every stream longer than seg outputs split into
+    # pieces (ranmar_batch_pack_split): the extra pieces' start states by the
+    # table jump by q seg, generation of all pieces, the last pieces' states
+    # copied back.  Outputs and states checked equal to the unsplit step's.
+    split = {}
+    try:
+        seg = 16384
+        n_extra = rm.Batch.split_extra(lens, seg)
+        sts = torch.empty((ns + n_extra, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+        outs = torch.empty_like(outf)
+        sstat = torch.zeros(1, dtype=torch.int32, device=dev)
+        sdesc, ssrc, sexp, _ = b.pack_split(counts, seg, n_extra, flags=rm.DESC_WRITE_BACK,
+                                            status=sstat)
+
+        def split_step(s_):
+            bplan.partition(base, 0, ns, out=sts[:ns], stream=s_)
+            bd._check(bd._lib().ranmar_batch_pack_split(
+                b._h, counts.data_ptr(), ns, seg, n_extra, rm.DESC_WRITE_BACK, sdesc.data_ptr(),
+                ssrc.data_ptr(), sexp.data_ptr(), None, sstat.data_ptr(), s_.cuda_stream),
+                "pack_split")
+            table.jump(sts[:ns], sexp, base_idx=ssrc, out=sts[ns:], status=sstat, stream=s_)
+            b.generate_f32(sts, sdesc, outs, status=sstat, stream=s_)
+            rm.Batch.split_finish(sts, ns, ssrc, stream=s_)
+
+        split_step(gs)
+        with rm.capture(gs) as cap:
+            split_step(gs)
+        cap.graph.launch(gs)
+        gs.synchronize()
+        best_s = float("inf")
+        for _ in range(5):
+            ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ga.record(gs)
+            cap.graph.launch(gs)
+            gb.record(gs)
+            gs.synchronize()
+            best_s = min(best_s, ga.elapsed_time(gb))
+        cap.graph.close()
+        # reference: one unsplit step (with write-back) from the same start states
+        wdesc, word, _ = b.pack(counts, flags=rm.DESC_WRITE_BACK)
+        bplan.partition(base, 0, ns, out=stb)
+        b.generate_f32(stb, wdesc, outf, order=word)
+        torch.cuda.synchronize()
+        split = {"seg": seg, "extra_pieces": n_extra, "graph_step_ms": best_s,
+                 "step_outputs_per_s": total / (best_s * 1e-3),
+                 "vs_unsplit_graph_step": best_s / best_g,
+                 "outputs_identical": bool(torch.equal(outs.view(torch.int32),
+                                                       outf.view(torch.int32))),
+                 "states_identical": bool(torch.equal(sts[:ns], stb)),
+                 "status": int(sstat.item()),
+                 "note": "streams longer than seg cut into pieces; the extra pieces start from "
+                         "table jumps by q*seg; the trade-off: the extra jumps against the "
+                         "persistent kernel's tail"}
+        del sts, outs, sdesc, ssrc, sexp
+    except Exception as e:  # noqa: BLE001
+        split = {"error": f"{type(e).__name__}: {e}"}
     bplan.close()
     gen_bytes = total * 4 + ns * (400 + 24 + 4)
     # plain comparator on a sample: generation only, one launch per stream
@@ -1128,6 +1185,7 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak, probes):
         "plan_states_identical": plan_same, "plan_status": plan_status,
         "pack_ms": ms_pack, "generate_ms": ms_gen,
         "graph_step_ms": best_g, "graph_step_table_jump_ms": best_g_table,
+        "split_long_streams": split,
         "step_outputs_per_s": total / (best_g * 1e-3),
         "generate_outputs_per_s": total / (ms_gen * 1e-3),
         "generate_hbm_gbs": gen_bytes / (ms_gen * 1e-3) / 1e9,
