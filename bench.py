@@ -838,6 +838,17 @@ def run_ours(args):
                  "algorithmic_flops": plan_flops,
                  "traffic": tp["bytes_per_launch"] if tp else None, "avg_launch_ms": exp_ms,
                  "note": "one launch (510 tiles x matrices over 152 SMs)"}
+    # the whole step against the same ceiling: what one step must move through
+    # DRAM is its outputs and the states written back (the plan level's new
+    # states are read back from L2 by the generation that follows)
+    step_bytes = n * count * 4 + n * 400
+    roof_step = {"bound": "hbm", "algorithmic_bytes": step_bytes,
+                 "achieved": step_bytes / (ms_step * 1e-3) / 1e9, "peak": hbm_peak,
+                 "unit": "GB/s", "frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak,
+                 "note": "the timed step (table jump of 256 streams + plan level + "
+                         "generation, graph replay) as one HBM-write-bound unit: outputs + "
+                         "state write-back per step over ms_per_step, against the in-run "
+                         "store-only ceiling"}
     fused_bytes = n * count * 4 + n * 400
     roof_fused = {"kernel": "partition_generate_kernel<u24>", "bound": "hbm",
                   "ms": ms_fused, "frac": fused_bytes / (ms_fused * 1e-3) / 1e9 / hbm_peak,
@@ -861,7 +872,8 @@ def run_ours(args):
         "fused_ms_per_step": ms_fused, "fused_outputs_per_s": world * n * count / (ms_fused * 1e-3),
         "two_kernel_pipelined_ms_per_step": ms_two,
         "two_kernel_outputs_per_s": world * n * count / (ms_two * 1e-3),
-        "roofline": roof_gen, "roofline_plan": roof_plan, "roofline_generate": roof_gen,
+        "roofline": roof_gen, "roofline_step": roof_step, "roofline_plan": roof_plan,
+        "roofline_generate": roof_gen,
         "roofline_jump": roof_jump, "roofline_fused": roof_fused,
         "plan": {"build_ms": plan_build_ms, "expand_ms": exp_ms, "status": plan_status,
                  "states_identical_to_table_jump": plan_ok},
