@@ -88,6 +88,32 @@ class Serving:
         return t, seeds, ks, counts, f32
 
 
+@dataclass(frozen=True)
+class ServingHot:
+    """A labelled variant of the serving stream in which requests revisit a
+    small set of streams (seeds 1..64, stream index 0..15: 1,024 streams), so
+    that most requests resume a stream an earlier request left resident:
+    Poisson 20k req/s for 10 s (seed 13), J = 2^48, count
+    floor(10^(3 + 3u)), u24 or f32 with probability 1/2."""
+    rate: float = 20000.0
+    duration: float = 10.0
+    rng_seed: int = 13
+    J: int = 1 << 48
+    seeds: int = 64
+    ks: int = 16
+
+    def requests(self, duration: float | None = None):
+        dur = self.duration if duration is None else duration
+        rng = np.random.default_rng(self.rng_seed)
+        n = rng.poisson(self.rate * dur)
+        t = np.sort(rng.random(n) * dur)
+        seeds = rng.integers(1, self.seeds + 1, n)
+        ks = rng.integers(0, self.ks, n)
+        counts = np.floor(10.0 ** (3.0 + 3.0 * rng.random(n))).astype(np.int64)
+        f32 = rng.random(n) < 0.5
+        return t, seeds, ks, counts, f32
+
+
 def random_exponents(n: int, max_bits: int, seed: int) -> list[int]:
     """n exponents with bit lengths spread over 0..max_bits (edge cases first)."""
     rng = np.random.default_rng(seed)

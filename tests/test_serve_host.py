@@ -101,3 +101,17 @@ def test_admit_refuses_requests_that_can_never_fit():
         r.done = r.host_done = r.t + 0.001
     s = serve.summarize(reqs)
     assert (s["requests"], s["served"], s["rejected"]) == (4, 2, 2)
+
+
+def test_hot_stream_recipe():
+    """The hot-stream serving variant: 1,024 streams revisited, so nearly every
+    stream has many requests and later ones resume at the earlier ones' end."""
+    from paper_2512_00093_gb300.workloads import ServingHot
+    w = ServingHot()
+    t, seeds, ks, counts, f32 = w.requests(duration=1.0)
+    assert abs(len(t) / 20000 - 1) < 0.03
+    assert seeds.min() >= 1 and seeds.max() <= 64 and ks.min() >= 0 and ks.max() <= 15
+    assert counts.min() >= 1000 and counts.max() < 10**6
+    reqs = serve.make_requests(t, seeds, ks, counts, f32, w.J)
+    assert len({r.key for r in reqs}) <= 1024
+    assert sum(r.offset > 0 for r in reqs) > 0.9 * len(reqs)
