@@ -123,14 +123,15 @@ int ranmar_seed_batch(const int32_t *d_seeds, size_t n, ranmar_state_t *d_out,
  * i the kernel forms P = t^{E_i} mod (t^97 + t^64 - 1) over Z/2^24 by
  * left-to-right square-and-multiply, applies x P(A) as sum_j b_j x_{j+k},
  * and sets c = (c_base - E_i d) mod m, pos = pos_base + E_i mod 2^64.
- * One 32-lane warp serves 16 streams, two lanes per stream (lane 0 forms
- * the low half of each square, lane 1 the high half from the reversed
- * polynomial); a batch of at most RANMAR_SQUARE_WARP_AUTO_MAX streams
- * instead gives each stream a whole warp.  That cuts the LATENCY of one
- * squaring about 5 times (each stream's dependent chain is spread over 32
- * lanes instead of 2), not the work: the warp mapping executes about three
- * times the instructions per stream, so large batches keep the lane pairs.
- * Same results either way.
+ * A CTA of two warps serves 16 streams, two lanes per stream in each warp
+ * (lane 0 forms the low half of each square, lane 1 the high half from the
+ * reversed polynomial; the two warps share each square's output blocks); a
+ * batch of at most RANMAR_SQUARE_WARP_AUTO_MAX streams instead gives each
+ * stream a whole warp.  That cuts the LATENCY of one squaring about 5 times
+ * (each stream's dependent chain is spread over 32 lanes instead of 4), not
+ * the work: the warp mapping executes about three times the instructions
+ * per stream, so larger batches keep the lane pairs.  Same results either
+ * way.
  * d_out must not overlap d_base.  n = 0 is a no-op.
  * Errors: RANMAR_EINVAL (null pointer with n > 0, misaligned states,
  * overlapping in/out), RANMAR_ERANGE (exp_words not in 1..5, n_base = 0, or
@@ -150,8 +151,9 @@ int ranmar_jump(const ranmar_state_t *d_base, size_t n_base,
  * ranmar_jump, for E_i the little-endian integer d_exp[i*exp_words ..
  * (i+1)*exp_words) (device).  d_poly (device, n x 100 uint32, caller-owned):
  * coefficients 0..96 of P_{E_i} (24-bit canonical, coefficient j of t^j),
- * then three zero words.  Two lanes per exponent, 16 per warp (a warp per
- * exponent up to RANMAR_SQUARE_WARP_AUTO_MAX exponents); asynchronous
+ * then three zero words.  Two lanes per exponent in each of two warps per
+ * 16 exponents (a warp per exponent up to RANMAR_SQUARE_WARP_AUTO_MAX
+ * exponents); asynchronous
  * on `stream`; n = 0 is a no-op.  Errors: RANMAR_EINVAL (NULL with n > 0,
  * misaligned or overlapping buffers), RANMAR_ERANGE (exp_words not in
  * 1..RANMAR_MAX_EXP_WORDS, or n too large for one launch).
