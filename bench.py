@@ -1396,6 +1396,22 @@ def serving(rm, torch, seconds):
         "note": f"the first {nplain} requests of the same list, each alone: one jump launch + "
                 "one one-warp generation launch; when it cannot sustain the offered rate its "
                 "latencies are queueing"}
+    # Both at a rate the plain path can sustain: the same first nplain requests
+    # with their arrival times stretched to 400 req/s on average, served by a
+    # fresh engine and by the plain path, so that neither latency is queueing.
+    slow = 400.0
+    ts = t[:nplain] * (w.rate / slow)
+    r_eng = make_requests(ts, seeds[:nplain], ks[:nplain], counts[:nplain], f32[:nplain], w.J)
+    r_pl = make_requests(ts, seeds[:nplain], ks[:nplain], counts[:nplain], f32[:nplain], w.J)
+    e_slow = eng.run(r_eng, realtime=True, max_wait=ts[-1] + 120)
+    p_slow = eng.run_plain(r_pl, realtime=True, max_wait=ts[-1] + 120)
+    res["at_400_req_per_s"] = {
+        "requests": nplain, "engine": e_slow, "plain_per_request": p_slow,
+        "checksums_equal": f"{sum(int(a.checksum == b.checksum) for a, b in zip(r_eng, r_pl))}"
+                           f"/{nplain}",
+        "note": "the same requests with arrival times stretched to 400 req/s, below the plain "
+                "path's saturation: latencies without queueing, engine against one jump + one "
+                "generation launch per request"}
     eng.close()
     return res
 
