@@ -899,8 +899,10 @@ def run_ours(args):
     except Exception as e:  # noqa: BLE001
         result["config4"] = {"error": f"{type(e).__name__}: {e}"}
     result["probes"] = probes
-    if not args.no_extras:
-        # side measurements never cost the headline line: errors are recorded
+    if not args.no_extras and world == 1:
+        # side measurements never cost the headline line: errors are recorded.
+        # They are per-GPU figures, taken in the one-GPU run only: under
+        # torchrun the other ranks would wait in the closing barrier meanwhile.
         try:
             result["extras"] = extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak, probes)
         except Exception as e:  # noqa: BLE001
