@@ -253,3 +253,48 @@ def test_split_pack_wrong_extra_count_is_flagged(rm, dev):
             assert np.all(d[4 + n_extra:, 2] == 0)
             assert np.all(src.cpu().numpy()[n_extra:].view(np.uint32) == 0xFFFFFFFF)
     b.close()
+
+
+def test_split_pack_edge_shapes(rm, dev, orc):
+    """n_extra = 0 (no stream longer than seg), every stream exactly seg,
+    one stream of 65,536 outputs in pieces of 97, and no write-back: the
+    split path still equals the unsplit batch (outputs; states untouched
+    without write-back)."""
+    J = 1 << 40
+    table = rm.Table()
+    base = rm.seed(54217138).to(dev)
+    for c, seg, wb in [(np.array([5, 0, 64, 100]), 128, True),
+                       (np.full(37, 256), 256, True),
+                       (np.array([65536, 3]), 97, True),
+                       (np.array([1000, 2000, 3000]), 512, False)]:
+        n = len(c)
+        flags = rm.DESC_WRITE_BACK if wb else 0
+        counts = torch.as_tensor(c.astype(np.int64), device=dev)
+        total = int(c.sum())
+        st0 = table.partition(base, J, 11, n)
+        b = rm.Batch(n)
+        desc, order, _ = b.pack(counts, flags=flags)
+        st_u = st0.clone()
+        out_u = torch.full((total,), -1, dtype=torch.int32, device=dev)
+        b.generate_u24(st_u, desc, out_u, order=order)
+        n_extra = rm.Batch.split_extra(c, seg)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        sdesc, src, exps, _ = b.pack_split(counts, seg, n_extra, flags=flags, status=status)
+        st_s = torch.empty((n + n_extra, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+        st_s[:n] = st0
+        if n_extra:
+            table.jump(st_s[:n], exps, base_idx=src, out=st_s[n:], status=status)
+        out_s = torch.full((total,), -1, dtype=torch.int32, device=dev)
+        b.generate_u24(st_s, sdesc, out_s, status=status)
+        if wb:
+            rm.Batch.split_finish(st_s, n, src)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert torch.equal(out_s, out_u), (c.tolist(), seg)
+        assert torch.equal(st_s[:n], st_u if wb else st0), (c.tolist(), seg)
+        i = int(np.argmax(c))
+        offs = np.concatenate([[0], np.cumsum(c)[:-1]])
+        ref = orc.stream(54217138, (11 + i) * J, int(c[i]))
+        assert np.array_equal(out_s.cpu().numpy().view(np.uint32)[offs[i]: offs[i] + c[i]], ref)
+        b.close()
+    table.close()
