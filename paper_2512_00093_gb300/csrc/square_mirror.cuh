@@ -44,9 +44,11 @@
 // words are masked to 24 bits only when a result leaves the kernel.
 //
 // Shared memory per stream (words): A (100: x_0..x_96, pad), Bv (100: the
-// reversed copy), C (96), Hr (96); stride 420 = 4 mod 32, so that the
-// 16-byte accesses of a quarter warp (8 streams) fall in distinct bank
-// groups.  The application that follows uses C/Hr as its 128-word ring.
+// reversed copy), C (96), Hr (96), c_96 and the application's four partial
+// sums; stride 420 = 4 mod 32, so that the 16-byte accesses of a quarter warp
+// (8 streams) fall in distinct bank groups.  The application that follows
+// (apply_mirror, all four threads of a stream) builds its window X(0..192)
+// over C/Hr.
 #pragma once
 
 #include "jump.cuh"
@@ -58,12 +60,14 @@ constexpr int kMirB = 100;
 constexpr int kMirC = 200;
 constexpr int kMirH = 296;
 constexpr int kMirC96 = 392;          // c_96, handed from warp 0 to warp 1
+constexpr int kMirP96 = 396;          // the application's four partial sums of output 96
 constexpr int kMirStreamWords = 420;
 constexpr int kMirWarps = 2;          // warps per CTA, sharing its 16 streams
 constexpr int kMirThreads = 32 * kMirWarps;
 constexpr size_t kMirSmemBytes = sizeof(uint32_t) * kMirStreamWords * kJumpStreamsPerWarp;
-static_assert(kMirH + 96 <= kMirC96 && kMirC96 < kMirStreamWords, "slice");
-static_assert(kMirC + kRingWords <= kMirStreamWords, "ring inside the slice");
+static_assert(kMirH + 96 <= kMirC96 && kMirC96 < kMirP96 && kMirP96 + 4 <= kMirStreamWords,
+              "slice");
+static_assert(kMirC + 193 <= kMirP96, "the application's window X(0..192) after C");
 static_assert(kMirStreamWords % 32 == 4, "bank spread");
 static_assert(kMirB % 4 == 0 && kMirC % 4 == 0 && kMirH % 4 == 0, "16-byte alignment");
 
@@ -213,6 +217,47 @@ __device__ __forceinline__ void mir_gather(uint32_t* __restrict__ A, uint32_t* _
   br[-7] = w[7];
 }
 
+// acc[r] += sum over the chunks c = 0 .. nch-1 of sum_{u<8} x_{8c+u}
+// y_{16m+r-8c-u} (part of output block m of x y).  The caller passes only
+// chunks whose every term has i < j, 1 <= 16m+r-8c-u <= 95: for a square,
+// the chunks below the diagonal (nch = m).  Chunk c's window is the octets O(2m-c-1), O(2m-c), O(2m-c+1) of y (O(k) =
+// y_{8k} .. y_{8k+7}), so the next chunk needs one new octet: four octet
+// registers rotate (period four, the loop unrolled by four) and each chunk
+// loads the next chunk's new octet and x octet O(c+1) while it multiplies.
+__device__ __forceinline__ void mir_chunks(uint32_t (&acc)[16], const uint32_t* __restrict__ X,
+                                           const uint32_t* __restrict__ Y, int m, int nch) {
+  if (nch <= 0) return;
+  const uint32_t* ob = Y + 16 * m - 8;   // O_y(2m-1-c) = ob - 8c
+  Oct w0 = lds8(ob), w1 = lds8(ob + 8), w2 = lds8(ob + 16), w3;
+  Oct x0 = lds8(X), x1;
+#pragma unroll 1
+  for (int c = 0; c < nch; c += 4) {
+    if (c + 1 < nch) {
+      w3 = lds8(ob - 8 * (c + 1));
+      x1 = lds8(X + 8 * (c + 1));
+    }
+    mir_para(acc, x0, w0, w1, w2);
+    if (c + 1 >= nch) break;
+    if (c + 2 < nch) {
+      w2 = lds8(ob - 8 * (c + 2));
+      x0 = lds8(X + 8 * (c + 2));
+    }
+    mir_para(acc, x1, w3, w0, w1);
+    if (c + 2 >= nch) break;
+    if (c + 3 < nch) {
+      w1 = lds8(ob - 8 * (c + 3));
+      x1 = lds8(X + 8 * (c + 3));
+    }
+    mir_para(acc, x0, w2, w3, w0);
+    if (c + 3 >= nch) break;
+    if (c + 4 < nch) {
+      w0 = lds8(ob - 8 * (c + 4));
+      x0 = lds8(X + 8 * (c + 4));
+    }
+    mir_para(acc, x1, w1, w2, w3);
+  }
+}
+
 // a_47 of the reduced square (the word below block 3), for warp 1's lane 0
 // at its first block: c_47 + h_47 - h_80 (the other terms of the gather do
 // not reach n = 47).
@@ -237,6 +282,44 @@ __device__ __forceinline__ uint32_t mir_a31(const uint32_t* __restrict__ C,
 // Warp 0 reduces blocks 0 .. kMirGatherSplit-1, warp 1 the rest (3 measured
 // fastest; 2 and 4 took 1.5-2% longer at 16,384 large jumps).
 constexpr int kMirGatherSplit = 3;
+
+// After both warps have stored their blocks of c (C[n] = c_n, Hr[k] =
+// c_{192-k}, *c96 = c_96): a CTA barrier, the closed-form reduction mod phi
+// with the shift by t^shift (warp 0 blocks 0..kMirGatherSplit-1, warp 1 the
+// rest and position 96), written forward to A and reversed to Bv, and a
+// second barrier.
+__device__ __forceinline__ void mir_reduce(uint32_t* __restrict__ A, uint32_t* __restrict__ Bv,
+                                           const uint32_t* __restrict__ C,
+                                           const uint32_t* __restrict__ Hr,
+                                           const uint32_t* __restrict__ c96, uint32_t shift,
+                                           unsigned g, unsigned w) {
+  __syncthreads();
+  const uint32_t a96 = *c96 + Hr[95 - 65] - Hr[95 - 32];
+  uint32_t last = 0;
+  constexpr int kSplit = kMirGatherSplit;
+  static_assert(kSplit >= 2 && kSplit <= 4, "gather split");
+  if (w == 0) {
+    uint32_t prev7 = 0;                      // a_{-1} = 0 below block 0
+    mir_gather<0>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    mir_gather<1>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    if constexpr (kSplit > 2) mir_gather<2>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    if constexpr (kSplit > 3) mir_gather<3>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+  } else {
+    // lane 1 hands lane 0 the word below warp 1's first block
+    uint32_t prev7 = 0;
+    if (g) prev7 = kSplit == 2 ? mir_a31(C, Hr) : kSplit == 3 ? mir_a47(C, Hr) : mir_a63(C, Hr);
+    if constexpr (kSplit <= 2) mir_gather<2>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    if constexpr (kSplit <= 3) mir_gather<3>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    mir_gather<4>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    mir_gather<5>(A, Bv, C, Hr, g, shift, a96, prev7, last);
+    if (g) {  // position 96: the old a_95 (lane 1's v[7] of block 5) or a_96
+      const uint32_t w96 = shift ? last : a96;
+      A[96] = w96;
+      Bv[0] = w96;
+    }
+  }
+  __syncthreads();
+}
 
 // x = x^2 t^shift mod phi in place (A forward, Bv reversed).  Both warps of
 // the CTA call it for the same 16 streams (lanes g = 0, 1 of each pair in
@@ -276,11 +359,7 @@ __device__ __forceinline__ void square_mirror_pair(uint32_t* __restrict__ slice,
     if (g == 0) slice[kMirC96] = c96;
   }
   // This warp's output blocks of the lane's half: block m = m full chunks
-  // (c = 0 .. m-1) then the last chunk.  Chunk c's window is the octets
-  // O(2m-c-1), O(2m-c), O(2m-c+1) (O(k) = x_{8k} .. x_{8k+7}), so the next
-  // chunk needs one new octet: four octet registers rotate (period four, the
-  // loop unrolled by four) and each chunk loads the next chunk's new octet
-  // and x octet O(c+1) while it multiplies.
+  // (c = 0 .. m-1, mir_chunks) then the last chunk (mir_tail).
   const uint32_t blocks = w ? 0x0124u : 0x35u;   // m, four bits each, first in the low bits
   const int nblocks = w ? 4 : 2;
   uint32_t acc[16];
@@ -289,65 +368,91 @@ __device__ __forceinline__ void square_mirror_pair(uint32_t* __restrict__ slice,
 #pragma unroll 1
   for (int k = 0; k < nblocks; ++k) {
     const int m = static_cast<int>((blocks >> (4 * k)) & 15u);
-    if (m > 0) {
-      const uint32_t* ob = X + 16 * m - 8;   // O(2m-1-c) = ob - 8c
-      Oct w0 = lds8(ob), w1 = lds8(ob + 8), w2 = lds8(ob + 16), w3;
-      Oct x0 = lds8(X), x1;
-#pragma unroll 1
-      for (int c = 0; c < m; c += 4) {
-        if (c + 1 < m) {
-          w3 = lds8(ob - 8 * (c + 1));
-          x1 = lds8(X + 8 * (c + 1));
-        }
-        mir_para(acc, x0, w0, w1, w2);
-        if (c + 1 >= m) break;
-        if (c + 2 < m) {
-          w2 = lds8(ob - 8 * (c + 2));
-          x0 = lds8(X + 8 * (c + 2));
-        }
-        mir_para(acc, x1, w3, w0, w1);
-        if (c + 2 >= m) break;
-        if (c + 3 < m) {
-          w1 = lds8(ob - 8 * (c + 3));
-          x1 = lds8(X + 8 * (c + 3));
-        }
-        mir_para(acc, x0, w2, w3, w0);
-        if (c + 3 >= m) break;
-        if (c + 4 < m) {
-          w0 = lds8(ob - 8 * (c + 4));
-          x0 = lds8(X + 8 * (c + 4));
-        }
-        mir_para(acc, x1, w1, w2, w3);
-      }
-    }
+    mir_chunks(acc, X, X, m, m);
     mir_tail(acc, lds16(X + 8 * m), dst, m);
   }
+  mir_reduce(A, Bv, C, Hr, slice + kMirC96, shift, g, w);
+}
+
+// dst = x P(A) (Sec. 3.1: new state word k = sum_i p_i X(i + k), with
+// X(0..96) the base state and X(q) = X(q - 97) - X(q - 33) beyond), c and pos
+// by E (Sec. 3.2), shared by the four threads of the stream (t = 2w + g, both
+// warps of the CTA call it: barriers inside).  The window X(0..192) is built
+// once in W (193 words, the recurrence in three rounds whose inputs lie in
+// the rounds before); worker t then forms the 8-output blocks B = t, t + 4,
+// t + 8 (outputs 8B .. 8B+7: twelve chunks of 8 coefficients, each against
+// two window octets, then the p_96 term) and a quarter of output 96, so the
+// four workers each do 2,352 of the 9,409 multiply-adds.  P may hold
+// unmasked words (arithmetic mod 2^32); outputs are masked to 24 bits.
+__device__ __forceinline__ void apply_mirror(const ranmar_state_t* __restrict__ base,
+                                             const uint32_t (&E)[kMaxExpWords], bool active,
+                                             ranmar_state_t* __restrict__ dst,
+                                             const uint32_t* __restrict__ P,
+                                             uint32_t* __restrict__ W,
+                                             uint32_t* __restrict__ part96, unsigned t) {
+  const int ti = static_cast<int>(t);
+  const uint4* bx = reinterpret_cast<const uint4*>(base->x);   // 16-byte aligned
+  for (int q = ti; q < 24; q += 4) reinterpret_cast<uint4*>(W)[q] = bx[q];
+  if (t == 0) W[96] = base->x[96];
   __syncthreads();
-  const uint32_t a96 = slice[kMirC96] + Hr[95 - 65] - Hr[95 - 32];
-  uint32_t last = 0;
-  constexpr int kSplit = kMirGatherSplit;
-  static_assert(kSplit >= 2 && kSplit <= 4, "gather split");
-  if (w == 0) {
-    uint32_t prev7 = 0;                      // a_{-1} = 0 below block 0
-    mir_gather<0>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-    mir_gather<1>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-    if constexpr (kSplit > 2) mir_gather<2>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-    if constexpr (kSplit > 3) mir_gather<3>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-  } else {
-    // lane 1 hands lane 0 the word below warp 1's first block
-    uint32_t prev7 = 0;
-    if (g) prev7 = kSplit == 2 ? mir_a31(C, Hr) : kSplit == 3 ? mir_a47(C, Hr) : mir_a63(C, Hr);
-    if constexpr (kSplit <= 2) mir_gather<2>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-    if constexpr (kSplit <= 3) mir_gather<3>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-    mir_gather<4>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-    mir_gather<5>(A, Bv, C, Hr, g, shift, a96, prev7, last);
-    if (g) {  // position 96: the old a_95 (lane 1's v[7] of block 5) or a_96
-      const uint32_t w96 = shift ? last : a96;
-      A[96] = w96;
-      Bv[0] = w96;
+  for (int q = 97 + ti; q <= 129; q += 4) W[q] = W[q - kR] - W[q - kS];
+  __syncthreads();
+  for (int q = 130 + ti; q <= 162; q += 4) W[q] = W[q - kR] - W[q - kS];
+  __syncthreads();
+  for (int q = 163 + ti; q <= 192; q += 4) W[q] = W[q - kR] - W[q - kS];
+  __syncthreads();
+  // output 96 = sum_i p_i X(96 + i): worker t takes i = 24t .. 24t+23 (and 96)
+  {
+    uint32_t s96 = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      uint32_t p4[4], x4[4];
+      lds4_to(p4, P + 24 * ti + 4 * q);
+      lds4_to(x4, W + 96 + 24 * ti + 4 * q);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s96 += p4[u] * x4[u];
+    }
+    if (t == 3) s96 += P[96] * W[192];
+    part96[t] = s96;
+  }
+  const uint32_t p96 = P[96];
+#pragma unroll 1
+  for (int bi = 0; bi < 3; ++bi) {
+    const int B = ti + 4 * bi;
+    uint32_t acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] = 0;
+    Oct w0 = lds8(W + 8 * B);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {   // p_{8c+u} X(8B + 8c + u + r)
+      const Oct w1 = lds8(W + 8 * (B + c + 1));
+      const Oct pc = lds8(P + 8 * c);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[r] += pc.v[u] * (r + u < 8 ? w0.v[r + u] : w1.v[r + u - 8]);
+      }
+      w0 = w1;
+    }
+    const Oct wl = lds8(W + 8 * B + 96);   // X(8B + 96 + r)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] += p96 * wl.v[r];
+    if (active) {
+      uint4* ox = reinterpret_cast<uint4*>(dst->x + 8 * B);
+      ox[0] = make_uint4(acc[0] & kMask24, acc[1] & kMask24, acc[2] & kMask24, acc[3] & kMask24);
+      ox[1] = make_uint4(acc[4] & kMask24, acc[5] & kMask24, acc[6] & kMask24, acc[7] & kMask24);
     }
   }
   __syncthreads();
+  if (t == 0 && active) {
+    dst->x[96] = (part96[0] + part96[1] + part96[2] + part96[3]) & kMask24;
+    const uint32_t e = exp_mod_m(E);
+    // (c - e d) mod m = (c + (m - e) d) mod m, non-negative residue.
+    const uint64_t cn =
+        (static_cast<uint64_t>(base->c) + static_cast<uint64_t>(kModM - e) * kD) % kModM;
+    dst->c = static_cast<uint32_t>(cn);
+    dst->pos = base->pos + (static_cast<uint64_t>(E[1]) << 32 | E[0]);
+  }
 }
 
 // A = t^E mod phi (and Bv its reverse) for the stream of this lane pair by
@@ -392,7 +497,7 @@ __device__ __forceinline__ void poly_power_mirror(const uint32_t (&E)[kMaxExpWor
 //
 // dst = f^E(base) per stream: t^Ep mod phi by the square-and-multiply above
 // (Ep = E, or E mod T for RANMAR_JUMP_REDUCE_PERIOD), the application x P(A)
-// through the C/Hr region as its ring, and c / pos by the full E.
+// with its window in the C/Hr region, and c / pos by the full E.
 __global__ void __launch_bounds__(kMirThreads, 7) jump_kernel(
     const ranmar_state_t* __restrict__ d_base, uint64_t n_base,
     const uint32_t* __restrict__ d_base_idx, const uint32_t* __restrict__ d_exp,
@@ -432,8 +537,8 @@ __global__ void __launch_bounds__(kMirThreads, 7) jump_kernel(
   for (int w = 0; w < kMaxExpWords; ++w) Ep[w] = E[w];
   if (part.flags & RANMAR_JUMP_REDUCE_PERIOD) reduce_period(Ep);
   poly_power_mirror(Ep, active, slice, g, w);
-  if (w != 0) return;                        // the application is warp 0's
-  apply_pair(base, E, active, d_out + (active ? di : 0), slice + kMirA, slice + kMirC, g);
+  apply_mirror(base, E, active, d_out + (active ? di : 0), slice + kMirA, slice + kMirC,
+               slice + kMirP96, 2 * w + g);
 }
 
 // P_{E_i} = t^{E_i} mod phi alone (the polynomial part of a jump, Sec. 3.1),

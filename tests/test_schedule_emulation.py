@@ -497,3 +497,44 @@ def test_mirror_square_dense_and_planted_edge(orc):
         low, high, ls, hs = mirror_block_ops(m)
         n += 136 * len(low) + 120 * len(high) + 64 * len(ls) + 56 * len(hs) + 8
     assert 2 * n + 49 == 97 * 98 // 2
+
+
+def mirror_apply(p, x, plant=0):
+    """x P(A) as the four-worker application forms it: the window X(0..192)
+    (the recurrence in three rounds, each reading only earlier rounds), worker
+    t forming 8-output blocks t, t+4, t+8 from twelve chunks of 8 coefficients
+    (each against two window octets) plus the p_96 term, and output 96 as four
+    quarters (i = 24t .. 24t+23, and 96 by worker 3)."""
+    P = [int(v) for v in p]
+    W = [int(v) for v in x] + [0] * 96
+    for lo, hi in ((97, 129), (130, 162), (163, 192)):
+        for q in range(lo, hi + 1):
+            assert q - S < lo                     # inputs from the rounds before
+            W[q] = (W[q - R] - W[q - S]) % W32
+    out = [0] * R
+    for t in range(4):
+        for B in (t, t + 4, t + 8):
+            acc = [0] * 8
+            for c in range(12):
+                win = W[8 * (B + c): 8 * (B + c) + 16]
+                for u in range(8):
+                    for r in range(8):
+                        acc[r] += P[8 * c + u] * win[r + u + (plant == 1)]
+            for r in range(8):
+                acc[r] += P[96] * W[8 * B + 96 + r]
+            out[8 * B: 8 * B + 8] = [v % (1 << 24) for v in acc]
+    parts = [sum(P[24 * t + i] * W[96 + 24 * t + i] for i in range(24)) for t in range(4)]
+    parts[3] += P[96] * W[192]
+    out[96] = sum(parts) % (1 << 24)
+    return np.array(out, dtype=np.uint32)
+
+
+def test_mirror_apply_schedule_matches_oracle(orc):
+    x, c = orc.seeded_state(12345)
+    rng = np.random.default_rng(19)
+    for e in (0, 1, 96, 97, 10**6, 2**40 + 5, (1 << 120) + 12345):
+        p = orc.poly_pow_t(e)
+        assert np.array_equal(mirror_apply(p, x), orc.jump(x, c, e)[0]), e
+    p = rng.integers(0, 1 << 24, R).astype(np.uint32)
+    assert np.array_equal(mirror_apply(p, x), orc.apply_dot(x, p))
+    assert not np.array_equal(mirror_apply(p, x, plant=1), orc.apply_dot(x, p))
