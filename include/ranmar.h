@@ -125,7 +125,8 @@ int ranmar_seed_batch(const int32_t *d_seeds, size_t n, ranmar_state_t *d_out,
  * and sets c = (c_base - E_i d) mod m, pos = pos_base + E_i mod 2^64.
  * A CTA of two warps serves 16 streams, two lanes per stream in each warp
  * (lane 0 forms the low half of each square, lane 1 the high half from the
- * reversed polynomial; the two warps share each square's output blocks); a
+ * reversed polynomial; the two warps share each square's output blocks and
+ * the application's, four threads per stream); a
  * batch of at most RANMAR_SQUARE_WARP_AUTO_MAX streams instead gives each
  * stream a whole warp.  That cuts the LATENCY of one squaring about 5 times
  * (each stream's dependent chain is spread over 32 lanes instead of 4), not
