@@ -71,39 +71,6 @@ static_assert(kMirC + 193 <= kMirP96, "the application's window X(0..192) after 
 static_assert(kMirStreamWords % 32 == 4, "bank spread");
 static_assert(kMirB % 4 == 0 && kMirC % 4 == 0 && kMirH % 4 == 0, "16-byte alignment");
 
-// acc[r] += sum_{p+q=r} x_p y_q: the low triangle of a 16 x 16 block product.
-__device__ __forceinline__ void mir_tri_low(uint32_t (&acc)[16], const Hex& x, const Hex& y) {
-#pragma unroll
-  for (int p = 0; p < 16; ++p) {
-#pragma unroll
-    for (int q = 0; q < 16 - p; ++q) acc[p + q] += x.v[p] * y.v[q];
-  }
-}
-// acc[r] += sum_{p+q=r+16} x_p y_q: the high triangle.
-__device__ __forceinline__ void mir_tri_high(uint32_t (&acc)[16], const Hex& x, const Hex& y) {
-#pragma unroll
-  for (int p = 1; p < 16; ++p) {
-#pragma unroll
-    for (int q = 16 - p; q < 16; ++q) acc[p + q - 16] += x.v[p] * y.v[q];
-  }
-}
-// Cross terms p < q of x^2 with p + q <= 15.
-__device__ __forceinline__ void mir_sym_low(uint32_t (&acc)[16], const Hex& x) {
-#pragma unroll
-  for (int p = 0; p < 8; ++p) {
-#pragma unroll
-    for (int q = p + 1; q < 16 - p; ++q) acc[p + q] += x.v[p] * x.v[q];
-  }
-}
-// Cross terms p < q of x^2 with p + q >= 16.
-__device__ __forceinline__ void mir_sym_high(uint32_t (&acc)[16], const Hex& x) {
-#pragma unroll
-  for (int p = 1; p < 16; ++p) {
-#pragma unroll
-    for (int q = (p + 1 > 16 - p ? p + 1 : 16 - p); q < 16; ++q) acc[p + q - 16] += x.v[p] * x.v[q];
-  }
-}
-
 // One full chunk of output block m: acc[r] += sum_{u<8} x_{8c+u} w[r-u+8]
 // for r = 0..15, with w[k] = x_{16m-8c-8+k} (24 words as three octets:
 // w[0..7] = lo, w[8..15] = mid, w[16..23] = hi); all its terms have i < j.
