@@ -241,12 +241,24 @@ __device__ __forceinline__ uint32_t exp_bit(const uint32_t (&E)[kMaxExpWords], i
   return (exp_word(E, p >> 5) >> (p & 31)) & 1u;
 }
 
-// Six bits of E starting at bit p (p >= 0).
-__device__ __forceinline__ uint32_t exp_bits6(const uint32_t (&E)[kMaxExpWords], int p) {
+// Seven bits of E starting at bit p (p >= 0).
+__device__ __forceinline__ uint32_t exp_bits7(const uint32_t (&E)[kMaxExpWords], int p) {
   const int w = p >> 5, sh = p & 31;
   const uint32_t lo = exp_word(E, w);
   const uint32_t hi = (w + 1 < kMaxExpWords) ? exp_word(E, w + 1) : 0u;
-  return __funnelshift_r(lo, hi, sh) & 63u;
+  return __funnelshift_r(lo, hi, sh) & 127u;
+}
+
+// The leading (up to) seven bits of E: v0 < 128 and the bit below them
+// (-1 when they are all of E).  t^v0 mod phi is t^v0 for v0 < 97, else
+// t^(v0-97) - t^(v0-33) (t^97 = 1 - t^64, and v0 - 33 < 97).
+__device__ __forceinline__ uint32_t exp_lead7(const uint32_t (&E)[kMaxExpWords], int L, int& p) {
+  if (L <= 7) {
+    p = -1;
+    return E[0] & 127u;
+  }
+  p = L - 8;
+  return exp_bits7(E, L - 7);
 }
 
 __device__ __forceinline__ int exp_bitlen(const uint32_t (&E)[kMaxExpWords]) {

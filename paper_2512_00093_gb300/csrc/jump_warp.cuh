@@ -307,18 +307,13 @@ __device__ __forceinline__ void square_times_warp(uint32_t* __restrict__ s, uint
 __device__ __forceinline__ void poly_power_warp(const uint32_t (&E)[kMaxExpWords],
                                                 uint32_t* __restrict__ s, unsigned lane) {
   const int L = exp_bitlen(E);
-  // leading (up to) six bits: t^v0 with v0 < 64 < 97 is a monomial
-  uint32_t v0;
+  // leading (up to) seven bits: t^v0 (v0 < 97) or t^(v0-97) - t^(v0-33)
   int pbit;
-  if (L <= 6) {
-    v0 = E[0] & 63u;
-    pbit = -1;
-  } else {
-    v0 = exp_bits6(E, L - 6);
-    pbit = L - 7;
-  }
+  const int v0 = static_cast<int>(exp_lead7(E, L, pbit));
+  const int lo = v0 < kR ? v0 : v0 - kR, hi = v0 < kR ? -1 : v0 - kS;
   uint32_t* a = s + kWjA;
-  for (int q = static_cast<int>(lane); q < kR; q += 32) a[q] = q == static_cast<int>(v0) ? 1u : 0u;
+  for (int q = static_cast<int>(lane); q < kR; q += 32)
+    a[q] = q == lo ? 1u : (q == hi ? 0xFFFFFFFFu : 0u);
   __syncwarp();
 #pragma unroll 1
   for (; pbit >= 0; --pbit) square_times_warp(s, exp_bit(E, pbit), lane);

@@ -431,23 +431,24 @@ __device__ __forceinline__ void poly_power_mirror(const uint32_t (&E)[kMaxExpWor
                                                   unsigned w) {
   const int nb = active ? exp_bitlen(E) : 0;
   const int L = static_cast<int>(__reduce_max_sync(kFull, static_cast<unsigned>(nb)));
-  // Leading (up to) six bits: P = t^v0 with v0 < 64 < 97 is a monomial.
-  uint32_t v0;
+  // Leading (up to) seven bits: P = t^v0 (v0 < 97) or t^(v0-97) - t^(v0-33).
   int p;
-  if (L <= 6) {
-    v0 = E[0] & 63u;
-    p = -1;
-  } else {
-    v0 = exp_bits6(E, L - 6);
-    p = L - 7;
-  }
+  uint32_t v0 = exp_lead7(E, L, p);
   if (!active) v0 = 0;
   for (int q = static_cast<int>(g + 2 * w); q < (kMirB + 100) / 4; q += 4)
     reinterpret_cast<uint4*>(slice)[q] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   if (g == 0 && w == 0) {
-    slice[kMirA + v0] = 1u;
-    slice[kMirB + 96 - v0] = 1u;
+    if (v0 < static_cast<uint32_t>(kR)) {
+      slice[kMirA + v0] = 1u;
+      slice[kMirB + 96 - v0] = 1u;
+    } else {
+      const uint32_t lo = v0 - kR, hi = v0 - kS;   // hi = v0 - 33 < 97
+      slice[kMirA + lo] = 1u;
+      slice[kMirA + hi] = 0xFFFFFFFFu;            // -1 mod 2^32
+      slice[kMirB + 96 - lo] = 1u;
+      slice[kMirB + 96 - hi] = 0xFFFFFFFFu;
+    }
   }
   __syncthreads();
 #pragma unroll 1

@@ -110,17 +110,24 @@ def test_warp_product_schedule_matches_oracle(orc):
         assert np.array_equal(warp_mulmod(a, b), orc.poly_mulmod(a, b))
 
 
+def lead7(e):
+    """The kernels' start: the leading (up to) seven bits v0 of e, the bit
+    below them (-1 when none), and t^v0 mod phi as (degree, coefficient)
+    terms: t^v0 below 97, else t^(v0-97) - t^(v0-33) (t^97 = 1 - t^64)."""
+    L = e.bit_length()
+    v0, p = (e & 127, -1) if L <= 7 else ((e >> (L - 7)) & 127, L - 8)
+    terms = [(v0, 1)] if v0 < R else [(v0 - R, 1), (v0 - S, -1)]
+    return v0, p, terms
+
+
 def warp_poly_power(e):
     """t^e mod phi as the warp square-and-multiply schedules it: the leading
-    six bits as a monomial, then per bit a warp square and, on a 1 bit, the
-    shift by t with the fold t^97 = 1 - t^64."""
-    L = e.bit_length()
-    if L <= 6:
-        v0, p = e & 63, -1
-    else:
-        v0, p = (e >> (L - 6)) & 63, L - 7
+    seven bits in closed form, then per bit a warp square and, on a 1 bit,
+    the shift by t with the fold t^97 = 1 - t^64."""
+    _, p, terms = lead7(e)
     a = np.zeros(R, np.uint32)
-    a[v0] = 1
+    for d, cf in terms:
+        a[d] = cf & MASK
     while p >= 0:
         a = warp_mulmod(a, a.copy())
         if (e >> p) & 1:
@@ -130,6 +137,19 @@ def warp_poly_power(e):
             a = np.array([x & MASK for x in v], dtype=np.uint32)
         p -= 1
     return a
+
+
+def test_lead7_start_matches_oracle(orc):
+    # every start the kernels can take (v0 < 128) against the oracle's t^v0
+    for v0 in range(128):
+        _, p, terms = lead7(v0)
+        assert p == -1
+        a = np.zeros(R, np.int64)
+        for d, cf in terms:
+            a[d] += cf
+        assert np.array_equal((a % (1 << 24)).astype(np.uint32), orc.poly_pow_t(v0)), v0
+    assert lead7((1 << 120) + 12345)[:2] == (64, 113)
+    assert lead7(1000)[:2] == (125, 2)
 
 
 def test_warp_square_multiply_schedule_matches_oracle(orc):
@@ -450,14 +470,11 @@ def mirror_square(A, Bv, shift, plant=0):
 
 
 def mirror_poly_power(e, plant=0):
-    L = e.bit_length()
-    if L <= 6:
-        v0, p = e & 63, -1
-    else:
-        v0, p = (e >> (L - 6)) & 63, L - 7
+    _, p, terms = lead7(e)
     A, Bv = [0] * 100, [0] * 100
-    A[v0] = 1
-    Bv[96 - v0] = 1
+    for d, cf in terms:
+        A[d] = cf % W32
+        Bv[96 - d] = cf % W32
     while p >= 0:
         A, Bv = mirror_square(A, Bv, (e >> p) & 1, plant)
         p -= 1
