@@ -1051,6 +1051,146 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak, probes):
     except Exception as ex_:  # noqa: BLE001
         res["large_jumps"]["plan"] = {"error": f"{type(ex_).__name__}: {ex_}"}
 
+    # Table 1 restated on the GPU: the same 65,536 x 4,096 outputs through the
+    # modular-integer form (u24 and f32 outputs) and the floating-point form
+    # (Algorithm 1 in float and in double); generation only, states as jumped.
+    w2 = Partitioned()
+    st0 = table.partition(rm.seed(w2.seed).to(dev), w2.J, 0, w2.n_streams)
+    tot2 = w2.n_streams * w2.count
+    d2 = rm.make_desc(np.arange(w2.n_streams), np.arange(w2.n_streams) * w2.count, w2.count, 0,
+                      device=dev)
+    o32 = torch.empty(tot2, dtype=torch.float32, device=dev)
+    o64 = torch.empty(tot2, dtype=torch.float64, device=dev)
+    oi = o32.view(torch.int32)
+    forms = {"modular_u24": lambda: rm.generate_u24(st0, d2, oi),
+             "modular_f32": lambda: rm.generate_f32(st0, d2, o32),
+             "float_alg1_f32": lambda: rm.generate_alg1_f32(st0, d2, o32),
+             "float_alg1_f64": lambda: rm.generate_alg1_f64(st0, d2, o64)}
+    fv = {}
+    for name, fn in forms.items():
+        ms_f = timed(fn)
+        fv[name] = {"ms": ms_f, "outputs_per_s": tot2 / (ms_f * 1e-3)}
+    fv["speedup_modular_f32_over_float_f32"] = fv["float_alg1_f32"]["ms"] / fv["modular_f32"]["ms"]
+    fv["speedup_modular_f32_over_float_f64"] = fv["float_alg1_f64"]["ms"] / fv["modular_f32"]["ms"]
+    fv["note"] = ("generation of 2^28 outputs.  The integer (Algorithm 2) and float32 "
+                  "(Algorithm 1) forms are both store-bound at the same time, so the paper's "
+                  "CPU speedup of the modular form does not appear on the GPU.  The float64 "
+                  "form is bound by GB300's FP64 rate, not by its bytes (twice the bytes "
+                  "would cost 2x, not ~27x): see fp64_rate")
+    # the FP64 bound: Algorithm 1 in double does about 3 dependent FP64
+    # add/compare/select operations per output on a chip with a small FP64 rate
+    fp64_ops = 6 * tot2      # per output: u_i - u_j, c - cd, uni - c, three conditional adds
+    fv["fp64_rate"] = {"outputs_per_s": fv["float_alg1_f64"]["outputs_per_s"],
+                       "ratio_to_f32": fv["float_alg1_f64"]["ms"] / fv["float_alg1_f32"]["ms"],
+                       "bytes_ratio": 2.0,
+                       "fp64_ops_per_output": 6,
+                       "fp64_adds_per_s": fp64_ops / (fv["float_alg1_f64"]["ms"] * 1e-3),
+                       "probe_dadd_per_s": probes["dadd_tops"] * 1e12,
+                       "bound_ms": fp64_ops / (probes["dadd_tops"] * 1e12) * 1e3,
+                       "note": "bound_ms = 6 double adds per output at the measured FP64 add "
+                               "rate; the f64 kernel's time against it shows the FP64 bound"}
+    res["float_vs_modular"] = fv
+    del o32, o64, st0
+
+    # partition plan: 256 from the powers of t^J + one radix-256 level of jump matrices
+    # on the tensor cores, against the per-stream table jump, same states
+    try:
+        pw = Partitioned()
+        pbase = rm.seed(pw.seed).to(dev)
+        tb = time.perf_counter()
+        plan = rm.Plan(table, pw.J, pw.n_streams)
+        plan_build = (time.perf_counter() - tb) * 1e3
+        pst = torch.empty((pw.n_streams, rm.STATE_WORDS), dtype=torch.int32, device=dev)
+        ms_p = timed(lambda: plan.partition(pbase, 0, pw.n_streams, out=pst))
+        ms_t = timed(lambda: table.partition(pbase, pw.J, 0, pw.n_streams, out=pst))
+        same = bool(torch.equal(plan.partition(pbase, 0, pw.n_streams),
+                                table.partition(pbase, pw.J, 0, pw.n_streams)))
+        levels = {str(m): timed(lambda m=m: plan.partition(pbase, 0, m, out=pst))
+                  for m in (256, 4096)}
+        res["partition_plan"] = {
+            "streams": pw.n_streams, "build_ms": plan_build, "ms": ms_p,
+            "table_jump_ms": ms_t, "states_identical": same,
+            "ms_for_first_streams": levels,
+            "macs_per_stream": 97 * 97,
+            "note": "256 streams from the plan's powers of t^J, then one level x -> x M_{r 256 J}"}
+        plan.close()
+        del pst
+        # many items per CTA: 256 streams expanded to 2^20 (the radix-256 level,
+        # then a radix-16 level of 7,680 items), each method, L2 flushed before each
+        nb = 1 << 20
+        bplan = rm.Plan(table, pw.J, nb)
+        bst = bplan.partition(pbase, 0, nb)
+        flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
+        ref4k = table.partition(pbase, pw.J, 0, 4096)
+        big = {"streams": nb, "algorithmic_flops": 2.0 * 6 * 97 * 97 * (nb - 256),
+               "note": "CUDA events around ranmar_plan_expand (the states of all 2^20 "
+                       "streams from the first 256), L2 flushed before each; tensor_frac "
+                       "of the measured bf16 burst peak"}
+        tc_peak = peaks.get("bf16_tflops", 1900.0)
+        for mname, mth in [("tensor_pipelined", rm.Plan.TENSOR_PIPELINED),
+                           ("tensor", rm.Plan.TENSOR)]:
+            bplan.set_method(mth)
+
+            def one(bplan=bplan, bst=bst):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                bplan.expand(bst, nb, stream=stream)
+                b0.record(stream)
+                torch.cuda.synchronize()
+                return a0.elapsed_time(b0)
+            one()
+            ms_b = min(one() for _ in range(5))
+            tf = big["algorithmic_flops"] / (ms_b * 1e-3) / 1e12
+            big[mname] = {"ms": ms_b, "tflops": tf, "tensor_frac": tf / tc_peak,
+                          "status": bplan.status(),
+                          "first_4096_identical": bool(torch.equal(bst[:4096], ref4k))}
+        res["partition_plan"]["expand_2p20"] = big
+        bplan.close()
+        del bst, flush
+    except Exception as e:  # noqa: BLE001
+        res["partition_plan"] = {"error": f"{type(e).__name__}: {e}"}
+
+    # general lags (the concluding remarks): the jump of x_n = x_{n-r} - x_{n-s}
+    # mod 2^e for growing r, classical vs Karatsuba squarings (64-bit
+    # exponents with the top bit set: 63 squarings each)
+    try:
+        lag = {}
+        rng = np.random.default_rng(1)
+        for (r, s_, e) in [(97, 33, 24), (607, 273, 24), (1279, 418, 32), (2048, 1029, 24)]:
+            nl = 4096 if r < 1000 else 1216
+            xl = torch.as_tensor(rng.integers(0, 1 << e, (nl, r), dtype=np.uint64)
+                                 .astype(np.uint32).view(np.int32), device=dev)
+            exl = rm.exps_tensor([int(v) | (1 << 63) for v in rng.integers(0, 1 << 62, nl,
+                                                                          dtype=np.uint64)],
+                                 2, device=dev)
+            idl = torch.arange(nl, dtype=torch.int32, device=dev)
+            ol = torch.empty_like(xl)
+            row = {"streams": nl}
+            for name, m in [("classical", rm.LFG_CLASSICAL), ("karatsuba", rm.LFG_KARATSUBA)] + \
+                    [(f"karatsuba_L{L}", rm.LFG_KARATSUBA_LEVELS(L)) for L in (1, 2, 3)]:
+                try:
+                    L = rm.lfg_karatsuba_levels(r, s_, e, m)
+                    ms_l = timed(lambda m=m: rm.lfg_jump(r, s_, e, xl, exl, base_idx=idl, out=ol,
+                                                         method=m), reps=2)
+                    M = -(-r // (1 << L))
+                    macs = nl * (63 * (3 ** L) * M * M + r * r)
+                    row[name] = {"levels": L, "ms": ms_l, "jumps_per_s": nl / (ms_l * 1e-3),
+                                 "leaf_macs_per_s": macs / (ms_l * 1e-3),
+                                 "alu_frac": macs / (ms_l * 1e-3) / 1e12 / alu_peak}
+                except rm.RanmarError:
+                    row[name] = None
+            lag[f"r{r}_s{s_}_e{e}"] = row
+            del xl, exl, idl, ol
+        res["general_lags"] = lag
+    except Exception as ex_:  # noqa: BLE001
+        res["general_lags"] = {"error": f"{type(ex_).__name__}: {ex_}"}
+
+    # The batched workload runs last: once its ~38 GB of buffers are freed,
+    # new device buffers were measured ~17% slower to fill (the same
+    # generation of 2^28 outputs 0.177 -> 0.208 ms), which would skew the
+    # HBM-bound side measurements above.
     # Batched uneven workload at full size: 10^6 streams at k*2^64, lengths
     # log-uniform in [64, 65536] (seed 7), f32 packed by prefix sum.  One step
     # = partition (the plan; the per-stream table jump beside it) + device
@@ -1217,142 +1357,6 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak, probes):
     del outf, stb, desc, order, desc_g, ord_g
     b.close()
     torch.cuda.empty_cache()
-
-    # Table 1 restated on the GPU: the same 65,536 x 4,096 outputs through the
-    # modular-integer form (u24 and f32 outputs) and the floating-point form
-    # (Algorithm 1 in float and in double); generation only, states as jumped.
-    w2 = Partitioned()
-    st0 = table.partition(rm.seed(w2.seed).to(dev), w2.J, 0, w2.n_streams)
-    tot2 = w2.n_streams * w2.count
-    d2 = rm.make_desc(np.arange(w2.n_streams), np.arange(w2.n_streams) * w2.count, w2.count, 0,
-                      device=dev)
-    o32 = torch.empty(tot2, dtype=torch.float32, device=dev)
-    o64 = torch.empty(tot2, dtype=torch.float64, device=dev)
-    oi = o32.view(torch.int32)
-    forms = {"modular_u24": lambda: rm.generate_u24(st0, d2, oi),
-             "modular_f32": lambda: rm.generate_f32(st0, d2, o32),
-             "float_alg1_f32": lambda: rm.generate_alg1_f32(st0, d2, o32),
-             "float_alg1_f64": lambda: rm.generate_alg1_f64(st0, d2, o64)}
-    fv = {}
-    for name, fn in forms.items():
-        ms_f = timed(fn)
-        fv[name] = {"ms": ms_f, "outputs_per_s": tot2 / (ms_f * 1e-3)}
-    fv["speedup_modular_f32_over_float_f32"] = fv["float_alg1_f32"]["ms"] / fv["modular_f32"]["ms"]
-    fv["speedup_modular_f32_over_float_f64"] = fv["float_alg1_f64"]["ms"] / fv["modular_f32"]["ms"]
-    fv["note"] = ("generation of 2^28 outputs.  The integer (Algorithm 2) and float32 "
-                  "(Algorithm 1) forms are both store-bound at the same time, so the paper's "
-                  "CPU speedup of the modular form does not appear on the GPU.  The float64 "
-                  "form is bound by GB300's FP64 rate, not by its bytes (twice the bytes "
-                  "would cost 2x, not ~27x): see fp64_rate")
-    # the FP64 bound: Algorithm 1 in double does about 3 dependent FP64
-    # add/compare/select operations per output on a chip with a small FP64 rate
-    fp64_ops = 6 * tot2      # per output: u_i - u_j, c - cd, uni - c, three conditional adds
-    fv["fp64_rate"] = {"outputs_per_s": fv["float_alg1_f64"]["outputs_per_s"],
-                       "ratio_to_f32": fv["float_alg1_f64"]["ms"] / fv["float_alg1_f32"]["ms"],
-                       "bytes_ratio": 2.0,
-                       "fp64_ops_per_output": 6,
-                       "fp64_adds_per_s": fp64_ops / (fv["float_alg1_f64"]["ms"] * 1e-3),
-                       "probe_dadd_per_s": probes["dadd_tops"] * 1e12,
-                       "bound_ms": fp64_ops / (probes["dadd_tops"] * 1e12) * 1e3,
-                       "note": "bound_ms = 6 double adds per output at the measured FP64 add "
-                               "rate; the f64 kernel's time against it shows the FP64 bound"}
-    res["float_vs_modular"] = fv
-    del o32, o64, st0
-
-    # partition plan: 256 from the powers of t^J + one radix-256 level of jump matrices
-    # on the tensor cores, against the per-stream table jump, same states
-    try:
-        pw = Partitioned()
-        pbase = rm.seed(pw.seed).to(dev)
-        tb = time.perf_counter()
-        plan = rm.Plan(table, pw.J, pw.n_streams)
-        plan_build = (time.perf_counter() - tb) * 1e3
-        pst = torch.empty((pw.n_streams, rm.STATE_WORDS), dtype=torch.int32, device=dev)
-        ms_p = timed(lambda: plan.partition(pbase, 0, pw.n_streams, out=pst))
-        ms_t = timed(lambda: table.partition(pbase, pw.J, 0, pw.n_streams, out=pst))
-        same = bool(torch.equal(plan.partition(pbase, 0, pw.n_streams),
-                                table.partition(pbase, pw.J, 0, pw.n_streams)))
-        levels = {str(m): timed(lambda m=m: plan.partition(pbase, 0, m, out=pst))
-                  for m in (256, 4096)}
-        res["partition_plan"] = {
-            "streams": pw.n_streams, "build_ms": plan_build, "ms": ms_p,
-            "table_jump_ms": ms_t, "states_identical": same,
-            "ms_for_first_streams": levels,
-            "macs_per_stream": 97 * 97,
-            "note": "256 streams from the plan's powers of t^J, then one level x -> x M_{r 256 J}"}
-        plan.close()
-        del pst
-        # many items per CTA: 256 streams expanded to 2^20 (the radix-256 level,
-        # then a radix-16 level of 7,680 items), each method, L2 flushed before each
-        nb = 1 << 20
-        bplan = rm.Plan(table, pw.J, nb)
-        bst = bplan.partition(pbase, 0, nb)
-        flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
-        ref4k = table.partition(pbase, pw.J, 0, 4096)
-        big = {"streams": nb, "algorithmic_flops": 2.0 * 6 * 97 * 97 * (nb - 256),
-               "note": "CUDA events around ranmar_plan_expand (the states of all 2^20 "
-                       "streams from the first 256), L2 flushed before each; tensor_frac "
-                       "of the measured bf16 burst peak"}
-        tc_peak = peaks.get("bf16_tflops", 1900.0)
-        for mname, mth in [("tensor_pipelined", rm.Plan.TENSOR_PIPELINED),
-                           ("tensor", rm.Plan.TENSOR)]:
-            bplan.set_method(mth)
-
-            def one(bplan=bplan, bst=bst):
-                flush.fill_(1)
-                torch.cuda.synchronize()
-                a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a0.record(stream)
-                bplan.expand(bst, nb, stream=stream)
-                b0.record(stream)
-                torch.cuda.synchronize()
-                return a0.elapsed_time(b0)
-            one()
-            ms_b = min(one() for _ in range(5))
-            tf = big["algorithmic_flops"] / (ms_b * 1e-3) / 1e12
-            big[mname] = {"ms": ms_b, "tflops": tf, "tensor_frac": tf / tc_peak,
-                          "status": bplan.status(),
-                          "first_4096_identical": bool(torch.equal(bst[:4096], ref4k))}
-        res["partition_plan"]["expand_2p20"] = big
-        bplan.close()
-        del bst, flush
-    except Exception as e:  # noqa: BLE001
-        res["partition_plan"] = {"error": f"{type(e).__name__}: {e}"}
-
-    # general lags (the concluding remarks): the jump of x_n = x_{n-r} - x_{n-s}
-    # mod 2^e for growing r, classical vs Karatsuba squarings (64-bit
-    # exponents with the top bit set: 63 squarings each)
-    try:
-        lag = {}
-        rng = np.random.default_rng(1)
-        for (r, s_, e) in [(97, 33, 24), (607, 273, 24), (1279, 418, 32), (2048, 1029, 24)]:
-            nl = 4096 if r < 1000 else 1216
-            xl = torch.as_tensor(rng.integers(0, 1 << e, (nl, r), dtype=np.uint64)
-                                 .astype(np.uint32).view(np.int32), device=dev)
-            exl = rm.exps_tensor([int(v) | (1 << 63) for v in rng.integers(0, 1 << 62, nl,
-                                                                          dtype=np.uint64)],
-                                 2, device=dev)
-            idl = torch.arange(nl, dtype=torch.int32, device=dev)
-            ol = torch.empty_like(xl)
-            row = {"streams": nl}
-            for name, m in [("classical", rm.LFG_CLASSICAL), ("karatsuba", rm.LFG_KARATSUBA)] + \
-                    [(f"karatsuba_L{L}", rm.LFG_KARATSUBA_LEVELS(L)) for L in (1, 2, 3)]:
-                try:
-                    L = rm.lfg_karatsuba_levels(r, s_, e, m)
-                    ms_l = timed(lambda m=m: rm.lfg_jump(r, s_, e, xl, exl, base_idx=idl, out=ol,
-                                                         method=m), reps=2)
-                    M = -(-r // (1 << L))
-                    macs = nl * (63 * (3 ** L) * M * M + r * r)
-                    row[name] = {"levels": L, "ms": ms_l, "jumps_per_s": nl / (ms_l * 1e-3),
-                                 "leaf_macs_per_s": macs / (ms_l * 1e-3),
-                                 "alu_frac": macs / (ms_l * 1e-3) / 1e12 / alu_peak}
-                except rm.RanmarError:
-                    row[name] = None
-            lag[f"r{r}_s{s_}_e{e}"] = row
-            del xl, exl, idl, ol
-        res["general_lags"] = lag
-    except Exception as ex_:  # noqa: BLE001
-        res["general_lags"] = {"error": f"{type(ex_).__name__}: {ex_}"}
 
     return res
 
