@@ -100,7 +100,7 @@ def emit(obj):
 
 
 def dense_squarings(e: int) -> int:
-    return max(0, e.bit_length() - 8)
+    return max(0, e.bit_length() - 11)
 
 
 def jump_macs(exps) -> int:
@@ -397,7 +397,7 @@ def config4(rm, torch, dev, stream, alu_peak, alu_derived, steps=5) -> dict:
                              "frac": macs / (jump_ms * 1e-3) / 1e12 / alu_peak,
                              "peak_source": "measured in this run: independent mad.lo.u32 chains",
                              "frac_of_derived": macs / (jump_ms * 1e-3) / 1e12 / alu_derived,
-                             "macs_per_stream": "(bitlen(E) - 8) x 4,753 (symmetric squares) + "
+                             "macs_per_stream": "(bitlen(E) - 11) x 4,753 (symmetric squares) + "
                                                 "9,409 (application)"}}
     # states of the last step: the same numbers by the fixed-base table jump
     chk = rm.Table()

@@ -241,24 +241,55 @@ __device__ __forceinline__ uint32_t exp_bit(const uint32_t (&E)[kMaxExpWords], i
   return (exp_word(E, p >> 5) >> (p & 31)) & 1u;
 }
 
-// Seven bits of E starting at bit p (p >= 0).
-__device__ __forceinline__ uint32_t exp_bits7(const uint32_t (&E)[kMaxExpWords], int p) {
+// kBits (<= 32) bits of E starting at bit p (p >= 0).
+template <int kBits>
+__device__ __forceinline__ uint32_t exp_bits(const uint32_t (&E)[kMaxExpWords], int p) {
   const int w = p >> 5, sh = p & 31;
   const uint32_t lo = exp_word(E, w);
   const uint32_t hi = (w + 1 < kMaxExpWords) ? exp_word(E, w + 1) : 0u;
-  return __funnelshift_r(lo, hi, sh) & 127u;
+  return __funnelshift_r(lo, hi, sh) & ((1u << kBits) - 1u);
 }
 
-// The leading (up to) seven bits of E: v0 < 128 and the bit below them
-// (-1 when they are all of E).  t^v0 mod phi is t^v0 for v0 < 97, else
-// t^(v0-97) - t^(v0-33) (t^97 = 1 - t^64, and v0 - 33 < 97).
-__device__ __forceinline__ uint32_t exp_lead7(const uint32_t (&E)[kMaxExpWords], int L, int& p) {
-  if (L <= 7) {
+// The leading (up to) kLeadBits bits v0 of an exponent whose bit length is
+// at most L, and the bit below them (-1 when they are all of E): the
+// square-and-multiply starts from t^v0 mod phi.
+constexpr int kLeadBits = 10;
+__device__ __forceinline__ uint32_t exp_lead(const uint32_t (&E)[kMaxExpWords], int L, int& p) {
+  if (L <= kLeadBits) {
     p = -1;
-    return E[0] & 127u;
+    return E[0] & ((1u << kLeadBits) - 1u);
   }
-  p = L - 8;
-  return exp_bits7(E, L - 7);
+  p = L - kLeadBits - 1;
+  return exp_bits<kLeadBits>(E, L - kLeadBits);
+}
+
+// dst = src (1 - t^64) mod phi at n = first + kStep k < 97 (0 <= first <
+// kStep; src and dst distinct, 97 words each).  t^64 src folds in closed
+// form (t^97 = 1 - t^64): for n <= 63 its coefficient is src_{n+33} - [n <=
+// 30] src_{n+66}, for n >= 64 it is src_{n-64} - src_{n-31} + [n <= 94]
+// src_{n+2}.  With v0 = 97 q + r, t^v0 = t^r (t^97)^q = t^r (1 - t^64)^q mod
+// phi.  Unrolled over k, so the loads are independent and every range test
+// that holds for the whole of n's range kStep k .. kStep k + kStep - 1 folds
+// at compile time.
+template <int kStep>
+__device__ __forceinline__ void mul_one_minus_t64(const uint32_t* __restrict__ src,
+                                                  uint32_t* __restrict__ dst, int first) {
+#pragma unroll
+  for (int k = 0; k < (kR + kStep - 1) / kStep; ++k) {
+    const int lo = kStep * k, hi = kStep * k + kStep - 1;   // n's range
+    const int n = first + lo;
+    if (hi >= kR && n >= kR) continue;
+    uint32_t v = src[n];
+    if (hi <= 63 || (lo <= 63 && n <= 63)) {
+      v -= src[n + 33];
+      if (hi <= 30 || (lo <= 30 && n <= 30)) v += src[n + 66];
+    } else {
+      v -= src[n - 64];
+      v += src[n - 31];
+      if (hi <= 94 || (lo <= 94 && n <= 94)) v -= src[n + 2];
+    }
+    dst[n] = v;
+  }
 }
 
 __device__ __forceinline__ int exp_bitlen(const uint32_t (&E)[kMaxExpWords]) {

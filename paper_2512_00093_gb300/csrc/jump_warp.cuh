@@ -307,14 +307,24 @@ __device__ __forceinline__ void square_times_warp(uint32_t* __restrict__ s, uint
 __device__ __forceinline__ void poly_power_warp(const uint32_t (&E)[kMaxExpWords],
                                                 uint32_t* __restrict__ s, unsigned lane) {
   const int L = exp_bitlen(E);
-  // leading (up to) seven bits: t^v0 (v0 < 97) or t^(v0-97) - t^(v0-33)
+  // leading (up to) ten bits v0 = 97 q + r: t^r (1 - t^64)^q, the factors
+  // applied between a and the product scratch
   int pbit;
-  const int v0 = static_cast<int>(exp_lead7(E, L, pbit));
-  const int lo = v0 < kR ? v0 : v0 - kR, hi = v0 < kR ? -1 : v0 - kS;
+  const uint32_t v0 = exp_lead(E, L, pbit);
+  const int q = static_cast<int>(v0 / kR), r = static_cast<int>(v0) - q * kR;
   uint32_t* a = s + kWjA;
-  for (int q = static_cast<int>(lane); q < kR; q += 32)
-    a[q] = q == lo ? 1u : (q == hi ? 0xFFFFFFFFu : 0u);
+  uint32_t* T = s + kWjC;
+  for (int i = static_cast<int>(lane); i < kR; i += 32) a[i] = i == r ? 1u : 0u;
   __syncwarp();
+#pragma unroll 1
+  for (int st = 0; st < q; ++st) {
+    mul_one_minus_t64<32>((st & 1) ? T : a, (st & 1) ? a : T, static_cast<int>(lane));
+    __syncwarp();
+  }
+  if (q & 1) {
+    for (int i = static_cast<int>(lane); i < kR; i += 32) a[i] = T[i];
+    __syncwarp();
+  }
 #pragma unroll 1
   for (; pbit >= 0; --pbit) square_times_warp(s, exp_bit(E, pbit), lane);
 }

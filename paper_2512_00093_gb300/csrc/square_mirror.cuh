@@ -431,24 +431,33 @@ __device__ __forceinline__ void poly_power_mirror(const uint32_t (&E)[kMaxExpWor
                                                   unsigned w) {
   const int nb = active ? exp_bitlen(E) : 0;
   const int L = static_cast<int>(__reduce_max_sync(kFull, static_cast<unsigned>(nb)));
-  // Leading (up to) seven bits: P = t^v0 (v0 < 97) or t^(v0-97) - t^(v0-33).
+  // Leading (up to) ten bits v0 = 97 q + r: P = t^r (1 - t^64)^q, the q
+  // factors applied by all four threads of the stream (T, in the C region,
+  // and A take turns as source and destination: the result is in T for odd
+  // q), then the forward and reversed copies.
   int p;
-  uint32_t v0 = exp_lead7(E, L, p);
+  uint32_t v0 = exp_lead(E, L, p);
   if (!active) v0 = 0;
-  for (int q = static_cast<int>(g + 2 * w); q < (kMirB + 100) / 4; q += 4)
-    reinterpret_cast<uint4*>(slice)[q] = make_uint4(0u, 0u, 0u, 0u);
+  const uint32_t q = v0 / kR, r = v0 - q * kR;
+  const int Q = static_cast<int>(__reduce_max_sync(kFull, q));   // the same in every warp
+  for (int i = static_cast<int>(g + 2 * w); i < (kMirB + 100) / 4; i += 4)
+    reinterpret_cast<uint4*>(slice)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
-  if (g == 0 && w == 0) {
-    if (v0 < static_cast<uint32_t>(kR)) {
-      slice[kMirA + v0] = 1u;
-      slice[kMirB + 96 - v0] = 1u;
-    } else {
-      const uint32_t lo = v0 - kR, hi = v0 - kS;   // hi = v0 - 33 < 97
-      slice[kMirA + lo] = 1u;
-      slice[kMirA + hi] = 0xFFFFFFFFu;            // -1 mod 2^32
-      slice[kMirB + 96 - lo] = 1u;
-      slice[kMirB + 96 - hi] = 0xFFFFFFFFu;
-    }
+  if (g == 0 && w == 0) slice[kMirA + r] = 1u;
+  __syncthreads();
+  const int t = static_cast<int>(g + 2 * w);
+  uint32_t* A = slice + kMirA;
+  uint32_t* T = slice + kMirC;   // 97 words: C and the first word of Hr
+#pragma unroll 1
+  for (int s = 0; s < Q; ++s) {   // a stream whose q is reached sits out
+    if (s < static_cast<int>(q)) mul_one_minus_t64<4>((s & 1) ? T : A, (s & 1) ? A : T, t);
+    __syncthreads();
+  }
+  const uint32_t* res = (q & 1) ? T : A;
+  for (int n = t; n < kR; n += 4) {
+    const uint32_t v = res[n];
+    A[n] = v;
+    slice[kMirB + 96 - n] = v;
   }
   __syncthreads();
 #pragma unroll 1

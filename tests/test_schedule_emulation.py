@@ -110,24 +110,44 @@ def test_warp_product_schedule_matches_oracle(orc):
         assert np.array_equal(warp_mulmod(a, b), orc.poly_mulmod(a, b))
 
 
-def lead7(e):
-    """The kernels' start: the leading (up to) seven bits v0 of e, the bit
-    below them (-1 when none), and t^v0 mod phi as (degree, coefficient)
-    terms: t^v0 below 97, else t^(v0-97) - t^(v0-33) (t^97 = 1 - t^64)."""
+LEAD_BITS = 10
+
+
+def mul_one_minus_t64(a, plant=0):
+    """a (1 - t^64) mod phi as the kernels form it: t^64 a folded in closed
+    form (t^97 = 1 - t^64): coefficient n of t^64 a is a_{n+33} - [n <= 30]
+    a_{n+66} for n <= 63 and a_{n-64} - a_{n-31} + [n <= 94] a_{n+2} above."""
+    b = []
+    for n in range(R):
+        if n <= 63:
+            t64 = a[n + 33] - (a[n + 66] if n <= 30 and plant != 1 else 0)
+        else:
+            t64 = a[n - 64] - a[n - 31] + (a[n + 2] if n <= 94 and plant != 2 else 0)
+        b.append(a[n] - t64)
+    return b
+
+
+def lead(e, bits=LEAD_BITS, plant=0):
+    """The kernels' start: the leading (up to) ten bits v0 = 97 q + r of e,
+    the bit below them (-1 when none), and t^v0 mod phi = t^r (1 - t^64)^q
+    (exact integers, before any reduction mod 2^24)."""
     L = e.bit_length()
-    v0, p = (e & 127, -1) if L <= 7 else ((e >> (L - 7)) & 127, L - 8)
-    terms = [(v0, 1)] if v0 < R else [(v0 - R, 1), (v0 - S, -1)]
-    return v0, p, terms
+    v0, p = (e & ((1 << bits) - 1), -1) if L <= bits else ((e >> (L - bits)) & ((1 << bits) - 1),
+                                                          L - bits - 1)
+    q, r = divmod(v0, R)
+    a = [0] * R
+    a[r] = 1
+    for _ in range(q):
+        a = mul_one_minus_t64(a, plant)
+    return v0, p, a
 
 
 def warp_poly_power(e):
     """t^e mod phi as the warp square-and-multiply schedules it: the leading
-    seven bits in closed form, then per bit a warp square and, on a 1 bit,
+    ten bits as t^r (1 - t^64)^q, then per bit a warp square and, on a 1 bit,
     the shift by t with the fold t^97 = 1 - t^64."""
-    _, p, terms = lead7(e)
-    a = np.zeros(R, np.uint32)
-    for d, cf in terms:
-        a[d] = cf & MASK
+    _, p, start = lead(e)
+    a = np.array([v & MASK for v in start], dtype=np.uint32)
     while p >= 0:
         a = warp_mulmod(a, a.copy())
         if (e >> p) & 1:
@@ -139,17 +159,20 @@ def warp_poly_power(e):
     return a
 
 
-def test_lead7_start_matches_oracle(orc):
-    # every start the kernels can take (v0 < 128) against the oracle's t^v0
-    for v0 in range(128):
-        _, p, terms = lead7(v0)
+def test_lead_start_matches_oracle(orc):
+    # every start the kernels can take (v0 < 1024) against the oracle's t^v0
+    for v0 in range(1 << LEAD_BITS):
+        _, p, a = lead(v0)
         assert p == -1
-        a = np.zeros(R, np.int64)
-        for d, cf in terms:
-            a[d] += cf
-        assert np.array_equal((a % (1 << 24)).astype(np.uint32), orc.poly_pow_t(v0)), v0
-    assert lead7((1 << 120) + 12345)[:2] == (64, 113)
-    assert lead7(1000)[:2] == (125, 2)
+        assert np.array_equal(np.array([v % (1 << 24) for v in a], dtype=np.uint32),
+                              orc.poly_pow_t(v0)), v0
+    assert lead((1 << 120) + 12345)[:2] == (512, 110)
+    assert lead(1000)[:2] == (1000, -1)
+    assert lead(5000)[:2] == (625, 2)
+    # each dropped fold term (a_{n+66} below 31, a_{n+2} above 63) fails it
+    for pl in (1, 2):
+        assert any(np.any(np.array([v % (1 << 24) for v in lead(v0, plant=pl)[2]], dtype=np.uint32)
+                          != orc.poly_pow_t(v0)) for v0 in range(1 << LEAD_BITS)), pl
 
 
 def test_warp_square_multiply_schedule_matches_oracle(orc):
@@ -470,9 +493,9 @@ def mirror_square(A, Bv, shift, plant=0):
 
 
 def mirror_poly_power(e, plant=0):
-    _, p, terms = lead7(e)
+    _, p, start = lead(e)
     A, Bv = [0] * 100, [0] * 100
-    for d, cf in terms:
+    for d, cf in enumerate(start):
         A[d] = cf % W32
         Bv[96 - d] = cf % W32
     while p >= 0:
