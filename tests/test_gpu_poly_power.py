@@ -74,3 +74,21 @@ def test_square_multiply_jump_warp_and_pair_agree(rm):
         warp = rm.partition_ex(base, J, 3, n - 1, flags=flags)
         torch.cuda.synchronize()
         assert torch.equal(pair[: n - 1], warp), (J, flags)
+
+
+def test_poly_power_every_ten_bit_start(rm, orc):
+    """Both kernels start from the leading ten bits v0 = 97 q + r of E as
+    t^r (1 - t^64)^q mod phi.  Every E < 1,024 (the start alone, no
+    squaring) and, for every v0, an exponent v0 2^40 + tail (the start
+    followed by 40 squarings), through the warp mapping (1,024 exponents)
+    and the lane pairs (all 2,048 at once, so that a CTA's 16 streams mix
+    different q and, for the small ones, different bit lengths)."""
+    dev = torch.device("cuda:0")
+    small = list(range(1024))
+    large = [(v << 40) + (v * 2654435761) % (1 << 40) for v in range(1024)]
+    want = {e: orc.poly_pow_t(e) for e in small + large}
+    assert len(small) <= rm.SQUARE_WARP_AUTO_MAX < len(small) + len(large)
+    for exps in (small, large, small + large):
+        got = rm.poly_power(rm.exps_tensor(exps, 2, device=dev)).cpu().numpy().view(np.uint32)
+        for i, e in enumerate(exps):
+            assert np.array_equal(got[i, :97], want[e]), (len(exps), e)
