@@ -81,18 +81,28 @@ struct GenCtx {
   unsigned ssrc;   // the lane whose output this lane stores when realigned, (L - a) mod W
   bool lo;         // realigned: L < a (stores the previous step's output)
   uint32_t up;     // realigned: this lane's rotated output of the previous step
+  uint32_t c0;     // kEarlyWb: the state's c and pos as loaded, for the
+  uint64_t pos0;   // write-back (read with the window: the stream's end waits on no load)
 };
 
 // kRealign: prepare realigned stores (p at the aligned window, ssrc, lo);
 // otherwise p = out + out_base + L and the stores are never realigned.
-template <int W, bool F32, bool kRealign>
+// kEarlyWb: also keep c and pos for the write-back (three registers), so
+// that the end of the stream reads nothing; measured faster for the
+// one-warp-per-stream kernels, where each warp's end is exposed.
+template <int W, bool F32, bool kRealign, bool kEarlyWb = false>
 __device__ __forceinline__ void gen_load(GenCtx<W, F32>& g, const ranmar_state_t* st, void* out,
                                          uint64_t out_base, unsigned gl, const LaneConsts& k) {
   const uint32_t* xs = st->x;
 #pragma unroll
   for (int j = 0; j < GenCtx<W, F32>::NR; ++j) g.r[j] = xs[W * j + gl];  // R_{j-NR}[L] = X(W(j-NR) + L - 1)
   g.carry = xs[96];                                                       // X(-1)
-  g.cl = sub_mod_m(st->c, k.delta_lane);                                  // c_{L+1}
+  const uint32_t c = st->c;
+  if constexpr (kEarlyWb) {
+    g.c0 = c;
+    g.pos0 = st->pos;
+  }
+  g.cl = sub_mod_m(c, k.delta_lane);                                      // c_{L+1}
   using T = typename GenCtx<W, F32>::T;
   g.up = 0;
   if constexpr (kRealign) {
@@ -144,7 +154,7 @@ __device__ __forceinline__ void gen_turn(GenCtx<W, F32>& g, unsigned gl, unsigne
 // Continues the stream from block b0 (a multiple of NR; the context holds
 // R_{b0-NR} .. R_{b0-1}) to `count` outputs, then optionally writes the
 // advanced state back.
-template <int W, bool F32, bool kRot>
+template <int W, bool F32, bool kRot, bool kEarlyWb = false>
 __device__ void gen_finish(GenCtx<W, F32>& g, ranmar_state_t* st, uint64_t count, uint64_t b0,
                            bool write_back, unsigned gl, unsigned gmask, const LaneConsts& k) {
   constexpr int NR = GenCtx<W, F32>::NR, Q = GenCtx<W, F32>::Q;
@@ -191,8 +201,15 @@ __device__ void gen_finish(GenCtx<W, F32>& g, ranmar_state_t* st, uint64_t count
   }
 
   if (!write_back) return;
-  const uint32_t c0 = st->c;
-  const uint64_t pos0 = st->pos;
+  uint32_t c0;
+  uint64_t pos0;
+  if constexpr (kEarlyWb) {
+    c0 = g.c0;
+    pos0 = g.pos0;
+  } else {
+    c0 = st->c;
+    pos0 = st->pos;
+  }
   __syncwarp(gmask);
   // Positions relative to WB: r[j] = X(Wj + L - 97), carry (lane 0) = X(-1),
   // xb = X(L).  New state word q = X(rem - 97 + q).
@@ -225,11 +242,11 @@ __device__ void generate_stream(ranmar_state_t* st, uint64_t count, void* out, u
                                 bool write_back, unsigned gl, unsigned gmask,
                                 const LaneConsts& k) {
   GenCtx<W, F32> g;
-  gen_load<W, F32, kRealign>(g, st, out, out_base, gl, k);
+  gen_load<W, F32, kRealign, true>(g, st, out, out_base, gl, k);
   if (kRealign && g.ssrc != gl)
-    gen_finish<W, F32, kRealign>(g, st, count, 0, write_back, gl, gmask, k);
+    gen_finish<W, F32, kRealign, true>(g, st, count, 0, write_back, gl, gmask, k);
   else
-    gen_finish<W, F32, false>(g, st, count, 0, write_back, gl, gmask, k);
+    gen_finish<W, F32, false, true>(g, st, count, 0, write_back, gl, gmask, k);
 }
 
 // The interleaved part of generate_streams: `common` blocks (whole ring

@@ -210,14 +210,23 @@ int launch_generate(bool f32, ranmar_state_t* states, size_t n_states, const ran
   if (!aligned(states, 16) || !aligned(desc, 8) || !aligned(out, 4)) return RANMAR_EINVAL;
   const int threads = 256;
   const uint64_t warps_per_block = threads / 32;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // Shared memory the kernel does not use, reserved only to cap residency at
+  // four CTAs (32 warps, 32 streams being written) per SM: the HBM write
+  // rate falls with the number of output regions written at once, and four
+  // CTAs measured faster than the six that the registers allow (the 2^28-
+  // output launch 0.170 against 0.173 ms).  Below the 48 KB that needs no
+  // attribute.
+  constexpr size_t kGenResidencyCapSmem = 46 * 1024;
   uint64_t blocks = (n_desc + warps_per_block - 1) / warps_per_block;
   if (blocks > (1u << 20)) blocks = 1u << 20;   // grid-stride beyond ~8.4M descriptors
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (f32)
-    ranmar::generate_desc_kernel<true><<<static_cast<unsigned>(blocks), threads, 0, s>>>(
+    ranmar::generate_desc_kernel<true><<<static_cast<unsigned>(blocks), threads,
+                                         kGenResidencyCapSmem, s>>>(
         states, n_states, desc, n_desc, out, out_len, status);
   else
-    ranmar::generate_desc_kernel<false><<<static_cast<unsigned>(blocks), threads, 0, s>>>(
+    ranmar::generate_desc_kernel<false><<<static_cast<unsigned>(blocks), threads,
+                                          kGenResidencyCapSmem, s>>>(
         states, n_states, desc, n_desc, out, out_len, status);
   return check_launch();
 }
