@@ -197,6 +197,11 @@ int ranmar_partition(const ranmar_state_t *d_base, const uint32_t *h_J,
  * 2^24 of its stream, as uint32 (u24) or as float y_n * 2^-24 (f32; exact,
  * in [0, 1), 0.0 possible).  One warp runs one stream, 32 consecutive
  * outputs per step (the lag 33 allows 32 in parallel), stores coalesced.
+ * The launch reserves 46 KB of shared memory per 256-thread CTA that it
+ * does not use, which holds it to four CTAs per SM (fewer output regions
+ * written at once write HBM faster); kernels running beside it on other
+ * streams share the rest.  A state written back must belong to one
+ * descriptor of the batch only (descriptors run concurrently).
  * out_len is the element count of d_out.
  * Errors: RANMAR_EINVAL (null pointer with n_desc > 0, misaligned states or
  * output), RANMAR_ERANGE (n_states = 0 with n_desc > 0).  Device:
