@@ -185,6 +185,20 @@ def _need(t: torch.Tensor, dtype, name: str, cuda: bool = True):
         raise ValueError(f"{name}: must be a CUDA tensor")
 
 
+def _need_len(t: torch.Tensor | None, n: int, name: str, per: int = 1) -> None:
+    """t (when given) holds at least n items of `per` elements: the C ABI
+    receives only pointers, so a short buffer would be read or written past
+    its end."""
+    if t is not None and t.numel() < n * per:
+        raise ValueError(f"{name}: {t.numel()} elements, needs at least {n * per}")
+
+
+def _need_status(status: torch.Tensor | None) -> None:
+    if status is not None:
+        _need(status, torch.int32, "status")
+        _need_len(status, 1, "status")
+
+
 def words(e: int, nw: int | None = None) -> list[int]:
     """Non-negative integer -> little-endian 32-bit words (marshalling)."""
     if e < 0:
@@ -223,8 +237,8 @@ def seed_batch(seeds: torch.Tensor, out: torch.Tensor | None = None,
         out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=seeds.device)
     out2 = out.reshape(-1, STATE_WORDS)
     _need(out2, torch.int32, "out")
-    if status is not None:
-        _need(status, torch.int32, "status")
+    _need_len(out2, n, "out", STATE_WORDS)
+    _need_status(status)
     _check(_lib().ranmar_seed_batch(_ptr(seeds), n, _ptr(out2), _ptr(status), _stream(stream)),
            "ranmar_seed_batch")
     return out
@@ -241,10 +255,11 @@ def jump(base: torch.Tensor, exps: torch.Tensor, base_idx: torch.Tensor | None =
     if out is None:
         out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=base.device)
     _need(out, torch.int32, "out")
+    _need_len(out, n, "out", STATE_WORDS)
     if base_idx is not None:
         _need(base_idx, torch.int32, "base_idx")
-    if status is not None:
-        _need(status, torch.int32, "status")
+        _need_len(base_idx, n, "base_idx")
+    _need_status(status)
     _check(_lib().ranmar_jump(_ptr(base), base.shape[0], _ptr(base_idx), _ptr(exps), nw,
                               _ptr(out), n, _ptr(status), _stream(stream)), "ranmar_jump")
     return out
@@ -279,6 +294,10 @@ def jump_scatter(base: torch.Tensor, exps: torch.Tensor, dst: torch.Tensor,
         _need(base_idx, torch.int32, "base_idx")
     nw = exps.shape[1]
     n = exps.shape[0] if n is None else int(n)
+    _need_len(exps, n, "exps", nw)
+    _need_len(dst_idx, n, "dst_idx")
+    _need_len(base_idx, n, "base_idx")
+    _need_status(status)
     _check(_lib().ranmar_jump_scatter(_ptr(base), base.shape[0], _ptr(base_idx), _ptr(exps), nw,
                                       _ptr(dst), dst.shape[0], _ptr(dst_idx), n, _ptr(status),
                                       _stream(stream)), "ranmar_jump_scatter")
@@ -292,6 +311,8 @@ def checksum(data: torch.Tensor, items: torch.Tensor, results: torch.Tensor,
     _need(items, torch.int64, "items")
     _need(results, torch.int64, "results")
     n = items.shape[0] if n is None else int(n)
+    _need_len(items, n, "items", 4)
+    _need_status(status)
     _check(_lib().ranmar_checksum(_ptr(data), data.numel(), _ptr(items), n, _ptr(results),
                                   results.numel(), _ptr(status), _stream(stream)),
            "ranmar_checksum")
@@ -313,6 +334,7 @@ def partition(base: torch.Tensor, J: int, k0: int, n: int, out: torch.Tensor | N
     if out is None:
         out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=base.device)
     _need(out, torch.int32, "out")
+    _need_len(out, n, "out", STATE_WORDS)
     jw = np.array(words(int(J)), dtype=np.uint32)
     _check(_lib().ranmar_partition(_ptr(base), jw.ctypes.data, len(jw), int(k0), _ptr(out),
                                    int(n), _stream(stream)), "ranmar_partition")
@@ -335,6 +357,7 @@ def partition_ex(base: torch.Tensor, J: int, k0: int, n: int, table=None, flags:
     if out is None:
         out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=base.device)
     _need(out, torch.int32, "out")
+    _need_len(out, n, "out", STATE_WORDS)
     jw = np.array(words(int(J)), dtype=np.uint32)
     _check(_lib().ranmar_partition_ex(table._h if table is not None else None, _ptr(base),
                                       jw.ctypes.data, len(jw), int(k0), _ptr(out), int(n),
@@ -380,8 +403,7 @@ def _generate(fn: str, out_dtype, states, desc, out, status, stream):
     _need(states, torch.int32, "states")
     _need(desc, torch.int64, "desc")
     optr = _out_ptr(out, out_dtype, "out")
-    if status is not None:
-        _need(status, torch.int32, "status")
+    _need_status(status)
     _check(getattr(_lib(), fn)(_ptr(states), states.shape[0], _ptr(desc), desc.shape[0],
                                optr, out.numel(), _ptr(status), _stream(stream)), fn)
     return out
@@ -412,9 +434,10 @@ def check_overlap(states, desc, k, J: int, status=None, stream=None) -> torch.Te
     _need(states, torch.int32, "states")
     _need(desc, torch.int64, "desc")
     _need(k, torch.int64, "k")
+    _need_len(k, desc.shape[0], "k")
     if status is None:
         status = torch.zeros(1, dtype=torch.int32, device=states.device)
-    _need(status, torch.int32, "status")
+    _need_status(status)
     jw = np.array(words(int(J)), dtype=np.uint32)
     _check(_lib().ranmar_check_overlap(_ptr(states), states.shape[0], _ptr(desc), desc.shape[0],
                                        _ptr(k), jw.ctypes.data, len(jw), _ptr(status),
@@ -532,8 +555,7 @@ class Batch:
         src = torch.empty(max(1, n_extra), dtype=torch.int32, device=dev)[:n_extra]
         exps = torch.empty((max(1, n_extra), 2), dtype=torch.int32, device=dev)[:n_extra]
         total = torch.empty(1, dtype=torch.int64, device=dev)
-        if status is not None:
-            _need(status, torch.int32, "status")
+        _need_status(status)
         _check(_lib().ranmar_batch_pack_split(self._h, _ptr(counts), n, int(seg), int(n_extra),
                                               int(flags), _ptr(desc), _ptr(src) if n_extra else None,
                                               _ptr(exps) if n_extra else None, _ptr(total),
@@ -550,6 +572,7 @@ class Batch:
         if src.numel() == 0:
             return states
         _need(src, torch.int32, "src")
+        _need_len(states, int(n) + src.numel(), "states", STATE_WORDS)
         _check(_lib().ranmar_batch_split_finish(_ptr(states), int(n), _ptr(src), src.numel(),
                                                 _stream(stream)), "ranmar_batch_split_finish")
         return states
@@ -561,8 +584,8 @@ class Batch:
         _need(out, dtype, "out")
         if order is not None:
             _need(order, torch.int32, "order")
-        if status is not None:
-            _need(status, torch.int32, "status")
+            _need_len(order, desc.shape[0], "order")
+        _need_status(status)
         _check(getattr(_lib(), fn)(self._h, _ptr(states), states.shape[0], _ptr(desc),
                                    desc.shape[0], _ptr(order), _ptr(out), out.numel(),
                                    _ptr(status), _stream(stream)), fn)
@@ -583,6 +606,12 @@ class Batch:
         not advanced) and keeps the fastest.  Returns (config, best_ms)."""
         states = states.reshape(-1, STATE_WORDS)
         f32 = out.dtype == torch.float32
+        _need(states, torch.int32, "states")
+        _need(desc, torch.int64, "desc")
+        _need(out, torch.float32 if f32 else torch.int32, "out")
+        if order is not None:
+            _need(order, torch.int32, "order")
+            _need_len(order, desc.shape[0], "order")
         ms = ctypes.c_float(0.0)
         _check(_lib().ranmar_batch_tune(self._h, int(f32), _ptr(states), states.shape[0],
                                         _ptr(desc), desc.shape[0], _ptr(order), _ptr(out),
@@ -729,6 +758,11 @@ class Table:
         for t, nm in ((base_idx, "base_idx"), (dst_idx, "dst_idx")):
             if t is not None:
                 _need(t, torch.int32, nm)
+                _need_len(t, n, nm)
+        _need_len(exps, n, "exps", nw)
+        if dst_idx is None:
+            _need_len(out2, n, "out", STATE_WORDS)
+        _need_status(status)
         _check(_lib().ranmar_jump_tab(self._h, _ptr(base), base.shape[0], _ptr(base_idx),
                                       _ptr(exps), nw, _ptr(out2), out2.shape[0], _ptr(dst_idx),
                                       n, _ptr(status), _stream(stream)), "ranmar_jump_tab")
@@ -742,6 +776,7 @@ class Table:
         if out is None:
             out = torch.empty((n, STATE_WORDS), dtype=torch.int32, device=base.device)
         _need(out, torch.int32, "out")
+        _need_len(out, n, "out", STATE_WORDS)
         jw = np.array(words(int(J)), dtype=np.uint32)
         _check(_lib().ranmar_partition_tab(self._h, _ptr(base), jw.ctypes.data, len(jw),
                                            int(k0), _ptr(out), int(n), _stream(stream)),
@@ -800,8 +835,11 @@ def lfg_jump(r: int, s: int, e: int, x: torch.Tensor, exps: torch.Tensor, base_i
     if out is None:
         out = torch.empty((n, r), dtype=torch.int32, device=x.device)
     _need(out, torch.int32, "out")
+    _need_len(out, n, "out", r)
     if base_idx is not None:
         _need(base_idx, torch.int32, "base_idx")
+        _need_len(base_idx, n, "base_idx")
+    _need_status(status)
     _check(_lib().ranmar_lfg_jump(r, s, e, int(method), _ptr(x), x.shape[0], _ptr(base_idx),
                                   _ptr(exps), nw, _ptr(out), n, _ptr(status), _stream(stream)),
            "ranmar_lfg_jump")
@@ -818,6 +856,7 @@ def lfg_generate(r: int, s: int, e: int, x: torch.Tensor, count: int, out=None,
     if out is None:
         out = torch.empty((n, count), dtype=torch.int32, device=x.device)
     _need(out, torch.int32, "out")
+    _need_len(out, n, "out", count)
     _check(_lib().ranmar_lfg_generate(r, s, e, _ptr(x), n, int(count), _ptr(out), _stream(stream)),
            "ranmar_lfg_generate")
     return out

@@ -292,6 +292,8 @@ class Engine:
         if not new:
             return
         r0 = len(self.seed_row)
+        if r0 + len(new) > self.base.shape[0]:
+            raise ValueError(f"more than {self.base.shape[0]} distinct seeds (max_seeds)")
         for i, sd in enumerate(new):
             self.seed_row[sd] = r0 + i
         m = len(new)
