@@ -1380,36 +1380,41 @@ def extras(rm, torch, dev, stream, peaks, alu_peak, hbm_peak, probes):
 def serving(rm, torch, seconds):
     """Poisson request stream (20k req/s, seed 11; seed U{1..10^4}, k U{0..2^20},
     J = 2^48, count log-uniform 10^3..10^7, u24/f32 with p = 1/2) served in real
-    time with continuous batching under a 40 GB state+output budget; outputs
-    consumed by the on-device checksum.  Comparator: every request alone with
-    plain launches, on the first requests of the same stream (its checksums,
-    from independent kernels, must equal the engine's)."""
-    from paper_2512_00093_gb300.serve import Engine, make_requests, summarize
+    time with continuous batching under a 40 GB state+output budget by the
+    native scheduler; outputs consumed by the on-device checksum.  Comparator:
+    every request alone with plain launches, on the first requests of the same
+    stream (its checksums, from independent kernels, must equal the engine's)."""
+    from paper_2512_00093_gb300.serve import Engine, requests_array, summarize_array
     from paper_2512_00093_gb300.workloads import Serving
     w = Serving()
     t, seeds, ks, counts, f32 = w.requests(duration=seconds)
-    reqs = make_requests(t, seeds, ks, counts, f32, w.J)
+    reqs = requests_array(t, seeds, ks, counts, f32, w.J)
+    torch.cuda.empty_cache()                    # the engine allocates its 40 GB itself
     eng = Engine(budget_bytes=40 << 30)
     eng.preload_seeds(range(1, 10**4 + 1))      # engine set-up: the recipe's seed range
     summ = eng.run(reqs, realtime=True, max_wait=seconds * 10 + 60)
+    st = eng.stats
     res = {"offered_req_per_s": w.rate, "seconds": seconds, **summ,
-           "iterations": eng.stats["iterations"], "segments": eng.stats["segments"],
-           "jumps": eng.stats["jumps"], "resumed": eng.stats["resumed"],
-           "evicted": eng.stats["evicted"], "budget_gb": 40}
+           "iterations": st["iterations"], "segments": st["segments"], "jumps": st["jumps"],
+           "resumed": st["resumed"], "evicted": st["evicted"], "budget_gb": 40,
+           "max_iterations_in_flight": st["max_inflight"],
+           "host_us_per_iteration": st["host_ns"] / max(1, st["iterations"]) / 1e3,
+           "requests_per_iteration": summ["served"] / max(1, st["iterations"])}
     res["latency_note"] = ("p50/p99: the GPU event that ends a request's iteration minus its "
                            "arrival; host_p50/host_p99: when the scheduler loop saw that event "
-                           "complete, minus arrival")
+                           "complete, minus arrival; host_us_per_iteration: the native "
+                           "scheduler's time to build and enqueue one iteration")
     # Comparator on the same requests: the first nplain of the list, each alone
     # with plain launches, arriving at the recipe's times.  It cannot keep up
     # with 20k req/s, so its latencies are queueing; its sustained rate is
     # reported beside the engine's figures for the same requests (taken from
     # the full run above).
     nplain = min(len(reqs), 2000)
-    plain = make_requests(t[:nplain], seeds[:nplain], ks[:nplain], counts[:nplain],
-                          f32[:nplain], w.J)
+    plain = requests_array(t[:nplain], seeds[:nplain], ks[:nplain], counts[:nplain],
+                           f32[:nplain], w.J)
     ps = eng.run_plain(plain, realtime=True, max_wait=seconds * 10 + 120)
-    ok_plain = sum(int(a.checksum == b.checksum) for a, b in zip(plain, reqs[:nplain]))
-    same = summarize(reqs[:nplain])
+    ok_plain = int((plain["checksum"] == reqs["checksum"][:nplain]).sum())
+    same = summarize_array(reqs[:nplain])
     res["plain_per_request"] = {
         **ps, "sustained_req_per_s": nplain / ps["span_s"] if ps["span_s"] else None,
         "saturated": bool(ps["span_s"] and nplain / ps["span_s"] < 0.9 * w.rate),
@@ -1423,14 +1428,13 @@ def serving(rm, torch, seconds):
     # fresh engine and by the plain path, so that neither latency is queueing.
     slow = 400.0
     ts = t[:nplain] * (w.rate / slow)
-    r_eng = make_requests(ts, seeds[:nplain], ks[:nplain], counts[:nplain], f32[:nplain], w.J)
-    r_pl = make_requests(ts, seeds[:nplain], ks[:nplain], counts[:nplain], f32[:nplain], w.J)
+    r_eng = requests_array(ts, seeds[:nplain], ks[:nplain], counts[:nplain], f32[:nplain], w.J)
+    r_pl = requests_array(ts, seeds[:nplain], ks[:nplain], counts[:nplain], f32[:nplain], w.J)
     e_slow = eng.run(r_eng, realtime=True, max_wait=ts[-1] + 120)
     p_slow = eng.run_plain(r_pl, realtime=True, max_wait=ts[-1] + 120)
     res["at_400_req_per_s"] = {
         "requests": nplain, "engine": e_slow, "plain_per_request": p_slow,
-        "checksums_equal": f"{sum(int(a.checksum == b.checksum) for a, b in zip(r_eng, r_pl))}"
-                           f"/{nplain}",
+        "checksums_equal": f"{int((r_eng['checksum'] == r_pl['checksum']).sum())}/{nplain}",
         "note": "the same requests with arrival times stretched to 400 req/s, below the plain "
                 "path's saturation: latencies without queueing, engine against one jump + one "
                 "generation launch per request"}
@@ -1442,25 +1446,27 @@ def serving_hot(rm, torch):
     """The labelled hot-stream variant (1,024 streams revisited, 20k req/s,
     10 s): most requests resume a resident stream and need no jump.  The
     first 1,000 requests are checked against the plain per-request path."""
-    from paper_2512_00093_gb300.serve import Engine, make_requests
+    from paper_2512_00093_gb300.serve import Engine, requests_array
     from paper_2512_00093_gb300.workloads import ServingHot
     w = ServingHot()
     t, seeds, ks, counts, f32 = w.requests()
-    reqs = make_requests(t, seeds, ks, counts, f32, w.J)
+    reqs = requests_array(t, seeds, ks, counts, f32, w.J)
+    torch.cuda.empty_cache()
     eng = Engine(budget_bytes=40 << 30)
     eng.preload_seeds(range(1, w.seeds + 1))
     summ = eng.run(reqs, realtime=True, max_wait=w.duration * 10 + 60)
+    st = eng.stats
     res = {"workload": "hot streams: seeds 1..64 x k 0..15, 20k req/s, 10 s, counts "
                        "10^3..10^6 (labelled variant, not the recipe)",
-           **summ, "iterations": eng.stats["iterations"], "segments": eng.stats["segments"],
-           "jumps": eng.stats["jumps"], "resumed": eng.stats["resumed"],
-           "evicted": eng.stats["evicted"],
-           "resumed_frac": eng.stats["resumed"] / max(1, len(reqs))}
+           **summ, "iterations": st["iterations"], "segments": st["segments"],
+           "jumps": st["jumps"], "resumed": st["resumed"], "evicted": st["evicted"],
+           "resumed_frac": st["resumed"] / max(1, len(reqs)),
+           "host_us_per_iteration": st["host_ns"] / max(1, st["iterations"]) / 1e3}
     nchk = min(len(reqs), 1000)
-    plain = make_requests(t[:nchk], seeds[:nchk], ks[:nchk], counts[:nchk], f32[:nchk], w.J)
+    plain = requests_array(t[:nchk], seeds[:nchk], ks[:nchk], counts[:nchk], f32[:nchk], w.J)
     eng.run_plain(plain, realtime=False, max_wait=600)
     res["checksums_equal_plain"] = \
-        f"{sum(int(a.checksum == b.checksum) for a, b in zip(plain, reqs[:nchk]))}/{nchk}"
+        f"{int((plain['checksum'] == reqs['checksum'][:nchk]).sum())}/{nchk}"
     eng.close()
     return res
 

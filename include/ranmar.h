@@ -53,6 +53,9 @@ extern "C" {
 #define RANMAR_ECUDA (-3)         /* CUDA launch/runtime error              */
 #define RANMAR_ENOMEM (-4)        /* workspace allocation failed            */
 #define RANMAR_EDEVICE (-5)       /* device not sm_103a / not usable        */
+#define RANMAR_ETIME (-6)         /* a serving run passed its time limit    */
+#define RANMAR_ESTATUS (-7)       /* a kernel of a serving run set a        */
+                                  /* RANMAR_ST_* bit (ranmar_serve_stats)    */
 
 /* Bits OR-ed into *d_status by kernels. */
 #define RANMAR_ST_BAD_INDEX 1u    /* state or base index out of range       */
@@ -761,6 +764,168 @@ int ranmar_checksum(const uint32_t *d_data, size_t data_len,
                     const ranmar_sum_item_t *d_items, size_t n_items,
                     uint64_t *d_results, size_t n_results,
                     uint32_t *d_status, ranmar_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Serving engine: a native continuous-batching scheduler over the calls
+ * above.  A request asks for the next `count` outputs of stream k of
+ * (seed, J) -- the block that starts k J transitions after the seeded state
+ * of `seed` (Sec. 1) -- from output `offset` of that block on.  The engine
+ * keeps stream states resident in a device state pool, so that a request
+ * that starts where an earlier one of the same stream ended needs no jump.
+ * Every scheduler iteration admits arrived requests in arrival order while
+ * the output pool and the state pool allow, cuts each into segments of at
+ * most `seg` outputs (one state each), and enqueues on one stream, after
+ * ONE host-to-device copy of a packed staging buffer: the jumps of the
+ * segment start states (from the seeded state by k J + offset + j seg, or
+ * from the resident state by j seg; Sec. 3.1 / 3.2), one persistent batched
+ * generation per output type, and ranmar_checksum of every request's
+ * outputs (the outputs are consumed on the device; their region is then
+ * recycled).  Up to max_inflight iterations are on the device while the
+ * host builds the next.  Unlike the calls above, an engine owns device
+ * memory (budget_bytes + 400 * max_seeds bytes and small buffers) and
+ * synchronizes its stream.  An engine is used by one host thread at a time.
+ * ------------------------------------------------------------------------ */
+typedef struct ranmar_serve ranmar_serve_t;
+
+#define RANMAR_SERVE_SQUARE 1u      /* jumps by square-and-multiply           */
+                                    /* (ranmar_jump_scatter), not the table   */
+#define RANMAR_SERVE_HOST_ONLY 2u   /* no device at all: the scheduler alone, */
+                                    /* which records its plan (tests)         */
+
+typedef struct ranmar_serve_config {
+    uint64_t budget_bytes;   /* state pool (400 bytes an entry) + output pool */
+    uint64_t seg;            /* outputs per segment, >= 1 */
+    uint32_t state_entries;  /* states of the pool, >= 1 */
+    uint32_t max_seeds;      /* rows of the seeded-state table, >= 1 */
+    uint32_t result_slots;   /* checksum ring, >= (max_inflight + 2) max_segments */
+    uint32_t max_segments;   /* segments one iteration takes (a larger request */
+                             /* still runs, alone in its iteration) */
+    uint32_t max_inflight;   /* iterations on the device at once, >= 1 */
+    uint32_t flags;          /* RANMAR_SERVE_* */
+} ranmar_serve_config_t;   /* 40 bytes */
+
+/* ranmar_request_t.status */
+#define RANMAR_REQ_PENDING (-1)   /* not served (the run ended before it)     */
+#define RANMAR_REQ_DONE 0
+#define RANMAR_REQ_TOO_LARGE 1    /* more outputs than the output pool, or    */
+                                  /* more segments than the state pool holds  */
+#define RANMAR_REQ_BAD 2          /* seed outside 1..900000000, or            */
+                                  /* k J + offset + count > 2^160             */
+
+typedef struct ranmar_request {
+    double   t;          /* in: arrival, seconds after the start of the run;
+                            non-decreasing along the array */
+    int32_t  seed;       /* in */
+    uint32_t f32;        /* in: 0 = 24-bit words, else float32 (word 2^-24) */
+    uint64_t k;          /* in: stream index */
+    uint64_t J[2];       /* in: stream length, little-endian 128-bit */
+    uint64_t offset;     /* in: outputs of (seed, k, J) taken by earlier
+                            requests (the request starts at k J + offset) */
+    uint64_t count;      /* in: outputs asked for (0 is served, checksum 0) */
+    double   done;       /* out: when the device finished its iteration,
+                            seconds after the start (CUDA events) */
+    double   host_done;  /* out: when the scheduler saw it (host clock) */
+    uint64_t checksum;   /* out: ranmar_checksum of its outputs, its first
+                            output having index 0 */
+    int32_t  status;     /* out: RANMAR_REQ_* */
+    uint32_t iteration;  /* out: the scheduler iteration that served it */
+} ranmar_request_t;     /* 88 bytes */
+
+typedef struct ranmar_serve_stats {   /* totals over the engine's runs */
+    uint64_t iterations, segments, base_jumps, pool_jumps;
+    uint64_t resumed;        /* requests that started from a resident state */
+    uint64_t evicted;        /* resident states taken back for other work */
+    uint64_t rejected;       /* requests with status TOO_LARGE or BAD */
+    uint64_t outputs;        /* outputs served */
+    uint64_t new_seeds;      /* seeds seeded during runs */
+    uint64_t slow_loops;     /* scheduler loop turns longer than 10 ms */
+    uint64_t max_loop_ns;    /* longest scheduler loop turn */
+    uint64_t max_inflight;   /* most iterations on the device at once */
+    uint64_t host_ns;        /* host time spent building + enqueueing */
+    uint64_t resident;       /* resident streams now */
+    uint32_t status;         /* RANMAR_ST_* bits the kernels set */
+    uint32_t pad;
+} ranmar_serve_stats_t;
+
+/* Trace of a RANMAR_SERVE_HOST_ONLY engine: one record per segment. */
+#define RANMAR_SEG_FROM_SEED 0    /* state = f^E(seeded state of the seed)   */
+#define RANMAR_SEG_FROM_POOL 1    /* state = f^E(pool state src)             */
+#define RANMAR_SEG_RESIDENT 2     /* pool state `entry` as it stands         */
+typedef struct ranmar_serve_seg {
+    uint32_t iteration;
+    uint32_t request;     /* index into the run's request array */
+    uint32_t kind;        /* RANMAR_SEG_* */
+    uint32_t entry;       /* pool state jumped into and generated from */
+    uint32_t src;         /* FROM_SEED: row of the seed table; FROM_POOL: entry */
+    uint32_t flags;       /* RANMAR_DESC_WRITE_BACK on a request's last segment */
+    uint32_t exp[RANMAR_MAX_EXP_WORDS];   /* E, little-endian (FROM_*) */
+    uint32_t live_until;  /* iterations enqueued when its iteration retired */
+    uint64_t out_offset;  /* first word in the output pool */
+    uint64_t count;
+    uint64_t index0;      /* index of its first output within the request */
+} ranmar_serve_seg_t;   /* 72 bytes */
+
+/*
+ * ranmar_serve_create -- allocates an engine on the current device (with
+ * RANMAR_SERVE_HOST_ONLY: host memory only, no CUDA call).  The output pool
+ * is (budget_bytes - 400 state_entries) / 4 words.  Errors: RANMAR_EINVAL
+ * (NULL, a zero size, unknown flags), RANMAR_ERANGE (budget below the state
+ * pool, result_slots too small), RANMAR_ENOMEM, RANMAR_ECUDA.
+ */
+int ranmar_serve_create(const ranmar_serve_config_t *cfg, ranmar_serve_t **out);
+/* Waits for the device and frees everything (NULL is a no-op).  Errors:
+ * RANMAR_EINVAL when called with another device current. */
+int ranmar_serve_destroy(ranmar_serve_t *e);
+
+/*
+ * ranmar_serve_preload -- gives the seeds h_seeds[0..n) rows of the seeded
+ * state table and seeds them on `stream` (Algorithm 3), synchronously.
+ * Errors: RANMAR_EINVAL (NULL, a seed outside 1..900000000), RANMAR_ERANGE
+ * (more distinct seeds than max_seeds), RANMAR_ENOMEM, RANMAR_ECUDA.
+ */
+int ranmar_serve_preload(ranmar_serve_t *e, const int32_t *h_seeds, size_t n,
+                         ranmar_stream_t stream);
+
+/*
+ * ranmar_serve_run -- serves h_reqs[0..n) (host, caller-owned, read and
+ * written during the call) and returns when all are done, refused, or the
+ * run fails.  realtime != 0 replays the arrival times against the host
+ * clock (a request is seen at h_reqs[i].t); realtime == 0 makes every
+ * request available at once.  Writes each request's out fields.  Results do
+ * not depend on how requests are batched: request i's outputs are outputs
+ * offset .. offset + count - 1 of its stream whatever else runs.
+ * Errors: RANMAR_EINVAL (NULL with n > 0, arrival times not sorted, an
+ * engine whose earlier run failed), RANMAR_ERANGE (more distinct seeds than
+ * max_seeds), RANMAR_ETIME (the run took longer than max_wait_s),
+ * RANMAR_ESTATUS (a kernel set a status bit), and the errors of the calls
+ * it makes.  After an error the engine refuses further runs; destroy it.
+ */
+int ranmar_serve_run(ranmar_serve_t *e, ranmar_request_t *h_reqs, size_t n, int realtime,
+                     double max_wait_s, ranmar_stream_t stream);
+
+/*
+ * ranmar_serve_run_plain -- the comparator: every request alone, in
+ * arrival order, with one square-and-multiply jump launch and one plain
+ * one-warp generation launch (no batching, no segments, no resident
+ * states), checksummed as above.  Same arguments, results and errors as
+ * ranmar_serve_run (not on a host-only engine: RANMAR_EINVAL).
+ */
+int ranmar_serve_run_plain(ranmar_serve_t *e, ranmar_request_t *h_reqs, size_t n,
+                           int realtime, double max_wait_s, ranmar_stream_t stream);
+
+/* Totals over the engine's runs.  Errors: RANMAR_EINVAL (NULL). */
+int ranmar_serve_get_stats(const ranmar_serve_t *e, ranmar_serve_stats_t *out);
+
+/*
+ * ranmar_serve_trace -- the segments a host-only engine planned, in the
+ * order it planned them: copies min(cap, total) records to h_out and sets
+ * *n_out = total.  A host-only engine runs no device work: its iterations
+ * complete only when the scheduler must wait for one (so that as many as
+ * max_inflight are in flight), and its checksums are 0.
+ * Errors: RANMAR_EINVAL (NULL, or an engine with a device).
+ */
+int ranmar_serve_trace(const ranmar_serve_t *e, ranmar_serve_seg_t *h_out, size_t cap,
+                       size_t *n_out);
 
 /*
  * ranmar_host_device_pointer -- the device address of pinned (page-locked)

@@ -28,7 +28,7 @@ ST_BAD_SEED = 4
 ST_TIMEOUT = 8
 ST_OVERLAP = 16
 
-OK, EINVAL, ERANGE, ECUDA, ENOMEM, EDEVICE = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ERANGE, ECUDA, ENOMEM, EDEVICE, ETIME, ESTATUS = 0, -1, -2, -3, -4, -5, -6, -7
 
 
 class RanmarError(RuntimeError):
@@ -47,6 +47,41 @@ class BatchConfig(ctypes.Structure):
 
     def as_tuple(self):
         return (self.lanes_per_stream, self.threads_per_cta, self.ctas_per_sm, self.chunk)
+
+
+class ServeConfig(ctypes.Structure):
+    """ranmar_serve_config_t."""
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("seg", ctypes.c_uint64),
+                ("state_entries", ctypes.c_uint32), ("max_seeds", ctypes.c_uint32),
+                ("result_slots", ctypes.c_uint32), ("max_segments", ctypes.c_uint32),
+                ("max_inflight", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class ServeStats(ctypes.Structure):
+    """ranmar_serve_stats_t."""
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "iterations", "segments", "base_jumps", "pool_jumps", "resumed", "evicted", "rejected",
+        "outputs", "new_seeds", "slow_loops", "max_loop_ns", "max_inflight", "host_ns",
+        "resident")] + [("status", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "pad"}
+
+
+SERVE_SQUARE = 1
+SERVE_HOST_ONLY = 2
+REQ_PENDING, REQ_DONE, REQ_TOO_LARGE, REQ_BAD = -1, 0, 1, 2
+SEG_FROM_SEED, SEG_FROM_POOL, SEG_RESIDENT = 0, 1, 2
+# ranmar_request_t (88 bytes) and ranmar_serve_seg_t (72 bytes) as numpy records
+REQUEST_DTYPE = np.dtype([("t", "<f8"), ("seed", "<i4"), ("f32", "<u4"), ("k", "<u8"),
+                          ("J", "<u8", (2,)), ("offset", "<u8"), ("count", "<u8"),
+                          ("done", "<f8"), ("host_done", "<f8"), ("checksum", "<u8"),
+                          ("status", "<i4"), ("iteration", "<u4")])
+SEG_DTYPE = np.dtype([("iteration", "<u4"), ("request", "<u4"), ("kind", "<u4"),
+                      ("entry", "<u4"), ("src", "<u4"), ("flags", "<u4"),
+                      ("exp", "<u4", (MAX_EXP_WORDS,)), ("live_until", "<u4"),
+                      ("out_offset", "<u8"), ("count", "<u8"), ("index0", "<u8")])
+assert REQUEST_DTYPE.itemsize == 88 and SEG_DTYPE.itemsize == 72
 
 
 _L: ctypes.CDLL | None = None
@@ -128,6 +163,17 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.ranmar_partition_ex.restype = ctypes.c_int
     for nm in ("ranmar_partition_generate_u24", "ranmar_partition_generate_f32"):
         getattr(lib, nm).argtypes = [_vp, _vp, _vp, _u32, _u64, _sz, _u64, _u32, _vp, _vp, _vp]
+        getattr(lib, nm).restype = ctypes.c_int
+    lib.ranmar_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(_vp)]
+    lib.ranmar_serve_destroy.argtypes = [_vp]
+    lib.ranmar_serve_preload.argtypes = [_vp, _vp, _sz, _vp]
+    lib.ranmar_serve_run.argtypes = [_vp, _vp, _sz, ctypes.c_int, ctypes.c_double, _vp]
+    lib.ranmar_serve_run_plain.argtypes = [_vp, _vp, _sz, ctypes.c_int, ctypes.c_double, _vp]
+    lib.ranmar_serve_get_stats.argtypes = [_vp, ctypes.POINTER(ServeStats)]
+    lib.ranmar_serve_trace.argtypes = [_vp, _vp, _sz, ctypes.POINTER(_sz)]
+    for nm in ("ranmar_serve_create", "ranmar_serve_destroy", "ranmar_serve_preload",
+               "ranmar_serve_run", "ranmar_serve_run_plain", "ranmar_serve_get_stats",
+               "ranmar_serve_trace"):
         getattr(lib, nm).restype = ctypes.c_int
     lib.ranmar_graph_begin.argtypes = [_vp]
     lib.ranmar_graph_end.argtypes = [_vp, ctypes.POINTER(_vp)]
@@ -966,3 +1012,76 @@ def _wrap_device_ptr(ptr: int, n_int32: int) -> torch.Tensor:
         __cuda_array_interface__ = {"shape": (n_int32,), "typestr": "<i4",
                                     "data": (ptr, False), "version": 2}
     return torch.as_tensor(_Holder(), device="cuda")
+
+
+class Serve:
+    """A ranmar_serve_t engine (the native serving scheduler).  Requests are
+    REQUEST_DTYPE records in a host numpy array, read and written in place
+    by run() / run_plain()."""
+
+    def __init__(self, budget_bytes: int, seg: int, state_entries: int, max_seeds: int,
+                 result_slots: int, max_segments: int, max_inflight: int, flags: int = 0):
+        self.cfg = ServeConfig(budget_bytes, seg, state_entries, max_seeds, result_slots,
+                               max_segments, max_inflight, flags)
+        h = _vp()
+        _check(_lib().ranmar_serve_create(ctypes.byref(self.cfg), ctypes.byref(h)),
+               "ranmar_serve_create")
+        self.h = h
+
+    @property
+    def host_only(self) -> bool:
+        return bool(self.cfg.flags & SERVE_HOST_ONLY)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(_lib().ranmar_serve_destroy(self.h), "ranmar_serve_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _s(self, stream):
+        return None if self.host_only else _stream(stream)
+
+    def preload(self, seeds, stream=None) -> None:
+        a = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32))
+        _check(_lib().ranmar_serve_preload(self.h, a.ctypes.data, a.size, self._s(stream)),
+               "ranmar_serve_preload")
+
+    @staticmethod
+    def _reqs(reqs: np.ndarray) -> np.ndarray:
+        if not isinstance(reqs, np.ndarray) or reqs.dtype != REQUEST_DTYPE or reqs.ndim != 1:
+            raise TypeError("requests: a 1-d numpy array of REQUEST_DTYPE records")
+        if not reqs.flags.c_contiguous or not reqs.flags.writeable:
+            raise ValueError("requests: must be contiguous and writeable")
+        return reqs
+
+    def run(self, reqs: np.ndarray, realtime: bool = True, max_wait: float = 120.0,
+            stream=None) -> None:
+        r = self._reqs(reqs)
+        _check(_lib().ranmar_serve_run(self.h, r.ctypes.data, r.size, int(realtime),
+                                       float(max_wait), self._s(stream)), "ranmar_serve_run")
+
+    def run_plain(self, reqs: np.ndarray, realtime: bool = True, max_wait: float = 120.0,
+                  stream=None) -> None:
+        r = self._reqs(reqs)
+        _check(_lib().ranmar_serve_run_plain(self.h, r.ctypes.data, r.size, int(realtime),
+                                             float(max_wait), self._s(stream)),
+               "ranmar_serve_run_plain")
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        _check(_lib().ranmar_serve_get_stats(self.h, ctypes.byref(st)), "ranmar_serve_get_stats")
+        return st.as_dict()
+
+    def trace(self) -> np.ndarray:
+        n = _sz()
+        _check(_lib().ranmar_serve_trace(self.h, None, 0, ctypes.byref(n)), "ranmar_serve_trace")
+        out = np.zeros(n.value, dtype=SEG_DTYPE)
+        got = _sz()
+        _check(_lib().ranmar_serve_trace(self.h, out.ctypes.data if n.value else None, n.value,
+                                         ctypes.byref(got)), "ranmar_serve_trace")
+        return out

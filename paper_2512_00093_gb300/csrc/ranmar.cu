@@ -95,6 +95,17 @@ int cuda_fail(cudaError_t e) {
   return RANMAR_ECUDA;
 }
 
+}  // namespace
+
+namespace ranmar {
+namespace host {
+// The library's CUDA error mapping, for its other translation units.
+int cuda_fail(cudaError_t e) { return ::cuda_fail(e); }
+}  // namespace host
+}  // namespace ranmar
+
+namespace {
+
 // Host-side failure injection (ranmar_debug_fail_next): the next launch
 // check returns this code once.
 std::atomic<int> g_fail_next{0};
@@ -515,7 +526,7 @@ bool lfg_shape(uint32_t r, uint32_t s, uint32_t e, int method, ranmar::LfgShape&
 
 extern "C" {
 
-int ranmar_abi_version(void) { return (1 << 16) | 0; }
+int ranmar_abi_version(void) { return (1 << 16) | 1; }
 
 const char* ranmar_strerror(int code) {
   switch (code) {
@@ -525,6 +536,8 @@ const char* ranmar_strerror(int code) {
     case RANMAR_ECUDA: return "RANMAR_ECUDA: CUDA error (see ranmar_last_cuda_error)";
     case RANMAR_ENOMEM: return "RANMAR_ENOMEM: allocation failed";
     case RANMAR_EDEVICE: return "RANMAR_EDEVICE: unsupported or unusable device";
+    case RANMAR_ETIME: return "RANMAR_ETIME: the serving run passed its time limit";
+    case RANMAR_ESTATUS: return "RANMAR_ESTATUS: a kernel set a RANMAR_ST_* status bit";
     default: return "RANMAR: unknown status";
   }
 }

@@ -119,3 +119,44 @@ def test_serving_injected_failure_then_recovers(rm, orc):
     eng.run(reqs, realtime=False)
     check_all(orc, rm, reqs)
     eng.close()
+
+
+def test_serving_multiword_J_empty_requests_and_arrays(rm, orc):
+    """Streams of length J = 2^120 + 12345 (start exponents k J + offset
+    across four words), requests of 0 and 1 outputs, and the same requests
+    as REQUEST_DTYPE records give the same checksums as the oracle."""
+    from paper_2512_00093_gb300.serve import Engine, make_requests, requests_array
+    J = (1 << 120) + 12345
+    rng = np.random.default_rng(31)
+    n = 40
+    t = np.sort(rng.random(n) * 0.01)
+    sd, k = rng.integers(1, 4, n), rng.integers(0, 5, n)
+    c = rng.integers(0, 20_000, n)
+    c[:4] = [0, 1, 0, 4097]
+    f32 = rng.random(n) < 0.5
+    reqs = make_requests(t, sd, k, c, f32, J)
+    eng = Engine(budget_bytes=64 << 20, seg=4096, state_entries=128, max_segments_per_iter=16)
+    eng.run(reqs, realtime=False)
+    check_all(orc, rm, reqs)
+    assert reqs[0].checksum == 0 and reqs[2].checksum == 0
+    a = requests_array(t, sd, k, c, f32, J)
+    e2 = Engine(budget_bytes=64 << 20, seg=1000, state_entries=128, use_table=False)
+    s = e2.run(a, realtime=False)
+    assert s["served"] == n
+    assert [int(x) for x in a["checksum"]] == [r.checksum for r in reqs]
+    eng.close()
+    e2.close()
+
+
+def test_serving_iterations_overlap_on_the_device(rm, orc):
+    """Continuous batching: with requests arriving while earlier iterations
+    run, more than one iteration is on the device at once, and the results
+    still equal the oracle's."""
+    from paper_2512_00093_gb300.serve import Engine
+    reqs = mixed_requests(300, 17, seeds=20, ks=50, cmax=400_000, duration=0.05)
+    eng = Engine(budget_bytes=512 << 20, seg=1 << 14, state_entries=4096, max_inflight=4)
+    eng.run(reqs, realtime=True)
+    st = eng.stats
+    assert st["max_inflight"] >= 2 and st["iterations"] > 10
+    check_all(orc, rm, reqs)
+    eng.close()
