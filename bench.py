@@ -78,10 +78,15 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--serve-seconds", type=float, default=60.0,
                    help="duration of the serving run (60 s: the recipe's full request list)")
-    p.add_argument("--case", choices=["partitioned", "uneven", "large", "plan"],
+    p.add_argument("--case", choices=["partitioned", "uneven", "large", "plan", "serve"],
                    default="partitioned",
-                   help="partitioned = the benchmark; uneven / large run only that workload's "
-                        "step (for profiling) and print a line for it")
+                   help="partitioned = the benchmark; uneven / large / plan run only that "
+                        "workload's step (for profiling) and print a line for it; serve runs "
+                        "--serve-seconds of the serving recipe alone")
+    p.add_argument("--serve-max-segments", type=int, default=8192,
+                   help="--case serve: segments one scheduler iteration takes at most")
+    p.add_argument("--serve-offline", action="store_true",
+                   help="--case serve: all requests available at once, one iteration in flight")
     p.add_argument("--streams", type=int, default=65536,
                    help="streams per GPU (65536 is the benchmark; smaller for profiling)")
     return p.parse_args()
@@ -1399,6 +1404,8 @@ def serving(rm, torch, seconds):
            "resumed": st["resumed"], "evicted": st["evicted"], "budget_gb": 40,
            "max_iterations_in_flight": st["max_inflight"],
            "host_us_per_iteration": st["host_ns"] / max(1, st["iterations"]) / 1e3,
+           "gpu_us_per_iteration": st["gpu_ns"] / max(1, st["iterations"]) / 1e3,
+           "gpu_busy_frac": st["gpu_ns"] / 1e9 / max(1e-9, summ["span_s"]),
            "requests_per_iteration": summ["served"] / max(1, st["iterations"])}
     res["latency_note"] = ("p50/p99: the GPU event that ends a request's iteration minus its "
                            "arrival; host_p50/host_p99: when the scheduler loop saw that event "
@@ -1476,12 +1483,38 @@ def run_case(args):
     persistent batch kernel on log-uniform lengths, large = J = 2^120 + 12345
     (square-and-multiply and table jumps, 1,024 outputs each), plan = the
     partition plan of the partitioned workload alone (256 from the powers of t^J + the
-    tensor-core level, no generation)."""
+    tensor-core level, no generation), serve = the serving recipe's first
+    --serve-seconds through the engine in real time."""
     import torch
     import paper_2512_00093_gb300 as rm
     from paper_2512_00093_gb300.workloads import BatchedUneven, LargeJumps
     dev = torch.device("cuda", 0)
     n = args.streams
+    if args.case == "serve":
+        from paper_2512_00093_gb300.serve import Engine, requests_array
+        from paper_2512_00093_gb300.workloads import Serving
+        w = Serving()
+        a = requests_array(*w.requests(duration=args.serve_seconds), w.J)
+        # offline: every request available at once and one iteration at a
+        # time, so that the iterations (and a profiler's launch list) do not
+        # depend on timing
+        eng = Engine(budget_bytes=40 << 30, max_segments_per_iter=args.serve_max_segments,
+                     max_inflight=1 if args.serve_offline else 4)
+        eng.preload_seeds(range(1, 10**4 + 1))
+        s = eng.run(a, realtime=not args.serve_offline, max_wait=args.serve_seconds * 10 + 60)
+        st = eng.stats
+        eng.close()
+        emit({"case": "serve", "offline": args.serve_offline,
+              "max_segments_per_iter": args.serve_max_segments,
+              "seconds": args.serve_seconds, "served": s["served"],
+              # offline: arrival times are not replayed, so there is no latency
+              "p50_ms": None if args.serve_offline else s["p50_ms"],
+              "p99_ms": None if args.serve_offline else s["p99_ms"],
+              "iterations": st["iterations"],
+              "host_us_per_iteration": st["host_ns"] / max(1, st["iterations"]) / 1e3,
+              "gpu_us_per_iteration": st["gpu_ns"] / max(1, st["iterations"]) / 1e3,
+              "segments": st["segments"]})
+        return 0
     table = rm.Table()
     if args.case == "plan":
         from paper_2512_00093_gb300.workloads import Partitioned

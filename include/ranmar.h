@@ -626,6 +626,19 @@ int ranmar_batch_generate_f32(ranmar_batch_t *b, ranmar_state_t *d_states, size_
                               const uint32_t *d_order, float *d_out, size_t out_len,
                               uint32_t *d_status, ranmar_stream_t stream);
 
+/* ranmar_batch_generate_mixed -- one persistent launch for a descriptor list
+ * whose first n_u24 descriptors produce 24-bit words (as
+ * ranmar_batch_generate_u24) and whose others, d_desc[n_u24 .. n_desc),
+ * produce float32 outputs (as ranmar_batch_generate_f32, their bit patterns
+ * in the same word array d_out), in index order.  The outputs and write-backs
+ * equal those of the two separate calls.  The handle's config applies, with
+ * at most 256 threads a CTA (d_order is not taken).  Errors as
+ * ranmar_batch_generate_u24, plus RANMAR_ERANGE for n_u24 > n_desc. */
+int ranmar_batch_generate_mixed(ranmar_batch_t *b, ranmar_state_t *d_states, size_t n_states,
+                                const ranmar_desc_t *d_desc, size_t n_desc, size_t n_u24,
+                                uint32_t *d_out, size_t out_len, uint32_t *d_status,
+                                ranmar_stream_t stream);
+
 /* ranmar_batch_tune -- autotuner: times every candidate config (group
  * width 32/16/8, 128/256/512 threads, chunk 1/8, all resident CTAs) on this
  * batch (write-back disabled, so the states are not advanced; the outputs
@@ -775,7 +788,8 @@ int ranmar_checksum(const uint32_t *d_data, size_t data_len,
  * Every scheduler iteration admits arrived requests in arrival order while
  * the output pool and the state pool allow, cuts each into segments of at
  * most `seg` outputs (one state each), and enqueues on one stream, after
- * ONE host-to-device copy of a packed staging buffer: the jumps of the
+ * ONE host-to-device copy of a packed staging buffer (which also holds the
+ * iteration's zeroed checksum slots): the jumps of the
  * segment start states (from the seeded state by k J + offset + j seg, or
  * from the resident state by j seg; Sec. 3.1 / 3.2), one persistent batched
  * generation per output type, and ranmar_checksum of every request's
@@ -797,11 +811,11 @@ typedef struct ranmar_serve_config {
     uint64_t seg;            /* outputs per segment, >= 1 */
     uint32_t state_entries;  /* states of the pool, >= 1 */
     uint32_t max_seeds;      /* rows of the seeded-state table, >= 1 */
-    uint32_t result_slots;   /* checksum ring, >= (max_inflight + 2) max_segments */
     uint32_t max_segments;   /* segments one iteration takes (a larger request */
                              /* still runs, alone in its iteration) */
     uint32_t max_inflight;   /* iterations on the device at once, >= 1 */
     uint32_t flags;          /* RANMAR_SERVE_* */
+    uint32_t reserved;       /* 0 */
 } ranmar_serve_config_t;   /* 40 bytes */
 
 /* ranmar_request_t.status */
@@ -842,6 +856,8 @@ typedef struct ranmar_serve_stats {   /* totals over the engine's runs */
     uint64_t max_loop_ns;    /* longest scheduler loop turn */
     uint64_t max_inflight;   /* most iterations on the device at once */
     uint64_t host_ns;        /* host time spent building + enqueueing */
+    uint64_t gpu_ns;         /* device time of the iterations: from the
+                                start of each one's first copy to its end */
     uint64_t resident;       /* resident streams now */
     uint32_t status;         /* RANMAR_ST_* bits the kernels set */
     uint32_t pad;
@@ -869,8 +885,8 @@ typedef struct ranmar_serve_seg {
  * ranmar_serve_create -- allocates an engine on the current device (with
  * RANMAR_SERVE_HOST_ONLY: host memory only, no CUDA call).  The output pool
  * is (budget_bytes - 400 state_entries) / 4 words.  Errors: RANMAR_EINVAL
- * (NULL, a zero size, unknown flags), RANMAR_ERANGE (budget below the state
- * pool, result_slots too small), RANMAR_ENOMEM, RANMAR_ECUDA.
+ * (NULL, a zero size, unknown flags or reserved != 0), RANMAR_ERANGE (budget
+ * below the state pool), RANMAR_ENOMEM, RANMAR_ECUDA.
  */
 int ranmar_serve_create(const ranmar_serve_config_t *cfg, ranmar_serve_t **out);
 /* Waits for the device and frees everything (NULL is a no-op).  Errors:

@@ -53,8 +53,8 @@ class ServeConfig(ctypes.Structure):
     """ranmar_serve_config_t."""
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("seg", ctypes.c_uint64),
                 ("state_entries", ctypes.c_uint32), ("max_seeds", ctypes.c_uint32),
-                ("result_slots", ctypes.c_uint32), ("max_segments", ctypes.c_uint32),
-                ("max_inflight", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+                ("max_segments", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class ServeStats(ctypes.Structure):
@@ -62,7 +62,7 @@ class ServeStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "iterations", "segments", "base_jumps", "pool_jumps", "resumed", "evicted", "rejected",
         "outputs", "new_seeds", "slow_loops", "max_loop_ns", "max_inflight", "host_ns",
-        "resident")] + [("status", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+        "gpu_ns", "resident")] + [("status", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "pad"}
@@ -82,6 +82,7 @@ SEG_DTYPE = np.dtype([("iteration", "<u4"), ("request", "<u4"), ("kind", "<u4"),
                       ("exp", "<u4", (MAX_EXP_WORDS,)), ("live_until", "<u4"),
                       ("out_offset", "<u8"), ("count", "<u8"), ("index0", "<u8")])
 assert REQUEST_DTYPE.itemsize == 88 and SEG_DTYPE.itemsize == 72
+assert ctypes.sizeof(ServeConfig) == 40 and ctypes.sizeof(ServeStats) == 128
 
 
 _L: ctypes.CDLL | None = None
@@ -175,6 +176,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
                "ranmar_serve_run", "ranmar_serve_run_plain", "ranmar_serve_get_stats",
                "ranmar_serve_trace"):
         getattr(lib, nm).restype = ctypes.c_int
+    lib.ranmar_batch_generate_mixed.argtypes = [_vp, _vp, _sz, _vp, _sz, _sz, _vp, _sz, _vp, _vp]
+    lib.ranmar_batch_generate_mixed.restype = ctypes.c_int
     lib.ranmar_graph_begin.argtypes = [_vp]
     lib.ranmar_graph_end.argtypes = [_vp, ctypes.POINTER(_vp)]
     lib.ranmar_graph_launch.argtypes = [_vp, _vp]
@@ -647,6 +650,20 @@ class Batch:
         return self._gen("ranmar_batch_generate_f32", torch.float32, states, desc, out, order,
                          status, stream)
 
+    def generate_mixed(self, states, desc, n_u24: int, out, status=None, stream=None):
+        """ranmar_batch_generate_mixed: desc[:n_u24] give 24-bit words, the rest
+        float32 bit patterns, all into the int32 word tensor `out`, one launch."""
+        states = states.reshape(-1, STATE_WORDS)
+        _need(states, torch.int32, "states")
+        _need(desc, torch.int64, "desc")
+        _need(out, torch.int32, "out")
+        _need_status(status)
+        _check(_lib().ranmar_batch_generate_mixed(self._h, _ptr(states), states.shape[0],
+                                                  _ptr(desc), desc.shape[0], int(n_u24),
+                                                  _ptr(out), out.numel(), _ptr(status),
+                                                  _stream(stream)), "ranmar_batch_generate_mixed")
+        return out
+
     def tune(self, states, desc, out, order=None, stream=None):
         """ranmar_batch_tune: times the candidate configs on this batch (states are
         not advanced) and keeps the fastest.  Returns (config, best_ms)."""
@@ -1020,9 +1037,9 @@ class Serve:
     by run() / run_plain()."""
 
     def __init__(self, budget_bytes: int, seg: int, state_entries: int, max_seeds: int,
-                 result_slots: int, max_segments: int, max_inflight: int, flags: int = 0):
-        self.cfg = ServeConfig(budget_bytes, seg, state_entries, max_seeds, result_slots,
-                               max_segments, max_inflight, flags)
+                 max_segments: int, max_inflight: int, flags: int = 0):
+        self.cfg = ServeConfig(budget_bytes, seg, state_entries, max_seeds, max_segments,
+                               max_inflight, flags, 0)
         h = _vp()
         _check(_lib().ranmar_serve_create(ctypes.byref(self.cfg), ctypes.byref(h)),
                "ranmar_serve_create")

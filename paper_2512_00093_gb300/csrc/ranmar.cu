@@ -26,6 +26,7 @@
 #include "plan_mma2.cuh"
 #include "lfg.cuh"
 #include "overlap.cuh"
+#include "generate_mixed.cuh"
 
 // Batch handle: the workspace of the persistent path on one device.
 struct ranmar_batch {
@@ -192,23 +193,61 @@ __global__ void __launch_bounds__(128) seed_kernel(const int32_t* __restrict__ s
 
 // Weighted checksum of 32-bit words: result[item.result] +=
 // sum_i word[offset + i] * (2 (index0 + i) + 1) mod 2^64, one CTA per item.
+// Each thread issues its 16-byte loads of a pass before it uses any: the
+// words are read once, so for items of a few thousand words the load
+// latency, not the bandwidth, sets the time.  Four words x_0..x_3 of weights
+// w, w + 2, w + 4, w + 6 add w (x_0 + x_1 + x_2 + x_3) + 2 x_1 + 4 x_2 + 6 x_3.
 __global__ void __launch_bounds__(256) checksum_kernel(const uint32_t* __restrict__ data,
                                                       const ranmar_sum_item_t* __restrict__ items,
                                                       uint64_t n_items, uint64_t data_len,
                                                       unsigned long long* __restrict__ results,
                                                       uint64_t n_results, uint32_t* status) {
+  constexpr int kPass = 4;    // 16-byte loads in flight per thread
+  __shared__ unsigned long long part[32];
+  const unsigned tid = threadIdx.x, nt = blockDim.x;
   for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const ranmar_sum_item_t w = items[it];
     if (w.result >= n_results || w.count > data_len || w.offset > data_len - w.count) {
-      if (threadIdx.x == 0) ranmar::flag_status(status, RANMAR_ST_OUT_RANGE);
+      if (tid == 0) ranmar::flag_status(status, RANMAR_ST_OUT_RANGE);
       continue;
     }
+    const uint32_t* p = data + w.offset;
+    const uint64_t mis = (reinterpret_cast<uintptr_t>(p) >> 2) & 3;   // words past a 16-byte line
+    const uint64_t head = min(static_cast<uint64_t>((4 - mis) & 3), w.count);
+    const uint64_t nvec = (w.count - head) >> 2;
+    const uint64_t tail0 = head + 4 * nvec;
+    const uint4* v = reinterpret_cast<const uint4*>(p + head);
+    const unsigned long long w0 = 2ull * w.index0 + 1ull;
     unsigned long long acc = 0;
-    for (uint64_t i = threadIdx.x; i < w.count; i += blockDim.x)
-      acc += static_cast<unsigned long long>(data[w.offset + i]) * (2ull * (w.index0 + i) + 1ull);
+    if (tid < head) acc += static_cast<unsigned long long>(p[tid]) * (w0 + 2ull * tid);
+    if (tid < w.count - tail0)
+      acc += static_cast<unsigned long long>(p[tail0 + tid]) * (w0 + 2ull * (tail0 + tid));
+    for (uint64_t b = tid; b < nvec; b += static_cast<uint64_t>(kPass) * nt) {
+      uint4 x[kPass];
+#pragma unroll
+      for (int u = 0; u < kPass; ++u) {
+        const uint64_t q = b + static_cast<uint64_t>(u) * nt;
+        x[u] = q < nvec ? v[q] : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < kPass; ++u) {
+        const uint64_t q = b + static_cast<uint64_t>(u) * nt;
+        const unsigned long long wt = w0 + 2ull * (head + 4 * q);
+        const unsigned long long sum = static_cast<unsigned long long>(x[u].x) + x[u].y +
+                                       x[u].z + x[u].w;
+        acc += wt * sum + 2ull * x[u].y + 4ull * x[u].z + 6ull * x[u].w;
+      }
+    }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(ranmar::kFull, acc, d);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&results[w.result], acc);
+    if ((tid & 31) == 0) part[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long tot = 0;
+      for (unsigned q = 0; q < nt / 32; ++q) tot += part[q];
+      atomicAdd(&results[w.result], tot);
+    }
+    __syncthreads();
   }
 }
 
@@ -353,6 +392,68 @@ int run_persistent(ranmar_batch* b, const ranmar_batch_config_t& c, bool f32,
   }
 #undef RANMAR_LAUNCH
   return check_launch();
+}
+
+template <int W, int S>
+int mixed_occupancy(int threads) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &nb, ranmar::generate_persistent_mixed_kernel<W, S>, threads, 0);
+  return nb;
+}
+
+// Enqueues queue reset + the mixed-type persistent kernel with config c: a
+// stream a group (S = 1) when every descriptor's group can be resident at
+// once, else the interleaved width of the other persistent kernels.
+template <int W>
+int launch_mixed(ranmar_batch* b, const ranmar_batch_config_t& c, int T, ranmar_state_t* states,
+                 size_t n_states, const ranmar_desc_t* desc, size_t n_desc, size_t n_u24,
+                 uint32_t* out, size_t out_len, uint32_t* status, cudaStream_t s) {
+  constexpr int kIlp = ranmar::persistent_ilp<W>();
+  const int occ1 = mixed_occupancy<W, 1>(T);
+  const int per_sm1 = c.ctas_per_sm > 0 && c.ctas_per_sm < occ1 ? c.ctas_per_sm : occ1;
+  const uint64_t groups_per_cta = static_cast<uint64_t>(T / W);
+  const uint64_t groups_needed = (n_desc + c.chunk - 1) / c.chunk;
+  const bool one = kIlp == 1 || groups_needed <= static_cast<uint64_t>(per_sm1) *
+                                                     b->num_sms * groups_per_cta;
+  const int occ = one ? occ1 : mixed_occupancy<W, kIlp>(T);
+  if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration);
+  const int per_sm = c.ctas_per_sm > 0 ? (c.ctas_per_sm < occ ? c.ctas_per_sm : occ) : occ;
+  uint64_t grid = static_cast<uint64_t>(per_sm) * b->num_sms;
+  const uint64_t need = (groups_needed + groups_per_cta - 1) / groups_per_cta;
+  if (need < grid) grid = need;
+  if (grid < 1) grid = 1;
+  cudaError_t e = cudaMemsetAsync(b->queue, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (one)
+    ranmar::generate_persistent_mixed_kernel<W, 1><<<static_cast<unsigned>(grid), T, 0, s>>>(
+        states, n_states, desc, n_desc, n_u24, out, out_len, status, b->queue, c.chunk);
+  else
+    ranmar::generate_persistent_mixed_kernel<W, kIlp><<<static_cast<unsigned>(grid), T, 0, s>>>(
+        states, n_states, desc, n_desc, n_u24, out, out_len, status, b->queue, c.chunk);
+  return check_launch();
+}
+
+int run_persistent_mixed(ranmar_batch* b, const ranmar_batch_config_t& c, ranmar_state_t* states,
+                         size_t n_states, const ranmar_desc_t* desc, size_t n_desc,
+                         size_t n_u24, uint32_t* out, size_t out_len, uint32_t* status,
+                         cudaStream_t s) {
+  // the kernel is compiled for at most 256 threads a CTA (two CTAs an SM)
+  const int T = c.threads_per_cta < 256 ? c.threads_per_cta : 256;
+  switch (c.lanes_per_stream) {
+    case 32:
+      return launch_mixed<32>(b, c, T, states, n_states, desc, n_desc, n_u24, out, out_len,
+                              status, s);
+    case 16:
+      return launch_mixed<16>(b, c, T, states, n_states, desc, n_desc, n_u24, out, out_len,
+                              status, s);
+    case 8:
+      return launch_mixed<8>(b, c, T, states, n_states, desc, n_desc, n_u24, out, out_len,
+                             status, s);
+    default:
+      return launch_mixed<4>(b, c, T, states, n_states, desc, n_desc, n_u24, out, out_len,
+                             status, s);
+  }
 }
 
 int batch_generate(ranmar_batch* b, bool f32, ranmar_state_t* states, size_t n_states,
@@ -831,6 +932,21 @@ int ranmar_batch_generate_f32(ranmar_batch_t* b, ranmar_state_t* d_states, size_
   NvtxRange nvtx_("ranmar_batch_generate_f32");
   return batch_generate(b, true, d_states, n_states, d_desc, n_desc, d_order, d_out, out_len,
                         d_status, stream);
+}
+
+int ranmar_batch_generate_mixed(ranmar_batch_t* b, ranmar_state_t* d_states, size_t n_states,
+                                const ranmar_desc_t* d_desc, size_t n_desc, size_t n_u24,
+                                uint32_t* d_out, size_t out_len, uint32_t* d_status,
+                                ranmar_stream_t stream) {
+  NvtxRange nvtx_("ranmar_batch_generate_mixed");
+  if (!on_device(b)) return RANMAR_EINVAL;
+  if (n_u24 > n_desc) return RANMAR_ERANGE;
+  if (n_desc == 0) return RANMAR_OK;
+  if (!d_states || !d_desc || !d_out) return RANMAR_EINVAL;
+  if (n_states == 0) return RANMAR_ERANGE;
+  if (!aligned(d_states, 16) || !aligned(d_desc, 8) || !aligned(d_out, 4)) return RANMAR_EINVAL;
+  return run_persistent_mixed(b, b->cfg, d_states, n_states, d_desc, n_desc, n_u24, d_out,
+                              out_len, d_status, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int ranmar_batch_tune(ranmar_batch_t* b, int f32, ranmar_state_t* d_states, size_t n_states,

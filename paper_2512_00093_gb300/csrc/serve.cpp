@@ -11,7 +11,8 @@
 //   * the jumps of the segment start states (Sec. 3.1 / 3.2) -- from the
 //     seed's seeded state by k J + offset + j seg, or, when the stream's
 //     state is still resident at `offset`, from that state by j seg;
-//   * one persistent batched generation per output type (Algorithm 2);
+//   * one persistent batched generation of all segments, both output
+//     types (Algorithm 2);
 //   * the device checksums of the outputs (how they are consumed before
 //     their memory is recycled) and their copy back to pinned host memory.
 // Up to max_inflight iterations are on the device while the host builds
@@ -55,6 +56,7 @@ constexpr size_t kPlainRing = 1024;             // plain-mode requests in flight
 static_assert(sizeof(ranmar_request_t) == 88, "request layout");
 static_assert(sizeof(ranmar_serve_seg_t) == 72, "trace layout");
 static_assert(sizeof(ranmar_serve_config_t) == 40, "config layout");
+static_assert(sizeof(ranmar_serve_stats_t) == 128, "stats layout");
 
 double seconds_since(Clock::time_point t0) {
   return std::chrono::duration<double>(Clock::now() - t0).count();
@@ -184,7 +186,7 @@ struct Admitted {
 struct Iter {
   uint32_t number = 0;
   uint32_t stage = 0;
-  uint64_t lo_slot = 0;
+  size_t res_off = 0;   // its checksum slots in the stage buffers
   std::vector<Admitted> reqs;
   std::vector<uint32_t> ents;
 };
@@ -194,13 +196,15 @@ struct Stage {
   unsigned char* h = nullptr;
   unsigned char* d = nullptr;
   size_t cap = 0;
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr;        // end of the iteration's device work
+  cudaEvent_t ev_start = nullptr;  // before its first copy
   bool busy = false;      // enqueued and not yet retired
 };
 
-// Per-segment bytes of the staging layout, at most: a checksum item, a
-// descriptor, one jump (exponent + two indices) and one new seed.
-constexpr size_t kStageBytesPerSeg = sizeof(ranmar_sum_item_t) + sizeof(ranmar_desc_t) +
+// Per-segment bytes of the staging layout, at most: a checksum slot (one
+// per request), a checksum item, a descriptor, one jump (exponent + two
+// indices) and one new seed.
+constexpr size_t kStageBytesPerSeg = 8 + sizeof(ranmar_sum_item_t) + sizeof(ranmar_desc_t) +
                                      RANMAR_MAX_EXP_WORDS * 4 + 8 + 4;
 constexpr size_t kStagePad = 16 * 12;
 
@@ -219,9 +223,7 @@ struct ranmar_serve {
   ranmar_state_t* pool = nullptr;      // state_entries states
   uint32_t* out = nullptr;             // output pool (words / float bit patterns)
   ranmar_state_t* base = nullptr;      // seeded states, one row per seed
-  uint64_t* results = nullptr;         // checksum ring
   uint32_t* status = nullptr;
-  uint64_t* results_host = nullptr;    // pinned mirror of the ring
   ranmar_table_t* table = nullptr;
   ranmar_batch_t* batch = nullptr;
   std::vector<Stage> stages;
@@ -241,7 +243,6 @@ struct ranmar_serve {
   std::unordered_map<StreamKey, Resident, StreamKeyHash> resident;
   std::list<StreamKey> lru;            // front: least recently used
   std::unordered_map<int32_t, uint32_t> seed_row;
-  uint64_t res_next = 0;
   uint32_t iter_count = 0;
   ranmar_serve_stats_t stats{};
   // host-only trace
@@ -331,14 +332,6 @@ void admit(ranmar_serve& e, std::deque<uint32_t>& waiting, Iter& it) {
   }
 }
 
-uint64_t take_slots(ranmar_serve& e, uint64_t n) {
-  const uint64_t size = e.cfg.result_slots;
-  if (e.res_next % size + n > size) e.res_next += size - e.res_next % size;
-  const uint64_t lo = e.res_next % size;
-  e.res_next += n;
-  return lo;
-}
-
 int ensure_stage(ranmar_serve& e, Stage& st, size_t bytes) {
   if (bytes <= st.cap) return RANMAR_OK;
   if (e.host_only) {
@@ -417,18 +410,20 @@ int enqueue(ranmar_serve& e, Iter& it) {
     else
       nj += a.nseg;
   }
-  const size_t nf = ntot - nu, m = fresh.size();
-  // layout: items | desc_u | desc_f | jump exps | base idx | dst idx |
-  //         pool exps (two words) | pool base idx | pool dst idx | seeds
+  const size_t m = fresh.size();
+  // layout: checksum slots (zeroed here, summed into on the device, copied
+  //         back) | items | descriptors (u24 ones, then f32 ones) | jump
+  //         exps | base idx | dst idx | pool exps (two words) | pool base
+  //         idx | pool dst idx | seeds
   size_t off = 0;
   auto place = [&off](size_t bytes) {
     const size_t at = off;
     off = align16(off + bytes);
     return at;
   };
+  const size_t o_res = place(nreq * sizeof(uint64_t));
   const size_t o_items = place(ntot * sizeof(ranmar_sum_item_t));
-  const size_t o_du = place(nu * sizeof(ranmar_desc_t));
-  const size_t o_df = place(nf * sizeof(ranmar_desc_t));
+  const size_t o_du = place(ntot * sizeof(ranmar_desc_t));
   const size_t o_je = place(nj * RANMAR_MAX_EXP_WORDS * 4);
   const size_t o_jb = place(nj * 4);
   const size_t o_jd = place(nj * 4);
@@ -441,7 +436,7 @@ int enqueue(ranmar_serve& e, Iter& it) {
   unsigned char* h = st.h;
   auto* items = reinterpret_cast<ranmar_sum_item_t*>(h + o_items);
   auto* du = reinterpret_cast<ranmar_desc_t*>(h + o_du);
-  auto* df = reinterpret_cast<ranmar_desc_t*>(h + o_df);
+  auto* df = du + nu;
   auto* je = reinterpret_cast<uint32_t*>(h + o_je);
   auto* jb = reinterpret_cast<uint32_t*>(h + o_jb);
   auto* jd = reinterpret_cast<uint32_t*>(h + o_jd);
@@ -449,7 +444,8 @@ int enqueue(ranmar_serve& e, Iter& it) {
   auto* pb = reinterpret_cast<uint32_t*>(h + o_pb);
   auto* pd = reinterpret_cast<uint32_t*>(h + o_pd);
   if (m) std::memcpy(h + o_sd, fresh.data(), m * 4);
-  it.lo_slot = take_slots(e, nreq);
+  std::memset(h + o_res, 0, nreq * sizeof(uint64_t));
+  it.res_off = o_res;
   const uint64_t seg = e.cfg.seg;
   size_t ci = 0, cu = 0, cf = 0, cj = 0, cp = 0;
   for (uint32_t q = 0; q < nreq; ++q) {
@@ -496,7 +492,7 @@ int enqueue(ranmar_serve& e, Iter& it) {
         df[cf++] = d;
       else
         du[cu++] = d;
-      items[ci++] = {a.region + js, cnt, js, static_cast<uint32_t>(it.lo_slot + q), 0u};
+      items[ci++] = {a.region + js, cnt, js, q, 0u};
       if (e.host_only) {
         tr.iteration = it.number;
         tr.request = a.req;
@@ -524,6 +520,8 @@ int enqueue(ranmar_serve& e, Iter& it) {
   cudaStream_t s = e.stream;
   ranmar_stream_t rs = reinterpret_cast<ranmar_stream_t>(s);
   unsigned char* d = st.d;
+  rc = cuda_check(cudaEventRecord(st.ev_start, s));
+  if (rc) return rc;
   rc = cuda_check(cudaMemcpyAsync(d, h, off, cudaMemcpyHostToDevice, s));
   if (rc) return rc;
   if (m) {
@@ -543,25 +541,16 @@ int enqueue(ranmar_serve& e, Iter& it) {
                  reinterpret_cast<const uint32_t*>(d + o_pd), npj);
     if (rc) return rc;
   }
-  if (nu) {
-    rc = ranmar_batch_generate_u24(e.batch, e.pool, e.cfg.state_entries,
-                                   reinterpret_cast<const ranmar_desc_t*>(d + o_du), nu, nullptr,
+  // both output types in one persistent launch
+  rc = ranmar_batch_generate_mixed(e.batch, e.pool, e.cfg.state_entries,
+                                   reinterpret_cast<const ranmar_desc_t*>(d + o_du), ntot, nu,
                                    e.out, e.out_words, e.status, rs);
-    if (rc) return rc;
-  }
-  if (nf) {
-    rc = ranmar_batch_generate_f32(e.batch, e.pool, e.cfg.state_entries,
-                                   reinterpret_cast<const ranmar_desc_t*>(d + o_df), nf, nullptr,
-                                   reinterpret_cast<float*>(e.out), e.out_words, e.status, rs);
-    if (rc) return rc;
-  }
-  rc = cuda_check(cudaMemsetAsync(e.results + it.lo_slot, 0, nreq * sizeof(uint64_t), s));
   if (rc) return rc;
   rc = ranmar_checksum(e.out, e.out_words, reinterpret_cast<const ranmar_sum_item_t*>(d + o_items),
-                       ntot, e.results, e.cfg.result_slots, e.status, rs);
+                       ntot, reinterpret_cast<uint64_t*>(d + o_res), nreq, e.status, rs);
   if (rc) return rc;
-  rc = cuda_check(cudaMemcpyAsync(e.results_host + it.lo_slot, e.results + it.lo_slot,
-                                  nreq * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  rc = cuda_check(cudaMemcpyAsync(h + o_res, d + o_res, nreq * sizeof(uint64_t),
+                                  cudaMemcpyDeviceToHost, s));
   if (rc) return rc;
   rc = cuda_check(cudaEventRecord(st.ev, s));
   e.stats.host_ns += static_cast<uint64_t>(seconds_since(tb) * 1e9);
@@ -592,10 +581,12 @@ int retire(ranmar_serve& e, const Iter& it) {
   if (!e.host_only) {
     int rc = cuda_check(cudaEventSynchronize(st.ev));
     if (rc) return rc;
-    float ms = 0.f;
+    float ms = 0.f, busy_ms = 0.f;
     rc = cuda_check(cudaEventElapsedTime(&ms, e.t0, st.ev));
+    if (!rc) rc = cuda_check(cudaEventElapsedTime(&busy_ms, st.ev_start, st.ev));
     if (rc) return rc;
     done = ms * 1e-3;
+    e.stats.gpu_ns += static_cast<uint64_t>(busy_ms * 1e6);
   } else {
     e.trace_live_until[it.number] = e.iter_count;
   }
@@ -607,7 +598,7 @@ int retire(ranmar_serve& e, const Iter& it) {
     ranmar_request_t& r = e.reqs[a.req];
     r.done = done;
     r.host_done = host_done;
-    r.checksum = e.host_only ? 0 : e.results_host[it.lo_slot + q];
+    r.checksum = e.host_only ? 0 : reinterpret_cast<const uint64_t*>(st.h + it.res_off)[q];
     r.status = RANMAR_REQ_DONE;
     e.alloc.release(a.region, std::max<uint64_t>(1, r.count));
     const uint32_t* ents = it.ents.data() + a.first;
@@ -753,6 +744,7 @@ void free_device(ranmar_serve* e) {
       if (st.h) cudaFreeHost(st.h);
       if (st.d) cudaFree(st.d);
       if (st.ev) cudaEventDestroy(st.ev);
+      if (st.ev_start) cudaEventDestroy(st.ev_start);
     }
   }
   if (!e->host_only) {
@@ -762,33 +754,33 @@ void free_device(ranmar_serve* e) {
     cudaFree(e->pool);
     cudaFree(e->out);
     cudaFree(e->base);
-    cudaFree(e->results);
     cudaFree(e->status);
     cudaFree(e->plain_d);
     cudaFree(e->plain_state);
-    if (e->results_host) cudaFreeHost(e->results_host);
     if (e->plain_h) cudaFreeHost(e->plain_h);
     if (e->table) ranmar_table_destroy(e->table);
     if (e->batch) ranmar_batch_destroy(e->batch);
   }
 }
 
-// Plain-mode record: one request's jump exponent and indices, seed and
-// checksum item (64 bytes, pinned, one per request in flight).
-struct PlainRec {
+// Plain-mode record: one request's jump exponent and indices, seed,
+// checksum item and checksum (80 bytes, pinned and on the device, one per
+// request in flight; the checksum is zeroed on the host, summed into on the
+// device and copied back).
+struct alignas(16) PlainRec {
   uint32_t exp[RANMAR_MAX_EXP_WORDS];
   uint32_t base_idx;
   uint32_t dst_idx;
   int32_t seed;
   ranmar_sum_item_t item;
+  uint64_t result;
 };
-static_assert(sizeof(PlainRec) == 64, "plain record");
+static_assert(sizeof(PlainRec) == 80, "plain record");
 
 struct PlainPending {
   uint32_t req;
   uint32_t rec;
   uint64_t region;
-  uint64_t slot;
 };
 
 int plain_retire(ranmar_serve& e, const PlainPending& p) {
@@ -799,7 +791,7 @@ int plain_retire(ranmar_serve& e, const PlainPending& p) {
   ranmar_request_t& r = e.reqs[p.req];
   r.done = ms * 1e-3;
   r.host_done = seconds_since(e.h0);
-  r.checksum = e.results_host[p.slot];
+  r.checksum = (reinterpret_cast<const PlainRec*>(e.plain_h) + p.rec)->result;
   r.status = RANMAR_REQ_DONE;
   e.alloc.release(p.region, std::max<uint64_t>(1, r.count));
   return RANMAR_OK;
@@ -852,8 +844,8 @@ int plain_loop(ranmar_serve& e, size_t n, bool realtime, double max_wait) {
       fresh = true;
     }
     h->base_idx = row->second;
-    const uint64_t slot = take_slots(e, 1);
-    h->item = {0, r.count, 0, static_cast<uint32_t>(slot), 0u};
+    h->item = {0, r.count, 0, 0u, 0u};
+    h->result = 0;
     int rc = cuda_check(cudaMemcpyAsync(d, h, sizeof(PlainRec), cudaMemcpyHostToDevice, s));
     if (!rc && fresh) rc = ranmar_seed_batch(&d->seed, 1, e.base + row->second, e.status, rs);
     if (!rc)
@@ -864,16 +856,15 @@ int plain_loop(ranmar_serve& e, size_t n, bool realtime, double max_wait) {
       rc = r.f32 ? ranmar_generate_plain_f32(e.plain_state, r.count,
                                              reinterpret_cast<float*>(e.out) + region, 0, rs)
                  : ranmar_generate_plain_u24(e.plain_state, r.count, e.out + region, 0, rs);
-    if (!rc) rc = cuda_check(cudaMemsetAsync(e.results + slot, 0, sizeof(uint64_t), s));
     if (!rc)
-      rc = ranmar_checksum(e.out + region, r.count ? r.count : 1, &d->item, 1, e.results,
-                           e.cfg.result_slots, e.status, rs);
+      rc = ranmar_checksum(e.out + region, r.count ? r.count : 1, &d->item, 1, &d->result, 1,
+                           e.status, rs);
     if (!rc)
-      rc = cuda_check(cudaMemcpyAsync(e.results_host + slot, e.results + slot, sizeof(uint64_t),
+      rc = cuda_check(cudaMemcpyAsync(&h->result, &d->result, sizeof(uint64_t),
                                       cudaMemcpyDeviceToHost, s));
     if (!rc) rc = cuda_check(cudaEventRecord(e.plain_ev[ri], s));
     if (rc) return rc;
-    pending.push_back({static_cast<uint32_t>(i), ri, region, slot});
+    pending.push_back({static_cast<uint32_t>(i), ri, region});
     while (!pending.empty() && event_done(e.plain_ev[pending.front().rec])) {
       rc = plain_retire(e, pending.front());
       if (rc) return rc;
@@ -897,11 +888,9 @@ int ranmar_serve_create(const ranmar_serve_config_t* cfg, ranmar_serve_t** out) 
   *out = nullptr;
   const ranmar_serve_config_t c = *cfg;
   if (c.seg == 0 || c.state_entries == 0 || c.max_seeds == 0 || c.max_segments == 0 ||
-      c.max_inflight == 0 || (c.flags & ~(RANMAR_SERVE_SQUARE | RANMAR_SERVE_HOST_ONLY)))
+      c.max_inflight == 0 || (c.flags & ~(RANMAR_SERVE_SQUARE | RANMAR_SERVE_HOST_ONLY)) ||
+      c.reserved != 0)
     return RANMAR_EINVAL;
-  if (static_cast<uint64_t>(c.result_slots) <
-      (static_cast<uint64_t>(c.max_inflight) + 2) * c.max_segments)
-    return RANMAR_ERANGE;
   const uint64_t state_bytes = static_cast<uint64_t>(c.state_entries) * sizeof(ranmar_state_t);
   if (c.budget_bytes <= state_bytes + 4 * kRegionAlign) return RANMAR_ERANGE;
   ranmar_serve* e = new (std::nothrow) ranmar_serve();
@@ -927,15 +916,11 @@ int ranmar_serve_create(const ranmar_serve_config_t* cfg, ranmar_serve_t** out) 
     dalloc(reinterpret_cast<void**>(&e->out), e->out_words * 4);
     dalloc(reinterpret_cast<void**>(&e->base),
            static_cast<size_t>(c.max_seeds) * sizeof(ranmar_state_t));
-    dalloc(reinterpret_cast<void**>(&e->results), static_cast<size_t>(c.result_slots) * 8);
     dalloc(reinterpret_cast<void**>(&e->status), 4);
     dalloc(reinterpret_cast<void**>(&e->plain_d), kPlainRing * sizeof(PlainRec));
     dalloc(reinterpret_cast<void**>(&e->plain_state), sizeof(ranmar_state_t));
-    if (!rc && (cudaHostAlloc(reinterpret_cast<void**>(&e->results_host),
-                              static_cast<size_t>(c.result_slots) * 8, cudaHostAllocDefault) !=
-                    cudaSuccess ||
-                cudaHostAlloc(reinterpret_cast<void**>(&e->plain_h), kPlainRing * sizeof(PlainRec),
-                              cudaHostAllocDefault) != cudaSuccess)) {
+    if (!rc && cudaHostAlloc(reinterpret_cast<void**>(&e->plain_h), kPlainRing * sizeof(PlainRec),
+                             cudaHostAllocDefault) != cudaSuccess) {
       cudaGetLastError();
       rc = RANMAR_ENOMEM;
     }
@@ -943,6 +928,7 @@ int ranmar_serve_create(const ranmar_serve_config_t* cfg, ranmar_serve_t** out) 
     if (!rc) rc = cuda_check(cudaEventCreate(&e->t0));
     for (Stage& st : e->stages) {
       if (!rc) rc = cuda_check(cudaEventCreate(&st.ev));
+      if (!rc) rc = cuda_check(cudaEventCreate(&st.ev_start));
       if (!rc) rc = ensure_stage(*e, st, stage_bytes);
     }
     e->plain_ev.assign(kPlainRing, nullptr);

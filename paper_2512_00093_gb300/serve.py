@@ -161,12 +161,11 @@ class Engine:
 
     def __init__(self, budget_bytes: int = 40 << 30, seg: int = 4096,
                  state_entries: int = 1 << 18, max_seeds: int = 10**4 + 1,
-                 result_slots: int = 1 << 17, max_segments_per_iter: int = 8192,
-                 max_inflight: int = 4, device="cuda", use_table: bool = True,
-                 host_only: bool = False):
+                 max_segments_per_iter: int = 8192, max_inflight: int = 4, device="cuda",
+                 use_table: bool = True, host_only: bool = False):
         flags = (0 if use_table else bd.SERVE_SQUARE) | (bd.SERVE_HOST_ONLY if host_only else 0)
-        args = (budget_bytes, seg, state_entries, max_seeds, result_slots,
-                max_segments_per_iter, max_inflight, flags)
+        args = (budget_bytes, seg, state_entries, max_seeds, max_segments_per_iter,
+                max_inflight, flags)
         self.host_only = host_only
         self.dev = None if host_only else torch.device(device)
         if host_only:

@@ -94,6 +94,47 @@ def test_persistent_equals_reference(rm, dev, orc, lanes, f32):
     b.close()
 
 
+@pytest.mark.parametrize("lanes,threads,ctas,n", [
+    (32, 256, 0, 701), (16, 256, 0, 701), (8, 128, 0, 701), (4, 256, 0, 701),
+    (32, 512, 0, 701),                           # more than 256 threads: clamped
+    (32, 256, 1, 2001), (16, 128, 1, 2001)])     # more groups than resident: interleaved
+def test_mixed_launch_equals_separate_calls(rm, dev, orc, lanes, threads, ctas, n):
+    """ranmar_batch_generate_mixed: descriptors [0, n_u24) as 24-bit words,
+    the rest as float32, in one launch, equal the two separate calls (outputs
+    and written-back states), for a boundary inside an interleaved group and
+    at the ends, with a stream a group (every group resident) and with
+    interleaved groups (more descriptors than resident groups)."""
+    c = counts_mix(n, 23)
+    J = (1 << 100) + 77
+    base = rm.seed(4242).to(dev)
+    states0 = rm.partition(base, J, 0, n)
+    b = rm.Batch(n)
+    b.config = (lanes, threads, ctas, 1)
+    desc, _, total = b.pack(torch.as_tensor(c, device=dev), flags=rm.DESC_WRITE_BACK)
+    tot = int(total.item())
+    for n_u24 in (0, 1, 350, 351, n - 3, n):
+        st_ref = states0.clone()
+        out_ref = torch.full((tot + 3,), -1, dtype=torch.int32, device=dev)
+        rm.generate_u24(st_ref, desc[:n_u24], out_ref)
+        rm.generate_f32(st_ref, desc[n_u24:], out_ref.view(torch.float32))
+        st = states0.clone()
+        out = torch.full_like(out_ref, -1)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        b.generate_mixed(st, desc, n_u24, out, status=status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert torch.equal(out, out_ref), n_u24
+        assert torch.equal(st, st_ref), n_u24
+    got = out.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum(c)[:-1]])
+    for i in [0, 349, 350, n - 1]:         # n_u24 = n: all u24
+        ref = orc.stream(4242, i * J, int(c[i]))
+        assert np.array_equal(got[offs[i]:offs[i] + c[i]].view(np.uint32), ref), i
+    with pytest.raises(rm.RanmarError):
+        b.generate_mixed(st, desc, n + 1, out)
+    b.close()
+
+
 def test_tune_keeps_states_and_outputs(rm, dev):
     n = 3000
     c = counts_mix(n, 5)

@@ -59,6 +59,32 @@ def test_checksum_kernel_matches_host(rm):
     assert int(got[1]) == rm.checksum_np(h[5:12], index0=3)
 
 
+def test_checksum_kernel_ragged_items(rm):
+    """Items at every alignment, of lengths 0..9 and across several passes of
+    the kernel's vector loop, some sharing a result slot: each slot equals
+    the host sum of its items."""
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(2)
+    data_h = rng.integers(0, 1 << 32, 300_000, dtype=np.uint64).astype(np.uint32)
+    data = torch.as_tensor(data_h.view(np.int32), device=dev)
+    items, want = [], {}
+    for q in range(400):
+        off = int(rng.integers(0, 200_000))
+        cnt = int(rng.integers(0, 10)) if q % 2 else int(rng.integers(0, 90_000))
+        idx0 = int(rng.integers(0, 1 << 40))
+        slot = q % 37
+        items.append([off, cnt, idx0, slot])
+        want[slot] = (want.get(slot, 0) + rm.checksum_np(data_h[off:off + cnt], index0=idx0)) \
+            % (1 << 64)
+    res = torch.zeros(37, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rm.checksum(data, torch.tensor(items, dtype=torch.int64, device=dev), res, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    got = res.cpu().numpy().astype(np.uint64)
+    assert [int(got[s]) for s in range(37)] == [want[s] for s in range(37)]
+
+
 def test_serving_mix_matches_oracle_and_alone(rm, orc):
     from paper_2512_00093_gb300.serve import Engine, Request
     reqs = mixed_requests(260, 7)

@@ -20,8 +20,7 @@ def bd():
 
 def host_engine(**kw):
     args = dict(budget_bytes=64 << 20, seg=16, state_entries=64, max_seeds=64,
-                result_slots=1 << 12, max_segments_per_iter=24, max_inflight=3,
-                host_only=True)
+                max_segments_per_iter=24, max_inflight=3, host_only=True)
     args.update(kw)
     return serve.Engine(**args)
 
@@ -73,12 +72,12 @@ def test_overlap_flag_in_summary():
 
 
 def test_create_argument_checks(bd):
-    ok = dict(budget_bytes=1 << 20, seg=16, state_entries=8, max_seeds=4, result_slots=1024,
+    ok = dict(budget_bytes=1 << 20, seg=16, state_entries=8, max_seeds=4,
               max_segments=16, max_inflight=2, flags=bd.SERVE_HOST_ONLY)
     bd.Serve(**ok).close()
     for bad, code in [(dict(seg=0), bd.EINVAL), (dict(state_entries=0), bd.EINVAL),
                       (dict(max_inflight=0), bd.EINVAL), (dict(flags=8), bd.EINVAL),
-                      (dict(result_slots=63), bd.ERANGE),          # < (2 + 2) * 16
+                      (dict(max_segments=0), bd.EINVAL),
                       (dict(budget_bytes=8 * 400), bd.ERANGE)]:     # no room for outputs
         with pytest.raises(bd.RanmarError) as ei:
             bd.Serve(**{**ok, **bad})
