@@ -787,17 +787,21 @@ int ranmar_checksum(const uint32_t *d_data, size_t data_len,
  * that starts where an earlier one of the same stream ended needs no jump.
  * Every scheduler iteration admits arrived requests in arrival order while
  * the output pool and the state pool allow, cuts each into segments of at
- * most `seg` outputs (one state each), and enqueues on one stream, after
- * ONE host-to-device copy of a packed staging buffer (which also holds the
- * iteration's zeroed checksum slots): the jumps of the
- * segment start states (from the seeded state by k J + offset + j seg, or
- * from the resident state by j seg; Sec. 3.1 / 3.2), one persistent batched
- * generation per output type, and ranmar_checksum of every request's
- * outputs (the outputs are consumed on the device; their region is then
- * recycled).  Up to max_inflight iterations are on the device while the
- * host builds the next.  Unlike the calls above, an engine owns device
- * memory (budget_bytes + 400 * max_seeds bytes and small buffers) and
- * synchronizes its stream.  An engine is used by one host thread at a time.
+ * most `seg` outputs (one state each), and enqueues:
+ *   - on a stream of the engine's own: ONE host-to-device copy of a packed
+ *     staging buffer (which also holds the iteration's zeroed checksum
+ *     slots), the seeding of new seeds, and the jumps of the segment start
+ *     states (from the seeded state by k J + offset + j seg, or from the
+ *     resident state by j seg; Sec. 3.1 / 3.2);
+ *   - then on the caller's stream: one persistent generation of all
+ *     segments (ranmar_batch_generate_mixed), ranmar_checksum of every
+ *     request's outputs (the outputs are consumed on the device; their
+ *     region is then recycled), and the copy of the checksums back.
+ * An iteration's jumps thus run while earlier iterations generate.  Up to
+ * max_inflight iterations are on the device while the host builds the next.
+ * Unlike the calls above, an engine owns device memory (budget_bytes + 400
+ * max_seeds bytes and small buffers) and a stream, and synchronizes the
+ * caller's stream.  An engine is used by one host thread at a time.
  * ------------------------------------------------------------------------ */
 typedef struct ranmar_serve ranmar_serve_t;
 

@@ -198,6 +198,7 @@ struct Stage {
   size_t cap = 0;
   cudaEvent_t ev = nullptr;        // end of the iteration's device work
   cudaEvent_t ev_start = nullptr;  // before its first copy
+  cudaEvent_t ev_jumped = nullptr; // its start states are written
   bool busy = false;      // enqueued and not yet retired
 };
 
@@ -252,7 +253,8 @@ struct ranmar_serve {
   cudaEvent_t t0 = nullptr;
   Clock::time_point h0;
   ranmar_request_t* reqs = nullptr;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;       // the caller's: generation, checksums, copies back
+  cudaStream_t jstream = nullptr;      // the engine's: staging copy, seeding, jumps
 };
 
 namespace {
@@ -375,7 +377,7 @@ int new_seed_rows(ranmar_serve& e, const Iter& it, std::vector<int32_t>& fresh, 
 
 int do_jump(ranmar_serve& e, const ranmar_state_t* src, size_t n_src, const uint32_t* idx,
             const uint32_t* exps, uint32_t words, const uint32_t* dst_idx, size_t n) {
-  ranmar_stream_t s = reinterpret_cast<ranmar_stream_t>(e.stream);
+  ranmar_stream_t s = reinterpret_cast<ranmar_stream_t>(e.jstream);
   if (e.table)
     return ranmar_jump_tab(e.table, src, n_src, idx, exps, words, e.pool, e.cfg.state_entries,
                            dst_idx, n, e.status, s);
@@ -517,16 +519,22 @@ int enqueue(ranmar_serve& e, Iter& it) {
     e.stats.host_ns += static_cast<uint64_t>(seconds_since(tb) * 1e9);
     return RANMAR_OK;
   }
-  cudaStream_t s = e.stream;
+  // The staging copy, new seeds and jumps go on the engine's stream, the
+  // rest on the caller's after them: the jumps of this iteration then run
+  // while earlier iterations still generate.  They touch no state an
+  // earlier iteration still uses: start states go to entries taken from the
+  // free list, and the resident states they read were written by retired
+  // iterations.
+  cudaStream_t s = e.stream, js = e.jstream;
   ranmar_stream_t rs = reinterpret_cast<ranmar_stream_t>(s);
   unsigned char* d = st.d;
-  rc = cuda_check(cudaEventRecord(st.ev_start, s));
+  rc = cuda_check(cudaEventRecord(st.ev_start, js));
   if (rc) return rc;
-  rc = cuda_check(cudaMemcpyAsync(d, h, off, cudaMemcpyHostToDevice, s));
+  rc = cuda_check(cudaMemcpyAsync(d, h, off, cudaMemcpyHostToDevice, js));
   if (rc) return rc;
   if (m) {
     rc = ranmar_seed_batch(reinterpret_cast<const int32_t*>(d + o_sd), m, e.base + r0, e.status,
-                           rs);
+                           reinterpret_cast<ranmar_stream_t>(js));
     if (rc) return rc;
   }
   if (nj) {
@@ -541,6 +549,9 @@ int enqueue(ranmar_serve& e, Iter& it) {
                  reinterpret_cast<const uint32_t*>(d + o_pd), npj);
     if (rc) return rc;
   }
+  rc = cuda_check(cudaEventRecord(st.ev_jumped, js));
+  if (!rc) rc = cuda_check(cudaStreamWaitEvent(s, st.ev_jumped, 0));
+  if (rc) return rc;
   // both output types in one persistent launch
   rc = ranmar_batch_generate_mixed(e.batch, e.pool, e.cfg.state_entries,
                                    reinterpret_cast<const ranmar_desc_t*>(d + o_du), ntot, nu,
@@ -652,7 +663,8 @@ void wait_until(const ranmar_serve& e, double until) {
 
 int finish_run(ranmar_serve& e, int rc) {
   if (!e.host_only) {
-    const int rs = cuda_check(cudaStreamSynchronize(e.stream));
+    int rs = cuda_check(cudaStreamSynchronize(e.stream));
+    if (!rs) rs = cuda_check(cudaStreamSynchronize(e.jstream));
     if (!rc) rc = rs;
     uint32_t st = 0;
     if (!rc) rc = cuda_check(cudaMemcpy(&st, e.status, 4, cudaMemcpyDeviceToHost));
@@ -745,12 +757,14 @@ void free_device(ranmar_serve* e) {
       if (st.d) cudaFree(st.d);
       if (st.ev) cudaEventDestroy(st.ev);
       if (st.ev_start) cudaEventDestroy(st.ev_start);
+      if (st.ev_jumped) cudaEventDestroy(st.ev_jumped);
     }
   }
   if (!e->host_only) {
     for (cudaEvent_t ev : e->plain_ev)
       if (ev) cudaEventDestroy(ev);
     if (e->t0) cudaEventDestroy(e->t0);
+    if (e->jstream) cudaStreamDestroy(e->jstream);
     cudaFree(e->pool);
     cudaFree(e->out);
     cudaFree(e->base);
@@ -926,9 +940,11 @@ int ranmar_serve_create(const ranmar_serve_config_t* cfg, ranmar_serve_t** out) 
     }
     if (!rc) rc = cuda_check(cudaMemset(e->status, 0, 4));
     if (!rc) rc = cuda_check(cudaEventCreate(&e->t0));
+    if (!rc) rc = cuda_check(cudaStreamCreateWithFlags(&e->jstream, cudaStreamNonBlocking));
     for (Stage& st : e->stages) {
       if (!rc) rc = cuda_check(cudaEventCreate(&st.ev));
       if (!rc) rc = cuda_check(cudaEventCreate(&st.ev_start));
+      if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&st.ev_jumped, cudaEventDisableTiming));
       if (!rc) rc = ensure_stage(*e, st, stage_bytes);
     }
     e->plain_ev.assign(kPlainRing, nullptr);
