@@ -1404,8 +1404,6 @@ def serving(rm, torch, seconds):
            "resumed": st["resumed"], "evicted": st["evicted"], "budget_gb": 40,
            "max_iterations_in_flight": st["max_inflight"],
            "host_us_per_iteration": st["host_ns"] / max(1, st["iterations"]) / 1e3,
-           "gpu_us_per_iteration": st["gpu_ns"] / max(1, st["iterations"]) / 1e3,
-           "gpu_busy_frac": st["gpu_ns"] / 1e9 / max(1e-9, summ["span_s"]),
            "requests_per_iteration": summ["served"] / max(1, st["iterations"])}
     res["latency_note"] = ("p50/p99: the GPU event that ends a request's iteration minus its "
                            "arrival; host_p50/host_p99: when the scheduler loop saw that event "
@@ -1512,7 +1510,6 @@ def run_case(args):
               "p99_ms": None if args.serve_offline else s["p99_ms"],
               "iterations": st["iterations"],
               "host_us_per_iteration": st["host_ns"] / max(1, st["iterations"]) / 1e3,
-              "gpu_us_per_iteration": st["gpu_ns"] / max(1, st["iterations"]) / 1e3,
               "segments": st["segments"]})
         return 0
     table = rm.Table()

@@ -860,8 +860,9 @@ typedef struct ranmar_serve_stats {   /* totals over the engine's runs */
     uint64_t max_loop_ns;    /* longest scheduler loop turn */
     uint64_t max_inflight;   /* most iterations on the device at once */
     uint64_t host_ns;        /* host time spent building + enqueueing */
-    uint64_t gpu_ns;         /* device time of the iterations: from the
-                                start of each one's first copy to its end */
+    uint64_t max_admit_ns;   /* longest admission (incl. evictions) */
+    uint64_t max_enqueue_ns; /* longest build + enqueue of an iteration */
+    uint64_t max_retire_ns;  /* longest retirement (incl. waiting for it) */
     uint64_t resident;       /* resident streams now */
     uint32_t status;         /* RANMAR_ST_* bits the kernels set */
     uint32_t pad;

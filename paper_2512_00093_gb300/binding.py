@@ -62,7 +62,7 @@ class ServeStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "iterations", "segments", "base_jumps", "pool_jumps", "resumed", "evicted", "rejected",
         "outputs", "new_seeds", "slow_loops", "max_loop_ns", "max_inflight", "host_ns",
-        "gpu_ns", "resident")] + [("status", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+        "max_admit_ns", "max_enqueue_ns", "max_retire_ns", "resident")] + [("status", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "pad"}
@@ -82,7 +82,7 @@ SEG_DTYPE = np.dtype([("iteration", "<u4"), ("request", "<u4"), ("kind", "<u4"),
                       ("exp", "<u4", (MAX_EXP_WORDS,)), ("live_until", "<u4"),
                       ("out_offset", "<u8"), ("count", "<u8"), ("index0", "<u8")])
 assert REQUEST_DTYPE.itemsize == 88 and SEG_DTYPE.itemsize == 72
-assert ctypes.sizeof(ServeConfig) == 40 and ctypes.sizeof(ServeStats) == 128
+assert ctypes.sizeof(ServeConfig) == 40 and ctypes.sizeof(ServeStats) == 144
 
 
 _L: ctypes.CDLL | None = None

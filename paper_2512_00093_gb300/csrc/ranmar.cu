@@ -317,12 +317,32 @@ int launch_jump(const ranmar_state_t* base, size_t n_base, const uint32_t* base_
   return check_launch();
 }
 
+// Resident CTAs an SM of a kernel at `threads` threads a CTA on the current
+// device, queried once per (kernel, device, threads) and kept: the query
+// costs about a microsecond of host time, and the serving engine launches a
+// persistent kernel every iteration.
+constexpr int kOccDevices = 64;
+using OccCache = std::atomic<int>[kOccDevices][33];
+
+template <typename K>
+int cached_occupancy(K kernel, OccCache& cache, int threads) {
+  int dev = -1;
+  const bool keep = cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kOccDevices &&
+                    threads >= 32 && threads <= 1024 && threads % 32 == 0;
+  if (keep) {
+    const int v = cache[dev][threads / 32].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0);
+  if (keep && nb > 0) cache[dev][threads / 32].store(nb, std::memory_order_relaxed);
+  return nb;
+}
+
 template <int W, bool F32>
 int persistent_occupancy(int threads) {
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &nb, ranmar::generate_persistent_kernel<W, F32>, threads, 0);
-  return nb;
+  static OccCache cache;
+  return cached_occupancy(ranmar::generate_persistent_kernel<W, F32>, cache, threads);
 }
 
 template <int W, bool F32>
@@ -396,10 +416,8 @@ int run_persistent(ranmar_batch* b, const ranmar_batch_config_t& c, bool f32,
 
 template <int W, int S>
 int mixed_occupancy(int threads) {
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &nb, ranmar::generate_persistent_mixed_kernel<W, S>, threads, 0);
-  return nb;
+  static OccCache cache;
+  return cached_occupancy(ranmar::generate_persistent_mixed_kernel<W, S>, cache, threads);
 }
 
 // Enqueues queue reset + the mixed-type persistent kernel with config c: a

@@ -24,7 +24,6 @@
 #include <cstring>
 #include <deque>
 #include <iterator>
-#include <list>
 #include <map>
 #include <new>
 #include <thread>
@@ -50,13 +49,16 @@ using Clock = std::chrono::steady_clock;
 
 constexpr uint64_t kRegionAlign = 32;          // output regions start on 128-byte lines
 constexpr double kSlowLoopSeconds = 0.01;       // a loop turn longer than this is counted
-constexpr double kSpinSeconds = 1e-4;           // waits shorter than this spin instead of sleeping
+// Waits for an arrival shorter than this spin instead of sleeping: a sleep
+// can overrun by milliseconds on a loaded host, which would delay every
+// request that arrives meanwhile.
+constexpr double kSpinSeconds = 2e-3;
 constexpr size_t kPlainRing = 1024;             // plain-mode requests in flight at most
 
 static_assert(sizeof(ranmar_request_t) == 88, "request layout");
 static_assert(sizeof(ranmar_serve_seg_t) == 72, "trace layout");
 static_assert(sizeof(ranmar_serve_config_t) == 40, "config layout");
-static_assert(sizeof(ranmar_serve_stats_t) == 128, "stats layout");
+static_assert(sizeof(ranmar_serve_stats_t) == 144, "stats layout");
 
 double seconds_since(Clock::time_point t0) {
   return std::chrono::duration<double>(Clock::now() - t0).count();
@@ -174,6 +176,92 @@ struct StreamKeyHash {
 
 StreamKey key_of(const ranmar_request_t& r) { return {r.seed, r.k, r.J[0], r.J[1]}; }
 
+// Resident stream states: which pool entry holds the state of which stream
+// (and where in the stream it stands), with least-recently-used order.
+// Everything is indexed by pool entry -- the key and end of the stream an
+// entry holds, and the LRU links -- plus an open-addressing table from
+// stream key to entry (linear probing, deletion by backward shift).  An
+// eviction is a few array operations, so that taking thousands of entries
+// for a long request costs microseconds, not the milliseconds of node-based
+// containers.
+class ResidentSet {
+ public:
+  void init(uint32_t entries) {
+    key_.assign(entries, StreamKey{});
+    end_.assign(entries, 0);
+    prev_.assign(entries, -1);
+    next_.assign(entries, -1);
+    size_t cap = 16;
+    while (cap < 2 * static_cast<size_t>(entries)) cap <<= 1;
+    slots_.assign(cap, -1);
+    mask_ = cap - 1;
+  }
+  size_t size() const { return count_; }
+  bool empty() const { return count_ == 0; }
+  uint64_t end_of(int32_t entry) const { return end_[entry]; }
+
+  // The entry holding stream `k`, or -1.
+  int32_t find(const StreamKey& k) const {
+    for (size_t i = home(k);; i = (i + 1) & mask_) {
+      const int32_t s = slots_[i];
+      if (s < 0) return -1;
+      if (key_[s] == k) return s;
+    }
+  }
+  // Makes `entry` hold stream k (absent) at `end`, most recently used.
+  void insert(const StreamKey& k, uint32_t entry, uint64_t end) {
+    size_t i = home(k);
+    while (slots_[i] >= 0) i = (i + 1) & mask_;
+    slots_[i] = static_cast<int32_t>(entry);
+    key_[entry] = k;
+    end_[entry] = end;
+    prev_[entry] = tail_;
+    next_[entry] = -1;
+    if (tail_ >= 0)
+      next_[tail_] = static_cast<int32_t>(entry);
+    else
+      head_ = static_cast<int32_t>(entry);
+    tail_ = static_cast<int32_t>(entry);
+    ++count_;
+  }
+  // Removes resident `entry` (from the table and the LRU order).
+  void erase(int32_t entry) {
+    size_t i = home(key_[entry]);
+    while (slots_[i] != entry) i = (i + 1) & mask_;
+    for (size_t j = i;;) {   // backward shift over the rest of the probe run
+      j = (j + 1) & mask_;
+      const int32_t s = slots_[j];
+      if (s < 0) break;
+      const size_t h = home(key_[s]);
+      const bool stays = i <= j ? (i < h && h <= j) : (i < h || h <= j);
+      if (!stays) {
+        slots_[i] = s;
+        i = j;
+      }
+    }
+    slots_[i] = -1;
+    const int32_t p = prev_[entry], n = next_[entry];
+    if (p >= 0) next_[p] = n; else head_ = n;
+    if (n >= 0) prev_[n] = p; else tail_ = p;
+    --count_;
+  }
+  // Removes and returns the least recently used entry (-1 when empty).
+  int32_t pop_lru() {
+    const int32_t e = head_;
+    if (e >= 0) erase(e);
+    return e;
+  }
+
+ private:
+  size_t home(const StreamKey& k) const { return StreamKeyHash{}(k) & mask_; }
+  std::vector<StreamKey> key_;
+  std::vector<uint64_t> end_;
+  std::vector<int32_t> prev_, next_;
+  std::vector<int32_t> slots_;
+  size_t mask_ = 0, count_ = 0;
+  int32_t head_ = -1, tail_ = -1;
+};
+
 // One admitted request of an iteration.
 struct Admitted {
   uint32_t req;       // index into the run's request array
@@ -197,7 +285,6 @@ struct Stage {
   unsigned char* d = nullptr;
   size_t cap = 0;
   cudaEvent_t ev = nullptr;        // end of the iteration's device work
-  cudaEvent_t ev_start = nullptr;  // before its first copy
   cudaEvent_t ev_jumped = nullptr; // its start states are written
   bool busy = false;      // enqueued and not yet retired
 };
@@ -236,13 +323,7 @@ struct ranmar_serve {
   // host scheduler state
   FirstFit alloc{0};
   std::vector<uint32_t> free_entries;
-  struct Resident {
-    uint32_t entry;
-    uint64_t end;
-    std::list<StreamKey>::iterator lru;
-  };
-  std::unordered_map<StreamKey, Resident, StreamKeyHash> resident;
-  std::list<StreamKey> lru;            // front: least recently used
+  ResidentSet resident;
   std::unordered_map<int32_t, uint32_t> seed_row;
   uint32_t iter_count = 0;
   ranmar_serve_stats_t stats{};
@@ -274,22 +355,14 @@ bool fits_ever(const ranmar_serve& e, const ranmar_request_t& r) {
 // Takes n free states, evicting least recently used resident states; false
 // (nothing taken) when even all of them do not make n.
 bool take_entries(ranmar_serve& e, uint32_t n, std::vector<uint32_t>& dst) {
-  while (e.free_entries.size() < n && !e.lru.empty()) {
-    auto it = e.resident.find(e.lru.front());
-    e.free_entries.push_back(it->second.entry);
-    e.resident.erase(it);
-    e.lru.pop_front();
+  while (e.free_entries.size() < n && !e.resident.empty()) {
+    e.free_entries.push_back(static_cast<uint32_t>(e.resident.pop_lru()));
     e.stats.evicted++;
   }
   if (e.free_entries.size() < n) return false;
   dst.insert(dst.end(), e.free_entries.end() - n, e.free_entries.end());
   e.free_entries.resize(e.free_entries.size() - n);
   return true;
-}
-
-void make_resident(ranmar_serve& e, const StreamKey& key, uint32_t entry, uint64_t end) {
-  e.lru.push_back(key);
-  e.resident[key] = {entry, end, std::prev(e.lru.end())};
 }
 
 // Admission: requests leave the queue head in arrival order while their
@@ -308,21 +381,20 @@ void admit(ranmar_serve& e, std::deque<uint32_t>& waiting, Iter& it) {
     const uint32_t ns = nseg_of(e, r.count);
     if (!it.reqs.empty() && nsegs + ns > e.cfg.max_segments) break;
     const StreamKey key = key_of(r);
-    auto res = e.resident.find(key);
-    const bool resume = res != e.resident.end() && res->second.end == r.offset;
+    const int32_t res = e.resident.find(key);
+    const bool resume = res >= 0 && e.resident.end_of(res) == r.offset;
     uint64_t region = 0;
     if (!e.alloc.alloc(std::max<uint64_t>(1, r.count), &region)) break;
     const uint32_t first = static_cast<uint32_t>(it.ents.size());
     if (resume) {
       // out of the resident map first, so that eviction cannot pick it
-      it.ents.push_back(res->second.entry);
-      e.lru.erase(res->second.lru);
+      it.ents.push_back(static_cast<uint32_t>(res));
       e.resident.erase(res);
     }
     if (!take_entries(e, resume ? ns - 1 : ns, it.ents)) {
       e.alloc.release(region, std::max<uint64_t>(1, r.count));
       if (resume) {
-        make_resident(e, key, it.ents.back(), r.offset);
+        e.resident.insert(key, it.ents.back(), r.offset);
         it.ents.pop_back();
       }
       break;
@@ -528,8 +600,6 @@ int enqueue(ranmar_serve& e, Iter& it) {
   cudaStream_t s = e.stream, js = e.jstream;
   ranmar_stream_t rs = reinterpret_cast<ranmar_stream_t>(s);
   unsigned char* d = st.d;
-  rc = cuda_check(cudaEventRecord(st.ev_start, js));
-  if (rc) return rc;
   rc = cuda_check(cudaMemcpyAsync(d, h, off, cudaMemcpyHostToDevice, js));
   if (rc) return rc;
   if (m) {
@@ -564,7 +634,9 @@ int enqueue(ranmar_serve& e, Iter& it) {
                                   cudaMemcpyDeviceToHost, s));
   if (rc) return rc;
   rc = cuda_check(cudaEventRecord(st.ev, s));
-  e.stats.host_ns += static_cast<uint64_t>(seconds_since(tb) * 1e9);
+  const uint64_t ns = static_cast<uint64_t>(seconds_since(tb) * 1e9);
+  e.stats.host_ns += ns;
+  e.stats.max_enqueue_ns = std::max(e.stats.max_enqueue_ns, ns);
   return rc;
 }
 
@@ -592,12 +664,10 @@ int retire(ranmar_serve& e, const Iter& it) {
   if (!e.host_only) {
     int rc = cuda_check(cudaEventSynchronize(st.ev));
     if (rc) return rc;
-    float ms = 0.f, busy_ms = 0.f;
+    float ms = 0.f;
     rc = cuda_check(cudaEventElapsedTime(&ms, e.t0, st.ev));
-    if (!rc) rc = cuda_check(cudaEventElapsedTime(&busy_ms, st.ev_start, st.ev));
     if (rc) return rc;
     done = ms * 1e-3;
-    e.stats.gpu_ns += static_cast<uint64_t>(busy_ms * 1e6);
   } else {
     e.trace_live_until[it.number] = e.iter_count;
   }
@@ -617,14 +687,13 @@ int retire(ranmar_serve& e, const Iter& it) {
     const uint32_t last = ents[a.nseg - 1];
     const uint64_t end = r.offset + r.count;
     const StreamKey key = key_of(r);
-    auto cur = e.resident.find(key);
-    if (cur == e.resident.end()) {
-      make_resident(e, key, last, end);
-    } else if (cur->second.end < end) {
-      e.free_entries.push_back(cur->second.entry);
-      e.lru.erase(cur->second.lru);
+    const int32_t cur = e.resident.find(key);
+    if (cur < 0) {
+      e.resident.insert(key, last, end);
+    } else if (e.resident.end_of(cur) < end) {
+      e.free_entries.push_back(static_cast<uint32_t>(cur));
       e.resident.erase(cur);
-      make_resident(e, key, last, end);
+      e.resident.insert(key, last, end);
     } else {
       e.free_entries.push_back(last);
     }
@@ -649,16 +718,28 @@ void arrive(ranmar_serve& e, uint32_t i, std::deque<uint32_t>& waiting) {
   waiting.push_back(i);
 }
 
-// Busy-waits (short waits) or sleeps until `until` seconds after h0.
-void wait_until(const ranmar_serve& e, double until) {
+// While the loop is idle: evicts a few least recently used resident states
+// until a reserve of free states exists, so that a long request seldom has
+// to evict thousands at once when it is admitted.
+void trim(ranmar_serve& e, int budget) {
+  const size_t reserve = std::min<size_t>(e.cfg.max_segments, e.cfg.state_entries / 8);
+  while (budget-- > 0 && e.free_entries.size() < reserve && !e.resident.empty()) {
+    e.free_entries.push_back(static_cast<uint32_t>(e.resident.pop_lru()));
+    e.stats.evicted++;
+  }
+}
+
+// Busy-waits (short waits) or sleeps until `until` seconds after h0,
+// trimming the resident states meanwhile.
+void wait_until(ranmar_serve& e, double until) {
+  trim(e, 64);
   double left = until - seconds_since(e.h0);
   if (left <= 0) return;
   if (left > kSpinSeconds) {
-    std::this_thread::sleep_for(std::chrono::duration<double>(std::min(left - kSpinSeconds, 2e-4)));
+    std::this_thread::sleep_for(std::chrono::duration<double>(std::min(left - kSpinSeconds, 1e-3)));
     return;
   }
-  while (seconds_since(e.h0) < until) {
-  }
+  while (seconds_since(e.h0) < until) trim(e, 8);
 }
 
 int finish_run(ranmar_serve& e, int rc) {
@@ -695,7 +776,10 @@ int run_loop(ranmar_serve& e, size_t n, bool realtime, double max_wait) {
     bool admitted = false;
     if (inflight.size() < e.cfg.max_inflight && !waiting.empty()) {
       Iter it;
+      const Clock::time_point ta = Clock::now();
       admit(e, waiting, it);
+      e.stats.max_admit_ns = std::max<uint64_t>(
+          e.stats.max_admit_ns, static_cast<uint64_t>(seconds_since(ta) * 1e9));
       if (!it.reqs.empty()) {
         const int rc = enqueue(e, it);
         if (rc) return rc;
@@ -707,8 +791,11 @@ int run_loop(ranmar_serve& e, size_t n, bool realtime, double max_wait) {
     bool progressed = admitted;
     while (!inflight.empty() && (iteration_done(e, inflight.front()) ||
                                  (!admitted && (!waiting.empty() || i >= n)))) {
+      const Clock::time_point tr = Clock::now();
       const int rc = retire(e, inflight.front());
       if (rc) return rc;
+      e.stats.max_retire_ns = std::max<uint64_t>(
+          e.stats.max_retire_ns, static_cast<uint64_t>(seconds_since(tr) * 1e9));
       inflight.pop_front();
       progressed = true;
       if (!inflight.empty() && !iteration_done(e, inflight.front())) break;
@@ -719,8 +806,8 @@ int run_loop(ranmar_serve& e, size_t n, bool realtime, double max_wait) {
       if (inflight.empty() || e.host_only) {
         wait_until(e, e.reqs[i].t);
       } else {
-        while (seconds_since(e.h0) < e.reqs[i].t && !iteration_done(e, inflight.front())) {
-        }
+        while (seconds_since(e.h0) < e.reqs[i].t && !iteration_done(e, inflight.front()))
+          trim(e, 8);
       }
     }
   }
@@ -756,7 +843,6 @@ void free_device(ranmar_serve* e) {
       if (st.h) cudaFreeHost(st.h);
       if (st.d) cudaFree(st.d);
       if (st.ev) cudaEventDestroy(st.ev);
-      if (st.ev_start) cudaEventDestroy(st.ev_start);
       if (st.ev_jumped) cudaEventDestroy(st.ev_jumped);
     }
   }
@@ -913,6 +999,10 @@ int ranmar_serve_create(const ranmar_serve_config_t* cfg, ranmar_serve_t** out) 
   e->host_only = (c.flags & RANMAR_SERVE_HOST_ONLY) != 0;
   e->out_words = (c.budget_bytes - state_bytes) / 4;
   e->alloc = FirstFit(e->out_words);
+  // full-size tables up front: a rehash of 2^18 resident streams in the
+  // middle of a run is a stall of milliseconds
+  e->resident.init(c.state_entries);
+  e->seed_row.reserve(c.max_seeds);
   e->free_entries.resize(c.state_entries);
   for (uint32_t q = 0; q < c.state_entries; ++q) e->free_entries[q] = c.state_entries - 1 - q;
   e->stages.resize(c.max_inflight + 1);
@@ -943,7 +1033,6 @@ int ranmar_serve_create(const ranmar_serve_config_t* cfg, ranmar_serve_t** out) 
     if (!rc) rc = cuda_check(cudaStreamCreateWithFlags(&e->jstream, cudaStreamNonBlocking));
     for (Stage& st : e->stages) {
       if (!rc) rc = cuda_check(cudaEventCreate(&st.ev));
-      if (!rc) rc = cuda_check(cudaEventCreate(&st.ev_start));
       if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&st.ev_jumped, cudaEventDisableTiming));
       if (!rc) rc = ensure_stage(*e, st, stage_bytes);
     }

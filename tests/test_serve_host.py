@@ -2,6 +2,8 @@
 recipe, and the native scheduler run with RANMAR_SERVE_HOST_ONLY, whose
 recorded plan (jumps, segments, write-backs, regions) is executed here with
 the oracle and must give every request exactly its stream's outputs."""
+import collections
+
 import numpy as np
 import pytest
 
@@ -282,3 +284,167 @@ def test_host_preload_fills_the_seed_table(bd):
         eng.preload_seeds([9])
     assert ei.value.code == bd.ERANGE
     eng.close()
+
+
+class SchedulerModel:
+    """The scheduler's rules written out in Python for a host-only engine
+    run with every request available at once (no timing involved): FIFO
+    admission while the iteration's segments, a first-fit output region and
+    the state entries allow (least recently used resident states evicted
+    first), resume when the stream's resident state stands at the request's
+    offset, iterations retired oldest first when the loop must wait, the
+    last state of each request kept resident.  Produces the plan the native
+    engine must record."""
+
+    def __init__(self, out_words, entries, seg, max_segs, max_inflight, max_seeds):
+        self.free_blocks = {0: out_words}          # start -> length
+        self.out_words, self.entries, self.seg = out_words, entries, seg
+        self.max_segs, self.max_inflight, self.max_seeds = max_segs, max_inflight, max_seeds
+        self.free = list(range(entries - 1, -1, -1))
+        self.resident = collections.OrderedDict()  # key -> (entry, end), LRU first
+        self.seed_row = {}
+        self.evicted = self.resumed = 0
+
+    @staticmethod
+    def rounded(n):
+        return (max(n, 1) + 31) // 32 * 32
+
+    def alloc(self, n):
+        n = self.rounded(n)
+        for st in sorted(self.free_blocks):
+            ln = self.free_blocks[st]
+            if ln >= n:
+                del self.free_blocks[st]
+                if ln > n:
+                    self.free_blocks[st + n] = ln - n
+                return st
+        return None
+
+    def release(self, st, n):
+        n = self.rounded(n)
+        self.free_blocks[st] = n
+        nxt = st + n
+        if nxt in self.free_blocks:
+            self.free_blocks[st] += self.free_blocks.pop(nxt)
+        prev = [s for s in self.free_blocks if s < st]
+        if prev and max(prev) + self.free_blocks[max(prev)] == st:
+            p = max(prev)
+            self.free_blocks[p] += self.free_blocks.pop(st)
+
+    def nseg(self, count):
+        return max(1, -(-count // self.seg))
+
+    def take(self, n):
+        while len(self.free) < n and self.resident:
+            _, (e, _) = self.resident.popitem(last=False)
+            self.free.append(e)
+            self.evicted += 1
+        if len(self.free) < n:
+            return None
+        got = self.free[len(self.free) - n:]
+        del self.free[len(self.free) - n:]
+        return got
+
+    def run(self, reqs):
+        waiting = collections.deque(range(len(reqs)))
+        inflight, plan, live, n_iter = collections.deque(), [], {}, 0
+        while waiting or inflight:
+            it, nsegs = [], 0
+            if len(inflight) < self.max_inflight:
+                while waiting:
+                    r = reqs[waiting[0]]
+                    ns = self.nseg(r.count)
+                    if self.rounded(r.count) > self.out_words or ns > self.entries:
+                        waiting.popleft()
+                        continue
+                    if it and nsegs + ns > self.max_segs:
+                        break
+                    res = self.resident.get(r.key)
+                    resume = res is not None and res[1] == r.offset
+                    region = self.alloc(r.count)
+                    if region is None:
+                        break
+                    ents = []
+                    if resume:
+                        ents.append(self.resident.pop(r.key)[0])
+                    got = self.take(ns - 1 if resume else ns)
+                    if got is None:
+                        self.release(region, r.count)
+                        if resume:
+                            self.resident[r.key] = (ents[0], r.offset)
+                        break
+                    self.resumed += resume
+                    it.append((waiting.popleft(), region, ents + got, resume))
+                    nsegs += ns
+            if it:
+                for q, _, _, _ in it:
+                    if reqs[q].seed not in self.seed_row:
+                        self.seed_row[reqs[q].seed] = len(self.seed_row)
+                for q, region, ents, resume in it:
+                    r = reqs[q]
+                    for j, ent in enumerate(ents):
+                        js = j * self.seg
+                        if not resume:
+                            kind, src, e = 0, self.seed_row[r.seed], r.k * r.J + r.offset + js
+                        elif j:
+                            kind, src, e = 1, ents[0], js
+                        else:
+                            kind, src, e = 2, ent, 0
+                        plan.append((n_iter, q, kind, ent, src, int(j == len(ents) - 1), e,
+                                     region + js, max(0, min(self.seg, r.count - js)), js))
+                inflight.append((n_iter, it))
+                n_iter += 1
+                continue
+            num, old = inflight.popleft()
+            live[num] = n_iter
+            for q, region, ents, _ in old:
+                r = reqs[q]
+                self.release(region, r.count)
+                self.free.extend(ents[:-1])
+                cur = self.resident.get(r.key)
+                end = r.offset + r.count
+                if cur is None:
+                    self.resident[r.key] = (ents[-1], end)
+                elif cur[1] < end:
+                    self.free.append(cur[0])
+                    del self.resident[r.key]
+                    self.resident[r.key] = (ents[-1], end)
+                else:
+                    self.free.append(ents[-1])
+        return plan, live
+
+
+@pytest.mark.parametrize("entries,max_inflight,max_segs", [(40, 3, 24), (12, 2, 24),
+                                                           (300, 4, 7), (64, 1, 100)])
+def test_native_scheduler_follows_the_model(bd, entries, max_inflight, max_segs):
+    """The native scheduler's plan (iterations, entries, eviction and resume
+    choices, regions, exponents) equals the Python model's, record for
+    record, on request mixes with many repeats of few streams."""
+    rng = np.random.default_rng(entries + max_segs)
+    n = 400
+    t = np.sort(rng.random(n))
+    sd, k = rng.integers(1, 4, n), rng.integers(0, 7, n)
+    c = np.minimum(10 * 16, np.floor(10.0 ** (2.3 * rng.random(n)))).astype(np.int64)
+    c[:5] = [0, 1, 16, 17, 160]
+    J = (1 << 64) + 5
+    reqs = serve.make_requests(t, sd, k, c, np.zeros(n, bool), J)
+    out_words = 3000
+    eng = host_engine(budget_bytes=entries * 400 + out_words * 4, state_entries=entries,
+                      max_inflight=max_inflight, max_segments_per_iter=max_segs)
+    eng.run(reqs, realtime=False)
+    tr = eng.trace()
+    st = eng.stats
+    eng.close()
+    model = SchedulerModel(out_words, entries, 16, max_segs, max_inflight, 64)
+    plan, live = model.run(reqs)
+    got = [(int(x["iteration"]), int(x["request"]), int(x["kind"]), int(x["entry"]),
+            int(x["src"]), int(x["flags"]), exponent(x) if x["kind"] != 2 else 0,
+            int(x["out_offset"]), int(x["count"]), int(x["index0"])) for x in tr]
+    assert len(got) == len(plan)
+    for a, b in zip(got, plan):
+        assert a == b, (a, b)
+    assert [int(x["live_until"]) for x in tr] == [live[p[0]] for p in plan]
+    assert (st["evicted"], st["resumed"]) == (model.evicted, model.resumed)
+    assert st["resumed"] > 0
+    if entries <= 64:
+        assert st["evicted"] > 0
