@@ -1405,6 +1405,22 @@ def serving(rm, torch, seconds):
            "max_iterations_in_flight": st["max_inflight"],
            "host_us_per_iteration": st["host_ns"] / max(1, st["iterations"]) / 1e3,
            "requests_per_iteration": summ["served"] / max(1, st["iterations"])}
+    # Capacity: the first 10 s of the same list (~2·10^5 requests) all
+    # available at once, served as fast as the engine can: the highest
+    # request rate it could sustain, against the recipe's 20k req/s.
+    ncap = int(np.searchsorted(t, min(10.0, seconds)))
+    cap = requests_array(t[:ncap], seeds[:ncap], ks[:ncap], counts[:ncap], f32[:ncap], w.J)
+    it0 = eng.stats["iterations"]
+    eng.run(cap, realtime=False, max_wait=600)
+    span = float(cap["done"].max())
+    outs = int(cap["count"].sum())
+    res["capacity"] = {
+        "requests": ncap, "outputs": outs, "seconds": span,
+        "req_per_s": ncap / span, "outputs_per_s": outs / span,
+        "iterations": eng.stats["iterations"] - it0,
+        "checksums_equal": f"{int((cap['checksum'] == reqs['checksum'][:ncap]).sum())}/{ncap}",
+        "note": "the first 10 s of requests, all available at once (no arrival times), "
+                "start to last completion on the GPU clock"}
     res["latency_note"] = ("p50/p99: the GPU event that ends a request's iteration minus its "
                            "arrival; host_p50/host_p99: when the scheduler loop saw that event "
                            "complete, minus arrival; host_us_per_iteration: the native "
