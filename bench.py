@@ -454,6 +454,31 @@ def config4(rm, torch, dev, stream, alu_peak, alu_derived, steps=5) -> dict:
         "jump_ms": ms, "jumps_per_s": n / (ms * 1e-3),
         "note": "the paper's square-and-multiply on E mod (2^97 - 1) 2^23 (the order of t), "
                 "c by E mod m: identical states, about 10 fewer squarings"}
+    # Two consecutive steps in flight, on two streams with their own states
+    # and outputs: one step's 2,048 jump warps load the 608 warp schedulers
+    # unevenly (3 or 4 each, the 4s set the time); two launches side by
+    # side fill them.  Same work per step; each step's own latency grows.
+    s2 = [stream, torch.cuda.Stream(dev)]
+    st2 = [st, torch.empty_like(st)]
+    out2 = [out, torch.empty_like(out)]
+    K = 2 * steps
+    torch.cuda.synchronize()
+    a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a2.record(stream)
+    s2[1].wait_event(a2)
+    for i in range(K):
+        q = i % 2
+        with torch.cuda.stream(s2[q]):
+            rm.partition(base, lj.J, (steps + 20 + i) * n, n, out=st2[q])
+            rm.generate_u24(st2[q], desc, out2[q])
+    stream.wait_stream(s2[1])
+    b2.record(stream)
+    torch.cuda.synchronize()
+    ms2 = a2.elapsed_time(b2) / K
+    var["two_steps_in_flight"] = {
+        "step_ms": ms2, "step_jumps_per_s": n / (ms2 * 1e-3),
+        "note": f"{K} steps alternating over two streams (square-and-multiply jump + 1,024 "
+                "outputs each, as the timed step): throughput with two steps overlapped"}
     res["variants"] = var
     chk.close()
     return res
