@@ -38,13 +38,6 @@ constexpr size_t kWarpJumpSmemBytes = sizeof(uint32_t) * kWjWords * kWarpJumpWar
 static_assert(kWjB0 + 192 <= kWjC && kWjC + 196 <= kWjWords, "slice");
 static_assert(kWjWords % 4 == 0 && kWjB0 % 4 == 0 && kWjC % 4 == 0, "16-byte rows");
 
-// Copies one 100-word table row (25 x 16 bytes) into shared memory.
-__device__ __forceinline__ void copy_row_warp(uint32_t* __restrict__ dst,
-                                              const uint32_t* __restrict__ src, unsigned lane) {
-  if (lane < kTabRowWords / 4)
-    reinterpret_cast<uint4*>(dst)[lane] = __ldg(reinterpret_cast<const uint4*>(src) + lane);
-}
-
 // a = a b mod phi; b sits at bz + 96 with zeros at bz[0..95] and
 // bz[193..287] (a table row's words 97..99 are zero); c is scratch.
 // Lane l forms c_n for n = 6l .. 6l+5 with a sliding window: at step i its
@@ -101,31 +94,53 @@ __device__ __forceinline__ void poly_mulmod_warp(uint32_t* __restrict__ a,
   __syncwarp();
 }
 
+// The first window at or after j whose base-256 digit of D is nonzero
+// (nwin when there is none).
+__device__ __forceinline__ int next_digit(const uint32_t (&D)[kMaxExpWords], int j, int nwin) {
+  while (j < nwin && exp_digit(D, j) == 0) ++j;
+  return j;
+}
+
+// This lane's 16-byte part of table row (j, d_j) (lanes 0..24 of a row of
+// 100 words), held in registers until it is stored.
+__device__ __forceinline__ uint4 row_part(const uint32_t* __restrict__ table,
+                                          const uint32_t (&D)[kMaxExpWords], int j,
+                                          unsigned lane) {
+  const uint32_t* row =
+      table + static_cast<size_t>(j * kTabDigits + exp_digit(D, j)) * kTabRowWords;
+  return lane < kTabRowWords / 4 ? __ldg(reinterpret_cast<const uint4*>(row) + lane)
+                                 : make_uint4(0u, 0u, 0u, 0u);
+}
+
 // a = prod over the nonzero base-256 digits d_j of D of table row (j, d_j)
 // (the fixed-base table, or a table of the powers of t^J); a = 1 for D = 0.
-// D is the same in every lane.
+// D is the same in every lane.  The row of the next product is loaded into
+// registers before the current product starts, so that its latency is
+// spent under the product's multiply-adds instead of before them.
 __device__ __forceinline__ void table_poly_warp(const uint32_t* __restrict__ table,
                                                 const uint32_t (&D)[kMaxExpWords],
                                                 uint32_t* __restrict__ s, unsigned lane) {
   uint32_t* a = s + kWjA;
-  for (int q = static_cast<int>(lane); q < kR; q += 32) a[q] = q == 0 ? 1u : 0u;
-  __syncwarp();
   const int nwin = (exp_bitlen(D) + kTabWindowBits - 1) / kTabWindowBits;
-  bool have = false;
+  int j = next_digit(D, 0, nwin);
+  if (j >= nwin) {
+    for (int q = static_cast<int>(lane); q < kR; q += 32) a[q] = q == 0 ? 1u : 0u;
+    __syncwarp();
+    return;
+  }
+  uint4 v = row_part(table, D, j, lane);
+  if (lane < kTabRowWords / 4) reinterpret_cast<uint4*>(a)[lane] = v;
+  j = next_digit(D, j + 1, nwin);
+  if (j < nwin) v = row_part(table, D, j, lane);
+  __syncwarp();
 #pragma unroll 1
-  for (int j = 0; j < nwin; ++j) {
-    const uint32_t d = exp_digit(D, j);
-    if (d == 0) continue;
-    const uint32_t* row = table + static_cast<size_t>(j * kTabDigits + d) * kTabRowWords;
-    if (!have) {
-      copy_row_warp(a, row, lane);
-      __syncwarp();
-    } else {
-      copy_row_warp(s + kWjB0, row, lane);
-      __syncwarp();
-      poly_mulmod_warp(a, s + kWjBz, s + kWjC, lane);
-    }
-    have = true;
+  while (j < nwin) {
+    if (lane < kTabRowWords / 4) reinterpret_cast<uint4*>(s + kWjB0)[lane] = v;
+    __syncwarp();
+    const int jn = next_digit(D, j + 1, nwin);
+    if (jn < nwin) v = row_part(table, D, jn, lane);   // in flight during the product
+    poly_mulmod_warp(a, s + kWjBz, s + kWjC, lane);
+    j = jn;
   }
 }
 
