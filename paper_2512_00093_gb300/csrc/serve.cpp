@@ -6,19 +6,25 @@
 // state (Sec. 1), resumed at `offset`.  Every scheduler iteration takes the
 // requests that arrived, in order, while the output pool and the state pool
 // allow; cuts each into segments of at most `seg` outputs (one state each,
-// so a long request runs on many warps); and enqueues on one CUDA stream,
-// after ONE host-to-device copy of a packed staging buffer:
-//   * the jumps of the segment start states (Sec. 3.1 / 3.2) -- from the
-//     seed's seeded state by k J + offset + j seg, or, when the stream's
-//     state is still resident at `offset`, from that state by j seg;
-//   * one persistent batched generation of all segments, both output
-//     types (Algorithm 2);
-//   * the device checksums of the outputs (how they are consumed before
-//     their memory is recycled) and their copy back to pinned host memory.
+// so a long request runs on many warps); and enqueues
+//   * on the engine's own stream: ONE host-to-device copy of a packed
+//     staging buffer (descriptors, checksum items, jump exponents and
+//     indices, new seeds, the iteration's zeroed checksum slots), the
+//     seeding of new seeds, and the jumps of the segment start states
+//     (Sec. 3.1 / 3.2) -- from the seed's seeded state by k J + offset +
+//     j seg, or, when the stream's state is still resident at `offset`,
+//     from that state by j seg;
+//   * then, on the caller's stream: one persistent generation of all
+//     segments, both output types (Algorithm 2); the device checksums of
+//     the outputs (how they are consumed before their memory is recycled)
+//     and their copy back to the pinned staging buffer.
 // Up to max_inflight iterations are on the device while the host builds
-// the next; an iteration is retired (regions and states freed, the last
-// state of each request kept resident, least recently used evicted first)
-// once its event has completed.
+// the next, and an iteration's jumps run while earlier ones generate; an
+// iteration is retired (regions and states freed, the last state of each
+// request kept resident, least recently used evicted first) once its event
+// has completed.  Host-side structures are flat (first-fit free map,
+// entry-indexed resident set with an open-addressing key table), so that
+// one iteration costs the host ~13 us and no admission stalls on evictions.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
