@@ -114,6 +114,20 @@ def test_host_argument_checks(lib):
     assert L.ranmar_check_overlap(None, 0, None, 0, None, d, 1, None, None) == 0     # n = 0
     assert L.ranmar_check_overlap(fake, 1, fake, 1, fake, d, 1, None, None) == -1    # status
     assert L.ranmar_check_overlap(fake, 0, fake, 1, fake, d, 1, fake, None) == -2    # n_states
+    L.ranmar_batch_generate_mixed.argtypes = [vp, vp, ctypes.c_size_t, vp, ctypes.c_size_t,
+                                              ctypes.c_size_t, vp, ctypes.c_size_t, vp, vp]
+    assert L.ranmar_batch_generate_mixed(None, fake, 1, fake, 1, 0, fake, 10, None,
+                                         None) == -1                                   # handle
+    L.ranmar_serve_create.argtypes = [vp, vp]
+    L.ranmar_serve_run.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_double, vp]
+    L.ranmar_serve_get_stats.argtypes = [vp, vp]
+    L.ranmar_serve_trace.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.ranmar_serve_destroy.argtypes = [vp]
+    assert L.ranmar_serve_create(None, None) == -1
+    assert L.ranmar_serve_run(None, None, 0, 0, 1.0, None) == -1
+    assert L.ranmar_serve_get_stats(None, fake) == -1
+    assert L.ranmar_serve_trace(None, None, 0, fake) == -1
+    assert L.ranmar_serve_destroy(None) == 0
 
 
 def test_workload_recipes():
