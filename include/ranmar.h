@@ -97,6 +97,16 @@ typedef struct ranmar_desc {
     uint64_t count;
 } ranmar_desc_t;
 
+/* One checksum work item: words data[offset .. offset+count), whose first
+ * word has index index0 within its request; added into results[result]. */
+typedef struct ranmar_sum_item {
+    uint64_t offset;
+    uint64_t count;
+    uint64_t index0;
+    uint32_t result;
+    uint32_t pad;
+} ranmar_sum_item_t;   /* 32 bytes */
+
 typedef struct CUstream_st *ranmar_stream_t;   /* == cudaStream_t */
 
 /*
@@ -631,13 +641,22 @@ int ranmar_batch_generate_f32(ranmar_batch_t *b, ranmar_state_t *d_states, size_
  * ranmar_batch_generate_u24) and whose others, d_desc[n_u24 .. n_desc),
  * produce float32 outputs (as ranmar_batch_generate_f32, their bit patterns
  * in the same word array d_out), in index order.  The outputs and write-backs
- * equal those of the two separate calls.  The handle's config applies, with
- * at most 256 threads a CTA (d_order is not taken).  Errors as
- * ranmar_batch_generate_u24, plus RANMAR_ERANGE for n_u24 > n_desc. */
+ * equal those of the two separate calls.  With d_items (device, n_desc
+ * items, or NULL for none) the launch also adds the ranmar_checksum of each
+ * descriptor's outputs, read back from d_out after they are stored, into
+ * d_results[d_items[t].result] (device, n_results words, zeroed by the
+ * caller), with word i of descriptor t weighted by 2 (d_items[t].index0 + i)
+ * + 1; the items' offset and count are not read (the descriptor's are
+ * used).  The handle's config applies, with at most 256 threads a CTA
+ * (d_order is not taken).  Errors as ranmar_batch_generate_u24, plus
+ * RANMAR_ERANGE for n_u24 > n_desc and RANMAR_EINVAL for d_items without
+ * d_results.  Device: RANMAR_ST_OUT_RANGE for an item's result >= n_results
+ * (its sum is skipped). */
 int ranmar_batch_generate_mixed(ranmar_batch_t *b, ranmar_state_t *d_states, size_t n_states,
                                 const ranmar_desc_t *d_desc, size_t n_desc, size_t n_u24,
-                                uint32_t *d_out, size_t out_len, uint32_t *d_status,
-                                ranmar_stream_t stream);
+                                uint32_t *d_out, size_t out_len,
+                                const ranmar_sum_item_t *d_items, uint64_t *d_results,
+                                size_t n_results, uint32_t *d_status, ranmar_stream_t stream);
 
 /* ranmar_batch_tune -- autotuner: times every candidate config (group
  * width 32/16/8, 128/256/512 threads, chunk 1/8, all resident CTAs) on this
@@ -752,15 +771,7 @@ int ranmar_graph_destroy(ranmar_graph_t *g);
  * Output checksums (serving: outputs are consumed on the device).
  * ------------------------------------------------------------------------ */
 
-/* One checksum work item: words data[offset .. offset+count), whose first
- * word has index index0 within its request; added into results[result]. */
-typedef struct ranmar_sum_item {
-    uint64_t offset;
-    uint64_t count;
-    uint64_t index0;
-    uint32_t result;
-    uint32_t pad;
-} ranmar_sum_item_t;   /* 32 bytes */
+/* (ranmar_sum_item_t: see the descriptor types above.) */
 
 /*
  * ranmar_checksum -- for each item: results[item.result] += sum_i

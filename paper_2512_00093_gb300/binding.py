@@ -176,7 +176,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
                "ranmar_serve_run", "ranmar_serve_run_plain", "ranmar_serve_get_stats",
                "ranmar_serve_trace"):
         getattr(lib, nm).restype = ctypes.c_int
-    lib.ranmar_batch_generate_mixed.argtypes = [_vp, _vp, _sz, _vp, _sz, _sz, _vp, _sz, _vp, _vp]
+    lib.ranmar_batch_generate_mixed.argtypes = [_vp, _vp, _sz, _vp, _sz, _sz, _vp, _sz, _vp, _vp,
+                                                _sz, _vp, _vp]
     lib.ranmar_batch_generate_mixed.restype = ctypes.c_int
     lib.ranmar_graph_begin.argtypes = [_vp]
     lib.ranmar_graph_end.argtypes = [_vp, ctypes.POINTER(_vp)]
@@ -650,18 +651,28 @@ class Batch:
         return self._gen("ranmar_batch_generate_f32", torch.float32, states, desc, out, order,
                          status, stream)
 
-    def generate_mixed(self, states, desc, n_u24: int, out, status=None, stream=None):
+    def generate_mixed(self, states, desc, n_u24: int, out, items=None, results=None,
+                       status=None, stream=None):
         """ranmar_batch_generate_mixed: desc[:n_u24] give 24-bit words, the rest
-        float32 bit patterns, all into the int32 word tensor `out`, one launch."""
+        float32 bit patterns, all into the int32 word tensor `out`, one launch;
+        with items ((n, 4) int64, one per descriptor: offset, count, index0,
+        result) each descriptor's checksum is added into results[result]."""
         states = states.reshape(-1, STATE_WORDS)
         _need(states, torch.int32, "states")
         _need(desc, torch.int64, "desc")
         _need(out, torch.int32, "out")
+        if items is not None:
+            _need(items, torch.int64, "items")
+            _need_len(items, desc.shape[0], "items", 4)
+            if results is None:
+                raise ValueError("items given without results")
+            _need(results, torch.int64, "results")
         _need_status(status)
-        _check(_lib().ranmar_batch_generate_mixed(self._h, _ptr(states), states.shape[0],
-                                                  _ptr(desc), desc.shape[0], int(n_u24),
-                                                  _ptr(out), out.numel(), _ptr(status),
-                                                  _stream(stream)), "ranmar_batch_generate_mixed")
+        _check(_lib().ranmar_batch_generate_mixed(
+            self._h, _ptr(states), states.shape[0], _ptr(desc), desc.shape[0], int(n_u24),
+            _ptr(out), out.numel(), _ptr(items), _ptr(results),
+            0 if results is None else results.numel(), _ptr(status), _stream(stream)),
+            "ranmar_batch_generate_mixed")
         return out
 
     def tune(self, states, desc, out, order=None, stream=None):

@@ -10,6 +10,15 @@
 
 namespace ranmar {
 
+// Checksums kept with the generation: item t (index0, result) applies to
+// descriptor t's outputs, which the group reads back from memory after
+// writing them (so the sum checks what was stored, as ranmar_checksum does).
+struct MixedSums {
+  const ranmar_sum_item_t* items;   // NULL: no checksums
+  unsigned long long* results;
+  uint64_t n_results;
+};
+
 // Descriptors [lo, hi) of one interleaved group (hi - lo <= S streams),
 // all of one output type.
 template <int W, int S, bool F32>
@@ -17,7 +26,7 @@ __device__ __forceinline__ void mixed_group(ranmar_state_t* __restrict__ states,
                                             const ranmar_desc_t* __restrict__ desc, uint64_t lo,
                                             uint64_t hi, void* out, uint64_t out_len,
                                             uint32_t* status, unsigned gl, unsigned gmask,
-                                            const LaneConsts& k) {
+                                            const LaneConsts& k, const MixedSums& sums) {
   ranmar_state_t* st[S];
   uint64_t cnt[S], ob[S];
   bool wb[S], ok[S];
@@ -37,6 +46,26 @@ __device__ __forceinline__ void mixed_group(ranmar_state_t* __restrict__ states,
     ok[s] = true;
   }
   generate_streams<W, F32, S, true>(st, cnt, out, ob, wb, ok, gl, gmask, k);
+  if (sums.items == nullptr) return;
+  __syncwarp(gmask);   // the group's stores are visible to the group
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    if (!ok[s]) continue;
+    const ranmar_sum_item_t it = sums.items[lo + s];
+    if (it.result >= sums.n_results) {
+      if (gl == 0) flag_status(status, RANMAR_ST_OUT_RANGE);
+      continue;
+    }
+    const uint32_t* p = static_cast<const uint32_t*>(out) + ob[s];
+    const unsigned long long w0 = 2ull * it.index0 + 1ull;
+    unsigned long long acc = 0;
+#pragma unroll 4
+    for (uint64_t i = gl; i < cnt[s]; i += W)
+      acc += static_cast<unsigned long long>(p[i]) * (w0 + 2ull * i);
+#pragma unroll
+    for (int d = W / 2; d > 0; d >>= 1) acc += __shfl_xor_sync(gmask, acc, d, W);
+    if (gl == 0) atomicAdd(&sums.results[it.result], acc);
+  }
 }
 
 // Groups of W lanes pull `chunk` descriptors at a time from an atomic queue
@@ -50,7 +79,8 @@ __global__ void __launch_bounds__(256, 2) generate_persistent_mixed_kernel(ranma
                                                  const ranmar_desc_t* __restrict__ desc,
                                                  uint64_t n_desc, uint64_t n_u24, void* out,
                                                  uint64_t out_len, uint32_t* status,
-                                                 unsigned long long* queue, uint32_t chunk) {
+                                                 unsigned long long* queue, uint32_t chunk,
+                                                 MixedSums sums) {
   const unsigned lane = threadIdx.x & 31;
   const unsigned gl = lane % W;
   const unsigned gbase = lane - gl;
@@ -69,10 +99,10 @@ __global__ void __launch_bounds__(256, 2) generate_persistent_mixed_kernel(ranma
       const uint64_t mid = min(max(t0, n_u24), hi);
       if (t0 < mid)
         mixed_group<W, S, false>(states, n_states, desc, t0, mid, out, out_len, status, gl, gmask,
-                                 k);
+                                 k, sums);
       if (mid < hi)
         mixed_group<W, S, true>(states, n_states, desc, mid, hi, out, out_len, status, gl, gmask,
-                                k);
+                                k, sums);
     }
   }
 }

@@ -426,7 +426,8 @@ int mixed_occupancy(int threads) {
 template <int W>
 int launch_mixed(ranmar_batch* b, const ranmar_batch_config_t& c, int T, ranmar_state_t* states,
                  size_t n_states, const ranmar_desc_t* desc, size_t n_desc, size_t n_u24,
-                 uint32_t* out, size_t out_len, uint32_t* status, cudaStream_t s) {
+                 uint32_t* out, size_t out_len, uint32_t* status, cudaStream_t s,
+                 const ranmar::MixedSums& sums) {
   constexpr int kIlp = ranmar::persistent_ilp<W>();
   const int occ1 = mixed_occupancy<W, 1>(T);
   const int per_sm1 = c.ctas_per_sm > 0 && c.ctas_per_sm < occ1 ? c.ctas_per_sm : occ1;
@@ -445,32 +446,32 @@ int launch_mixed(ranmar_batch* b, const ranmar_batch_config_t& c, int T, ranmar_
   if (e != cudaSuccess) return cuda_fail(e);
   if (one)
     ranmar::generate_persistent_mixed_kernel<W, 1><<<static_cast<unsigned>(grid), T, 0, s>>>(
-        states, n_states, desc, n_desc, n_u24, out, out_len, status, b->queue, c.chunk);
+        states, n_states, desc, n_desc, n_u24, out, out_len, status, b->queue, c.chunk, sums);
   else
     ranmar::generate_persistent_mixed_kernel<W, kIlp><<<static_cast<unsigned>(grid), T, 0, s>>>(
-        states, n_states, desc, n_desc, n_u24, out, out_len, status, b->queue, c.chunk);
+        states, n_states, desc, n_desc, n_u24, out, out_len, status, b->queue, c.chunk, sums);
   return check_launch();
 }
 
 int run_persistent_mixed(ranmar_batch* b, const ranmar_batch_config_t& c, ranmar_state_t* states,
                          size_t n_states, const ranmar_desc_t* desc, size_t n_desc,
                          size_t n_u24, uint32_t* out, size_t out_len, uint32_t* status,
-                         cudaStream_t s) {
+                         cudaStream_t s, const ranmar::MixedSums& sums) {
   // the kernel is compiled for at most 256 threads a CTA (two CTAs an SM)
   const int T = c.threads_per_cta < 256 ? c.threads_per_cta : 256;
   switch (c.lanes_per_stream) {
     case 32:
       return launch_mixed<32>(b, c, T, states, n_states, desc, n_desc, n_u24, out, out_len,
-                              status, s);
+                              status, s, sums);
     case 16:
       return launch_mixed<16>(b, c, T, states, n_states, desc, n_desc, n_u24, out, out_len,
-                              status, s);
+                              status, s, sums);
     case 8:
       return launch_mixed<8>(b, c, T, states, n_states, desc, n_desc, n_u24, out, out_len,
-                             status, s);
+                             status, s, sums);
     default:
       return launch_mixed<4>(b, c, T, states, n_states, desc, n_desc, n_u24, out, out_len,
-                             status, s);
+                             status, s, sums);
   }
 }
 
@@ -954,17 +955,22 @@ int ranmar_batch_generate_f32(ranmar_batch_t* b, ranmar_state_t* d_states, size_
 
 int ranmar_batch_generate_mixed(ranmar_batch_t* b, ranmar_state_t* d_states, size_t n_states,
                                 const ranmar_desc_t* d_desc, size_t n_desc, size_t n_u24,
-                                uint32_t* d_out, size_t out_len, uint32_t* d_status,
-                                ranmar_stream_t stream) {
+                                uint32_t* d_out, size_t out_len,
+                                const ranmar_sum_item_t* d_items, uint64_t* d_results,
+                                size_t n_results, uint32_t* d_status, ranmar_stream_t stream) {
   NvtxRange nvtx_("ranmar_batch_generate_mixed");
   if (!on_device(b)) return RANMAR_EINVAL;
   if (n_u24 > n_desc) return RANMAR_ERANGE;
   if (n_desc == 0) return RANMAR_OK;
-  if (!d_states || !d_desc || !d_out) return RANMAR_EINVAL;
+  if (!d_states || !d_desc || !d_out || (d_items && !d_results)) return RANMAR_EINVAL;
   if (n_states == 0) return RANMAR_ERANGE;
-  if (!aligned(d_states, 16) || !aligned(d_desc, 8) || !aligned(d_out, 4)) return RANMAR_EINVAL;
+  if (!aligned(d_states, 16) || !aligned(d_desc, 8) || !aligned(d_out, 4) ||
+      !aligned(d_items, 8) || !aligned(d_results, 8))
+    return RANMAR_EINVAL;
+  const ranmar::MixedSums sums{d_items, reinterpret_cast<unsigned long long*>(d_results),
+                               d_items ? n_results : 0};
   return run_persistent_mixed(b, b->cfg, d_states, n_states, d_desc, n_desc, n_u24, d_out,
-                              out_len, d_status, reinterpret_cast<cudaStream_t>(stream));
+                              out_len, d_status, reinterpret_cast<cudaStream_t>(stream), sums);
 }
 
 int ranmar_batch_tune(ranmar_batch_t* b, int f32, ranmar_state_t* d_states, size_t n_states,

@@ -527,7 +527,7 @@ int enqueue(ranmar_serve& e, Iter& it) {
   std::memset(h + o_res, 0, nreq * sizeof(uint64_t));
   it.res_off = o_res;
   const uint64_t seg = e.cfg.seg;
-  size_t ci = 0, cu = 0, cf = 0, cj = 0, cp = 0;
+  size_t cu = 0, cf = 0, cj = 0, cp = 0;
   for (uint32_t q = 0; q < nreq; ++q) {
     const Admitted& a = it.reqs[q];
     ranmar_request_t& r = e.reqs[a.req];
@@ -572,7 +572,7 @@ int enqueue(ranmar_serve& e, Iter& it) {
         df[cf++] = d;
       else
         du[cu++] = d;
-      items[ci++] = {a.region + js, cnt, js, q, 0u};
+      items[r.f32 ? nu + cf - 1 : cu - 1] = {a.region + js, cnt, js, q, 0u};   // desc order
       if (e.host_only) {
         tr.iteration = it.number;
         tr.request = a.req;
@@ -628,13 +628,13 @@ int enqueue(ranmar_serve& e, Iter& it) {
   rc = cuda_check(cudaEventRecord(st.ev_jumped, js));
   if (!rc) rc = cuda_check(cudaStreamWaitEvent(s, st.ev_jumped, 0));
   if (rc) return rc;
-  // both output types in one persistent launch
+  // both output types in one persistent launch, each segment's checksum
+  // summed by the group that generated it from the words it stored
   rc = ranmar_batch_generate_mixed(e.batch, e.pool, e.cfg.state_entries,
                                    reinterpret_cast<const ranmar_desc_t*>(d + o_du), ntot, nu,
-                                   e.out, e.out_words, e.status, rs);
-  if (rc) return rc;
-  rc = ranmar_checksum(e.out, e.out_words, reinterpret_cast<const ranmar_sum_item_t*>(d + o_items),
-                       ntot, reinterpret_cast<uint64_t*>(d + o_res), nreq, e.status, rs);
+                                   e.out, e.out_words,
+                                   reinterpret_cast<const ranmar_sum_item_t*>(d + o_items),
+                                   reinterpret_cast<uint64_t*>(d + o_res), nreq, e.status, rs);
   if (rc) return rc;
   rc = cuda_check(cudaMemcpyAsync(h + o_res, d + o_res, nreq * sizeof(uint64_t),
                                   cudaMemcpyDeviceToHost, s));

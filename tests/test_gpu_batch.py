@@ -125,8 +125,31 @@ def test_mixed_launch_equals_separate_calls(rm, dev, orc, lanes, threads, ctas, 
         assert int(status.item()) == 0
         assert torch.equal(out, out_ref), n_u24
         assert torch.equal(st, st_ref), n_u24
-    got = out.cpu().numpy()
+    # with the checksums kept by the launch: each descriptor's words, read
+    # back after they are stored, into its slot (three descriptors a slot)
+    idx0 = (np.arange(n) * 7919) % 100_003
+    items = torch.tensor(np.stack([np.zeros(n), c, idx0, np.arange(n) // 3], 1).astype(np.int64),
+                         device=dev)
+    sums = torch.zeros((n + 2) // 3, dtype=torch.int64, device=dev)
+    st3 = states0.clone()
+    out3 = torch.full_like(out_ref, -1)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    b.generate_mixed(st3, desc, 351, out3, items=items, results=sums, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref_out = torch.full_like(out_ref, -1)
+    st_ref = states0.clone()
+    rm.generate_u24(st_ref, desc[:351], ref_out)
+    rm.generate_f32(st_ref, desc[351:], ref_out.view(torch.float32))
+    assert torch.equal(out3, ref_out) and torch.equal(st3, st_ref)
+    words = ref_out.cpu().numpy().view(np.uint32)
     offs = np.concatenate([[0], np.cumsum(c)[:-1]])
+    want = [0] * sums.numel()
+    for i in range(n):
+        want[i // 3] = (want[i // 3] + rm.checksum_np(words[offs[i]:offs[i] + c[i]],
+                                                      index0=int(idx0[i]))) % (1 << 64)
+    assert [int(x) for x in sums.cpu().numpy().astype(np.uint64)] == want
+    got = out.cpu().numpy()
     for i in [0, 349, 350, n - 1]:         # n_u24 = n: all u24
         ref = orc.stream(4242, i * J, int(c[i]))
         assert np.array_equal(got[offs[i]:offs[i] + c[i]].view(np.uint32), ref), i
