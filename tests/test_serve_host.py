@@ -448,3 +448,20 @@ def test_native_scheduler_follows_the_model(bd, entries, max_inflight, max_segs)
     assert st["resumed"] > 0
     if entries <= 64:
         assert st["evicted"] > 0
+
+
+def test_request_records_with_long_streams(bd):
+    """J of 2^64 and more splits over the record's two words; offsets group
+    by the whole key; a request is overlapping only when it runs past J."""
+    J = (1 << 100) + 3
+    a = serve.requests_array([0.0, 0.1, 0.2], [5, 5, 5], [(1 << 63) + 1, (1 << 63) + 1, 2],
+                             [10, 20, 30], [False, True, False], J)
+    assert [int(x) for x in a["J"][:, 0]] == [3] * 3 and [int(x) for x in a["J"][:, 1]] == [1 << 36] * 3
+    assert [int(x) for x in a["offset"]] == [0, 10, 0]
+    a["status"] = bd.REQ_DONE
+    a["done"] = a["t"] + 1e-3
+    assert serve.summarize_array(a)["overlapping_requests"] == 0
+    b = serve.requests_array([0.0, 0.1], [5, 5], [0, 0], [60, 50], [False, False], 100)
+    b["status"] = bd.REQ_DONE
+    b["done"] = b["t"] + 1e-3
+    assert serve.summarize_array(b)["overlapping_requests"] == 1     # 60 + 50 > 100
