@@ -60,6 +60,7 @@ constexpr double kSlowLoopSeconds = 0.01;       // a loop turn longer than this 
 // request that arrives meanwhile.
 constexpr double kSpinSeconds = 2e-3;
 constexpr size_t kPlainRing = 1024;             // plain-mode requests in flight at most
+constexpr size_t kFusedSumsMax = 4096;          // segments an iteration sums inside its generation
 
 static_assert(sizeof(ranmar_request_t) == 88, "request layout");
 static_assert(sizeof(ranmar_serve_seg_t) == 72, "trace layout");
@@ -628,13 +629,21 @@ int enqueue(ranmar_serve& e, Iter& it) {
   rc = cuda_check(cudaEventRecord(st.ev_jumped, js));
   if (!rc) rc = cuda_check(cudaStreamWaitEvent(s, st.ev_jumped, 0));
   if (rc) return rc;
-  // both output types in one persistent launch, each segment's checksum
-  // summed by the group that generated it from the words it stored
+  // Both output types in one persistent launch.  In an iteration of up to
+  // kFusedSumsMax segments (a warp per segment) each segment's checksum is
+  // summed by the warp that generated it, from the words it stored: one
+  // launch fewer on the latency path.  A larger iteration, whose generation
+  // interleaves several segments per warp, sums faster in the separate
+  // checksum kernel.
+  const auto* sum_items = reinterpret_cast<const ranmar_sum_item_t*>(d + o_items);
+  auto* sums = reinterpret_cast<uint64_t*>(d + o_res);
+  const bool fused = ntot <= kFusedSumsMax;
   rc = ranmar_batch_generate_mixed(e.batch, e.pool, e.cfg.state_entries,
                                    reinterpret_cast<const ranmar_desc_t*>(d + o_du), ntot, nu,
-                                   e.out, e.out_words,
-                                   reinterpret_cast<const ranmar_sum_item_t*>(d + o_items),
-                                   reinterpret_cast<uint64_t*>(d + o_res), nreq, e.status, rs);
+                                   e.out, e.out_words, fused ? sum_items : nullptr,
+                                   fused ? sums : nullptr, nreq, e.status, rs);
+  if (!rc && !fused)
+    rc = ranmar_checksum(e.out, e.out_words, sum_items, ntot, sums, nreq, e.status, rs);
   if (rc) return rc;
   rc = cuda_check(cudaMemcpyAsync(h + o_res, d + o_res, nreq * sizeof(uint64_t),
                                   cudaMemcpyDeviceToHost, s));

@@ -186,3 +186,22 @@ def test_serving_iterations_overlap_on_the_device(rm, orc):
     assert st["max_inflight"] >= 2 and st["iterations"] > 10
     check_all(orc, rm, reqs)
     eng.close()
+
+
+def test_serving_large_iterations_sum_separately(rm, orc):
+    """Iterations of more than 4,096 segments take the separate checksum
+    kernel instead of the sums inside the generation: checksums still equal
+    the oracle's."""
+    from paper_2512_00093_gb300.serve import Engine, make_requests
+    rng = np.random.default_rng(41)
+    n = 12
+    t = np.zeros(n)
+    sd, k = rng.integers(1, 4, n), rng.integers(0, 50, n)
+    c = rng.integers(150_000, 250_000, n)
+    reqs = make_requests(t, sd, k, c, rng.random(n) < 0.5, J48)
+    eng = Engine(budget_bytes=64 << 20, seg=64, state_entries=16384, max_segments_per_iter=8192)
+    eng.run(reqs, realtime=False)
+    st = eng.stats
+    eng.close()
+    assert st["segments"] / st["iterations"] > 4096
+    check_all(orc, rm, reqs)
