@@ -805,9 +805,11 @@ int ranmar_checksum(const uint32_t *d_data, size_t data_len,
  *     states (from the seeded state by k J + offset + j seg, or from the
  *     resident state by j seg; Sec. 3.1 / 3.2);
  *   - then on the caller's stream: one persistent generation of all
- *     segments (ranmar_batch_generate_mixed), ranmar_checksum of every
- *     request's outputs (the outputs are consumed on the device; their
- *     region is then recycled), and the copy of the checksums back.
+ *     segments (ranmar_batch_generate_mixed) with the checksum of every
+ *     request's outputs (summed inside that launch from the stored words,
+ *     or by ranmar_checksum after it for an iteration of more than 4,096
+ *     segments; the outputs are consumed on the device and their region is
+ *     then recycled), and the copy of the checksums back.
  * An iteration's jumps thus run while earlier iterations generate.  Up to
  * max_inflight iterations are on the device while the host builds the next.
  * Unlike the calls above, an engine owns device memory (budget_bytes + 400
